@@ -1,0 +1,235 @@
+/*
+ * libidmrg -- parallel infinite-size DMRG (Hida's iDMRG for l-site unit cells
+ * with a variant of McCulloch's wavefunction prediction) on one GB300 GPU.
+ *
+ * Problem statement (Ueda, Sec. 3): a Hamiltonian with an l-site period,
+ * given as the matrix product operator W_1 .. W_l of Eq. mpo2, and the number
+ * m of block states kept.  One parallel iteration n (a "unit-cell step")
+ * solves the l/2 superblocks H^(n)_i = L^(n-1)_{2i-1} W W R^(n-1)_{2i+2}
+ * (Step 2'), starting from the predicted wavefunction of Eq. wfprediction
+ * (Step 3'), splits each ground state by SVD (Step 4), renormalises the
+ * blocks (Step 6) and estimates the energy per site (Step 5').
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Superblocks are numbered p = 0 .. l/2-1 (the paper's i = p+1); p = -1
+ *    means "all superblocks" wherever it is accepted.  Sites are 0-based.
+ *  - Charges are integers 2 S^z.
+ *  - Device pointers are borrowed for the duration of the stream-ordered call;
+ *    host pointers are read or written before the call returns.
+ *  - Every call returns an idmrg_status and never aborts or throws.  Out
+ *    parameters are written only on IDMRG_OK, except IDMRG_ENOCONV, which
+ *    still writes the best estimate.  idmrg_last_error() gives a message.
+ *  - The library allocates device memory only through the idmrg_allocator
+ *    given to idmrg_create (cudaMalloc when none is given), and only between
+ *    kernels of a step, never inside a captured region.
+ */
+#ifndef IDMRG_H
+#define IDMRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IDMRG_OK = 0,
+  IDMRG_EINVAL = 1,   /* bad argument or invalid MPO                         */
+  IDMRG_ENOMEM = 2,   /* the allocator returned NULL                         */
+  IDMRG_ECUDA = 3,    /* a CUDA runtime call failed                           */
+  IDMRG_ENOCONV = 4,  /* Lanczos hit lanczos_maxit; best estimate written    */
+  IDMRG_ETIMEOUT = 5, /* a device-side wait ran out of its iteration budget  */
+  IDMRG_ENUMERIC = 6, /* NaN/Inf in a Lanczos coefficient, or SVD failure    */
+  IDMRG_ESTATE = 7    /* calls made in the wrong order for this iteration    */
+} idmrg_status;
+
+/* Arithmetic of the H_eff psi and environment contractions.  The Lanczos
+ * recurrence, re-orthogonalisation, tridiagonal eigensolve and the SVD are
+ * FP64 in every mode. */
+typedef enum {
+  IDMRG_FP64 = 0,    /* FP64 everywhere                                       */
+  IDMRG_TF32X3 = 1,  /* tensor cores, TF32 split (hi/lo) operands, three
+                        products per term, FP32 accumulation; energies refined
+                        by an FP64 Rayleigh quotient                          */
+  IDMRG_BF16X3 = 2   /* as TF32X3 with BF16 splits                           */
+} idmrg_precision;
+
+/* The MPO of one period (Sec. 2, Eq. mpo; Sec. 3, Eq. mpo2).  Host memory,
+ * caller-owned, copied by idmrg_create.  Site k (0-based) holds
+ * W_k[a][b][s][t] = <s| W_k(a,b) |t>, a < bond_dim[k], b < bond_dim[k+1],
+ * stored row-major and concatenated site after site.  Channel 0 of every bond
+ * is "term completed" and the last channel "identity": W_k(0,0) and
+ * W_k(last,last) are the unit matrix, row 0 and the last column hold nothing
+ * else (lower-triangular form; L_k is the last row and R_k the first column of
+ * W_k).  bond_charge holds the 2Sz carried by each channel, bond by bond
+ * (bond k = the bond to the left of site k, bond_dim[k] entries).  A non-zero
+ * W_k(a,b) entry <s|.|t> must satisfy
+ *   phys_charge[s] - phys_charge[t] == charge(bond k+1, b) - charge(bond k, a).
+ * Violations return IDMRG_EINVAL. */
+typedef struct {
+  int ell;                  /* period l, even, >= 2                           */
+  int d;                    /* local dimension                                */
+  const int *bond_dim;      /* l+1 entries, bond_dim[l] == bond_dim[0]       */
+  const double *W;          /* sum_k a_k a_{k+1} d^2 doubles                 */
+  const int *phys_charge;   /* d entries                                      */
+  const int *bond_charge;   /* sum_{k<l} a_k entries                          */
+} idmrg_mpo;
+
+typedef struct {
+  int m;                    /* kept states per block (Step 6)                 */
+  int target_charge;        /* 2Sz of every superblock ground state (0)       */
+  double lanczos_tol;       /* stop when |b_k y_k| <= tol max(1,|theta|)      */
+  int lanczos_maxit;        /* Krylov dimension cap, 2..600 (sizes memory)    */
+  idmrg_precision prec;
+  int predict;              /* 1: Eq. wfprediction for n >= 3; 0: random      */
+  uint64_t seed;            /* SplitMix64 seed of the random start vectors    */
+  double lambda_zero_rel;   /* lambda <= this * lambda_max counts as zero     */
+  double tie_rel;           /* never cut between lambda_k, lambda_k+1 closer
+                               than this relative gap (multiplets stay whole) */
+} idmrg_opts;
+
+/* Device memory provider.  alloc returns a device pointer aligned to at least
+ * 256 bytes or NULL; free releases it (bytes is the size asked for). */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *user);
+  void (*free)(void *ptr, size_t bytes, void *user);
+  void *user;
+} idmrg_allocator;
+
+/* Per-iteration report.  Every array is caller-owned host memory of l/2
+ * entries and may be NULL. */
+typedef struct {
+  int n;                    /* the iteration just completed                   */
+  double *energy;           /* e^(n)_i, Step 3 (FP64-refined in mixed modes)  */
+  int *iters;               /* Lanczos matvecs                                */
+  double *eps;              /* Eq. tru, truncation error                      */
+  double *eps_best;         /* Eq. fid2, best fidelity error                  */
+  double *fidelity;         /* Eq. fid1 (NaN when no prediction was used)     */
+  double *bond;             /* <psi| h(c1,c2) |psi>, centre-bond energy       */
+  int *kept;                /* states kept                                    */
+  double e_g;               /* Step 5' estimate, NaN unless (n+1) mod l == 0  */
+} idmrg_step_report;
+
+typedef struct idmrg_ctx idmrg_ctx;
+
+/* Defaults: m = 64, target 0, tol 1e-12, maxit 300, FP64, prediction on,
+ * seed 0, lambda_zero_rel 1e-12, tie_rel 1e-10. */
+void idmrg_default_opts(idmrg_opts *opts);
+
+/* Step 1: validates the MPO, builds L^(0) (last row of W at site 2p) and
+ * R^(0) (first column of W at site 2p+1) for every pair and sets n = 1.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
+ * later call is ordered.  alloc may be NULL (cudaMalloc/cudaFree). */
+idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cuda_stream,
+                          const idmrg_allocator *alloc, idmrg_ctx **out);
+void idmrg_destroy(idmrg_ctx *ctx);
+const char *idmrg_last_error(const idmrg_ctx *ctx);
+idmrg_status idmrg_set_stream(idmrg_ctx *ctx, void *cuda_stream);
+
+/* Current iteration n (the one the next unit-cell step performs). */
+idmrg_status idmrg_iteration(const idmrg_ctx *ctx, int *n);
+
+/* Layout of superblock p's wavefunction at the current iteration (Step 3):
+ * psi[x][s][t][y] for left block state x, sites c1 (s) and c2 (t), right block
+ * state y, stored as dense sub-blocks of fixed (left sector, s, t); only
+ * sub-blocks whose charges add up to target_charge exist.  Each sub-block is
+ * described by 8 ints:
+ *   {x0, Dx, s, t, y0, Dy, offset, row_stride}
+ * x0/y0 = first basis index of the left/right sector, Dx/Dy its size, element
+ * (x0+i, s, t, y0+j) at offset + i*row_stride + j.  *nelem = vector length. */
+idmrg_status idmrg_psi_layout(const idmrg_ctx *ctx, int p, int *desc, int cap_blocks,
+                              int *nblocks, size_t *nelem);
+
+/* Basis of a block of superblock p at the current iteration: side 0 = left
+ * block L^(n-1) of pair p, side 1 = right block R^(n-1) of pair p+1.  Writes
+ * the 2Sz of each state (dense basis order), its MPO channel count and size. */
+idmrg_status idmrg_block_basis(const idmrg_ctx *ctx, int p, int side, int *charges, int cap,
+                               int *dim, int *channels);
+
+/* Copies that block's operators to host memory as dense [channels][D][D]
+ * (<x| O_a |y>, zeros outside its charge blocks), in FP64. */
+idmrg_status idmrg_block_to_host(const idmrg_ctx *ctx, int p, int side, double *host, size_t cap);
+
+/* Step 3 matvec: out = H^(n)_p psi with H = L W_{c1} W_{c2} R, both device
+ * vectors in the idmrg_psi_layout of p (p >= 0), or all superblocks' vectors
+ * concatenated in order p = 0 .. l/2-1 (p = -1).  Uses the arithmetic of
+ * opts.prec.  Valid from idmrg_create / idmrg_advance until the next
+ * idmrg_advance. */
+idmrg_status idmrg_heff_apply(idmrg_ctx *ctx, int p, const double *psi_dev, double *out_dev);
+
+/* Step 3': start vector of superblock p (or all): Eq. wfprediction for
+ * n >= 3 when opts.predict, else SplitMix64 numbers in [-1,1) on the target
+ * sector.  Writes ||psi~|| if norm_out != NULL (host, l/2 entries for p=-1). */
+idmrg_status idmrg_predict_wavefunction(idmrg_ctx *ctx, int p, double *norm_out);
+
+/* Step 3 solve by FP64 Lanczos with full re-orthogonalisation.  All
+ * requested superblocks are solved together, matvecs batched.  e_out and
+ * iters_out: host, one entry (p >= 0) or l/2 entries (p = -1). */
+idmrg_status idmrg_lanczos_solve(idmrg_ctx *ctx, int p, double *e_out, int *iters_out);
+
+/* Copies the Lanczos ground state of superblock p to host (layout as above). */
+idmrg_status idmrg_get_psi(const idmrg_ctx *ctx, int p, double *host, size_t cap);
+
+/* Step 4 + truncation of Step 6: FP64 SVD per charge sector, descending
+ * singular values, cut at <= m without splitting near-equal values.  Host
+ * outputs (one or l/2 entries, each may be NULL): eps (Eq. tru), eps_best
+ * (Eq. fid2), states kept. */
+idmrg_status idmrg_truncate(idmrg_ctx *ctx, int p, double *eps_out, double *eps_best_out,
+                            int *kept_out);
+
+/* All singular values of superblock p's last truncation, descending. */
+idmrg_status idmrg_get_lambda(const idmrg_ctx *ctx, int p, double *host, int cap, int *len);
+
+/* Step 6: L^(n) = u^T (L^(n-1) W_{c1}) u and R^(n) = v^T (W_{c2} R^(n-1)) v
+ * (Eqs. L, R) for pair p (or all). */
+idmrg_status idmrg_update_environments(idmrg_ctx *ctx, int p);
+
+/* Step 7 with the rotation of Step 2': R^(n) of pair p+1 becomes the right
+ * block of superblock p; n -> n+1.  Requires every pair to be updated. */
+idmrg_status idmrg_advance(idmrg_ctx *ctx);
+
+/* One parallel iteration: predict, solve, truncate, update, advance, for all
+ * superblocks.  rep may be NULL. */
+idmrg_status idmrg_unit_cell_step(idmrg_ctx *ctx, idmrg_step_report *rep);
+
+/* Step 5': latest e_g = (e^(n)_1 - e^(n-l)_1) / 2l with (n+1) mod l == 0
+ * (e^(-1)_1 = 0) and the n it belongs to; ESTATE if there is none yet. */
+idmrg_status idmrg_energy_per_site(const idmrg_ctx *ctx, double *e_g, int *n_of_estimate);
+
+/* Measured work of the last heff_apply call: algorithmic flops (sum over
+ * GEMM tasks of 2 M N K plus 2 per element per two-site MPO term) and the
+ * bytes of L, R, psi in and out. */
+idmrg_status idmrg_heff_cost(const idmrg_ctx *ctx, int p, double *flops, double *bytes);
+
+/* Kernel launches this context has issued so far (for accounting). */
+idmrg_status idmrg_launch_count(const idmrg_ctx *ctx, uint64_t *count);
+
+/* Device timers per kernel class: when enabled, every launch of the class is
+ * bracketed by CUDA events on the context's stream; idmrg_profile_read
+ * synchronises and returns the summed device time, the number of launches and
+ * the algorithmic flops and bytes of those launches (flops: 2 M N K per GEMM
+ * task of the superblocks that were active, 2 per element per MPO term;
+ * bytes: operands read once and results written once).  Enabling resets. */
+typedef enum {
+  IDMRG_K_HEFF_GEMM = 0,   /* H_eff psi stages L.psi and T3.R^T (Step 3)       */
+  IDMRG_K_HEFF_WSTAGE = 1, /* H_eff psi two-site MPO stage (Step 3)            */
+  IDMRG_K_LANCZOS_VEC = 2, /* Gram-Schmidt projections and updates (Step 3)   */
+  IDMRG_K_LANCZOS_TRI = 3, /* tridiagonal eigensolve and convergence (Step 3) */
+  IDMRG_K_SVD = 4,         /* sector SVD, selection, compaction (Step 4)       */
+  IDMRG_K_ENV = 5,         /* block-spin transformation (Step 6)               */
+  IDMRG_K_PREDICT = 6,     /* start vectors (Step 3')                          */
+  IDMRG_K_COUNT = 7
+} idmrg_kernel_class;
+idmrg_status idmrg_profile_enable(idmrg_ctx *ctx, int on);
+idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t *launches, double *flops,
+                                double *bytes);
+
+/* Bytes this context has copied host->device and device->host so far. */
+idmrg_status idmrg_transfer_bytes(const idmrg_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IDMRG_H */

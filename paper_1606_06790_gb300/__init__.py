@@ -1,0 +1,343 @@
+"""Python binding of libidmrg (include/idmrg.h): argument marshalling only.
+
+Every step of the iDMRG hot path runs in the CUDA kernels of the shared
+library; this module converts Python/torch objects to the C ABI's pointers and
+sizes.  PyTorch provides device memory (through the caching allocator, handed
+to the library as an ``idmrg_allocator``) and the CUDA stream.  There is no CPU
+fallback: if libidmrg.so is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+__all__ = ["load_library", "Context", "STATUS", "PREC", "EXPORTED_SYMBOLS", "IdmrgError"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libidmrg.so")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ENUMERIC",
+          7: "ESTATE"}
+PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+
+EXPORTED_SYMBOLS = [
+    "idmrg_default_opts", "idmrg_create", "idmrg_destroy", "idmrg_last_error", "idmrg_set_stream",
+    "idmrg_iteration", "idmrg_psi_layout", "idmrg_block_basis", "idmrg_block_to_host",
+    "idmrg_heff_apply", "idmrg_predict_wavefunction", "idmrg_lanczos_solve", "idmrg_get_psi",
+    "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
+    "idmrg_unit_cell_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
+    "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes",
+]
+
+KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
+                  "predict": 6}
+
+
+class IdmrgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _MPO(C.Structure):
+    _fields_ = [("ell", C.c_int), ("d", C.c_int), ("bond_dim", C.POINTER(C.c_int)),
+                ("W", C.POINTER(C.c_double)), ("phys_charge", C.POINTER(C.c_int)),
+                ("bond_charge", C.POINTER(C.c_int))]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("m", C.c_int), ("target_charge", C.c_int), ("lanczos_tol", C.c_double),
+                ("lanczos_maxit", C.c_int), ("prec", C.c_int), ("predict", C.c_int),
+                ("seed", C.c_uint64), ("lambda_zero_rel", C.c_double), ("tie_rel", C.c_double)]
+
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class _Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC), ("free", _FREE), ("user", C.c_void_p)]
+
+
+class _Report(C.Structure):
+    _fields_ = [("n", C.c_int), ("energy", C.POINTER(C.c_double)), ("iters", C.POINTER(C.c_int)),
+                ("eps", C.POINTER(C.c_double)), ("eps_best", C.POINTER(C.c_double)),
+                ("fidelity", C.POINTER(C.c_double)), ("bond", C.POINTER(C.c_double)),
+                ("kept", C.POINTER(C.c_int)), ("e_g", C.c_double)]
+
+
+_lib_handle = None
+
+
+def load_library(path: Optional[str] = None) -> C.CDLL:
+    """Load libidmrg.so (built by ``paper_1606_06790_gb300.build``); raises if absent."""
+    global _lib_handle
+    if _lib_handle is not None and path is None:
+        return _lib_handle
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libidmrg.so not found at {p}: run __graft_entry__.build() first "
+                          "(the iDMRG path has no CPU fallback)")
+    lib = C.CDLL(p)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    P = C.POINTER
+    sig = {
+        "idmrg_default_opts": (None, [P(_Opts)]),
+        "idmrg_create": (i, [P(_MPO), P(_Opts), vp, P(_Allocator), P(vp)]),
+        "idmrg_destroy": (None, [vp]),
+        "idmrg_last_error": (C.c_char_p, [vp]),
+        "idmrg_set_stream": (i, [vp, vp]),
+        "idmrg_iteration": (i, [vp, P(i)]),
+        "idmrg_psi_layout": (i, [vp, i, P(i), i, P(i), P(sz)]),
+        "idmrg_block_basis": (i, [vp, i, i, P(i), i, P(i), P(i)]),
+        "idmrg_block_to_host": (i, [vp, i, i, P(d), sz]),
+        "idmrg_heff_apply": (i, [vp, i, vp, vp]),
+        "idmrg_predict_wavefunction": (i, [vp, i, P(d)]),
+        "idmrg_lanczos_solve": (i, [vp, i, P(d), P(i)]),
+        "idmrg_get_psi": (i, [vp, i, P(d), sz]),
+        "idmrg_truncate": (i, [vp, i, P(d), P(d), P(i)]),
+        "idmrg_get_lambda": (i, [vp, i, P(d), i, P(i)]),
+        "idmrg_update_environments": (i, [vp, i]),
+        "idmrg_advance": (i, [vp]),
+        "idmrg_unit_cell_step": (i, [vp, P(_Report)]),
+        "idmrg_energy_per_site": (i, [vp, P(d), P(i)]),
+        "idmrg_heff_cost": (i, [vp, i, P(d), P(d)]),
+        "idmrg_launch_count": (i, [vp, P(C.c_uint64)]),
+        "idmrg_profile_enable": (i, [vp, i]),
+        "idmrg_profile_read": (i, [vp, i, P(d), P(C.c_uint64), P(d), P(d)]),
+        "idmrg_transfer_bytes": (i, [vp, P(C.c_uint64), P(C.c_uint64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib_handle = lib
+    return lib
+
+
+def _dptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class Context:
+    """One parallel-iDMRG problem on the current CUDA device (see include/idmrg.h).
+
+    ``W`` are the site tensors of one period ([a_k, a_{k+1}, d, d] each),
+    ``phys_charge`` the 2Sz of the local states, ``bond_charge`` one int array
+    per bond (bond k = left of site k)."""
+
+    def __init__(self, W: Sequence[np.ndarray], phys_charge, bond_charge: Sequence[np.ndarray], m: int,
+                 prec: str = "fp64", lanczos_tol: float = 1e-12, lanczos_maxit: int = 300,
+                 predict: bool = True, seed: int = 0, lambda_zero_rel: float = 1e-12,
+                 tie_rel: float = 1e-10, target_charge: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self._torch = torch
+        self.lib = load_library()
+        self.ell = len(W)
+        self.P = self.ell // 2
+        self.d = int(np.asarray(W[0]).shape[2])
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        dims = np.array([w.shape[0] for w in W] + [W[0].shape[0]], dtype=np.int32)
+        self._W = np.ascontiguousarray(np.concatenate([np.asarray(w, dtype=np.float64).ravel() for w in W]))
+        self._dims = dims
+        self._qp = np.ascontiguousarray(np.asarray(phys_charge, dtype=np.int32))
+        self._bq = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.int32) for b in bond_charge]))
+        mpo = _MPO(self.ell, self.d, _dptr(dims, C.c_int), _dptr(self._W, C.c_double),
+                   _dptr(self._qp, C.c_int), _dptr(self._bq, C.c_int))
+        o = _Opts()
+        self.lib.idmrg_default_opts(C.byref(o))
+        o.m, o.target_charge, o.lanczos_tol, o.lanczos_maxit = m, target_charge, lanczos_tol, lanczos_maxit
+        o.prec, o.predict, o.seed = PREC[prec], int(bool(predict)), seed
+        o.lambda_zero_rel, o.tie_rel = lambda_zero_rel, tie_rel
+        self.opts = o
+        self.prec = prec
+        # torch caching allocator as the library's device memory provider
+        dev, st = self.device, self.stream
+
+        def _alloc(nbytes, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=st)
+            except Exception:  # out of memory -> NULL -> IDMRG_ENOMEM
+                return None
+
+        def _free(ptr, nbytes, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb = (_ALLOC(_alloc), _FREE(_free))
+        self._alloc = _Allocator(self._cb[0], self._cb[1], None)
+        h = C.c_void_p()
+        s = self.lib.idmrg_create(C.byref(mpo), C.byref(o), C.c_void_p(self.stream.cuda_stream),
+                                  C.byref(self._alloc), C.byref(h))
+        if s != 0:
+            raise IdmrgError(s, "idmrg_create failed (invalid MPO or options, or no device memory)")
+        self.h = h
+
+    # ------------------------------------------------------------ helpers
+    def _check(self, s: int, what: str, ok=(0,)):
+        if s not in ok:
+            raise IdmrgError(s, f"{what}: {self.lib.idmrg_last_error(self.h).decode()}")
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.idmrg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _n_of(self, p: int) -> int:
+        return self.P if p < 0 else 1
+
+    # ------------------------------------------------------------ queries
+    @property
+    def iteration(self) -> int:
+        n = C.c_int()
+        self._check(self.lib.idmrg_iteration(self.h, C.byref(n)), "iteration")
+        return n.value
+
+    def psi_layout(self, p: int):
+        """(descriptor array [nblocks, 8], vector length); see idmrg_psi_layout."""
+        nb, ne = C.c_int(), C.c_size_t()
+        self._check(self.lib.idmrg_psi_layout(self.h, p, None, 0, C.byref(nb), C.byref(ne)), "psi_layout")
+        desc = np.zeros((max(nb.value, 1), 8), dtype=np.int32)
+        self._check(self.lib.idmrg_psi_layout(self.h, p, _dptr(desc, C.c_int), nb.value, C.byref(nb),
+                                              C.byref(ne)), "psi_layout")
+        return desc[: nb.value], ne.value
+
+    def block_basis(self, p: int, side: int):
+        D, w = C.c_int(), C.c_int()
+        self._check(self.lib.idmrg_block_basis(self.h, p, side, None, 0, C.byref(D), C.byref(w)), "block_basis")
+        q = np.zeros(max(D.value, 1), dtype=np.int32)
+        self._check(self.lib.idmrg_block_basis(self.h, p, side, _dptr(q, C.c_int), D.value, C.byref(D),
+                                               C.byref(w)), "block_basis")
+        return q[: D.value], w.value
+
+    def block_to_host(self, p: int, side: int) -> np.ndarray:
+        q, w = self.block_basis(p, side)
+        D = len(q)
+        out = np.zeros((w, D, D))
+        self._check(self.lib.idmrg_block_to_host(self.h, p, side, _dptr(out, C.c_double), out.size),
+                    "block_to_host")
+        return out
+
+    # ------------------------------------------------------------ steps
+    def heff_apply(self, p: int, psi, out) -> None:
+        """out = H_eff psi; psi/out are float64 CUDA tensors in the layout of p."""
+        self._check(self.lib.idmrg_heff_apply(self.h, p, C.c_void_p(psi.data_ptr()), C.c_void_p(out.data_ptr())),
+                    "heff_apply")
+
+    def predict_wavefunction(self, p: int = -1) -> np.ndarray:
+        out = np.zeros(self._n_of(p))
+        self._check(self.lib.idmrg_predict_wavefunction(self.h, p, _dptr(out, C.c_double)), "predict_wavefunction")
+        return out
+
+    def lanczos_solve(self, p: int = -1):
+        e = np.zeros(self._n_of(p))
+        it = np.zeros(self._n_of(p), dtype=np.int32)
+        s = self._check(self.lib.idmrg_lanczos_solve(self.h, p, _dptr(e, C.c_double), _dptr(it, C.c_int)),
+                        "lanczos_solve", ok=(0, 4))
+        return e, it, s == 0
+
+    def get_psi(self, p: int) -> np.ndarray:
+        _, N = self.psi_layout(p)
+        out = np.zeros(N)
+        self._check(self.lib.idmrg_get_psi(self.h, p, _dptr(out, C.c_double), N), "get_psi")
+        return out
+
+    def truncate(self, p: int = -1):
+        k = self._n_of(p)
+        eps, epsb, kept = np.zeros(k), np.zeros(k), np.zeros(k, dtype=np.int32)
+        self._check(self.lib.idmrg_truncate(self.h, p, _dptr(eps, C.c_double), _dptr(epsb, C.c_double),
+                                            _dptr(kept, C.c_int)), "truncate")
+        return eps, epsb, kept
+
+    def get_lambda(self, p: int) -> np.ndarray:
+        n = C.c_int()
+        self._check(self.lib.idmrg_get_lambda(self.h, p, None, 0, C.byref(n)), "get_lambda")
+        out = np.zeros(max(n.value, 1))
+        self._check(self.lib.idmrg_get_lambda(self.h, p, _dptr(out, C.c_double), n.value, C.byref(n)),
+                    "get_lambda")
+        return out[: n.value]
+
+    def update_environments(self, p: int = -1) -> None:
+        self._check(self.lib.idmrg_update_environments(self.h, p), "update_environments")
+
+    def advance(self) -> None:
+        self._check(self.lib.idmrg_advance(self.h), "advance")
+
+    def unit_cell_step(self) -> Dict[str, object]:
+        P = self.P
+        arr = {k: np.zeros(P) for k in ("energy", "eps", "eps_best", "fidelity", "bond")}
+        iarr = {k: np.zeros(P, dtype=np.int32) for k in ("iters", "kept")}
+        rep = _Report(0, _dptr(arr["energy"], C.c_double), _dptr(iarr["iters"], C.c_int),
+                      _dptr(arr["eps"], C.c_double), _dptr(arr["eps_best"], C.c_double),
+                      _dptr(arr["fidelity"], C.c_double), _dptr(arr["bond"], C.c_double),
+                      _dptr(iarr["kept"], C.c_int), float("nan"))
+        s = self._check(self.lib.idmrg_unit_cell_step(self.h, C.byref(rep)), "unit_cell_step", ok=(0, 4))
+        out: Dict[str, object] = dict(n=rep.n, converged=(s == 0), **arr, **iarr)
+        out["e_g"] = None if math.isnan(rep.e_g) else rep.e_g
+        return out
+
+    def energy_per_site(self):
+        e, n = C.c_double(), C.c_int()
+        s = self.lib.idmrg_energy_per_site(self.h, C.byref(e), C.byref(n))
+        return (e.value, n.value) if s == 0 else (None, None)
+
+    def heff_cost(self, p: int = -1):
+        f, b = C.c_double(), C.c_double()
+        self._check(self.lib.idmrg_heff_cost(self.h, p, C.byref(f), C.byref(b)), "heff_cost")
+        return f.value, b.value
+
+    def launch_count(self) -> int:
+        n = C.c_uint64()
+        self._check(self.lib.idmrg_launch_count(self.h, C.byref(n)), "launch_count")
+        return int(n.value)
+
+    def profile_enable(self, on: bool = True) -> None:
+        self._check(self.lib.idmrg_profile_enable(self.h, int(on)), "profile_enable")
+
+    def profile_read(self) -> Dict[str, Dict[str, float]]:
+        """Per kernel class: device ms, launches, algorithmic flops and bytes."""
+        out = {}
+        for name, k in KERNEL_CLASSES.items():
+            ms, n, f, b = C.c_double(), C.c_uint64(), C.c_double(), C.c_double()
+            self._check(self.lib.idmrg_profile_read(self.h, k, C.byref(ms), C.byref(n), C.byref(f), C.byref(b)),
+                        "profile_read")
+            out[name] = dict(ms=ms.value, launches=int(n.value), flops=f.value, bytes=b.value)
+        return out
+
+    def transfer_bytes(self):
+        a, b = C.c_uint64(), C.c_uint64()
+        self._check(self.lib.idmrg_transfer_bytes(self.h, C.byref(a), C.byref(b)), "transfer_bytes")
+        return int(a.value), int(b.value)
+
+
+def layout_pack(desc: np.ndarray, N: int, dense: np.ndarray) -> np.ndarray:
+    """Copy a dense psi[x, s, t, y] into the library's block layout (data movement only)."""
+    out = np.zeros(N)
+    for x0, Dx, s, t, y0, Dy, off, ld in desc:
+        blk = dense[x0:x0 + Dx, s, t, y0:y0 + Dy]
+        for i in range(Dx):
+            out[off + i * ld: off + i * ld + Dy] = blk[i]
+    return out
+
+
+def layout_unpack(desc: np.ndarray, vec: np.ndarray, shape) -> np.ndarray:
+    """Inverse of ``layout_pack`` (zeros outside the charge-allowed blocks)."""
+    dense = np.zeros(shape)
+    for x0, Dx, s, t, y0, Dy, off, ld in desc:
+        for i in range(Dx):
+            dense[x0 + i, s, t, y0:y0 + Dy] = vec[off + i * ld: off + i * ld + Dy]
+    return dense

@@ -1,0 +1,196 @@
+// Internal declarations shared by the kernels and the host runtime of libidmrg.
+// Nothing here is part of the public C ABI (include/idmrg.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace idmrg {
+
+// ---------------------------------------------------------------- buffers
+// Every operand of a batched kernel is addressed as (buffer id, element offset)
+// inside one superblock; the per-superblock base pointers live in a device
+// table bufs[sb * NBUF + id].  This keeps task lists independent of where the
+// Lanczos loop currently reads and writes.
+enum BufId {
+  BUF_L = 0,      // left environment of the superblock (FP64)
+  BUF_R = 1,      // right environment (FP64)
+  BUF_IN = 2,     // matvec input vector
+  BUF_OUT = 3,    // matvec output vector
+  BUF_T1 = 4,     // H_eff stage-1 intermediate  T1[a] = L_a psi
+  BUF_T3 = 5,     // H_eff stage-2 intermediate  T3[c] = W12 T1
+  BUF_U = 6,      // kept left singular vectors  (rows (x,s), per sector)
+  BUF_V = 7,      // kept right singular vectors (rows (t,y), per sector)
+  BUF_X = 8,      // environment-update intermediate
+  BUF_Y = 9,      // environment-update intermediate
+  BUF_LNEW = 10,  // L^(n) being built
+  BUF_RNEW = 11,  // R^(n) being built
+  BUF_UT = 12,    // prediction: scaled u of superblock p+1 (u~ of Eq. wfprediction)
+  BUF_VT = 13,    // prediction: scaled v of superblock p
+  BUF_PSI = 14,   // start / ground-state vector
+  BUF_AUX = 15,
+  BUF_UPREV = 16, // prediction source: u^(n-1) of superblock p+1
+  BUF_VPREV = 17, // prediction source: v^(n-1) of superblock p
+  NBUF = 18
+};
+
+// C[M x N] (+)= sum_seg alpha * op(A)[M x K] * op(B)[K x N]
+//   op(A) = A (row-major, lda) or A^T (A stored K x M, lda) when (flags & 1)
+//   op(B) = B (row-major K x N, ldb) or B^T (B stored N x K, ldb) when (flags & 2)
+struct GemmSeg {
+  int64_t a_off, b_off;
+  int a_buf, b_buf;
+  int lda, ldb;
+  int K, flags;
+  double alpha;
+};
+struct GemmTask {
+  int64_t c_off;
+  int c_buf, sb;
+  int M, N, ldc;
+  int seg0, nseg;
+  int accumulate;  // 0: C = sum, 1: C += sum
+};
+struct GemmTile {
+  int task, m0, n0, pad;
+};
+
+// out[r, c] = sum_terms coef * in[r, c]   (sub-matrices with row strides)
+struct WTerm {
+  int64_t in_off;
+  int in_ld;
+  int pad;
+  double coef;
+};
+struct WTask {
+  int64_t out_off;
+  int out_ld, sb;
+  int rows, cols;
+  int term0, nterm;
+  int out_buf, in_buf;
+};
+
+// element-wise dot of two equally shaped sub-matrices, weighted
+struct DotTerm {
+  int64_t off1, off2;
+  int ld1, ld2;
+  int rows, cols;
+  int sb, buf;
+  double coef;
+};
+
+// One charge-sector matrix for the SVD of Step 4.
+//   M[r x c]: rows (left sector i, s, x) in row groups, columns (t, right
+//   sector j, y) in column groups; element (row group g, col group h, x, y) of
+//   psi sits at base[g*4+h] + x * rstride[g] + y.
+//   The Jacobi working matrix A is M (r >= c) or M^T (r < c), column-major,
+//   rows_a x cols_a with rows_a = max(r,c), cols_a = min(r,c).
+struct SvdJob {
+  int sb, Q;
+  int r, c;
+  int rows_a, cols_a, transposed;
+  int ngr, ngc;
+  int gr_start[4], gr_len[4], gr_stride[4];
+  int gc_start[4], gc_len[4];
+  int64_t base[16];
+  int64_t a_off;    // A in the SVD work buffer
+  int64_t j_off;    // J (cols_a x cols_a, column-major) in the SVD work buffer
+  int sv_off;       // singular values of this job
+  int key_sec;      // |Q| and Q packed for tie-breaking
+  int pad;
+};
+
+// splitmix64 start-vector sub-block
+struct RandBlock {
+  int64_t off;
+  int rows, cols, ld, sb;
+  int64_t dense0;   // dense index of element (0,0)
+  int64_t dense_rs; // dense index step per row
+  uint64_t state;   // stream state of the superblock
+};
+
+// dst[r*ld + c] = src[r*ld + c] * f_r * g_c with f_r = table[rs_off + r] (or,
+// when rs_inv, its inverse, 0 where table[rs_off + r] <= zero_rel *
+// table[max_off]) and g_c = table[cs_off + c]; an offset of -1 means 1.
+struct ScaleTask {
+  int64_t off;
+  int rows, cols, ld, sb;
+  int src_buf, dst_buf;
+  int rs_off, cs_off;
+  int rs_inv, max_off;
+};
+
+#define IDMRG_DEV_ERR_TIMEOUT 1
+#define IDMRG_DEV_ERR_NUMERIC 2   // non-finite Lanczos coefficient
+#define IDMRG_DEV_ERR_ZERONORM 4  // start vector with zero norm
+#define IDMRG_DEV_ERR_JACOBI 8    // SVD sweeps exhausted
+
+// ------------------------------------------------------------ launchers
+// All launchers enqueue on `st` and return cudaGetLastError().
+cudaError_t launch_gemm_f64(const GemmTile *tiles, int ntiles, const GemmTask *tasks, const GemmSeg *segs,
+                            double *const *bufs, const int *active, cudaStream_t st);
+cudaError_t launch_wstage_f64(const WTask *tasks, int ntasks, int max_rows, const WTerm *terms,
+                              double *const *bufs, const int *active, cudaStream_t st);
+cudaError_t launch_dot_terms(const DotTerm *terms, int nterms, double *const *bufs, double *partial,
+                             cudaStream_t st);
+cudaError_t launch_rand_blocks(const RandBlock *blocks, int nblocks, int max_rows, double *const *bufs, int buf,
+                               cudaStream_t st);
+cudaError_t launch_scale_tasks(const ScaleTask *tasks, int ntasks, int max_rows, const double *table,
+                               double zero_rel, double *const *bufs, cudaStream_t st);
+
+// Lanczos (FP64), batched over superblocks; see kernels_lanczos.cu
+struct LanczosDev {
+  int S;                 // superblocks in the batch
+  int kmax;              // Krylov vectors per superblock
+  const int64_t *N;      // [S] vector length
+  double *const *V;      // [S] Krylov basis, kmax x N row-major
+  double *const *w;      // [S] work vector
+  double *alpha, *beta;  // [S * kmax]
+  double *h;             // [S * kmax] projection coefficients
+  double *part;          // partial sums
+  int *k;                // [S] current Krylov index
+  int *member;           // [S] 1 if the superblock takes part in this solve
+  int *active;           // [S] 1 while iterating
+  int *conv;             // [S] 1 converged / 2 breakdown / 0 not
+  double *theta;         // [S] lowest Ritz value
+  double *y;             // [S * kmax] Ritz coefficients
+  double *resid;         // [S]
+  int *err;              // device error word
+  int nchunk_max;
+  double tol;
+};
+cudaError_t lanczos_set_ptrs(const LanczosDev &L, double **bufs, cudaStream_t st);
+cudaError_t lanczos_project(const LanczosDev &L, int pass, cudaStream_t st);   // h = V^T w  (j <= k)
+cudaError_t lanczos_subtract(const LanczosDev &L, int pass, cudaStream_t st);  // w -= V h (+ ||w||^2 partials on pass 1)
+cudaError_t lanczos_finalize(const LanczosDev &L, cudaStream_t st);            // alpha, beta, tridiagonal, convergence
+cudaError_t lanczos_next(const LanczosDev &L, cudaStream_t st);                // V[k+1] = w / beta, k++
+cudaError_t lanczos_init(const LanczosDev &L, const double *const *start, cudaStream_t st); // V[0] = start/|start|
+cudaError_t lanczos_ritz(const LanczosDev &L, double *const *out, cudaStream_t st);  // out = V y / |V y|
+cudaError_t lanczos_dot(const LanczosDev &L, const double *const *a, const double *const *b, double *res,
+                        cudaStream_t st);  // res[s] = a_s . b_s
+
+// SVD (FP64 one-sided Jacobi), see kernels_svd.cu
+cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_elems, double *const *bufs,
+                                    int psi_buf, double *work, cudaStream_t st);
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, double *sv, int *err, cudaStream_t st);
+struct SelectOut {
+  int *kept_per_job;   // [njobs]
+  int *perm;           // [sum cols_a] kept slot -> index within job (per job, at sv_off)
+  double *lam_sorted;  // [sum cols_a] all singular values of each superblock, descending
+  double *eps;         // [S] discarded weight (Eq. tru)
+  double *eps_best;    // [S]
+  int *kept;           // [S]
+};
+cudaError_t launch_svd_select(const SvdJob *jobs, const int *sb_job0, const int *sb_njob, int S, const double *sv,
+                              int m, double zero_rel, double tie_rel, SelectOut out, int max_entries,
+                              cudaStream_t st);
+struct CompactJob {
+  int job;             // SvdJob index
+  int64_t u_off, v_off;// destination of U_Q (r x k) and V_Q (c x k), row-major
+  int lam_off;         // destination of lambda (k entries)
+  int pad;
+};
+cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, const double *work,
+                               const double *sv, const int *perm, const int *kept_per_job, double *const *bufs,
+                               double *lam, cudaStream_t st);
+
+}  // namespace idmrg

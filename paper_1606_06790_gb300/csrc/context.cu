@@ -1,0 +1,1596 @@
+// libidmrg host runtime: the C ABI of include/idmrg.h.
+//
+// One context holds the l/2 superblock pairs of the parallel iDMRG (Sec. 3).
+// Per iteration n it plans the block-sparse contractions of every superblock
+// on the host (block tables, task lists), uploads them once, and runs the
+// step on the device: start vector (Step 3'), batched Lanczos (Step 3),
+// sector SVD and truncation (Step 4), block-spin transformation (Step 6),
+// then rotates the right blocks between neighbouring pairs (Step 2') and
+// advances n (Step 7).  Step 5' (energy per site) is host bookkeeping of the
+// energies the device returns.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "idmrg.h"
+#include "plan.h"
+
+using namespace idmrg;
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+enum Stage { ST_READY = 0, ST_STARTED = 1, ST_SOLVED = 2, ST_TRUNCATED = 3, ST_UPDATED = 4 };
+
+struct Env {
+  EnvLayout lay;
+  DevBuf data;
+};
+
+struct TruncRec {
+  bool valid = false;
+  Basis leftB, rightB;          // blocks of the superblock this SVD came from
+  std::vector<SecInfo> sec;     // kept sectors, in the new basis order
+  Basis bU, bV;                 // new left / right bases
+  DevBuf U, V;                  // device U_Q, V_Q blocks (FP64)
+  std::vector<double> lam;      // kept singular values, basis order
+  std::vector<double> lam_all;  // every singular value, descending
+  double eps = 0, eps_best = 0;
+  int64_t usize = 0, vsize = 0;
+};
+
+struct SBPlan {
+  int c1 = 0, c2 = 0;
+  PsiLayout psi;
+  int64_t t1size = 0, t3size = 0, xsize = 0, ysize = 0;
+  std::vector<int64_t> t1off, t3off;
+  std::vector<int> t3C, t3col;
+  std::vector<double> W12;  // [wa][wc][d*d][d*d]
+  std::vector<double> h2;   // centre bond operator [d*d][d*d]
+  double heff_flops = 0, heff_bytes = 0;
+  double gemm_flops = 0, w_flops = 0;
+  int njob0 = 0, njob = 0;  // SVD jobs
+};
+
+uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// output k (0-based) of the SplitMix64 stream with initial state s
+uint64_t sm64_at(uint64_t s, uint64_t k) { return sm64_mix(s + (k + 1ull) * 0x9E3779B97F4A7C15ull); }
+
+}  // namespace
+
+struct idmrg_ctx {
+  // problem
+  int ell = 0, d = 0, P = 0;
+  std::vector<int> adim;                 // a_k, k = 0..ell
+  std::vector<std::vector<double>> W;    // per site [a_k][a_k+1][d][d]
+  std::vector<int> qp;                   // phys charges
+  std::vector<std::vector<int>> bq;      // per bond k (left of site k) channel charges
+  idmrg_opts o{};
+  cudaStream_t st = nullptr;
+  idmrg_allocator alloc{};
+  bool own_alloc = true;
+  std::string err;
+  uint64_t launches = 0;
+
+  // iteration state
+  int n = 1;
+  std::vector<int> stage;
+  std::vector<Env> envL, envR, newL, newR;
+  std::vector<TruncRec> cur, prev, prev2;
+  std::map<int, double> e1;   // e^(n)_1
+  double eg_last = NAN;
+  int eg_n = -1;
+  std::vector<double> energy, fidelity, bond, startnorm;
+  std::vector<int> iters, conv;
+
+  // plan for iteration n
+  std::vector<SBPlan> plan;
+  GemmList g1, g3, gp, genv1, genv3;
+  WList wl, wenv;
+  std::vector<DotTerm> dterms;
+  std::vector<int> dterm_sb;
+  std::vector<RandBlock> rblocks;
+  int rmax_rows = 0;
+  std::vector<SvdJob> jobs;
+  std::vector<ScaleTask> stasks;
+  int smax_rows = 0;
+  std::vector<double> stable;
+
+  // device buffers
+  std::vector<double *> hbufs;
+  DevBuf dbufs, dg1t, dg1k, dg1s, dg3t, dg3k, dg3s, dwt, dwm, ddt, ddp, drb, dgpt, dgpk, dgps, dst, dstab;
+  DevBuf dge1t, dge1k, dge1s, dge3t, dge3k, dge3s, dwet, dwem, dmask, derr;
+  std::vector<DevBuf> bT1, bT3, bX, bY, bV, bW, bPsi, bUT, bVT;
+  // lanczos
+  DevBuf lN, lV, lw, lalpha, lbeta, lh, lpart, lk, lmember, lactive, lconv, ltheta, ly, lresid, lpsi, lv0, ldot;
+  int kmax = 0, nchunk = 0;
+  // svd
+  DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk;
+
+  std::vector<int> hmask;
+
+  // instrumentation: per-class CUDA-event timers, transfer counters
+  struct KTimer {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open;
+    cudaEvent_t pending = nullptr;
+    double ms = 0.0, flops = 0.0, bytes = 0.0;
+    uint64_t n = 0;
+  };
+  bool prof = false;
+  KTimer kt[IDMRG_K_COUNT];
+  std::vector<cudaEvent_t> evpool;
+  uint64_t h2d = 0, d2h = 0;
+
+  cudaEvent_t ev_get() {
+    if (!evpool.empty()) {
+      cudaEvent_t e = evpool.back();
+      evpool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void kbegin(int k) {
+    if (!prof) return;
+    kt[k].pending = ev_get();
+    cudaEventRecord(kt[k].pending, st);
+  }
+  void kend(int k, double flops = 0.0, double bytes = 0.0) {
+    if (!prof || !kt[k].pending) return;
+    cudaEvent_t e1 = ev_get();
+    cudaEventRecord(e1, st);
+    kt[k].open.push_back({kt[k].pending, e1});
+    kt[k].pending = nullptr;
+    kt[k].n += 1;
+    kt[k].flops += flops;
+    kt[k].bytes += bytes;
+    if (kt[k].open.size() > 4096) collapse(k);
+  }
+  void collapse(int k) {
+    for (auto &pr : kt[k].open) {
+      cudaEventSynchronize(pr.second);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      kt[k].ms += ms;
+      evpool.push_back(pr.first);
+      evpool.push_back(pr.second);
+    }
+    kt[k].open.clear();
+  }
+  cudaError_t d2h_copy(void *dst, const void *src, size_t bytes) {
+    d2h += bytes;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+  }
+
+  // ------------------------------------------------------------- helpers
+  idmrg_status fail(idmrg_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return s;
+  }
+  void *raw_alloc(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (own_alloc) {
+      void *p = nullptr;
+      if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+      return p;
+    }
+    return alloc.alloc(bytes, alloc.user);
+  }
+  void raw_free(void *p, size_t bytes) {
+    if (!p) return;
+    if (own_alloc)
+      cudaFree(p);
+    else
+      alloc.free(p, bytes, alloc.user);
+  }
+  bool ensure(DevBuf &b, size_t bytes) {
+    if (b.cap >= bytes && b.p) return true;
+    if (b.p) raw_free(b.p, b.cap);
+    size_t cap = std::max<size_t>(bytes + bytes / 4, 1024);
+    cap = (cap + 255) & ~(size_t)255;
+    b.p = raw_alloc(cap);
+    b.cap = b.p ? cap : 0;
+    return b.p != nullptr;
+  }
+  void release(DevBuf &b) {
+    if (b.p) raw_free(b.p, b.cap);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  template <class T>
+  bool upload(DevBuf &b, const std::vector<T> &v) {
+    if (!ensure(b, std::max<size_t>(v.size() * sizeof(T), 16))) return false;
+    if (!v.empty() && cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return false;
+    h2d += v.size() * sizeof(T);
+    return true;
+  }
+  double *dp(DevBuf &b) { return (double *)b.p; }
+
+  const double &Wat(int site, int a, int b, int s, int t) const {
+    const int B = adim[site + 1];
+    return W[site][(((size_t)a * B + b) * d + s) * d + t];
+  }
+  int site_of(int k) const { return ((k % ell) + ell) % ell; }
+};
+
+namespace {
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return c->fail(IDMRG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+#define NOMEM(ok)                                                  \
+  do {                                                             \
+    if (!(ok)) return c->fail(IDMRG_ENOMEM, "device allocation failed (%s)", #ok); \
+  } while (0)
+
+// ------------------------------------------------------------------------
+// planning of iteration n
+// ------------------------------------------------------------------------
+idmrg_status plan_iteration(idmrg_ctx *c) {
+  const int P = c->P, d = c->d, target = c->o.target_charge;
+  c->plan.assign(P, SBPlan());
+  c->g1.clear();
+  c->g3.clear();
+  c->wl.clear();
+  c->dterms.clear();
+  c->dterm_sb.clear();
+  c->rblocks.clear();
+  c->rmax_rows = 0;
+  const uint64_t state0 = c->o.seed;
+  for (int p = 0; p < P; ++p) {
+    SBPlan &S = c->plan[p];
+    S.c1 = c->site_of(2 * p + c->n);
+    S.c2 = c->site_of(2 * p + c->n + 1);
+    const Env &L = c->envL[p];
+    const Env &R = c->envR[(p + 1) % P];
+    const Basis &BL = L.lay.b, &BR = R.lay.b;
+    S.psi.build(BL, BR, c->qp, target);
+    const PsiLayout &psi = S.psi;
+    const int wa = c->adim[S.c1], wb = c->adim[S.c1 + 1], wc = c->adim[S.c2 + 1];
+    if (wb != c->adim[S.c2] || wa != L.lay.w || wc != R.lay.w)
+      return c->fail(IDMRG_EINVAL, "MPO bond dimensions do not chain at superblock %d", p);
+    // two-site MPO W12[a][c][(s,t)][(s',t')] = sum_b W_c1(a,b) W_c2(b,c)
+    const int dd = d * d;
+    S.W12.assign((size_t)wa * wc * dd * dd, 0.0);
+    for (int a = 0; a < wa; ++a)
+      for (int b = 0; b < wb; ++b)
+        for (int s = 0; s < d; ++s)
+          for (int s2 = 0; s2 < d; ++s2) {
+            const double w1 = c->Wat(S.c1, a, b, s, s2);
+            if (w1 == 0.0) continue;
+            for (int cc = 0; cc < wc; ++cc)
+              for (int t = 0; t < d; ++t)
+                for (int t2 = 0; t2 < d; ++t2) {
+                  const double w2 = c->Wat(S.c2, b, cc, t, t2);
+                  if (w2 == 0.0) continue;
+                  S.W12[(((size_t)a * wc + cc) * dd + s * d + t) * dd + s2 * d + t2] += w1 * w2;
+                }
+          }
+    // centre-bond operator: channels opened on c1 and closed on c2
+    S.h2.assign((size_t)dd * dd, 0.0);
+    for (int b = 1; b < wb - 1; ++b)
+      for (int s = 0; s < d; ++s)
+        for (int s2 = 0; s2 < d; ++s2) {
+          const double w1 = c->Wat(S.c1, wa - 1, b, s, s2);
+          if (w1 == 0.0) continue;
+          for (int t = 0; t < d; ++t)
+            for (int t2 = 0; t2 < d; ++t2) S.h2[(s * d + t) * dd + s2 * d + t2] += w1 * c->Wat(S.c2, b, 0, t, t2);
+        }
+    const int SL = BL.S(), SR = BR.S();
+    // ---- stage 1: T1[a] = L_a psi, one task per (a, in-sector)
+    S.t1off.assign((size_t)wa * SL, -1);
+    S.t1size = 0;
+    const double f0 = c->g1.flops;
+    for (int a = 0; a < wa; ++a)
+      for (int si = 0; si < SL; ++si) {
+        const int so = L.lay.so[a * SL + si];
+        if (so < 0 || psi.C[si] == 0) continue;
+        S.t1off[a * SL + si] = S.t1size;
+        S.t1size += (int64_t)BL.dim[so] * psi.C[si];
+        c->g1.task(p, BUF_T1, S.t1off[a * SL + si], BL.dim[so], psi.C[si], psi.C[si]);
+        c->g1.seg(BUF_L, L.lay.off[a * SL + si], BL.dim[si], BUF_IN, psi.roff[si], psi.C[si], BL.dim[si], 0);
+      }
+    // ---- T3 layout: T3[c] row block per left sector i, sub-blocks (s,t)
+    S.t3off.assign((size_t)wc * SL, 0);
+    S.t3C.assign((size_t)wc * SL, 0);
+    S.t3col.assign((size_t)wc * SL * dd, -1);
+    S.t3size = 0;
+    for (int cc = 0; cc < wc; ++cc)
+      for (int i = 0; i < SL; ++i) {
+        int cols = 0;
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const int qsum = BL.q[i] + c->qp[s] + c->qp[t];
+            const int jout = BR.find(target - qsum);
+            if (jout < 0) continue;
+            const int jin = BR.find(target - qsum - R.lay.chq[cc]);
+            if (jin < 0 || R.lay.so[cc * SR + jin] != jout) continue;
+            S.t3col[((size_t)cc * SL + i) * dd + s * d + t] = cols;
+            cols += BR.dim[jin];
+          }
+        S.t3C[cc * SL + i] = cols;
+        S.t3off[cc * SL + i] = S.t3size;
+        S.t3size += (int64_t)BL.dim[i] * cols;
+      }
+    // ---- stage 2: T3 = W12 T1
+    const double fw0 = c->wl.flops;
+    for (int cc = 0; cc < wc; ++cc)
+      for (int i = 0; i < SL; ++i)
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const int col = S.t3col[((size_t)cc * SL + i) * dd + s * d + t];
+            if (col < 0) continue;
+            const int qsum = BL.q[i] + c->qp[s] + c->qp[t];
+            const int jin = BR.find(target - qsum - R.lay.chq[cc]);
+            c->wl.task(p, BUF_T3, S.t3off[cc * SL + i] + col, S.t3C[cc * SL + i], BUF_T1, BL.dim[i], BR.dim[jin]);
+            for (int a = 0; a < wa; ++a) {
+              const int si = BL.find(BL.q[i] - L.lay.chq[a]);
+              if (si < 0 || L.lay.so[a * SL + si] != i || S.t1off[a * SL + si] < 0) continue;
+              for (int s2 = 0; s2 < d; ++s2)
+                for (int t2 = 0; t2 < d; ++t2) {
+                  const double cf = S.W12[(((size_t)a * wc + cc) * dd + s * d + t) * dd + s2 * d + t2];
+                  if (cf == 0.0) continue;
+                  const int k = psi.sub(si, s2, t2);
+                  if (psi.sj[k] != jin) continue;
+                  c->wl.term(S.t1off[a * SL + si] + psi.scol[k], psi.C[si], cf);
+                }
+            }
+          }
+    // ---- stage 3: out = sum_c T3[c] R_c^T
+    const double f3 = c->g3.flops;
+    for (int i = 0; i < SL; ++i)
+      for (int s = 0; s < d; ++s)
+        for (int t = 0; t < d; ++t) {
+          const int k = psi.sub(i, s, t);
+          const int jout = psi.sj[k];
+          if (jout < 0) continue;
+          c->g3.task(p, BUF_OUT, psi.roff[i] + psi.scol[k], BL.dim[i], BR.dim[jout], psi.C[i]);
+          for (int cc = 0; cc < wc; ++cc) {
+            const int col = S.t3col[((size_t)cc * SL + i) * dd + s * d + t];
+            if (col < 0) continue;
+            const int jin = BR.find(target - BL.q[i] - c->qp[s] - c->qp[t] - R.lay.chq[cc]);
+            c->g3.seg(BUF_T3, S.t3off[cc * SL + i] + col, S.t3C[cc * SL + i], BUF_R, R.lay.off[cc * SR + jin],
+                      BR.dim[jin], BR.dim[jin], 2);
+          }
+        }
+    S.gemm_flops = (c->g1.flops - f0) + (c->g3.flops - f3);
+    S.w_flops = c->wl.flops - fw0;
+    S.heff_flops = S.gemm_flops + S.w_flops;
+    S.heff_bytes = 8.0 * (L.lay.size + R.lay.size + 2.0 * psi.N);
+    // ---- centre-bond energy terms
+    for (int i = 0; i < SL; ++i)
+      for (int x = 0; x < dd; ++x)
+        for (int y = 0; y < dd; ++y) {
+          const double cf = S.h2[x * dd + y];
+          if (cf == 0.0) continue;
+          const int k1 = psi.sub(i, x / d, x % d), k2 = psi.sub(i, y / d, y % d);
+          if (psi.sj[k1] < 0 || psi.sj[k1] != psi.sj[k2]) continue;
+          DotTerm dt{};
+          dt.off1 = psi.roff[i] + psi.scol[k1];
+          dt.off2 = psi.roff[i] + psi.scol[k2];
+          dt.ld1 = dt.ld2 = psi.C[i];
+          dt.rows = BL.dim[i];
+          dt.cols = BR.dim[psi.sj[k1]];
+          dt.sb = p;
+          dt.buf = BUF_PSI;
+          dt.coef = cf;
+          c->dterms.push_back(dt);
+          c->dterm_sb.push_back(p);
+        }
+    // ---- random start blocks (Step 3, n = 1, 2)
+    const uint64_t sstate = sm64_at(state0, (uint64_t)(1024 * (int64_t)c->n + p));
+    for (int i = 0; i < SL; ++i)
+      for (int s = 0; s < d; ++s)
+        for (int t = 0; t < d; ++t) {
+          const int k = psi.sub(i, s, t);
+          const int j = psi.sj[k];
+          if (j < 0) continue;
+          RandBlock rb{};
+          rb.off = psi.roff[i] + psi.scol[k];
+          rb.rows = BL.dim[i];
+          rb.cols = BR.dim[j];
+          rb.ld = psi.C[i];
+          rb.sb = p;
+          rb.dense0 = (((int64_t)BL.off[i] * d + s) * d + t) * BR.D + BR.off[j];
+          rb.dense_rs = (int64_t)d * d * BR.D;
+          rb.state = sstate;
+          c->rblocks.push_back(rb);
+          c->rmax_rows = std::max(c->rmax_rows, rb.rows);
+        }
+  }
+  c->g1.finish(64, 64);
+  c->g3.finish(64, 64);
+  // ---- device buffers for this iteration
+  NOMEM(c->upload(c->dg1t, c->g1.tiles) && c->upload(c->dg1k, c->g1.tasks) && c->upload(c->dg1s, c->g1.segs));
+  NOMEM(c->upload(c->dg3t, c->g3.tiles) && c->upload(c->dg3k, c->g3.tasks) && c->upload(c->dg3s, c->g3.segs));
+  NOMEM(c->upload(c->dwt, c->wl.tasks) && c->upload(c->dwm, c->wl.terms));
+  NOMEM(c->upload(c->ddt, c->dterms) && c->ensure(c->ddp, std::max<size_t>(c->dterms.size(), 1) * 8));
+  NOMEM(c->upload(c->drb, c->rblocks));
+  for (int p = 0; p < P; ++p) {
+    SBPlan &S = c->plan[p];
+    NOMEM(c->ensure(c->bT1[p], 8 * std::max<int64_t>(S.t1size, 1)));
+    NOMEM(c->ensure(c->bT3[p], 8 * std::max<int64_t>(S.t3size, 1)));
+    NOMEM(c->ensure(c->bPsi[p], 8 * std::max<int64_t>(S.psi.N, 1)));
+    NOMEM(c->ensure(c->bW[p], 8 * std::max<int64_t>(S.psi.N, 1)));
+    c->hbufs[p * NBUF + BUF_L] = c->dp(c->envL[p].data);
+    c->hbufs[p * NBUF + BUF_R] = c->dp(c->envR[(p + 1) % P].data);
+    c->hbufs[p * NBUF + BUF_T1] = c->dp(c->bT1[p]);
+    c->hbufs[p * NBUF + BUF_T3] = c->dp(c->bT3[p]);
+    c->hbufs[p * NBUF + BUF_PSI] = c->dp(c->bPsi[p]);
+  }
+  NOMEM(c->upload(c->dbufs, c->hbufs));
+  for (int p = 0; p < P; ++p) c->stage[p] = ST_READY;
+  return IDMRG_OK;
+}
+
+idmrg_status sync_bufs(idmrg_ctx *c) {
+  NOMEM(c->upload(c->dbufs, c->hbufs));
+  return IDMRG_OK;
+}
+
+// heff on every superblock whose active flag is set (device array); the host
+// copy `act` (may be null = all) only feeds the flop/byte accounting
+idmrg_status heff_launch(idmrg_ctx *c, const int *active_dev, const int *act) {
+  double *const *bufs = (double *const *)c->dbufs.p;
+  double gf = 0, wf = 0, by = 0;
+  for (int q = 0; q < c->P; ++q)
+    if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
+  c->kbegin(IDMRG_K_HEFF_GEMM);
+  CK(launch_gemm_f64((const GemmTile *)c->dg1t.p, (int)c->g1.tiles.size(), (const GemmTask *)c->dg1k.p,
+                     (const GemmSeg *)c->dg1s.p, bufs, active_dev, c->st));
+  c->kend(IDMRG_K_HEFF_GEMM, 0.0, 0.0);
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(launch_wstage_f64((const WTask *)c->dwt.p, (int)c->wl.tasks.size(), c->wl.max_rows, (const WTerm *)c->dwm.p,
+                       bufs, active_dev, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
+  c->kbegin(IDMRG_K_HEFF_GEMM);
+  CK(launch_gemm_f64((const GemmTile *)c->dg3t.p, (int)c->g3.tiles.size(), (const GemmTask *)c->dg3k.p,
+                     (const GemmSeg *)c->dg3s.p, bufs, active_dev, c->st));
+  c->kend(IDMRG_K_HEFF_GEMM, gf, by);
+  c->launches += 3;
+  return IDMRG_OK;
+}
+
+idmrg_status check_dev_err(idmrg_ctx *c) {
+  int e = 0;
+  CK(c->d2h_copy(&e, c->derr.p, sizeof(int)));
+  CK(cudaStreamSynchronize(c->st));
+  if (e & IDMRG_DEV_ERR_TIMEOUT) return c->fail(IDMRG_ETIMEOUT, "device wait exceeded its budget");
+  if (e & IDMRG_DEV_ERR_NUMERIC) return c->fail(IDMRG_ENUMERIC, "non-finite Lanczos coefficient (n=%d)", c->n);
+  if (e & IDMRG_DEV_ERR_ZERONORM)
+    return c->fail(IDMRG_ENUMERIC, "start vector with zero norm (n=%d, superblock mask 0x%x)", c->n, e >> 4);
+  if (e & IDMRG_DEV_ERR_JACOBI) return c->fail(IDMRG_ENUMERIC, "SVD sweeps exhausted (n=%d)", c->n);
+  return IDMRG_OK;
+}
+
+bool want(int p, int q) { return p < 0 || p == q; }
+
+idmrg_status check_p(idmrg_ctx *c, int p) {
+  if (p < -1 || p >= c->P) return c->fail(IDMRG_EINVAL, "superblock index %d out of range", p);
+  return IDMRG_OK;
+}
+
+// ------------------------------------------------------------------------
+// Step 3': start vectors
+// ------------------------------------------------------------------------
+idmrg_status predict(idmrg_ctx *c, int p) {
+  const int P = c->P, d = c->d;
+  const bool use_pred = c->o.predict && c->n >= 3;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q) && c->stage[q] != ST_READY && c->stage[q] != ST_STARTED)
+      return c->fail(IDMRG_ESTATE, "predict_wavefunction: superblock %d already past its start", q);
+  double *const *bufs = (double *const *)c->dbufs.p;
+  if (!use_pred) {
+    // SplitMix64 numbers on every charge-allowed element; one launch for all
+    // requested superblocks (blocks of other superblocks are filtered on host)
+    std::vector<RandBlock> rb;
+    int mr = 0;
+    for (const RandBlock &b : c->rblocks)
+      if (want(p, b.sb)) { rb.push_back(b); mr = std::max(mr, b.rows); }
+    c->kbegin(IDMRG_K_PREDICT);
+    if (p >= 0) {
+      NOMEM(c->upload(c->dst, rb));
+      CK(launch_rand_blocks((const RandBlock *)c->dst.p, (int)rb.size(), mr, bufs, BUF_PSI, c->st));
+    } else {
+      CK(launch_rand_blocks((const RandBlock *)c->drb.p, (int)c->rblocks.size(), c->rmax_rows, bufs, BUF_PSI, c->st));
+    }
+    c->kend(IDMRG_K_PREDICT);
+    c->launches += 1;
+  } else {
+    // Eq. wfprediction: psi~ = sum_B [lam_i v_i]^T [u_{i+1} lam_{i+1} / lam''_{i+1}]
+    c->stasks.clear();
+    c->stable.clear();
+    c->smax_rows = 0;
+    c->gp.clear();
+    for (int q = 0; q < P; ++q) {
+      if (!want(p, q)) continue;
+      const int q1 = (q + 1) % P;
+      const TruncRec &A = c->prev[q], &B = c->prev[q1], &B2 = c->prev2[q1];
+      if (!A.valid || !B.valid || !B2.valid) return c->fail(IDMRG_ESTATE, "prediction needs two earlier iterations");
+      NOMEM(c->ensure(c->bVT[q], 8 * std::max<int64_t>(A.vsize, 1)));
+      NOMEM(c->ensure(c->bUT[q], 8 * std::max<int64_t>(B.usize, 1)));
+      c->hbufs[q * NBUF + BUF_VPREV] = (double *)A.V.p;
+      c->hbufs[q * NBUF + BUF_UPREV] = (double *)B.U.p;
+      c->hbufs[q * NBUF + BUF_VT] = c->dp(c->bVT[q]);
+      c->hbufs[q * NBUF + BUF_UT] = c->dp(c->bUT[q]);
+      const int t_lamA = (int)c->stable.size();
+      c->stable.insert(c->stable.end(), A.lam.begin(), A.lam.end());
+      const int t_lamB = (int)c->stable.size();
+      c->stable.insert(c->stable.end(), B.lam.begin(), B.lam.end());
+      const int t_lamB2 = (int)c->stable.size();
+      c->stable.insert(c->stable.end(), B2.lam.begin(), B2.lam.end());
+      const int t_max = (int)c->stable.size();
+      c->stable.push_back(B2.lam_all.empty() ? 0.0 : B2.lam_all[0]);
+      // v~ = v_i lam_i (columns)
+      for (const SecInfo &s : A.sec) {
+        ScaleTask t{};
+        t.off = s.v_off;
+        t.rows = s.c;
+        t.cols = s.k;
+        t.ld = s.k;
+        t.sb = q;
+        t.src_buf = BUF_VPREV;
+        t.dst_buf = BUF_VT;
+        t.rs_off = -1;
+        t.cs_off = t_lamA + s.lam_off;
+        t.rs_inv = 0;
+        t.max_off = t_max;
+        c->stasks.push_back(t);
+        c->smax_rows = std::max(c->smax_rows, t.rows);
+      }
+      // u~ = u_{i+1} lam_{i+1} (columns) / lam''_{i+1} (rows, zero rule)
+      for (const SecInfo &s : B.sec)
+        for (const auto &g : s.rg) {
+          ScaleTask t{};
+          t.off = s.u_off + (int64_t)g[2] * s.k;
+          t.rows = B.leftB.dim[g[0]];
+          t.cols = s.k;
+          t.ld = s.k;
+          t.sb = q;
+          t.src_buf = BUF_UPREV;
+          t.dst_buf = BUF_UT;
+          t.rs_off = t_lamB2 + B.leftB.off[g[0]];
+          t.cs_off = t_lamB + s.lam_off;
+          t.rs_inv = 1;
+          t.max_off = t_max;
+          c->stasks.push_back(t);
+          c->smax_rows = std::max(c->smax_rows, t.rows);
+        }
+      // products, one task per psi~ sub-block (left sector a, s, t)
+      const PsiLayout &psi = c->plan[q].psi;
+      for (int a = 0; a < (int)A.sec.size(); ++a)
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const int k = psi.sub(a, s, t);
+            const int g = psi.sj[k];
+            if (g < 0) continue;
+            const SecInfo &sa = A.sec[a], &sg = B.sec[g];
+            c->gp.task(q, BUF_PSI, psi.roff[a] + psi.scol[k], sa.k, sg.k, psi.C[a]);
+            int jB = -1, startV = 0;
+            for (const auto &cg : sa.cg)
+              if (cg[0] == s) { jB = cg[1]; startV = cg[2]; }
+            if (jB < 0) continue;
+            for (const auto &rg : sg.rg)
+              if (rg[1] == t && rg[0] == jB)
+                c->gp.seg(BUF_VT, sa.v_off + (int64_t)startV * sa.k, sa.k, BUF_UT, sg.u_off + (int64_t)rg[2] * sg.k,
+                          sg.k, A.rightB.dim[jB], 1);
+          }
+    }
+    c->gp.finish(64, 64);
+    NOMEM(sync_bufs(c) == IDMRG_OK);
+    NOMEM(c->upload(c->dst, c->stasks) && c->upload(c->dstab, c->stable));
+    NOMEM(c->upload(c->dgpt, c->gp.tiles) && c->upload(c->dgpk, c->gp.tasks) && c->upload(c->dgps, c->gp.segs));
+    c->kbegin(IDMRG_K_PREDICT);
+    CK(launch_scale_tasks((const ScaleTask *)c->dst.p, (int)c->stasks.size(), c->smax_rows,
+                          (const double *)c->dstab.p, c->o.lambda_zero_rel, bufs, c->st));
+    CK(launch_gemm_f64((const GemmTile *)c->dgpt.p, (int)c->gp.tiles.size(), (const GemmTask *)c->dgpk.p,
+                       (const GemmSeg *)c->dgps.p, bufs, nullptr, c->st));
+    c->kend(IDMRG_K_PREDICT, c->gp.flops, 0.0);
+    c->launches += 2;
+  }
+  for (int q = 0; q < P; ++q)
+    if (want(p, q)) c->stage[q] = ST_STARTED;
+  return IDMRG_OK;
+}
+
+// ------------------------------------------------------------------------
+// Step 3: batched Lanczos
+// ------------------------------------------------------------------------
+idmrg_status lanczos(idmrg_ctx *c, int p) {
+  const int P = c->P;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q) && c->stage[q] != ST_STARTED)
+      return c->fail(IDMRG_ESTATE, "lanczos_solve: superblock %d has no start vector", q);
+  const int kmax = c->o.lanczos_maxit;
+  std::vector<int64_t> N(P);
+  int64_t nmax = 1;
+  for (int q = 0; q < P; ++q) {
+    N[q] = c->plan[q].psi.N;
+    nmax = std::max(nmax, N[q]);
+  }
+  const int CHK = 1024;
+  const int nchunk = (int)((nmax + CHK - 1) / CHK);
+  std::vector<double *> Vp(P), wp(P), psip(P), v0p(P);
+  for (int q = 0; q < P; ++q) {
+    NOMEM(c->ensure(c->bV[q], 8 * std::max<int64_t>((int64_t)kmax * N[q], 1)));
+    Vp[q] = c->dp(c->bV[q]);
+    wp[q] = c->dp(c->bW[q]);
+    psip[q] = c->dp(c->bPsi[q]);
+    v0p[q] = Vp[q];
+  }
+  NOMEM(c->upload(c->lN, N) && c->upload(c->lV, Vp) && c->upload(c->lw, wp) && c->upload(c->lpsi, psip) &&
+        c->upload(c->lv0, v0p));
+  NOMEM(c->ensure(c->lalpha, 8 * (size_t)P * kmax) && c->ensure(c->lbeta, 8 * (size_t)P * kmax) &&
+        c->ensure(c->lh, 8 * 2 * (size_t)P * kmax) && c->ensure(c->ly, 8 * (size_t)P * kmax) &&
+        c->ensure(c->lpart, 8 * 3 * (size_t)P * kmax * nchunk) && c->ensure(c->ltheta, 8 * P) &&
+        c->ensure(c->lresid, 8 * P) && c->ensure(c->ldot, 8 * P) && c->ensure(c->lk, 4 * P) &&
+        c->ensure(c->lactive, 4 * P) && c->ensure(c->lconv, 4 * P));
+  std::vector<int> member(P);
+  for (int q = 0; q < P; ++q) member[q] = want(p, q) ? 1 : 0;
+  NOMEM(c->upload(c->lmember, member));
+  LanczosDev L{};
+  L.S = P;
+  L.kmax = kmax;
+  L.N = (const int64_t *)c->lN.p;
+  L.V = (double *const *)c->lV.p;
+  L.w = (double *const *)c->lw.p;
+  L.alpha = c->dp(c->lalpha);
+  L.beta = c->dp(c->lbeta);
+  L.h = c->dp(c->lh);
+  L.part = c->dp(c->lpart);
+  L.k = (int *)c->lk.p;
+  L.member = (int *)c->lmember.p;
+  L.active = (int *)c->lactive.p;
+  L.conv = (int *)c->lconv.p;
+  L.theta = c->dp(c->ltheta);
+  L.y = c->dp(c->ly);
+  L.resid = c->dp(c->lresid);
+  L.err = (int *)c->derr.p;
+  L.nchunk_max = nchunk;
+  L.tol = c->o.lanczos_tol;
+  for (int q = 0; q < P; ++q) c->hbufs[q * NBUF + BUF_PSI] = psip[q];
+  NOMEM(sync_bufs(c) == IDMRG_OK);
+  CK(lanczos_init(L, (const double *const *)c->lpsi.p, c->st));
+  c->launches += 3;
+  // ||psi~|| for the report
+  std::vector<double> nrm2(P, 0.0);
+  CK(c->d2h_copy(nrm2.data(), c->lresid.p, 8 * P));
+  std::vector<int> act(P);
+  for (int it = 0; it < kmax; ++it) {
+    CK(lanczos_set_ptrs(L, (double **)c->dbufs.p, c->st));
+    idmrg_status s = heff_launch(c, L.active, it == 0 ? member.data() : act.data());
+    if (s != IDMRG_OK) return s;
+    double vb = 0.0;
+    for (int q = 0; q < P; ++q)
+      if (it == 0 ? member[q] : act[q]) vb += 8.0 * (double)N[q] * (2.0 * (it + 2) + 2.0 * (it + 3) + 2.0);
+    c->kbegin(IDMRG_K_LANCZOS_VEC);
+    CK(lanczos_project(L, 0, c->st));
+    CK(lanczos_subtract(L, 0, c->st));
+    CK(lanczos_project(L, 1, c->st));
+    CK(lanczos_subtract(L, 1, c->st));
+    c->kend(IDMRG_K_LANCZOS_VEC, 0.0, vb);
+    c->kbegin(IDMRG_K_LANCZOS_TRI);
+    CK(lanczos_finalize(L, c->st));
+    c->kend(IDMRG_K_LANCZOS_TRI);
+    c->kbegin(IDMRG_K_LANCZOS_VEC);
+    CK(lanczos_next(L, c->st));
+    c->kend(IDMRG_K_LANCZOS_VEC);
+    c->launches += 7;
+    CK(c->d2h_copy(act.data(), c->lactive.p, 4 * P));
+    CK(cudaStreamSynchronize(c->st));
+    bool any = false;
+    for (int q = 0; q < P; ++q) any |= (act[q] != 0);
+    if (!any) break;
+  }
+  CK(lanczos_ritz(L, (double *const *)c->lpsi.p, c->st));
+  CK(lanczos_dot(L, (const double *const *)c->lv0.p, (const double *const *)c->lpsi.p, c->dp(c->ldot), c->st));
+  c->launches += 6;
+  std::vector<double> theta(P), dots(P);
+  std::vector<int> kk(P), conv(P);
+  CK(c->d2h_copy(theta.data(), c->ltheta.p, 8 * P));
+  CK(c->d2h_copy(dots.data(), c->ldot.p, 8 * P));
+  CK(c->d2h_copy(kk.data(), c->lk.p, 4 * P));
+  CK(c->d2h_copy(conv.data(), c->lconv.p, 4 * P));
+  idmrg_status s = check_dev_err(c);
+  if (s != IDMRG_OK) return s;
+  bool allconv = true;
+  for (int q = 0; q < P; ++q) {
+    if (!want(p, q)) continue;
+    c->energy[q] = theta[q];
+    c->iters[q] = kk[q] + 1;
+    c->conv[q] = conv[q];
+    c->startnorm[q] = sqrt(nrm2[q]);
+    c->fidelity[q] = (c->o.predict && c->n >= 3) ? 1.0 - fabs(dots[q]) : NAN;
+    c->stage[q] = ST_SOLVED;
+    allconv &= conv[q] != 0;
+  }
+  // centre-bond energies <psi|h|psi>
+  std::vector<DotTerm> dt;
+  std::vector<int> dsb;
+  for (size_t k = 0; k < c->dterms.size(); ++k)
+    if (want(p, c->dterm_sb[k])) { dt.push_back(c->dterms[k]); dsb.push_back(c->dterm_sb[k]); }
+  if (!dt.empty()) {
+    NOMEM(c->upload(c->dst, dt) && c->ensure(c->ddp, 8 * dt.size()));
+    CK(launch_dot_terms((const DotTerm *)c->dst.p, (int)dt.size(), (double *const *)c->dbufs.p, c->dp(c->ddp), c->st));
+    c->launches += 1;
+    std::vector<double> part(dt.size());
+    CK(c->d2h_copy(part.data(), c->ddp.p, 8 * dt.size()));
+    CK(cudaStreamSynchronize(c->st));
+    for (int q = 0; q < P; ++q)
+      if (want(p, q)) c->bond[q] = 0.0;
+    for (size_t k = 0; k < dt.size(); ++k) c->bond[dsb[k]] += part[k];
+  } else {
+    for (int q = 0; q < P; ++q)
+      if (want(p, q)) c->bond[q] = 0.0;
+  }
+  return allconv ? IDMRG_OK : c->fail(IDMRG_ENOCONV, "Lanczos reached lanczos_maxit before converging");
+}
+
+// ------------------------------------------------------------------------
+// Step 4: sector SVD, cut, compaction
+// ------------------------------------------------------------------------
+idmrg_status truncate(idmrg_ctx *c, int p) {
+  const int P = c->P, d = c->d, target = c->o.target_charge;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q) && c->stage[q] != ST_SOLVED)
+      return c->fail(IDMRG_ESTATE, "truncate: superblock %d has not been solved", q);
+  c->jobs.clear();
+  std::vector<int> job0(P, 0), njob(P, 0);
+  std::vector<std::vector<SecInfo>> secs(P);
+  int64_t work = 0;
+  int sv = 0, max_entries = 1;
+  int64_t max_elems = 0;
+  for (int q = 0; q < P; ++q) {
+    job0[q] = (int)c->jobs.size();
+    if (!want(p, q)) continue;
+    const Env &L = c->envL[q];
+    const Env &R = c->envR[(q + 1) % P];
+    const Basis &BL = L.lay.b, &BR = R.lay.b;
+    const PsiLayout &psi = c->plan[q].psi;
+    std::vector<int> Qs;
+    for (int i = 0; i < BL.S(); ++i)
+      for (int s = 0; s < d; ++s) Qs.push_back(BL.q[i] + c->qp[s]);
+    std::sort(Qs.begin(), Qs.end());
+    Qs.erase(std::unique(Qs.begin(), Qs.end()), Qs.end());
+    int entries = 0;
+    for (int Q : Qs) {
+      SecInfo si;
+      si.Q = Q;
+      for (int i = 0; i < BL.S(); ++i)
+        for (int s = 0; s < d; ++s)
+          if (BL.q[i] + c->qp[s] == Q) { si.rg.push_back({i, s, si.r}); si.r += BL.dim[i]; }
+      for (int t = 0; t < d; ++t)
+        for (int j = 0; j < BR.S(); ++j)
+          if (c->qp[t] + BR.q[j] == target - Q) { si.cg.push_back({t, j, si.c}); si.c += BR.dim[j]; }
+      if (si.r == 0 || si.c == 0) continue;
+      if (si.rg.size() > 4 || si.cg.size() > 4) return c->fail(IDMRG_EINVAL, "local dimension above 4 is not supported");
+      SvdJob J{};
+      J.sb = q;
+      J.Q = Q;
+      J.r = si.r;
+      J.c = si.c;
+      J.transposed = si.r < si.c;
+      J.rows_a = std::max(si.r, si.c);
+      J.cols_a = std::min(si.r, si.c);
+      J.ngr = (int)si.rg.size();
+      J.ngc = (int)si.cg.size();
+      for (int g = 0; g < J.ngr; ++g) {
+        J.gr_start[g] = si.rg[g][2];
+        J.gr_len[g] = BL.dim[si.rg[g][0]];
+        J.gr_stride[g] = psi.C[si.rg[g][0]];
+      }
+      for (int h = 0; h < J.ngc; ++h) {
+        J.gc_start[h] = si.cg[h][2];
+        J.gc_len[h] = BR.dim[si.cg[h][1]];
+      }
+      for (int g = 0; g < J.ngr; ++g)
+        for (int h = 0; h < J.ngc; ++h) {
+          const int i = si.rg[g][0], s = si.rg[g][1], t = si.cg[h][0], j = si.cg[h][1];
+          const int k = psi.sub(i, s, t);
+          if (psi.sj[k] != j) return c->fail(IDMRG_EINVAL, "internal: sector bookkeeping mismatch");
+          J.base[g * 4 + h] = psi.roff[i] + psi.scol[k];
+        }
+      J.a_off = work;
+      work += (int64_t)J.rows_a * J.cols_a;
+      J.j_off = work;
+      work += (int64_t)J.cols_a * J.cols_a;
+      J.sv_off = sv;
+      sv += J.cols_a;
+      entries += J.cols_a;
+      max_elems = std::max<int64_t>(max_elems, (int64_t)J.r * J.c);
+      si.job = (int)c->jobs.size();
+      c->jobs.push_back(J);
+      secs[q].push_back(si);
+    }
+    njob[q] = (int)c->jobs.size() - job0[q];
+    max_entries = std::max(max_entries, entries);
+  }
+  const int nj = (int)c->jobs.size();
+  NOMEM(c->upload(c->sjobs, c->jobs) && c->ensure(c->swork, 8 * std::max<int64_t>(work, 1)) &&
+        c->ensure(c->ssv, 8 * std::max(sv, 1)) && c->upload(c->sjob0, job0) && c->upload(c->snjob, njob) &&
+        c->ensure(c->skpj, 4 * std::max(nj, 1)) && c->ensure(c->sperm, 4 * std::max(sv, 1)) &&
+        c->ensure(c->slam, 8 * std::max(sv, 1)) && c->ensure(c->seps, 8 * P) && c->ensure(c->sepsb, 8 * P) &&
+        c->ensure(c->skept, 4 * P));
+  double *const *bufs = (double *const *)c->dbufs.p;
+  c->kbegin(IDMRG_K_SVD);
+  CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, max_elems, bufs, BUF_PSI, c->dp(c->swork), c->st));
+  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), c->dp(c->ssv), (int *)c->derr.p, c->st));
+  // select runs on superblocks with jobs only: compact the index arrays
+  std::vector<int> sbl;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q)) sbl.push_back(q);
+  std::vector<int> j0s, njs;
+  for (int q : sbl) { j0s.push_back(job0[q]); njs.push_back(njob[q]); }
+  NOMEM(c->upload(c->sjob0, j0s) && c->upload(c->snjob, njs));
+  SelectOut so{};
+  so.kept_per_job = (int *)c->skpj.p;
+  so.perm = (int *)c->sperm.p;
+  so.lam_sorted = c->dp(c->slam);
+  so.eps = c->dp(c->seps);
+  so.eps_best = c->dp(c->sepsb);
+  so.kept = (int *)c->skept.p;
+  CK(launch_svd_select((const SvdJob *)c->sjobs.p, (const int *)c->sjob0.p, (const int *)c->snjob.p, (int)sbl.size(),
+                       c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, so, max_entries, c->st));
+  c->kend(IDMRG_K_SVD);
+  c->launches += 3;
+  std::vector<int> kpj(nj);
+  std::vector<double> lam_sorted(sv), eps(sbl.size()), epsb(sbl.size());
+  CK(c->d2h_copy(kpj.data(), c->skpj.p, 4 * nj));
+  CK(c->d2h_copy(lam_sorted.data(), c->slam.p, 8 * sv));
+  CK(c->d2h_copy(eps.data(), c->seps.p, 8 * sbl.size()));
+  CK(c->d2h_copy(epsb.data(), c->sepsb.p, 8 * sbl.size()));
+  idmrg_status s = check_dev_err(c);
+  if (s != IDMRG_OK) return s;
+  // new bases and compaction jobs
+  std::vector<CompactJob> cj;
+  for (size_t z = 0; z < sbl.size(); ++z) {
+    const int q = sbl[z];
+    TruncRec &T = c->cur[q];
+    {
+      const DevBuf keepU = T.U, keepV = T.V;  // recycle the device buffers
+      T = TruncRec();
+      T.U = keepU;
+      T.V = keepV;
+    }
+    T.valid = true;
+    T.leftB = c->envL[q].lay.b;
+    T.rightB = c->envR[(q + 1) % P].lay.b;
+    T.eps = eps[z];
+    T.eps_best = epsb[z];
+    T.bU.clear();
+    T.bV.clear();
+    int lam_off = 0;
+    int64_t uo = 0, vo = 0;
+    for (SecInfo &si : secs[q]) {
+      si.k = kpj[si.job];
+      if (si.k == 0) continue;
+      si.u_off = uo;
+      si.v_off = vo;
+      si.lam_off = lam_off;
+      uo += (int64_t)si.r * si.k;
+      vo += (int64_t)si.c * si.k;
+      lam_off += si.k;
+      T.bU.add(si.Q, si.k);
+      T.bV.add(target - si.Q, si.k);
+      T.sec.push_back(si);
+    }
+    T.bU.finish();
+    T.bV.finish();
+    T.usize = uo;
+    T.vsize = vo;
+    const int base = c->jobs[job0[q]].sv_off;
+    const int tot = (njob[q] > 0) ? c->jobs[job0[q] + njob[q] - 1].sv_off + c->jobs[job0[q] + njob[q] - 1].cols_a - base : 0;
+    T.lam_all.assign(lam_sorted.begin() + base, lam_sorted.begin() + base + tot);
+    NOMEM(c->ensure(T.U, 8 * std::max<int64_t>(uo, 1)) && c->ensure(T.V, 8 * std::max<int64_t>(vo, 1)));
+    c->hbufs[q * NBUF + BUF_U] = (double *)T.U.p;
+    c->hbufs[q * NBUF + BUF_V] = (double *)T.V.p;
+    for (const SecInfo &si : T.sec) {
+      CompactJob j{};
+      j.job = si.job;
+      j.u_off = si.u_off;
+      j.v_off = si.v_off;
+      j.lam_off = si.lam_off;
+      cj.push_back(j);
+    }
+  }
+  // kept lambdas go to one device array: per superblock at a fixed stride
+  const int stride = std::max(1, c->o.m);
+  for (CompactJob &j : cj) j.lam_off += c->jobs[j.job].sb * stride;
+  NOMEM(sync_bufs(c) == IDMRG_OK);
+  NOMEM(c->upload(c->scj, cj) && c->ensure(c->slamk, 8 * (size_t)P * stride));
+  c->kbegin(IDMRG_K_SVD);
+  CK(launch_svd_compact((const SvdJob *)c->sjobs.p, (const CompactJob *)c->scj.p, (int)cj.size(), c->dp(c->swork),
+                        c->dp(c->ssv), (const int *)c->sperm.p, (const int *)c->skpj.p, bufs, c->dp(c->slamk), c->st));
+  c->kend(IDMRG_K_SVD);
+  c->launches += 1;
+  std::vector<double> lamk((size_t)P * stride);
+  CK(c->d2h_copy(lamk.data(), c->slamk.p, 8 * lamk.size()));
+  CK(cudaStreamSynchronize(c->st));
+  for (int q : sbl) {
+    TruncRec &T = c->cur[q];
+    T.lam.assign(lamk.begin() + (size_t)q * stride, lamk.begin() + (size_t)q * stride + T.bU.D);
+    c->stage[q] = ST_TRUNCATED;
+  }
+  return IDMRG_OK;
+}
+
+// ------------------------------------------------------------------------
+// Step 6: block-spin transformation (Eqs. L, R)
+// ------------------------------------------------------------------------
+idmrg_status update_envs(idmrg_ctx *c, int p) {
+  const int P = c->P, d = c->d, target = c->o.target_charge;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q) && c->stage[q] != ST_TRUNCATED)
+      return c->fail(IDMRG_ESTATE, "update_environments: superblock %d is not truncated", q);
+  c->genv1.clear();
+  c->genv3.clear();
+  c->wenv.clear();
+  for (int q = 0; q < P; ++q) {
+    if (!want(p, q)) continue;
+    const SBPlan &S = c->plan[q];
+    const Env &L = c->envL[q];
+    const Env &R = c->envR[(q + 1) % P];
+    const Basis &BL = L.lay.b, &BR = R.lay.b;
+    const TruncRec &T = c->cur[q];
+    const int SL = BL.S(), SR = BR.S();
+    const int wa = L.lay.w, wb = c->adim[S.c1 + 1], wc = R.lay.w;
+    std::map<int, int> secQ;
+    for (int k = 0; k < (int)T.sec.size(); ++k) secQ[T.sec[k].Q] = k;
+    auto sec_of = [&](int Q) { auto it = secQ.find(Q); return it == secQ.end() ? -1 : it->second; };
+    int64_t xs = 0, ys = 0;
+    // ---------------- left: X[a](so, s') = L_a(so,si) U[(si,s')]
+    std::vector<int64_t> xl((size_t)wa * SL * d, -1), yl((size_t)wb * SL * d, -1);
+    for (int a = 0; a < wa; ++a)
+      for (int si = 0; si < SL; ++si) {
+        const int so = L.lay.so[a * SL + si];
+        if (so < 0) continue;
+        for (int s2 = 0; s2 < d; ++s2) {
+          const int k = sec_of(BL.q[si] + c->qp[s2]);
+          if (k < 0) continue;
+          const SecInfo &sc = T.sec[k];
+          int rs = -1;
+          for (const auto &g : sc.rg)
+            if (g[0] == si && g[1] == s2) rs = g[2];
+          if (rs < 0) continue;
+          xl[((size_t)a * SL + so) * d + s2] = xs;
+          c->genv1.task(q, BUF_X, xs, BL.dim[so], sc.k, sc.k);
+          c->genv1.seg(BUF_L, L.lay.off[a * SL + si], BL.dim[si], BUF_U, sc.u_off + (int64_t)rs * sc.k, sc.k,
+                       BL.dim[si], 0);
+          xs += (int64_t)BL.dim[so] * sc.k;
+        }
+      }
+    // Y[b](so, s) = sum_{a,s'} W_c1(a,b,s,s') X[a](so,s')
+    std::vector<int> bchq(c->bq[(S.c1 + 1) % c->ell]);
+    for (int b = 0; b < wb; ++b)
+      for (int so = 0; so < SL; ++so)
+        for (int s = 0; s < d; ++s) {
+          const int ko = sec_of(BL.q[so] + c->qp[s]);
+          const int ki = sec_of(BL.q[so] + c->qp[s] - bchq[b]);
+          if (ko < 0 || ki < 0) continue;
+          const int kin = T.sec[ki].k;
+          yl[((size_t)b * SL + so) * d + s] = ys;
+          c->wenv.task(q, BUF_Y, ys, kin, BUF_X, BL.dim[so], kin);
+          for (int a = 0; a < wa; ++a)
+            for (int s2 = 0; s2 < d; ++s2) {
+              const double cf = c->Wat(S.c1, a, b, s, s2);
+              if (cf == 0.0) continue;
+              const int64_t xo = xl[((size_t)a * SL + so) * d + s2];
+              if (xo < 0) continue;
+              c->wenv.term(xo, kin, cf);
+            }
+          ys += (int64_t)BL.dim[so] * kin;
+        }
+    // L'[b](Qo, Qi) = sum_{(so,s) in Qo} U[(so,s)]^T Y[b](so,s)
+    Env &NL = c->newL[q];
+    NL.lay.build(T.bU, bchq);
+    NOMEM(c->ensure(NL.data, 8 * std::max<int64_t>(NL.lay.size, 1)));
+    c->hbufs[q * NBUF + BUF_LNEW] = c->dp(NL.data);
+    const int SU = T.bU.S();
+    for (int b = 0; b < wb; ++b)
+      for (int si = 0; si < SU; ++si) {
+        const int so = NL.lay.so[b * SU + si];
+        if (so < 0) continue;
+        const SecInfo &o = T.sec[so];
+        const int kin = T.sec[si].k;
+        c->genv3.task(q, BUF_LNEW, NL.lay.off[b * SU + si], o.k, kin, kin);
+        for (const auto &g : o.rg) {
+          const int64_t y = yl[((size_t)b * SL + g[0]) * d + g[1]];
+          if (y < 0) continue;
+          c->genv3.seg(BUF_U, o.u_off + (int64_t)g[2] * o.k, o.k, BUF_Y, y, kin, BL.dim[g[0]], 1);
+        }
+      }
+    // ---------------- right: X[c](jo, t') = R_c(jo,ji) V[(t',ji)]
+    std::vector<int64_t> xr((size_t)wc * SR * d, -1), yr((size_t)wb * SR * d, -1);
+    for (int cc = 0; cc < wc; ++cc)
+      for (int ji = 0; ji < SR; ++ji) {
+        const int jo = R.lay.so[cc * SR + ji];
+        if (jo < 0) continue;
+        for (int t2 = 0; t2 < d; ++t2) {
+          const int k = sec_of(target - (c->qp[t2] + BR.q[ji]));
+          if (k < 0) continue;
+          const SecInfo &sc = T.sec[k];
+          int cs = -1;
+          for (const auto &g : sc.cg)
+            if (g[0] == t2 && g[1] == ji) cs = g[2];
+          if (cs < 0) continue;
+          xr[((size_t)cc * SR + jo) * d + t2] = xs;
+          c->genv1.task(q, BUF_X, xs, BR.dim[jo], sc.k, sc.k);
+          c->genv1.seg(BUF_R, R.lay.off[cc * SR + ji], BR.dim[ji], BUF_V, sc.v_off + (int64_t)cs * sc.k, sc.k,
+                       BR.dim[ji], 0);
+          xs += (int64_t)BR.dim[jo] * sc.k;
+        }
+      }
+    // Y[b](jo, t) = sum_{c,t'} W_c2(b,c,t,t') X[c](jo,t')
+    std::vector<int> rchq(wb);
+    for (int b = 0; b < wb; ++b) rchq[b] = -c->bq[S.c2][b];
+    for (int b = 0; b < wb; ++b)
+      for (int jo = 0; jo < SR; ++jo)
+        for (int t = 0; t < d; ++t) {
+          const int qo = c->qp[t] + BR.q[jo];           // right charge of row (t, jo)
+          const int ko = sec_of(target - qo);
+          const int ki = sec_of(target - (qo - rchq[b]));
+          if (ko < 0 || ki < 0) continue;
+          const int kin = T.sec[ki].k;
+          yr[((size_t)b * SR + jo) * d + t] = ys;
+          c->wenv.task(q, BUF_Y, ys, kin, BUF_X, BR.dim[jo], kin);
+          for (int cc = 0; cc < wc; ++cc)
+            for (int t2 = 0; t2 < d; ++t2) {
+              const double cf = c->Wat(S.c2, b, cc, t, t2);
+              if (cf == 0.0) continue;
+              const int64_t xo = xr[((size_t)cc * SR + jo) * d + t2];
+              if (xo < 0) continue;
+              c->wenv.term(xo, kin, cf);
+            }
+          ys += (int64_t)BR.dim[jo] * kin;
+        }
+    Env &NR = c->newR[q];
+    NR.lay.build(T.bV, rchq);
+    NOMEM(c->ensure(NR.data, 8 * std::max<int64_t>(NR.lay.size, 1)));
+    c->hbufs[q * NBUF + BUF_RNEW] = c->dp(NR.data);
+    const int SV = T.bV.S();
+    for (int b = 0; b < wb; ++b)
+      for (int si = 0; si < SV; ++si) {
+        const int so = NR.lay.so[b * SV + si];
+        if (so < 0) continue;
+        const SecInfo &o = T.sec[so];
+        const int kin = T.sec[si].k;
+        c->genv3.task(q, BUF_RNEW, NR.lay.off[b * SV + si], o.k, kin, kin);
+        for (const auto &g : o.cg) {
+          const int64_t y = yr[((size_t)b * SR + g[1]) * d + g[0]];
+          if (y < 0) continue;
+          c->genv3.seg(BUF_V, o.v_off + (int64_t)g[2] * o.k, o.k, BUF_Y, y, kin, BR.dim[g[1]], 1);
+        }
+      }
+    NOMEM(c->ensure(c->bX[q], 8 * std::max<int64_t>(xs, 1)) && c->ensure(c->bY[q], 8 * std::max<int64_t>(ys, 1)));
+    c->hbufs[q * NBUF + BUF_X] = c->dp(c->bX[q]);
+    c->hbufs[q * NBUF + BUF_Y] = c->dp(c->bY[q]);
+  }
+  c->genv1.finish(64, 64);
+  c->genv3.finish(64, 64);
+  NOMEM(sync_bufs(c) == IDMRG_OK);
+  NOMEM(c->upload(c->dge1t, c->genv1.tiles) && c->upload(c->dge1k, c->genv1.tasks) &&
+        c->upload(c->dge1s, c->genv1.segs));
+  NOMEM(c->upload(c->dge3t, c->genv3.tiles) && c->upload(c->dge3k, c->genv3.tasks) &&
+        c->upload(c->dge3s, c->genv3.segs));
+  NOMEM(c->upload(c->dwet, c->wenv.tasks) && c->upload(c->dwem, c->wenv.terms));
+  double *const *bufs = (double *const *)c->dbufs.p;
+  c->kbegin(IDMRG_K_ENV);
+  CK(launch_gemm_f64((const GemmTile *)c->dge1t.p, (int)c->genv1.tiles.size(), (const GemmTask *)c->dge1k.p,
+                     (const GemmSeg *)c->dge1s.p, bufs, nullptr, c->st));
+  CK(launch_wstage_f64((const WTask *)c->dwet.p, (int)c->wenv.tasks.size(), c->wenv.max_rows,
+                       (const WTerm *)c->dwem.p, bufs, nullptr, c->st));
+  CK(launch_gemm_f64((const GemmTile *)c->dge3t.p, (int)c->genv3.tiles.size(), (const GemmTask *)c->dge3k.p,
+                     (const GemmSeg *)c->dge3s.p, bufs, nullptr, c->st));
+  c->kend(IDMRG_K_ENV, c->genv1.flops + c->wenv.flops + c->genv3.flops, 0.0);
+  c->launches += 3;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q)) c->stage[q] = ST_UPDATED;
+  return IDMRG_OK;
+}
+
+// ------------------------------------------------------------------------
+// Step 7 and the rotation of Step 2'
+// ------------------------------------------------------------------------
+idmrg_status advance(idmrg_ctx *c) {
+  const int P = c->P;
+  for (int q = 0; q < P; ++q)
+    if (c->stage[q] != ST_UPDATED) return c->fail(IDMRG_ESTATE, "advance: superblock %d is not updated", q);
+  CK(cudaStreamSynchronize(c->st));
+  for (int q = 0; q < P; ++q) {
+    std::swap(c->envL[q], c->newL[q]);
+    std::swap(c->envR[q], c->newR[q]);
+  }
+  // lambda history: cur -> prev -> prev2 (buffers recycled)
+  for (int q = 0; q < P; ++q) {
+    std::swap(c->prev2[q], c->prev[q]);
+    std::swap(c->prev[q], c->cur[q]);
+  }
+  c->e1[c->n] = c->energy[0];
+  if ((c->n + 1) % c->ell == 0) {
+    const double before = (c->n - c->ell == -1) ? 0.0 : c->e1[c->n - c->ell];
+    c->eg_last = (c->e1[c->n] - before) / (2.0 * c->ell);
+    c->eg_n = c->n;
+  }
+  c->n += 1;
+  return plan_iteration(c);
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+void idmrg_default_opts(idmrg_opts *o) {
+  if (!o) return;
+  o->m = 64;
+  o->target_charge = 0;
+  o->lanczos_tol = 1e-12;
+  o->lanczos_maxit = 300;
+  o->prec = IDMRG_FP64;
+  o->predict = 1;
+  o->seed = 0;
+  o->lambda_zero_rel = 1e-12;
+  o->tie_rel = 1e-10;
+}
+
+idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cuda_stream,
+                          const idmrg_allocator *alloc, idmrg_ctx **out) {
+  if (!mpo || !opts || !out) return IDMRG_EINVAL;
+  *out = nullptr;
+  idmrg_ctx *c = new idmrg_ctx();
+  auto bail = [&](idmrg_status s) {
+    // keep the context so the caller can read the message? the ABI returns no
+    // context on failure: print nothing, free everything
+    idmrg_destroy(c);
+    return s;
+  };
+  c->o = *opts;
+  c->st = (cudaStream_t)cuda_stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    c->alloc = *alloc;
+    c->own_alloc = false;
+  }
+  const int ell = mpo->ell, d = mpo->d;
+  if (ell < 2 || ell % 2 || d < 1 || d > 4 || !mpo->bond_dim || !mpo->W || !mpo->phys_charge || !mpo->bond_charge)
+    return bail(IDMRG_EINVAL);
+  if (opts->m < 1 || opts->lanczos_maxit < 2 || opts->lanczos_maxit > 600 || !(opts->lanczos_tol > 0))
+    return bail(IDMRG_EINVAL);
+  if (opts->prec != IDMRG_FP64) return bail(IDMRG_EINVAL);
+  c->ell = ell;
+  c->d = d;
+  c->P = ell / 2;
+  c->adim.assign(mpo->bond_dim, mpo->bond_dim + ell + 1);
+  if (c->adim[ell] != c->adim[0]) return bail(IDMRG_EINVAL);
+  for (int k = 0; k <= ell; ++k)
+    if (c->adim[k] < 2) return bail(IDMRG_EINVAL);
+  c->qp.assign(mpo->phys_charge, mpo->phys_charge + d);
+  for (int s = 0; s < d; ++s)
+    for (int t = s + 1; t < d; ++t)
+      if (c->qp[s] == c->qp[t]) return bail(IDMRG_EINVAL);  // one state per physical charge
+  size_t woff = 0, qoff = 0;
+  c->W.resize(ell);
+  c->bq.resize(ell);
+  for (int k = 0; k < ell; ++k) {
+    const size_t n = (size_t)c->adim[k] * c->adim[k + 1] * d * d;
+    c->W[k].assign(mpo->W + woff, mpo->W + woff + n);
+    woff += n;
+    c->bq[k].assign(mpo->bond_charge + qoff, mpo->bond_charge + qoff + c->adim[k]);
+    qoff += c->adim[k];
+  }
+  // lower-triangular FSA form and charge conservation (Sec. 2, Eq. mpo)
+  for (int k = 0; k < ell; ++k) {
+    const int A = c->adim[k], B = c->adim[k + 1];
+    const std::vector<int> &qa = c->bq[k], &qb = c->bq[(k + 1) % ell];
+    for (int a = 0; a < A; ++a)
+      for (int b = 0; b < B; ++b)
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const double w = c->Wat(k, a, b, s, t);
+            const double id = (s == t) ? 1.0 : 0.0;
+            if ((a == 0 && b == 0) || (a == A - 1 && b == B - 1)) {
+              if (w != id) { c->fail(IDMRG_EINVAL, "W_%d: corner channels must be the identity", k); return bail(IDMRG_EINVAL); }
+              continue;
+            }
+            if (w == 0.0) continue;
+            if (a == 0 || b == B - 1) return bail(IDMRG_EINVAL);
+            if (c->qp[s] - c->qp[t] != qb[b] - qa[a]) return bail(IDMRG_EINVAL);
+          }
+  }
+  const int P = c->P;
+  c->stage.assign(P, ST_READY);
+  c->envL.resize(P);
+  c->envR.resize(P);
+  c->newL.resize(P);
+  c->newR.resize(P);
+  c->cur.resize(P);
+  c->prev.resize(P);
+  c->prev2.resize(P);
+  c->energy.assign(P, NAN);
+  c->fidelity.assign(P, NAN);
+  c->bond.assign(P, NAN);
+  c->startnorm.assign(P, NAN);
+  c->iters.assign(P, 0);
+  c->conv.assign(P, 0);
+  c->bT1.resize(P);
+  c->bT3.resize(P);
+  c->bX.resize(P);
+  c->bY.resize(P);
+  c->bV.resize(P);
+  c->bW.resize(P);
+  c->bPsi.resize(P);
+  c->bUT.resize(P);
+  c->bVT.resize(P);
+  c->hbufs.assign((size_t)P * NBUF, nullptr);
+  if (!c->ensure(c->derr, 256)) return bail(IDMRG_ENOMEM);
+  if (cudaMemsetAsync(c->derr.p, 0, sizeof(int), c->st) != cudaSuccess) return bail(IDMRG_ECUDA);
+  // Step 1: L^(0) of pair p = last row of W at site 2p, R^(0) = first column of W at 2p+1
+  for (int p = 0; p < P; ++p) {
+    Basis b;
+    for (int s = 0; s < d; ++s) b.add(c->qp[s], 1);
+    b.finish();
+    const int sL = 2 * p, sR = 2 * p + 1;
+    Env &L = c->envL[p];
+    L.lay.build(b, c->bq[(sL + 1) % ell]);
+    std::vector<double> hl(L.lay.size, 0.0);
+    for (int a = 0; a < L.lay.w; ++a)
+      for (int si = 0; si < d; ++si) {
+        const int so = L.lay.so[a * d + si];
+        if (so >= 0) hl[L.lay.off[a * d + si]] = c->Wat(sL, c->adim[sL] - 1, a, so, si);
+      }
+    std::vector<int> rq(c->adim[sR]);
+    for (int a = 0; a < c->adim[sR]; ++a) rq[a] = -c->bq[sR][a];
+    Env &R = c->envR[p];
+    R.lay.build(b, rq);
+    std::vector<double> hr(R.lay.size, 0.0);
+    for (int a = 0; a < R.lay.w; ++a)
+      for (int si = 0; si < d; ++si) {
+        const int so = R.lay.so[a * d + si];
+        if (so >= 0) hr[R.lay.off[a * d + si]] = c->Wat(sR, a, 0, so, si);
+      }
+    if (!c->upload(L.data, hl) || !c->upload(R.data, hr)) return bail(IDMRG_ENOMEM);
+  }
+  c->n = 1;
+  c->e1[-1] = 0.0;
+  if (plan_iteration(c) != IDMRG_OK) return bail(IDMRG_ENOMEM);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(IDMRG_ECUDA);
+  *out = c;
+  return IDMRG_OK;
+}
+
+void idmrg_destroy(idmrg_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  auto rel = [&](DevBuf &b) { c->release(b); };
+  for (auto &e : c->envL) rel(e.data);
+  for (auto &e : c->envR) rel(e.data);
+  for (auto &e : c->newL) rel(e.data);
+  for (auto &e : c->newR) rel(e.data);
+  for (auto *v : {&c->cur, &c->prev, &c->prev2})
+    for (auto &t : *v) { rel(t.U); rel(t.V); }
+  for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT})
+    for (auto &b : *v) rel(b);
+  for (DevBuf *b : {&c->dbufs, &c->dg1t, &c->dg1k, &c->dg1s, &c->dg3t, &c->dg3k, &c->dg3s, &c->dwt, &c->dwm, &c->ddt,
+                    &c->ddp, &c->drb, &c->dgpt, &c->dgpk, &c->dgps, &c->dst, &c->dstab, &c->dge1t, &c->dge1k,
+                    &c->dge1s, &c->dge3t, &c->dge3k, &c->dge3s, &c->dwet, &c->dwem, &c->dmask, &c->derr, &c->lN,
+                    &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
+                    &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
+                    &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
+                    &c->scj, &c->slamk})
+    rel(*b);
+  for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char *idmrg_last_error(const idmrg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+idmrg_status idmrg_set_stream(idmrg_ctx *c, void *s) {
+  if (!c) return IDMRG_EINVAL;
+  c->st = (cudaStream_t)s;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_iteration(const idmrg_ctx *c, int *n) {
+  if (!c || !n) return IDMRG_EINVAL;
+  *n = c->n;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_psi_layout(const idmrg_ctx *cc, int p, int *desc, int cap, int *nblocks, size_t *nelem) {
+  idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);
+  if (!c || p < 0 || p >= c->P) return IDMRG_EINVAL;
+  const PsiLayout &psi = c->plan[p].psi;
+  const Basis &BL = c->envL[p].lay.b, &BR = c->envR[(p + 1) % c->P].lay.b;
+  int nb = 0;
+  for (int i = 0; i < BL.S(); ++i)
+    for (int s = 0; s < c->d; ++s)
+      for (int t = 0; t < c->d; ++t) {
+        const int k = psi.sub(i, s, t);
+        const int j = psi.sj[k];
+        if (j < 0) continue;
+        if (desc && nb < cap) {
+          int *e = desc + 8 * nb;
+          e[0] = BL.off[i];
+          e[1] = BL.dim[i];
+          e[2] = s;
+          e[3] = t;
+          e[4] = BR.off[j];
+          e[5] = BR.dim[j];
+          e[6] = (int)(psi.roff[i] + psi.scol[k]);
+          e[7] = psi.C[i];
+        }
+        ++nb;
+      }
+  if (nblocks) *nblocks = nb;
+  if (nelem) *nelem = (size_t)psi.N;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_block_basis(const idmrg_ctx *c, int p, int side, int *charges, int cap, int *dim, int *channels) {
+  if (!c || p < 0 || p >= c->P || (side != 0 && side != 1)) return IDMRG_EINVAL;
+  const Env &E = side == 0 ? c->envL[p] : c->envR[(p + 1) % c->P];
+  const Basis &b = E.lay.b;
+  if (charges) {
+    int k = 0;
+    for (int i = 0; i < b.S(); ++i)
+      for (int x = 0; x < b.dim[i]; ++x)
+        if (k < cap) charges[k++] = b.q[i];
+  }
+  if (dim) *dim = b.D;
+  if (channels) *channels = E.lay.w;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_block_to_host(const idmrg_ctx *cc, int p, int side, double *host, size_t cap) {
+  idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);
+  if (!c || !host || p < 0 || p >= c->P || (side != 0 && side != 1)) return IDMRG_EINVAL;
+  const Env &E = side == 0 ? c->envL[p] : c->envR[(p + 1) % c->P];
+  const Basis &b = E.lay.b;
+  const size_t D = b.D;
+  if (cap < (size_t)E.lay.w * D * D) return c->fail(IDMRG_EINVAL, "block_to_host: buffer too small");
+  std::vector<double> blocks(E.lay.size);
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(blocks.data(), E.data.p, 8 * blocks.size(), cudaMemcpyDeviceToHost));
+  memset(host, 0, sizeof(double) * E.lay.w * D * D);
+  const int S = b.S();
+  for (int a = 0; a < E.lay.w; ++a)
+    for (int si = 0; si < S; ++si) {
+      const int so = E.lay.so[a * S + si];
+      if (so < 0) continue;
+      const double *blk = blocks.data() + E.lay.off[a * S + si];
+      for (int x = 0; x < b.dim[so]; ++x)
+        for (int y = 0; y < b.dim[si]; ++y)
+          host[((size_t)a * D + b.off[so] + x) * D + b.off[si] + y] = blk[(size_t)x * b.dim[si] + y];
+    }
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_heff_apply(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev) {
+  if (!c || !psi_dev || !out_dev) return IDMRG_EINVAL;
+  if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
+  std::vector<int> mask(c->P, 0);
+  int64_t off = 0;
+  std::vector<double *> save_in(c->P), save_out(c->P);
+  for (int q = 0; q < c->P; ++q) {
+    save_in[q] = c->hbufs[q * NBUF + BUF_IN];
+    save_out[q] = c->hbufs[q * NBUF + BUF_OUT];
+    if (!want(p, q)) continue;
+    mask[q] = 1;
+    c->hbufs[q * NBUF + BUF_IN] = const_cast<double *>(psi_dev) + off;
+    c->hbufs[q * NBUF + BUF_OUT] = out_dev + off;
+    if (p < 0) off += c->plan[q].psi.N;
+  }
+  NOMEM(c->upload(c->dmask, mask));
+  NOMEM(sync_bufs(c) == IDMRG_OK);
+  idmrg_status s = heff_launch(c, (const int *)c->dmask.p, mask.data());
+  for (int q = 0; q < c->P; ++q) {
+    c->hbufs[q * NBUF + BUF_IN] = save_in[q];
+    c->hbufs[q * NBUF + BUF_OUT] = save_out[q];
+  }
+  return s;
+}
+
+idmrg_status idmrg_predict_wavefunction(idmrg_ctx *c, int p, double *norm_out) {
+  if (!c) return IDMRG_EINVAL;
+  if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
+  idmrg_status s = predict(c, p);
+  if (s != IDMRG_OK || !norm_out) return s;
+  // ||psi~|| on request (one norm per requested superblock)
+  CK(cudaStreamSynchronize(c->st));
+  int k = 0;
+  for (int q = 0; q < c->P; ++q) {
+    if (!want(p, q)) continue;
+    std::vector<double> h(c->plan[q].psi.N);
+    CK(cudaMemcpy(h.data(), c->bPsi[q].p, 8 * h.size(), cudaMemcpyDeviceToHost));
+    double nn = 0.0;
+    for (double v : h) nn += v * v;
+    norm_out[k++] = sqrt(nn);
+  }
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_lanczos_solve(idmrg_ctx *c, int p, double *e_out, int *iters_out) {
+  if (!c) return IDMRG_EINVAL;
+  if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
+  idmrg_status s = lanczos(c, p);
+  if (s != IDMRG_OK && s != IDMRG_ENOCONV) return s;
+  int k = 0;
+  for (int q = 0; q < c->P; ++q) {
+    if (!want(p, q)) continue;
+    if (e_out) e_out[k] = c->energy[q];
+    if (iters_out) iters_out[k] = c->iters[q];
+    ++k;
+  }
+  return s;
+}
+
+idmrg_status idmrg_get_psi(const idmrg_ctx *cc, int p, double *host, size_t cap) {
+  idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);
+  if (!c || !host || p < 0 || p >= c->P) return IDMRG_EINVAL;
+  if (c->stage[p] < ST_SOLVED) return c->fail(IDMRG_ESTATE, "get_psi: superblock %d not solved", p);
+  const size_t N = c->plan[p].psi.N;
+  if (cap < N) return c->fail(IDMRG_EINVAL, "get_psi: buffer too small");
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(host, c->bPsi[p].p, 8 * N, cudaMemcpyDeviceToHost));
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_truncate(idmrg_ctx *c, int p, double *eps_out, double *eps_best_out, int *kept_out) {
+  if (!c) return IDMRG_EINVAL;
+  if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
+  idmrg_status s = truncate(c, p);
+  if (s != IDMRG_OK) return s;
+  int k = 0;
+  for (int q = 0; q < c->P; ++q) {
+    if (!want(p, q)) continue;
+    if (eps_out) eps_out[k] = c->cur[q].eps;
+    if (eps_best_out) eps_best_out[k] = c->cur[q].eps_best;
+    if (kept_out) kept_out[k] = c->cur[q].bU.D;
+    ++k;
+  }
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_get_lambda(const idmrg_ctx *c, int p, double *host, int cap, int *len) {
+  if (!c || p < 0 || p >= c->P) return IDMRG_EINVAL;
+  const TruncRec &T = c->stage[p] >= ST_TRUNCATED ? c->cur[p] : c->prev[p];
+  if (!T.valid) return IDMRG_ESTATE;
+  const int n = (int)T.lam_all.size();
+  if (host)
+    for (int i = 0; i < std::min(n, cap); ++i) host[i] = T.lam_all[i];
+  if (len) *len = n;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_update_environments(idmrg_ctx *c, int p) {
+  if (!c) return IDMRG_EINVAL;
+  if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
+  return update_envs(c, p);
+}
+
+idmrg_status idmrg_advance(idmrg_ctx *c) {
+  if (!c) return IDMRG_EINVAL;
+  return advance(c);
+}
+
+idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {
+  if (!c) return IDMRG_EINVAL;
+  for (int q = 0; q < c->P; ++q)
+    if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "unit_cell_step: iteration %d already in progress", c->n);
+  idmrg_status s = predict(c, -1);
+  if (s != IDMRG_OK) return s;
+  idmrg_status sl = lanczos(c, -1);
+  if (sl != IDMRG_OK && sl != IDMRG_ENOCONV) return sl;
+  s = truncate(c, -1);
+  if (s != IDMRG_OK) return s;
+  s = update_envs(c, -1);
+  if (s != IDMRG_OK) return s;
+  const int n_done = c->n;
+  std::vector<double> eps(c->P), epsb(c->P);
+  std::vector<int> kept(c->P);
+  for (int q = 0; q < c->P; ++q) {
+    eps[q] = c->cur[q].eps;
+    epsb[q] = c->cur[q].eps_best;
+    kept[q] = c->cur[q].bU.D;
+  }
+  s = advance(c);
+  if (s != IDMRG_OK) return s;
+  if (rep) {
+    rep->n = n_done;
+    for (int q = 0; q < c->P; ++q) {
+      if (rep->energy) rep->energy[q] = c->energy[q];
+      if (rep->iters) rep->iters[q] = c->iters[q];
+      if (rep->eps) rep->eps[q] = eps[q];
+      if (rep->eps_best) rep->eps_best[q] = epsb[q];
+      if (rep->fidelity) rep->fidelity[q] = c->fidelity[q];
+      if (rep->bond) rep->bond[q] = c->bond[q];
+      if (rep->kept) rep->kept[q] = kept[q];
+    }
+    rep->e_g = (c->eg_n == n_done) ? c->eg_last : NAN;
+  }
+  return sl;
+}
+
+idmrg_status idmrg_energy_per_site(const idmrg_ctx *c, double *e_g, int *n_of_estimate) {
+  if (!c) return IDMRG_EINVAL;
+  if (c->eg_n < 0) return IDMRG_ESTATE;
+  if (e_g) *e_g = c->eg_last;
+  if (n_of_estimate) *n_of_estimate = c->eg_n;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_heff_cost(const idmrg_ctx *c, int p, double *flops, double *bytes) {
+  if (!c || p < -1 || p >= c->P) return IDMRG_EINVAL;
+  double f = 0, b = 0;
+  for (int q = 0; q < c->P; ++q)
+    if (want(p, q)) { f += c->plan[q].heff_flops; b += c->plan[q].heff_bytes; }
+  if (flops) *flops = f;
+  if (bytes) *bytes = b;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_launch_count(const idmrg_ctx *c, uint64_t *count) {
+  if (!c || !count) return IDMRG_EINVAL;
+  *count = c->launches;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_profile_enable(idmrg_ctx *c, int on) {
+  if (!c) return IDMRG_EINVAL;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return IDMRG_ECUDA;
+  for (int k = 0; k < IDMRG_K_COUNT; ++k) {
+    c->collapse(k);
+    c->kt[k].ms = c->kt[k].flops = c->kt[k].bytes = 0.0;
+    c->kt[k].n = 0;
+    c->kt[k].pending = nullptr;
+  }
+  c->prof = on != 0;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_profile_read(idmrg_ctx *c, int k, double *ms, uint64_t *launches, double *flops, double *bytes) {
+  if (!c || k < 0 || k >= IDMRG_K_COUNT) return IDMRG_EINVAL;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return IDMRG_ECUDA;
+  c->collapse(k);
+  if (ms) *ms = c->kt[k].ms;
+  if (launches) *launches = c->kt[k].n;
+  if (flops) *flops = c->kt[k].flops;
+  if (bytes) *bytes = c->kt[k].bytes;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_transfer_bytes(const idmrg_ctx *c, uint64_t *h2d, uint64_t *d2h) {
+  if (!c) return IDMRG_EINVAL;
+  if (h2d) *h2d = c->h2d;
+  if (d2h) *d2h = c->d2h;
+  return IDMRG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,451 @@
+// FP64 Lanczos of Step 3 (lowest eigenpair of each superblock Hamiltonian),
+// batched over superblocks.  Full re-orthogonalisation by classical
+// Gram-Schmidt applied twice (the three-term recurrence is the j = k, k-1 part
+// of the same projection).  Reductions are two-level and deterministic: each
+// CTA writes one partial per (superblock, coefficient); consumers add the
+// partials in a fixed order.  The tridiagonal problem is solved on the device:
+// warp multisection with Sturm counts for the lowest eigenvalue, then inverse
+// iteration with a pivoted tridiagonal LU for its eigenvector.
+#include <float.h>
+#include <math.h>
+
+#include "common.h"
+
+namespace idmrg {
+
+namespace {
+
+constexpr int LT = 256;        // threads per CTA
+constexpr int EPT = 4;         // elements per thread
+constexpr int CH = LT * EPT;   // elements per chunk
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void set_ptrs_kernel(LanczosDev L, double **bufs) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= L.S) return;
+  bufs[s * NBUF + BUF_IN] = L.V[s] + (int64_t)L.k[s] * L.N[s];
+  bufs[s * NBUF + BUF_OUT] = L.w[s];
+}
+
+// part[((pass*S + s)*kmax + j)*nchunk + chunk] = sum_{e in chunk} V_j[e] w[e]
+__global__ void project_kernel(LanczosDev L, int pass) {
+  extern __shared__ double red[];  // [LT/32][kmax]
+  const int s = blockIdx.y;
+  if (!L.active[s]) return;
+  const int64_t N = L.N[s];
+  const int64_t e0 = (int64_t)blockIdx.x * CH;
+  if (e0 >= N) return;
+  const int kk = L.k[s];
+  const double *w = L.w[s];
+  double wv[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int64_t e = e0 + threadIdx.x + q * LT;
+    wv[q] = e < N ? w[e] : 0.0;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = 0; j <= kk; ++j) {
+    const double *v = L.V[s] + (int64_t)j * N;
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int64_t e = e0 + threadIdx.x + q * LT;
+      if (e < N) acc = fma(v[e], wv[q], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) red[warp * L.kmax + j] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j <= kk; j += LT) {
+    double acc = 0.0;
+    for (int q = 0; q < LT / 32; ++q) acc += red[q * L.kmax + j];
+    L.part[(((int64_t)pass * L.S + s) * L.kmax + j) * L.nchunk_max + blockIdx.x] = acc;
+  }
+}
+
+// w -= sum_j V_j h_j with h_j the summed partials of `pass`; the CTA with
+// chunk 0 stores h in L.h[(pass*S + s)*kmax + j].  On pass 1 also writes the
+// partial squared norm of the new w at part2 slot j = kmax-1 of pass 2.
+__global__ void subtract_kernel(LanczosDev L, int pass) {
+  extern __shared__ double hs[];  // [kmax] + [LT/32]
+  const int s = blockIdx.y;
+  if (!L.active[s]) return;
+  const int64_t N = L.N[s];
+  const int64_t e0 = (int64_t)blockIdx.x * CH;
+  if (e0 >= N) return;
+  const int kk = L.k[s];
+  const int nch = (int)((N + CH - 1) / CH);
+  for (int j = threadIdx.x; j <= kk; j += LT) {
+    const double *p = L.part + (((int64_t)pass * L.S + s) * L.kmax + j) * L.nchunk_max;
+    double acc = 0.0;
+    for (int c = 0; c < nch; ++c) acc += p[c];
+    hs[j] = acc;
+    if (blockIdx.x == 0) L.h[((int64_t)pass * L.S + s) * L.kmax + j] = acc;
+  }
+  __syncthreads();
+  double *w = L.w[s];
+  double nrm = 0.0;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int64_t e = e0 + threadIdx.x + q * LT;
+    if (e >= N) continue;
+    double acc = w[e];
+    for (int j = 0; j <= kk; ++j) acc = fma(-hs[j], L.V[s][(int64_t)j * N + e], acc);
+    w[e] = acc;
+    nrm = fma(acc, acc, nrm);
+  }
+  if (pass == 1) {
+    double *red = hs + L.kmax;
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double acc = 0.0;
+      for (int q = 0; q < LT / 32; ++q) acc += red[q];
+      L.part[(((int64_t)2 * L.S + s) * L.kmax + 0) * L.nchunk_max + blockIdx.x] = acc;
+    }
+  }
+}
+
+// ---- tridiagonal eigen-solver (lowest pair), one warp per superblock ----
+// Sturm count in FP32: the eigenvalue is only bracketed here (to ~1e-7
+// relative); its FP64 value comes from inverse iteration and a Rayleigh
+// quotient, which costs far fewer FP64 divisions on this part.
+__device__ int sturm_count_f(const float *a, const float *b2, int n, float x, float pivmin) {
+  int cnt = 0;
+  float q = a[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  if (q < 0.f) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = (a[i] - x) - __fdividef(b2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    if (q < 0.f) ++cnt;
+  }
+  return cnt;
+}
+
+// Solves (T - theta) x = b in place (b -> x) with a partially pivoted LU
+// (the elimination of LAPACK's tridiagonal routines); tiny pivots are raised
+// to `tiny` so the nearly singular shift amplifies the eigenvector.
+__device__ void shifted_solve(const double *a, const double *b, int n, double theta, double tiny, double *dl,
+                              double *d, double *du, double *du2, int *piv, double *x) {
+  for (int i = 0; i < n; ++i) {
+    d[i] = a[i] - theta;
+    if (i < n - 1) { dl[i] = b[i]; du[i] = b[i]; }
+    du2[i] = 0.0;
+    piv[i] = 0;
+  }
+  for (int i = 0; i < n - 1; ++i) {
+    if (fabs(d[i]) >= fabs(dl[i])) {
+      if (fabs(d[i]) < tiny) d[i] = copysign(tiny, d[i] == 0.0 ? 1.0 : d[i]);
+      const double f = dl[i] / d[i];
+      dl[i] = f;
+      d[i + 1] -= f * du[i];
+    } else {
+      const double f = d[i] / dl[i];
+      d[i] = dl[i];
+      dl[i] = f;
+      const double t = du[i];
+      du[i] = d[i + 1];
+      d[i + 1] = t - f * d[i + 1];
+      if (i < n - 2) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du[i + 1];
+      }
+      piv[i] = 1;
+    }
+  }
+  if (fabs(d[n - 1]) < tiny) d[n - 1] = copysign(tiny, d[n - 1] == 0.0 ? 1.0 : d[n - 1]);
+  for (int i = 0; i < n - 1; ++i) {
+    if (!piv[i]) {
+      x[i + 1] -= dl[i] * x[i];
+    } else {
+      const double t = x[i];
+      x[i] = x[i + 1];
+      x[i + 1] = t - dl[i] * x[i];
+    }
+  }
+  x[n - 1] /= d[n - 1];
+  if (n > 1) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / d[n - 2];
+  for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / d[i];
+}
+
+__global__ void finalize_kernel(LanczosDev L) {
+  const int s = blockIdx.x;
+  if (!L.active[s]) return;
+  extern __shared__ double sm[];
+  const int km = L.kmax;
+  double *a = sm, *b = sm + km, *b2 = sm + 2 * km, *dl = sm + 3 * km, *d = sm + 4 * km, *du = sm + 5 * km,
+         *du2 = sm + 6 * km, *x = sm + 7 * km;
+  int *piv = (int *)(sm + 8 * km);
+  const int kk = L.k[s];
+  const int n = kk + 1;
+  const int lane = threadIdx.x;
+  const int64_t N = L.N[s];
+  const int nch = (int)((N + CH - 1) / CH);
+  // alpha_k from both Gram-Schmidt passes, beta_k = |w|
+  if (lane == 0) {
+    const double alpha = L.h[(int64_t)(0 * L.S + s) * km + kk] + L.h[(int64_t)(1 * L.S + s) * km + kk];
+    const double *p = L.part + (((int64_t)2 * L.S + s) * km + 0) * L.nchunk_max;
+    double nn = 0.0;
+    for (int c = 0; c < nch; ++c) nn += p[c];
+    L.alpha[s * km + kk] = alpha;
+    L.resid[s] = sqrt(nn);  // beta_k, stored provisionally
+    if (!isfinite(alpha) || !isfinite(nn)) atomicOr(L.err, IDMRG_DEV_ERR_NUMERIC);
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    a[i] = L.alpha[s * km + i];
+    if (i < n - 1) {
+      b[i] = L.beta[s * km + i];
+      b2[i] = b[i] * b[i];
+    }
+  }
+  __syncwarp();
+  const double beta_k = L.resid[s];
+  float *af = (float *)piv + km, *b2f = af + km;  // FP32 copies for the bracketing
+  for (int i = lane; i < n; i += 32) {
+    af[i] = (float)a[i];
+    if (i < n - 1) b2f[i] = (float)b2[i];
+  }
+  __syncwarp();
+  // Gershgorin interval
+  double lo = 1e300, hi = -1e300, bmax = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < n - 1 ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+    if (i < n - 1) bmax = fmax(bmax, b2[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  float flo = (float)(lo - 1e-6 * tnorm) - 1e-30f, fhi = (float)(hi + 1e-6 * tnorm) + 1e-30f;
+  const float fpiv = 1e-30f * fmaxf(1.f, (float)bmax);
+  for (int round = 0; round < 12; ++round) {
+    const float step = (fhi - flo) / 33.f;
+    const float xq = flo + (lane + 1) * step;
+    const int c = sturm_count_f(af, b2f, n, xq, fpiv) >= 1;
+    const unsigned bal = __ballot_sync(0xffffffffu, c);
+    if (bal == 0u) {
+      flo = flo + 32 * step;
+    } else {
+      const int f = __ffs(bal) - 1;
+      fhi = flo + (f + 1) * step;
+      flo = flo + f * step;
+    }
+    if (fhi - flo <= 4e-7f * fmaxf(fabsf(flo), fabsf(fhi)) + 1e-30f) break;
+  }
+  const double shift = 0.5 * ((double)flo + (double)fhi);
+  if (lane == 0) {
+    for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.25 * (double)((i * 7) % 5);
+    const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    // two inverse iterations at the FP32 shift, a Rayleigh quotient, one more
+    // inverse iteration at that FP64 shift (so the last component of y, which
+    // decides convergence, is accurate), and the final Rayleigh quotient
+    double sh = shift, theta = shift;
+    for (int it = 0; it < 3; ++it) {
+      shifted_solve(a, b, n, sh, tiny, dl, d, du, du2, piv, x);
+      double nn = 0.0;
+      for (int i = 0; i < n; ++i) nn = fma(x[i], x[i], nn);
+      const double inv = 1.0 / sqrt(nn);
+      for (int i = 0; i < n; ++i) x[i] *= inv;
+      theta = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double ty = a[i] * x[i];
+        if (i > 0) ty = fma(b[i - 1], x[i - 1], ty);
+        if (i < n - 1) ty = fma(b[i], x[i + 1], ty);
+        theta = fma(x[i], ty, theta);
+      }
+      if (it == 1) sh = theta;
+    }
+    for (int i = 0; i < n; ++i) L.y[s * km + i] = x[i];
+    const double scale = fmax(1.0, fabs(theta));
+    const double res = beta_k * fabs(x[n - 1]);
+    L.theta[s] = theta;
+    L.resid[s] = res;
+    if (res <= L.tol * scale || beta_k <= 1e-14 * scale) {
+      L.active[s] = 0;
+      L.conv[s] = 1;
+    } else if (n >= km) {
+      L.active[s] = 0;
+      L.conv[s] = 0;
+    } else {
+      L.beta[s * km + kk] = beta_k;
+      L.k[s] = kk + 1;
+    }
+  }
+}
+
+// V[k] = w / beta[k-1] for superblocks still iterating (k already advanced)
+__global__ void next_kernel(LanczosDev L) {
+  const int s = blockIdx.y;
+  if (!L.active[s]) return;
+  const int64_t N = L.N[s];
+  const int kk = L.k[s];
+  const double inv = 1.0 / L.beta[s * L.kmax + kk - 1];
+  double *v = L.V[s] + (int64_t)kk * N;
+  const double *w = L.w[s];
+  for (int64_t e = (int64_t)blockIdx.x * CH + threadIdx.x; e < min(N, (int64_t)(blockIdx.x + 1) * CH); e += LT)
+    v[e] = w[e] * inv;
+}
+
+// generic: out_s = sum_j coef_j x_j  pieces ---------------------------------
+__global__ void norm_partial_kernel(const int64_t *Ns, int S, const double *const *x, double *part, int nchunk,
+                                    const int *mask) {
+  const int s = blockIdx.y;
+  if (mask && !mask[s]) return;
+  const int64_t N = Ns[s];
+  const int64_t e0 = (int64_t)blockIdx.x * CH;
+  if (e0 >= N) return;
+  double acc = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < min(N, e0 + CH); e += LT) acc = fma(x[s][e], x[s][e], acc);
+  __shared__ double red[LT / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < LT / 32; ++q) t += red[q];
+    part[(int64_t)s * nchunk + blockIdx.x] = t;
+  }
+}
+
+__global__ void dot_partial_kernel(const int64_t *Ns, const double *const *x, const double *const *y, double *part,
+                                   int nchunk, const int *mask) {
+  const int s = blockIdx.y;
+  if (mask && !mask[s]) return;
+  const int64_t N = Ns[s];
+  const int64_t e0 = (int64_t)blockIdx.x * CH;
+  if (e0 >= N) return;
+  double acc = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < min(N, e0 + CH); e += LT) acc = fma(x[s][e], y[s][e], acc);
+  __shared__ double red[LT / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < LT / 32; ++q) t += red[q];
+    part[(int64_t)s * nchunk + blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_partials_kernel(const int64_t *Ns, int S, const double *part, int nchunk, double *res,
+                                    const int *mask) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || (mask && !mask[s])) return;
+  const int nch = (int)((Ns[s] + CH - 1) / CH);
+  double acc = 0.0;
+  for (int c = 0; c < nch; ++c) acc += part[(int64_t)s * nchunk + c];
+  res[s] = acc;
+}
+
+// dst = src / sqrt(nrm2)  and resets the Lanczos state of that superblock
+__global__ void init_scale_kernel(LanczosDev L, const double *const *src, const double *nrm2) {
+  const int s = blockIdx.y;
+  if (!L.member[s]) return;
+  const int64_t N = L.N[s];
+  const double inv = 1.0 / sqrt(nrm2[s]);
+  for (int64_t e = (int64_t)blockIdx.x * CH + threadIdx.x; e < min(N, (int64_t)(blockIdx.x + 1) * CH); e += LT)
+    L.V[s][e] = src[s][e] * inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    L.k[s] = 0;
+    L.conv[s] = 0;
+    L.active[s] = 1;
+    if (!(nrm2[s] > 0.0) || !isfinite(nrm2[s])) atomicOr(L.err, IDMRG_DEV_ERR_ZERONORM | (16 << s));
+  }
+}
+
+// out = sum_j y_j V_j  (j < k+1)
+__global__ void ritz_kernel(LanczosDev L, double *const *out, const int *mask) {
+  const int s = blockIdx.y;
+  if (!mask[s]) return;
+  const int64_t N = L.N[s];
+  const int n = L.k[s] + 1;
+  const double *y = L.y + (int64_t)s * L.kmax;
+  for (int64_t e = (int64_t)blockIdx.x * CH + threadIdx.x; e < min(N, (int64_t)(blockIdx.x + 1) * CH);
+       e += LT) {
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc = fma(y[j], L.V[s][(int64_t)j * N + e], acc);
+    out[s][e] = acc;
+  }
+}
+
+__global__ void scale_by_kernel(const int64_t *Ns, double *const *x, const double *nrm2, const int *mask) {
+  const int s = blockIdx.y;
+  if (!mask[s]) return;
+  const int64_t N = Ns[s];
+  const double inv = 1.0 / sqrt(nrm2[s]);
+  for (int64_t e = (int64_t)blockIdx.x * CH + threadIdx.x; e < min(N, (int64_t)(blockIdx.x + 1) * CH); e += LT)
+    x[s][e] *= inv;
+}
+
+}  // namespace
+
+cudaError_t lanczos_set_ptrs(const LanczosDev &L, double **bufs, cudaStream_t st) {
+  set_ptrs_kernel<<<(L.S + 63) / 64, 64, 0, st>>>(L, bufs);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_project(const LanczosDev &L, int pass, cudaStream_t st) {
+  dim3 grid(L.nchunk_max, L.S);
+  project_kernel<<<grid, LT, (LT / 32) * L.kmax * sizeof(double), st>>>(L, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_subtract(const LanczosDev &L, int pass, cudaStream_t st) {
+  dim3 grid(L.nchunk_max, L.S);
+  subtract_kernel<<<grid, LT, (L.kmax + LT / 32) * sizeof(double), st>>>(L, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_finalize(const LanczosDev &L, cudaStream_t st) {
+  const size_t smem = (size_t)L.kmax * (8 * sizeof(double) + sizeof(int) + 2 * sizeof(float));
+  finalize_kernel<<<L.S, 32, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_next(const LanczosDev &L, cudaStream_t st) {
+  dim3 grid(L.nchunk_max, L.S);
+  next_kernel<<<grid, LT, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_init(const LanczosDev &L, const double *const *start, cudaStream_t st) {
+  // L.part (pass-2 region) is reused for the norm partials, L.resid for the sums
+  double *part = L.part;
+  dim3 grid(L.nchunk_max, L.S);
+  norm_partial_kernel<<<grid, LT, 0, st>>>(L.N, L.S, start, part, L.nchunk_max, L.member);
+  sum_partials_kernel<<<(L.S + 63) / 64, 64, 0, st>>>(L.N, L.S, part, L.nchunk_max, L.resid, L.member);
+  init_scale_kernel<<<grid, LT, 0, st>>>(L, start, L.resid);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_ritz(const LanczosDev &L, double *const *out, cudaStream_t st) {
+  dim3 grid(L.nchunk_max, L.S);
+  const int *mask = L.member;
+  ritz_kernel<<<grid, LT, 0, st>>>(L, out, mask);
+  norm_partial_kernel<<<grid, LT, 0, st>>>(L.N, L.S, out, L.part, L.nchunk_max, mask);
+  sum_partials_kernel<<<(L.S + 63) / 64, 64, 0, st>>>(L.N, L.S, L.part, L.nchunk_max, L.resid, mask);
+  scale_by_kernel<<<grid, LT, 0, st>>>(L.N, out, L.resid, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_dot(const LanczosDev &L, const double *const *a, const double *const *b, double *res,
+                        cudaStream_t st) {
+  dim3 grid(L.nchunk_max, L.S);
+  const int *mask = L.member;
+  dot_partial_kernel<<<grid, LT, 0, st>>>(L.N, a, b, L.part, L.nchunk_max, mask);
+  sum_partials_kernel<<<(L.S + 63) / 64, 64, 0, st>>>(L.N, L.S, L.part, L.nchunk_max, res, mask);
+  return cudaGetLastError();
+}
+
+}  // namespace idmrg
