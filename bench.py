@@ -240,6 +240,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     wall = []
     reports = []
     for k in range(args.steps):
@@ -252,6 +253,7 @@ def main():
         torch.cuda.synchronize()
         wall.append(time.perf_counter() - t)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()

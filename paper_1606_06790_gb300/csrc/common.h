@@ -92,11 +92,13 @@ struct SvdJob {
   int gr_start[4], gr_len[4], gr_stride[4];
   int gc_start[4], gc_len[4];
   int64_t base[16];
-  int64_t a_off;    // A in the SVD work buffer
-  int64_t j_off;    // J (cols_a x cols_a, column-major) in the SVD work buffer
+  int64_t a_off;    // A (rows_a x cols_a): Householder vectors after the QR
+  int64_t j_off;    // Jm (cols_a x cols_a): accumulated Jacobi rotations
+  int64_t b_off;    // B = R^T (cols_a x cols_a), Jacobi working matrix
+  int64_t x_off;    // rows_a x cols_a scratch for the back-transformation
+  int64_t tau_off;  // cols_a Householder coefficients
+  int perm_off;     // cols_a column permutation of the pivoted QR (int work)
   int sv_off;       // singular values of this job
-  int key_sec;      // |Q| and Q packed for tie-breaking
-  int pad;
 };
 
 // splitmix64 start-vector sub-block
@@ -171,6 +173,7 @@ cudaError_t lanczos_dot(const LanczosDev &L, const double *const *a, const doubl
 // SVD (FP64 one-sided Jacobi), see kernels_svd.cu
 cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_elems, double *const *bufs,
                                     int psi_buf, double *work, cudaStream_t st);
+cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, cudaStream_t st);
 cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, double *sv, int *err, cudaStream_t st);
 struct SelectOut {
   int *kept_per_job;   // [njobs]
@@ -189,8 +192,8 @@ struct CompactJob {
   int lam_off;         // destination of lambda (k entries)
   int pad;
 };
-cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, const double *work,
-                               const double *sv, const int *perm, const int *kept_per_job, double *const *bufs,
-                               double *lam, cudaStream_t st);
+cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, double *work,
+                               const int *iwork, const double *sv, const int *perm, const int *kept_per_job,
+                               double *const *bufs, double *lam, cudaStream_t st);
 
 }  // namespace idmrg

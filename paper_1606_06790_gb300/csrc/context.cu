@@ -121,7 +121,7 @@ struct idmrg_ctx {
   DevBuf lN, lV, lw, lalpha, lbeta, lh, lpart, lk, lmember, lactive, lconv, ltheta, ly, lresid, lpsi, lv0, ldot;
   int kmax = 0, nchunk = 0;
   // svd
-  DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk;
+  DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk, siw;
 
   std::vector<int> hmask;
 
@@ -763,7 +763,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   std::vector<int> job0(P, 0), njob(P, 0);
   std::vector<std::vector<SecInfo>> secs(P);
   int64_t work = 0;
-  int sv = 0, max_entries = 1;
+  int sv = 0, max_entries = 1, iw = 0;
   int64_t max_elems = 0;
   for (int q = 0; q < P; ++q) {
     job0[q] = (int)c->jobs.size();
@@ -815,10 +815,19 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
           if (psi.sj[k] != j) return c->fail(IDMRG_EINVAL, "internal: sector bookkeeping mismatch");
           J.base[g * 4 + h] = psi.roff[i] + psi.scol[k];
         }
+      if (J.cols_a > 4096) return c->fail(IDMRG_EINVAL, "charge sector with more than 4096 states per side");
       J.a_off = work;
+      work += (int64_t)J.rows_a * J.cols_a;
+      J.x_off = work;
       work += (int64_t)J.rows_a * J.cols_a;
       J.j_off = work;
       work += (int64_t)J.cols_a * J.cols_a;
+      J.b_off = work;
+      work += (int64_t)J.cols_a * J.cols_a;
+      J.tau_off = work;
+      work += J.cols_a;
+      J.perm_off = iw;
+      iw += J.cols_a;
       J.sv_off = sv;
       sv += J.cols_a;
       entries += J.cols_a;
@@ -831,6 +840,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
     max_entries = std::max(max_entries, entries);
   }
   const int nj = (int)c->jobs.size();
+  NOMEM(c->ensure(c->siw, 4 * std::max(iw, 1)));
   NOMEM(c->upload(c->sjobs, c->jobs) && c->ensure(c->swork, 8 * std::max<int64_t>(work, 1)) &&
         c->ensure(c->ssv, 8 * std::max(sv, 1)) && c->upload(c->sjob0, job0) && c->upload(c->snjob, njob) &&
         c->ensure(c->skpj, 4 * std::max(nj, 1)) && c->ensure(c->sperm, 4 * std::max(sv, 1)) &&
@@ -839,6 +849,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   double *const *bufs = (double *const *)c->dbufs.p;
   c->kbegin(IDMRG_K_SVD);
   CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, max_elems, bufs, BUF_PSI, c->dp(c->swork), c->st));
+  CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), (int *)c->siw.p, c->st));
   CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), c->dp(c->ssv), (int *)c->derr.p, c->st));
   // select runs on superblocks with jobs only: compact the index arrays
   std::vector<int> sbl;
@@ -924,8 +935,11 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   NOMEM(sync_bufs(c) == IDMRG_OK);
   NOMEM(c->upload(c->scj, cj) && c->ensure(c->slamk, 8 * (size_t)P * stride));
   c->kbegin(IDMRG_K_SVD);
-  CK(launch_svd_compact((const SvdJob *)c->sjobs.p, (const CompactJob *)c->scj.p, (int)cj.size(), c->dp(c->swork),
-                        c->dp(c->ssv), (const int *)c->sperm.p, (const int *)c->skpj.p, bufs, c->dp(c->slamk), c->st));
+  int max_kept = 1;
+  for (int v : kpj) max_kept = std::max(max_kept, v);
+  CK(launch_svd_compact((const SvdJob *)c->sjobs.p, (const CompactJob *)c->scj.p, (int)cj.size(), max_kept,
+                        c->dp(c->swork), (const int *)c->siw.p, c->dp(c->ssv), (const int *)c->sperm.p,
+                        (const int *)c->skpj.p, bufs, c->dp(c->slamk), c->st));
   c->kend(IDMRG_K_SVD);
   c->launches += 1;
   std::vector<double> lamk((size_t)P * stride);
@@ -1302,7 +1316,7 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
-                    &c->scj, &c->slamk})
+                    &c->scj, &c->slamk, &c->siw})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);

@@ -3,20 +3,32 @@
 //  gather  : copies the sector matrix M_Q (rows (x,s) of left charge Q,
 //            columns (t,y) of the complementary charge) out of the wavefunction
 //            into a column-major working matrix A (M or M^T, tall side first).
-//  jacobi  : one-sided (Hestenes) Jacobi: plane rotations orthogonalise the
-//            columns of A; the rotations accumulate in J.  Then A = U S, J = V
-//            (or the roles swap when A = M^T).  Parallel round-robin ordering,
-//            one warp per column pair, one CTA per job.
+//  qrcp    : Householder QR with column pivoting, A P = Q R.  This is the
+//            preconditioner of the Jacobi SVD (Drmac and Veselic): one-sided
+//            Jacobi on R^T needs a few sweeps where the same method on A needs
+//            about twenty for the graded spectra of a wavefunction.
+//  jacobi  : one-sided (Hestenes) Jacobi on B = R^T: plane rotations make the
+//            columns of B orthogonal, B Jm = U~ S.  Parallel round-robin
+//            ordering, one warp per column pair, the pairs of a round spread
+//            over a cluster of CTAs that meet at the hardware cluster barrier.
+//            Then A = (Q Jm) S (P U~)^T.
 //  select  : per superblock, sorts all singular values in descending order
 //            (ties by |Q|, Q, index), drops values at or below zero_rel*max,
 //            cuts at D <= m without splitting values closer than tie_rel, and
 //            writes the discarded weight (Eq. tru) and best fidelity error
 //            (Eq. fid2).
-//  compact : writes the kept columns of U and V per sector, descending.
+//  compact : for the kept columns only, forms the singular vectors of A
+//            (Q Jm e_j by the stored reflectors, P U~ e_j by the permutation)
+//            and writes them as the U and V blocks of the new bases.
+#include <cooperative_groups.h>
 #include <float.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.h"
+
+namespace cg = cooperative_groups;
 
 namespace idmrg {
 
@@ -50,28 +62,154 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-constexpr int JAC_THREADS = 512;
-constexpr int JAC_REG = 8;              // column elements per lane held in registers
-constexpr int JAC_SMEM_DOUBLES = 24576; // A kept in shared memory up to 192 KiB
+// ------------------------------------------------------------------ QRCP
+constexpr int QR_THREADS = 512;
 
-// one column pair (p, q): overlap, rotation of A's and J's columns
-__device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, double *jq, int ra, int ca,
-                                            int lane, double tol, double abs_floor) {
+__global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work,
+                                                          int *__restrict__ iwork) {
+  extern __shared__ double qsm[];  // vn[ca], vref[ca]
+  const SvdJob Jb = jobs[blockIdx.x];
+  const int ra = Jb.rows_a, ca = Jb.cols_a;
+  double *A = work + Jb.a_off;
+  double *tau = work + Jb.tau_off;
+  double *B = work + Jb.b_off;
+  int *perm = iwork + Jb.perm_off;
+  double *vn = qsm, *vref = qsm + ca;
+  __shared__ double red_v[QR_THREADS / 32];
+  __shared__ int red_i[QR_THREADS / 32];
+  __shared__ double s_beta, s_tau, s_scale;
+  __shared__ int s_piv;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < ca; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < ra; i += 32) s = fma(A[(int64_t)j * ra + i], A[(int64_t)j * ra + i], s);
+    s = wsum(s);
+    if (lane == 0) { vn[j] = s; vref[j] = s; perm[j] = j; }
+  }
+  __syncthreads();
+  for (int k = 0; k < ca; ++k) {
+    // pivot: largest remaining column norm (first index on ties)
+    double bv = -1.0;
+    int bi = k;
+    for (int j = k + threadIdx.x; j < ca; j += blockDim.x)
+      if (vn[j] > bv) { bv = vn[j]; bi = j; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = red_v[0];
+      int idx = red_i[0];
+      for (int q = 1; q < nw; ++q)
+        if (red_v[q] > v || (red_v[q] == v && red_i[q] < idx)) { v = red_v[q]; idx = red_i[q]; }
+      s_piv = idx;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != k) {
+      for (int i = threadIdx.x; i < ra; i += blockDim.x) {
+        const double t = A[(int64_t)k * ra + i];
+        A[(int64_t)k * ra + i] = A[(int64_t)p * ra + i];
+        A[(int64_t)p * ra + i] = t;
+      }
+      if (threadIdx.x == 0) {
+        double t = vn[k]; vn[k] = vn[p]; vn[p] = t;
+        t = vref[k]; vref[k] = vref[p]; vref[p] = t;
+        const int ti = perm[k]; perm[k] = perm[p]; perm[p] = ti;
+      }
+      __syncthreads();
+    }
+    // Householder reflector for column k, rows k..ra-1
+    double *ak = A + (int64_t)k * ra;
+    double s2 = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < ra; i += blockDim.x) s2 = fma(ak[i], ak[i], s2);
+    s2 = wsum(s2);
+    if (lane == 0) red_v[warp] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sig = 0.0;
+      for (int q = 0; q < nw; ++q) sig += red_v[q];
+      const double alpha = ak[k];
+      if (sig == 0.0) {
+        s_tau = 0.0;
+        s_beta = alpha;
+        s_scale = 1.0;
+      } else {
+        const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+        s_tau = (beta - alpha) / beta;
+        s_beta = beta;
+        s_scale = 1.0 / (alpha - beta);
+      }
+      tau[k] = s_tau;
+    }
+    __syncthreads();
+    const double tk = s_tau;
+    if (tk != 0.0) {
+      const double sc = s_scale;
+      for (int i = k + 1 + threadIdx.x; i < ra; i += blockDim.x) ak[i] *= sc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ak[k] = s_beta;
+    // apply H_k to the trailing columns, one warp per column
+    if (tk != 0.0) {
+      for (int j = k + 1 + warp; j < ca; j += nw) {
+        double *aj = A + (int64_t)j * ra;
+        double w = 0.0;
+        for (int i = k + 1 + lane; i < ra; i += 32) w = fma(ak[i], aj[i], w);
+        w = (wsum(w) + aj[k]) * tk;
+        __syncwarp();
+        if (lane == 0) aj[k] -= w;
+        for (int i = k + 1 + lane; i < ra; i += 32) aj[i] = fma(-w, ak[i], aj[i]);
+      }
+    }
+    __syncthreads();
+    // downdate the remaining column norms; recompute where cancellation hurts
+    for (int j = k + 1 + warp; j < ca; j += nw) {
+      const double *aj = A + (int64_t)j * ra;
+      double nv = vn[j] - aj[k] * aj[k];
+      if (!(nv > 1e-8 * vref[j])) {
+        double s = 0.0;
+        for (int i = k + 1 + lane; i < ra; i += 32) s = fma(aj[i], aj[i], s);
+        nv = wsum(s);
+        if (lane == 0) vref[j] = nv;
+      }
+      if (lane == 0) vn[j] = fmax(nv, 0.0);
+    }
+    __syncthreads();
+  }
+  // B = R^T (ca x ca, column-major): B(a, b) = R(b, a) for b <= a
+  for (int64_t e = threadIdx.x; e < (int64_t)ca * ca; e += blockDim.x) {
+    const int a = (int)(e % ca), b = (int)(e / ca);
+    B[e] = (b <= a) ? A[(int64_t)a * ra + b] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- Jacobi
+constexpr int JAC_THREADS = 512;
+constexpr int JAC_CLUSTER = 8;
+constexpr int JAC_REG = 8;  // column elements per lane held in registers
+
+// one column pair (p, q): overlap, rotation of B's and Jm's columns
+__device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, double *jq, int n, int lane,
+                                            double tol, double abs_floor) {
   double x[JAC_REG], y[JAC_REG];
   double al = 0.0, be = 0.0, ga = 0.0;
-  const bool inreg = ra <= 32 * JAC_REG;
+  const bool inreg = n <= 32 * JAC_REG;
   if (inreg) {
 #pragma unroll
     for (int r = 0; r < JAC_REG; ++r) {
       const int i = lane + 32 * r;
-      x[r] = i < ra ? ap[i] : 0.0;
-      y[r] = i < ra ? aq[i] : 0.0;
+      x[r] = i < n ? ap[i] : 0.0;
+      y[r] = i < n ? aq[i] : 0.0;
       al = fma(x[r], x[r], al);
       be = fma(y[r], y[r], be);
       ga = fma(x[r], y[r], ga);
     }
   } else {
-    for (int i = lane; i < ra; i += 32) {
+    for (int i = lane; i < n; i += 32) {
       const double u = ap[i], v = aq[i];
       al = fma(u, u, al);
       be = fma(v, v, be);
@@ -82,26 +220,32 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
   be = wsum(be);
   ga = wsum(ga);
   if (ga == 0.0 || !(fabs(ga) > tol * sqrt(al * be)) || !(fabs(ga) > abs_floor)) return false;
-  const double zeta = (be - al) / (2.0 * ga);
-  const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+  double cs = 0.0, sn = 0.0;
+  if (lane == 0) {
+    const double zeta = (be - al) / (2.0 * ga);
+    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    cs = 1.0 / sqrt(1.0 + t * t);
+    sn = cs * t;
+  }
+  cs = __shfl_sync(0xffffffffu, cs, 0);
+  sn = __shfl_sync(0xffffffffu, sn, 0);
   if (inreg) {
 #pragma unroll
     for (int r = 0; r < JAC_REG; ++r) {
       const int i = lane + 32 * r;
-      if (i < ra) {
+      if (i < n) {
         ap[i] = cs * x[r] - sn * y[r];
         aq[i] = sn * x[r] + cs * y[r];
       }
     }
   } else {
-    for (int i = lane; i < ra; i += 32) {
+    for (int i = lane; i < n; i += 32) {
       const double u = ap[i], v = aq[i];
       ap[i] = cs * u - sn * v;
       aq[i] = sn * u + cs * v;
     }
   }
-  for (int i = lane; i < ca; i += 32) {
+  for (int i = lane; i < n; i += 32) {
     const double u = jp[i], v = jq[i];
     jp[i] = cs * u - sn * v;
     jq[i] = sn * u + cs * v;
@@ -109,71 +253,86 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
   return true;
 }
 
-__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const SvdJob *__restrict__ jobs,
-                                                             double *__restrict__ work, double *__restrict__ sv,
-                                                             int *err) {
-  extern __shared__ double As[];
-  const SvdJob Jb = jobs[blockIdx.x];
-  const int ra = Jb.rows_a, ca = Jb.cols_a;
-  double *Ag = work + Jb.a_off;
-  double *J = work + Jb.j_off;
-  const bool sm = (int64_t)ra * ca <= JAC_SMEM_DOUBLES;
-  double *A = sm ? As : Ag;
-  if (sm)
-    for (int64_t e = threadIdx.x; e < (int64_t)ra * ca; e += blockDim.x) As[e] = Ag[e];
-  for (int64_t e = threadIdx.x; e < (int64_t)ca * ca; e += blockDim.x)
-    J[e] = (e / ca == e % ca) ? 1.0 : 0.0;
-  __shared__ int changed;
-  __shared__ double fro_part[JAC_THREADS / 32];
+__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREADS)
+    jacobi_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work, double *__restrict__ sv, int *err) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const SvdJob Jb = jobs[blockIdx.x / JAC_CLUSTER];
+  const int n = Jb.cols_a;
+  double *B = work + Jb.b_off;
+  double *Jm = work + Jb.j_off;
+  __shared__ double fro_part[JAC_CLUSTER];
+  __shared__ double wred[JAC_THREADS / 32];
+  __shared__ int flag, local_changed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int np = ca + (ca & 1);
-  // rotation threshold sqrt(rows) * eps (as in LAPACK's one-sided Jacobi), and
-  // an absolute floor eps^2 ||A||_F^2: without it a column made of rounding
-  // noise along another one never meets the relative test (each rotation leaves
-  // an eps-sized overlap that dominates tol |a_p| |a_q| as |a_q| -> 0).
-  const double tol = sqrt((double)ra) * DBL_EPSILON;
+  const int gw = crank * nw + warp, gnw = JAC_CLUSTER * nw;
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)JAC_CLUSTER * blockDim.x)
+    Jm[e] = (e / n == e % n) ? 1.0 : 0.0;
+  // ||B||_F^2 over the cluster (partials gathered in rank 0's shared memory)
   double fro = 0.0;
-  for (int64_t e = threadIdx.x; e < (int64_t)ra * ca; e += blockDim.x) fro = fma(Ag[e], Ag[e], fro);
+  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)JAC_CLUSTER * blockDim.x)
+    fro = fma(B[e], B[e], fro);
   fro = wsum(fro);
-  if (lane == 0) fro_part[warp] = fro;
+  if (lane == 0) wred[warp] = fro;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += wred[q];
+    double *dst = cluster.map_shared_rank(fro_part, 0);
+    dst[crank] = t;
+  }
+  cluster.sync();
+  const double *fp0 = cluster.map_shared_rank(fro_part, 0);
   fro = 0.0;
-  for (int q = 0; q < nw; ++q) fro += fro_part[q];
+  for (int q = 0; q < JAC_CLUSTER; ++q) fro += fp0[q];
+  cluster.sync();  // every CTA has read rank 0's partials
+  // rotation threshold sqrt(rows) * eps (as in LAPACK's one-sided Jacobi) and
+  // an absolute floor eps^2 ||B||_F^2: without it a column made of rounding
+  // noise along another one never meets the relative test (each rotation
+  // leaves an eps-sized overlap that dominates tol |b_p| |b_q| as |b_q| -> 0).
+  const double tol = sqrt((double)n) * DBL_EPSILON;
   const double abs_floor = 4.0 * DBL_EPSILON * DBL_EPSILON * fro;
-  bool converged = (ca < 2);
-  for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
-    if (threadIdx.x == 0) changed = 0;
-    __syncthreads();
+  const int np = n + (n & 1);
+  int *flag0 = cluster.map_shared_rank(&flag, 0);
+  bool converged = (n < 2);
+  for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
+    if (threadIdx.x == 0) local_changed = 0;
+    if (crank == 0 && threadIdx.x == 0) flag = 0;
+    cluster.sync();
+    bool any = false;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
-      bool any = false;
-      for (int k = warp; k < np / 2; k += nw) {
+      for (int k = gw; k < np / 2; k += gnw) {
         const int i1 = k, i2 = np - 1 - k;
         const int p = i1 == 0 ? 0 : 1 + (i1 - 1 + rnd) % (np - 1);
         const int q = i2 == 0 ? 0 : 1 + (i2 - 1 + rnd) % (np - 1);
-        if (p >= ca || q >= ca) continue;
-        any |= jacobi_pair(A + (int64_t)p * ra, A + (int64_t)q * ra, J + (int64_t)p * ca, J + (int64_t)q * ca, ra,
-                           ca, lane, tol, abs_floor);
+        if (p >= n || q >= n) continue;
+        any |= jacobi_pair(B + (int64_t)p * n, B + (int64_t)q * n, Jm + (int64_t)p * n, Jm + (int64_t)q * n, n,
+                           lane, tol, abs_floor);
       }
-      if (any && lane == 0) changed = 1;
-      __syncthreads();
+      cluster.sync();
     }
-    converged = (changed == 0);
+    if (any && lane == 0) local_changed = 1;
     __syncthreads();
+    if (threadIdx.x == 0 && local_changed) atomicOr(flag0, 1);
+    cluster.sync();
+    converged = (*flag0 == 0);
+    cluster.sync();
   }
-  if (!converged && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
-  for (int j = warp; j < ca; j += nw) {
-    const double *aj = A + (int64_t)j * ra;
+  if (!converged && crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
+  // singular values; columns of B normalised in place
+  for (int j = gw; j < n; j += gnw) {
+    double *bj = B + (int64_t)j * n;
     double s = 0.0;
-    for (int i = lane; i < ra; i += 32) s = fma(aj[i], aj[i], s);
-    s = wsum(s);
-    if (lane == 0) sv[Jb.sv_off + j] = sqrt(s);
-  }
-  if (sm) {
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)ra * ca; e += blockDim.x) Ag[e] = As[e];
+    for (int i = lane; i < n; i += 32) s = fma(bj[i], bj[i], s);
+    s = sqrt(wsum(s));
+    if (lane == 0) sv[Jb.sv_off + j] = s;
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int i = lane; i < n; i += 32) bj[i] *= inv;
   }
 }
 
+// ---------------------------------------------------------------- select
 struct Entry {
   double s;
   int job, j;
@@ -251,33 +410,51 @@ __global__ void select_kernel(const SvdJob *__restrict__ jobs, const int *__rest
   }
 }
 
+// --------------------------------------------------------------- compact
+// One warp per kept column: left singular vector of A = Q [Jm e_j; 0]
+// (reflectors applied last to first), right one = P U~ e_j.
 __global__ void compact_kernel(const SvdJob *__restrict__ jobs, const CompactJob *__restrict__ cjs,
-                               const double *__restrict__ work, const double *__restrict__ sv,
-                               const int *__restrict__ perm, const int *__restrict__ kept_per_job,
-                               double *const *__restrict__ bufs, double *__restrict__ lam) {
+                               double *__restrict__ work, const int *__restrict__ iwork,
+                               const double *__restrict__ sv, const int *__restrict__ perm,
+                               const int *__restrict__ kept_per_job, double *const *__restrict__ bufs,
+                               double *__restrict__ lam) {
   const CompactJob cj = cjs[blockIdx.x];
   const SvdJob J = jobs[cj.job];
   const int k = kept_per_job[cj.job];
+  const int ra = J.rows_a, ca = J.cols_a;
   const double *A = work + J.a_off;
+  const double *tau = work + J.tau_off;
   const double *Jm = work + J.j_off;
+  const double *Bn = work + J.b_off;
+  const int *qperm = iwork + J.perm_off;
   double *U = bufs[J.sb * NBUF + BUF_U] + cj.u_off;
   double *V = bufs[J.sb * NBUF + BUF_V] + cj.v_off;
-  const int64_t nu = (int64_t)J.r * k, nv = (int64_t)J.c * k;
-  for (int64_t e = threadIdx.x + (int64_t)blockIdx.y * blockDim.x; e < nu + nv;
-       e += (int64_t)blockDim.x * gridDim.y) {
-    if (e < nu) {
-      const int row = (int)(e / k), slot = (int)(e % k);
-      const int jx = perm[J.sv_off + slot];
-      U[e] = !J.transposed ? A[(int64_t)jx * J.r + row] / sv[J.sv_off + jx] : Jm[(int64_t)jx * J.r + row];
-    } else {
-      const int64_t f = e - nu;
-      const int col = (int)(f / k), slot = (int)(f % k);
-      const int jx = perm[J.sv_off + slot];
-      V[f] = !J.transposed ? Jm[(int64_t)jx * J.c + col] : A[(int64_t)jx * J.c + col] / sv[J.sv_off + jx];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.y * (blockDim.x >> 5) + warp, gnw = gridDim.y * (blockDim.x >> 5);
+  for (int slot = gw; slot < k; slot += gnw) {
+    const int col = perm[J.sv_off + slot];
+    double *x = work + J.x_off + (int64_t)slot * ra;
+    for (int i = lane; i < ra; i += 32) x[i] = i < ca ? Jm[(int64_t)col * ca + i] : 0.0;
+    __syncwarp();
+    for (int kk = ca - 1; kk >= 0; --kk) {
+      const double t = tau[kk];
+      if (t == 0.0) continue;
+      const double *v = A + (int64_t)kk * ra;
+      double w = 0.0;
+      for (int i = kk + 1 + lane; i < ra; i += 32) w = fma(v[i], x[i], w);
+      w = (wsum(w) + x[kk]) * t;
+      __syncwarp();
+      if (lane == 0) x[kk] -= w;
+      for (int i = kk + 1 + lane; i < ra; i += 32) x[i] = fma(-w, v[i], x[i]);
+      __syncwarp();
     }
+    // left vectors of A: rows_a entries; right vectors: cols_a entries
+    double *Lout = !J.transposed ? U : V;
+    double *Rout = !J.transposed ? V : U;
+    for (int i = lane; i < ra; i += 32) Lout[(int64_t)i * k + slot] = x[i];
+    for (int i = lane; i < ca; i += 32) Rout[(int64_t)qperm[i] * k + slot] = Bn[(int64_t)col * ca + i];
+    if (lane == 0) lam[cj.lam_off + slot] = sv[J.sv_off + col];
   }
-  if (blockIdx.y == 0)
-    for (int slot = threadIdx.x; slot < k; slot += blockDim.x) lam[cj.lam_off + slot] = sv[J.sv_off + perm[J.sv_off + slot]];
 }
 
 }  // namespace
@@ -291,11 +468,17 @@ cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_e
   return cudaGetLastError();
 }
 
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, double *sv, int *err, cudaStream_t st) {
-  const int smem = JAC_SMEM_DOUBLES * (int)sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, cudaStream_t st) {
+  // shared: two norms per column; callers keep cols_a <= 4096
+  const int smem = 2 * 4096 * (int)sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (njobs > 0) jacobi_kernel<<<njobs, JAC_THREADS, smem, st>>>(jobs, work, sv, err);
+  if (njobs > 0) qrcp_kernel<<<njobs, QR_THREADS, smem, st>>>(jobs, work, iwork);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, double *sv, int *err, cudaStream_t st) {
+  if (njobs > 0) jacobi_kernel<<<njobs * JAC_CLUSTER, JAC_THREADS, 0, st>>>(jobs, work, sv, err);
   return cudaGetLastError();
 }
 
@@ -311,12 +494,13 @@ cudaError_t launch_svd_select(const SvdJob *jobs, const int *sb_job0, const int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, const double *work,
-                               const double *sv, const int *perm, const int *kept_per_job, double *const *bufs,
-                               double *lam, cudaStream_t st) {
+cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, double *work,
+                               const int *iwork, const double *sv, const int *perm, const int *kept_per_job,
+                               double *const *bufs, double *lam, cudaStream_t st) {
   if (ncj > 0) {
-    dim3 grid(ncj, 8);
-    compact_kernel<<<grid, 256, 0, st>>>(jobs, cj, work, sv, perm, kept_per_job, bufs, lam);
+    const int warps = 8;
+    dim3 grid(ncj, (unsigned)std::max(1, (max_kept + warps - 1) / warps));
+    compact_kernel<<<grid, 32 * warps, 0, st>>>(jobs, cj, work, iwork, sv, perm, kept_per_job, bufs, lam);
   }
   return cudaGetLastError();
 }
