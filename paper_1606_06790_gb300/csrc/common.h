@@ -30,8 +30,17 @@ enum BufId {
   BUF_AUX = 15,
   BUF_UPREV = 16, // prediction source: u^(n-1) of superblock p+1
   BUF_VPREV = 17, // prediction source: v^(n-1) of superblock p
-  NBUF = 18
+  // mixed-precision H_eff psi (tensor cores): packed TF32 hi/lo operands
+  BUF_PA1 = 18,   // stage 1 A: L blocks stacked over channels, per in-sector
+  BUF_PB1 = 19,   // stage 1 B: psi^T per in-sector (packed every matvec)
+  BUF_T1F = 20,   // stage 1 output, FP32
+  BUF_PA3 = 21,   // stage 3 A: T3 = W12 T1 (written by the W stage)
+  BUF_PB3 = 22,   // stage 3 B: R blocks concatenated over channels, per out-sector
+  BUF_RMAP = 23,  // stage 3 output row -> psi offset (int64)
+  NBUF = 24
 };
+
+
 
 // C[M x N] (+)= sum_seg alpha * op(A)[M x K] * op(B)[K x N]
 //   op(A) = A (row-major, lda) or A^T (A stored K x M, lda) when (flags & 1)
@@ -158,7 +167,9 @@ struct LanczosDev {
   double *resid;         // [S]
   int *err;              // device error word
   int nchunk_max;
-  double tol;
+  double tol;            // convergence: |b_k y_k| <= tol max(1, |theta|) ...
+  double inner_factor;   // ... or, from the second Krylov vector on, <= target[s]
+  double *target;        // [S] set at k = 0: max(tol max(1,|theta|), inner_factor b_0)
 };
 cudaError_t lanczos_set_ptrs(const LanczosDev &L, double **bufs, cudaStream_t st);
 cudaError_t lanczos_project(const LanczosDev &L, int pass, cudaStream_t st);   // h = V^T w  (j <= k)
@@ -195,5 +206,39 @@ struct CompactJob {
 cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, double *work,
                                const int *iwork, const double *sv, const int *perm, const int *kept_per_job,
                                double *const *bufs, double *lam, cudaStream_t st);
+
+// ---- tensor-core path (kernels_tc.cu)
+// Packed operand matrix: tiles of (8 G) rows x 32 K, K-major, core matrices
+// 8 x 4 (16 bytes) ordered [K chunk][row group][row][4]; per tile the hi part
+// then the lo part; tiles ordered [row tile][K block].
+struct PackSeg {
+  int64_t dst_off, src_off;
+  int row0, k0, rows, ks;
+  int src_ld, trans;      // trans: source element (row, k) at src[k * src_ld + row]
+  int KB, G;              // K blocks and row groups of the packed matrix
+  int sb, src_buf, dst_buf, src_fp32;
+};
+struct WTaskP {           // T3 rectangle written into a packed stage-3 A matrix
+  int64_t dst_off;
+  int row0, k0, KB, G;
+  int sb, rows, cols, term0, nterm, pad;
+};
+struct TcTask {
+  int64_t a_off, b_off, c_off, rmap_off;
+  int sb, M, N, KB;
+  int a_buf, b_buf, c_buf, rmap_buf;
+  int mode, ldc;          // mode 0: FP32 row-major C; 1: FP64 through the row map
+};
+struct TcTile {
+  int task, mt, nt, pad;
+};
+constexpr int TC_TN = 64;      // N tile (TMEM columns)
+constexpr int TC_STAGES = 2;   // shared-memory ring depth
+cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
+                        cudaStream_t st);
+cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
+                             double *const *bufs, const int *active, cudaStream_t st);
+cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
+                           const int *active, int *err, cudaStream_t st);
 
 }  // namespace idmrg

@@ -99,6 +99,17 @@ struct idmrg_ctx {
   std::vector<double> energy, fidelity, bond, startnorm;
   std::vector<int> iters, conv;
 
+  // mixed precision (tensor cores)
+  bool mixed = false;
+  std::vector<PackSeg> pk_step, pk_psi;   // per iteration (L, R) and per matvec (psi)
+  std::vector<TcTask> tc1k, tc3k;
+  std::vector<TcTile> tc1t, tc3t;
+  std::vector<WTaskP> wtp;
+  std::vector<WTerm> wtpm;
+  int pk_step_rows = 0, pk_psi_rows = 0, wtp_rows = 0;
+  DevBuf dpks, dpkp, dtc1k, dtc1t, dtc3k, dtc3t, dwtp, dwtpm, dtarget;
+  std::vector<DevBuf> bPA1, bPB1, bT1F, bPA3, bPB3, bRMAP;
+
   // plan for iteration n
   std::vector<SBPlan> plan;
   GemmList g1, g3, gp, genv1, genv3;
@@ -124,6 +135,7 @@ struct idmrg_ctx {
   DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk, siw;
 
   std::vector<int> hmask;
+  uint64_t mixed_matvecs = 0, fp64_matvecs = 0;
 
   // instrumentation: per-class CUDA-event timers, transfer counters
   struct KTimer {
@@ -251,6 +263,8 @@ namespace {
 // ------------------------------------------------------------------------
 // planning of iteration n
 // ------------------------------------------------------------------------
+idmrg_status plan_mixed(idmrg_ctx *c);
+
 idmrg_status plan_iteration(idmrg_ctx *c) {
   const int P = c->P, d = c->d, target = c->o.target_charge;
   c->plan.assign(P, SBPlan());
@@ -444,6 +458,10 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
     c->hbufs[p * NBUF + BUF_PSI] = c->dp(c->bPsi[p]);
   }
   NOMEM(c->upload(c->dbufs, c->hbufs));
+  if (c->mixed) {
+    idmrg_status s = plan_mixed(c);
+    if (s != IDMRG_OK) return s;
+  }
   for (int p = 0; p < P; ++p) c->stage[p] = ST_READY;
   return IDMRG_OK;
 }
@@ -453,9 +471,265 @@ idmrg_status sync_bufs(idmrg_ctx *c) {
   return IDMRG_OK;
 }
 
+// Tensor-core form of every superblock's H_eff psi (see kernels_tc.cu):
+//   stage 1, per in-sector si of the left block: rows = (channel a, x) of the
+//     L_a blocks stacked over a, K = x' in si, N = the psi row block of si;
+//   stage 3, per out-sector jo of the right block: rows = (i, s, t, x) of the
+//     psi sub-blocks with right sector jo, K = (channel c, y') concatenated over
+//     the R channels, N = y in jo.
+idmrg_status plan_mixed(idmrg_ctx *c) {
+  const int P = c->P, d = c->d, target = c->o.target_charge, dd = d * d;
+  const int GA = 16, GB = TC_TN / 8;
+  const int64_t TA = 128 * 32, TB = (int64_t)TC_TN * 32;
+  auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+  c->pk_step.clear();
+  c->pk_psi.clear();
+  c->tc1k.clear();
+  c->tc1t.clear();
+  c->tc3k.clear();
+  c->tc3t.clear();
+  c->wtp.clear();
+  c->wtpm.clear();
+  c->pk_step_rows = c->pk_psi_rows = c->wtp_rows = 0;
+  auto seg = [&](std::vector<PackSeg> &v, int &mr, int sb, int dst_buf, int64_t dst_off, int src_buf,
+                 int64_t src_off, int row0, int k0, int rows, int ks, int ld, int trans, int KB, int G) {
+    if (rows <= 0 || ks <= 0) return;
+    PackSeg p{};
+    p.dst_off = dst_off;
+    p.src_off = src_off;
+    p.row0 = row0;
+    p.k0 = k0;
+    p.rows = rows;
+    p.ks = ks;
+    p.src_ld = ld;
+    p.trans = trans;
+    p.KB = KB;
+    p.G = G;
+    p.sb = sb;
+    p.src_buf = src_buf;
+    p.dst_buf = dst_buf;
+    p.src_fp32 = 0;
+    v.push_back(p);
+    mr = std::max(mr, rows);
+  };
+  for (int p = 0; p < P; ++p) {
+    SBPlan &S = c->plan[p];
+    const Env &L = c->envL[p];
+    const Env &R = c->envR[(p + 1) % P];
+    const Basis &BL = L.lay.b, &BR = R.lay.b;
+    const PsiLayout &psi = S.psi;
+    const int SL = BL.S(), SR = BR.S();
+    const int wa = L.lay.w, wc = R.lay.w;
+    // ---------------- stage 1
+    std::vector<int64_t> pa1(SL, -1), pb1(SL, -1), t1f(SL, -1);
+    std::vector<std::vector<int>> rs1(SL, std::vector<int>(wa, -1));
+    int64_t pa1n = 0, pb1n = 0, t1fn = 0;
+    for (int si = 0; si < SL; ++si) {
+      if (psi.C[si] == 0) continue;
+      int M = 0;
+      for (int a = 0; a < wa; ++a) {
+        const int so = L.lay.so[a * SL + si];
+        if (so < 0) continue;
+        rs1[si][a] = M;
+        M += BL.dim[so];
+      }
+      if (M == 0) continue;
+      const int K = BL.dim[si], N = psi.C[si];
+      const int KB = (int)cdiv(K, 32), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      pa1[si] = pa1n;
+      pa1n += (int64_t)MT * KB * 2 * TA;
+      pb1[si] = pb1n;
+      pb1n += (int64_t)NT * KB * 2 * TB;
+      t1f[si] = t1fn;
+      t1fn += (int64_t)M * N;
+      for (int a = 0; a < wa; ++a) {
+        if (rs1[si][a] < 0) continue;
+        const int so = L.lay.so[a * SL + si];
+        seg(c->pk_step, c->pk_step_rows, p, BUF_PA1, pa1[si], BUF_L, L.lay.off[a * SL + si], rs1[si][a], 0,
+            BL.dim[so], K, K, 0, KB, GA);
+      }
+      seg(c->pk_psi, c->pk_psi_rows, p, BUF_PB1, pb1[si], BUF_IN, psi.roff[si], 0, 0, N, K, N, 1, KB, GB);
+      TcTask t{};
+      t.a_off = pa1[si];
+      t.b_off = pb1[si];
+      t.c_off = t1f[si];
+      t.sb = p;
+      t.M = M;
+      t.N = N;
+      t.KB = KB;
+      t.a_buf = BUF_PA1;
+      t.b_buf = BUF_PB1;
+      t.c_buf = BUF_T1F;
+      t.mode = 0;
+      t.ldc = N;
+      const int id = (int)c->tc1k.size();
+      c->tc1k.push_back(t);
+      for (int mt = 0; mt < MT; ++mt)
+        for (int nt = 0; nt < NT; ++nt) c->tc1t.push_back(TcTile{id, mt, nt, 0});
+    }
+    // ---------------- stage 3
+    std::vector<int64_t> pa3(SR, -1), pb3(SR, -1), rmo(SR, -1);
+    std::vector<int64_t> rmap;
+    int64_t pa3n = 0, pb3n = 0;
+    for (int jo = 0; jo < SR; ++jo) {
+      // K: channels c whose R_c block lands in jo
+      std::vector<int> ks(wc, -1);
+      int K = 0;
+      for (int cc = 0; cc < wc; ++cc) {
+        const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+        if (jin < 0 || R.lay.so[cc * SR + jin] != jo) continue;
+        ks[cc] = K;
+        K += BR.dim[jin];
+      }
+      // rows: sub-blocks (i, s, t) with right sector jo
+      std::vector<int> rows_of(SL * dd, -1);
+      int M = 0;
+      const int64_t r0 = (int64_t)rmap.size();
+      for (int i = 0; i < SL; ++i)
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const int k = psi.sub(i, s, t);
+            if (psi.sj[k] != jo) continue;
+            rows_of[k] = M;
+            for (int x = 0; x < BL.dim[i]; ++x) rmap.push_back(psi.roff[i] + (int64_t)x * psi.C[i] + psi.scol[k]);
+            M += BL.dim[i];
+          }
+      if (M == 0) continue;
+      const int N = BR.dim[jo];
+      const int KB = (int)cdiv(std::max(K, 1), 32), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      pa3[jo] = pa3n;
+      pa3n += (int64_t)MT * KB * 2 * TA;
+      pb3[jo] = pb3n;
+      pb3n += (int64_t)NT * KB * 2 * TB;
+      rmo[jo] = r0;
+      for (int cc = 0; cc < wc; ++cc) {
+        if (ks[cc] < 0) continue;
+        const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+        seg(c->pk_step, c->pk_step_rows, p, BUF_PB3, pb3[jo], BUF_R, R.lay.off[cc * SR + jin], 0, ks[cc], N,
+            BR.dim[jin], BR.dim[jin], 0, KB, GB);
+      }
+      // W stage: T3[c](i,s,t) into rows rows_of(i,s,t), columns ks[c]
+      for (int i = 0; i < SL; ++i)
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const int k = psi.sub(i, s, t);
+            if (rows_of[k] < 0) continue;
+            for (int cc = 0; cc < wc; ++cc) {
+              if (ks[cc] < 0) continue;
+              const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+              WTaskP w{};
+              w.dst_off = pa3[jo];
+              w.row0 = rows_of[k];
+              w.k0 = ks[cc];
+              w.KB = KB;
+              w.G = GA;
+              w.sb = p;
+              w.rows = BL.dim[i];
+              w.cols = BR.dim[jin];
+              w.term0 = (int)c->wtpm.size();
+              for (int a = 0; a < wa; ++a) {
+                const int si = BL.find(BL.q[i] - L.lay.chq[a]);
+                if (si < 0 || L.lay.so[a * SL + si] != i || rs1[si][a] < 0) continue;
+                for (int s2 = 0; s2 < d; ++s2)
+                  for (int t2 = 0; t2 < d; ++t2) {
+                    const double cf = S.W12[(((size_t)a * wc + cc) * dd + s * d + t) * dd + s2 * d + t2];
+                    if (cf == 0.0) continue;
+                    const int k2 = psi.sub(si, s2, t2);
+                    if (psi.sj[k2] != jin) continue;
+                    WTerm term{};
+                    term.in_off = t1f[si] + (int64_t)rs1[si][a] * psi.C[si] + psi.scol[k2];
+                    term.in_ld = psi.C[si];
+                    term.coef = cf;
+                    c->wtpm.push_back(term);
+                  }
+              }
+              w.nterm = (int)c->wtpm.size() - w.term0;
+              if (w.nterm == 0) continue;  // the packed rectangle stays zero
+              c->wtp.push_back(w);
+              c->wtp_rows = std::max(c->wtp_rows, w.rows);
+            }
+          }
+      TcTask t{};
+      t.a_off = pa3[jo];
+      t.b_off = pb3[jo];
+      t.rmap_off = rmo[jo];
+      t.sb = p;
+      t.M = M;
+      t.N = N;
+      t.KB = K > 0 ? KB : 0;
+      t.a_buf = BUF_PA3;
+      t.b_buf = BUF_PB3;
+      t.c_buf = BUF_OUT;
+      t.rmap_buf = BUF_RMAP;
+      t.mode = 1;
+      const int id = (int)c->tc3k.size();
+      c->tc3k.push_back(t);
+      for (int mt = 0; mt < MT; ++mt)
+        for (int nt = 0; nt < NT; ++nt) c->tc3t.push_back(TcTile{id, mt, nt, 0});
+    }
+    NOMEM(c->ensure(c->bPA1[p], 4 * std::max<int64_t>(pa1n, 4)) &&
+          c->ensure(c->bPB1[p], 4 * std::max<int64_t>(pb1n, 4)) &&
+          c->ensure(c->bT1F[p], 4 * std::max<int64_t>(t1fn, 4)) &&
+          c->ensure(c->bPA3[p], 4 * std::max<int64_t>(pa3n, 4)) &&
+          c->ensure(c->bPB3[p], 4 * std::max<int64_t>(pb3n, 4)) && c->upload(c->bRMAP[p], rmap));
+    // zero padding of every packed operand (only real elements are rewritten later)
+    CK(cudaMemsetAsync(c->bPA1[p].p, 0, 4 * pa1n, c->st));
+    CK(cudaMemsetAsync(c->bPB1[p].p, 0, 4 * pb1n, c->st));
+    CK(cudaMemsetAsync(c->bPA3[p].p, 0, 4 * pa3n, c->st));
+    CK(cudaMemsetAsync(c->bPB3[p].p, 0, 4 * pb3n, c->st));
+    c->hbufs[p * NBUF + BUF_PA1] = c->dp(c->bPA1[p]);
+    c->hbufs[p * NBUF + BUF_PB1] = c->dp(c->bPB1[p]);
+    c->hbufs[p * NBUF + BUF_T1F] = c->dp(c->bT1F[p]);
+    c->hbufs[p * NBUF + BUF_PA3] = c->dp(c->bPA3[p]);
+    c->hbufs[p * NBUF + BUF_PB3] = c->dp(c->bPB3[p]);
+    c->hbufs[p * NBUF + BUF_RMAP] = c->dp(c->bRMAP[p]);
+  }
+  NOMEM(c->upload(c->dpks, c->pk_step) && c->upload(c->dpkp, c->pk_psi) && c->upload(c->dtc1k, c->tc1k) &&
+        c->upload(c->dtc1t, c->tc1t) && c->upload(c->dtc3k, c->tc3k) && c->upload(c->dtc3t, c->tc3t) &&
+        c->upload(c->dwtp, c->wtp) && c->upload(c->dwtpm, c->wtpm));
+  NOMEM(c->upload(c->dbufs, c->hbufs));
+  // split the environments once for this iteration
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(launch_pack((const PackSeg *)c->dpks.p, (int)c->pk_step.size(), c->pk_step_rows, (double *const *)c->dbufs.p,
+                 nullptr, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE);
+  c->launches += 1;
+  return IDMRG_OK;
+}
+
 // heff on every superblock whose active flag is set (device array); the host
 // copy `act` (may be null = all) only feeds the flop/byte accounting
-idmrg_status heff_launch(idmrg_ctx *c, const int *active_dev, const int *act) {
+idmrg_status heff_launch_fp64(idmrg_ctx *c, const int *active_dev, const int *act);
+idmrg_status heff_launch_mixed(idmrg_ctx *c, const int *active_dev, const int *act) {
+  double *const *bufs = (double *const *)c->dbufs.p;
+  double gf = 0, by = 0, wf = 0;
+  for (int q = 0; q < c->P; ++q)
+    if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(launch_pack((const PackSeg *)c->dpkp.p, (int)c->pk_psi.size(), c->pk_psi_rows, bufs, active_dev, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE);
+  c->kbegin(IDMRG_K_HEFF_GEMM);
+  CK(launch_tc_gemm((const TcTile *)c->dtc1t.p, (int)c->tc1t.size(), (const TcTask *)c->dtc1k.p, bufs, active_dev,
+                    (int *)c->derr.p, c->st));
+  c->kend(IDMRG_K_HEFF_GEMM);
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(launch_wstage_tc((const WTaskP *)c->dwtp.p, (int)c->wtp.size(), c->wtp_rows, (const WTerm *)c->dwtpm.p, bufs,
+                      active_dev, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
+  c->kbegin(IDMRG_K_HEFF_GEMM);
+  CK(launch_tc_gemm((const TcTile *)c->dtc3t.p, (int)c->tc3t.size(), (const TcTask *)c->dtc3k.p, bufs, active_dev,
+                    (int *)c->derr.p, c->st));
+  c->kend(IDMRG_K_HEFF_GEMM, gf, by);
+  c->launches += 4;
+  c->mixed_matvecs += 1;
+  return IDMRG_OK;
+}
+idmrg_status heff_launch(idmrg_ctx *c, const int *active_dev, const int *act, bool fp64) {
+  if (c->mixed && !fp64) return heff_launch_mixed(c, active_dev, act);
+  return heff_launch_fp64(c, active_dev, act);
+}
+idmrg_status heff_launch_fp64(idmrg_ctx *c, const int *active_dev, const int *act) {
+  c->fp64_matvecs += 1;
   double *const *bufs = (double *const *)c->dbufs.p;
   double gf = 0, wf = 0, by = 0;
   for (int q = 0; q < c->P; ++q)
@@ -673,61 +947,89 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   L.err = (int *)c->derr.p;
   L.nchunk_max = nchunk;
   L.tol = c->o.lanczos_tol;
+  NOMEM(c->ensure(c->dtarget, 8 * P));
+  L.target = c->dp(c->dtarget);
+  // FP64: one Lanczos run.  Mixed precision: restarts.  Each restart begins
+  // with an FP64 matvec on its start vector, so k = 0 checks the true residual
+  // against tol (and its alpha_0 is the FP64 Rayleigh quotient); the following
+  // matvecs run on the tensor cores until the residual estimate falls by the
+  // inner factor; the Ritz vector starts the next restart.
+  L.inner_factor = c->mixed ? 1e-5 : 0.0;
+  const int max_restarts = c->mixed ? 8 : 1;
+  const int inner_cap = c->mixed ? std::min(kmax, 80) : kmax;
   for (int q = 0; q < P; ++q) c->hbufs[q * NBUF + BUF_PSI] = psip[q];
   NOMEM(sync_bufs(c) == IDMRG_OK);
-  CK(lanczos_init(L, (const double *const *)c->lpsi.p, c->st));
-  c->launches += 3;
-  // ||psi~|| for the report
-  std::vector<double> nrm2(P, 0.0);
-  CK(c->d2h_copy(nrm2.data(), c->lresid.p, 8 * P));
-  std::vector<int> act(P);
-  for (int it = 0; it < kmax; ++it) {
-    CK(lanczos_set_ptrs(L, (double **)c->dbufs.p, c->st));
-    idmrg_status s = heff_launch(c, L.active, it == 0 ? member.data() : act.data());
-    if (s != IDMRG_OK) return s;
-    double vb = 0.0;
-    for (int q = 0; q < P; ++q)
-      if (it == 0 ? member[q] : act[q]) vb += 8.0 * (double)N[q] * (2.0 * (it + 2) + 2.0 * (it + 3) + 2.0);
-    c->kbegin(IDMRG_K_LANCZOS_VEC);
-    CK(lanczos_project(L, 0, c->st));
-    CK(lanczos_subtract(L, 0, c->st));
-    CK(lanczos_project(L, 1, c->st));
-    CK(lanczos_subtract(L, 1, c->st));
-    c->kend(IDMRG_K_LANCZOS_VEC, 0.0, vb);
-    c->kbegin(IDMRG_K_LANCZOS_TRI);
-    CK(lanczos_finalize(L, c->st));
-    c->kend(IDMRG_K_LANCZOS_TRI);
-    c->kbegin(IDMRG_K_LANCZOS_VEC);
-    CK(lanczos_next(L, c->st));
-    c->kend(IDMRG_K_LANCZOS_VEC);
-    c->launches += 7;
-    CK(c->d2h_copy(act.data(), c->lactive.p, 4 * P));
-    CK(cudaStreamSynchronize(c->st));
-    bool any = false;
-    for (int q = 0; q < P; ++q) any |= (act[q] != 0);
-    if (!any) break;
-  }
-  CK(lanczos_ritz(L, (double *const *)c->lpsi.p, c->st));
-  CK(lanczos_dot(L, (const double *const *)c->lv0.p, (const double *const *)c->lpsi.p, c->dp(c->ldot), c->st));
-  c->launches += 6;
-  std::vector<double> theta(P), dots(P);
-  std::vector<int> kk(P), conv(P);
-  CK(c->d2h_copy(theta.data(), c->ltheta.p, 8 * P));
-  CK(c->d2h_copy(dots.data(), c->ldot.p, 8 * P));
-  CK(c->d2h_copy(kk.data(), c->lk.p, 4 * P));
-  CK(c->d2h_copy(conv.data(), c->lconv.p, 4 * P));
-  idmrg_status s = check_dev_err(c);
-  if (s != IDMRG_OK) return s;
+  std::vector<double> nrm2(P, 0.0), theta(P, 0.0), dots(P, 0.0);
+  std::vector<int> act(P), kk(P), conv(P), total(P, 0), final_(P, 0);
   bool allconv = true;
+  for (int r = 0; r < max_restarts; ++r) {
+    bool anym = false;
+    for (int q = 0; q < P; ++q) anym |= member[q] != 0;
+    if (!anym) break;
+    NOMEM(c->upload(c->lmember, member));
+    CK(lanczos_init(L, (const double *const *)c->lpsi.p, c->st));
+    c->launches += 3;
+    if (r == 0) CK(c->d2h_copy(nrm2.data(), c->lresid.p, 8 * P));  // ||psi~|| for the report
+    for (int it = 0; it < inner_cap; ++it) {
+      CK(lanczos_set_ptrs(L, (double **)c->dbufs.p, c->st));
+      idmrg_status s = heff_launch(c, L.active, it == 0 ? member.data() : act.data(), it == 0);
+      if (s != IDMRG_OK) return s;
+      double vb = 0.0;
+      for (int q = 0; q < P; ++q)
+        if (it == 0 ? member[q] : act[q]) vb += 8.0 * (double)N[q] * (2.0 * (it + 2) + 2.0 * (it + 3) + 2.0);
+      c->kbegin(IDMRG_K_LANCZOS_VEC);
+      CK(lanczos_project(L, 0, c->st));
+      CK(lanczos_subtract(L, 0, c->st));
+      CK(lanczos_project(L, 1, c->st));
+      CK(lanczos_subtract(L, 1, c->st));
+      c->kend(IDMRG_K_LANCZOS_VEC, 0.0, vb);
+      c->kbegin(IDMRG_K_LANCZOS_TRI);
+      CK(lanczos_finalize(L, c->st));
+      c->kend(IDMRG_K_LANCZOS_TRI);
+      c->kbegin(IDMRG_K_LANCZOS_VEC);
+      CK(lanczos_next(L, c->st));
+      c->kend(IDMRG_K_LANCZOS_VEC);
+      c->launches += 7;
+      CK(c->d2h_copy(act.data(), c->lactive.p, 4 * P));
+      CK(cudaStreamSynchronize(c->st));
+      bool any = false;
+      for (int q = 0; q < P; ++q) any |= (act[q] != 0);
+      if (!any) break;
+    }
+    CK(lanczos_ritz(L, (double *const *)c->lpsi.p, c->st));
+    c->launches += 4;
+    if (r == 0) {
+      CK(lanczos_dot(L, (const double *const *)c->lv0.p, (const double *const *)c->lpsi.p, c->dp(c->ldot), c->st));
+      c->launches += 2;
+      CK(c->d2h_copy(dots.data(), c->ldot.p, 8 * P));
+    }
+    std::vector<double> th(P);
+    CK(c->d2h_copy(th.data(), c->ltheta.p, 8 * P));
+    CK(c->d2h_copy(kk.data(), c->lk.p, 4 * P));
+    CK(c->d2h_copy(conv.data(), c->lconv.p, 4 * P));
+    idmrg_status s = check_dev_err(c);
+    if (s != IDMRG_OK) return s;
+    for (int q = 0; q < P; ++q) {
+      if (!member[q]) continue;
+      total[q] += kk[q] + 1;
+      theta[q] = th[q];
+      // FP64 mode: done.  Mixed: done only when the FP64 check at k = 0 passed
+      const bool done = !c->mixed || (conv[q] && kk[q] == 0);
+      if (done) {
+        final_[q] = conv[q];
+        member[q] = 0;
+      }
+    }
+  }
   for (int q = 0; q < P; ++q) {
     if (!want(p, q)) continue;
     c->energy[q] = theta[q];
-    c->iters[q] = kk[q] + 1;
-    c->conv[q] = conv[q];
+    c->iters[q] = total[q];
+    c->conv[q] = final_[q];
     c->startnorm[q] = sqrt(nrm2[q]);
     c->fidelity[q] = (c->o.predict && c->n >= 3) ? 1.0 - fabs(dots[q]) : NAN;
     c->stage[q] = ST_SOLVED;
-    allconv &= conv[q] != 0;
+    allconv &= final_[q] != 0;
   }
   // centre-bond energies <psi|h|psi>
   std::vector<DotTerm> dt;
@@ -1196,7 +1498,8 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
     return bail(IDMRG_EINVAL);
   if (opts->m < 1 || opts->lanczos_maxit < 2 || opts->lanczos_maxit > 600 || !(opts->lanczos_tol > 0))
     return bail(IDMRG_EINVAL);
-  if (opts->prec != IDMRG_FP64) return bail(IDMRG_EINVAL);
+  if (opts->prec != IDMRG_FP64 && opts->prec != IDMRG_TF32X3) return bail(IDMRG_EINVAL);
+  c->mixed = opts->prec == IDMRG_TF32X3;
   c->ell = ell;
   c->d = d;
   c->P = ell / 2;
@@ -1261,6 +1564,7 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
   c->bPsi.resize(P);
   c->bUT.resize(P);
   c->bVT.resize(P);
+  for (auto *v : {&c->bPA1, &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP}) v->resize(P);
   c->hbufs.assign((size_t)P * NBUF, nullptr);
   if (!c->ensure(c->derr, 256)) return bail(IDMRG_ENOMEM);
   if (cudaMemsetAsync(c->derr.p, 0, sizeof(int), c->st) != cudaSuccess) return bail(IDMRG_ECUDA);
@@ -1308,7 +1612,8 @@ void idmrg_destroy(idmrg_ctx *c) {
   for (auto &e : c->newR) rel(e.data);
   for (auto *v : {&c->cur, &c->prev, &c->prev2})
     for (auto &t : *v) { rel(t.U); rel(t.V); }
-  for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT})
+  for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT, &c->bPA1,
+                  &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP})
     for (auto &b : *v) rel(b);
   for (DevBuf *b : {&c->dbufs, &c->dg1t, &c->dg1k, &c->dg1s, &c->dg3t, &c->dg3k, &c->dg3s, &c->dwt, &c->dwm, &c->ddt,
                     &c->ddp, &c->drb, &c->dgpt, &c->dgpk, &c->dgps, &c->dst, &c->dstab, &c->dge1t, &c->dge1k,
@@ -1316,7 +1621,8 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
-                    &c->scj, &c->slamk, &c->siw})
+                    &c->scj, &c->slamk, &c->siw, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
+                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -1423,7 +1729,7 @@ idmrg_status idmrg_heff_apply(idmrg_ctx *c, int p, const double *psi_dev, double
   }
   NOMEM(c->upload(c->dmask, mask));
   NOMEM(sync_bufs(c) == IDMRG_OK);
-  idmrg_status s = heff_launch(c, (const int *)c->dmask.p, mask.data());
+  idmrg_status s = heff_launch(c, (const int *)c->dmask.p, mask.data(), false);
   for (int q = 0; q < c->P; ++q) {
     c->hbufs[q * NBUF + BUF_IN] = save_in[q];
     c->hbufs[q * NBUF + BUF_OUT] = save_out[q];

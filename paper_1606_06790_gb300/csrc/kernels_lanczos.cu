@@ -271,7 +271,11 @@ __global__ void finalize_kernel(LanczosDev L) {
     const double res = beta_k * fabs(x[n - 1]);
     L.theta[s] = theta;
     L.resid[s] = res;
-    if (res <= L.tol * scale || beta_k <= 1e-14 * scale) {
+    // k = 0: the test against tol; with an inner factor (mixed-precision
+    // restarts) later iterations stop at the target fixed here
+    if (kk == 0) L.target[s] = fmax(L.tol * scale, L.inner_factor * beta_k);
+    const double goal = (kk == 0 || L.inner_factor == 0.0) ? L.tol * scale : L.target[s];
+    if (res <= goal || beta_k <= 1e-14 * scale) {
       L.active[s] = 0;
       L.conv[s] = 1;
     } else if (n >= km) {

@@ -1,0 +1,254 @@
+// Mixed-precision H_eff psi on the 5th-generation tensor cores (Step 3).
+//
+// Every FP64 operand x is split into two TF32 numbers, hi = x rounded to TF32
+// and lo = x - hi (also used at TF32 precision), and a product is formed from
+// three tcgen05.mma of kind::tf32 (hi.hi + hi.lo + lo.hi) accumulated in FP32
+// in tensor memory: about 21 significant bits per product.
+//
+//  pack      : splits FP64 or FP32 source blocks into packed hi/lo tiles in the
+//              tensor-core operand layout (K-major, no swizzle, core matrices
+//              of 8 rows x 16 bytes), so that a K block of a tile is one
+//              contiguous range that a single bulk (TMA) copy moves.
+//  wstage_tc : T3[c] = sum W12 T1[a] from the FP32 stage-1 output, written
+//              straight into the packed A operand of stage 3.
+//  tc_gemm   : grouped GEMM, one 128 x 64 output tile per CTA.  Thread 0
+//              streams the hi/lo tiles of A and B through a ring of shared
+//              memory stages with cp.async.bulk and issues the tcgen05.mma
+//              chain; the four warps then read the accumulator out of tensor
+//              memory (tcgen05.ld) and store it as FP32 (stage 1) or, through a
+//              row map, as FP64 into the output wavefunction (stage 3).
+//              Every mbarrier wait is bounded; a timeout sets the context's
+//              error word.
+#include <stdint.h>
+
+#include "common.h"
+#include "tc_ptx.h"
+
+namespace idmrg {
+
+namespace {
+
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ int64_t packed_off(int row, int k, int KB, int G) {
+  const int rows_per_tile = 8 * G;
+  const int rt = row / rows_per_tile, rr = row - rt * rows_per_tile;
+  const int kb = k >> 5, kc = (k & 31) >> 2;
+  const int64_t tile_floats = (int64_t)rows_per_tile * 32;
+  return ((int64_t)rt * KB + kb) * 2 * tile_floats + (((int64_t)kc * G + (rr >> 3)) * 8 + (rr & 7)) * 4 + (k & 3);
+}
+
+constexpr int PROWS = 16;
+
+__global__ void pack_kernel(const PackSeg *__restrict__ segs, double *const *__restrict__ bufs,
+                            const int *__restrict__ active) {
+  const PackSeg s = segs[blockIdx.x];
+  if (active && !active[s.sb]) return;
+  const int r0 = blockIdx.y * PROWS;
+  if (r0 >= s.rows) return;
+  const int r1 = min(s.rows, r0 + PROWS);
+  float *dst = (float *)bufs[s.sb * NBUF + s.dst_buf] + s.dst_off;
+  const int64_t tile_floats = (int64_t)8 * s.G * 32;
+  const int n = (r1 - r0) * s.ks;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = r0 + e / s.ks, k = e % s.ks;
+    const int64_t si = s.trans ? (int64_t)k * s.src_ld + r : (int64_t)r * s.src_ld + k;
+    float hi, lo;
+    if (s.src_fp32) {
+      const float x = ((const float *)bufs[s.sb * NBUF + s.src_buf])[s.src_off + si];
+      hi = tf32_round(x);
+      lo = x - hi;
+    } else {
+      const double x = bufs[s.sb * NBUF + s.src_buf][s.src_off + si];
+      hi = tf32_round((float)x);
+      lo = (float)(x - (double)hi);
+    }
+    const int64_t o = packed_off(s.row0 + r, s.k0 + k, s.KB, s.G);
+    dst[o] = hi;
+    dst[o + tile_floats] = lo;
+  }
+}
+
+__global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *__restrict__ terms,
+                                 double *const *__restrict__ bufs, const int *__restrict__ active) {
+  const WTaskP t = tasks[blockIdx.x];
+  if (active && !active[t.sb]) return;
+  const int r0 = blockIdx.y * PROWS;
+  if (r0 >= t.rows) return;
+  const int r1 = min(t.rows, r0 + PROWS);
+  const float *in = (const float *)bufs[t.sb * NBUF + BUF_T1F];
+  float *dst = (float *)bufs[t.sb * NBUF + BUF_PA3] + t.dst_off;
+  const int64_t tile_floats = (int64_t)8 * t.G * 32;
+  const int n = (r1 - r0) * t.cols;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = r0 + e / t.cols, c = e % t.cols;
+    float acc = 0.f;
+    for (int q = 0; q < t.nterm; ++q) {
+      const WTerm w = terms[t.term0 + q];
+      acc = fmaf((float)w.coef, in[w.in_off + (int64_t)r * w.in_ld + c], acc);
+    }
+    const float hi = tf32_round(acc);
+    const int64_t o = packed_off(t.row0 + r, t.k0 + c, t.KB, t.G);
+    dst[o] = hi;
+    dst[o + tile_floats] = acc - hi;
+  }
+}
+
+constexpr int TM = 128;
+constexpr int A_TILE = TM * 32;         // floats per A tile (one of hi/lo)
+constexpr int B_TILE = TC_TN * 32;      // floats per B tile
+constexpr int STAGE_FLOATS = 2 * A_TILE + 2 * B_TILE;
+constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (about 2 s)
+
+__global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__ tiles,
+                                                      const TcTask *__restrict__ tasks,
+                                                      double *const *__restrict__ bufs,
+                                                      const int *__restrict__ active, int *err) {
+  extern __shared__ __align__(1024) float sm[];
+  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const TcTile tile = tiles[blockIdx.x];
+  const TcTask T = tasks[tile.task];
+  if (active && !active[T.sb]) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, TC_TN);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&done, 1);
+    abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  if (threadIdx.x == 0) {
+    const float *A = (const float *)bufs[T.sb * NBUF + T.a_buf] + T.a_off + (int64_t)tile.mt * T.KB * 2 * A_TILE;
+    const float *B = (const float *)bufs[T.sb * NBUF + T.b_buf] + T.b_off + (int64_t)tile.nt * T.KB * 2 * B_TILE;
+    constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, 2);
+    constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TC_TN / 8) * 128, sbo = 128;
+    constexpr uint32_t stage_bytes = 4u * STAGE_FLOATS;
+    auto issue = [&](int kb) {
+      const int s = kb % TC_STAGES;
+      float *st = sm + s * STAGE_FLOATS;
+      tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+      tc::bulk_g2s(st, A + (int64_t)kb * 2 * A_TILE, 4u * 2 * A_TILE, &full[s]);
+      tc::bulk_g2s(st + 2 * A_TILE, B + (int64_t)kb * 2 * B_TILE, 4u * 2 * B_TILE, &full[s]);
+    };
+    bool ok = true;
+    for (int kb = 0; kb < T.KB && kb < TC_STAGES - 1; ++kb) issue(kb);
+    for (int kb = 0; kb < T.KB && ok; ++kb) {
+      const int kn = kb + TC_STAGES - 1;
+      if (kn < T.KB) {
+        const int sn = kn % TC_STAGES;
+        if (kn >= TC_STAGES && !tc::mbar_wait(&empty[sn], ((kn / TC_STAGES) - 1) & 1, WAIT_BUDGET)) {
+          ok = false;
+          break;
+        }
+        issue(kn);
+      }
+      const int s = kb % TC_STAGES;
+      if (!tc::mbar_wait(&full[s], (kb / TC_STAGES) & 1, WAIT_BUDGET)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(sm + s * STAGE_FLOATS);
+      const uint32_t sb = sa + 4u * 2 * A_TILE;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ahi = tc::smem_desc(sa + kk * 2 * lboA, lboA, sbo);
+        const uint64_t alo = tc::smem_desc(sa + 4u * A_TILE + kk * 2 * lboA, lboA, sbo);
+        const uint64_t bhi = tc::smem_desc(sb + kk * 2 * lboB, lboB, sbo);
+        const uint64_t blo = tc::smem_desc(sb + 4u * B_TILE + kk * 2 * lboB, lboB, sbo);
+        tc::mma_tf32(tmem, ahi, bhi, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        tc::mma_tf32(tmem, ahi, blo, idesc, 1u);
+        tc::mma_tf32(tmem, alo, bhi, idesc, 1u);
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    if (!ok) {
+      atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+      abort_flag = 1;
+    }
+    tc::mma_commit(&done);  // fires when every MMA issued above has completed
+  }
+  // epilogue: every thread waits for the accumulator
+  const bool ready = tc::mbar_wait(&done, 0, WAIT_BUDGET);
+  if (!ready && lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (ready && !abort_flag) {
+    const int row = tile.mt * TM + 32 * warp + lane;
+    const int col0 = tile.nt * TC_TN;
+    double *cbase = bufs[T.sb * NBUF + T.c_buf];
+    int64_t obase = 0;
+    if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
+#pragma unroll
+    for (int c = 0; c < TC_TN; c += 16) {
+      float v[16];
+      if (T.KB > 0) {
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if (row < T.M) {
+        if (T.mode == 0) {
+          float *out = (float *)cbase + T.c_off + (int64_t)row * T.ldc + col0 + c;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (col0 + c + i < T.N) out[i] = v[i];
+        } else {
+          double *out = cbase + obase + col0 + c;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (col0 + c + i < T.N) out[i] = (double)v[i];
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TC_TN);
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
+                        cudaStream_t st) {
+  if (nseg > 0 && max_rows > 0) {
+    dim3 grid(nseg, (max_rows + PROWS - 1) / PROWS);
+    pack_kernel<<<grid, 256, 0, st>>>(segs, bufs, active);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
+                             double *const *bufs, const int *active, cudaStream_t st) {
+  if (ntasks > 0 && max_rows > 0) {
+    dim3 grid(ntasks, (max_rows + PROWS - 1) / PROWS);
+    wstage_tc_kernel<<<grid, 256, 0, st>>>(tasks, terms, bufs, active);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
+                           const int *active, int *err, cudaStream_t st) {
+  const int smem = TC_STAGES * STAGE_FLOATS * (int)sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (ntiles > 0) tc_gemm_kernel<<<ntiles, 128, smem, st>>>(tiles, tasks, bufs, active, err);
+  return cudaGetLastError();
+}
+
+}  // namespace idmrg
