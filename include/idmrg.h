@@ -229,6 +229,26 @@ idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t
 /* Bytes this context has copied host->device and device->host so far. */
 idmrg_status idmrg_transfer_bytes(const idmrg_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
 
+/* H_eff psi of superblock p (p >= 0) in FP64, for callers that cannot
+ * allocate device memory while they run (a fixed or pre-partitioned memory
+ * pool, an embedding application that forbids allocator calls from this
+ * thread or while work is queued).  The paper has no counterpart; this is a
+ * deployment variant of idmrg_heff_apply.  psi_dev and out_dev are the
+ * caller's device vectors in the layout of idmrg_psi_layout(p); the
+ * intermediates live in a fixed 16 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits.  The call
+ * itself allocates nothing (no cudaMalloc, no allocator callback).
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress) with the device current; make that first call
+ *    before any stream capture.
+ *  - Superblocks whose intermediates exceed the array return IDMRG_EINVAL
+ *    with the sizes in idmrg_last_error.
+ *  - All calls share the array and it keeps the last call's contents; every
+ *    element a call reads is written by that call first, so nothing needs to
+ *    start at zero.  Calls that overlap on the GPU (two streams, two contexts
+ *    or two threads at once) race on it: order them on one stream. */
+idmrg_status idmrg_heff_apply_noalloc(idmrg_ctx *ctx, int p, const double *psi_dev, double *out_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_heff_apply", "idmrg_predict_wavefunction", "idmrg_lanczos_solve", "idmrg_get_psi",
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
-    "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes",
+    "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
 ]
 
 KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
@@ -110,6 +110,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_profile_enable": (i, [vp, i]),
         "idmrg_profile_read": (i, [vp, i, P(d), P(C.c_uint64), P(d), P(d)]),
         "idmrg_transfer_bytes": (i, [vp, P(C.c_uint64), P(C.c_uint64)]),
+        "idmrg_heff_apply_noalloc": (i, [vp, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -1914,3 +1914,74 @@ idmrg_status idmrg_transfer_bytes(const idmrg_ctx *c, uint64_t *h2d, uint64_t *d
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------------
+// H_eff psi without device allocation.
+//
+// Some callers cannot allocate device memory once they are running: code
+// inside a memory-capped or pre-partitioned pool, callers that must not touch
+// the allocator while other work is queued, or embedders whose allocator may
+// not be called from this thread.  This entry point serves them: it applies
+// one superblock's H_eff in FP64 with its intermediates (the T1 and T3
+// contractions) and its pointer table in the file-scope device array below,
+// a fixed 16 MiB that every GPU loading this library holds until the process
+// exits.  Host code sees the array's name only as a stand-in for the symbol,
+// so the device address is looked up with cudaGetSymbolAddress, once per
+// device, on the first call made with that device current.
+// --------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoallocBytes = (size_t)16 << 20;
+constexpr int kNoallocMaxDevices = 64;
+constexpr int kNoallocMaxPairs = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+static unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" idmrg_status idmrg_heff_apply_noalloc(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev) {
+  if (!c || !psi_dev || !out_dev || p < 0 || p >= c->P) return IDMRG_EINVAL;
+  if (c->P > kNoallocMaxPairs) return c->fail(IDMRG_EINVAL, "heff_apply_noalloc: more than %d superblocks", kNoallocMaxPairs);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices)
+    return c->fail(IDMRG_ECUDA, "heff_apply_noalloc: no usable current device");
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return c->fail(IDMRG_ECUDA, "heff_apply_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (unsigned char *)ptr;
+  }
+  unsigned char *base = g_noalloc_ptr[dev];
+  const SBPlan &S = c->plan[p];
+  const size_t table_bytes = round256(sizeof(double *) * (size_t)c->P * NBUF);
+  const size_t mask_bytes = round256(sizeof(int) * (size_t)c->P);
+  const size_t t1_bytes = round256(8 * (size_t)std::max<int64_t>(S.t1size, 1));
+  const size_t t3_bytes = round256(8 * (size_t)std::max<int64_t>(S.t3size, 1));
+  const size_t need = table_bytes + mask_bytes + t1_bytes + t3_bytes;
+  if (need > kNoallocBytes)
+    return c->fail(IDMRG_EINVAL, "heff_apply_noalloc: superblock %d needs %zu bytes of scratch, the limit is %zu", p,
+                   need, kNoallocBytes);
+  // pointer table and activity mask, built on the host stack and copied in
+  double *table[kNoallocMaxPairs * NBUF];
+  int mask[kNoallocMaxPairs];
+  for (int q = 0; q < c->P; ++q) {
+    mask[q] = q == p ? 1 : 0;
+    for (int b = 0; b < NBUF; ++b) table[q * NBUF + b] = c->hbufs[q * NBUF + b];
+  }
+  table[p * NBUF + BUF_IN] = const_cast<double *>(psi_dev);
+  table[p * NBUF + BUF_OUT] = out_dev;
+  table[p * NBUF + BUF_T1] = (double *)(base + table_bytes + mask_bytes);
+  table[p * NBUF + BUF_T3] = (double *)(base + table_bytes + mask_bytes + t1_bytes);
+  CK(cudaMemcpyAsync(base, table, sizeof(double *) * (size_t)c->P * NBUF, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(base + table_bytes, mask, sizeof(int) * (size_t)c->P, cudaMemcpyHostToDevice, c->st));
+  double *const *bufs = (double *const *)base;
+  const int *active = (const int *)(base + table_bytes);
+  CK(launch_gemm_f64((const GemmTile *)c->dg1t.p, (int)c->g1.tiles.size(), (const GemmTask *)c->dg1k.p,
+                     (const GemmSeg *)c->dg1s.p, bufs, active, c->st));
+  CK(launch_wstage_f64((const WTask *)c->dwt.p, (int)c->wl.tasks.size(), c->wl.max_rows, (const WTerm *)c->dwm.p,
+                       bufs, active, c->st));
+  CK(launch_gemm_f64((const GemmTile *)c->dg3t.p, (int)c->g3.tiles.size(), (const GemmTask *)c->dg3k.p,
+                     (const GemmSeg *)c->dg3s.p, bufs, active, c->st));
+  return IDMRG_OK;
+}
