@@ -115,7 +115,9 @@ typedef struct {
 typedef struct idmrg_ctx idmrg_ctx;
 
 /* Defaults: m = 64, target 0, tol 1e-12, maxit 300, FP64, prediction on,
- * seed 0, lambda_zero_rel 1e-12, tie_rel 1e-10. */
+ * seed 0, lambda_zero_rel 1e-12, tie_rel 1e-7 (states degenerate by symmetry
+ * come out of a solver stopped at residual tol|E| split by ~tol|E|/gap; a
+ * tie_rel below that would let rounding decide the cut). */
 void idmrg_default_opts(idmrg_opts *opts);
 
 /* Step 1: validates the MPO, builds L^(0) (last row of W at site 2p) and

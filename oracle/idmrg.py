@@ -25,7 +25,11 @@ R1 singular values are kept in descending order (the printed ascending
    inequality of Step 4 contradicts "keep beta = 1..m" of Eqs. fid2, tru);
 R2 the cut never splits a group of equal singular values: keep the largest
    D <= m with lam_{D+1} < lam_D (1 - tie_rel); singular values at or below
-   zero_rel * lam_max are treated as zero and dropped (Step 4, Step 6);
+   zero_rel * lam_max are treated as zero and dropped (Step 4, Step 6).
+   tie_rel = 1e-7: states degenerate by symmetry (SU(2) multiplets spread over
+   the 2Sz sectors) come out of any eigensolver stopped at a residual tol |E|
+   split by up to about tol |E| / gap, i.e. ~1e-9 relative near the cut for
+   tol = 1e-12; a smaller tie_rel would let solver rounding decide the cut;
 R3 in the prediction, lam^(n-2) <= zero_rel * max(lam^(n-2)) counts as zero;
 R4 in Eq. wfprediction lam^(n-2) and u^(n-1) belong to superblock i+1 and
    v^(n-1), lam^(n-1) (left factor) to superblock i; i+1 wraps to 1;
@@ -164,7 +168,7 @@ class Truncation:
     eps_best: float      # Eq. fid2 (best fidelity error)
 
 
-def truncate(psi, qL, qp, qR, m: int, tie_rel: float = 1e-10, zero_rel: float = 1e-12,
+def truncate(psi, qL, qp, qR, m: int, tie_rel: float = 1e-7, zero_rel: float = 1e-12,
              target: int = 0) -> Truncation:
     """Step 4 and the truncation of Step 6.  psi is split as (x s) x (t y); for
     every charge Q of the left half the block with rows of charge Q and columns
@@ -279,7 +283,7 @@ class ParallelIDMRG:
 
     def __init__(self, W, phys_charge, bond_charge, m: int, lanczos_tol: float = 1e-12,
                  lanczos_maxit: int = 300, predict: bool = True, seed: int = 0,
-                 zero_rel: float = 1e-12, tie_rel: float = 1e-10, target: int = 0):
+                 zero_rel: float = 1e-12, tie_rel: float = 1e-7, target: int = 0):
         self.W = [np.asarray(w, dtype=np.float64) for w in W]
         self.qp = np.asarray(phys_charge, dtype=np.int64)
         check_mpo(self.W, self.qp, [np.asarray(c) for c in bond_charge])

@@ -135,7 +135,7 @@ class Context:
     def __init__(self, W: Sequence[np.ndarray], phys_charge, bond_charge: Sequence[np.ndarray], m: int,
                  prec: str = "fp64", lanczos_tol: float = 1e-12, lanczos_maxit: int = 300,
                  predict: bool = True, seed: int = 0, lambda_zero_rel: float = 1e-12,
-                 tie_rel: float = 1e-10, target_charge: int = 0, stream=None):
+                 tie_rel: float = 1e-7, target_charge: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")

@@ -106,7 +106,8 @@ struct SvdJob {
   int64_t b_off;    // B = R^T (cols_a x cols_a), Jacobi working matrix
   int64_t x_off;    // rows_a x cols_a scratch for the back-transformation
   int64_t tau_off;  // cols_a Householder coefficients
-  int perm_off;     // cols_a column permutation of the pivoted QR (int work)
+  int perm_off;     // cols_a column permutation of the pivoted QR (int work),
+                    // followed by the numerical rank found by the QR
   int sv_off;       // singular values of this job
 };
 
@@ -184,8 +185,9 @@ cudaError_t lanczos_dot(const LanczosDev &L, const double *const *a, const doubl
 // SVD (FP64 one-sided Jacobi), see kernels_svd.cu
 cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_elems, double *const *bufs,
                                     int psi_buf, double *work, cudaStream_t st);
-cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, cudaStream_t st);
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, double *sv, int *err, cudaStream_t st);
+cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, double zero_rel, cudaStream_t st);
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, const int *iwork, double *sv, int *err,
+                              cudaStream_t st);
 struct SelectOut {
   int *kept_per_job;   // [njobs]
   int *perm;           // [sum cols_a] kept slot -> index within job (per job, at sv_off)

@@ -1129,7 +1129,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
       J.tau_off = work;
       work += J.cols_a;
       J.perm_off = iw;
-      iw += J.cols_a;
+      iw += J.cols_a + 1;
       J.sv_off = sv;
       sv += J.cols_a;
       entries += J.cols_a;
@@ -1151,8 +1151,9 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   double *const *bufs = (double *const *)c->dbufs.p;
   c->kbegin(IDMRG_K_SVD);
   CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, max_elems, bufs, BUF_PSI, c->dp(c->swork), c->st));
-  CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), (int *)c->siw.p, c->st));
-  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), c->dp(c->ssv), (int *)c->derr.p, c->st));
+  CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, c->st));
+  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), (const int *)c->siw.p, c->dp(c->ssv),
+                       (int *)c->derr.p, c->st));
   // select runs on superblocks with jobs only: compact the index arrays
   std::vector<int> sbl;
   for (int q = 0; q < P; ++q)
@@ -1473,7 +1474,7 @@ void idmrg_default_opts(idmrg_opts *o) {
   o->predict = 1;
   o->seed = 0;
   o->lambda_zero_rel = 1e-12;
-  o->tie_rel = 1e-10;
+  o->tie_rel = 1e-7;
 }
 
 idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cuda_stream,

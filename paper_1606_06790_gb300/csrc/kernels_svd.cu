@@ -66,7 +66,7 @@ __device__ __forceinline__ double wsum(double v) {
 constexpr int QR_THREADS = 512;
 
 __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work,
-                                                          int *__restrict__ iwork) {
+                                                          int *__restrict__ iwork, double zero_rel) {
   extern __shared__ double qsm[];  // vn[ca], vref[ca]
   const SvdJob Jb = jobs[blockIdx.x];
   const int ra = Jb.rows_a, ca = Jb.cols_a;
@@ -87,7 +87,15 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restri
     if (lane == 0) { vn[j] = s; vref[j] = s; perm[j] = j; }
   }
   __syncthreads();
-  for (int k = 0; k < ca; ++k) {
+  // The QR stops at the numerical rank: once the largest remaining column
+  // norm is below 0.1 zero_rel |R_00| / sqrt(cols), every singular value left
+  // in the trailing block is below 0.1 zero_rel sigma_max, i.e. one the cut
+  // treats as zero anyway, and the kept ones move by less than that.
+  __shared__ double s_stop2;
+  __shared__ int s_rank;
+  if (threadIdx.x == 0) { s_rank = ca; s_stop2 = -1.0; }
+  int k = 0;
+  for (; k < ca; ++k) {
     // pivot: largest remaining column norm (first index on ties)
     double bv = -1.0;
     int bi = k;
@@ -109,6 +117,12 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restri
     }
     __syncthreads();
     const int p = s_piv;
+    if (threadIdx.x == 0) {
+      if (k == 0) s_stop2 = vn[p] * (0.01 * zero_rel * zero_rel / (double)ca);
+      if (!(vn[p] > s_stop2)) s_rank = k;
+    }
+    __syncthreads();
+    if (s_rank == k) break;
     if (p != k) {
       for (int i = threadIdx.x; i < ra; i += blockDim.x) {
         const double t = A[(int64_t)k * ra + i];
@@ -180,8 +194,10 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restri
     }
     __syncthreads();
   }
-  // B = R^T (ca x ca, column-major): B(a, b) = R(b, a) for b <= a
-  for (int64_t e = threadIdx.x; e < (int64_t)ca * ca; e += blockDim.x) {
+  const int rk = s_rank;
+  if (threadIdx.x == 0) perm[ca] = rk;
+  // B = [R11 R12]^T (ca x rk, column-major): B(a, b) = R(b, a) for b <= a, b < rk
+  for (int64_t e = threadIdx.x; e < (int64_t)ca * rk; e += blockDim.x) {
     const int a = (int)(e % ca), b = (int)(e / ca);
     B[e] = (b <= a) ? A[(int64_t)a * ra + b] : 0.0;
   }
@@ -193,8 +209,8 @@ constexpr int JAC_CLUSTER = 8;
 constexpr int JAC_REG = 8;  // column elements per lane held in registers
 
 // one column pair (p, q): overlap, rotation of B's and Jm's columns
-__device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, double *jq, int n, int lane,
-                                            double tol, double abs_floor) {
+__device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, double *jq, int n, int nj,
+                                            int lane, double tol, double abs_floor) {
   double x[JAC_REG], y[JAC_REG];
   double al = 0.0, be = 0.0, ga = 0.0;
   const bool inreg = n <= 32 * JAC_REG;
@@ -245,7 +261,7 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
       aq[i] = sn * u + cs * v;
     }
   }
-  for (int i = lane; i < n; i += 32) {
+  for (int i = lane; i < nj; i += 32) {
     const double u = jp[i], v = jq[i];
     jp[i] = cs * u - sn * v;
     jq[i] = sn * u + cs * v;
@@ -254,11 +270,13 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
 }
 
 __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREADS)
-    jacobi_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work, double *__restrict__ sv, int *err) {
+    jacobi_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work, const int *__restrict__ iwork,
+                  double *__restrict__ sv, int *err) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const SvdJob Jb = jobs[blockIdx.x / JAC_CLUSTER];
-  const int n = Jb.cols_a;
+  const int nr = Jb.cols_a;                       // rows of B
+  const int n = iwork[Jb.perm_off + Jb.cols_a];   // columns of B: numerical rank
   double *B = work + Jb.b_off;
   double *Jm = work + Jb.j_off;
   __shared__ double fro_part[JAC_CLUSTER];
@@ -266,12 +284,12 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREAD
   __shared__ int flag, local_changed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int gw = crank * nw + warp, gnw = JAC_CLUSTER * nw;
-  const int64_t nn = (int64_t)n * n;
+  const int64_t nn = (int64_t)n * n, nb = (int64_t)nr * n;
   for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)JAC_CLUSTER * blockDim.x)
     Jm[e] = (e / n == e % n) ? 1.0 : 0.0;
   // ||B||_F^2 over the cluster (partials gathered in rank 0's shared memory)
   double fro = 0.0;
-  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)JAC_CLUSTER * blockDim.x)
+  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nb; e += (int64_t)JAC_CLUSTER * blockDim.x)
     fro = fma(B[e], B[e], fro);
   fro = wsum(fro);
   if (lane == 0) wred[warp] = fro;
@@ -291,7 +309,7 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREAD
   // an absolute floor eps^2 ||B||_F^2: without it a column made of rounding
   // noise along another one never meets the relative test (each rotation
   // leaves an eps-sized overlap that dominates tol |b_p| |b_q| as |b_q| -> 0).
-  const double tol = sqrt((double)n) * DBL_EPSILON;
+  const double tol = sqrt((double)nr) * DBL_EPSILON;
   const double abs_floor = 4.0 * DBL_EPSILON * DBL_EPSILON * fro;
   const int np = n + (n & 1);
   int *flag0 = cluster.map_shared_rank(&flag, 0);
@@ -307,8 +325,8 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREAD
         const int p = i1 == 0 ? 0 : 1 + (i1 - 1 + rnd) % (np - 1);
         const int q = i2 == 0 ? 0 : 1 + (i2 - 1 + rnd) % (np - 1);
         if (p >= n || q >= n) continue;
-        any |= jacobi_pair(B + (int64_t)p * n, B + (int64_t)q * n, Jm + (int64_t)p * n, Jm + (int64_t)q * n, n,
-                           lane, tol, abs_floor);
+        any |= jacobi_pair(B + (int64_t)p * nr, B + (int64_t)q * nr, Jm + (int64_t)p * n, Jm + (int64_t)q * n, nr,
+                           n, lane, tol, abs_floor);
       }
       cluster.sync();
     }
@@ -320,15 +338,20 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREAD
     cluster.sync();
   }
   if (!converged && crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
-  // singular values; columns of B normalised in place
-  for (int j = gw; j < n; j += gnw) {
-    double *bj = B + (int64_t)j * n;
+  // singular values; columns of B normalised in place; the columns beyond
+  // the numerical rank have singular value zero
+  for (int j = gw; j < Jb.cols_a; j += gnw) {
+    if (j >= n) {
+      if (lane == 0) sv[Jb.sv_off + j] = 0.0;
+      continue;
+    }
+    double *bj = B + (int64_t)j * nr;
     double s = 0.0;
-    for (int i = lane; i < n; i += 32) s = fma(bj[i], bj[i], s);
+    for (int i = lane; i < nr; i += 32) s = fma(bj[i], bj[i], s);
     s = sqrt(wsum(s));
     if (lane == 0) sv[Jb.sv_off + j] = s;
     const double inv = s > 0.0 ? 1.0 / s : 0.0;
-    for (int i = lane; i < n; i += 32) bj[i] *= inv;
+    for (int i = lane; i < nr; i += 32) bj[i] *= inv;
   }
 }
 
@@ -427,6 +450,7 @@ __global__ void compact_kernel(const SvdJob *__restrict__ jobs, const CompactJob
   const double *Jm = work + J.j_off;
   const double *Bn = work + J.b_off;
   const int *qperm = iwork + J.perm_off;
+  const int rk = qperm[ca];
   double *U = bufs[J.sb * NBUF + BUF_U] + cj.u_off;
   double *V = bufs[J.sb * NBUF + BUF_V] + cj.v_off;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -434,9 +458,9 @@ __global__ void compact_kernel(const SvdJob *__restrict__ jobs, const CompactJob
   for (int slot = gw; slot < k; slot += gnw) {
     const int col = perm[J.sv_off + slot];
     double *x = work + J.x_off + (int64_t)slot * ra;
-    for (int i = lane; i < ra; i += 32) x[i] = i < ca ? Jm[(int64_t)col * ca + i] : 0.0;
+    for (int i = lane; i < ra; i += 32) x[i] = i < rk ? Jm[(int64_t)col * rk + i] : 0.0;
     __syncwarp();
-    for (int kk = ca - 1; kk >= 0; --kk) {
+    for (int kk = rk - 1; kk >= 0; --kk) {
       const double t = tau[kk];
       if (t == 0.0) continue;
       const double *v = A + (int64_t)kk * ra;
@@ -468,17 +492,18 @@ cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_e
   return cudaGetLastError();
 }
 
-cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, cudaStream_t st) {
+cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, double zero_rel, cudaStream_t st) {
   // shared: two norms per column; callers keep cols_a <= 4096
   const int smem = 2 * 4096 * (int)sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (njobs > 0) qrcp_kernel<<<njobs, QR_THREADS, smem, st>>>(jobs, work, iwork);
+  if (njobs > 0) qrcp_kernel<<<njobs, QR_THREADS, smem, st>>>(jobs, work, iwork, zero_rel);
   return cudaGetLastError();
 }
 
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, double *sv, int *err, cudaStream_t st) {
-  if (njobs > 0) jacobi_kernel<<<njobs * JAC_CLUSTER, JAC_THREADS, 0, st>>>(jobs, work, sv, err);
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, const int *iwork, double *sv, int *err,
+                              cudaStream_t st) {
+  if (njobs > 0) jacobi_kernel<<<njobs * JAC_CLUSTER, JAC_THREADS, 0, st>>>(jobs, work, iwork, sv, err);
   return cudaGetLastError();
 }
 
