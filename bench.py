@@ -297,6 +297,7 @@ def main():
                 "h2d_bytes_per_step": (h2d1 - h2d0) // args.steps, "d2h_bytes_per_step": (d2h1 - d2h0) // args.steps,
                 "note": "wall clock around idmrg_unit_cell_step with its host-side block tables and report"},
         "kernels": kernels,
+        "svd": ctx.svd_stats(),
         "heff": {"flops_per_matvec_all_superblocks": flops,
                  "lanczos_iters_last_step": [int(x) for x in last["iters"]]},
         "clocks": clk,

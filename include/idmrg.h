@@ -228,6 +228,12 @@ idmrg_status idmrg_profile_enable(idmrg_ctx *ctx, int on);
 idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t *launches, double *flops,
                                 double *bytes);
 
+/* Shape of the last truncation's SVD work (Step 4): sector matrices, their
+ * largest short side, largest numerical rank, and the Jacobi sweeps taken
+ * (maximum and mean over the sectors). */
+idmrg_status idmrg_svd_stats(const idmrg_ctx *ctx, int *jobs, int *max_cols, int *max_rank, int *max_sweeps,
+                             double *mean_sweeps);
+
 /* Bytes this context has copied host->device and device->host so far. */
 idmrg_status idmrg_transfer_bytes(const idmrg_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
 

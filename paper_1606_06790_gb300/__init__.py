@@ -31,6 +31,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
+    "idmrg_svd_stats",
 ]
 
 KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
@@ -111,6 +112,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_profile_read": (i, [vp, i, P(d), P(C.c_uint64), P(d), P(d)]),
         "idmrg_transfer_bytes": (i, [vp, P(C.c_uint64), P(C.c_uint64)]),
         "idmrg_heff_apply_noalloc": (i, [vp, i, vp, vp]),
+        "idmrg_svd_stats": (i, [vp, P(i), P(i), P(i), P(i), P(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -318,6 +320,12 @@ class Context:
                         "profile_read")
             out[name] = dict(ms=ms.value, launches=int(n.value), flops=f.value, bytes=b.value)
         return out
+
+    def svd_stats(self) -> Dict[str, float]:
+        j, mc, mr, ms, me = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        self._check(self.lib.idmrg_svd_stats(self.h, C.byref(j), C.byref(mc), C.byref(mr), C.byref(ms), C.byref(me)),
+                    "svd_stats")
+        return dict(jobs=j.value, max_cols=mc.value, max_rank=mr.value, max_sweeps=ms.value, mean_sweeps=me.value)
 
     def transfer_bytes(self):
         a, b = C.c_uint64(), C.c_uint64()

@@ -107,7 +107,8 @@ struct SvdJob {
   int64_t x_off;    // rows_a x cols_a scratch for the back-transformation
   int64_t tau_off;  // cols_a Householder coefficients
   int perm_off;     // cols_a column permutation of the pivoted QR (int work),
-                    // followed by the numerical rank found by the QR
+                    // then the numerical rank found by the QR and the sweeps
+                    // the Jacobi stage needed
   int sv_off;       // singular values of this job
 };
 
@@ -157,6 +158,7 @@ struct LanczosDev {
   double *const *V;      // [S] Krylov basis, kmax x N row-major
   double *const *w;      // [S] work vector
   double *alpha, *beta;  // [S * kmax]
+  double *ibeta;         // [S * kmax] 1 / beta
   double *h;             // [S * kmax] projection coefficients
   double *part;          // partial sums
   int *k;                // [S] current Krylov index
@@ -185,9 +187,10 @@ cudaError_t lanczos_dot(const LanczosDev &L, const double *const *a, const doubl
 // SVD (FP64 one-sided Jacobi), see kernels_svd.cu
 cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_elems, double *const *bufs,
                                     int psi_buf, double *work, cudaStream_t st);
-cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, double zero_rel, cudaStream_t st);
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, const int *iwork, double *sv, int *err,
-                              cudaStream_t st);
+cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, double *work, int *iwork, double zero_rel,
+                            cudaStream_t st);
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, int nbig, double *work, int *iwork,
+                              double *sv, int *err, cudaStream_t st);
 struct SelectOut {
   int *kept_per_job;   // [njobs]
   int *perm;           // [sum cols_a] kept slot -> index within job (per job, at sv_off)

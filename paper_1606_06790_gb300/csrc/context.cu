@@ -129,10 +129,12 @@ struct idmrg_ctx {
   DevBuf dge1t, dge1k, dge1s, dge3t, dge3k, dge3s, dwet, dwem, dmask, derr;
   std::vector<DevBuf> bT1, bT3, bX, bY, bV, bW, bPsi, bUT, bVT;
   // lanczos
-  DevBuf lN, lV, lw, lalpha, lbeta, lh, lpart, lk, lmember, lactive, lconv, ltheta, ly, lresid, lpsi, lv0, ldot;
+  DevBuf lN, lV, lw, lalpha, lbeta, libeta, lh, lpart, lk, lmember, lactive, lconv, ltheta, ly, lresid, lpsi, lv0, ldot;
   int kmax = 0, nchunk = 0;
   // svd
-  DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk, siw;
+  DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk, siw, sorder;
+  int svd_jobs = 0, svd_max_cols = 0, svd_max_rank = 0, svd_max_sweeps = 0;
+  double svd_mean_sweeps = 0.0;
 
   std::vector<int> hmask;
   uint64_t mixed_matvecs = 0, fp64_matvecs = 0;
@@ -920,6 +922,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   NOMEM(c->upload(c->lN, N) && c->upload(c->lV, Vp) && c->upload(c->lw, wp) && c->upload(c->lpsi, psip) &&
         c->upload(c->lv0, v0p));
   NOMEM(c->ensure(c->lalpha, 8 * (size_t)P * kmax) && c->ensure(c->lbeta, 8 * (size_t)P * kmax) &&
+        c->ensure(c->libeta, 8 * (size_t)P * kmax) &&
         c->ensure(c->lh, 8 * 2 * (size_t)P * kmax) && c->ensure(c->ly, 8 * (size_t)P * kmax) &&
         c->ensure(c->lpart, 8 * 3 * (size_t)P * kmax * nchunk) && c->ensure(c->ltheta, 8 * P) &&
         c->ensure(c->lresid, 8 * P) && c->ensure(c->ldot, 8 * P) && c->ensure(c->lk, 4 * P) &&
@@ -935,6 +938,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   L.w = (double *const *)c->lw.p;
   L.alpha = c->dp(c->lalpha);
   L.beta = c->dp(c->lbeta);
+  L.ibeta = c->dp(c->libeta);
   L.h = c->dp(c->lh);
   L.part = c->dp(c->lpart);
   L.k = (int *)c->lk.p;
@@ -1129,7 +1133,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
       J.tau_off = work;
       work += J.cols_a;
       J.perm_off = iw;
-      iw += J.cols_a + 1;
+      iw += J.cols_a + 2;
       J.sv_off = sv;
       sv += J.cols_a;
       entries += J.cols_a;
@@ -1151,9 +1155,18 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   double *const *bufs = (double *const *)c->dbufs.p;
   c->kbegin(IDMRG_K_SVD);
   CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, max_elems, bufs, BUF_PSI, c->dp(c->swork), c->st));
-  CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, c->st));
-  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, nj, c->dp(c->swork), (const int *)c->siw.p, c->dp(c->ssv),
-                       (int *)c->derr.p, c->st));
+  // largest sector matrices first: they set the length of the SVD phase
+  std::vector<int> order(nj);
+  for (int j = 0; j < nj; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return c->jobs[a].cols_a * (int64_t)c->jobs[a].rows_a > c->jobs[b].cols_a * (int64_t)c->jobs[b].rows_a; });
+  NOMEM(c->upload(c->sorder, order));
+  CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, c->dp(c->swork), (int *)c->siw.p,
+                     c->o.lambda_zero_rel, c->st));
+  int nbig = 0;
+  for (int j = 0; j < nj; ++j) nbig += c->jobs[order[j]].cols_a >= 64 ? 1 : 0;
+  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, nbig, c->dp(c->swork),
+                       (int *)c->siw.p, c->dp(c->ssv), (int *)c->derr.p, c->st));
   // select runs on superblocks with jobs only: compact the index arrays
   std::vector<int> sbl;
   for (int q = 0; q < P; ++q)
@@ -1172,14 +1185,25 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
                        c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, so, max_entries, c->st));
   c->kend(IDMRG_K_SVD);
   c->launches += 3;
-  std::vector<int> kpj(nj);
+  std::vector<int> kpj(nj), iwh(iw);
   std::vector<double> lam_sorted(sv), eps(sbl.size()), epsb(sbl.size());
+  CK(c->d2h_copy(iwh.data(), c->siw.p, 4 * (size_t)iw));
   CK(c->d2h_copy(kpj.data(), c->skpj.p, 4 * nj));
   CK(c->d2h_copy(lam_sorted.data(), c->slam.p, 8 * sv));
   CK(c->d2h_copy(eps.data(), c->seps.p, 8 * sbl.size()));
   CK(c->d2h_copy(epsb.data(), c->sepsb.p, 8 * sbl.size()));
   idmrg_status s = check_dev_err(c);
   if (s != IDMRG_OK) return s;
+  c->svd_jobs = nj;
+  c->svd_max_cols = c->svd_max_rank = c->svd_max_sweeps = 0;
+  c->svd_mean_sweeps = 0.0;
+  for (const SvdJob &J : c->jobs) {
+    const int rk = iwh[J.perm_off + J.cols_a], sw = iwh[J.perm_off + J.cols_a + 1];
+    c->svd_max_cols = std::max(c->svd_max_cols, J.cols_a);
+    c->svd_max_rank = std::max(c->svd_max_rank, rk);
+    c->svd_max_sweeps = std::max(c->svd_max_sweeps, sw);
+    c->svd_mean_sweeps += (double)sw / std::max(nj, 1);
+  }
   // new bases and compaction jobs
   std::vector<CompactJob> cj;
   for (size_t z = 0; z < sbl.size(); ++z) {
@@ -1619,10 +1643,10 @@ void idmrg_destroy(idmrg_ctx *c) {
   for (DevBuf *b : {&c->dbufs, &c->dg1t, &c->dg1k, &c->dg1s, &c->dg3t, &c->dg3k, &c->dg3s, &c->dwt, &c->dwm, &c->ddt,
                     &c->ddp, &c->drb, &c->dgpt, &c->dgpk, &c->dgps, &c->dst, &c->dstab, &c->dge1t, &c->dge1k,
                     &c->dge1s, &c->dge3t, &c->dge3k, &c->dge3s, &c->dwet, &c->dwem, &c->dmask, &c->derr, &c->lN,
-                    &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
+                    &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->libeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
-                    &c->scj, &c->slamk, &c->siw, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
+                    &c->scj, &c->slamk, &c->siw, &c->sorder, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
                     &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
@@ -1904,6 +1928,17 @@ idmrg_status idmrg_profile_read(idmrg_ctx *c, int k, double *ms, uint64_t *launc
   if (launches) *launches = c->kt[k].n;
   if (flops) *flops = c->kt[k].flops;
   if (bytes) *bytes = c->kt[k].bytes;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_svd_stats(const idmrg_ctx *c, int *jobs, int *max_cols, int *max_rank, int *max_sweeps,
+                             double *mean_sweeps) {
+  if (!c) return IDMRG_EINVAL;
+  if (jobs) *jobs = c->svd_jobs;
+  if (max_cols) *max_cols = c->svd_max_cols;
+  if (max_rank) *max_rank = c->svd_max_rank;
+  if (max_sweeps) *max_sweeps = c->svd_max_sweeps;
+  if (mean_sweeps) *mean_sweeps = c->svd_mean_sweeps;
   return IDMRG_OK;
 }
 

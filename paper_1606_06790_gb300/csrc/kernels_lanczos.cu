@@ -4,8 +4,9 @@
 // of the same projection).  Reductions are two-level and deterministic: each
 // CTA writes one partial per (superblock, coefficient); consumers add the
 // partials in a fixed order.  The tridiagonal problem is solved on the device:
-// warp multisection with Sturm counts for the lowest eigenvalue, then inverse
-// iteration with a pivoted tridiagonal LU for its eigenvector.
+// warp multisection with FP32 Sturm counts brackets the lowest eigenvalue, the
+// eigenvector follows from the backward three-term recurrence and the FP64
+// Rayleigh quotient refines the eigenvalue.
 #include <float.h>
 #include <math.h>
 
@@ -128,60 +129,12 @@ __device__ int sturm_count_f(const float *a, const float *b2, int n, float x, fl
   return cnt;
 }
 
-// Solves (T - theta) x = b in place (b -> x) with a partially pivoted LU
-// (the elimination of LAPACK's tridiagonal routines); tiny pivots are raised
-// to `tiny` so the nearly singular shift amplifies the eigenvector.
-__device__ void shifted_solve(const double *a, const double *b, int n, double theta, double tiny, double *dl,
-                              double *d, double *du, double *du2, int *piv, double *x) {
-  for (int i = 0; i < n; ++i) {
-    d[i] = a[i] - theta;
-    if (i < n - 1) { dl[i] = b[i]; du[i] = b[i]; }
-    du2[i] = 0.0;
-    piv[i] = 0;
-  }
-  for (int i = 0; i < n - 1; ++i) {
-    if (fabs(d[i]) >= fabs(dl[i])) {
-      if (fabs(d[i]) < tiny) d[i] = copysign(tiny, d[i] == 0.0 ? 1.0 : d[i]);
-      const double f = dl[i] / d[i];
-      dl[i] = f;
-      d[i + 1] -= f * du[i];
-    } else {
-      const double f = d[i] / dl[i];
-      d[i] = dl[i];
-      dl[i] = f;
-      const double t = du[i];
-      du[i] = d[i + 1];
-      d[i + 1] = t - f * d[i + 1];
-      if (i < n - 2) {
-        du2[i] = du[i + 1];
-        du[i + 1] = -f * du[i + 1];
-      }
-      piv[i] = 1;
-    }
-  }
-  if (fabs(d[n - 1]) < tiny) d[n - 1] = copysign(tiny, d[n - 1] == 0.0 ? 1.0 : d[n - 1]);
-  for (int i = 0; i < n - 1; ++i) {
-    if (!piv[i]) {
-      x[i + 1] -= dl[i] * x[i];
-    } else {
-      const double t = x[i];
-      x[i] = x[i + 1];
-      x[i + 1] = t - dl[i] * x[i];
-    }
-  }
-  x[n - 1] /= d[n - 1];
-  if (n > 1) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / d[n - 2];
-  for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / d[i];
-}
-
 __global__ void finalize_kernel(LanczosDev L) {
   const int s = blockIdx.x;
   if (!L.active[s]) return;
   extern __shared__ double sm[];
   const int km = L.kmax;
-  double *a = sm, *b = sm + km, *b2 = sm + 2 * km, *dl = sm + 3 * km, *d = sm + 4 * km, *du = sm + 5 * km,
-         *du2 = sm + 6 * km, *x = sm + 7 * km;
-  int *piv = (int *)(sm + 8 * km);
+  double *a = sm, *b = sm + km, *b2 = sm + 2 * km, *x = sm + 3 * km;
   const int kk = L.k[s];
   const int n = kk + 1;
   const int lane = threadIdx.x;
@@ -207,7 +160,7 @@ __global__ void finalize_kernel(LanczosDev L) {
   }
   __syncwarp();
   const double beta_k = L.resid[s];
-  float *af = (float *)piv + km, *b2f = af + km;  // FP32 copies for the bracketing
+  float *af = (float *)(sm + 4 * km), *b2f = af + km;  // FP32 copies for the bracketing
   for (int i = lane; i < n; i += 32) {
     af[i] = (float)a[i];
     if (i < n - 1) b2f[i] = (float)b2[i];
@@ -245,27 +198,32 @@ __global__ void finalize_kernel(LanczosDev L) {
   }
   const double shift = 0.5 * ((double)flo + (double)fhi);
   if (lane == 0) {
-    for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.25 * (double)((i * 7) % 5);
-    const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-    // two inverse iterations at the FP32 shift, a Rayleigh quotient, one more
-    // inverse iteration at that FP64 shift (so the last component of y, which
-    // decides convergence, is accurate), and the final Rayleigh quotient
-    double sh = shift, theta = shift;
-    for (int it = 0; it < 3; ++it) {
-      shifted_solve(a, b, n, sh, tiny, dl, d, du, du2, piv, x);
-      double nn = 0.0;
-      for (int i = 0; i < n; ++i) nn = fma(x[i], x[i], nn);
-      const double inv = 1.0 / sqrt(nn);
-      for (int i = 0; i < n; ++i) x[i] *= inv;
-      theta = 0.0;
-      for (int i = 0; i < n; ++i) {
-        double ty = a[i] * x[i];
-        if (i > 0) ty = fma(b[i - 1], x[i - 1], ty);
-        if (i < n - 1) ty = fma(b[i], x[i + 1], ty);
-        theta = fma(x[i], ty, theta);
+    // Eigenvector by the backward three-term recurrence at shift theta
+    // (rows n-1 .. 1 of (T - theta) y = 0 with y_{n-1} = 1): this is one step
+    // of inverse iteration applied to e_0, stable because the lowest Ritz
+    // vector grows towards j = 0, and it needs no division (1/beta_j is kept
+    // from the iteration that produced beta_j).  The residual left in row 0,
+    // r, gives the Rayleigh quotient theta + r y_0 / |y|^2, which converges
+    // cubically from the FP32 bracket.
+    const double *ib = L.ibeta + (int64_t)s * km;
+    double theta = shift, nrm2 = 1.0;
+    for (int it = 0; it < 4; ++it) {
+      x[n - 1] = 1.0;
+      if (n >= 2) x[n - 2] = (theta - a[n - 1]) * ib[n - 2];
+      for (int j = n - 2; j >= 1; --j) {
+        x[j - 1] = fma(theta - a[j], x[j], -b[j] * x[j + 1]) * ib[j - 1];
+        if (fabs(x[j - 1]) > 1e150)
+          for (int i = j - 1; i < n; ++i) x[i] *= 1e-150;
       }
-      if (it == 1) sh = theta;
+      const double r = (n >= 2) ? fma(a[0] - theta, x[0], b[0] * x[1]) : (a[0] - theta) * x[0];
+      nrm2 = 0.0;
+      for (int i = 0; i < n; ++i) nrm2 = fma(x[i], x[i], nrm2);
+      const double dth = r * x[0] / nrm2;
+      theta += dth;
+      if (!(fabs(dth) > 2.0 * DBL_EPSILON * fabs(theta))) break;
     }
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int i = 0; i < n; ++i) x[i] *= inv;
     for (int i = 0; i < n; ++i) L.y[s * km + i] = x[i];
     const double scale = fmax(1.0, fabs(theta));
     const double res = beta_k * fabs(x[n - 1]);
@@ -283,6 +241,7 @@ __global__ void finalize_kernel(LanczosDev L) {
       L.conv[s] = 0;
     } else {
       L.beta[s * km + kk] = beta_k;
+      L.ibeta[s * km + kk] = 1.0 / beta_k;
       L.k[s] = kk + 1;
     }
   }
@@ -412,7 +371,7 @@ cudaError_t lanczos_subtract(const LanczosDev &L, int pass, cudaStream_t st) {
 }
 
 cudaError_t lanczos_finalize(const LanczosDev &L, cudaStream_t st) {
-  const size_t smem = (size_t)L.kmax * (8 * sizeof(double) + sizeof(int) + 2 * sizeof(float));
+  const size_t smem = (size_t)L.kmax * (4 * sizeof(double) + 2 * sizeof(float));
   finalize_kernel<<<L.S, 32, smem, st>>>(L);
   return cudaGetLastError();
 }

@@ -65,10 +65,11 @@ __device__ __forceinline__ double wsum(double v) {
 // ------------------------------------------------------------------ QRCP
 constexpr int QR_THREADS = 512;
 
-__global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work,
-                                                          int *__restrict__ iwork, double zero_rel) {
+__global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order,
+                                                          double *__restrict__ work, int *__restrict__ iwork,
+                                                          double zero_rel) {
   extern __shared__ double qsm[];  // vn[ca], vref[ca]
-  const SvdJob Jb = jobs[blockIdx.x];
+  const SvdJob Jb = jobs[order[blockIdx.x]];
   const int ra = Jb.rows_a, ca = Jb.cols_a;
   double *A = work + Jb.a_off;
   double *tau = work + Jb.tau_off;
@@ -205,24 +206,48 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restri
 
 // ---------------------------------------------------------------- Jacobi
 constexpr int JAC_THREADS = 512;
-constexpr int JAC_CLUSTER = 8;
+constexpr int JAC_MAX_CLUSTER = 16;
 constexpr int JAC_REG = 8;  // column elements per lane held in registers
+
+// Rotation that zeroes the overlap g of two columns with squared norms a, b:
+// tan(theta) = t, t = sgn(z) / (|z| + sqrt(1 + z^2)), z = (b - a) / (2 g).
+// The angle only steers convergence, so t is formed in FP32 (after scaling
+// both operands of the quotient into FP32 range); cos = 1/sqrt(1 + t^2) is
+// refined to FP64 by two Newton steps on the reciprocal square root, so the
+// pair (cos, sin = cos t) is orthogonal to FP64 precision.
+__device__ __forceinline__ void rotation(double a, double b, double g, double &cs, double &sn) {
+  const double num = b - a, den = 2.0 * g;
+  const int e = max(ilogb(fabs(num)), ilogb(fabs(den)));
+  const float z = (float)scalbn(num, -e) / (float)scalbn(den, -e);
+  const float az = fabsf(z);
+  const float tf = az > 1e15f ? 0.5f / z : copysignf(1.0f, z) / (az + sqrtf(fmaf(z, z, 1.0f)));
+  const double t = (double)tf;
+  const double x = fma(t, t, 1.0);
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  cs = y;
+  sn = y * t;
+}
 
 // one column pair (p, q): overlap, rotation of B's and Jm's columns
 __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, double *jq, int n, int nj,
-                                            int lane, double tol, double abs_floor) {
+                                            int lane, double tol2, double abs_floor) {
   double x[JAC_REG], y[JAC_REG];
   double al = 0.0, be = 0.0, ga = 0.0;
   const bool inreg = n <= 32 * JAC_REG;
+  const int nreg = (n + 31) >> 5;
   if (inreg) {
 #pragma unroll
     for (int r = 0; r < JAC_REG; ++r) {
-      const int i = lane + 32 * r;
-      x[r] = i < n ? ap[i] : 0.0;
-      y[r] = i < n ? aq[i] : 0.0;
-      al = fma(x[r], x[r], al);
-      be = fma(y[r], y[r], be);
-      ga = fma(x[r], y[r], ga);
+      if (r < nreg) {
+        const int i = lane + 32 * r;
+        x[r] = i < n ? ap[i] : 0.0;
+        y[r] = i < n ? aq[i] : 0.0;
+        al = fma(x[r], x[r], al);
+        be = fma(y[r], y[r], be);
+        ga = fma(x[r], y[r], ga);
+      }
     }
   } else {
     for (int i = lane; i < n; i += 32) {
@@ -235,23 +260,21 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
   al = wsum(al);
   be = wsum(be);
   ga = wsum(ga);
-  if (ga == 0.0 || !(fabs(ga) > tol * sqrt(al * be)) || !(fabs(ga) > abs_floor)) return false;
+  // rotate unless |g| <= tol sqrt(a b) (compared squared) or below the floor
+  if (!(ga * ga > tol2 * (al * be)) || !(fabs(ga) > abs_floor)) return false;
   double cs = 0.0, sn = 0.0;
-  if (lane == 0) {
-    const double zeta = (be - al) / (2.0 * ga);
-    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    cs = 1.0 / sqrt(1.0 + t * t);
-    sn = cs * t;
-  }
+  if (lane == 0) rotation(al, be, ga, cs, sn);
   cs = __shfl_sync(0xffffffffu, cs, 0);
   sn = __shfl_sync(0xffffffffu, sn, 0);
   if (inreg) {
 #pragma unroll
     for (int r = 0; r < JAC_REG; ++r) {
-      const int i = lane + 32 * r;
-      if (i < n) {
-        ap[i] = cs * x[r] - sn * y[r];
-        aq[i] = sn * x[r] + cs * y[r];
+      if (r < nreg) {
+        const int i = lane + 32 * r;
+        if (i < n) {
+          ap[i] = cs * x[r] - sn * y[r];
+          aq[i] = sn * x[r] + cs * y[r];
+        }
       }
     }
   } else {
@@ -269,27 +292,34 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
   return true;
 }
 
-__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREADS)
-    jacobi_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work, const int *__restrict__ iwork,
-                  double *__restrict__ sv, int *err) {
+// One job per cluster (cluster size chosen at launch); the pairs of a round
+// are spread over all warps of the cluster, rounds separated by the hardware
+// cluster barrier.
+__global__ void __launch_bounds__(JAC_THREADS, 2)
+    jacobi_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                  int *__restrict__ iwork, double *__restrict__ sv, int *err) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
-  const SvdJob Jb = jobs[blockIdx.x / JAC_CLUSTER];
+  const int csize = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / csize]];
   const int nr = Jb.cols_a;                       // rows of B
   const int n = iwork[Jb.perm_off + Jb.cols_a];   // columns of B: numerical rank
   double *B = work + Jb.b_off;
   double *Jm = work + Jb.j_off;
-  __shared__ double fro_part[JAC_CLUSTER];
+  __shared__ double fro_part[JAC_MAX_CLUSTER];
   __shared__ double wred[JAC_THREADS / 32];
   __shared__ int flag, local_changed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int gw = crank * nw + warp, gnw = JAC_CLUSTER * nw;
+  // pair k of a round goes to CTA k mod csize: the FP64 work of a round is
+  // spread over every SM of the cluster (blocked by CTA it piled up on the
+  // first few while the others waited at the barrier)
+  const int gw = warp * csize + crank, gnw = csize * nw;
   const int64_t nn = (int64_t)n * n, nb = (int64_t)nr * n;
-  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)JAC_CLUSTER * blockDim.x)
+  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)csize * blockDim.x)
     Jm[e] = (e / n == e % n) ? 1.0 : 0.0;
   // ||B||_F^2 over the cluster (partials gathered in rank 0's shared memory)
   double fro = 0.0;
-  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nb; e += (int64_t)JAC_CLUSTER * blockDim.x)
+  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nb; e += (int64_t)csize * blockDim.x)
     fro = fma(B[e], B[e], fro);
   fro = wsum(fro);
   if (lane == 0) wred[warp] = fro;
@@ -303,18 +333,20 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREAD
   cluster.sync();
   const double *fp0 = cluster.map_shared_rank(fro_part, 0);
   fro = 0.0;
-  for (int q = 0; q < JAC_CLUSTER; ++q) fro += fp0[q];
+  for (int q = 0; q < csize; ++q) fro += fp0[q];
   cluster.sync();  // every CTA has read rank 0's partials
   // rotation threshold sqrt(rows) * eps (as in LAPACK's one-sided Jacobi) and
   // an absolute floor eps^2 ||B||_F^2: without it a column made of rounding
   // noise along another one never meets the relative test (each rotation
   // leaves an eps-sized overlap that dominates tol |b_p| |b_q| as |b_q| -> 0).
   const double tol = sqrt((double)nr) * DBL_EPSILON;
+  const double tol2 = tol * tol;
   const double abs_floor = 4.0 * DBL_EPSILON * DBL_EPSILON * fro;
   const int np = n + (n & 1);
   int *flag0 = cluster.map_shared_rank(&flag, 0);
   bool converged = (n < 2);
-  for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
+  int sweep = 0;
+  for (; sweep < 40 && !converged; ++sweep) {
     if (threadIdx.x == 0) local_changed = 0;
     if (crank == 0 && threadIdx.x == 0) flag = 0;
     cluster.sync();
@@ -326,7 +358,7 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREAD
         const int q = i2 == 0 ? 0 : 1 + (i2 - 1 + rnd) % (np - 1);
         if (p >= n || q >= n) continue;
         any |= jacobi_pair(B + (int64_t)p * nr, B + (int64_t)q * nr, Jm + (int64_t)p * n, Jm + (int64_t)q * n, nr,
-                           n, lane, tol, abs_floor);
+                           n, lane, tol2, abs_floor);
       }
       cluster.sync();
     }
@@ -338,6 +370,7 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(JAC_THREAD
     cluster.sync();
   }
   if (!converged && crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
+  if (crank == 0 && threadIdx.x == 0) iwork[Jb.perm_off + Jb.cols_a + 1] = sweep;
   // singular values; columns of B normalised in place; the columns beyond
   // the numerical rank have singular value zero
   for (int j = gw; j < Jb.cols_a; j += gnw) {
@@ -492,18 +525,52 @@ cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_e
   return cudaGetLastError();
 }
 
-cudaError_t launch_svd_qrcp(const SvdJob *jobs, int njobs, double *work, int *iwork, double zero_rel, cudaStream_t st) {
+cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, double *work, int *iwork, double zero_rel,
+                            cudaStream_t st) {
   // shared: two norms per column; callers keep cols_a <= 4096
   const int smem = 2 * 4096 * (int)sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (njobs > 0) qrcp_kernel<<<njobs, QR_THREADS, smem, st>>>(jobs, work, iwork, zero_rel);
+  if (njobs > 0) qrcp_kernel<<<njobs, QR_THREADS, smem, st>>>(jobs, order, work, iwork, zero_rel);
   return cudaGetLastError();
 }
 
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, int njobs, double *work, const int *iwork, double *sv, int *err,
-                              cudaStream_t st) {
-  if (njobs > 0) jacobi_kernel<<<njobs * JAC_CLUSTER, JAC_THREADS, 0, st>>>(jobs, work, iwork, sv, err);
+static cudaError_t launch_jacobi_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, double *work,
+                                          int *iwork, double *sv, int *err, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * csize, 1, 1);
+  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_kernel, jobs, order, work, iwork, sv, err);
+}
+
+// `order` lists the jobs largest first; the first `nbig` of them get
+// clusters of up to 16 CTAs, the rest clusters of 4.
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, int nbig, double *work, int *iwork,
+                              double *sv, int *err, cudaStream_t st) {
+  if (njobs <= 0) return cudaGetLastError();
+  cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaGetLastError();
+  if (nbig > 0) {
+    cudaError_t e = launch_jacobi_clusters(jobs, order, nbig, 16, work, iwork, sv, err, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // 16-CTA clusters not available here: fall back to 8
+      e = launch_jacobi_clusters(jobs, order, nbig, 8, work, iwork, sv, err, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (njobs > nbig) {
+    cudaError_t e = launch_jacobi_clusters(jobs, order + nbig, njobs - nbig, 4, work, iwork, sv, err, st);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
