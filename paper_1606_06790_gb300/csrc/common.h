@@ -189,8 +189,12 @@ cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_e
                                     int psi_buf, double *work, cudaStream_t st);
 cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, double *work, int *iwork, double zero_rel,
                             cudaStream_t st);
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, int nbig, double *work, int *iwork,
-                              double *sv, int *err, cudaStream_t st);
+// Jacobi groups and shared memory: see kernels_svd.cu
+constexpr size_t SVD_BLOCK_SMEM_MAX = 200 * 1024;
+size_t svd_block_smem(int cols, int csize);
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const size_t *smem,
+                              double *work, int *iwork, double *sv, int *err, cudaStream_t st,
+                              const cudaStream_t *side, const cudaEvent_t *ev);
 struct SelectOut {
   int *kept_per_job;   // [njobs]
   int *perm;           // [sum cols_a] kept slot -> index within job (per job, at sv_off)

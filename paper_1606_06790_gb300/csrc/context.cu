@@ -83,6 +83,17 @@ struct idmrg_ctx {
   std::vector<std::vector<int>> bq;      // per bond k (left of site k) channel charges
   idmrg_opts o{};
   cudaStream_t st = nullptr;
+  // side streams of the SVD (small Jacobi groups run beside the large one),
+  // forked from and joined back to st by events
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};
+  idmrg_status side_streams() {
+    for (auto &x : side)
+      if (!x && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return IDMRG_ECUDA;
+    for (auto &e : sev)
+      if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return IDMRG_ECUDA;
+    return IDMRG_OK;
+  }
   idmrg_allocator alloc{};
   bool own_alloc = true;
   std::string err;
@@ -1158,15 +1169,36 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   // largest sector matrices first: they set the length of the SVD phase
   std::vector<int> order(nj);
   for (int j = 0; j < nj; ++j) order[j] = j;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return c->jobs[a].cols_a * (int64_t)c->jobs[a].rows_a > c->jobs[b].cols_a * (int64_t)c->jobs[b].rows_a; });
+  auto bigger = [&](int a, int b) {
+    const SvdJob &x = c->jobs[a], &y = c->jobs[b];
+    if (x.cols_a != y.cols_a) return x.cols_a > y.cols_a;
+    return x.rows_a > y.rows_a;
+  };
+  std::stable_sort(order.begin(), order.end(), bigger);
   NOMEM(c->upload(c->sorder, order));
   CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, c->dp(c->swork), (int *)c->siw.p,
                      c->o.lambda_zero_rel, c->st));
-  int nbig = 0;
-  for (int j = 0; j < nj; ++j) nbig += c->jobs[order[j]].cols_a >= 64 ? 1 : 0;
-  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, nbig, c->dp(c->swork),
-                       (int *)c->siw.p, c->dp(c->ssv), (int *)c->derr.p, c->st));
+  // Jacobi groups by column count: beyond the shared memory of a 16-CTA
+  // cluster in global memory; then block Jacobi on 16, 8, 4 and 1 CTAs
+  int g[4] = {0, 0, 0, 0};
+  size_t gsm[4] = {0, 0, 0, 0};
+  for (int j = 0; j < nj; ++j) {
+    const int ca = c->jobs[order[j]].cols_a;
+    if (ca >= 96 && svd_block_smem(ca, 16) > SVD_BLOCK_SMEM_MAX) g[0] = j + 1;
+    if (ca >= 96) g[1] = j + 1;
+    if (ca >= 40) g[2] = j + 1;
+    if (ca >= 12) g[3] = j + 1;
+  }
+  const int csz[4] = {16, 8, 4, 1};
+  if (g[1] > g[0]) gsm[0] = svd_block_smem(c->jobs[order[g[0]]].cols_a, csz[0]);
+  if (g[2] > g[1]) gsm[1] = svd_block_smem(c->jobs[order[g[1]]].cols_a, csz[1]);
+  if (g[3] > g[2]) gsm[2] = svd_block_smem(c->jobs[order[g[2]]].cols_a, csz[2]);
+  if (nj > g[3]) gsm[3] = svd_block_smem(c->jobs[order[g[3]]].cols_a, csz[3]);
+  for (int k = 0; k < 4; ++k)
+    if (gsm[k] > SVD_BLOCK_SMEM_MAX) return c->fail(IDMRG_EINVAL, "truncate: sector too large for the Jacobi groups");
+  if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
+  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, gsm, c->dp(c->swork),
+                       (int *)c->siw.p, c->dp(c->ssv), (int *)c->derr.p, c->st, c->side, c->sev));
   // select runs on superblocks with jobs only: compact the index arrays
   std::vector<int> sbl;
   for (int q = 0; q < P; ++q)
@@ -1651,6 +1683,10 @@ void idmrg_destroy(idmrg_ctx *c) {
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  for (cudaStream_t x : c->side)
+    if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t e : c->sev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 

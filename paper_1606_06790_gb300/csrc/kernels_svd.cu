@@ -388,6 +388,358 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
   }
 }
 
+// ------------------------------------------------- block Jacobi (shared memory)
+// Same rotations as jacobi_kernel, ordered by blocks so that the columns stay
+// in shared memory.  The rank-n columns of B (and of Jm) are cut into 2C
+// blocks of bw columns, C the cluster size; CTA c holds the blocks at
+// tournament positions c and 2C-1-c.  In a round a CTA rotates every column
+// of one of its blocks against every column of the other (bw sub-rounds of
+// bw disjoint pairs, separated by __syncthreads); then the blocks move one
+// position along the circle (position 0 stays), each CTA writing its two
+// blocks into the receiving CTAs' second buffer through distributed shared
+// memory, so that after 2C-1 rounds every two blocks have met once.  The pairs
+// inside each block are taken in the first round of a sweep.  A sweep costs
+// 2C-1 cluster barriers instead of n-1, and no column leaves the SMs.
+//
+// FP64 arithmetic is the scarce resource here, so the rotations are the
+// scaled ("fast") form: column j is held as d_j x_j, a rotation changes the
+// x of both columns by one FMA per element and multiplies both d by cos; the
+// squared column norms are carried along in closed form (recomputed from the
+// data when cancellation makes the update inaccurate, and at every sweep,
+// when d is folded back into the columns), so each pair needs one dot
+// product instead of three.
+constexpr int BJ_THREADS = 256;
+constexpr int BJ_REG = 10;  // rows per lane held in registers: columns of up to 320 rows
+
+__device__ __forceinline__ int bj_block_at(int pos, int r, int P) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + (P - 1) - r % (P - 1)) % (P - 1);
+}
+
+// 1/x for x > 0 in the range of FP32 normals: FP32 estimate and two Newton
+// steps e <- e (2 - x e) in FP64 (the error squares at each step)
+__device__ __forceinline__ double recip_nr(double x) {
+  double e = (double)__frcp_rn((float)x);
+  e = e * fma(-x, e, 2.0);
+  e = e * fma(-x, e, 2.0);
+  return e;
+}
+
+// The pairs of a sub-round are rotated in three phases (separated by
+// __syncthreads): each warp forms the overlap of its pair's columns (one dot
+// product, the columns stay in its registers); one lane per pair then
+// computes the rotation (bj_rotation: FP64 scalar work is done once per pair,
+// not by 32 lanes); each warp finally updates its pair.  Columns are padded
+// with zero rows to nreg*32 (B) and nregj*32 (Jm), so no loop carries bounds
+// checks.
+
+struct BjPair {   // per pair of a sub-round, in shared memory
+  double g;       // overlap of the stored (unscaled) columns
+  double cp, cq;  // update coefficients
+  int i, j;       // column indices within the two blocks (-1: no pair)
+  int rot;        // 1 rotate, 2 rotate and recompute both norms from the data
+};
+
+// phase 2 for one pair: norms a, b and scales d1, d2 in, updated in place
+__device__ __forceinline__ int bj_rotation(double graw, double &a, double &b, double &d1, double &d2, double tol2,
+                                           double abs_floor, double &cp, double &cq) {
+  const double g = d1 * d2 * graw;
+  if (!(g * g > tol2 * (a * b)) || !(fabs(g) > abs_floor)) return 0;
+  // angle in FP32 from z = (b - a) / (2 g), both scaled by a power of two
+  // that brings 2g to [1, 2): the exponent is read from the bits of g
+  const double num = b - a, den = 2.0 * g;
+  const int ex = ((__double2hiint(den) >> 20) & 0x7ff) - 1023;
+  const double sc = __hiloint2double((1023 - ex) << 20, 0);
+  const float z = __fdividef((float)(num * sc), (float)(den * sc));
+  const float az = fabsf(z);
+  if (!(az < 1e30f)) return 0;  // rotation below FP32 resolution: nothing to do
+  const float tf = az > 1e15f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + __fsqrt_rn(fmaf(z, z, 1.0f))), z);
+  const double t = (double)tf;
+  // cos = 1/sqrt(1 + t^2) to FP64 precision: FP32 estimate, two Newton steps
+  const double xx = fma(t, t, 1.0);
+  double cs = (double)rsqrtf((float)xx);
+  cs = cs * fma(-0.5 * xx * cs, cs, 1.5);
+  cs = cs * fma(-0.5 * xx * cs, cs, 1.5);
+  // x_p <- x_p - t (d_q/d_p) x_q,  x_q <- x_q + t (d_p/d_q) x_p,  d <- cos d
+  cp = -t * (d2 * recip_nr(d1));
+  cq = t * (d1 * recip_nr(d2));
+  // new squared norms cos^2 (a -+ 2 t g + t^2 b); recomputed from the data
+  // when the subtraction has cancelled most of the value
+  const double c2 = cs * cs, tg = 2.0 * t * g, t2 = t * t;
+  const double a2 = c2 * (fma(t2, b, a) - tg), b2 = c2 * (fma(t2, a, b) + tg);
+  const double small = fmax(a, b) * 1e-6;
+  d1 *= cs;
+  d2 *= cs;
+  a = a2;
+  b = b2;
+  return (a2 > small && b2 > small) ? 1 : 2;
+}
+
+__global__ void __launch_bounds__(BJ_THREADS, 2)
+    jacobi_block_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                        int *__restrict__ iwork, double *__restrict__ sv, int *err) {
+  extern __shared__ __align__(16) double bj_sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / C]];
+  const int nr = Jb.cols_a;                       // rows of B
+  const int n = iwork[Jb.perm_off + Jb.cols_a];   // columns of B: numerical rank
+  const int P = 2 * C;
+  const int bw = (n + P - 1) / P;                 // columns per block
+  const int nreg = (nr + 31) >> 5, nregj = (n + 31) >> 5;
+  const int ldb = 32 * nreg, ldj = 32 * nregj;    // padded with zero rows
+  // one block: B columns, Jm columns, squared norms, scales
+  const int offJ = bw * ldb, offN = offJ + bw * ldj, offD = offN + bw;
+  const int slot = (offD + bw + 1) & ~1;          // even: blocks start on 16 bytes
+  __shared__ double fro_part[JAC_MAX_CLUSTER];
+  __shared__ double wred[BJ_THREADS / 32];
+  __shared__ int flag, local_changed;
+  __shared__ BjPair pairs[BJ_THREADS / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double *Bg = work + Jb.b_off;
+  double *Jg = work + Jb.j_off;
+  const int pos[2] = {crank, P - 1 - crank};
+  auto slotp = [&](int buf, int which) { return bj_sm + (buf * 2 + which) * slot; };
+  auto valid = [&](int k) { return max(0, min(bw, n - k * bw)); };
+  if (nreg > BJ_REG || nregj > BJ_REG) {  // excluded by the host; never rotate out of bounds
+    if (crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
+    return;
+  }
+
+  // load: block k = pos at the start of a sweep; Jm starts as the identity
+  double fro = 0.0;
+  for (int w = 0; w < 2; ++w) {
+    const int k = pos[w], nv = valid(k);
+    double *sb = slotp(0, w);
+    for (int e = threadIdx.x; e < offJ; e += blockDim.x) {
+      const int j = e / ldb, i = e - j * ldb;
+      const double v = (j < nv && i < nr) ? Bg[(int64_t)(k * bw + j) * nr + i] : 0.0;
+      sb[e] = v;
+      fro = fma(v, v, fro);
+    }
+    for (int e = threadIdx.x; e < bw * ldj; e += blockDim.x) {
+      const int j = e / ldj, i = e - j * ldj;
+      sb[offJ + e] = (j < nv && i == k * bw + j) ? 1.0 : 0.0;
+    }
+    for (int j = threadIdx.x; j < bw; j += blockDim.x) sb[offD + j] = 1.0;
+  }
+  fro = wsum(fro);
+  if (lane == 0) wred[warp] = fro;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += wred[q];
+    double *dst = cluster.map_shared_rank(fro_part, 0);
+    dst[crank] = t;
+  }
+  cluster.sync();
+  const double *fp0 = cluster.map_shared_rank(fro_part, 0);
+  fro = 0.0;
+  for (int q = 0; q < C; ++q) fro += fp0[q];
+  cluster.sync();
+  const double tol = sqrt((double)nr) * DBL_EPSILON;
+  const double tol2 = tol * tol;
+  const double abs_floor = 4.0 * DBL_EPSILON * DBL_EPSILON * fro;
+  int *flag0 = cluster.map_shared_rank(&flag, 0);
+  bool converged = (n < 2);
+  int sweep = 0, cur = 0;
+  // fold the scales into the columns of the home blocks and recompute norms
+  auto fold = [&]() {
+    for (int t = warp; t < 2 * bw; t += nw) {
+      const int w = t >= bw ? 1 : 0, j = t - w * bw;
+      double *sb = slotp(cur, w);
+      const double d = sb[offD + j];
+      double *bj = sb + j * ldb, *jj = sb + offJ + j * ldj;
+      double s = 0.0;
+      for (int i = lane; i < ldb; i += 32) {
+        const double v = bj[i] * d;
+        bj[i] = v;
+        s = fma(v, v, s);
+      }
+      for (int i = lane; i < ldj; i += 32) jj[i] *= d;
+      s = wsum(s);
+      __syncwarp();
+      if (lane == 0) {
+        sb[offN + j] = s;
+        sb[offD + j] = 1.0;
+      }
+    }
+    __syncthreads();
+  };
+  // one sub-round: pairs (s0 col pi[k], s1 col pj[k]), k < np, one warp each
+  auto subround = [&](double *s0, double *s1, int np) -> bool {
+    const bool mine = warp < np && pairs[warp].i >= 0;
+    double x[BJ_REG], y[BJ_REG];
+    double *xp = nullptr, *xq = nullptr;
+    if (mine) {
+      xp = s0 + pairs[warp].i * ldb;
+      xq = s1 + pairs[warp].j * ldb;
+      double ga = 0.0;
+#pragma unroll
+      for (int r = 0; r < BJ_REG; ++r)
+        if (r < nreg) {
+          x[r] = xp[lane + 32 * r];
+          y[r] = xq[lane + 32 * r];
+          ga = fma(x[r], y[r], ga);
+        }
+      ga = wsum(ga);
+      if (lane == 0) pairs[warp].g = ga;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < np && pairs[lane].i >= 0) {
+      BjPair &pr = pairs[lane];
+      double a = s0[offN + pr.i], b = s1[offN + pr.j], d1 = s0[offD + pr.i], d2 = s1[offD + pr.j];
+      double cp = 0.0, cq = 0.0;
+      pr.rot = bj_rotation(pr.g, a, b, d1, d2, tol2, abs_floor, cp, cq);
+      if (pr.rot) {
+        pr.cp = cp;
+        pr.cq = cq;
+        s0[offN + pr.i] = a;
+        s1[offN + pr.j] = b;
+        s0[offD + pr.i] = d1;
+        s1[offD + pr.j] = d2;
+      }
+    }
+    __syncthreads();
+    bool rot = false;
+    if (mine && pairs[warp].rot) {
+      rot = true;
+      const double cp = pairs[warp].cp, cq = pairs[warp].cq;
+#pragma unroll
+      for (int r = 0; r < BJ_REG; ++r)
+        if (r < nreg) {
+          const double u = fma(cp, y[r], x[r]), v = fma(cq, x[r], y[r]);
+          x[r] = u;
+          y[r] = v;
+          xp[lane + 32 * r] = u;
+          xq[lane + 32 * r] = v;
+        }
+      double *jp = s0 + offJ + pairs[warp].i * ldj, *jq = s1 + offJ + pairs[warp].j * ldj;
+#pragma unroll
+      for (int r = 0; r < BJ_REG; ++r)
+        if (r < nregj) {
+          const double u = jp[lane + 32 * r], v = jq[lane + 32 * r];
+          jp[lane + 32 * r] = fma(cp, v, u);
+          jq[lane + 32 * r] = fma(cq, u, v);
+        }
+      if (pairs[warp].rot == 2) {  // cancellation: norms from the rotated data
+        double np2 = 0.0, nq2 = 0.0;
+#pragma unroll
+        for (int r = 0; r < BJ_REG; ++r)
+          if (r < nreg) {
+            np2 = fma(x[r], x[r], np2);
+            nq2 = fma(y[r], y[r], nq2);
+          }
+        np2 = wsum(np2);
+        nq2 = wsum(nq2);
+        if (lane == 0) {
+          const double dp = s0[offD + pairs[warp].i], dq = s1[offD + pairs[warp].j];
+          s0[offN + pairs[warp].i] = dp * dp * np2;
+          s1[offN + pairs[warp].j] = dq * dq * nq2;
+        }
+      }
+    }
+    __syncthreads();
+    return rot;
+  };
+  for (; sweep < 40 && !converged; ++sweep) {
+    fold();
+    if (threadIdx.x == 0) local_changed = 0;
+    if (crank == 0 && threadIdx.x == 0) flag = 0;
+    cluster.sync();
+    bool any = false;
+    for (int rnd = 0; rnd < P - 1; ++rnd) {
+      double *st0 = slotp(cur, 0), *st1 = slotp(cur, 1);
+      const int nv0 = valid(bj_block_at(pos[0], rnd, P)), nv1 = valid(bj_block_at(pos[1], rnd, P));
+      if (rnd == 0) {
+        // pairs inside each block: round-robin over bp slots, one block at a
+        // time (a sub-round's pairs share the two block pointers)
+        const int bp = bw + (bw & 1), half = bp / 2, bm = bp - 1;
+        for (int w = 0; w < 2; ++w) {
+          const int nv = w ? nv1 : nv0;
+          double *sb = w ? st1 : st0;
+          for (int sr = 0; sr < bm; ++sr) {
+            for (int c0 = 0; c0 < half; c0 += nw) {
+              const int np = min(nw, half - c0);
+              if (threadIdx.x < np) {
+                const int i = c0 + threadIdx.x;
+                int p = 0, q;
+                if (i != 0) {
+                  p = i - 1 + sr;
+                  p = 1 + (p >= bm ? p - bm : p);
+                }
+                q = bp - 2 - i + sr;
+                q = 1 + (q >= bm ? q - bm : q);
+                const bool ok = p < nv && q < nv;
+                pairs[threadIdx.x].i = ok ? p : -1;
+                pairs[threadIdx.x].j = ok ? q : -1;
+                pairs[threadIdx.x].rot = 0;
+              }
+              __syncthreads();
+              any |= subround(sb, sb, np);
+            }
+          }
+        }
+      }
+      // every column of the first block against every column of the second
+      for (int sr = 0; sr < bw; ++sr) {
+        for (int c0 = 0; c0 < bw; c0 += nw) {
+          const int np = min(nw, bw - c0);
+          if (threadIdx.x < np) {
+            const int i = c0 + threadIdx.x;
+            int j = i + sr;
+            if (j >= bw) j -= bw;
+            const bool ok = i < nv0 && j < nv1;
+            pairs[threadIdx.x].i = ok ? i : -1;
+            pairs[threadIdx.x].j = ok ? j : -1;
+            pairs[threadIdx.x].rot = 0;
+          }
+          __syncthreads();
+          any |= subround(st0, st1, np);
+        }
+      }
+      if (C > 1) {
+        // move both blocks one position on: position 0 stays, P-1 goes to 1
+        for (int w = 0; w < 2; ++w) {
+          const int dpn = pos[w] == 0 ? 0 : (pos[w] == P - 1 ? 1 : pos[w] + 1);
+          const int drank = dpn < C ? dpn : P - 1 - dpn, dw = dpn < C ? 0 : 1;
+          double2 *dst = reinterpret_cast<double2 *>(cluster.map_shared_rank(slotp(cur ^ 1, dw), drank));
+          const double2 *src = reinterpret_cast<const double2 *>(w ? st1 : st0);
+          for (int e = threadIdx.x; e < slot / 2; e += blockDim.x) dst[e] = src[e];
+        }
+        cluster.sync();
+        cur ^= 1;
+      }
+    }
+    if (any && lane == 0) local_changed = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && local_changed) atomicOr(flag0, 1);
+    cluster.sync();
+    converged = (*flag0 == 0);
+    cluster.sync();
+  }
+  fold();
+  if (!converged && crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
+  if (crank == 0 && threadIdx.x == 0) iwork[Jb.perm_off + Jb.cols_a + 1] = sweep;
+  // after whole sweeps every block is back at its starting position: singular
+  // values, normalised columns of B and the columns of Jm go back to memory
+  for (int w = 0; w < 2; ++w) {
+    const int k = pos[w], nv = valid(k);
+    const double *sb = slotp(cur, w);
+    for (int j = warp; j < nv; j += nw) {
+      const double *bj = sb + j * ldb;
+      const double s = sqrt(sb[offN + j]);
+      const int g = k * bw + j;
+      if (lane == 0) sv[Jb.sv_off + g] = s;
+      const double inv = s > 0.0 ? 1.0 / s : 0.0;
+      for (int i = lane; i < nr; i += 32) Bg[(int64_t)g * nr + i] = bj[i] * inv;
+      for (int i = lane; i < n; i += 32) Jg[(int64_t)g * n + i] = sb[offJ + j * ldj + i];
+    }
+  }
+  if (crank == 0)
+    for (int j = n + (int)threadIdx.x; j < Jb.cols_a; j += blockDim.x) sv[Jb.sv_off + j] = 0.0;
+}
+
 // ---------------------------------------------------------------- select
 struct Entry {
   double s;
@@ -552,23 +904,83 @@ static cudaError_t launch_jacobi_clusters(const SvdJob *jobs, const int *order, 
   return cudaLaunchKernelEx(&cfg, jacobi_kernel, jobs, order, work, iwork, sv, err);
 }
 
-// `order` lists the jobs largest first; the first `nbig` of them get
-// clusters of up to 16 CTAs, the rest clusters of 4.
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, int nbig, double *work, int *iwork,
-                              double *sv, int *err, cudaStream_t st) {
+static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, size_t smem,
+                                         double *work, int *iwork, double *sv, int *err, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * csize, 1, 1);
+  cfg.blockDim = dim3(BJ_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_block_kernel, jobs, order, work, iwork, sv, err);
+}
+
+// shared memory of the block kernel for a job of `cols` columns in clusters
+// of `csize` (the rank is at most cols): four blocks of B and Jm columns
+size_t svd_block_smem(int cols, int csize) {
+  const int64_t bw = (cols + 2 * csize - 1) / (2 * csize);
+  const int64_t pad = 32 * (((int64_t)cols + 31) / 32);
+  if (pad > 32 * BJ_REG) return (size_t)-1;  // beyond the registers of the block kernel
+  return (size_t)(4 * (bw * (2 * pad + 2) + 1) * sizeof(double));
+}
+
+// `order` lists the jobs by column count, largest first, in five groups
+// [g[k-1], g[k]) (g[-1] = 0, g[4] = njobs): 0 Jacobi in global memory on
+// 16-CTA clusters (columns beyond the shared memory of the block kernel),
+// 1..4 block Jacobi on clusters of 16, 8, 4 and 1 CTAs with smem[k-1] bytes
+// of shared memory.  Groups 0 and 1 run on `st`, the others on the side
+// streams side[0..2], forked from and joined back to `st` by the events
+// ev[0..3].
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const size_t *smem,
+                              double *work, int *iwork, double *sv, int *err, cudaStream_t st,
+                              const cudaStream_t *side, const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
   cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(jacobi_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SVD_BLOCK_SMEM_MAX);
+  if (e != cudaSuccess) return e;
   cudaGetLastError();
-  if (nbig > 0) {
-    cudaError_t e = launch_jacobi_clusters(jobs, order, nbig, 16, work, iwork, sv, err, st);
+  const int lo[5] = {0, g[0], g[1], g[2], g[3]}, hi[5] = {g[0], g[1], g[2], g[3], njobs};
+  const int csz[5] = {16, 16, 8, 4, 1};
+  e = cudaEventRecord(ev[0], st);
+  if (e != cudaSuccess) return e;
+  for (int k = 2; k < 5; ++k) {
+    if (hi[k] <= lo[k]) continue;
+    e = cudaStreamWaitEvent(side[k - 2], ev[0], 0);
+    if (e != cudaSuccess) return e;
+    e = launch_block_clusters(jobs, order + lo[k], hi[k] - lo[k], csz[k], smem[k - 1], work, iwork, sv, err,
+                              side[k - 2]);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev[k - 1], side[k - 2]);
+    if (e != cudaSuccess) return e;
+  }
+  if (hi[0] > lo[0]) {
+    e = launch_jacobi_clusters(jobs, order, hi[0], 16, work, iwork, sv, err, st);
     if (e != cudaSuccess) {
       cudaGetLastError();  // 16-CTA clusters not available here: fall back to 8
-      e = launch_jacobi_clusters(jobs, order, nbig, 8, work, iwork, sv, err, st);
+      e = launch_jacobi_clusters(jobs, order, hi[0], 8, work, iwork, sv, err, st);
     }
     if (e != cudaSuccess) return e;
   }
-  if (njobs > nbig) {
-    cudaError_t e = launch_jacobi_clusters(jobs, order + nbig, njobs - nbig, 4, work, iwork, sv, err, st);
+  if (hi[1] > lo[1]) {
+    e = launch_block_clusters(jobs, order + lo[1], hi[1] - lo[1], 16, smem[0], work, iwork, sv, err, st);
+    if (e != cudaSuccess) {
+      // 16-CTA clusters not available: the global-memory kernel on 8
+      cudaGetLastError();
+      e = launch_jacobi_clusters(jobs, order + lo[1], hi[1] - lo[1], 8, work, iwork, sv, err, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  for (int k = 2; k < 5; ++k) {
+    if (hi[k] <= lo[k]) continue;
+    e = cudaStreamWaitEvent(st, ev[k - 1], 0);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
