@@ -7,7 +7,11 @@ renormalised, all through the C ABI of libidmrg.  Workload: S=1/2 random-bond
 Heisenberg chain, l = 16 (8 superblocks per step), J_k ~ U[0.5, 1.5] from
 PCG64 seed 1606, m = 256, measured in the saturated regime (D = m).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64] [--impl reference]
+The headline is the mixed-precision path (H_eff psi on the tensor cores in
+TF32x3, Lanczos and SVD in FP64); the same run times the FP64 path on the
+same workload and reports the largest |dE/site| between the two.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|fp64] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own
 disorder realisation (seed 1606 + rank): independent problems, no exchange.
@@ -17,7 +21,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -31,23 +34,45 @@ METRIC = "iDMRG unit-cell steps/sec and H_eff·ψ TFLOP/s (mixed vs FP64) at |Δ
 WORKLOAD = "randchain_l16_m256"
 SATURATE = 11            # iterations until every block holds m states (n >= log2 m + 2)
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
-HBM_FALLBACK, BF16_FALLBACK = 6800.0, 1900.0
+HBM_FALLBACK, BF16_FALLBACK, BF16_SUST_FALLBACK = 6800.0, 1900.0, 1700.0
 FP64_ALU_PEAK = 152 * 2070e6 * 4 / 1e9   # GFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 
 
-def peaks():
+def peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return p["hbm_gbs"], p["bf16_tflops"], p.get("bf16_tflops_sustained", p["bf16_tflops"]), "measured"
+        return {"hbm": p["hbm_gbs"], "bf16": p["bf16_tflops"],
+                "bf16_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]), "src": "measured"}
     except Exception:
-        return HBM_FALLBACK, BF16_FALLBACK, 1700.0, "fallback"
+        return {"hbm": HBM_FALLBACK, "bf16": BF16_FALLBACK, "bf16_sustained": BF16_SUST_FALLBACK, "src": "fallback"}
 
 
-def make_workload(rank: int, m: int):
+def rank_seed(rank: int) -> int:
+    """Disorder realisation of a rank: independent problems, one per GPU."""
+    return 1606 + rank
+
+
+def make_workload(rank: int):
     from workloads import build_mpo, random_chain_bonds
-    seed = 1606 + rank
+    seed = rank_seed(rank)
     return build_mpo(random_chain_bonds(16, 0.5, 1.5, seed), 16), seed
+
+
+def job_value(world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank ran `steps` steps of its own problem;
+    `seconds` is the slowest rank's time."""
+    return world * steps / seconds
+
+
+def reduce_max(values, dist, device):
+    """Max over ranks of a few timings (the job takes as long as its slowest rank)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
 
 
 class Clocks:
@@ -104,16 +129,18 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"heff_gemm": ["kernels_f64.cu"], "lanczos_vec": ["kernels_lanczos.cu"],
-                  "svd": ["kernels_svd.cu"], "env": ["kernels_f64.cu"], "heff_wstage": ["kernels_f64.cu"]}
+KERNEL_SOURCES = {"heff_gemm": ["kernels_f64.cu", "kernels_tc.cu"], "heff_wstage": ["kernels_f64.cu", "kernels_tc.cu"],
+                  "lanczos_vec": ["kernels_lanczos.cu"], "lanczos_tri": ["kernels_lanczos.cu"],
+                  "svd": ["kernels_svd.cu"], "env": ["kernels_f64.cu"], "predict": ["kernels_f64.cu"]}
 
 
-def traffic_for(kclass: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged since."""
+def traffic_for(kclass: str, prec: str):
+    """DRAM bytes per launch of a kernel class from a committed ncu summary
+    (profiles/traffic.json), used only while the class's sources are unchanged."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        e = t[kclass]
+        e = t[f"{kclass}/{prec}"]
         if e.get("source_hash") == source_hash(*KERNEL_SOURCES[kclass]):
             return e["dram_bytes_per_launch"]
     except Exception:
@@ -121,27 +148,42 @@ def traffic_for(kclass: str):
     return None
 
 
-def roofline(prof: dict, prec: str, hbm: float, bf16: float, src: str):
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
+def class_roofline(name: str, d: dict, prec: str, pk: dict):
+    """Roofline of one kernel class from its event-timed launches.
+
+    FP64 arithmetic (SVD, FP64 H_eff, environments, prediction) is bound by
+    the FP64 units: 152 SMs x 2 FMA/clk x 2.07 GHz; the reduced-precision
+    H_eff by the TF32 tensor pipe (measured sustained bf16 x nominal
+    tf32/bf16); the Lanczos vector kernels by HBM bandwidth."""
     sec = d["ms"] * 1e-3
-    per_launch_ms = d["ms"] / max(d["launches"], 1)
-    if dom in ("heff_gemm", "env", "heff_wstage", "predict") and d["flops"] > 0:
-        if prec == "fp64":
-            achieved = d["flops"] / sec / 1e9
-            return dom, {"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_ALU_PEAK, "traffic": traffic_for(dom),
-                         "kernel": dom, "launch_ms": per_launch_ms,
-                         "peak_source": "FP64 FMA units x clock (152 SMs x 2 FMA/clk x 2.07 GHz)"}
-        peak = bf16 * (1.1 / 2.25) if prec == "tf32x3" else bf16
-        achieved = d["flops"] / sec / 1e12
-        return dom, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic_for(dom), "kernel": dom,
-                     "launch_ms": per_launch_ms, "peak_source": f"{src} bf16 x nominal tf32/bf16 ratio"}
-    achieved = d["bytes"] / sec / 1e9 if d["bytes"] > 0 else 0.0
-    return dom, {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                 "traffic": traffic_for(dom), "kernel": dom, "launch_ms": per_launch_ms,
-                 "peak_source": f"{src} copy bandwidth"}
+    out = {"kernel": name, "launch_ms": d["ms"] / max(d["launches"], 1), "traffic": traffic_for(name, prec)}
+    if name in ("heff_gemm", "heff_wstage") and prec != "fp64":
+        peak = pk["bf16_sustained"] * (1.1 / 2.25)
+        achieved = d["flops"] / sec / 1e12 if sec > 0 else 0.0
+        out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": f"{pk['src']} sustained bf16 x nominal tf32/bf16 (1.1/2.25); "
+                                   "split products counted once"})
+    elif name in ("heff_gemm", "heff_wstage", "svd", "env", "predict"):
+        achieved = d["flops"] / sec / 1e9 if sec > 0 else 0.0
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
+                    "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"})
+    else:
+        achieved = d["bytes"] / sec / 1e9 if sec > 0 else 0.0
+        out.update({"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
+                    "peak_source": f"{pk['src']} copy bandwidth"})
+    out["frac"] = out["achieved"] / out["peak"]
+    keys = ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "launch_ms", "peak_source")
+    return {k: out[k] for k in keys}
+
+
+def heff_roofline(prof: dict, prec: str, pk: dict):
+    """H_eff psi as a whole (GEMM stages + two-site MPO stage): the metric's FLOP/s."""
+    d = {"ms": prof["heff_gemm"]["ms"] + prof["heff_wstage"]["ms"], "launches": prof["heff_gemm"]["launches"],
+         "flops": prof["heff_gemm"]["flops"] + prof["heff_wstage"]["flops"], "bytes": 0.0}
+    r = class_roofline("heff_gemm", d, prec, pk)
+    r["kernel"] = "heff (gemm + wstage)"
+    r["traffic"] = None
+    return r
 
 
 def cpu_baseline(mpo, m: int, budget_s: float = 25.0, timed_steps: int = 2):
@@ -174,7 +216,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    mpo, seed = make_workload(0, args.m)
+    mpo, seed = make_workload(0)
     from oracle.idmrg import ParallelIDMRG
     ref = ParallelIDMRG.from_mpo(mpo, m=args.m)
     while ref.n <= SATURATE:
@@ -198,15 +240,77 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_run(pkg, mpo, m: int, prec: str, steps: int, warmup: int, dev, flush, dist, with_clocks: bool, local: int):
+    """Saturate, warm up, then time `steps` unit-cell steps with CUDA events on
+    the context's stream (L2 flushed before each step, outside the events)."""
+    import torch
+    ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=prec)
+    for _ in range(SATURATE):
+        ctx.unit_cell_step()
+    for _ in range(max(warmup, 3)):
+        ctx.unit_cell_step()
+    stream = ctx.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    clocks = Clocks(local) if with_clocks else None
+    launches0 = ctx.launch_count()
+    h2d0, d2h0 = ctx.transfer_bytes()
+    ctx.profile_enable(True)
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    torch.cuda.nvtx.range_push("timed")
+    wall, reports = [], []
+    for k in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ev[k][0].record(stream)
+        reports.append(ctx.unit_cell_step())
+        ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall.append(time.perf_counter() - t)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    clk = clocks.stop() if clocks else None
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    res = {"ctx": ctx, "step_ms": step_ms, "wall_s": sum(wall), "reports": reports, "prof": prof, "clocks": clk,
+           "launches": ctx.launch_count() - launches0}
+    h2d1, d2h1 = ctx.transfer_bytes()
+    res["h2d"] = (h2d1 - h2d0) // steps
+    res["d2h"] = (d2h1 - d2h0) // steps
+    return res
+
+
+def max_de_per_site(ra, rb):
+    """Largest |e_a - e_b| / (2n+2) over the superblocks of steps with equal n."""
+    worst = 0.0
+    by_n = {int(r["n"]): r for r in rb}
+    for r in ra:
+        o = by_n.get(int(r["n"]))
+        if o is None:
+            continue
+        sites = 2 * int(r["n"]) + 2
+        for x, y in zip(r["energy"], o["energy"]):
+            worst = max(worst, abs(float(x) - float(y)) / sites)
+    return worst
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3"])
     ap.add_argument("--m", type=int, default=256)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -220,89 +324,66 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    mpo, seed = make_workload(rank, args.m)
-    ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=args.m, prec=args.prec)
-    for _ in range(SATURATE):
-        ctx.unit_cell_step()
-    for _ in range(max(args.warmup, 3)):
-        ctx.unit_cell_step()
+    mpo, seed = make_workload(rank)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = ctx.stream
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(local)
-    launches0 = ctx.launch_count()
-    h2d0, d2h0 = ctx.transfer_bytes()
-    ctx.profile_enable(True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    torch.cuda.nvtx.range_push("timed")
-    wall = []
-    reports = []
-    for k in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        ev[k][0].record(stream)
-        reports.append(ctx.unit_cell_step())
-        ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        wall.append(time.perf_counter() - t)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-    step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    launches = ctx.launch_count() - launches0
-    h2d1, d2h1 = ctx.transfer_bytes()
-    t_dev = step_ms * 1e-3
-    t_wall = sum(wall)
-    if world > 1:
-        tt = torch.tensor([t_dev, t_wall], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev, t_wall = float(tt[0]), float(tt[1])
-    value = world * args.steps / t_dev
-    e2e = world * args.steps / t_wall
-    hbm, bf16, bf16s, src = peaks()
-    dom, roof = roofline(prof, args.prec, hbm, bf16, src)
+    run = timed_run(pkg, mpo, args.m, args.prec, args.steps, args.warmup, dev, flush, dist, True, local)
+    cmp = None
+    if args.prec != "fp64" and not args.no_fp64_compare:
+        cmp = timed_run(pkg, mpo, args.m, "fp64", args.steps, args.warmup, dev, flush, dist, False, local)
+    t_dev, t_wall = run["step_ms"] * 1e-3, run["wall_s"]
+    t_dev64 = cmp["step_ms"] * 1e-3 if cmp else 0.0
+    t_dev, t_wall, t_dev64 = reduce_max([t_dev, t_wall, t_dev64], dist, dev)
+    pk = peaks()
+    prof = run["prof"]
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    roof = class_roofline(dom, prof[dom], args.prec, pk)
     kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                    "gflops_per_s": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0,
                    "gbytes_per_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
                for k, v in prof.items()}
+    ctx = run["ctx"]
     flops, _ = ctx.heff_cost(-1)
-    last = reports[-1]
+    last = run["reports"][-1]
     if rank != 0:
         ctx.close()
+        if cmp is not None:
+            cmp["ctx"].close()
         if world > 1:
             dist.destroy_process_group()
         return
     line = {
-        "metric": METRIC, "value": value, "unit": "unit-cell steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
+        "metric": METRIC, "value": job_value(world, args.steps, t_dev), "unit": "unit-cell steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else f"{args.prec}+f64",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "ell": 16, "m": args.m, "solves_per_step": 8, "seed": seed,
                    "regime": f"saturated (n > {SATURATE}, D = {int(max(last['kept']))})",
-                   "precision": args.prec, "parallelism": f"{world} independent realisation(s)",
+                   "precision": args.prec + ("" if args.prec == "fp64" else " H_eff psi; FP64 Lanczos and SVD"),
+                   "parallelism": f"{world} independent realisation(s), one per GPU",
                    "l2": "flushed before every timed step (256 MiB write, outside the events)"},
         "roofline": roof,
-        "gpu_launches": launches,
-        "e2e": {"value": e2e, "unit": "unit-cell steps/s",
-                "h2d_bytes_per_step": (h2d1 - h2d0) // args.steps, "d2h_bytes_per_step": (d2h1 - d2h0) // args.steps,
-                "note": "wall clock around idmrg_unit_cell_step with its host-side block tables and report"},
+        "roofline_heff": heff_roofline(prof, args.prec, pk),
+        "gpu_launches": run["launches"],
+        "e2e": {"value": job_value(world, args.steps, t_wall), "unit": "unit-cell steps/s",
+                "h2d_bytes_per_step": run["h2d"], "d2h_bytes_per_step": run["d2h"],
+                "note": "wall clock around idmrg_unit_cell_step: host block tables in, step report out"},
         "kernels": kernels,
         "svd": ctx.svd_stats(),
         "heff": {"flops_per_matvec_all_superblocks": flops,
                  "lanczos_iters_last_step": [int(x) for x in last["iters"]]},
-        "clocks": clk,
+        "clocks": run["clocks"],
         "energy_per_site_last": float(last["energy"][0] / (2 * last["n"] + 2)),
     }
+    if cmp is not None:
+        line["fp64"] = {"value": job_value(world, args.steps, t_dev64), "unit": "unit-cell steps/s",
+                        "ms_per_step": t_dev64 * 1e3 / args.steps,
+                        "max_abs_de_per_site": max_de_per_site(run["reports"], cmp["reports"]),
+                        "heff_roofline": heff_roofline(cmp["prof"], "fp64", pk)}
+        cmp["ctx"].close()
     if world == 1 and not args.no_cpu_baseline:
         _, cb = cpu_baseline(mpo, args.m)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

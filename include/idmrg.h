@@ -212,7 +212,8 @@ idmrg_status idmrg_launch_count(const idmrg_ctx *ctx, uint64_t *count);
  * bracketed by CUDA events on the context's stream; idmrg_profile_read
  * synchronises and returns the summed device time, the number of launches and
  * the algorithmic flops and bytes of those launches (flops: 2 M N K per GEMM
- * task of the superblocks that were active, 2 per element per MPO term;
+ * task of the superblocks that were active, 2 per element per MPO term; for
+ * the SVD class the R-SVD count 6 r c^2 + 20 c^3 per r x c sector matrix;
  * bytes: operands read once and results written once).  Enabling resets. */
 typedef enum {
   IDMRG_K_HEFF_GEMM = 0,   /* H_eff psi stages L.psi and T3.R^T (Step 3)       */

@@ -1215,7 +1215,14 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   so.kept = (int *)c->skept.p;
   CK(launch_svd_select((const SvdJob *)c->sjobs.p, (const int *)c->sjob0.p, (const int *)c->snjob.p, (int)sbl.size(),
                        c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, so, max_entries, c->st));
-  c->kend(IDMRG_K_SVD);
+  // algorithmic flops of the sector SVDs: the R-SVD count 6 r c^2 + 20 c^3
+  // for singular values and both thin factors of an r x c matrix, r >= c
+  double svd_flops = 0.0;
+  for (const SvdJob &j : c->jobs) {
+    const double r = j.rows_a, cc = j.cols_a;
+    svd_flops += 6.0 * r * cc * cc + 20.0 * cc * cc * cc;
+  }
+  c->kend(IDMRG_K_SVD, svd_flops, 0.0);
   c->launches += 3;
   std::vector<int> kpj(nj), iwh(iw);
   std::vector<double> lam_sorted(sv), eps(sbl.size()), epsb(sbl.size());
