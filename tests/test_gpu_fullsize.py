@@ -1,0 +1,86 @@
+"""The bench workload at full size, in the launch configuration bench.py
+times: random-bond chain l = 16, J ~ U[0.5, 1.5] (seed 1606), m = 256, all
+8 superblocks batched, run in lockstep with the FP64 oracle from n = 1 into
+the saturated regime (D = m).  FP64 mode within 1e-10 per site, TF32x3 mode
+within 1e-8 per site, every step; kept dimensions equal except where the
+zero threshold decides them (see _check_kept).
+
+Also the wider MPOs (w up to 20) and longer unit cells of the two cylinder
+models, at reduced m: J1-J2 on the 4-leg square cylinder (l = 8) and the
+kagome YC8 cylinder (l = 12), FP64 within 1e-10 per site.
+"""
+import numpy as np
+import pytest
+
+from oracle.idmrg import ParallelIDMRG
+from workloads import build_mpo, kagome_yc8_bonds, make_config, yc4_j1j2_bonds
+
+from gpu_helpers import context
+
+pytestmark = pytest.mark.gpu
+
+
+ZERO_REL = 1e-12  # singular values at or below zero_rel * lam_max are dropped (both sides)
+
+
+def _check_kept(ctx, g, r):
+    """Kept dimensions: equal, except where the cut is decided by the zero
+    threshold.  Singular values near zero_rel * lam_max carry rounding of
+    ~1e-16 absolute on either side, so which of them fall below the threshold
+    is not unique; every state between the two cuts must then lie within 10x
+    of the threshold in both spectra (and weigh nothing)."""
+    if np.array_equal(g["kept"], r.kept):
+        return
+    for p in range(len(r.kept)):
+        kg, kr = int(g["kept"][p]), int(r.kept[p])
+        if kg == kr:
+            continue
+        lo, hi = min(kg, kr), max(kg, kr)
+        lg, lr = np.asarray(ctx.get_lambda(p)), np.asarray(r.lam_all[p])
+        band = 10 * ZERO_REL
+        assert np.all(lr[lo:hi] <= band * lr[0]), (r.n, p, kg, kr, lr[lo:hi] / lr[0])
+        assert np.all(lg[lo:min(hi, len(lg))] <= band * lg[0]), (r.n, p, kg, kr, lg[lo:hi] / lg[0])
+
+
+def _check(ctx, g, r, tol):
+    sites = 2 * r.n + 2
+    assert g["n"] == r.n
+    assert np.max(np.abs(g["energy"] - r.energies)) / sites < tol, (r.n, g["energy"], r.energies)
+    assert np.max(np.abs(g["eps"] - r.eps)) < tol, (r.n, g["eps"], r.eps)
+    assert np.max(np.abs(g["bond"] - r.bond)) < tol, (r.n, g["bond"], r.bond)
+    _check_kept(ctx, g, r)
+    if r.e_g is not None:
+        assert abs(g["e_g"] - r.e_g) < tol
+
+
+def test_bench_workload_fp64_and_tf32x3_against_oracle():
+    mpo, o = make_config("randchain_l16_m256")
+    m = o["m"]
+    ref = ParallelIDMRG.from_mpo(mpo, m=m)
+    g64 = context(mpo, m, prec="fp64")
+    gmx = context(mpo, m, prec="tf32x3")
+    saturated = 0
+    for _ in range(16):
+        r = ref.step()
+        a = g64.unit_cell_step()
+        b = gmx.unit_cell_step()
+        _check(g64, a, r, 1e-10)
+        _check(gmx, b, r, 1e-8)
+        # the cut at m (less the multiplet it would split) decides D
+        saturated += int(np.min(r.kept) >= 0.9 * m)
+    assert saturated >= 3          # several steps in the benchmarked regime
+    g64.close()
+    gmx.close()
+
+
+@pytest.mark.parametrize("name,bonds,ell,m,steps", [
+    ("yc4_j1j2_l8_m48", yc4_j1j2_bonds(1.0, 0.5), 8, 48, 12),
+    ("kagome_yc8_l12_m32", kagome_yc8_bonds(1.0), 12, 32, 12),
+])
+def test_cylinder_models_fp64(name, bonds, ell, m, steps):
+    mpo = build_mpo(bonds, ell)
+    ref = ParallelIDMRG.from_mpo(mpo, m=m)
+    ctx = context(mpo, m)
+    for _ in range(steps):
+        _check(ctx, ctx.unit_cell_step(), ref.step(), 1e-10)
+    ctx.close()
