@@ -192,7 +192,7 @@ cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, dou
 // Jacobi groups and shared memory: see kernels_svd.cu
 constexpr size_t SVD_BLOCK_SMEM_MAX = 200 * 1024;
 size_t svd_block_smem(int cols, int csize);
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const size_t *smem,
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
                               double *work, int *iwork, double *sv, int *err, cudaStream_t st,
                               const cudaStream_t *side, const cudaEvent_t *ev);
 struct SelectOut {

@@ -143,7 +143,17 @@ struct idmrg_ctx {
   DevBuf lN, lV, lw, lalpha, lbeta, libeta, lh, lpart, lk, lmember, lactive, lconv, ltheta, ly, lresid, lpsi, lv0, ldot;
   int kmax = 0, nchunk = 0;
   // svd
-  DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk, siw, sorder;
+  DevBuf sjobs, swork, ssv, sjob0, snjob, skpj, sperm, slam, seps, sepsb, skept, scj, slamk, siw, sorder, sorderq;
+  // SVD job plan of the iteration (built once, used by the batched and the
+  // pipelined truncation): sectors, job ranges, per-superblock job order
+  // (largest first) and Jacobi groups
+  std::vector<std::vector<SecInfo>> tsecs;
+  std::vector<int> tjob0, tnjob, tentries, torder, torderq, to0;
+  std::vector<int64_t> tmaxel;
+  std::vector<std::array<int, 4>> tg, tgcols;
+  int tiw = 0, tsv = 0, tentries_max = 1;
+  int64_t tmaxel_all = 0;
+
   int svd_jobs = 0, svd_max_cols = 0, svd_max_rank = 0, svd_max_sweeps = 0;
   double svd_mean_sweeps = 0.0;
 
@@ -1071,19 +1081,26 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
 // ------------------------------------------------------------------------
 // Step 4: sector SVD, cut, compaction
 // ------------------------------------------------------------------------
-idmrg_status truncate(idmrg_ctx *c, int p) {
+// SVD jobs of every superblock of `p`: one job per charge sector Q of the
+// left half, (x s) rows of charge Q against (t y) columns of charge
+// target - Q.  Uploads the jobs, the global and the per-superblock orders
+// (largest first) and sizes every work array; nothing depends on psi.
+idmrg_status trunc_plan(idmrg_ctx *c, int p) {
   const int P = c->P, d = c->d, target = c->o.target_charge;
-  for (int q = 0; q < P; ++q)
-    if (want(p, q) && c->stage[q] != ST_SOLVED)
-      return c->fail(IDMRG_ESTATE, "truncate: superblock %d has not been solved", q);
   c->jobs.clear();
-  std::vector<int> job0(P, 0), njob(P, 0);
-  std::vector<std::vector<SecInfo>> secs(P);
+  c->tsecs.assign(P, {});
+  c->tjob0.assign(P, 0);
+  c->tnjob.assign(P, 0);
+  c->tentries.assign(P, 1);
+  c->tmaxel.assign(P, 0);
+  c->tg.assign(P, {0, 0, 0, 0});
+  c->tgcols.assign(P, {0, 0, 0, 0});
   int64_t work = 0;
-  int sv = 0, max_entries = 1, iw = 0;
-  int64_t max_elems = 0;
+  int sv = 0, iw = 0;
+  c->tentries_max = 1;
+  c->tmaxel_all = 0;
   for (int q = 0; q < P; ++q) {
-    job0[q] = (int)c->jobs.size();
+    c->tjob0[q] = (int)c->jobs.size();
     if (!want(p, q)) continue;
     const Env &L = c->envL[q];
     const Env &R = c->envR[(q + 1) % P];
@@ -1148,166 +1165,253 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
       J.sv_off = sv;
       sv += J.cols_a;
       entries += J.cols_a;
-      max_elems = std::max<int64_t>(max_elems, (int64_t)J.r * J.c);
+      c->tmaxel[q] = std::max<int64_t>(c->tmaxel[q], (int64_t)J.r * J.c);
       si.job = (int)c->jobs.size();
       c->jobs.push_back(J);
-      secs[q].push_back(si);
+      c->tsecs[q].push_back(si);
     }
-    njob[q] = (int)c->jobs.size() - job0[q];
-    max_entries = std::max(max_entries, entries);
+    c->tnjob[q] = (int)c->jobs.size() - c->tjob0[q];
+    c->tentries[q] = std::max(1, entries);
+    c->tentries_max = std::max(c->tentries_max, entries);
+    c->tmaxel_all = std::max(c->tmaxel_all, c->tmaxel[q]);
   }
   const int nj = (int)c->jobs.size();
-  NOMEM(c->ensure(c->siw, 4 * std::max(iw, 1)));
-  NOMEM(c->upload(c->sjobs, c->jobs) && c->ensure(c->swork, 8 * std::max<int64_t>(work, 1)) &&
-        c->ensure(c->ssv, 8 * std::max(sv, 1)) && c->upload(c->sjob0, job0) && c->upload(c->snjob, njob) &&
-        c->ensure(c->skpj, 4 * std::max(nj, 1)) && c->ensure(c->sperm, 4 * std::max(sv, 1)) &&
-        c->ensure(c->slam, 8 * std::max(sv, 1)) && c->ensure(c->seps, 8 * P) && c->ensure(c->sepsb, 8 * P) &&
-        c->ensure(c->skept, 4 * P));
-  double *const *bufs = (double *const *)c->dbufs.p;
-  c->kbegin(IDMRG_K_SVD);
-  CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, max_elems, bufs, BUF_PSI, c->dp(c->swork), c->st));
+  c->tiw = iw;
+  c->tsv = sv;
   // largest sector matrices first: they set the length of the SVD phase
-  std::vector<int> order(nj);
-  for (int j = 0; j < nj; ++j) order[j] = j;
   auto bigger = [&](int a, int b) {
     const SvdJob &x = c->jobs[a], &y = c->jobs[b];
     if (x.cols_a != y.cols_a) return x.cols_a > y.cols_a;
     return x.rows_a > y.rows_a;
   };
-  std::stable_sort(order.begin(), order.end(), bigger);
-  NOMEM(c->upload(c->sorder, order));
+  c->torder.resize(nj);
+  for (int j = 0; j < nj; ++j) c->torder[j] = j;
+  std::stable_sort(c->torder.begin(), c->torder.end(), bigger);
+  c->torderq.clear();
+  c->to0.assign(P, 0);
+  for (int q = 0; q < P; ++q) {
+    c->to0[q] = (int)c->torderq.size();
+    for (int j = 0; j < c->tnjob[q]; ++j) c->torderq.push_back(c->tjob0[q] + j);
+    std::stable_sort(c->torderq.begin() + c->to0[q], c->torderq.end(), bigger);
+  }
+  // Jacobi groups by column count, per superblock: beyond the shared memory
+  // of a 16-CTA cluster in global memory; then block Jacobi on 16, 8, 4 and
+  // 1 CTAs (g[k] ends group k; gcols[k] the largest columns of block group k)
+  for (int q = 0; q < P; ++q) {
+    std::array<int, 4> &g = c->tg[q];
+    std::array<int, 4> &gc = c->tgcols[q];
+    const int *ord = c->torderq.data() + c->to0[q];
+    const int m = c->tnjob[q];
+    for (int j = 0; j < m; ++j) {
+      const int ca = c->jobs[ord[j]].cols_a;
+      if (ca >= 96 && svd_block_smem(ca, 16) > SVD_BLOCK_SMEM_MAX) g[0] = j + 1;
+      if (ca >= 96) g[1] = j + 1;
+      if (ca >= 40) g[2] = j + 1;
+      if (ca >= 12) g[3] = j + 1;
+    }
+    if (g[1] > g[0]) gc[0] = c->jobs[ord[g[0]]].cols_a;
+    if (g[2] > g[1]) gc[1] = c->jobs[ord[g[1]]].cols_a;
+    if (g[3] > g[2]) gc[2] = c->jobs[ord[g[2]]].cols_a;
+    if (m > g[3]) gc[3] = c->jobs[ord[g[3]]].cols_a;
+  }
+  NOMEM(c->ensure(c->siw, 4 * std::max(iw, 1)));
+  NOMEM(c->upload(c->sjobs, c->jobs) && c->ensure(c->swork, 8 * std::max<int64_t>(work, 1)) &&
+        c->ensure(c->ssv, 8 * std::max(sv, 1)) && c->upload(c->sjob0, c->tjob0) && c->upload(c->snjob, c->tnjob) &&
+        c->ensure(c->skpj, 4 * std::max(nj, 1)) && c->ensure(c->sperm, 4 * std::max(sv, 1)) &&
+        c->ensure(c->slam, 8 * std::max(sv, 1)) && c->ensure(c->seps, 8 * P) && c->ensure(c->sepsb, 8 * P) &&
+        c->ensure(c->skept, 4 * P) && c->upload(c->sorder, c->torder) && c->upload(c->sorderq, c->torderq) &&
+        c->ensure(c->slamk, 8 * (size_t)P * std::max(1, c->o.m)));
+  return IDMRG_OK;
+}
+
+// algorithmic flops of the sector SVDs of superblock q (all if q < 0): the
+// R-SVD count 6 r c^2 + 20 c^3 for singular values and both thin factors of
+// an r x c matrix, r >= c
+double svd_flops(const idmrg_ctx *c, int q) {
+  double f = 0.0;
+  for (const SvdJob &j : c->jobs) {
+    if (q >= 0 && j.sb != q) continue;
+    const double r = j.rows_a, cc = j.cols_a;
+    f += 6.0 * r * cc * cc + 20.0 * cc * cc * cc;
+  }
+  return f;
+}
+
+SelectOut select_out(idmrg_ctx *c, int q0) {
+  SelectOut so{};
+  so.kept_per_job = (int *)c->skpj.p;
+  so.perm = (int *)c->sperm.p;
+  so.lam_sorted = c->dp(c->slam);
+  so.eps = c->dp(c->seps) + q0;
+  so.eps_best = c->dp(c->sepsb) + q0;
+  so.kept = (int *)c->skept.p + q0;
+  return so;
+}
+
+// Step 4 for one superblock on stream s: gather, pivoted QR, Jacobi, select.
+idmrg_status trunc_launch_one(idmrg_ctx *c, int q, cudaStream_t s) {
+  const int m = c->tnjob[q];
+  if (m == 0) return IDMRG_OK;
+  double *const *bufs = (double *const *)c->dbufs.p;
+  const SvdJob *jobs = (const SvdJob *)c->sjobs.p;
+  const int *ord = (const int *)c->sorderq.p + c->to0[q];
+  CK(launch_svd_gather_sized(jobs + c->tjob0[q], m, c->tmaxel[q], bufs, BUF_PSI, c->dp(c->swork), s));
+  CK(launch_svd_qrcp(jobs, ord, m, c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, s));
+  if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
+  CK(launch_svd_jacobi(jobs, ord, m, c->tg[q].data(), c->tgcols[q].data(), c->dp(c->swork), (int *)c->siw.p,
+                       c->dp(c->ssv), (int *)c->derr.p, s, c->side, c->sev));
+  CK(launch_svd_select(jobs, (const int *)c->sjob0.p + q, (const int *)c->snjob.p + q, 1, c->dp(c->ssv), c->o.m,
+                       c->o.lambda_zero_rel, c->o.tie_rel, select_out(c, q), c->tentries[q], s));
+  c->launches += 8;
+  return IDMRG_OK;
+}
+
+// New bases of superblock q from the selection (host arrays indexed like the
+// device ones: kpj per job, lam per singular value, iw per job slot, eps and
+// eps_best per superblock); appends q's compaction jobs to cj.
+idmrg_status trunc_host(idmrg_ctx *c, int q, const int *kpj, const double *lam, const int *iwh, const double *eps,
+                        const double *epsb, std::vector<CompactJob> &cj) {
+  const int P = c->P, target = c->o.target_charge;
+  for (int j = c->tjob0[q]; j < c->tjob0[q] + c->tnjob[q]; ++j) {
+    const SvdJob &J = c->jobs[j];
+    const int rk = iwh[J.perm_off + J.cols_a], sw = iwh[J.perm_off + J.cols_a + 1];
+    c->svd_max_cols = std::max(c->svd_max_cols, J.cols_a);
+    c->svd_max_rank = std::max(c->svd_max_rank, rk);
+    c->svd_max_sweeps = std::max(c->svd_max_sweeps, sw);
+    c->svd_mean_sweeps += (double)sw / std::max(c->svd_jobs, 1);
+  }
+  TruncRec &T = c->cur[q];
+  {
+    const DevBuf keepU = T.U, keepV = T.V;  // recycle the device buffers
+    T = TruncRec();
+    T.U = keepU;
+    T.V = keepV;
+  }
+  T.valid = true;
+  T.leftB = c->envL[q].lay.b;
+  T.rightB = c->envR[(q + 1) % P].lay.b;
+  T.eps = eps[q];
+  T.eps_best = epsb[q];
+  int lam_off = 0;
+  int64_t uo = 0, vo = 0;
+  for (SecInfo si : c->tsecs[q]) {
+    si.k = kpj[si.job];
+    if (si.k == 0) continue;
+    si.u_off = uo;
+    si.v_off = vo;
+    si.lam_off = lam_off;
+    uo += (int64_t)si.r * si.k;
+    vo += (int64_t)si.c * si.k;
+    lam_off += si.k;
+    T.bU.add(si.Q, si.k);
+    T.bV.add(target - si.Q, si.k);
+    T.sec.push_back(si);
+  }
+  T.bU.finish();
+  T.bV.finish();
+  T.usize = uo;
+  T.vsize = vo;
+  if (c->tnjob[q] > 0) {
+    const SvdJob &J0 = c->jobs[c->tjob0[q]], &J1 = c->jobs[c->tjob0[q] + c->tnjob[q] - 1];
+    T.lam_all.assign(lam + J0.sv_off, lam + J1.sv_off + J1.cols_a);
+  }
+  NOMEM(c->ensure(T.U, 8 * std::max<int64_t>(uo, 1)) && c->ensure(T.V, 8 * std::max<int64_t>(vo, 1)));
+  c->hbufs[q * NBUF + BUF_U] = (double *)T.U.p;
+  c->hbufs[q * NBUF + BUF_V] = (double *)T.V.p;
+  // kept lambdas go to one device array: per superblock at a fixed stride
+  const int stride = std::max(1, c->o.m);
+  for (const SecInfo &si : T.sec) {
+    CompactJob j{};
+    j.job = si.job;
+    j.u_off = si.u_off;
+    j.v_off = si.v_off;
+    j.lam_off = si.lam_off + q * stride;
+    cj.push_back(j);
+  }
+  return IDMRG_OK;
+}
+
+idmrg_status trunc_compact(idmrg_ctx *c, DevBuf &dcj, const std::vector<CompactJob> &cj, int max_kept,
+                           cudaStream_t s) {
+  if (cj.empty()) return IDMRG_OK;
+  NOMEM(c->ensure(dcj, std::max<size_t>(cj.size() * sizeof(CompactJob), 16)));
+  CK(cudaMemcpyAsync(dcj.p, cj.data(), cj.size() * sizeof(CompactJob), cudaMemcpyHostToDevice, s));
+  c->h2d += cj.size() * sizeof(CompactJob);
+  CK(launch_svd_compact((const SvdJob *)c->sjobs.p, (const CompactJob *)dcj.p, (int)cj.size(), std::max(1, max_kept),
+                        c->dp(c->swork), (const int *)c->siw.p, c->dp(c->ssv), (const int *)c->sperm.p,
+                        (const int *)c->skpj.p, (double *const *)c->dbufs.p, c->dp(c->slamk), s));
+  c->launches += 1;
+  return IDMRG_OK;
+}
+
+void svd_stats_reset(idmrg_ctx *c) {
+  c->svd_jobs = (int)c->jobs.size();
+  c->svd_max_cols = c->svd_max_rank = c->svd_max_sweeps = 0;
+  c->svd_mean_sweeps = 0.0;
+}
+
+idmrg_status truncate(idmrg_ctx *c, int p) {
+  const int P = c->P;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q) && c->stage[q] != ST_SOLVED)
+      return c->fail(IDMRG_ESTATE, "truncate: superblock %d has not been solved", q);
+  idmrg_status s0 = trunc_plan(c, p);
+  if (s0 != IDMRG_OK) return s0;
+  const int nj = (int)c->jobs.size();
+  double *const *bufs = (double *const *)c->dbufs.p;
+  c->kbegin(IDMRG_K_SVD);
+  CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, c->tmaxel_all, bufs, BUF_PSI, c->dp(c->swork), c->st));
   CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, c->dp(c->swork), (int *)c->siw.p,
                      c->o.lambda_zero_rel, c->st));
-  // Jacobi groups by column count: beyond the shared memory of a 16-CTA
-  // cluster in global memory; then block Jacobi on 16, 8, 4 and 1 CTAs
+  // Jacobi groups over all jobs (largest first across superblocks)
   int g[4] = {0, 0, 0, 0};
-  size_t gsm[4] = {0, 0, 0, 0};
   for (int j = 0; j < nj; ++j) {
-    const int ca = c->jobs[order[j]].cols_a;
+    const int ca = c->jobs[c->torder[j]].cols_a;
     if (ca >= 96 && svd_block_smem(ca, 16) > SVD_BLOCK_SMEM_MAX) g[0] = j + 1;
     if (ca >= 96) g[1] = j + 1;
     if (ca >= 40) g[2] = j + 1;
     if (ca >= 12) g[3] = j + 1;
   }
-  const int csz[4] = {16, 8, 4, 1};
-  if (g[1] > g[0]) gsm[0] = svd_block_smem(c->jobs[order[g[0]]].cols_a, csz[0]);
-  if (g[2] > g[1]) gsm[1] = svd_block_smem(c->jobs[order[g[1]]].cols_a, csz[1]);
-  if (g[3] > g[2]) gsm[2] = svd_block_smem(c->jobs[order[g[2]]].cols_a, csz[2]);
-  if (nj > g[3]) gsm[3] = svd_block_smem(c->jobs[order[g[3]]].cols_a, csz[3]);
-  for (int k = 0; k < 4; ++k)
-    if (gsm[k] > SVD_BLOCK_SMEM_MAX) return c->fail(IDMRG_EINVAL, "truncate: sector too large for the Jacobi groups");
+  int gcols[4] = {0, 0, 0, 0};
+  if (g[1] > g[0]) gcols[0] = c->jobs[c->torder[g[0]]].cols_a;
+  if (g[2] > g[1]) gcols[1] = c->jobs[c->torder[g[1]]].cols_a;
+  if (g[3] > g[2]) gcols[2] = c->jobs[c->torder[g[2]]].cols_a;
+  if (nj > g[3]) gcols[3] = c->jobs[c->torder[g[3]]].cols_a;
   if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
-  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, gsm, c->dp(c->swork),
+  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, gcols, c->dp(c->swork),
                        (int *)c->siw.p, c->dp(c->ssv), (int *)c->derr.p, c->st, c->side, c->sev));
-  // select runs on superblocks with jobs only: compact the index arrays
+  // select: one launch, one CTA per superblock (no jobs: nothing kept)
   std::vector<int> sbl;
   for (int q = 0; q < P; ++q)
     if (want(p, q)) sbl.push_back(q);
-  std::vector<int> j0s, njs;
-  for (int q : sbl) { j0s.push_back(job0[q]); njs.push_back(njob[q]); }
-  NOMEM(c->upload(c->sjob0, j0s) && c->upload(c->snjob, njs));
-  SelectOut so{};
-  so.kept_per_job = (int *)c->skpj.p;
-  so.perm = (int *)c->sperm.p;
-  so.lam_sorted = c->dp(c->slam);
-  so.eps = c->dp(c->seps);
-  so.eps_best = c->dp(c->sepsb);
-  so.kept = (int *)c->skept.p;
-  CK(launch_svd_select((const SvdJob *)c->sjobs.p, (const int *)c->sjob0.p, (const int *)c->snjob.p, (int)sbl.size(),
-                       c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, so, max_entries, c->st));
-  // algorithmic flops of the sector SVDs: the R-SVD count 6 r c^2 + 20 c^3
-  // for singular values and both thin factors of an r x c matrix, r >= c
-  double svd_flops = 0.0;
-  for (const SvdJob &j : c->jobs) {
-    const double r = j.rows_a, cc = j.cols_a;
-    svd_flops += 6.0 * r * cc * cc + 20.0 * cc * cc * cc;
-  }
-  c->kend(IDMRG_K_SVD, svd_flops, 0.0);
+  CK(launch_svd_select((const SvdJob *)c->sjobs.p, (const int *)c->sjob0.p, (const int *)c->snjob.p, P,
+                       c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, select_out(c, 0), c->tentries_max,
+                       c->st));
+  c->kend(IDMRG_K_SVD, svd_flops(c, -1), 0.0);
   c->launches += 3;
-  std::vector<int> kpj(nj), iwh(iw);
-  std::vector<double> lam_sorted(sv), eps(sbl.size()), epsb(sbl.size());
-  CK(c->d2h_copy(iwh.data(), c->siw.p, 4 * (size_t)iw));
-  CK(c->d2h_copy(kpj.data(), c->skpj.p, 4 * nj));
-  CK(c->d2h_copy(lam_sorted.data(), c->slam.p, 8 * sv));
-  CK(c->d2h_copy(eps.data(), c->seps.p, 8 * sbl.size()));
-  CK(c->d2h_copy(epsb.data(), c->sepsb.p, 8 * sbl.size()));
+  std::vector<int> kpj(std::max(nj, 1)), iwh(std::max(c->tiw, 1));
+  std::vector<double> lam_sorted(std::max(c->tsv, 1)), eps(P), epsb(P);
+  CK(c->d2h_copy(iwh.data(), c->siw.p, 4 * (size_t)c->tiw));
+  CK(c->d2h_copy(kpj.data(), c->skpj.p, 4 * (size_t)nj));
+  CK(c->d2h_copy(lam_sorted.data(), c->slam.p, 8 * (size_t)c->tsv));
+  CK(c->d2h_copy(eps.data(), c->seps.p, 8 * P));
+  CK(c->d2h_copy(epsb.data(), c->sepsb.p, 8 * P));
   idmrg_status s = check_dev_err(c);
   if (s != IDMRG_OK) return s;
-  c->svd_jobs = nj;
-  c->svd_max_cols = c->svd_max_rank = c->svd_max_sweeps = 0;
-  c->svd_mean_sweeps = 0.0;
-  for (const SvdJob &J : c->jobs) {
-    const int rk = iwh[J.perm_off + J.cols_a], sw = iwh[J.perm_off + J.cols_a + 1];
-    c->svd_max_cols = std::max(c->svd_max_cols, J.cols_a);
-    c->svd_max_rank = std::max(c->svd_max_rank, rk);
-    c->svd_max_sweeps = std::max(c->svd_max_sweeps, sw);
-    c->svd_mean_sweeps += (double)sw / std::max(nj, 1);
-  }
-  // new bases and compaction jobs
+  svd_stats_reset(c);
   std::vector<CompactJob> cj;
-  for (size_t z = 0; z < sbl.size(); ++z) {
-    const int q = sbl[z];
-    TruncRec &T = c->cur[q];
-    {
-      const DevBuf keepU = T.U, keepV = T.V;  // recycle the device buffers
-      T = TruncRec();
-      T.U = keepU;
-      T.V = keepV;
-    }
-    T.valid = true;
-    T.leftB = c->envL[q].lay.b;
-    T.rightB = c->envR[(q + 1) % P].lay.b;
-    T.eps = eps[z];
-    T.eps_best = epsb[z];
-    T.bU.clear();
-    T.bV.clear();
-    int lam_off = 0;
-    int64_t uo = 0, vo = 0;
-    for (SecInfo &si : secs[q]) {
-      si.k = kpj[si.job];
-      if (si.k == 0) continue;
-      si.u_off = uo;
-      si.v_off = vo;
-      si.lam_off = lam_off;
-      uo += (int64_t)si.r * si.k;
-      vo += (int64_t)si.c * si.k;
-      lam_off += si.k;
-      T.bU.add(si.Q, si.k);
-      T.bV.add(target - si.Q, si.k);
-      T.sec.push_back(si);
-    }
-    T.bU.finish();
-    T.bV.finish();
-    T.usize = uo;
-    T.vsize = vo;
-    const int base = c->jobs[job0[q]].sv_off;
-    const int tot = (njob[q] > 0) ? c->jobs[job0[q] + njob[q] - 1].sv_off + c->jobs[job0[q] + njob[q] - 1].cols_a - base : 0;
-    T.lam_all.assign(lam_sorted.begin() + base, lam_sorted.begin() + base + tot);
-    NOMEM(c->ensure(T.U, 8 * std::max<int64_t>(uo, 1)) && c->ensure(T.V, 8 * std::max<int64_t>(vo, 1)));
-    c->hbufs[q * NBUF + BUF_U] = (double *)T.U.p;
-    c->hbufs[q * NBUF + BUF_V] = (double *)T.V.p;
-    for (const SecInfo &si : T.sec) {
-      CompactJob j{};
-      j.job = si.job;
-      j.u_off = si.u_off;
-      j.v_off = si.v_off;
-      j.lam_off = si.lam_off;
-      cj.push_back(j);
-    }
+  for (int q : sbl) {
+    s = trunc_host(c, q, kpj.data(), lam_sorted.data(), iwh.data(), eps.data(), epsb.data(), cj);
+    if (s != IDMRG_OK) return s;
   }
-  // kept lambdas go to one device array: per superblock at a fixed stride
-  const int stride = std::max(1, c->o.m);
-  for (CompactJob &j : cj) j.lam_off += c->jobs[j.job].sb * stride;
   NOMEM(sync_bufs(c) == IDMRG_OK);
-  NOMEM(c->upload(c->scj, cj) && c->ensure(c->slamk, 8 * (size_t)P * stride));
-  c->kbegin(IDMRG_K_SVD);
   int max_kept = 1;
   for (int v : kpj) max_kept = std::max(max_kept, v);
-  CK(launch_svd_compact((const SvdJob *)c->sjobs.p, (const CompactJob *)c->scj.p, (int)cj.size(), max_kept,
-                        c->dp(c->swork), (const int *)c->siw.p, c->dp(c->ssv), (const int *)c->sperm.p,
-                        (const int *)c->skpj.p, bufs, c->dp(c->slamk), c->st));
+  c->kbegin(IDMRG_K_SVD);
+  s = trunc_compact(c, c->scj, cj, max_kept, c->st);
+  if (s != IDMRG_OK) return s;
   c->kend(IDMRG_K_SVD);
-  c->launches += 1;
+  const int stride = std::max(1, c->o.m);
   std::vector<double> lamk((size_t)P * stride);
   CK(c->d2h_copy(lamk.data(), c->slamk.p, 8 * lamk.size()));
   CK(cudaStreamSynchronize(c->st));
@@ -1322,8 +1426,153 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
 // ------------------------------------------------------------------------
 // Step 6: block-spin transformation (Eqs. L, R)
 // ------------------------------------------------------------------------
-idmrg_status update_envs(idmrg_ctx *c, int p) {
+// Step 6 task lists of pair q: X = env . U (V), Y = W . X, new env = U^T Y
+// (V Y); appends to g1, w, g3 and sizes the pair's new environments and
+// scratch (pointer table entries LNEW, RNEW, X, Y of q).
+idmrg_status env_build(idmrg_ctx *c, int q, GemmList &g1, GemmList &g3, WList &w) {
   const int P = c->P, d = c->d, target = c->o.target_charge;
+  const SBPlan &S = c->plan[q];
+  const Env &L = c->envL[q];
+  const Env &R = c->envR[(q + 1) % P];
+  const Basis &BL = L.lay.b, &BR = R.lay.b;
+  const TruncRec &T = c->cur[q];
+  const int SL = BL.S(), SR = BR.S();
+  const int wa = L.lay.w, wb = c->adim[S.c1 + 1], wc = R.lay.w;
+  std::map<int, int> secQ;
+  for (int k = 0; k < (int)T.sec.size(); ++k) secQ[T.sec[k].Q] = k;
+  auto sec_of = [&](int Q) { auto it = secQ.find(Q); return it == secQ.end() ? -1 : it->second; };
+  int64_t xs = 0, ys = 0;
+  // ---------------- left: X[a](so, s') = L_a(so,si) U[(si,s')]
+  std::vector<int64_t> xl((size_t)wa * SL * d, -1), yl((size_t)wb * SL * d, -1);
+  for (int a = 0; a < wa; ++a)
+    for (int si = 0; si < SL; ++si) {
+      const int so = L.lay.so[a * SL + si];
+      if (so < 0) continue;
+      for (int s2 = 0; s2 < d; ++s2) {
+        const int k = sec_of(BL.q[si] + c->qp[s2]);
+        if (k < 0) continue;
+        const SecInfo &sc = T.sec[k];
+        int rs = -1;
+        for (const auto &g : sc.rg)
+          if (g[0] == si && g[1] == s2) rs = g[2];
+        if (rs < 0) continue;
+        xl[((size_t)a * SL + so) * d + s2] = xs;
+        g1.task(q, BUF_X, xs, BL.dim[so], sc.k, sc.k);
+        g1.seg(BUF_L, L.lay.off[a * SL + si], BL.dim[si], BUF_U, sc.u_off + (int64_t)rs * sc.k, sc.k,
+                     BL.dim[si], 0);
+        xs += (int64_t)BL.dim[so] * sc.k;
+      }
+    }
+  // Y[b](so, s) = sum_{a,s'} W_c1(a,b,s,s') X[a](so,s')
+  std::vector<int> bchq(c->bq[(S.c1 + 1) % c->ell]);
+  for (int b = 0; b < wb; ++b)
+    for (int so = 0; so < SL; ++so)
+      for (int s = 0; s < d; ++s) {
+        const int ko = sec_of(BL.q[so] + c->qp[s]);
+        const int ki = sec_of(BL.q[so] + c->qp[s] - bchq[b]);
+        if (ko < 0 || ki < 0) continue;
+        const int kin = T.sec[ki].k;
+        yl[((size_t)b * SL + so) * d + s] = ys;
+        w.task(q, BUF_Y, ys, kin, BUF_X, BL.dim[so], kin);
+        for (int a = 0; a < wa; ++a)
+          for (int s2 = 0; s2 < d; ++s2) {
+            const double cf = c->Wat(S.c1, a, b, s, s2);
+            if (cf == 0.0) continue;
+            const int64_t xo = xl[((size_t)a * SL + so) * d + s2];
+            if (xo < 0) continue;
+            w.term(xo, kin, cf);
+          }
+        ys += (int64_t)BL.dim[so] * kin;
+      }
+  // L'[b](Qo, Qi) = sum_{(so,s) in Qo} U[(so,s)]^T Y[b](so,s)
+  Env &NL = c->newL[q];
+  NL.lay.build(T.bU, bchq);
+  NOMEM(c->ensure(NL.data, 8 * std::max<int64_t>(NL.lay.size, 1)));
+  c->hbufs[q * NBUF + BUF_LNEW] = c->dp(NL.data);
+  const int SU = T.bU.S();
+  for (int b = 0; b < wb; ++b)
+    for (int si = 0; si < SU; ++si) {
+      const int so = NL.lay.so[b * SU + si];
+      if (so < 0) continue;
+      const SecInfo &o = T.sec[so];
+      const int kin = T.sec[si].k;
+      g3.task(q, BUF_LNEW, NL.lay.off[b * SU + si], o.k, kin, kin);
+      for (const auto &g : o.rg) {
+        const int64_t y = yl[((size_t)b * SL + g[0]) * d + g[1]];
+        if (y < 0) continue;
+        g3.seg(BUF_U, o.u_off + (int64_t)g[2] * o.k, o.k, BUF_Y, y, kin, BL.dim[g[0]], 1);
+      }
+    }
+  // ---------------- right: X[c](jo, t') = R_c(jo,ji) V[(t',ji)]
+  std::vector<int64_t> xr((size_t)wc * SR * d, -1), yr((size_t)wb * SR * d, -1);
+  for (int cc = 0; cc < wc; ++cc)
+    for (int ji = 0; ji < SR; ++ji) {
+      const int jo = R.lay.so[cc * SR + ji];
+      if (jo < 0) continue;
+      for (int t2 = 0; t2 < d; ++t2) {
+        const int k = sec_of(target - (c->qp[t2] + BR.q[ji]));
+        if (k < 0) continue;
+        const SecInfo &sc = T.sec[k];
+        int cs = -1;
+        for (const auto &g : sc.cg)
+          if (g[0] == t2 && g[1] == ji) cs = g[2];
+        if (cs < 0) continue;
+        xr[((size_t)cc * SR + jo) * d + t2] = xs;
+        g1.task(q, BUF_X, xs, BR.dim[jo], sc.k, sc.k);
+        g1.seg(BUF_R, R.lay.off[cc * SR + ji], BR.dim[ji], BUF_V, sc.v_off + (int64_t)cs * sc.k, sc.k,
+                     BR.dim[ji], 0);
+        xs += (int64_t)BR.dim[jo] * sc.k;
+      }
+    }
+  // Y[b](jo, t) = sum_{c,t'} W_c2(b,c,t,t') X[c](jo,t')
+  std::vector<int> rchq(wb);
+  for (int b = 0; b < wb; ++b) rchq[b] = -c->bq[S.c2][b];
+  for (int b = 0; b < wb; ++b)
+    for (int jo = 0; jo < SR; ++jo)
+      for (int t = 0; t < d; ++t) {
+        const int qo = c->qp[t] + BR.q[jo];           // right charge of row (t, jo)
+        const int ko = sec_of(target - qo);
+        const int ki = sec_of(target - (qo - rchq[b]));
+        if (ko < 0 || ki < 0) continue;
+        const int kin = T.sec[ki].k;
+        yr[((size_t)b * SR + jo) * d + t] = ys;
+        w.task(q, BUF_Y, ys, kin, BUF_X, BR.dim[jo], kin);
+        for (int cc = 0; cc < wc; ++cc)
+          for (int t2 = 0; t2 < d; ++t2) {
+            const double cf = c->Wat(S.c2, b, cc, t, t2);
+            if (cf == 0.0) continue;
+            const int64_t xo = xr[((size_t)cc * SR + jo) * d + t2];
+            if (xo < 0) continue;
+            w.term(xo, kin, cf);
+          }
+        ys += (int64_t)BR.dim[jo] * kin;
+      }
+  Env &NR = c->newR[q];
+  NR.lay.build(T.bV, rchq);
+  NOMEM(c->ensure(NR.data, 8 * std::max<int64_t>(NR.lay.size, 1)));
+  c->hbufs[q * NBUF + BUF_RNEW] = c->dp(NR.data);
+  const int SV = T.bV.S();
+  for (int b = 0; b < wb; ++b)
+    for (int si = 0; si < SV; ++si) {
+      const int so = NR.lay.so[b * SV + si];
+      if (so < 0) continue;
+      const SecInfo &o = T.sec[so];
+      const int kin = T.sec[si].k;
+      g3.task(q, BUF_RNEW, NR.lay.off[b * SV + si], o.k, kin, kin);
+      for (const auto &g : o.cg) {
+        const int64_t y = yr[((size_t)b * SR + g[1]) * d + g[0]];
+        if (y < 0) continue;
+        g3.seg(BUF_V, o.v_off + (int64_t)g[2] * o.k, o.k, BUF_Y, y, kin, BR.dim[g[1]], 1);
+      }
+    }
+  NOMEM(c->ensure(c->bX[q], 8 * std::max<int64_t>(xs, 1)) && c->ensure(c->bY[q], 8 * std::max<int64_t>(ys, 1)));
+  c->hbufs[q * NBUF + BUF_X] = c->dp(c->bX[q]);
+  c->hbufs[q * NBUF + BUF_Y] = c->dp(c->bY[q]);
+  return IDMRG_OK;
+}
+
+idmrg_status update_envs(idmrg_ctx *c, int p) {
+  const int P = c->P;
   for (int q = 0; q < P; ++q)
     if (want(p, q) && c->stage[q] != ST_TRUNCATED)
       return c->fail(IDMRG_ESTATE, "update_environments: superblock %d is not truncated", q);
@@ -1332,143 +1581,8 @@ idmrg_status update_envs(idmrg_ctx *c, int p) {
   c->wenv.clear();
   for (int q = 0; q < P; ++q) {
     if (!want(p, q)) continue;
-    const SBPlan &S = c->plan[q];
-    const Env &L = c->envL[q];
-    const Env &R = c->envR[(q + 1) % P];
-    const Basis &BL = L.lay.b, &BR = R.lay.b;
-    const TruncRec &T = c->cur[q];
-    const int SL = BL.S(), SR = BR.S();
-    const int wa = L.lay.w, wb = c->adim[S.c1 + 1], wc = R.lay.w;
-    std::map<int, int> secQ;
-    for (int k = 0; k < (int)T.sec.size(); ++k) secQ[T.sec[k].Q] = k;
-    auto sec_of = [&](int Q) { auto it = secQ.find(Q); return it == secQ.end() ? -1 : it->second; };
-    int64_t xs = 0, ys = 0;
-    // ---------------- left: X[a](so, s') = L_a(so,si) U[(si,s')]
-    std::vector<int64_t> xl((size_t)wa * SL * d, -1), yl((size_t)wb * SL * d, -1);
-    for (int a = 0; a < wa; ++a)
-      for (int si = 0; si < SL; ++si) {
-        const int so = L.lay.so[a * SL + si];
-        if (so < 0) continue;
-        for (int s2 = 0; s2 < d; ++s2) {
-          const int k = sec_of(BL.q[si] + c->qp[s2]);
-          if (k < 0) continue;
-          const SecInfo &sc = T.sec[k];
-          int rs = -1;
-          for (const auto &g : sc.rg)
-            if (g[0] == si && g[1] == s2) rs = g[2];
-          if (rs < 0) continue;
-          xl[((size_t)a * SL + so) * d + s2] = xs;
-          c->genv1.task(q, BUF_X, xs, BL.dim[so], sc.k, sc.k);
-          c->genv1.seg(BUF_L, L.lay.off[a * SL + si], BL.dim[si], BUF_U, sc.u_off + (int64_t)rs * sc.k, sc.k,
-                       BL.dim[si], 0);
-          xs += (int64_t)BL.dim[so] * sc.k;
-        }
-      }
-    // Y[b](so, s) = sum_{a,s'} W_c1(a,b,s,s') X[a](so,s')
-    std::vector<int> bchq(c->bq[(S.c1 + 1) % c->ell]);
-    for (int b = 0; b < wb; ++b)
-      for (int so = 0; so < SL; ++so)
-        for (int s = 0; s < d; ++s) {
-          const int ko = sec_of(BL.q[so] + c->qp[s]);
-          const int ki = sec_of(BL.q[so] + c->qp[s] - bchq[b]);
-          if (ko < 0 || ki < 0) continue;
-          const int kin = T.sec[ki].k;
-          yl[((size_t)b * SL + so) * d + s] = ys;
-          c->wenv.task(q, BUF_Y, ys, kin, BUF_X, BL.dim[so], kin);
-          for (int a = 0; a < wa; ++a)
-            for (int s2 = 0; s2 < d; ++s2) {
-              const double cf = c->Wat(S.c1, a, b, s, s2);
-              if (cf == 0.0) continue;
-              const int64_t xo = xl[((size_t)a * SL + so) * d + s2];
-              if (xo < 0) continue;
-              c->wenv.term(xo, kin, cf);
-            }
-          ys += (int64_t)BL.dim[so] * kin;
-        }
-    // L'[b](Qo, Qi) = sum_{(so,s) in Qo} U[(so,s)]^T Y[b](so,s)
-    Env &NL = c->newL[q];
-    NL.lay.build(T.bU, bchq);
-    NOMEM(c->ensure(NL.data, 8 * std::max<int64_t>(NL.lay.size, 1)));
-    c->hbufs[q * NBUF + BUF_LNEW] = c->dp(NL.data);
-    const int SU = T.bU.S();
-    for (int b = 0; b < wb; ++b)
-      for (int si = 0; si < SU; ++si) {
-        const int so = NL.lay.so[b * SU + si];
-        if (so < 0) continue;
-        const SecInfo &o = T.sec[so];
-        const int kin = T.sec[si].k;
-        c->genv3.task(q, BUF_LNEW, NL.lay.off[b * SU + si], o.k, kin, kin);
-        for (const auto &g : o.rg) {
-          const int64_t y = yl[((size_t)b * SL + g[0]) * d + g[1]];
-          if (y < 0) continue;
-          c->genv3.seg(BUF_U, o.u_off + (int64_t)g[2] * o.k, o.k, BUF_Y, y, kin, BL.dim[g[0]], 1);
-        }
-      }
-    // ---------------- right: X[c](jo, t') = R_c(jo,ji) V[(t',ji)]
-    std::vector<int64_t> xr((size_t)wc * SR * d, -1), yr((size_t)wb * SR * d, -1);
-    for (int cc = 0; cc < wc; ++cc)
-      for (int ji = 0; ji < SR; ++ji) {
-        const int jo = R.lay.so[cc * SR + ji];
-        if (jo < 0) continue;
-        for (int t2 = 0; t2 < d; ++t2) {
-          const int k = sec_of(target - (c->qp[t2] + BR.q[ji]));
-          if (k < 0) continue;
-          const SecInfo &sc = T.sec[k];
-          int cs = -1;
-          for (const auto &g : sc.cg)
-            if (g[0] == t2 && g[1] == ji) cs = g[2];
-          if (cs < 0) continue;
-          xr[((size_t)cc * SR + jo) * d + t2] = xs;
-          c->genv1.task(q, BUF_X, xs, BR.dim[jo], sc.k, sc.k);
-          c->genv1.seg(BUF_R, R.lay.off[cc * SR + ji], BR.dim[ji], BUF_V, sc.v_off + (int64_t)cs * sc.k, sc.k,
-                       BR.dim[ji], 0);
-          xs += (int64_t)BR.dim[jo] * sc.k;
-        }
-      }
-    // Y[b](jo, t) = sum_{c,t'} W_c2(b,c,t,t') X[c](jo,t')
-    std::vector<int> rchq(wb);
-    for (int b = 0; b < wb; ++b) rchq[b] = -c->bq[S.c2][b];
-    for (int b = 0; b < wb; ++b)
-      for (int jo = 0; jo < SR; ++jo)
-        for (int t = 0; t < d; ++t) {
-          const int qo = c->qp[t] + BR.q[jo];           // right charge of row (t, jo)
-          const int ko = sec_of(target - qo);
-          const int ki = sec_of(target - (qo - rchq[b]));
-          if (ko < 0 || ki < 0) continue;
-          const int kin = T.sec[ki].k;
-          yr[((size_t)b * SR + jo) * d + t] = ys;
-          c->wenv.task(q, BUF_Y, ys, kin, BUF_X, BR.dim[jo], kin);
-          for (int cc = 0; cc < wc; ++cc)
-            for (int t2 = 0; t2 < d; ++t2) {
-              const double cf = c->Wat(S.c2, b, cc, t, t2);
-              if (cf == 0.0) continue;
-              const int64_t xo = xr[((size_t)cc * SR + jo) * d + t2];
-              if (xo < 0) continue;
-              c->wenv.term(xo, kin, cf);
-            }
-          ys += (int64_t)BR.dim[jo] * kin;
-        }
-    Env &NR = c->newR[q];
-    NR.lay.build(T.bV, rchq);
-    NOMEM(c->ensure(NR.data, 8 * std::max<int64_t>(NR.lay.size, 1)));
-    c->hbufs[q * NBUF + BUF_RNEW] = c->dp(NR.data);
-    const int SV = T.bV.S();
-    for (int b = 0; b < wb; ++b)
-      for (int si = 0; si < SV; ++si) {
-        const int so = NR.lay.so[b * SV + si];
-        if (so < 0) continue;
-        const SecInfo &o = T.sec[so];
-        const int kin = T.sec[si].k;
-        c->genv3.task(q, BUF_RNEW, NR.lay.off[b * SV + si], o.k, kin, kin);
-        for (const auto &g : o.cg) {
-          const int64_t y = yr[((size_t)b * SR + g[1]) * d + g[0]];
-          if (y < 0) continue;
-          c->genv3.seg(BUF_V, o.v_off + (int64_t)g[2] * o.k, o.k, BUF_Y, y, kin, BR.dim[g[1]], 1);
-        }
-      }
-    NOMEM(c->ensure(c->bX[q], 8 * std::max<int64_t>(xs, 1)) && c->ensure(c->bY[q], 8 * std::max<int64_t>(ys, 1)));
-    c->hbufs[q * NBUF + BUF_X] = c->dp(c->bX[q]);
-    c->hbufs[q * NBUF + BUF_Y] = c->dp(c->bY[q]);
+    idmrg_status s = env_build(c, q, c->genv1, c->genv3, c->wenv);
+    if (s != IDMRG_OK) return s;
   }
   c->genv1.finish(64, 64);
   c->genv3.finish(64, 64);
@@ -1685,7 +1799,7 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->libeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
-                    &c->scj, &c->slamk, &c->siw, &c->sorder, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
+                    &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
                     &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);

@@ -408,20 +408,11 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
 // data when cancellation makes the update inaccurate, and at every sweep,
 // when d is folded back into the columns), so each pair needs one dot
 // product instead of three.
-constexpr int BJ_THREADS = 256;
+constexpr int BJ_THREADS = 256;  // largest block; groups launch one warp per pair of a sub-round
 constexpr int BJ_REG = 10;  // rows per lane held in registers: columns of up to 320 rows
 
 __device__ __forceinline__ int bj_block_at(int pos, int r, int P) {
   return pos == 0 ? 0 : 1 + (pos - 1 + (P - 1) - r % (P - 1)) % (P - 1);
-}
-
-// 1/x for x > 0 in the range of FP32 normals: FP32 estimate and two Newton
-// steps e <- e (2 - x e) in FP64 (the error squares at each step)
-__device__ __forceinline__ double recip_nr(double x) {
-  double e = (double)__frcp_rn((float)x);
-  e = e * fma(-x, e, 2.0);
-  e = e * fma(-x, e, 2.0);
-  return e;
 }
 
 // The pairs of a sub-round are rotated in three phases (separated by
@@ -439,39 +430,98 @@ struct BjPair {   // per pair of a sub-round, in shared memory
   int rot;        // 1 rotate, 2 rotate and recompute both norms from the data
 };
 
-// phase 2 for one pair: norms a, b and scales d1, d2 in, updated in place
-__device__ __forceinline__ int bj_rotation(double graw, double &a, double &b, double &d1, double &d2, double tol2,
-                                           double abs_floor, double &cp, double &cq) {
-  const double g = d1 * d2 * graw;
-  if (!(g * g > tol2 * (a * b)) || !(fabs(g) > abs_floor)) return 0;
-  // angle in FP32 from z = (b - a) / (2 g), both scaled by a power of two
-  // that brings 2g to [1, 2): the exponent is read from the bits of g
-  const double num = b - a, den = 2.0 * g;
-  const int ex = ((__double2hiint(den) >> 20) & 0x7ff) - 1023;
-  const double sc = __hiloint2double((1023 - ex) << 20, 0);
-  const float z = __fdividef((float)(num * sc), (float)(den * sc));
-  const float az = fabsf(z);
-  if (!(az < 1e30f)) return 0;  // rotation below FP32 resolution: nothing to do
-  const float tf = az > 1e15f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + __fsqrt_rn(fmaf(z, z, 1.0f))), z);
-  const double t = (double)tf;
-  // cos = 1/sqrt(1 + t^2) to FP64 precision: FP32 estimate, two Newton steps
-  const double xx = fma(t, t, 1.0);
-  double cs = (double)rsqrtf((float)xx);
-  cs = cs * fma(-0.5 * xx * cs, cs, 1.5);
-  cs = cs * fma(-0.5 * xx * cs, cs, 1.5);
+// Exponent and FP32 mantissa of a double, by integer operations only (an
+// FP64 instruction costs 64 cycles of its sub-partition's FP64 unit here):
+// x = m 2^e with |m| in [1, 2) (mantissa truncated to 23 bits); zero and
+// subnormals give m = 0.
+struct Split {
+  float m;
+  int e;
+};
+__device__ __forceinline__ Split split_f64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int be = (int)((hi >> 20) & 0x7ffu);
+  Split r;
+  if (be == 0) {
+    r.m = 0.0f;
+    r.e = 0;
+    return r;
+  }
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  r.m = __uint_as_float((hi & 0x80000000u) | (127u << 23) | mant);
+  r.e = be - 1023;
+  return r;
+}
+
+// the double of an FP32 number times 2^k (integer operations; f normal or
+// zero, result in the normal range)
+__device__ __forceinline__ double f64_of(float f, int k = 0) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0) return 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((ex + 896u + (unsigned)k) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 0x7u) << 29));
+}
+
+// 1/x for x > 0 in the normal range: FP32 estimate of the mantissa's
+// reciprocal, then two Newton steps e <- e (2 - x e) in FP64
+__device__ __forceinline__ double recip_split(double x) {
+  const Split s = split_f64(x);
+  double e = f64_of(__frcp_rn(s.m), -s.e);
+  e = e * fma(-x, e, 2.0);
+  e = e * fma(-x, e, 2.0);
+  return e;
+}
+
+// phase 2 for one pair: norms a, b and scales d1, d2 in, updated in place.
+// The tests and the angle use exponents and FP32 mantissas; FP64 is spent
+// only where the rotation must be exact: cos (Newton), the update
+// coefficients and the carried norms.
+__device__ __forceinline__ int bj_rotation(double graw, double &a, double &b, double &d1, double &d2, float log2_tol2,
+                                           Split fl, double &cp, double &cq) {
+  const double g = (d1 * d2) * graw;
+  const Split sg = split_f64(g), sa = split_f64(a), sb = split_f64(b);
+  if (sg.m == 0.0f || sa.m == 0.0f || sb.m == 0.0f) return 0;
+  const float mg = fabsf(sg.m);
+  // rotate iff g^2 > tol^2 a b and |g| > abs_floor
+  const float lrel = (float)(2 * sg.e - sa.e - sb.e) + __log2f(mg * mg / (sa.m * sb.m));
+  if (!(lrel > log2_tol2)) return 0;
+  if (fl.m != 0.0f && !((float)(sg.e - fl.e) + __log2f(mg / fl.m) > 0.0f)) return 0;
+  // z = (b - a) / (2 g) in FP32 from exponents and mantissas
+  const Split sn = split_f64(b - a);
+  float tf;
+  if (sn.m == 0.0f) {
+    tf = copysignf(1.0f, sg.m);
+  } else {
+    const int ez = sn.e - sg.e - 1;
+    if (ez > 120) return 0;  // angle below 2^-120: nothing to rotate
+    const float mz = __fdividef(sn.m, sg.m);
+    const float z = ez < -120 ? copysignf(0.0f, mz) : ldexpf(mz, ez);
+    const float az = fabsf(z);
+    tf = az > 1e15f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + __fsqrt_rn(fmaf(z, z, 1.0f))), z);
+    if (!(fabsf(tf) >= 1.17549435e-38f)) return 0;  // below FP32 normals: no rotation
+  }
+  const double t = f64_of(tf);
+  // cos = 1/sqrt(1 + t^2): FP32 estimate, two Newton steps in FP64
+  const double xx = fma(t, t, 1.0), h = 0.5 * xx;
+  double cs = f64_of(rsqrtf(fmaf(tf, tf, 1.0f)));
+  cs = cs * fma(-h * cs, cs, 1.5);
+  cs = cs * fma(-h * cs, cs, 1.5);
   // x_p <- x_p - t (d_q/d_p) x_q,  x_q <- x_q + t (d_p/d_q) x_p,  d <- cos d
-  cp = -t * (d2 * recip_nr(d1));
-  cq = t * (d1 * recip_nr(d2));
+  cp = -t * (d2 * recip_split(d1));
+  cq = t * (d1 * recip_split(d2));
   // new squared norms cos^2 (a -+ 2 t g + t^2 b); recomputed from the data
-  // when the subtraction has cancelled most of the value
-  const double c2 = cs * cs, tg = 2.0 * t * g, t2 = t * t;
-  const double a2 = c2 * (fma(t2, b, a) - tg), b2 = c2 * (fma(t2, a, b) + tg);
-  const double small = fmax(a, b) * 1e-6;
+  // when they fall below 2^-20 of the larger input (cancellation)
+  const double c2 = cs * cs, t2 = t * t, tg = t * g;
+  const double a2 = c2 * fma(-2.0, tg, fma(t2, b, a)), b2 = c2 * fma(2.0, tg, fma(t2, a, b));
   d1 *= cs;
   d2 *= cs;
   a = a2;
   b = b2;
-  return (a2 > small && b2 > small) ? 1 : 2;
+  const int emax = max(sa.e, sb.e) - 20;
+  const Split s2a = split_f64(a2), s2b = split_f64(b2);
+  const bool oka = s2a.m > 0.0f && s2a.e > emax, okb = s2b.m > 0.0f && s2b.e > emax;
+  return (oka && okb) ? 1 : 2;
 }
 
 __global__ void __launch_bounds__(BJ_THREADS, 2)
@@ -537,9 +587,10 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
   fro = 0.0;
   for (int q = 0; q < C; ++q) fro += fp0[q];
   cluster.sync();
-  const double tol = sqrt((double)nr) * DBL_EPSILON;
-  const double tol2 = tol * tol;
-  const double abs_floor = 4.0 * DBL_EPSILON * DBL_EPSILON * fro;
+  // rotation threshold sqrt(rows) eps, as a log2 of its square, and the
+  // absolute floor 4 eps^2 ||B||_F^2 (see jacobi_kernel)
+  const float log2_tol2 = __log2f((float)nr) - 104.0f;  // log2(nr eps^2), eps = 2^-52
+  const Split floor_split = split_f64(4.0 * DBL_EPSILON * DBL_EPSILON * fro);
   int *flag0 = cluster.map_shared_rank(&flag, 0);
   bool converged = (n < 2);
   int sweep = 0, cur = 0;
@@ -590,7 +641,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
       BjPair &pr = pairs[lane];
       double a = s0[offN + pr.i], b = s1[offN + pr.j], d1 = s0[offD + pr.i], d2 = s1[offD + pr.j];
       double cp = 0.0, cq = 0.0;
-      pr.rot = bj_rotation(pr.g, a, b, d1, d2, tol2, abs_floor, cp, cq);
+      pr.rot = bj_rotation(pr.g, a, b, d1, d2, log2_tol2, floor_split, cp, cq);
       if (pr.rot) {
         pr.cp = cp;
         pr.cq = cq;
@@ -762,6 +813,14 @@ __global__ void select_kernel(const SvdJob *__restrict__ jobs, const int *__rest
   int *cnt = (int *)(E + P);
   const int s = blockIdx.x;
   const int j0 = sb_job0[s], nj = sb_njob[s];
+  if (nj == 0) {  // superblock not being truncated: no job to read
+    if (threadIdx.x == 0) {
+      out.eps[s] = 0.0;
+      out.eps_best[s] = 0.0;
+      out.kept[s] = 0;
+    }
+    return;
+  }
   const int base = jobs[j0].sv_off;
   int total = 0;
   for (int q = 0; q < nj; ++q) total += jobs[j0 + q].cols_a;
@@ -904,11 +963,27 @@ static cudaError_t launch_jacobi_clusters(const SvdJob *jobs, const int *order, 
   return cudaLaunchKernelEx(&cfg, jacobi_kernel, jobs, order, work, iwork, sv, err);
 }
 
-static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, size_t smem,
+// shared memory of the block kernel for a job of `cols` columns in clusters
+// of `csize` (the rank is at most cols): four blocks of B and Jm columns
+size_t svd_block_smem(int cols, int csize) {
+  const int64_t bw = (cols + 2 * csize - 1) / (2 * csize);
+  const int64_t pad = 32 * (((int64_t)cols + 31) / 32);
+  if (pad > 32 * BJ_REG) return (size_t)-1;  // beyond the registers of the block kernel
+  return (size_t)(4 * (bw * (2 * pad + 2) + 1) * sizeof(double));
+}
+
+// block kernel for jobs of at most `cols` columns on clusters of `csize`
+static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, int cols,
                                          double *work, int *iwork, double *sv, int *err, cudaStream_t st) {
+  // one warp per pair of a sub-round (at least two, at most BJ_THREADS / 32):
+  // small blocks let three or four CTAs of different clusters share an SM
+  const int bw = (cols + 2 * csize - 1) / (2 * csize);
+  const int warps = std::min(BJ_THREADS / 32, std::max(2, bw));
+  const size_t smem = svd_block_smem(cols, csize);
+  if (smem > SVD_BLOCK_SMEM_MAX) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * csize, 1, 1);
-  cfg.blockDim = dim3(BJ_THREADS, 1, 1);
+  cfg.blockDim = dim3(32 * warps, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -921,23 +996,14 @@ static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, i
   return cudaLaunchKernelEx(&cfg, jacobi_block_kernel, jobs, order, work, iwork, sv, err);
 }
 
-// shared memory of the block kernel for a job of `cols` columns in clusters
-// of `csize` (the rank is at most cols): four blocks of B and Jm columns
-size_t svd_block_smem(int cols, int csize) {
-  const int64_t bw = (cols + 2 * csize - 1) / (2 * csize);
-  const int64_t pad = 32 * (((int64_t)cols + 31) / 32);
-  if (pad > 32 * BJ_REG) return (size_t)-1;  // beyond the registers of the block kernel
-  return (size_t)(4 * (bw * (2 * pad + 2) + 1) * sizeof(double));
-}
-
 // `order` lists the jobs by column count, largest first, in five groups
 // [g[k-1], g[k]) (g[-1] = 0, g[4] = njobs): 0 Jacobi in global memory on
 // 16-CTA clusters (columns beyond the shared memory of the block kernel),
-// 1..4 block Jacobi on clusters of 16, 8, 4 and 1 CTAs with smem[k-1] bytes
-// of shared memory.  Groups 0 and 1 run on `st`, the others on the side
+// 1..4 block Jacobi on clusters of 16, 8, 4 and 1 CTAs; cols[k-1] is the
+// largest column count of block group k.  Groups 0 and 1 run on `st`, the others on the side
 // streams side[0..2], forked from and joined back to `st` by the events
 // ev[0..3].
-cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const size_t *smem,
+cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
                               double *work, int *iwork, double *sv, int *err, cudaStream_t st,
                               const cudaStream_t *side, const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
@@ -955,7 +1021,7 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     if (hi[k] <= lo[k]) continue;
     e = cudaStreamWaitEvent(side[k - 2], ev[0], 0);
     if (e != cudaSuccess) return e;
-    e = launch_block_clusters(jobs, order + lo[k], hi[k] - lo[k], csz[k], smem[k - 1], work, iwork, sv, err,
+    e = launch_block_clusters(jobs, order + lo[k], hi[k] - lo[k], csz[k], cols[k - 1], work, iwork, sv, err,
                               side[k - 2]);
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(ev[k - 1], side[k - 2]);
@@ -970,7 +1036,7 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     if (e != cudaSuccess) return e;
   }
   if (hi[1] > lo[1]) {
-    e = launch_block_clusters(jobs, order + lo[1], hi[1] - lo[1], 16, smem[0], work, iwork, sv, err, st);
+    e = launch_block_clusters(jobs, order + lo[1], hi[1] - lo[1], 16, cols[0], work, iwork, sv, err, st);
     if (e != cudaSuccess) {
       // 16-CTA clusters not available: the global-memory kernel on 8
       cudaGetLastError();
