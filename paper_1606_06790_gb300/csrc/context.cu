@@ -1001,7 +1001,8 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
       if (s != IDMRG_OK) return s;
       double vb = 0.0;
       for (int q = 0; q < P; ++q)
-        if (it == 0 ? member[q] : act[q]) vb += 8.0 * (double)N[q] * (2.0 * (it + 2) + 2.0 * (it + 3) + 2.0);
+        // three-term step 6 N, full pass (k + 2) N + (k + 3) N, k = it
+        if (it == 0 ? member[q] : act[q]) vb += 8.0 * (double)N[q] * (2.0 * it + 11.0);
       c->kbegin(IDMRG_K_LANCZOS_VEC);
       CK(lanczos_project(L, 0, c->st));
       CK(lanczos_subtract(L, 0, c->st));

@@ -32,45 +32,48 @@ __global__ void set_ptrs_kernel(LanczosDev L, double **bufs) {
   bufs[s * NBUF + BUF_OUT] = L.w[s];
 }
 
+// Re-orthogonalisation in two passes: pass 0 is the three-term step, the
+// projection on v_k only (alpha) and w -= alpha v_k + beta_{k-1} v_{k-1};
+// pass 1 projects the result on every Krylov vector and subtracts it once.
+// After the three-term step the components of w along the older vectors are
+// small, so one classical Gram-Schmidt pass leaves w orthogonal to working
+// precision (no cancellation for a second pass to repair).  FP64 work per
+// iteration: (2k + 4) N fused multiply-adds instead of 4 k N.
+
 // part[((pass*S + s)*kmax + j)*nchunk + chunk] = sum_{e in chunk} V_j[e] w[e]
+// for j in [jmin, k]: the chunk of w sits in shared memory and each warp
+// takes whole vectors, so every lane issues one FMA per element and one warp
+// reduction per vector and chunk.
+constexpr int PCH = 1024;  // elements per projection chunk (32 per lane per vector)
+
 __global__ void project_kernel(LanczosDev L, int pass) {
-  extern __shared__ double red[];  // [LT/32][kmax]
+  __shared__ double ws[PCH];
   const int s = blockIdx.y;
   if (!L.active[s]) return;
   const int64_t N = L.N[s];
-  const int64_t e0 = (int64_t)blockIdx.x * CH;
+  const int64_t e0 = (int64_t)blockIdx.x * PCH;
   if (e0 >= N) return;
+  const int n = (int)min((int64_t)PCH, N - e0);
   const int kk = L.k[s];
-  const double *w = L.w[s];
-  double wv[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int64_t e = e0 + threadIdx.x + q * LT;
-    wv[q] = e < N ? w[e] : 0.0;
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = 0; j <= kk; ++j) {
-    const double *v = L.V[s] + (int64_t)j * N;
-    double acc = 0.0;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int64_t e = e0 + threadIdx.x + q * LT;
-      if (e < N) acc = fma(v[e], wv[q], acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) red[warp * L.kmax + j] = acc;
-  }
+  const int jmin = pass == 0 ? kk : 0;
+  const double *w = L.w[s] + e0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[i];
   __syncthreads();
-  for (int j = threadIdx.x; j <= kk; j += LT) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = jmin + warp; j <= kk; j += nw) {
+    const double *v = L.V[s] + (int64_t)j * N + e0;
     double acc = 0.0;
-    for (int q = 0; q < LT / 32; ++q) acc += red[q * L.kmax + j];
-    L.part[(((int64_t)pass * L.S + s) * L.kmax + j) * L.nchunk_max + blockIdx.x] = acc;
+#pragma unroll 8
+    for (int i = lane; i < n; i += 32) acc = fma(v[i], ws[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) L.part[(((int64_t)pass * L.S + s) * L.kmax + j) * L.nchunk_max + blockIdx.x] = acc;
   }
 }
 
-// w -= sum_j V_j h_j with h_j the summed partials of `pass`; the CTA with
-// chunk 0 stores h in L.h[(pass*S + s)*kmax + j].  On pass 1 also writes the
-// partial squared norm of the new w at part2 slot j = kmax-1 of pass 2.
+// Pass 0: w -= alpha v_k + beta_{k-1} v_{k-1} with alpha the summed
+// partials (stored in L.h[0][k]).  Pass 1: w -= sum_j V_j h_j with h_j the
+// summed partials (stored in L.h[1][j]), and the partial squared norm of the
+// new w at part2 slot 0 of pass 2.  The CTA with chunk 0 stores h.
 __global__ void subtract_kernel(LanczosDev L, int pass) {
   extern __shared__ double hs[];  // [kmax] + [LT/32]
   const int s = blockIdx.y;
@@ -79,36 +82,50 @@ __global__ void subtract_kernel(LanczosDev L, int pass) {
   const int64_t e0 = (int64_t)blockIdx.x * CH;
   if (e0 >= N) return;
   const int kk = L.k[s];
-  const int nch = (int)((N + CH - 1) / CH);
-  for (int j = threadIdx.x; j <= kk; j += LT) {
+  const int npc = (int)((N + PCH - 1) / PCH);  // projection chunks
+  const int jmin = pass == 0 ? kk : 0;
+  for (int j = jmin + threadIdx.x; j <= kk; j += LT) {
     const double *p = L.part + (((int64_t)pass * L.S + s) * L.kmax + j) * L.nchunk_max;
     double acc = 0.0;
-    for (int c = 0; c < nch; ++c) acc += p[c];
+    for (int c = 0; c < npc; ++c) acc += p[c];
     hs[j] = acc;
     if (blockIdx.x == 0) L.h[((int64_t)pass * L.S + s) * L.kmax + j] = acc;
   }
+  if (pass == 0 && threadIdx.x == 0 && kk > 0) hs[kk - 1] = L.beta[s * L.kmax + kk - 1];
   __syncthreads();
   double *w = L.w[s];
+  const double *V = L.V[s];
   double nrm = 0.0;
+  if (pass == 0) {
+    const double a = hs[kk], b = kk > 0 ? hs[kk - 1] : 0.0;
+    const double *vk = V + (int64_t)kk * N, *vp = V + (int64_t)(kk > 0 ? kk - 1 : kk) * N;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int64_t e = e0 + threadIdx.x + q * LT;
+      if (e >= N) continue;
+      double acc = fma(-a, vk[e], w[e]);
+      if (kk > 0) acc = fma(-b, vp[e], acc);
+      w[e] = acc;
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
     const int64_t e = e0 + threadIdx.x + q * LT;
     if (e >= N) continue;
     double acc = w[e];
-    for (int j = 0; j <= kk; ++j) acc = fma(-hs[j], L.V[s][(int64_t)j * N + e], acc);
+    for (int j = 0; j <= kk; ++j) acc = fma(-hs[j], V[(int64_t)j * N + e], acc);
     w[e] = acc;
     nrm = fma(acc, acc, nrm);
   }
-  if (pass == 1) {
-    double *red = hs + L.kmax;
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double acc = 0.0;
-      for (int q = 0; q < LT / 32; ++q) acc += red[q];
-      L.part[(((int64_t)2 * L.S + s) * L.kmax + 0) * L.nchunk_max + blockIdx.x] = acc;
-    }
+  double *red = hs + L.kmax;
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int q = 0; q < LT / 32; ++q) acc += red[q];
+    L.part[(((int64_t)2 * L.S + s) * L.kmax + 0) * L.nchunk_max + blockIdx.x] = acc;
   }
 }
 
@@ -359,8 +376,9 @@ cudaError_t lanczos_set_ptrs(const LanczosDev &L, double **bufs, cudaStream_t st
 }
 
 cudaError_t lanczos_project(const LanczosDev &L, int pass, cudaStream_t st) {
-  dim3 grid(L.nchunk_max, L.S);
-  project_kernel<<<grid, LT, (LT / 32) * L.kmax * sizeof(double), st>>>(L, pass);
+  // projection chunks of PCH elements: nchunk_max counts chunks of CH <= PCH
+  dim3 grid((L.nchunk_max * CH + PCH - 1) / PCH, L.S);
+  project_kernel<<<grid, LT, 0, st>>>(L, pass);
   return cudaGetLastError();
 }
 
