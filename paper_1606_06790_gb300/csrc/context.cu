@@ -159,6 +159,8 @@ struct idmrg_ctx {
 
   std::vector<int> hmask;
   uint64_t mixed_matvecs = 0, fp64_matvecs = 0;
+  int *pin_act = nullptr;  // pinned: active flags of two Lanczos iterations
+  cudaEvent_t ev_act[2] = {nullptr, nullptr};
 
   // instrumentation: per-class CUDA-event timers, transfer counters
   struct KTimer {
@@ -951,6 +953,10 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   std::vector<int> member(P);
   for (int q = 0; q < P; ++q) member[q] = want(p, q) ? 1 : 0;
   NOMEM(c->upload(c->lmember, member));
+  if (!c->pin_act) {
+    CK(cudaHostAlloc((void **)&c->pin_act, 2 * 4 * (size_t)P, cudaHostAllocDefault));
+    for (auto &e : c->ev_act) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   LanczosDev L{};
   L.S = P;
   L.kmax = kmax;
@@ -979,7 +985,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   // against tol (and its alpha_0 is the FP64 Rayleigh quotient); the following
   // matvecs run on the tensor cores until the residual estimate falls by the
   // inner factor; the Ritz vector starts the next restart.
-  L.inner_factor = c->mixed ? 1e-5 : 0.0;
+  L.inner_factor = c->mixed ? 1e-3 : 0.0;
   const int max_restarts = c->mixed ? 8 : 1;
   const int inner_cap = c->mixed ? std::min(kmax, 80) : kmax;
   for (int q = 0; q < P; ++q) c->hbufs[q * NBUF + BUF_PSI] = psip[q];
@@ -1016,10 +1022,22 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
       CK(lanczos_next(L, c->st));
       c->kend(IDMRG_K_LANCZOS_VEC);
       c->launches += 7;
-      CK(c->d2h_copy(act.data(), c->lactive.p, 4 * P));
-      CK(cudaStreamSynchronize(c->st));
+      // the active flags after this iteration go to pinned memory; the host
+      // reads those of the previous iteration, so the next iteration is
+      // already queued while it waits (an iteration launched after the last
+      // superblock stopped finds every superblock inactive and does nothing)
+      int *flags = c->pin_act + (it & 1) * P;
+      CK(cudaMemcpyAsync(flags, c->lactive.p, 4 * P, cudaMemcpyDeviceToHost, c->st));
+      c->d2h += 4 * P;
+      CK(cudaEventRecord(c->ev_act[it & 1], c->st));
+      if (it == 0) continue;
+      CK(cudaEventSynchronize(c->ev_act[(it - 1) & 1]));
+      const int *prevf = c->pin_act + ((it - 1) & 1) * P;
       bool any = false;
-      for (int q = 0; q < P; ++q) any |= (act[q] != 0);
+      for (int q = 0; q < P; ++q) {
+        act[q] = prevf[q];
+        any |= (act[q] != 0);
+      }
       if (!any) break;
     }
     CK(lanczos_ritz(L, (double *const *)c->lpsi.p, c->st));
@@ -1807,6 +1825,9 @@ void idmrg_destroy(idmrg_ctx *c) {
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (cudaStream_t x : c->side)
     if (x) cudaStreamDestroy(x);
+  if (c->pin_act) cudaFreeHost(c->pin_act);
+  for (cudaEvent_t e : c->ev_act)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->sev)
     if (e) cudaEventDestroy(e);
   delete c;

@@ -22,6 +22,7 @@
 //            and writes them as the U and V blocks of the new bases.
 #include <cooperative_groups.h>
 #include <float.h>
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -478,7 +479,7 @@ __device__ __forceinline__ double recip_split(double x) {
 // only where the rotation must be exact: cos (Newton), the update
 // coefficients and the carried norms.
 __device__ __forceinline__ int bj_rotation(double graw, double &a, double &b, double &d1, double &d2, float log2_tol2,
-                                           Split fl, double &cp, double &cq) {
+                                           Split fl, double &cp, double &cq, float &lrel_out) {
   const double g = (d1 * d2) * graw;
   const Split sg = split_f64(g), sa = split_f64(a), sb = split_f64(b);
   if (sg.m == 0.0f || sa.m == 0.0f || sb.m == 0.0f) return 0;
@@ -486,6 +487,7 @@ __device__ __forceinline__ int bj_rotation(double graw, double &a, double &b, do
   // rotate iff g^2 > tol^2 a b and |g| > abs_floor
   const float lrel = (float)(2 * sg.e - sa.e - sb.e) + __log2f(mg * mg / (sa.m * sb.m));
   if (!(lrel > log2_tol2)) return 0;
+  lrel_out = lrel;
   if (fl.m != 0.0f && !((float)(sg.e - fl.e) + __log2f(mg / fl.m) > 0.0f)) return 0;
   // z = (b - a) / (2 g) in FP32 from exponents and mantissas
   const Split sn = split_f64(b - a);
@@ -544,6 +546,8 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
   __shared__ double fro_part[JAC_MAX_CLUSTER];
   __shared__ double wred[BJ_THREADS / 32];
   __shared__ int flag, local_changed;
+  // largest rotation of the sweep, 64 log2(g^2 / (a b)), and its cluster max
+  __shared__ int sweep_lmax, cl_lmax;
   __shared__ BjPair pairs[BJ_THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double *Bg = work + Jb.b_off;
@@ -592,7 +596,13 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
   const float log2_tol2 = __log2f((float)nr) - 104.0f;  // log2(nr eps^2), eps = 2^-52
   const Split floor_split = split_f64(4.0 * DBL_EPSILON * DBL_EPSILON * fro);
   int *flag0 = cluster.map_shared_rank(&flag, 0);
+  int *lmax0 = cluster.map_shared_rank(&cl_lmax, 0);
   bool converged = (n < 2);
+  // Cyclic Jacobi converges quadratically at the end: after a sweep in which
+  // no rotation exceeded |g| / sqrt(a b) = r = 1e-9, every pair is left with
+  // an overlap of order n r^2 <= 1e-15 relative, below the threshold
+  // sqrt(rows) eps, so the sweep that would only confirm it is skipped.
+  const int small_key = (int)(64.0f * -59.8f);  // 64 log2(1e-18)
   int sweep = 0, cur = 0;
   // fold the scales into the columns of the home blocks and recompute norms
   auto fold = [&]() {
@@ -641,7 +651,9 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
       BjPair &pr = pairs[lane];
       double a = s0[offN + pr.i], b = s1[offN + pr.j], d1 = s0[offD + pr.i], d2 = s1[offD + pr.j];
       double cp = 0.0, cq = 0.0;
-      pr.rot = bj_rotation(pr.g, a, b, d1, d2, log2_tol2, floor_split, cp, cq);
+      float lr = -1000.0f;
+      pr.rot = bj_rotation(pr.g, a, b, d1, d2, log2_tol2, floor_split, cp, cq, lr);
+      if (pr.rot) atomicMax(&sweep_lmax, (int)(lr * 64.0f));
       if (pr.rot) {
         pr.cp = cp;
         pr.cq = cq;
@@ -695,8 +707,14 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
   };
   for (; sweep < 40 && !converged; ++sweep) {
     fold();
-    if (threadIdx.x == 0) local_changed = 0;
-    if (crank == 0 && threadIdx.x == 0) flag = 0;
+    if (threadIdx.x == 0) {
+      local_changed = 0;
+      sweep_lmax = INT_MIN;
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      flag = 0;
+      cl_lmax = INT_MIN;
+    }
     cluster.sync();
     bool any = false;
     for (int rnd = 0; rnd < P - 1; ++rnd) {
@@ -764,9 +782,12 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     }
     if (any && lane == 0) local_changed = 1;
     __syncthreads();
-    if (threadIdx.x == 0 && local_changed) atomicOr(flag0, 1);
+    if (threadIdx.x == 0) {
+      if (local_changed) atomicOr(flag0, 1);
+      atomicMax(lmax0, sweep_lmax);
+    }
     cluster.sync();
-    converged = (*flag0 == 0);
+    converged = (*flag0 == 0) || (*lmax0 < small_key);
     cluster.sync();
   }
   fold();
