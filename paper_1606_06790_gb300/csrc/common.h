@@ -27,7 +27,7 @@ enum BufId {
   BUF_UT = 12,    // prediction: scaled u of superblock p+1 (u~ of Eq. wfprediction)
   BUF_VT = 13,    // prediction: scaled v of superblock p
   BUF_PSI = 14,   // start / ground-state vector
-  BUF_AUX = 15,
+  BUF_SVD = 15,   // SVD work arena (the same for every superblock)
   BUF_UPREV = 16, // prediction source: u^(n-1) of superblock p+1
   BUF_VPREV = 17, // prediction source: v^(n-1) of superblock p
   // mixed-precision H_eff psi (tensor cores): packed TF32 hi/lo operands
@@ -106,6 +106,7 @@ struct SvdJob {
   int64_t b_off;    // B = R^T (cols_a x cols_a), Jacobi working matrix
   int64_t x_off;    // rows_a x cols_a scratch for the back-transformation
   int64_t tau_off;  // cols_a Householder coefficients
+  int64_t w_off;    // cols_a x cols_a scratch of the FP32-preconditioned Jacobi
   int perm_off;     // cols_a column permutation of the pivoted QR (int work),
                     // then the numerical rank found by the QR and the sweeps
                     // the Jacobi stage needed
@@ -193,8 +194,17 @@ cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, dou
 constexpr size_t SVD_BLOCK_SMEM_MAX = 200 * 1024;
 size_t svd_block_smem(int cols, int csize);
 cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                              double *work, int *iwork, double *sv, int *err, cudaStream_t st,
+                              double *work, int *iwork, double *sv, int *err, int jm_init, cudaStream_t st,
                               const cudaStream_t *side, const cudaEvent_t *ev);
+// FP32 block Jacobi on the block groups 1..4 (group 0 untouched): writes the
+// accumulated rotations of each job to its V (j_off, cols_a x cols_a)
+cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
+                                double *work, const int *iwork, cudaStream_t st, const cudaStream_t *side,
+                                const cudaEvent_t *ev);
+// per job over cols_a x cols_a elements: 0: V = I; 1: V = 1.5 V - 0.5 W
+// (Newton-Schulz step, W at w_off); 2: B = X (X at w_off)
+cudaError_t launch_svd_elementwise(const SvdJob *jobs, int njobs, int max_cols, int mode, double *work,
+                                   cudaStream_t st);
 struct SelectOut {
   int *kept_per_job;   // [njobs]
   int *perm;           // [sum cols_a] kept slot -> index within job (per job, at sv_off)

@@ -151,7 +151,10 @@ struct idmrg_ctx {
   std::vector<int> tjob0, tnjob, tentries, torder, torderq, to0;
   std::vector<int64_t> tmaxel;
   std::vector<std::array<int, 4>> tg, tgcols;
-  int tiw = 0, tsv = 0, tentries_max = 1;
+  int tiw = 0, tsv = 0, tentries_max = 1, tmaxcols = 0;
+  // FP32-preconditioned Jacobi: G = V^T V, W = V G (Newton-Schulz), X = B V
+  GemmList svdG, svdW, svdX;
+  DevBuf dsgt, dsgk, dsgs, dswt, dswk, dsws, dsxt, dsxk, dsxs;
   int64_t tmaxel_all = 0;
 
   int svd_jobs = 0, svd_max_cols = 0, svd_max_rank = 0, svd_max_sweeps = 0;
@@ -1100,6 +1103,28 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
 // ------------------------------------------------------------------------
 // Step 4: sector SVD, cut, compaction
 // ------------------------------------------------------------------------
+// Jacobi launch groups of jobs listed largest first (ord[0..m)): a job's
+// time is about (columns) x (latency of a sub-round) whatever the cluster
+// size, so only the largest sectors need 16 CTAs; smaller ones take 8, 4 or
+// 1 and finish within the same time on fewer SMs.  g[k] ends group k (0:
+// global-memory kernel for sectors beyond the block kernel's shared memory,
+// 1..4: block kernel on 16, 8, 4, 1 CTAs); gcols[k] is the largest column
+// count of block group k+1.
+void jacobi_groups(const idmrg_ctx *c, const int *ord, int m, int g[4], int gcols[4]) {
+  for (int k = 0; k < 4; ++k) g[k] = gcols[k] = 0;
+  for (int j = 0; j < m; ++j) {
+    const int ca = c->jobs[ord[j]].cols_a;
+    if (ca >= 128 && svd_block_smem(ca, 16) > SVD_BLOCK_SMEM_MAX) g[0] = j + 1;
+    if (ca >= 128) g[1] = j + 1;
+    if (ca >= 64) g[2] = j + 1;
+    if (ca >= 24) g[3] = j + 1;
+  }
+  if (g[1] > g[0]) gcols[0] = c->jobs[ord[g[0]]].cols_a;
+  if (g[2] > g[1]) gcols[1] = c->jobs[ord[g[1]]].cols_a;
+  if (g[3] > g[2]) gcols[2] = c->jobs[ord[g[2]]].cols_a;
+  if (m > g[3]) gcols[3] = c->jobs[ord[g[3]]].cols_a;
+}
+
 // SVD jobs of every superblock of `p`: one job per charge sector Q of the
 // left half, (x s) rows of charge Q against (t y) columns of charge
 // target - Q.  Uploads the jobs, the global and the per-superblock orders
@@ -1179,6 +1204,8 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
       work += (int64_t)J.cols_a * J.cols_a;
       J.tau_off = work;
       work += J.cols_a;
+      J.w_off = work;
+      work += (int64_t)J.cols_a * J.cols_a;
       J.perm_off = iw;
       iw += J.cols_a + 2;
       J.sv_off = sv;
@@ -1213,26 +1240,28 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
     for (int j = 0; j < c->tnjob[q]; ++j) c->torderq.push_back(c->tjob0[q] + j);
     std::stable_sort(c->torderq.begin() + c->to0[q], c->torderq.end(), bigger);
   }
-  // Jacobi groups by column count, per superblock: beyond the shared memory
-  // of a 16-CTA cluster in global memory; then block Jacobi on 16, 8, 4 and
-  // 1 CTAs (g[k] ends group k; gcols[k] the largest columns of block group k)
-  for (int q = 0; q < P; ++q) {
-    std::array<int, 4> &g = c->tg[q];
-    std::array<int, 4> &gc = c->tgcols[q];
-    const int *ord = c->torderq.data() + c->to0[q];
-    const int m = c->tnjob[q];
-    for (int j = 0; j < m; ++j) {
-      const int ca = c->jobs[ord[j]].cols_a;
-      if (ca >= 96 && svd_block_smem(ca, 16) > SVD_BLOCK_SMEM_MAX) g[0] = j + 1;
-      if (ca >= 96) g[1] = j + 1;
-      if (ca >= 40) g[2] = j + 1;
-      if (ca >= 12) g[3] = j + 1;
-    }
-    if (g[1] > g[0]) gc[0] = c->jobs[ord[g[0]]].cols_a;
-    if (g[2] > g[1]) gc[1] = c->jobs[ord[g[1]]].cols_a;
-    if (g[3] > g[2]) gc[2] = c->jobs[ord[g[2]]].cols_a;
-    if (m > g[3]) gc[3] = c->jobs[ord[g[3]]].cols_a;
+  for (int q = 0; q < P; ++q)
+    jacobi_groups(c, c->torderq.data() + c->to0[q], c->tnjob[q], c->tg[q].data(), c->tgcols[q].data());
+  // Newton-Schulz steps and X = B V of the FP32-preconditioned Jacobi.  V is
+  // column-major cols_a x cols_a, i.e. the row-major matrix V^T:
+  // G = V^T V (x_off), W^T = G V^T (w_off), X^T = V^T B^T (w_off)
+  c->svdG.clear();
+  c->svdW.clear();
+  c->svdX.clear();
+  c->tmaxcols = 0;
+  for (const SvdJob &J : c->jobs) {
+    const int ca = J.cols_a;
+    c->tmaxcols = std::max(c->tmaxcols, ca);
+    c->svdG.task(J.sb, BUF_SVD, J.x_off, ca, ca, ca);
+    c->svdG.seg(BUF_SVD, J.j_off, ca, BUF_SVD, J.j_off, ca, ca, 2);
+    c->svdW.task(J.sb, BUF_SVD, J.w_off, ca, ca, ca);
+    c->svdW.seg(BUF_SVD, J.x_off, ca, BUF_SVD, J.j_off, ca, ca, 0);
+    c->svdX.task(J.sb, BUF_SVD, J.w_off, ca, ca, ca);
+    c->svdX.seg(BUF_SVD, J.j_off, ca, BUF_SVD, J.b_off, ca, ca, 0);
   }
+  c->svdG.finish(64, 64);
+  c->svdW.finish(64, 64);
+  c->svdX.finish(64, 64);
   NOMEM(c->ensure(c->siw, 4 * std::max(iw, 1)));
   NOMEM(c->upload(c->sjobs, c->jobs) && c->ensure(c->swork, 8 * std::max<int64_t>(work, 1)) &&
         c->ensure(c->ssv, 8 * std::max(sv, 1)) && c->upload(c->sjob0, c->tjob0) && c->upload(c->snjob, c->tnjob) &&
@@ -1240,6 +1269,11 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
         c->ensure(c->slam, 8 * std::max(sv, 1)) && c->ensure(c->seps, 8 * P) && c->ensure(c->sepsb, 8 * P) &&
         c->ensure(c->skept, 4 * P) && c->upload(c->sorder, c->torder) && c->upload(c->sorderq, c->torderq) &&
         c->ensure(c->slamk, 8 * (size_t)P * std::max(1, c->o.m)));
+  NOMEM(c->upload(c->dsgt, c->svdG.tiles) && c->upload(c->dsgk, c->svdG.tasks) && c->upload(c->dsgs, c->svdG.segs) &&
+        c->upload(c->dswt, c->svdW.tiles) && c->upload(c->dswk, c->svdW.tasks) && c->upload(c->dsws, c->svdW.segs) &&
+        c->upload(c->dsxt, c->svdX.tiles) && c->upload(c->dsxk, c->svdX.tasks) && c->upload(c->dsxs, c->svdX.segs));
+  for (int q = 0; q < P; ++q) c->hbufs[q * NBUF + BUF_SVD] = c->dp(c->swork);
+  NOMEM(sync_bufs(c) == IDMRG_OK);
   return IDMRG_OK;
 }
 
@@ -1265,24 +1299,6 @@ SelectOut select_out(idmrg_ctx *c, int q0) {
   so.eps_best = c->dp(c->sepsb) + q0;
   so.kept = (int *)c->skept.p + q0;
   return so;
-}
-
-// Step 4 for one superblock on stream s: gather, pivoted QR, Jacobi, select.
-idmrg_status trunc_launch_one(idmrg_ctx *c, int q, cudaStream_t s) {
-  const int m = c->tnjob[q];
-  if (m == 0) return IDMRG_OK;
-  double *const *bufs = (double *const *)c->dbufs.p;
-  const SvdJob *jobs = (const SvdJob *)c->sjobs.p;
-  const int *ord = (const int *)c->sorderq.p + c->to0[q];
-  CK(launch_svd_gather_sized(jobs + c->tjob0[q], m, c->tmaxel[q], bufs, BUF_PSI, c->dp(c->swork), s));
-  CK(launch_svd_qrcp(jobs, ord, m, c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, s));
-  if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
-  CK(launch_svd_jacobi(jobs, ord, m, c->tg[q].data(), c->tgcols[q].data(), c->dp(c->swork), (int *)c->siw.p,
-                       c->dp(c->ssv), (int *)c->derr.p, s, c->side, c->sev));
-  CK(launch_svd_select(jobs, (const int *)c->sjob0.p + q, (const int *)c->snjob.p + q, 1, c->dp(c->ssv), c->o.m,
-                       c->o.lambda_zero_rel, c->o.tie_rel, select_out(c, q), c->tentries[q], s));
-  c->launches += 8;
-  return IDMRG_OK;
 }
 
 // New bases of superblock q from the selection (host arrays indexed like the
@@ -1383,22 +1399,31 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, c->dp(c->swork), (int *)c->siw.p,
                      c->o.lambda_zero_rel, c->st));
   // Jacobi groups over all jobs (largest first across superblocks)
-  int g[4] = {0, 0, 0, 0};
-  for (int j = 0; j < nj; ++j) {
-    const int ca = c->jobs[c->torder[j]].cols_a;
-    if (ca >= 96 && svd_block_smem(ca, 16) > SVD_BLOCK_SMEM_MAX) g[0] = j + 1;
-    if (ca >= 96) g[1] = j + 1;
-    if (ca >= 40) g[2] = j + 1;
-    if (ca >= 12) g[3] = j + 1;
-  }
-  int gcols[4] = {0, 0, 0, 0};
-  if (g[1] > g[0]) gcols[0] = c->jobs[c->torder[g[0]]].cols_a;
-  if (g[2] > g[1]) gcols[1] = c->jobs[c->torder[g[1]]].cols_a;
-  if (g[3] > g[2]) gcols[2] = c->jobs[c->torder[g[2]]].cols_a;
-  if (nj > g[3]) gcols[3] = c->jobs[c->torder[g[3]]].cols_a;
+  int g[4], gcols[4];
+  jacobi_groups(c, c->torder.data(), nj, g, gcols);
   if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
-  CK(launch_svd_jacobi((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, gcols, c->dp(c->swork),
-                       (int *)c->siw.p, c->dp(c->ssv), (int *)c->derr.p, c->st, c->side, c->sev));
+  // FP32 stage: rotations V to FP32 accuracy; Newton-Schulz makes V
+  // orthogonal to FP64 precision (V <- 1.5 V - 0.5 V V^T V, twice); X = B V;
+  // the FP64 stage starts from X with its rotations initialised to V
+  const SvdJob *dj = (const SvdJob *)c->sjobs.p;
+  double *sw = c->dp(c->swork);
+  double *const *svb = (double *const *)c->dbufs.p;
+  CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 0, sw, c->st));
+  CK(launch_svd_jacobi32(dj, (const int *)c->sorder.p, nj, g, gcols, sw, (const int *)c->siw.p, c->st, c->side,
+                         c->sev));
+  for (int it = 0; it < 2; ++it) {
+    CK(launch_gemm_f64((const GemmTile *)c->dsgt.p, (int)c->svdG.tiles.size(), (const GemmTask *)c->dsgk.p,
+                       (const GemmSeg *)c->dsgs.p, svb, nullptr, c->st));
+    CK(launch_gemm_f64((const GemmTile *)c->dswt.p, (int)c->svdW.tiles.size(), (const GemmTask *)c->dswk.p,
+                       (const GemmSeg *)c->dsws.p, svb, nullptr, c->st));
+    CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 1, sw, c->st));
+  }
+  CK(launch_gemm_f64((const GemmTile *)c->dsxt.p, (int)c->svdX.tiles.size(), (const GemmTask *)c->dsxk.p,
+                     (const GemmSeg *)c->dsxs.p, svb, nullptr, c->st));
+  CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 2, sw, c->st));
+  CK(launch_svd_jacobi(dj, (const int *)c->sorder.p, nj, g, gcols, sw, (int *)c->siw.p, c->dp(c->ssv),
+                       (int *)c->derr.p, 1, c->st, c->side, c->sev));
+  c->launches += 12;
   // select: one launch, one CTA per superblock (no jobs: nothing kept)
   std::vector<int> sbl;
   for (int q = 0; q < P; ++q)
@@ -1818,7 +1843,8 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->libeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
-                    &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
+                    &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgt, &c->dsgk, &c->dsgs, &c->dswt,
+                    &c->dswk, &c->dsws, &c->dsxt, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
                     &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);

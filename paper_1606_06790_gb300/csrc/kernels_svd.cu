@@ -198,10 +198,11 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restri
   }
   const int rk = s_rank;
   if (threadIdx.x == 0) perm[ca] = rk;
-  // B = [R11 R12]^T (ca x rk, column-major): B(a, b) = R(b, a) for b <= a, b < rk
-  for (int64_t e = threadIdx.x; e < (int64_t)ca * rk; e += blockDim.x) {
+  // B = [R11 R12]^T (ca x rk, column-major): B(a, b) = R(b, a) for b <= a, b < rk;
+  // the columns beyond the rank are zero (B's slot is ca x ca)
+  for (int64_t e = threadIdx.x; e < (int64_t)ca * ca; e += blockDim.x) {
     const int a = (int)(e % ca), b = (int)(e / ca);
-    B[e] = (b <= a) ? A[(int64_t)a * ra + b] : 0.0;
+    B[e] = (b <= a && b < rk) ? A[(int64_t)a * ra + b] : 0.0;
   }
 }
 
@@ -526,9 +527,12 @@ __device__ __forceinline__ int bj_rotation(double graw, double &a, double &b, do
   return (oka && okb) ? 1 : 2;
 }
 
+// jm_init = 1: the rotations start from the matrix at j_off (cols_a x
+// cols_a, column-major: the FP32 stage's orthogonalised rotations) instead
+// of the identity; B then holds the preconditioned columns
 __global__ void __launch_bounds__(BJ_THREADS, 2)
     jacobi_block_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
-                        int *__restrict__ iwork, double *__restrict__ sv, int *err) {
+                        int *__restrict__ iwork, double *__restrict__ sv, int *err, int jm_init) {
   extern __shared__ __align__(16) double bj_sm[];
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
@@ -573,7 +577,9 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     }
     for (int e = threadIdx.x; e < bw * ldj; e += blockDim.x) {
       const int j = e / ldj, i = e - j * ldj;
-      sb[offJ + e] = (j < nv && i == k * bw + j) ? 1.0 : 0.0;
+      double v = 0.0;
+      if (j < nv && i < n) v = jm_init ? Jg[(int64_t)(k * bw + j) * nr + i] : (i == k * bw + j ? 1.0 : 0.0);
+      sb[offJ + e] = v;
     }
     for (int j = threadIdx.x; j < bw; j += blockDim.x) sb[offD + j] = 1.0;
   }
@@ -812,6 +818,197 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     for (int j = n + (int)threadIdx.x; j < Jb.cols_a; j += blockDim.x) sv[Jb.sv_off + j] = 0.0;
 }
 
+// ------------------------------------------------- FP32 stage of the Jacobi SVD
+// The same block tournament in FP32, whose instructions cost a sixteenth of
+// FP64 ones here: it converges the rotations to FP32 accuracy (relative
+// overlaps ~1e-6), the rotation matrix is then made orthogonal to FP64
+// precision by Newton-Schulz steps and applied to B (FP64 GEMMs), and the
+// FP64 block Jacobi finishes from there in two sweeps or so instead of five
+// to eight.  The FP32 result only preconditions: singular values and vectors
+// come from the FP64 stage.  Each warp takes one pair at a time (plain
+// rotations, column norms recomputed); the tests avoid squares so that
+// columns near the underflow of FP32 are merely skipped.
+__global__ void __launch_bounds__(BJ_THREADS, 2)
+    jacobi32_block_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                          const int *__restrict__ iwork) {
+  extern __shared__ __align__(16) float bf_sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / C]];
+  const int nr = Jb.cols_a;
+  const int n = iwork[Jb.perm_off + Jb.cols_a];
+  const int P = 2 * C;
+  const int bw = (n + P - 1) / P;
+  const int nreg = (nr + 31) >> 5, nregj = (n + 31) >> 5;
+  const int ldb = 32 * nreg, ldj = 32 * nregj;
+  const int offJ = bw * ldb;
+  const int slot = (offJ + bw * ldj + 3) & ~3;  // 16-byte aligned blocks
+  __shared__ int flag, local_changed, sweep_rmax, cl_rmax;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const double *Bg = work + Jb.b_off;
+  double *Vg = work + Jb.j_off;
+  const int pos[2] = {crank, P - 1 - crank};
+  auto slotp = [&](int buf, int which) { return bf_sm + (buf * 2 + which) * slot; };
+  auto valid = [&](int k) { return max(0, min(bw, n - k * bw)); };
+  if (nreg > BJ_REG || nregj > BJ_REG || n < 2) return;  // uniform over the cluster
+  for (int w = 0; w < 2; ++w) {
+    const int k = pos[w], nv = valid(k);
+    float *sb = slotp(0, w);
+    for (int e = threadIdx.x; e < offJ; e += blockDim.x) {
+      const int j = e / ldb, i = e - j * ldb;
+      sb[e] = (j < nv && i < nr) ? (float)Bg[(int64_t)(k * bw + j) * nr + i] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < bw * ldj; e += blockDim.x) {
+      const int j = e / ldj, i = e - j * ldj;
+      sb[offJ + e] = (j < nv && i == k * bw + j) ? 1.0f : 0.0f;
+    }
+  }
+  const float tol = sqrtf((float)nr) * FLT_EPSILON;
+  int *flag0 = cluster.map_shared_rank(&flag, 0);
+  int *rmax0 = cluster.map_shared_rank(&cl_rmax, 0);
+  int cur = 0;
+  bool converged = false;
+  auto wsumf = [](float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  };
+  // one pair, one warp; returns 1 if rotated (ratio |g|/sqrt(ab) into rmax)
+  auto pair = [&](float *s0, int i, float *s1, int j, float &rmax) -> bool {
+    float *xp = s0 + i * ldb, *xq = s1 + j * ldb, *jp = s0 + offJ + i * ldj, *jq = s1 + offJ + j * ldj;
+    float x[BJ_REG], y[BJ_REG], a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+    for (int r = 0; r < BJ_REG; ++r)
+      if (r < nreg) {
+        x[r] = xp[lane + 32 * r];
+        y[r] = xq[lane + 32 * r];
+        a = fmaf(x[r], x[r], a);
+        b = fmaf(y[r], y[r], b);
+        g = fmaf(x[r], y[r], g);
+      }
+    a = wsumf(a);
+    b = wsumf(b);
+    g = wsumf(g);
+    if (!(a > 0.f) || !(b > 0.f)) return false;
+    const float ra = sqrtf(a), rb = sqrtf(b);
+    const float ratio = fabsf(g) / ra / rb;
+    if (!(ratio > tol)) return false;
+    const float z = (b - a) / (2.0f * g);
+    const float t = z == 0.f ? 1.0f : copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
+    if (!(fabsf(t) >= FLT_MIN) || !isfinite(t)) return false;
+    const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
+#pragma unroll
+    for (int r = 0; r < BJ_REG; ++r)
+      if (r < nreg) {
+        xp[lane + 32 * r] = c * x[r] - sn * y[r];
+        xq[lane + 32 * r] = fmaf(sn, x[r], c * y[r]);
+      }
+#pragma unroll
+    for (int r = 0; r < BJ_REG; ++r)
+      if (r < nregj) {
+        const float u = jp[lane + 32 * r], v = jq[lane + 32 * r];
+        jp[lane + 32 * r] = c * u - sn * v;
+        jq[lane + 32 * r] = fmaf(sn, u, c * v);
+      }
+    rmax = fmaxf(rmax, ratio);
+    return true;
+  };
+  for (int sweep = 0; sweep < 15 && !converged; ++sweep) {
+    if (threadIdx.x == 0) {
+      local_changed = 0;
+      sweep_rmax = 0;
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      flag = 0;
+      cl_rmax = 0;
+    }
+    cluster.sync();
+    bool any = false;
+    float rmax = 0.f;
+    for (int rnd = 0; rnd < P - 1; ++rnd) {
+      float *st0 = slotp(cur, 0), *st1 = slotp(cur, 1);
+      const int nv0 = valid(bj_block_at(pos[0], rnd, P)), nv1 = valid(bj_block_at(pos[1], rnd, P));
+      if (rnd == 0) {
+        const int bp = bw + (bw & 1), half = bp / 2, bm = bp - 1;
+        for (int w = 0; w < 2; ++w) {
+          const int nv = w ? nv1 : nv0;
+          float *sb = w ? st1 : st0;
+          for (int sr = 0; sr < bm; ++sr) {
+            for (int i = warp; i < half; i += nw) {
+              int p = 0, q;
+              if (i != 0) {
+                p = i - 1 + sr;
+                p = 1 + (p >= bm ? p - bm : p);
+              }
+              q = bp - 2 - i + sr;
+              q = 1 + (q >= bm ? q - bm : q);
+              if (p < nv && q < nv) any |= pair(sb, p, sb, q, rmax);
+            }
+            __syncthreads();
+          }
+        }
+      }
+      for (int sr = 0; sr < bw; ++sr) {
+        for (int i = warp; i < bw; i += nw) {
+          int j = i + sr;
+          if (j >= bw) j -= bw;
+          if (i < nv0 && j < nv1) any |= pair(st0, i, st1, j, rmax);
+        }
+        __syncthreads();
+      }
+      if (C > 1) {
+        for (int w = 0; w < 2; ++w) {
+          const int dpn = pos[w] == 0 ? 0 : (pos[w] == P - 1 ? 1 : pos[w] + 1);
+          const int drank = dpn < C ? dpn : P - 1 - dpn, dw = dpn < C ? 0 : 1;
+          float4 *dst = reinterpret_cast<float4 *>(cluster.map_shared_rank(slotp(cur ^ 1, dw), drank));
+          const float4 *src = reinterpret_cast<const float4 *>(w ? st1 : st0);
+          for (int e = threadIdx.x; e < slot / 4; e += blockDim.x) dst[e] = src[e];
+        }
+        cluster.sync();
+        cur ^= 1;
+      }
+    }
+    if (any && lane == 0) local_changed = 1;
+    if (lane == 0) atomicMax(&sweep_rmax, __float_as_int(rmax));  // non-negative floats order as ints
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (local_changed) atomicOr(flag0, 1);
+      atomicMax(rmax0, sweep_rmax);
+    }
+    cluster.sync();
+    // done when nothing rotated, or the largest rotation leaves overlaps of
+    // order n r^2 below the FP32 threshold
+    const float r = __int_as_float(*rmax0);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    cluster.sync();
+  }
+  // rotations to V (FP64, cols_a x cols_a, identity outside the rank)
+  for (int w = 0; w < 2; ++w) {
+    const int k = pos[w], nv = valid(k);
+    const float *sb = slotp(cur, w);
+    for (int e = threadIdx.x; e < nv * n; e += blockDim.x) {
+      const int j = e / n, i = e - j * n;
+      Vg[(int64_t)(k * bw + j) * nr + i] = (double)sb[offJ + j * ldj + i];
+    }
+  }
+}
+
+// per job over cols_a x cols_a elements: 0 V = I, 1 V = 1.5 V - 0.5 W, 2 B = X
+__global__ void svd_elementwise_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work, int mode) {
+  const SvdJob J = jobs[blockIdx.y];
+  const int ca = J.cols_a;
+  const int64_t tot = (int64_t)ca * ca;
+  double *V = work + J.j_off, *W = work + J.w_off, *B = work + J.b_off;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    if (mode == 0)
+      V[e] = (e / ca == e % ca) ? 1.0 : 0.0;
+    else if (mode == 1)
+      V[e] = fma(-0.5, W[e], 1.5 * V[e]);
+    else
+      B[e] = W[e];
+  }
+}
+
 // ---------------------------------------------------------------- select
 struct Entry {
   double s;
@@ -995,7 +1192,8 @@ size_t svd_block_smem(int cols, int csize) {
 
 // block kernel for jobs of at most `cols` columns on clusters of `csize`
 static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, int cols,
-                                         double *work, int *iwork, double *sv, int *err, cudaStream_t st) {
+                                         double *work, int *iwork, double *sv, int *err, int jm_init,
+                                         cudaStream_t st) {
   // one warp per pair of a sub-round (at least two, at most BJ_THREADS / 32):
   // small blocks let three or four CTAs of different clusters share an SM
   const int bw = (cols + 2 * csize - 1) / (2 * csize);
@@ -1014,7 +1212,7 @@ static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, jacobi_block_kernel, jobs, order, work, iwork, sv, err);
+  return cudaLaunchKernelEx(&cfg, jacobi_block_kernel, jobs, order, work, iwork, sv, err, jm_init);
 }
 
 // `order` lists the jobs by column count, largest first, in five groups
@@ -1025,7 +1223,7 @@ static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, i
 // streams side[0..2], forked from and joined back to `st` by the events
 // ev[0..3].
 cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                              double *work, int *iwork, double *sv, int *err, cudaStream_t st,
+                              double *work, int *iwork, double *sv, int *err, int jm_init, cudaStream_t st,
                               const cudaStream_t *side, const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
   cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1043,7 +1241,7 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     e = cudaStreamWaitEvent(side[k - 2], ev[0], 0);
     if (e != cudaSuccess) return e;
     e = launch_block_clusters(jobs, order + lo[k], hi[k] - lo[k], csz[k], cols[k - 1], work, iwork, sv, err,
-                              side[k - 2]);
+                              jm_init, side[k - 2]);
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(ev[k - 1], side[k - 2]);
     if (e != cudaSuccess) return e;
@@ -1057,7 +1255,7 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     if (e != cudaSuccess) return e;
   }
   if (hi[1] > lo[1]) {
-    e = launch_block_clusters(jobs, order + lo[1], hi[1] - lo[1], 16, cols[0], work, iwork, sv, err, st);
+    e = launch_block_clusters(jobs, order + lo[1], hi[1] - lo[1], 16, cols[0], work, iwork, sv, err, jm_init, st);
     if (e != cudaSuccess) {
       // 16-CTA clusters not available: the global-memory kernel on 8
       cudaGetLastError();
@@ -1093,6 +1291,70 @@ cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj
     dim3 grid(ncj, (unsigned)std::max(1, (max_kept + warps - 1) / warps));
     compact_kernel<<<grid, 32 * warps, 0, st>>>(jobs, cj, work, iwork, sv, perm, kept_per_job, bufs, lam);
   }
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_block32_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, int cols,
+                                           double *work, const int *iwork, cudaStream_t st) {
+  const int bw = (cols + 2 * csize - 1) / (2 * csize);
+  const int warps = std::min(BJ_THREADS / 32, std::max(2, bw));
+  const int64_t pad = 32 * (((int64_t)cols + 31) / 32);
+  const size_t smem = (size_t)(4 * ((bw * 2 * pad + 3) & ~(int64_t)3) * sizeof(float));
+  if (pad > 32 * BJ_REG || smem > SVD_BLOCK_SMEM_MAX) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * csize, 1, 1);
+  cfg.blockDim = dim3(32 * warps, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi32_block_kernel, jobs, order, work, iwork);
+}
+
+cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
+                                double *work, const int *iwork, cudaStream_t st, const cudaStream_t *side,
+                                const cudaEvent_t *ev) {
+  if (njobs <= 0) return cudaGetLastError();
+  cudaFuncSetAttribute(jacobi32_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cudaFuncSetAttribute(jacobi32_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SVD_BLOCK_SMEM_MAX);
+  if (e != cudaSuccess) return e;
+  const int lo[5] = {0, g[0], g[1], g[2], g[3]}, hi[5] = {g[0], g[1], g[2], g[3], njobs};
+  const int csz[5] = {16, 16, 8, 4, 1};
+  e = cudaEventRecord(ev[0], st);
+  if (e != cudaSuccess) return e;
+  for (int k = 2; k < 5; ++k) {
+    if (hi[k] <= lo[k]) continue;
+    e = cudaStreamWaitEvent(side[k - 2], ev[0], 0);
+    if (e != cudaSuccess) return e;
+    e = launch_block32_clusters(jobs, order + lo[k], hi[k] - lo[k], csz[k], cols[k - 1], work, iwork, side[k - 2]);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev[k - 1], side[k - 2]);
+    if (e != cudaSuccess) return e;
+  }
+  if (hi[1] > lo[1]) {
+    e = launch_block32_clusters(jobs, order + lo[1], hi[1] - lo[1], 16, cols[0], work, iwork, st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int k = 2; k < 5; ++k) {
+    if (hi[k] <= lo[k]) continue;
+    e = cudaStreamWaitEvent(st, ev[k - 1], 0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_svd_elementwise(const SvdJob *jobs, int njobs, int max_cols, int mode, double *work,
+                                   cudaStream_t st) {
+  if (njobs <= 0 || max_cols <= 0) return cudaGetLastError();
+  const int64_t tot = (int64_t)max_cols * max_cols;
+  dim3 grid((unsigned)std::min<int64_t>((tot + 255) / 256, 64), (unsigned)njobs);
+  svd_elementwise_kernel<<<grid, 256, 0, st>>>(jobs, work, mode);
   return cudaGetLastError();
 }
 
