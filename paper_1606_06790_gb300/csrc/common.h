@@ -140,8 +140,12 @@ struct ScaleTask {
 
 // ------------------------------------------------------------ launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
+// tile shapes of the grouped GEMM (TM x TN outputs per CTA)
+enum GemmShape { GEMM_64x64 = 0, GEMM_64x32 = 1, GEMM_32x64 = 2, GEMM_32x32 = 3, GEMM_NSHAPE = 4 };
+constexpr int GEMM_TM[GEMM_NSHAPE] = {64, 64, 32, 32};
+constexpr int GEMM_TN[GEMM_NSHAPE] = {64, 32, 64, 32};
 cudaError_t launch_gemm_f64(const GemmTile *tiles, int ntiles, const GemmTask *tasks, const GemmSeg *segs,
-                            double *const *bufs, const int *active, cudaStream_t st);
+                            double *const *bufs, const int *active, cudaStream_t st, int shape = GEMM_64x64);
 cudaError_t launch_wstage_f64(const WTask *tasks, int ntasks, int max_rows, const WTerm *terms,
                               double *const *bufs, const int *active, cudaStream_t st);
 cudaError_t launch_dot_terms(const DotTerm *terms, int nterms, double *const *bufs, double *partial,

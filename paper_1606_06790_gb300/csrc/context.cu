@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.h"
@@ -73,6 +74,21 @@ uint64_t sm64_mix(uint64_t z) {
 uint64_t sm64_at(uint64_t s, uint64_t k) { return sm64_mix(s + (k + 1ull) * 0x9E3779B97F4A7C15ull); }
 
 }  // namespace
+
+// Autotuned tile shape of one grouped-GEMM list.  Every shape gives the same
+// result bit for bit (each output element sums its K terms in the same
+// order), so the first calls of a list try each shape once on real work,
+// timed with CUDA events on the stream, and the fastest is kept until the
+// list's work changes by more than 10 %.
+struct GemmTune {
+  DevBuf tiles[GEMM_NSHAPE];
+  int ntiles[GEMM_NSHAPE] = {0, 0, 0, 0};
+  int choice = -1;
+  int state[GEMM_NSHAPE] = {0, 0, 0, 0};  // 0 untried, 1 timing, 2 timed
+  float ms[GEMM_NSHAPE] = {0, 0, 0, 0};
+  cudaEvent_t e0[GEMM_NSHAPE] = {}, e1[GEMM_NSHAPE] = {};
+  double work = -1.0;
+};
 
 struct idmrg_ctx {
   // problem
@@ -136,8 +152,8 @@ struct idmrg_ctx {
 
   // device buffers
   std::vector<double *> hbufs;
-  DevBuf dbufs, dg1t, dg1k, dg1s, dg3t, dg3k, dg3s, dwt, dwm, ddt, ddp, drb, dgpt, dgpk, dgps, dst, dstab;
-  DevBuf dge1t, dge1k, dge1s, dge3t, dge3k, dge3s, dwet, dwem, dmask, derr;
+  DevBuf dbufs, dg1k, dg1s, dg3k, dg3s, dwt, dwm, ddt, ddp, drb, dgpk, dgps, dst, dstab;
+  DevBuf dge1k, dge1s, dge3k, dge3s, dwet, dwem, dmask, derr;
   std::vector<DevBuf> bT1, bT3, bX, bY, bV, bW, bPsi, bUT, bVT;
   // lanczos
   DevBuf lN, lV, lw, lalpha, lbeta, libeta, lh, lpart, lk, lmember, lactive, lconv, ltheta, ly, lresid, lpsi, lv0, ldot;
@@ -154,7 +170,9 @@ struct idmrg_ctx {
   int tiw = 0, tsv = 0, tentries_max = 1, tmaxcols = 0;
   // FP32-preconditioned Jacobi: G = V^T V, W = V G (Newton-Schulz), X = B V
   GemmList svdG, svdW, svdX;
-  DevBuf dsgt, dsgk, dsgs, dswt, dswk, dsws, dsxt, dsxk, dsxs;
+  DevBuf dsgk, dsgs, dswk, dsws, dsxk, dsxs;
+  // tile-shape autotuning of every grouped-GEMM list
+  GemmTune tn_g1, tn_g3, tn_gp, tn_env1, tn_env3, tn_svdG, tn_svdW, tn_svdX;
   int64_t tmaxel_all = 0;
 
   int svd_jobs = 0, svd_max_cols = 0, svd_max_rank = 0, svd_max_sweeps = 0;
@@ -287,6 +305,67 @@ namespace {
   do {                                                             \
     if (!(ok)) return c->fail(IDMRG_ENOMEM, "device allocation failed (%s)", #ok); \
   } while (0)
+
+// tiles of every shape (L.tiles ends with the 64 x 64 ones) plus tasks and
+// segments to the device
+idmrg_status gemm_upload(idmrg_ctx *c, GemmList &L, DevBuf &dk, DevBuf &ds, GemmTune &T) {
+  for (int sh = GEMM_NSHAPE - 1; sh >= 0; --sh) {
+    L.finish(GEMM_TM[sh], GEMM_TN[sh]);
+    T.ntiles[sh] = (int)L.tiles.size();
+    NOMEM(c->upload(T.tiles[sh], L.tiles));
+  }
+  NOMEM(c->upload(dk, L.tasks) && c->upload(ds, L.segs));
+  const double w = L.flops;
+  if (T.work < 0.0 || fabs(w - T.work) > 0.1 * T.work) {  // new work: tune again
+    T.work = w;
+    T.choice = -1;
+    for (int sh = 0; sh < GEMM_NSHAPE; ++sh) T.state[sh] = 0;
+  }
+  return IDMRG_OK;
+}
+
+idmrg_status gemm_run(idmrg_ctx *c, GemmTune &T, DevBuf &dk, DevBuf &ds, const int *active) {
+  double *const *bufs = (double *const *)c->dbufs.p;
+  int sh = T.choice;
+  if (sh < 0) {
+    bool all = true;
+    for (int k = 0; k < GEMM_NSHAPE; ++k) {
+      if (T.state[k] == 1 && cudaEventQuery(T.e1[k]) == cudaSuccess) {
+        cudaEventElapsedTime(&T.ms[k], T.e0[k], T.e1[k]);
+        T.state[k] = 2;
+      }
+      all &= T.state[k] == 2;
+    }
+    if (all) {
+      int best = 0;
+      for (int k = 1; k < GEMM_NSHAPE; ++k)
+        if (T.ms[k] < T.ms[best]) best = k;
+      T.choice = sh = best;
+    }
+  }
+  if (sh >= 0) {
+    CK(launch_gemm_f64((const GemmTile *)T.tiles[sh].p, T.ntiles[sh], (const GemmTask *)dk.p, (const GemmSeg *)ds.p,
+                       bufs, active, c->st, sh));
+    return IDMRG_OK;
+  }
+  int k = 0;
+  while (k < GEMM_NSHAPE && T.state[k] != 0) ++k;
+  if (k == GEMM_NSHAPE) k = 0;  // every shape in flight: the default
+  const bool timed = T.state[k] == 0;
+  if (timed) {
+    if (!T.e0[k]) CK(cudaEventCreate(&T.e0[k]));
+    if (!T.e1[k]) CK(cudaEventCreate(&T.e1[k]));
+    CK(cudaEventRecord(T.e0[k], c->st));
+  }
+  CK(launch_gemm_f64((const GemmTile *)T.tiles[k].p, T.ntiles[k], (const GemmTask *)dk.p, (const GemmSeg *)ds.p, bufs,
+                     active, c->st, k));
+  if (timed) {
+    CK(cudaEventRecord(T.e1[k], c->st));
+    T.state[k] = 1;
+  }
+  return IDMRG_OK;
+}
+
 
 // ------------------------------------------------------------------------
 // planning of iteration n
@@ -465,11 +544,14 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
           c->rmax_rows = std::max(c->rmax_rows, rb.rows);
         }
   }
-  c->g1.finish(64, 64);
-  c->g3.finish(64, 64);
+
   // ---- device buffers for this iteration
-  NOMEM(c->upload(c->dg1t, c->g1.tiles) && c->upload(c->dg1k, c->g1.tasks) && c->upload(c->dg1s, c->g1.segs));
-  NOMEM(c->upload(c->dg3t, c->g3.tiles) && c->upload(c->dg3k, c->g3.tasks) && c->upload(c->dg3s, c->g3.segs));
+  {
+    idmrg_status sg = gemm_upload(c, c->g1, c->dg1k, c->dg1s, c->tn_g1);
+    if (sg != IDMRG_OK) return sg;
+    sg = gemm_upload(c, c->g3, c->dg3k, c->dg3s, c->tn_g3);
+    if (sg != IDMRG_OK) return sg;
+  }
   NOMEM(c->upload(c->dwt, c->wl.tasks) && c->upload(c->dwm, c->wl.terms));
   NOMEM(c->upload(c->ddt, c->dterms) && c->ensure(c->ddp, std::max<size_t>(c->dterms.size(), 1) * 8));
   NOMEM(c->upload(c->drb, c->rblocks));
@@ -763,16 +845,20 @@ idmrg_status heff_launch_fp64(idmrg_ctx *c, const int *active_dev, const int *ac
   for (int q = 0; q < c->P; ++q)
     if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
   c->kbegin(IDMRG_K_HEFF_GEMM);
-  CK(launch_gemm_f64((const GemmTile *)c->dg1t.p, (int)c->g1.tiles.size(), (const GemmTask *)c->dg1k.p,
-                     (const GemmSeg *)c->dg1s.p, bufs, active_dev, c->st));
+  {
+    idmrg_status sg_ = gemm_run(c, c->tn_g1, c->dg1k, c->dg1s, active_dev);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
   c->kend(IDMRG_K_HEFF_GEMM, 0.0, 0.0);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_wstage_f64((const WTask *)c->dwt.p, (int)c->wl.tasks.size(), c->wl.max_rows, (const WTerm *)c->dwm.p,
                        bufs, active_dev, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
   c->kbegin(IDMRG_K_HEFF_GEMM);
-  CK(launch_gemm_f64((const GemmTile *)c->dg3t.p, (int)c->g3.tiles.size(), (const GemmTask *)c->dg3k.p,
-                     (const GemmSeg *)c->dg3s.p, bufs, active_dev, c->st));
+  {
+    idmrg_status sg_ = gemm_run(c, c->tn_g3, c->dg3k, c->dg3s, active_dev);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
   c->kend(IDMRG_K_HEFF_GEMM, gf, by);
   c->launches += 3;
   return IDMRG_OK;
@@ -903,15 +989,20 @@ idmrg_status predict(idmrg_ctx *c, int p) {
                           sg.k, A.rightB.dim[jB], 1);
           }
     }
-    c->gp.finish(64, 64);
+
     NOMEM(sync_bufs(c) == IDMRG_OK);
     NOMEM(c->upload(c->dst, c->stasks) && c->upload(c->dstab, c->stable));
-    NOMEM(c->upload(c->dgpt, c->gp.tiles) && c->upload(c->dgpk, c->gp.tasks) && c->upload(c->dgps, c->gp.segs));
+    {
+      idmrg_status sg = gemm_upload(c, c->gp, c->dgpk, c->dgps, c->tn_gp);
+      if (sg != IDMRG_OK) return sg;
+    }
     c->kbegin(IDMRG_K_PREDICT);
     CK(launch_scale_tasks((const ScaleTask *)c->dst.p, (int)c->stasks.size(), c->smax_rows,
                           (const double *)c->dstab.p, c->o.lambda_zero_rel, bufs, c->st));
-    CK(launch_gemm_f64((const GemmTile *)c->dgpt.p, (int)c->gp.tiles.size(), (const GemmTask *)c->dgpk.p,
-                       (const GemmSeg *)c->dgps.p, bufs, nullptr, c->st));
+    {
+    idmrg_status sg_ = gemm_run(c, c->tn_gp, c->dgpk, c->dgps, nullptr);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
     c->kend(IDMRG_K_PREDICT, c->gp.flops, 0.0);
     c->launches += 2;
   }
@@ -1259,9 +1350,6 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
     c->svdX.task(J.sb, BUF_SVD, J.w_off, ca, ca, ca);
     c->svdX.seg(BUF_SVD, J.j_off, ca, BUF_SVD, J.b_off, ca, ca, 0);
   }
-  c->svdG.finish(64, 64);
-  c->svdW.finish(64, 64);
-  c->svdX.finish(64, 64);
   NOMEM(c->ensure(c->siw, 4 * std::max(iw, 1)));
   NOMEM(c->upload(c->sjobs, c->jobs) && c->ensure(c->swork, 8 * std::max<int64_t>(work, 1)) &&
         c->ensure(c->ssv, 8 * std::max(sv, 1)) && c->upload(c->sjob0, c->tjob0) && c->upload(c->snjob, c->tnjob) &&
@@ -1269,9 +1357,12 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
         c->ensure(c->slam, 8 * std::max(sv, 1)) && c->ensure(c->seps, 8 * P) && c->ensure(c->sepsb, 8 * P) &&
         c->ensure(c->skept, 4 * P) && c->upload(c->sorder, c->torder) && c->upload(c->sorderq, c->torderq) &&
         c->ensure(c->slamk, 8 * (size_t)P * std::max(1, c->o.m)));
-  NOMEM(c->upload(c->dsgt, c->svdG.tiles) && c->upload(c->dsgk, c->svdG.tasks) && c->upload(c->dsgs, c->svdG.segs) &&
-        c->upload(c->dswt, c->svdW.tiles) && c->upload(c->dswk, c->svdW.tasks) && c->upload(c->dsws, c->svdW.segs) &&
-        c->upload(c->dsxt, c->svdX.tiles) && c->upload(c->dsxk, c->svdX.tasks) && c->upload(c->dsxs, c->svdX.segs));
+  for (auto [L, dk, ds, T] : {std::make_tuple(&c->svdG, &c->dsgk, &c->dsgs, &c->tn_svdG),
+                               std::make_tuple(&c->svdW, &c->dswk, &c->dsws, &c->tn_svdW),
+                               std::make_tuple(&c->svdX, &c->dsxk, &c->dsxs, &c->tn_svdX)}) {
+    idmrg_status sg = gemm_upload(c, *L, *dk, *ds, *T);
+    if (sg != IDMRG_OK) return sg;
+  }
   for (int q = 0; q < P; ++q) c->hbufs[q * NBUF + BUF_SVD] = c->dp(c->swork);
   NOMEM(sync_bufs(c) == IDMRG_OK);
   return IDMRG_OK;
@@ -1412,14 +1503,20 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   CK(launch_svd_jacobi32(dj, (const int *)c->sorder.p, nj, g, gcols, sw, (const int *)c->siw.p, c->st, c->side,
                          c->sev));
   for (int it = 0; it < 2; ++it) {
-    CK(launch_gemm_f64((const GemmTile *)c->dsgt.p, (int)c->svdG.tiles.size(), (const GemmTask *)c->dsgk.p,
-                       (const GemmSeg *)c->dsgs.p, svb, nullptr, c->st));
-    CK(launch_gemm_f64((const GemmTile *)c->dswt.p, (int)c->svdW.tiles.size(), (const GemmTask *)c->dswk.p,
-                       (const GemmSeg *)c->dsws.p, svb, nullptr, c->st));
+    {
+    idmrg_status sg_ = gemm_run(c, c->tn_svdG, c->dsgk, c->dsgs, nullptr);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
+    {
+    idmrg_status sg_ = gemm_run(c, c->tn_svdW, c->dswk, c->dsws, nullptr);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
     CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 1, sw, c->st));
   }
-  CK(launch_gemm_f64((const GemmTile *)c->dsxt.p, (int)c->svdX.tiles.size(), (const GemmTask *)c->dsxk.p,
-                     (const GemmSeg *)c->dsxs.p, svb, nullptr, c->st));
+  {
+    idmrg_status sg_ = gemm_run(c, c->tn_svdX, c->dsxk, c->dsxs, nullptr);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
   CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 2, sw, c->st));
   CK(launch_svd_jacobi(dj, (const int *)c->sorder.p, nj, g, gcols, sw, (int *)c->siw.p, c->dp(c->ssv),
                        (int *)c->derr.p, 1, c->st, c->side, c->sev));
@@ -1628,22 +1725,26 @@ idmrg_status update_envs(idmrg_ctx *c, int p) {
     idmrg_status s = env_build(c, q, c->genv1, c->genv3, c->wenv);
     if (s != IDMRG_OK) return s;
   }
-  c->genv1.finish(64, 64);
-  c->genv3.finish(64, 64);
   NOMEM(sync_bufs(c) == IDMRG_OK);
-  NOMEM(c->upload(c->dge1t, c->genv1.tiles) && c->upload(c->dge1k, c->genv1.tasks) &&
-        c->upload(c->dge1s, c->genv1.segs));
-  NOMEM(c->upload(c->dge3t, c->genv3.tiles) && c->upload(c->dge3k, c->genv3.tasks) &&
-        c->upload(c->dge3s, c->genv3.segs));
+  {
+    idmrg_status sg = gemm_upload(c, c->genv1, c->dge1k, c->dge1s, c->tn_env1);
+    if (sg != IDMRG_OK) return sg;
+    sg = gemm_upload(c, c->genv3, c->dge3k, c->dge3s, c->tn_env3);
+    if (sg != IDMRG_OK) return sg;
+  }
   NOMEM(c->upload(c->dwet, c->wenv.tasks) && c->upload(c->dwem, c->wenv.terms));
   double *const *bufs = (double *const *)c->dbufs.p;
   c->kbegin(IDMRG_K_ENV);
-  CK(launch_gemm_f64((const GemmTile *)c->dge1t.p, (int)c->genv1.tiles.size(), (const GemmTask *)c->dge1k.p,
-                     (const GemmSeg *)c->dge1s.p, bufs, nullptr, c->st));
+  {
+    idmrg_status sg_ = gemm_run(c, c->tn_env1, c->dge1k, c->dge1s, nullptr);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
   CK(launch_wstage_f64((const WTask *)c->dwet.p, (int)c->wenv.tasks.size(), c->wenv.max_rows,
                        (const WTerm *)c->dwem.p, bufs, nullptr, c->st));
-  CK(launch_gemm_f64((const GemmTile *)c->dge3t.p, (int)c->genv3.tiles.size(), (const GemmTask *)c->dge3k.p,
-                     (const GemmSeg *)c->dge3s.p, bufs, nullptr, c->st));
+  {
+    idmrg_status sg_ = gemm_run(c, c->tn_env3, c->dge3k, c->dge3s, nullptr);
+    if (sg_ != IDMRG_OK) return sg_;
+  }
   c->kend(IDMRG_K_ENV, c->genv1.flops + c->wenv.flops + c->genv3.flops, 0.0);
   c->launches += 3;
   for (int q = 0; q < P; ++q)
@@ -1837,14 +1938,14 @@ void idmrg_destroy(idmrg_ctx *c) {
   for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT, &c->bPA1,
                   &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP})
     for (auto &b : *v) rel(b);
-  for (DevBuf *b : {&c->dbufs, &c->dg1t, &c->dg1k, &c->dg1s, &c->dg3t, &c->dg3k, &c->dg3s, &c->dwt, &c->dwm, &c->ddt,
-                    &c->ddp, &c->drb, &c->dgpt, &c->dgpk, &c->dgps, &c->dst, &c->dstab, &c->dge1t, &c->dge1k,
-                    &c->dge1s, &c->dge3t, &c->dge3k, &c->dge3s, &c->dwet, &c->dwem, &c->dmask, &c->derr, &c->lN,
+  for (DevBuf *b : {&c->dbufs, &c->dg1k, &c->dg1s, &c->dg3k, &c->dg3s, &c->dwt, &c->dwm, &c->ddt,
+                    &c->ddp, &c->drb, &c->dgpk, &c->dgps, &c->dst, &c->dstab, &c->dge1k,
+                    &c->dge1s, &c->dge3k, &c->dge3s, &c->dwet, &c->dwem, &c->dmask, &c->derr, &c->lN,
                     &c->lV, &c->lw, &c->lalpha, &c->lbeta, &c->libeta, &c->lh, &c->lpart, &c->lk, &c->lmember, &c->lactive,
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
-                    &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgt, &c->dsgk, &c->dsgs, &c->dswt,
-                    &c->dswk, &c->dsws, &c->dsxt, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
+                    &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgk, &c->dsgs,
+                    &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
                     &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
@@ -1852,6 +1953,13 @@ void idmrg_destroy(idmrg_ctx *c) {
   for (cudaStream_t x : c->side)
     if (x) cudaStreamDestroy(x);
   if (c->pin_act) cudaFreeHost(c->pin_act);
+  for (GemmTune *t : {&c->tn_g1, &c->tn_g3, &c->tn_gp, &c->tn_env1, &c->tn_env3, &c->tn_svdG, &c->tn_svdW, &c->tn_svdX}) {
+    for (auto &b : t->tiles) rel(b);
+    for (int k = 0; k < GEMM_NSHAPE; ++k) {
+      if (t->e0[k]) cudaEventDestroy(t->e0[k]);
+      if (t->e1[k]) cudaEventDestroy(t->e1[k]);
+    }
+  }
   for (cudaEvent_t e : c->ev_act)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->sev)
@@ -2218,11 +2326,11 @@ extern "C" idmrg_status idmrg_heff_apply_noalloc(idmrg_ctx *c, int p, const doub
   CK(cudaMemcpyAsync(base + table_bytes, mask, sizeof(int) * (size_t)c->P, cudaMemcpyHostToDevice, c->st));
   double *const *bufs = (double *const *)base;
   const int *active = (const int *)(base + table_bytes);
-  CK(launch_gemm_f64((const GemmTile *)c->dg1t.p, (int)c->g1.tiles.size(), (const GemmTask *)c->dg1k.p,
-                     (const GemmSeg *)c->dg1s.p, bufs, active, c->st));
+  CK(launch_gemm_f64((const GemmTile *)c->tn_g1.tiles[GEMM_64x64].p, c->tn_g1.ntiles[GEMM_64x64],
+                     (const GemmTask *)c->dg1k.p, (const GemmSeg *)c->dg1s.p, bufs, active, c->st, GEMM_64x64));
   CK(launch_wstage_f64((const WTask *)c->dwt.p, (int)c->wl.tasks.size(), c->wl.max_rows, (const WTerm *)c->dwm.p,
                        bufs, active, c->st));
-  CK(launch_gemm_f64((const GemmTile *)c->dg3t.p, (int)c->g3.tiles.size(), (const GemmTask *)c->dg3k.p,
-                     (const GemmSeg *)c->dg3s.p, bufs, active, c->st));
+  CK(launch_gemm_f64((const GemmTile *)c->tn_g3.tiles[GEMM_64x64].p, c->tn_g3.ntiles[GEMM_64x64],
+                     (const GemmTask *)c->dg3k.p, (const GemmSeg *)c->dg3s.p, bufs, active, c->st, GEMM_64x64));
   return IDMRG_OK;
 }

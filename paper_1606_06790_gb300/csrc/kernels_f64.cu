@@ -16,20 +16,27 @@ namespace idmrg {
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
+// Tile shapes of the grouped GEMM: TM x TN outputs per CTA, 4 x 4 per
+// thread, K in steps of TK.  On this part one 64 x 64 tile holds an SM's
+// FP64 units for K x 2048 cycles, so the shape that wastes least in padding
+// and in the last wave differs between task lists; the host's autotuner
+// times each shape on real calls and keeps the fastest.
+constexpr int TK = 16;
 
-__global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTile *__restrict__ tiles,
-                                                       const GemmTask *__restrict__ tasks,
-                                                       const GemmSeg *__restrict__ segs,
-                                                       double *const *__restrict__ bufs,
-                                                       const int *__restrict__ active) {
+template <int TM, int TN>
+__global__ void __launch_bounds__(TM *TN / 16) gemm_f64_kernel(const GemmTile *__restrict__ tiles,
+                                                               const GemmTask *__restrict__ tasks,
+                                                               const GemmSeg *__restrict__ segs,
+                                                               double *const *__restrict__ bufs,
+                                                               const int *__restrict__ active) {
+  constexpr int NT = TM * TN / 16;
   __shared__ double As[TK][TM + 1];
   __shared__ double Bs[TK][TN + 1];
   const GemmTile tile = tiles[blockIdx.x];
   const GemmTask task = tasks[tile.task];
   if (active && !active[task.sb]) return;
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % (TN / 4), ty = tid / (TN / 4);
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -41,6 +48,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTile *__restrict
     const double *A = bufs[task.sb * NBUF + sg.a_buf] + sg.a_off;
     const double *B = bufs[task.sb * NBUF + sg.b_buf] + sg.b_off;
     const bool ta = sg.flags & 1, tb = sg.flags & 2;
+    const bool scale = sg.alpha != 1.0;
     for (int k0 = 0; k0 < sg.K; k0 += TK) {
       // A tile: TM x TK (op(A) rows m, cols k)
 #pragma unroll
@@ -51,7 +59,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTile *__restrict
         const int gm = tile.m0 + m, gk = k0 + k;
         double v = 0.0;
         if (gm < task.M && gk < sg.K) v = ta ? A[(int64_t)gk * sg.lda + gm] : A[(int64_t)gm * sg.lda + gk];
-        As[k][m] = v * sg.alpha;
+        As[k][m] = scale ? v * sg.alpha : v;
       }
 #pragma unroll
       for (int r = 0; r < (TN * TK) / NT; ++r) {
@@ -68,9 +76,9 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTile *__restrict
       for (int k = 0; k < TK; ++k) {
         double a[4], b[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+        for (int i = 0; i < 4; ++i) a[i] = As[k][ty + (TM / 4) * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+        for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + (TN / 4) * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -82,11 +90,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTile *__restrict
   double *C = bufs[task.sb * NBUF + task.c_buf] + task.c_off;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int gm = tile.m0 + ty + 16 * i;
+    const int gm = tile.m0 + ty + (TM / 4) * i;
     if (gm >= task.M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int gn = tile.n0 + tx + 16 * j;
+      const int gn = tile.n0 + tx + (TN / 4) * j;
       if (gn >= task.N) continue;
       double *p = C + (int64_t)gm * task.ldc + gn;
       *p = task.accumulate ? *p + acc[i][j] : acc[i][j];
@@ -188,8 +196,14 @@ __global__ void scale_tasks_kernel(const ScaleTask *__restrict__ tasks, const do
 }  // namespace
 
 cudaError_t launch_gemm_f64(const GemmTile *tiles, int ntiles, const GemmTask *tasks, const GemmSeg *segs,
-                            double *const *bufs, const int *active, cudaStream_t st) {
-  if (ntiles > 0) gemm_f64_kernel<<<ntiles, NT, 0, st>>>(tiles, tasks, segs, bufs, active);
+                            double *const *bufs, const int *active, cudaStream_t st, int shape) {
+  if (ntiles <= 0) return cudaGetLastError();
+  switch (shape) {
+    case GEMM_64x64: gemm_f64_kernel<64, 64><<<ntiles, 256, 0, st>>>(tiles, tasks, segs, bufs, active); break;
+    case GEMM_64x32: gemm_f64_kernel<64, 32><<<ntiles, 128, 0, st>>>(tiles, tasks, segs, bufs, active); break;
+    case GEMM_32x64: gemm_f64_kernel<32, 64><<<ntiles, 128, 0, st>>>(tiles, tasks, segs, bufs, active); break;
+    default: gemm_f64_kernel<32, 32><<<ntiles, 64, 0, st>>>(tiles, tasks, segs, bufs, active); break;
+  }
   return cudaGetLastError();
 }
 
