@@ -241,8 +241,11 @@ def run_reference(args):
 
 
 def timed_run(pkg, mpo, m: int, prec: str, steps: int, warmup: int, dev, flush, dist, with_clocks: bool, local: int):
-    """Saturate, warm up, then time `steps` unit-cell steps with CUDA events on
-    the context's stream (L2 flushed before each step, outside the events)."""
+    """Saturate, warm up, then two timed regions of `steps` unit-cell steps,
+    each step bracketed by CUDA events on the context's stream with the L2
+    flushed before it (outside the events): the first without per-class
+    timers (the step time, e2e wall clock and clocks), the second with the
+    per-class event timers on (kernel classes and rooflines)."""
     import torch
     ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=prec)
     for _ in range(SATURATE):
@@ -250,40 +253,48 @@ def timed_run(pkg, mpo, m: int, prec: str, steps: int, warmup: int, dev, flush, 
     for _ in range(max(warmup, 3)):
         ctx.unit_cell_step()
     stream = ctx.stream
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    clocks = Clocks(local) if with_clocks else None
-    launches0 = ctx.launch_count()
-    h2d0, d2h0 = ctx.transfer_bytes()
-    ctx.profile_enable(True)
-    if dist is not None and dist.is_initialized():
-        dist.barrier()
-    torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-    torch.cuda.nvtx.range_push("timed")
-    wall, reports = [], []
-    for k in range(steps):
-        flush.zero_()
+
+    def region(profiled: bool, clocks):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches0 = ctx.launch_count()
+        h2d0, d2h0 = ctx.transfer_bytes()
+        ctx.profile_enable(profiled)
+        if dist is not None and dist.is_initialized():
+            dist.barrier()
         torch.cuda.synchronize()
-        t = time.perf_counter()
-        ev[k][0].record(stream)
-        reports.append(ctx.unit_cell_step())
-        ev[k][1].record(stream)
+        if clocks:
+            clocks.start()
+        torch.cuda.nvtx.range_push("timed")
+        wall, reports = [], []
+        for k in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ev[k][0].record(stream)
+            reports.append(ctx.unit_cell_step())
+            ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            wall.append(time.perf_counter() - t)
         torch.cuda.synchronize()
-        wall.append(time.perf_counter() - t)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    clk = clocks.stop() if clocks else None
-    if dist is not None and dist.is_initialized():
-        dist.barrier()
-    step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    res = {"ctx": ctx, "step_ms": step_ms, "wall_s": sum(wall), "reports": reports, "prof": prof, "clocks": clk,
-           "launches": ctx.launch_count() - launches0}
-    h2d1, d2h1 = ctx.transfer_bytes()
-    res["h2d"] = (h2d1 - h2d0) // steps
-    res["d2h"] = (d2h1 - d2h0) // steps
+        torch.cuda.nvtx.range_pop()
+        clk = clocks.stop() if clocks else None
+        if dist is not None and dist.is_initialized():
+            dist.barrier()
+        out = {"step_ms": sum(a.elapsed_time(b) for a, b in ev), "wall_s": sum(wall), "reports": reports,
+               "clocks": clk, "launches": ctx.launch_count() - launches0}
+        h2d1, d2h1 = ctx.transfer_bytes()
+        out["h2d"] = (h2d1 - h2d0) // steps
+        out["d2h"] = (d2h1 - d2h0) // steps
+        if profiled:
+            out["prof"] = ctx.profile_read()
+        ctx.profile_enable(False)
+        return out
+
+    res = region(False, Clocks(local) if with_clocks else None)
+    prof = region(True, None)
+    res["prof"] = prof["prof"]
+    res["prof_step_ms"] = prof["step_ms"]
+    res["ctx"] = ctx
     return res
 
 
@@ -372,6 +383,8 @@ def main():
                 "h2d_bytes_per_step": run["h2d"], "d2h_bytes_per_step": run["d2h"],
                 "note": "wall clock around idmrg_unit_cell_step: host block tables in, step report out"},
         "kernels": kernels,
+        "kernels_note": ("per-class CUDA-event timers of a second timed region of the same length "
+                         f"({run['prof_step_ms'] / args.steps:.2f} ms per step with the timers on)"),
         "svd": ctx.svd_stats(),
         "heff": {"flops_per_matvec_all_superblocks": flops,
                  "lanczos_iters_last_step": [int(x) for x in last["iters"]]},
