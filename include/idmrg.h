@@ -200,6 +200,17 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *ctx, idmrg_step_report *rep);
  * (e^(-1)_1 = 0) and the n it belongs to; ESTATE if there is none yet. */
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *ctx, double *e_g, int *n_of_estimate);
 
+/* Checkpoint between unit-cell steps (Step 7): the iteration n, the history
+ * of e^(n)_1 behind Step 5', every pair's current environments (Step 6) and
+ * the last two truncations (bases, U, V, lambda) that the prediction of
+ * Step 3' reads.  idmrg_save writes them to `path` (binary, host byte order);
+ * idmrg_load reads them into a context created with the same MPO and options
+ * (checked: EINVAL otherwise), which then continues exactly as the saved one
+ * would.  Both synchronise the context's stream; ESTATE while a step is in
+ * progress; EINVAL on I/O errors or a damaged file. */
+idmrg_status idmrg_save(const idmrg_ctx *ctx, const char *path);
+idmrg_status idmrg_load(idmrg_ctx *ctx, const char *path);
+
 /* Measured work of the last heff_apply call: algorithmic flops (sum over
  * GEMM tasks of 2 M N K plus 2 per element per two-site MPO term) and the
  * bytes of L, R, psi in and out. */

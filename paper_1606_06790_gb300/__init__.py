@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
-    "idmrg_svd_stats",
+    "idmrg_svd_stats", "idmrg_save", "idmrg_load",
 ]
 
 KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
@@ -112,6 +112,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_profile_read": (i, [vp, i, P(d), P(C.c_uint64), P(d), P(d)]),
         "idmrg_transfer_bytes": (i, [vp, P(C.c_uint64), P(C.c_uint64)]),
         "idmrg_heff_apply_noalloc": (i, [vp, i, vp, vp]),
+        "idmrg_save": (i, [vp, C.c_char_p]),
+        "idmrg_load": (i, [vp, C.c_char_p]),
         "idmrg_svd_stats": (i, [vp, P(i), P(i), P(i), P(i), P(d)]),
     }
     for name, (res, args) in sig.items():
@@ -292,6 +294,14 @@ class Context:
         out: Dict[str, object] = dict(n=rep.n, converged=(s == 0), **arr, **iarr)
         out["e_g"] = None if math.isnan(rep.e_g) else rep.e_g
         return out
+
+    def save(self, path: str) -> None:
+        """Checkpoint between steps (idmrg_save)."""
+        self._check(self.lib.idmrg_save(self.h, os.fsencode(path)), "save")
+
+    def load(self, path: str) -> None:
+        """Restore a checkpoint of the same MPO and options (idmrg_load)."""
+        self._check(self.lib.idmrg_load(self.h, os.fsencode(path)), "load")
 
     def energy_per_site(self):
         e, n = C.c_double(), C.c_int()

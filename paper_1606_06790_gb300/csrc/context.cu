@@ -1784,6 +1784,95 @@ idmrg_status advance(idmrg_ctx *c) {
 // ==========================================================================
 // C ABI
 // ==========================================================================
+// checkpoint file helpers (idmrg_save / idmrg_load)
+namespace {
+constexpr char CK_MAGIC[8] = {'I', 'D', 'M', 'R', 'G', 'C', 'K', '1'};
+
+struct CkFile {
+  FILE *f = nullptr;
+  bool ok = true;
+  ~CkFile() {
+    if (f) fclose(f);
+  }
+  template <class T>
+  void put(const T &v) {
+    ok = ok && fwrite(&v, sizeof(T), 1, f) == 1;
+  }
+  template <class T>
+  void putv(const std::vector<T> &v) {
+    put((int64_t)v.size());
+    if (!v.empty()) ok = ok && fwrite(v.data(), sizeof(T), v.size(), f) == v.size();
+  }
+  template <class T>
+  void get(T &v) {
+    ok = ok && fread(&v, sizeof(T), 1, f) == 1;
+  }
+  template <class T>
+  void getv(std::vector<T> &v, int64_t cap = (int64_t)1 << 40) {
+    int64_t n = 0;
+    get(n);
+    if (!ok || n < 0 || n > cap) {
+      ok = false;
+      return;
+    }
+    v.resize((size_t)n);
+    if (n > 0) ok = ok && fread(v.data(), sizeof(T), (size_t)n, f) == (size_t)n;
+  }
+};
+
+void ck_put_basis(CkFile &F, const Basis &b) {
+  F.putv(b.q);
+  F.putv(b.dim);
+}
+void ck_get_basis(CkFile &F, Basis &b) {
+  b.clear();
+  F.getv(b.q);
+  F.getv(b.dim);
+  if (b.q.size() != b.dim.size()) F.ok = false;
+  b.finish();
+}
+void ck_put_sec(CkFile &F, const SecInfo &si) {
+  F.put(si.Q);
+  F.put(si.k);
+  F.put(si.r);
+  F.put(si.c);
+  F.put(si.job);
+  F.put(si.u_off);
+  F.put(si.v_off);
+  F.put(si.lam_off);
+  F.putv(si.rg);
+  F.putv(si.cg);
+}
+void ck_get_sec(CkFile &F, SecInfo &si) {
+  F.get(si.Q);
+  F.get(si.k);
+  F.get(si.r);
+  F.get(si.c);
+  F.get(si.job);
+  F.get(si.u_off);
+  F.get(si.v_off);
+  F.get(si.lam_off);
+  F.getv(si.rg);
+  F.getv(si.cg);
+}
+}  // namespace
+
+idmrg_status ck_put_dev(idmrg_ctx *c, CkFile &F, const DevBuf &b, int64_t n) {
+  std::vector<double> h((size_t)std::max<int64_t>(n, 0));
+  if (n > 0) CK(cudaMemcpy(h.data(), b.p, 8 * (size_t)n, cudaMemcpyDeviceToHost));
+  F.putv(h);
+  return IDMRG_OK;
+}
+
+idmrg_status ck_get_dev(idmrg_ctx *c, CkFile &F, DevBuf &b, int64_t n) {
+  std::vector<double> h;
+  F.getv(h, n);
+  if (!F.ok || (int64_t)h.size() != n) return c->fail(IDMRG_EINVAL, "load: checkpoint truncated or inconsistent");
+  NOMEM(c->ensure(b, 8 * (size_t)std::max<int64_t>(n, 1)));
+  if (n > 0) CK(cudaMemcpy(b.p, h.data(), 8 * (size_t)n, cudaMemcpyHostToDevice));
+  return IDMRG_OK;
+}
+
 extern "C" {
 
 void idmrg_default_opts(idmrg_opts *o) {
@@ -2194,6 +2283,150 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {
     rep->e_g = (c->eg_n == n_done) ? c->eg_last : NAN;
   }
   return sl;
+}
+
+// ------------------------------------------------------------------------
+// Checkpoint between unit-cell steps: n, the e_g bookkeeping, every pair's
+// current environments and the last two truncations (bases, sector tables,
+// U, V, lambda) that the prediction reads.  Binary, host byte order.
+// ------------------------------------------------------------------------
+idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
+  if (!cc || !path) return IDMRG_EINVAL;
+  idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);  // errors are recorded in the context
+  for (int q = 0; q < c->P; ++q)
+    if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "save: a step is in progress");
+  CK(cudaStreamSynchronize(c->st));
+  CkFile F;
+  F.f = fopen(path, "wb");
+  if (!F.f) return c->fail(IDMRG_EINVAL, "save: cannot open %s", path);
+  F.ok = fwrite(CK_MAGIC, 1, 8, F.f) == 8;
+  F.put(c->ell);
+  F.put(c->d);
+  F.put(c->P);
+  F.put(c->o.m);
+  F.put((int)c->o.prec);
+  F.put(c->o.target_charge);
+  F.putv(c->adim);
+  F.put(c->n);
+  F.put(c->eg_n);
+  F.put(c->eg_last);
+  std::vector<int> e1n;
+  std::vector<double> e1v;
+  for (const auto &kv : c->e1) {
+    e1n.push_back(kv.first);
+    e1v.push_back(kv.second);
+  }
+  F.putv(e1n);
+  F.putv(e1v);
+  for (int q = 0; q < c->P; ++q) {
+    for (const Env *E : {&c->envL[q], &c->envR[q]}) {
+      ck_put_basis(F, E->lay.b);
+      F.putv(E->lay.chq);
+      idmrg_status s = ck_put_dev(c, F, E->data, E->lay.size);
+      if (s != IDMRG_OK) return s;
+    }
+    for (const TruncRec *T : {&c->prev[q], &c->prev2[q]}) {
+      F.put((int)T->valid);
+      ck_put_basis(F, T->leftB);
+      ck_put_basis(F, T->rightB);
+      ck_put_basis(F, T->bU);
+      ck_put_basis(F, T->bV);
+      F.put((int64_t)T->sec.size());
+      for (const SecInfo &si : T->sec) ck_put_sec(F, si);
+      F.putv(T->lam);
+      F.putv(T->lam_all);
+      F.put(T->eps);
+      F.put(T->eps_best);
+      F.put(T->usize);
+      F.put(T->vsize);
+      idmrg_status s = ck_put_dev(c, F, T->U, T->valid ? T->usize : 0);
+      if (s != IDMRG_OK) return s;
+      s = ck_put_dev(c, F, T->V, T->valid ? T->vsize : 0);
+      if (s != IDMRG_OK) return s;
+    }
+  }
+  if (!F.ok) return c->fail(IDMRG_EINVAL, "save: write to %s failed", path);
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
+  if (!c || !path) return IDMRG_EINVAL;
+  for (int q = 0; q < c->P; ++q)
+    if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "load: a step is in progress");
+  CkFile F;
+  F.f = fopen(path, "rb");
+  if (!F.f) return c->fail(IDMRG_EINVAL, "load: cannot open %s", path);
+  char magic[8] = {};
+  F.ok = fread(magic, 1, 8, F.f) == 8 && memcmp(magic, CK_MAGIC, 8) == 0;
+  int ell = 0, d = 0, P = 0, m = 0, prec = 0, target = 0;
+  std::vector<int> adim;
+  F.get(ell);
+  F.get(d);
+  F.get(P);
+  F.get(m);
+  F.get(prec);
+  F.get(target);
+  F.getv(adim, 1 << 20);
+  if (!F.ok || ell != c->ell || d != c->d || P != c->P || m != c->o.m || prec != (int)c->o.prec ||
+      target != c->o.target_charge || adim != c->adim)
+    return c->fail(IDMRG_EINVAL, "load: %s is not a checkpoint of this MPO and these options", path);
+  int n = 0, eg_n = 0;
+  double eg_last = 0.0;
+  std::vector<int> e1n;
+  std::vector<double> e1v;
+  F.get(n);
+  F.get(eg_n);
+  F.get(eg_last);
+  F.getv(e1n, 1 << 30);
+  F.getv(e1v, 1 << 30);
+  if (!F.ok || n < 1 || e1n.size() != e1v.size()) return c->fail(IDMRG_EINVAL, "load: checkpoint header damaged");
+  for (int q = 0; q < P; ++q) {
+    for (Env *E : {&c->envL[q], &c->envR[q]}) {
+      Basis b;
+      std::vector<int> chq;
+      ck_get_basis(F, b);
+      F.getv(chq, 1 << 20);
+      if (!F.ok) return c->fail(IDMRG_EINVAL, "load: checkpoint truncated");
+      E->lay.build(b, chq);
+      idmrg_status s = ck_get_dev(c, F, E->data, E->lay.size);
+      if (s != IDMRG_OK) return s;
+    }
+    for (TruncRec *T : {&c->prev[q], &c->prev2[q]}) {
+      const DevBuf keepU = T->U, keepV = T->V;
+      *T = TruncRec();
+      T->U = keepU;
+      T->V = keepV;
+      int valid = 0;
+      F.get(valid);
+      T->valid = valid != 0;
+      ck_get_basis(F, T->leftB);
+      ck_get_basis(F, T->rightB);
+      ck_get_basis(F, T->bU);
+      ck_get_basis(F, T->bV);
+      int64_t ns = 0;
+      F.get(ns);
+      if (!F.ok || ns < 0 || ns > (1 << 20)) return c->fail(IDMRG_EINVAL, "load: checkpoint truncated");
+      T->sec.resize((size_t)ns);
+      for (SecInfo &si : T->sec) ck_get_sec(F, si);
+      F.getv(T->lam);
+      F.getv(T->lam_all);
+      F.get(T->eps);
+      F.get(T->eps_best);
+      F.get(T->usize);
+      F.get(T->vsize);
+      if (!F.ok) return c->fail(IDMRG_EINVAL, "load: checkpoint truncated");
+      idmrg_status s = ck_get_dev(c, F, T->U, T->valid ? T->usize : 0);
+      if (s != IDMRG_OK) return s;
+      s = ck_get_dev(c, F, T->V, T->valid ? T->vsize : 0);
+      if (s != IDMRG_OK) return s;
+    }
+  }
+  c->n = n;
+  c->eg_n = eg_n;
+  c->eg_last = eg_last;
+  c->e1.clear();
+  for (size_t k = 0; k < e1n.size(); ++k) c->e1[e1n[k]] = e1v[k];
+  return plan_iteration(c);
 }
 
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *c, double *e_g, int *n_of_estimate) {
