@@ -1014,6 +1014,30 @@ idmrg_status predict(idmrg_ctx *c, int p) {
 // ------------------------------------------------------------------------
 // Step 3: batched Lanczos
 // ------------------------------------------------------------------------
+// One Lanczos iteration of every active superblock: matvec (FP64 or on the
+// tensor cores), three-term step, full re-orthogonalisation pass,
+// tridiagonal solve and convergence test, next Krylov vector.  `act` and
+// `vb` only feed the per-class timers (act may be null).
+idmrg_status lanczos_iteration(idmrg_ctx *c, const LanczosDev &L, bool fp64, const int *act, double vb) {
+  CK(lanczos_set_ptrs(L, (double **)c->dbufs.p, c->st));
+  idmrg_status s = heff_launch(c, L.active, act, fp64);
+  if (s != IDMRG_OK) return s;
+  c->kbegin(IDMRG_K_LANCZOS_VEC);
+  CK(lanczos_project(L, 0, c->st));
+  CK(lanczos_subtract(L, 0, c->st));
+  CK(lanczos_project(L, 1, c->st));
+  CK(lanczos_subtract(L, 1, c->st));
+  c->kend(IDMRG_K_LANCZOS_VEC, 0.0, vb);
+  c->kbegin(IDMRG_K_LANCZOS_TRI);
+  CK(lanczos_finalize(L, c->st));
+  c->kend(IDMRG_K_LANCZOS_TRI);
+  c->kbegin(IDMRG_K_LANCZOS_VEC);
+  CK(lanczos_next(L, c->st));
+  c->kend(IDMRG_K_LANCZOS_VEC);
+  c->launches += 7;
+  return IDMRG_OK;
+}
+
 idmrg_status lanczos(idmrg_ctx *c, int p) {
   const int P = c->P;
   for (int q = 0; q < P; ++q)
@@ -1087,6 +1111,18 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   std::vector<double> nrm2(P, 0.0), theta(P, 0.0), dots(P, 0.0);
   std::vector<int> act(P), kk(P), conv(P), total(P, 0), final_(P, 0);
   bool allconv = true;
+  // graphs of one iteration ([1]: FP64 matvec, [0]: reduced precision),
+  // captured on first use in this solve
+  cudaGraphExec_t iter_graph[2] = {nullptr, nullptr};
+  uint64_t graph_launches[2] = {0, 0};
+  bool graph_ok = true;
+  struct GraphGuard {
+    cudaGraphExec_t *g;
+    ~GraphGuard() {
+      for (int k = 0; k < 2; ++k)
+        if (g[k]) cudaGraphExecDestroy(g[k]);
+    }
+  } graph_guard{iter_graph};
   for (int r = 0; r < max_restarts; ++r) {
     bool anym = false;
     for (int q = 0; q < P; ++q) anym |= member[q] != 0;
@@ -1096,26 +1132,41 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
     c->launches += 3;
     if (r == 0) CK(c->d2h_copy(nrm2.data(), c->lresid.p, 8 * P));  // ||psi~|| for the report
     for (int it = 0; it < inner_cap; ++it) {
-      CK(lanczos_set_ptrs(L, (double **)c->dbufs.p, c->st));
-      idmrg_status s = heff_launch(c, L.active, it == 0 ? member.data() : act.data(), it == 0);
-      if (s != IDMRG_OK) return s;
-      double vb = 0.0;
-      for (int q = 0; q < P; ++q)
-        // three-term step 6 N, full pass (k + 2) N + (k + 3) N, k = it
-        if (it == 0 ? member[q] : act[q]) vb += 8.0 * (double)N[q] * (2.0 * it + 11.0);
-      c->kbegin(IDMRG_K_LANCZOS_VEC);
-      CK(lanczos_project(L, 0, c->st));
-      CK(lanczos_subtract(L, 0, c->st));
-      CK(lanczos_project(L, 1, c->st));
-      CK(lanczos_subtract(L, 1, c->st));
-      c->kend(IDMRG_K_LANCZOS_VEC, 0.0, vb);
-      c->kbegin(IDMRG_K_LANCZOS_TRI);
-      CK(lanczos_finalize(L, c->st));
-      c->kend(IDMRG_K_LANCZOS_TRI);
-      c->kbegin(IDMRG_K_LANCZOS_VEC);
-      CK(lanczos_next(L, c->st));
-      c->kend(IDMRG_K_LANCZOS_VEC);
-      c->launches += 7;
+      // the same iteration as a graph once the kernels of its matvec are
+      // fixed (reduced precision, or FP64 with tuned GEMM tiles)
+      const bool fp64 = it == 0 || !c->mixed;
+      const bool as_graph = graph_ok && !c->prof &&
+                            (fp64 ? (!c->mixed && c->tn_g1.choice >= 0 && c->tn_g3.choice >= 0) : true);
+      if (as_graph && !iter_graph[fp64]) {
+        const uint64_t l0 = c->launches, mm0 = c->mixed_matvecs, fm0 = c->fp64_matvecs;
+        cudaGraph_t g = nullptr;
+        bool okc = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        idmrg_status sc = okc ? lanczos_iteration(c, L, fp64, nullptr, 0.0) : IDMRG_ECUDA;
+        okc = (cudaStreamEndCapture(c->st, &g) == cudaSuccess) && okc && sc == IDMRG_OK;
+        okc = okc && cudaGraphInstantiate(&iter_graph[fp64], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        graph_launches[fp64] = c->launches - l0;
+        c->launches = l0;
+        c->mixed_matvecs = mm0;
+        c->fp64_matvecs = fm0;
+        if (!okc) {  // capture refused: stay with direct launches
+          cudaGetLastError();
+          iter_graph[fp64] = nullptr;
+          graph_ok = false;
+        }
+      }
+      if (as_graph && iter_graph[fp64]) {
+        CK(cudaGraphLaunch(iter_graph[fp64], c->st));
+        c->launches += graph_launches[fp64];
+        (fp64 ? c->fp64_matvecs : c->mixed_matvecs) += 1;
+      } else {
+        double vb = 0.0;
+        for (int q = 0; q < P; ++q)
+          // three-term step 6 N, full pass (k + 2) N + (k + 3) N, k = it
+          if (it == 0 ? member[q] : act[q]) vb += 8.0 * (double)N[q] * (2.0 * it + 11.0);
+        idmrg_status s = lanczos_iteration(c, L, fp64, it == 0 ? member.data() : act.data(), vb);
+        if (s != IDMRG_OK) return s;
+      }
       // the active flags after this iteration go to pinned memory; the host
       // reads those of the previous iteration, so the next iteration is
       // already queued while it waits (an iteration launched after the last

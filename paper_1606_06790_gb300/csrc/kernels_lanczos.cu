@@ -157,15 +157,19 @@ __global__ void finalize_kernel(LanczosDev L) {
   const int lane = threadIdx.x;
   const int64_t N = L.N[s];
   const int nch = (int)((N + CH - 1) / CH);
-  // alpha_k from both Gram-Schmidt passes, beta_k = |w|
-  if (lane == 0) {
-    const double alpha = L.h[(int64_t)(0 * L.S + s) * km + kk] + L.h[(int64_t)(1 * L.S + s) * km + kk];
+  // alpha_k from both Gram-Schmidt passes, beta_k = |w| (partials summed by
+  // the whole warp: a serial FP64 chain costs 64 cycles per term here)
+  {
     const double *p = L.part + (((int64_t)2 * L.S + s) * km + 0) * L.nchunk_max;
     double nn = 0.0;
-    for (int c = 0; c < nch; ++c) nn += p[c];
-    L.alpha[s * km + kk] = alpha;
-    L.resid[s] = sqrt(nn);  // beta_k, stored provisionally
-    if (!isfinite(alpha) || !isfinite(nn)) atomicOr(L.err, IDMRG_DEV_ERR_NUMERIC);
+    for (int c = lane; c < nch; c += 32) nn += p[c];
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane == 0) {
+      const double alpha = L.h[(int64_t)(0 * L.S + s) * km + kk] + L.h[(int64_t)(1 * L.S + s) * km + kk];
+      L.alpha[s * km + kk] = alpha;
+      L.resid[s] = sqrt(nn);  // beta_k, stored provisionally
+      if (!isfinite(alpha) || !isfinite(nn)) atomicOr(L.err, IDMRG_DEV_ERR_NUMERIC);
+    }
   }
   __syncwarp();
   for (int i = lane; i < n; i += 32) {
@@ -214,34 +218,49 @@ __global__ void finalize_kernel(LanczosDev L) {
     if (fhi - flo <= 4e-7f * fmaxf(fabsf(flo), fabsf(fhi)) + 1e-30f) break;
   }
   const double shift = 0.5 * ((double)flo + (double)fhi);
-  if (lane == 0) {
-    // Eigenvector by the backward three-term recurrence at shift theta
-    // (rows n-1 .. 1 of (T - theta) y = 0 with y_{n-1} = 1): this is one step
-    // of inverse iteration applied to e_0, stable because the lowest Ritz
-    // vector grows towards j = 0, and it needs no division (1/beta_j is kept
-    // from the iteration that produced beta_j).  The residual left in row 0,
-    // r, gives the Rayleigh quotient theta + r y_0 / |y|^2, which converges
-    // cubically from the FP32 bracket.
-    const double *ib = L.ibeta + (int64_t)s * km;
-    double theta = shift, nrm2 = 1.0;
-    for (int it = 0; it < 4; ++it) {
+  // Eigenvector by the backward three-term recurrence at shift theta (rows
+  // n-1 .. 1 of (T - theta) y = 0 with y_{n-1} = 1): one step of inverse
+  // iteration applied to e_0, stable because the lowest Ritz vector grows
+  // towards j = 0, and division-free (1/beta_j is kept from the iteration
+  // that produced beta_j).  The residual left in row 0, r, gives the
+  // Rayleigh quotient theta + r y_0 / |y|^2, which converges cubically from
+  // the FP32 bracket.  Lane 0 runs the recurrence; theta - a_j, the norm and
+  // the scaling are spread over the warp.
+  const double *ib = L.ibeta + (int64_t)s * km;
+  double *dd = sm + 5 * km;  // theta - a_j, after the FP32 copies (2 km floats at sm + 4 km)
+  double theta = shift, nrm2 = 1.0;
+  for (int it = 0; it < 4; ++it) {
+    for (int i = lane; i < n; i += 32) dd[i] = theta - a[i];
+    __syncwarp();
+    if (lane == 0) {
       x[n - 1] = 1.0;
-      if (n >= 2) x[n - 2] = (theta - a[n - 1]) * ib[n - 2];
+      if (n >= 2) x[n - 2] = dd[n - 1] * ib[n - 2];
       for (int j = n - 2; j >= 1; --j) {
-        x[j - 1] = fma(theta - a[j], x[j], -b[j] * x[j + 1]) * ib[j - 1];
+        x[j - 1] = fma(dd[j], x[j], -b[j] * x[j + 1]) * ib[j - 1];
         if (fabs(x[j - 1]) > 1e150)
           for (int i = j - 1; i < n; ++i) x[i] *= 1e-150;
       }
-      const double r = (n >= 2) ? fma(a[0] - theta, x[0], b[0] * x[1]) : (a[0] - theta) * x[0];
-      nrm2 = 0.0;
-      for (int i = 0; i < n; ++i) nrm2 = fma(x[i], x[i], nrm2);
-      const double dth = r * x[0] / nrm2;
-      theta += dth;
-      if (!(fabs(dth) > 2.0 * DBL_EPSILON * fabs(theta))) break;
     }
+    __syncwarp();
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) s2 = fma(x[i], x[i], s2);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    nrm2 = s2;
+    const double r = (n >= 2) ? fma(-dd[0], x[0], b[0] * x[1]) : -dd[0] * x[0];
+    const double dth = r * x[0] / nrm2;
+    theta += dth;
+    __syncwarp();
+    if (!(fabs(dth) > 2.0 * DBL_EPSILON * fabs(theta))) break;
+  }
+  {
     const double inv = 1.0 / sqrt(nrm2);
-    for (int i = 0; i < n; ++i) x[i] *= inv;
-    for (int i = 0; i < n; ++i) L.y[s * km + i] = x[i];
+    for (int i = lane; i < n; i += 32) {
+      x[i] *= inv;
+      L.y[s * km + i] = x[i];
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
     const double scale = fmax(1.0, fabs(theta));
     const double res = beta_k * fabs(x[n - 1]);
     L.theta[s] = theta;
@@ -389,7 +408,7 @@ cudaError_t lanczos_subtract(const LanczosDev &L, int pass, cudaStream_t st) {
 }
 
 cudaError_t lanczos_finalize(const LanczosDev &L, cudaStream_t st) {
-  const size_t smem = (size_t)L.kmax * (4 * sizeof(double) + 2 * sizeof(float));
+  const size_t smem = (size_t)L.kmax * 6 * sizeof(double);  // a, b, b^2, x, FP32 copies, theta - a
   finalize_kernel<<<L.S, 32, smem, st>>>(L);
   return cudaGetLastError();
 }
