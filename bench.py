@@ -11,7 +11,7 @@ The headline is the mixed-precision path (H_eff psi on the tensor cores in
 TF32x3, Lanczos and SVD in FP64); the same run times the FP64 path on the
 same workload and reports the largest |dE/site| between the two.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|fp64] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|bf16x3|fp64] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own
 disorder realisation (seed 1606 + rank): independent problems, no exchange.
@@ -153,16 +153,18 @@ def class_roofline(name: str, d: dict, prec: str, pk: dict):
 
     FP64 arithmetic (SVD, FP64 H_eff, environments, prediction) is bound by
     the FP64 units: 152 SMs x 2 FMA/clk x 2.07 GHz; the reduced-precision
-    H_eff by the TF32 tensor pipe (measured sustained bf16 x nominal
-    tf32/bf16); the Lanczos vector kernels by HBM bandwidth."""
+    H_eff by the tensor pipe of its split type (measured sustained bf16, times
+    the nominal tf32/bf16 ratio for TF32); the Lanczos vector kernels by HBM
+    bandwidth."""
     sec = d["ms"] * 1e-3
     out = {"kernel": name, "launch_ms": d["ms"] / max(d["launches"], 1), "traffic": traffic_for(name, prec)}
     if name in ("heff_gemm", "heff_wstage") and prec != "fp64":
-        peak = pk["bf16_sustained"] * (1.1 / 2.25)
+        bf = prec == "bf16x3"
+        peak = pk["bf16_sustained"] * (1.0 if bf else 1.1 / 2.25)
         achieved = d["flops"] / sec / 1e12 if sec > 0 else 0.0
+        src = "sustained bf16" if bf else "sustained bf16 x nominal tf32/bf16 (1.1/2.25)"
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": f"{pk['src']} sustained bf16 x nominal tf32/bf16 (1.1/2.25); "
-                                   "split products counted once"})
+                    "peak_source": f"{pk['src']} {src}; split products counted once"})
     elif name in ("heff_gemm", "heff_wstage", "svd", "env", "predict"):
         achieved = d["flops"] / sec / 1e9 if sec > 0 else 0.0
         out.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
@@ -317,7 +319,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--m", type=int, default=256)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

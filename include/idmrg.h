@@ -53,7 +53,8 @@ typedef enum {
   IDMRG_TF32X3 = 1,  /* tensor cores, TF32 split (hi/lo) operands, three
                         products per term, FP32 accumulation; energies refined
                         by an FP64 Rayleigh quotient                          */
-  IDMRG_BF16X3 = 2   /* as TF32X3 with BF16 splits                           */
+  IDMRG_BF16X3 = 2   /* as TF32X3 with BF16 splits (kind::f16 MMAs, ~16 bits
+                        per product, twice the K per instruction)             */
 } idmrg_precision;
 
 /* The MPO of one period (Sec. 2, Eq. mpo; Sec. 3, Eq. mpo2).  Host memory,

@@ -194,6 +194,12 @@ cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_e
                                     int psi_buf, double *work, cudaStream_t st);
 cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, double *work, int *iwork, double zero_rel,
                             cudaStream_t st);
+// the pivoted QR on thread-block clusters (groups as launch_svd_jacobi);
+// rows[k], cols[k]: largest rows and columns of block group k+1
+size_t svd_qrc_smem(int rows, int cols, int csize);
+cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *rows,
+                                    const int *cols, double *work, int *iwork, double zero_rel, cudaStream_t st,
+                                    const cudaStream_t *side, const cudaEvent_t *ev);
 // Jacobi groups and shared memory: see kernels_svd.cu
 constexpr size_t SVD_BLOCK_SMEM_MAX = 200 * 1024;
 size_t svd_block_smem(int cols, int csize);
@@ -231,9 +237,10 @@ cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj
                                double *const *bufs, double *lam, cudaStream_t st);
 
 // ---- tensor-core path (kernels_tc.cu)
-// Packed operand matrix: tiles of (8 G) rows x 32 K, K-major, core matrices
-// 8 x 4 (16 bytes) ordered [K chunk][row group][row][4]; per tile the hi part
-// then the lo part; tiles ordered [row tile][K block].
+// Packed operand matrix: tiles of (8 G) rows x 128 bytes of K (32 TF32 or 64
+// BF16 elements), K-major, core matrices of 8 rows x 16 bytes ordered
+// [K chunk][row group][row][16 bytes]; per tile the hi part then the lo part;
+// tiles ordered [row tile][K block].  `bf16` selects the BF16 split.
 struct PackSeg {
   int64_t dst_off, src_off;
   int row0, k0, rows, ks;
@@ -258,10 +265,10 @@ struct TcTile {
 constexpr int TC_TN = 64;      // N tile (TMEM columns)
 constexpr int TC_STAGES = 2;   // shared-memory ring depth
 cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
-                        cudaStream_t st);
+                        int bf16, cudaStream_t st);
 cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
-                             double *const *bufs, const int *active, cudaStream_t st);
+                             double *const *bufs, const int *active, int bf16, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
-                           const int *active, int *err, cudaStream_t st);
+                           const int *active, int *err, int bf16, cudaStream_t st);
 
 }  // namespace idmrg

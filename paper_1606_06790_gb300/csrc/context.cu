@@ -128,6 +128,7 @@ struct idmrg_ctx {
 
   // mixed precision (tensor cores)
   bool mixed = false;
+  int bf16 = 0;  // mixed with BF16 splits (64 K per packed block) instead of TF32 (32)
   std::vector<PackSeg> pk_step, pk_psi;   // per iteration (L, R) and per matvec (psi)
   std::vector<TcTask> tc1k, tc3k;
   std::vector<TcTile> tc1t, tc3t;
@@ -590,7 +591,9 @@ idmrg_status sync_bufs(idmrg_ctx *c) {
 idmrg_status plan_mixed(idmrg_ctx *c) {
   const int P = c->P, d = c->d, target = c->o.target_charge, dd = d * d;
   const int GA = 16, GB = TC_TN / 8;
+  // one packed K block is 128 bytes of every row: TA / TB floats per hi or lo tile
   const int64_t TA = 128 * 32, TB = (int64_t)TC_TN * 32;
+  const int kblk = c->bf16 ? 64 : 32;
   auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
   c->pk_step.clear();
   c->pk_psi.clear();
@@ -645,7 +648,7 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
       }
       if (M == 0) continue;
       const int K = BL.dim[si], N = psi.C[si];
-      const int KB = (int)cdiv(K, 32), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      const int KB = (int)cdiv(K, kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
       pa1[si] = pa1n;
       pa1n += (int64_t)MT * KB * 2 * TA;
       pb1[si] = pb1n;
@@ -706,7 +709,7 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
           }
       if (M == 0) continue;
       const int N = BR.dim[jo];
-      const int KB = (int)cdiv(std::max(K, 1), 32), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      const int KB = (int)cdiv(std::max(K, 1), kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
       pa3[jo] = pa3n;
       pa3n += (int64_t)MT * KB * 2 * TA;
       pb3[jo] = pb3n;
@@ -801,7 +804,7 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
   // split the environments once for this iteration
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_pack((const PackSeg *)c->dpks.p, (int)c->pk_step.size(), c->pk_step_rows, (double *const *)c->dbufs.p,
-                 nullptr, c->st));
+                 nullptr, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE);
   c->launches += 1;
   return IDMRG_OK;
@@ -816,19 +819,20 @@ idmrg_status heff_launch_mixed(idmrg_ctx *c, const int *active_dev, const int *a
   for (int q = 0; q < c->P; ++q)
     if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
-  CK(launch_pack((const PackSeg *)c->dpkp.p, (int)c->pk_psi.size(), c->pk_psi_rows, bufs, active_dev, c->st));
+  CK(launch_pack((const PackSeg *)c->dpkp.p, (int)c->pk_psi.size(), c->pk_psi_rows, bufs, active_dev, c->bf16,
+                 c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE);
   c->kbegin(IDMRG_K_HEFF_GEMM);
   CK(launch_tc_gemm((const TcTile *)c->dtc1t.p, (int)c->tc1t.size(), (const TcTask *)c->dtc1k.p, bufs, active_dev,
-                    (int *)c->derr.p, c->st));
+                    (int *)c->derr.p, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_GEMM);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_wstage_tc((const WTaskP *)c->dwtp.p, (int)c->wtp.size(), c->wtp_rows, (const WTerm *)c->dwtpm.p, bufs,
-                      active_dev, c->st));
+                      active_dev, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
   c->kbegin(IDMRG_K_HEFF_GEMM);
   CK(launch_tc_gemm((const TcTile *)c->dtc3t.p, (int)c->tc3t.size(), (const TcTask *)c->dtc3k.p, bufs, active_dev,
-                    (int *)c->derr.p, c->st));
+                    (int *)c->derr.p, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_GEMM, gf, by);
   c->launches += 4;
   c->mixed_matvecs += 1;
@@ -1103,8 +1107,10 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   // against tol (and its alpha_0 is the FP64 Rayleigh quotient); the following
   // matvecs run on the tensor cores until the residual estimate falls by the
   // inner factor; the Ritz vector starts the next restart.
+  // (BF16 splits carry ~16 bits per product against ~21 for TF32: each
+  // restart gains less, so more of them are allowed)
   L.inner_factor = c->mixed ? 1e-3 : 0.0;
-  const int max_restarts = c->mixed ? 8 : 1;
+  const int max_restarts = c->mixed ? (c->bf16 ? 12 : 8) : 1;
   const int inner_cap = c->mixed ? std::min(kmax, 80) : kmax;
   for (int q = 0; q < P; ++q) c->hbufs[q * NBUF + BUF_PSI] = psip[q];
   NOMEM(sync_bufs(c) == IDMRG_OK);
@@ -1538,11 +1544,17 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   double *const *bufs = (double *const *)c->dbufs.p;
   c->kbegin(IDMRG_K_SVD);
   CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, c->tmaxel_all, bufs, BUF_PSI, c->dp(c->swork), c->st));
-  CK(launch_svd_qrcp((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, c->dp(c->swork), (int *)c->siw.p,
-                     c->o.lambda_zero_rel, c->st));
-  // Jacobi groups over all jobs (largest first across superblocks)
-  int g[4], gcols[4];
+  // groups over all jobs (largest first across superblocks): the pivoted QR
+  // and both Jacobi stages run each group on clusters of the same size
+  int g[4], gcols[4], grows[4] = {0, 0, 0, 0};
   jacobi_groups(c, c->torder.data(), nj, g, gcols);
+  for (int k = 1; k < 5; ++k) {
+    const int lo = g[k - 1], hi = k < 4 ? g[k] : nj;
+    for (int j = lo; j < hi; ++j) grows[k - 1] = std::max(grows[k - 1], c->jobs[c->torder[j]].rows_a);
+  }
+  if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
+  CK(launch_svd_qrcp_grouped((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, grows, gcols,
+                             c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, c->st, c->side, c->sev));
   if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
   // FP32 stage: rotations V to FP32 accuracy; Newton-Schulz makes V
   // orthogonal to FP64 precision (V <- 1.5 V - 0.5 V V^T V, twice); X = B V;
@@ -1961,8 +1973,10 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
     return bail(IDMRG_EINVAL);
   if (opts->m < 1 || opts->lanczos_maxit < 2 || opts->lanczos_maxit > 600 || !(opts->lanczos_tol > 0))
     return bail(IDMRG_EINVAL);
-  if (opts->prec != IDMRG_FP64 && opts->prec != IDMRG_TF32X3) return bail(IDMRG_EINVAL);
-  c->mixed = opts->prec == IDMRG_TF32X3;
+  if (opts->prec != IDMRG_FP64 && opts->prec != IDMRG_TF32X3 && opts->prec != IDMRG_BF16X3)
+    return bail(IDMRG_EINVAL);
+  c->mixed = opts->prec != IDMRG_FP64;
+  c->bf16 = opts->prec == IDMRG_BF16X3 ? 1 : 0;
   c->ell = ell;
   c->d = d;
   c->P = ell / 2;

@@ -206,6 +206,241 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restri
   }
 }
 
+// ------------------------------------------------------------ cluster QRCP
+// The same pivoted Householder QR over a cluster of C CTAs.  Column position
+// j lives in the shared memory of CTA j mod C (cyclic, so the trailing
+// columns stay spread as k grows).  Step k: the pivot is the largest
+// remaining column norm over the cluster (candidates gathered in rank 0's
+// shared memory, ties to the lower position as in qrcp_kernel); positions k
+// and p are swapped between their owners through distributed shared memory;
+// the owner of k forms the reflector and publishes it; every CTA applies it
+// to its own trailing columns.  The trailing update, which holds the
+// single-CTA kernel at one SM's FP64 rate, is spread over C SMs.
+constexpr int QC_THREADS = 256;
+constexpr int QC_MAX_CLUSTER = 16;
+
+__global__ void __launch_bounds__(QC_THREADS)
+    qrcp_cluster_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                        int *__restrict__ iwork, double zero_rel) {
+  extern __shared__ __align__(16) double qc_sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / C]];
+  const int ra = Jb.rows_a, ca = Jb.cols_a;
+  double *A = work + Jb.a_off;
+  double *tau = work + Jb.tau_off;
+  double *B = work + Jb.b_off;
+  int *perm = iwork + Jb.perm_off;
+  const int nloc = (ca + C - 1) / C;
+  const int ld = (ra + 1) & ~1;                  // 16-byte aligned columns
+  double *cols = qc_sm;                          // [nloc][ld]
+  double *bcast = cols + (size_t)nloc * ld;      // [ld] reflector of the step
+  double *swp = bcast + ld;                      // [ld] incoming column of a swap
+  double *vn = swp + ld, *vref = vn + nloc;      // [nloc] squared norms
+  int *pl = (int *)(vref + nloc);                // [nloc] original column at each position
+  __shared__ double cand_v[QC_MAX_CLUSTER], red_v[QC_THREADS / 32], s_tau, s_beta, s_scale, s_swap_vn, s_swap_vref;
+  __shared__ int cand_i[QC_MAX_CLUSTER], red_i[QC_THREADS / 32], s_piv, s_stop, s_swap_pl;
+  __shared__ double s_vp, s_stop2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  auto pos = [&](int l) { return crank + C * l; };
+  // load the owned columns and their squared norms
+  for (int l = 0; l < nloc; ++l) {
+    const int j = pos(l);
+    if (j >= ca) break;
+    for (int i = threadIdx.x; i < ra; i += blockDim.x) cols[(size_t)l * ld + i] = A[(int64_t)j * ra + i];
+  }
+  __syncthreads();
+  for (int l = warp; l < nloc; l += nw) {
+    const int j = pos(l);
+    if (j >= ca) continue;
+    double s2 = 0.0;
+    for (int i = lane; i < ra; i += 32) s2 = fma(cols[(size_t)l * ld + i], cols[(size_t)l * ld + i], s2);
+    s2 = wsum(s2);
+    if (lane == 0) {
+      vn[l] = s2;
+      vref[l] = s2;
+      pl[l] = j;
+    }
+  }
+  if (threadIdx.x == 0) s_stop2 = -1.0;
+  __syncthreads();
+  double *cand_v0 = cluster.map_shared_rank(cand_v, 0);
+  int *cand_i0 = cluster.map_shared_rank(cand_i, 0);
+  int rank = ca;
+  for (int k = 0; k < ca; ++k) {
+    // (a) pivot: local candidate, gathered in rank 0, the same choice everywhere
+    double bv = -1.0;
+    int bi = 0x7fffffff;
+    for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
+      const int j = pos(l);
+      if (j >= k && j < ca && (vn[l] > bv || (vn[l] == bv && j < bi))) {
+        bv = vn[l];
+        bi = j;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < nw; ++q)
+        if (red_v[q] > red_v[0] || (red_v[q] == red_v[0] && red_i[q] < red_i[0])) { red_v[0] = red_v[q]; red_i[0] = red_i[q]; }
+      cand_v0[crank] = red_v[0];
+      cand_i0[crank] = red_i[0];
+    }
+    cluster.sync();
+    if (warp == 0) {  // one lane per CTA reads its candidate (remote loads in parallel)
+      double v = lane < C ? cand_v0[lane] : -1.0;
+      int idx = lane < C ? cand_i0[lane] : 0x7fffffff;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      }
+      if (lane == 0) {
+        s_piv = idx;
+        s_vp = v;
+        if (k == 0) s_stop2 = v * (0.01 * zero_rel * zero_rel / (double)ca);
+        s_stop = !(v > s_stop2);
+      }
+    }
+    __syncthreads();
+    if (s_stop) {  // the same decision in every CTA: numerical rank reached
+      rank = k;
+      break;
+    }
+    const int p = s_piv;
+    const int ok = k % C, op = p % C, lk = k / C, lp = p / C;
+    // (b) swap positions k and p
+    if (p != k) {
+      if (ok == op) {
+        if (crank == ok) {
+          for (int i = threadIdx.x; i < ra; i += blockDim.x) {
+            const double t = cols[(size_t)lk * ld + i];
+            cols[(size_t)lk * ld + i] = cols[(size_t)lp * ld + i];
+            cols[(size_t)lp * ld + i] = t;
+          }
+          if (threadIdx.x == 0) {
+            double t = vn[lk]; vn[lk] = vn[lp]; vn[lp] = t;
+            t = vref[lk]; vref[lk] = vref[lp]; vref[lp] = t;
+            const int ti = pl[lk]; pl[lk] = pl[lp]; pl[lp] = ti;
+          }
+        }
+        cluster.sync();  // every CTA passes the same barriers
+      } else {
+        // each owner writes its column into the other's swap buffer
+        if (crank == ok || crank == op) {
+          const int mine = crank == ok ? lk : lp, other = crank == ok ? op : ok;
+          double *dst = cluster.map_shared_rank(swp, other);
+          for (int i = threadIdx.x; i < ra; i += blockDim.x) dst[i] = cols[(size_t)mine * ld + i];
+          if (threadIdx.x == 0) {
+            *cluster.map_shared_rank(&s_swap_vn, other) = vn[mine];
+            *cluster.map_shared_rank(&s_swap_vref, other) = vref[mine];
+            *cluster.map_shared_rank(&s_swap_pl, other) = pl[mine];
+          }
+        }
+        cluster.sync();
+        if (crank == ok || crank == op) {
+          const int mine = crank == ok ? lk : lp;
+          for (int i = threadIdx.x; i < ra; i += blockDim.x) cols[(size_t)mine * ld + i] = swp[i];
+          if (threadIdx.x == 0) {
+            vn[mine] = s_swap_vn;
+            vref[mine] = s_swap_vref;
+            pl[mine] = s_swap_pl;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // (c) the owner of position k forms the reflector (rows k..ra-1)
+    if (crank == ok) {
+      double *ak = cols + (size_t)lk * ld;
+      double s2 = 0.0;
+      for (int i = k + 1 + threadIdx.x; i < ra; i += blockDim.x) s2 = fma(ak[i], ak[i], s2);
+      s2 = wsum(s2);
+      if (lane == 0) red_v[warp] = s2;
+      __syncthreads();
+      if (warp == 0) {
+        double sig = lane < nw ? red_v[lane] : 0.0;
+        for (int o = 4; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
+        const double alpha = ak[k];
+        if (lane == 0) {
+        if (sig == 0.0) {
+          s_tau = 0.0;
+          s_beta = alpha;
+          s_scale = 1.0;
+        } else {
+          const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+          s_tau = (beta - alpha) / beta;
+          s_beta = beta;
+          s_scale = 1.0 / (alpha - beta);
+        }
+        tau[k] = s_tau;
+        }
+      }
+      __syncthreads();
+      const double sc = s_scale;
+      if (s_tau != 0.0)
+        for (int i = k + 1 + threadIdx.x; i < ra; i += blockDim.x) ak[i] *= sc;
+      __syncthreads();
+      if (threadIdx.x == 0) ak[k] = s_beta;
+      for (int i = k + 1 + threadIdx.x; i < ra; i += blockDim.x) bcast[i] = ak[i];
+    }
+    cluster.sync();  // reflector published
+    // (d) every CTA applies H_k to its own trailing columns
+    const double tk = *cluster.map_shared_rank(&s_tau, ok);
+    if (tk != 0.0) {
+      if (crank != ok) {
+        const double *src = cluster.map_shared_rank(bcast, ok);
+        for (int i = k + 1 + threadIdx.x; i < ra; i += blockDim.x) bcast[i] = src[i];
+        __syncthreads();
+      }
+      for (int l = warp; l < nloc; l += nw) {
+        const int j = pos(l);
+        if (j <= k || j >= ca) continue;
+        double *aj = cols + (size_t)l * ld;
+        double w = 0.0;
+        for (int i = k + 1 + lane; i < ra; i += 32) w = fma(bcast[i], aj[i], w);
+        w = (wsum(w) + aj[k]) * tk;
+        __syncwarp();
+        if (lane == 0) aj[k] -= w;
+        for (int i = k + 1 + lane; i < ra; i += 32) aj[i] = fma(-w, bcast[i], aj[i]);
+      }
+      __syncthreads();
+    }
+    // downdate the remaining column norms; recompute where cancellation hurts
+    for (int l = warp; l < nloc; l += nw) {
+      const int j = pos(l);
+      if (j <= k || j >= ca) continue;
+      const double *aj = cols + (size_t)l * ld;
+      double nv = vn[l] - aj[k] * aj[k];
+      if (!(nv > 1e-8 * vref[l])) {
+        double s2 = 0.0;
+        for (int i = k + 1 + lane; i < ra; i += 32) s2 = fma(aj[i], aj[i], s2);
+        nv = wsum(s2);
+        if (lane == 0) vref[l] = nv;
+      }
+      if (lane == 0) vn[l] = fmax(nv, 0.0);
+    }
+    __syncthreads();
+  }
+  // Householder vectors, R, the permutation, the rank; B = [R11 R12]^T
+  for (int l = 0; l < nloc; ++l) {
+    const int j = pos(l);
+    if (j >= ca) break;
+    for (int i = threadIdx.x; i < ra; i += blockDim.x) A[(int64_t)j * ra + i] = cols[(size_t)l * ld + i];
+    if (threadIdx.x == 0) perm[j] = pl[l];
+    for (int b = threadIdx.x; b < ca; b += blockDim.x)
+      B[(int64_t)b * ca + j] = (b <= j && b < rank) ? cols[(size_t)l * ld + b] : 0.0;
+  }
+  if (crank == 0 && threadIdx.x == 0) perm[ca] = rank;
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 // ---------------------------------------------------------------- Jacobi
 constexpr int JAC_THREADS = 512;
 constexpr int JAC_MAX_CLUSTER = 16;
@@ -1355,6 +1590,67 @@ cudaError_t launch_svd_elementwise(const SvdJob *jobs, int njobs, int max_cols, 
   const int64_t tot = (int64_t)max_cols * max_cols;
   dim3 grid((unsigned)std::min<int64_t>((tot + 255) / 256, 64), (unsigned)njobs);
   svd_elementwise_kernel<<<grid, 256, 0, st>>>(jobs, work, mode);
+  return cudaGetLastError();
+}
+
+size_t svd_qrc_smem(int rows, int cols, int csize) {
+  const int64_t nloc = (cols + csize - 1) / csize, ld = (rows + 1) & ~1;
+  return (size_t)((nloc * ld + 2 * ld + 3 * nloc + 2) * sizeof(double));
+}
+
+// pivoted QR of the jobs order[0..njobs) in groups (as the Jacobi): group
+// 0 and any group whose columns do not fit in shared memory on the single-CTA
+// kernel, groups 1..4 on clusters of 16, 8, 4, 1 CTAs; rows[k], cols[k] are
+// the largest rows and columns of block group k+1
+cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *rows,
+                                    const int *cols, double *work, int *iwork, double zero_rel, cudaStream_t st,
+                                    const cudaStream_t *side, const cudaEvent_t *ev) {
+  if (njobs <= 0) return cudaGetLastError();
+  cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SVD_BLOCK_SMEM_MAX);
+  if (e != cudaSuccess) return e;
+  const int lo[5] = {0, g[0], g[1], g[2], g[3]}, hi[5] = {g[0], g[1], g[2], g[3], njobs};
+  const int csz[5] = {16, 16, 8, 4, 1};
+  // groups 2..4 on the side streams, concurrent with groups 0 and 1
+  e = cudaEventRecord(ev[0], st);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < 5; ++k) {
+    if (hi[k] <= lo[k]) continue;
+    const cudaStream_t sk = k >= 2 ? side[k - 2] : st;
+    if (k >= 2) {
+      e = cudaStreamWaitEvent(sk, ev[0], 0);
+      if (e != cudaSuccess) return e;
+    }
+    const size_t smem = k == 0 ? SVD_BLOCK_SMEM_MAX + 1 : svd_qrc_smem(rows[k - 1], cols[k - 1], csz[k]);
+    if (smem > SVD_BLOCK_SMEM_MAX) {
+      e = launch_svd_qrcp(jobs, order + lo[k], hi[k] - lo[k], work, iwork, zero_rel, sk);
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((hi[k] - lo[k]) * csz[k], 1, 1);
+      cfg.blockDim = dim3(QC_THREADS, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = sk;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = csz[k];
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, jobs, order + lo[k], work, iwork, zero_rel);
+    }
+    if (e != cudaSuccess) return e;
+    if (k >= 2) {
+      e = cudaEventRecord(ev[k - 1], sk);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  for (int k = 2; k < 5; ++k) {
+    if (hi[k] <= lo[k]) continue;
+    e = cudaStreamWaitEvent(st, ev[k - 1], 0);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

@@ -3,7 +3,11 @@
 // Every FP64 operand x is split into two TF32 numbers, hi = x rounded to TF32
 // and lo = x - hi (also used at TF32 precision), and a product is formed from
 // three tcgen05.mma of kind::tf32 (hi.hi + hi.lo + lo.hi) accumulated in FP32
-// in tensor memory: about 21 significant bits per product.
+// in tensor memory: about 21 significant bits per product.  The BF16 variant
+// splits into two BF16 numbers the same way and issues kind::f16 MMAs: about
+// 16 significant bits per product at twice the K per instruction.  Both use
+// the same byte layout (a K block is 128 bytes of every row: 32 TF32 or 64
+// BF16 elements), so the GEMM kernel differs only in the MMA it issues.
 //
 //  pack      : splits FP64 or FP32 source blocks into packed hi/lo tiles in the
 //              tensor-core operand layout (K-major, no swizzle, core matrices
@@ -19,6 +23,7 @@
 //              row map, as FP64 into the output wavefunction (stage 3).
 //              Every mbarrier wait is bounded; a timeout sets the context's
 //              error word.
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "common.h"
@@ -40,39 +45,56 @@ __device__ __forceinline__ int64_t packed_off(int row, int k, int KB, int G) {
   return ((int64_t)rt * KB + kb) * 2 * tile_floats + (((int64_t)kc * G + (rr >> 3)) * 8 + (rr & 7)) * 4 + (k & 3);
 }
 
+// The same position for 16-bit elements (in units of 16 bits): 64 per K
+// block, core matrices 8 rows x 8 elements.
+__device__ __forceinline__ int64_t packed_off_h(int row, int k, int KB, int G) {
+  const int rows_per_tile = 8 * G;
+  const int rt = row / rows_per_tile, rr = row - rt * rows_per_tile;
+  const int kb = k >> 6, kc = (k & 63) >> 3;
+  const int64_t tile_h = (int64_t)rows_per_tile * 64;
+  return ((int64_t)rt * KB + kb) * 2 * tile_h + (((int64_t)kc * G + (rr >> 3)) * 8 + (rr & 7)) * 8 + (k & 7);
+}
+
+// hi/lo split of x (given in FP64 or FP32) into the packed operand `dst` at
+// element (row, k): TF32 pair (bf16 = 0) or BF16 pair (bf16 = 1).
+__device__ __forceinline__ void put_split(float *dst, int row, int k, int KB, int G, int bf16, double x) {
+  if (bf16) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+    const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+    __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(dst);
+    const int64_t o = packed_off_h(row, k, KB, G);
+    h[o] = hi;
+    h[o + (int64_t)8 * G * 64] = lo;
+  } else {
+    const float hi = tf32_round((float)x);
+    const int64_t o = packed_off(row, k, KB, G);
+    dst[o] = hi;
+    dst[o + (int64_t)8 * G * 32] = (float)(x - (double)hi);
+  }
+}
+
 constexpr int PROWS = 16;
 
 __global__ void pack_kernel(const PackSeg *__restrict__ segs, double *const *__restrict__ bufs,
-                            const int *__restrict__ active) {
+                            const int *__restrict__ active, int bf16) {
   const PackSeg s = segs[blockIdx.x];
   if (active && !active[s.sb]) return;
   const int r0 = blockIdx.y * PROWS;
   if (r0 >= s.rows) return;
   const int r1 = min(s.rows, r0 + PROWS);
   float *dst = (float *)bufs[s.sb * NBUF + s.dst_buf] + s.dst_off;
-  const int64_t tile_floats = (int64_t)8 * s.G * 32;
   const int n = (r1 - r0) * s.ks;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int r = r0 + e / s.ks, k = e % s.ks;
     const int64_t si = s.trans ? (int64_t)k * s.src_ld + r : (int64_t)r * s.src_ld + k;
-    float hi, lo;
-    if (s.src_fp32) {
-      const float x = ((const float *)bufs[s.sb * NBUF + s.src_buf])[s.src_off + si];
-      hi = tf32_round(x);
-      lo = x - hi;
-    } else {
-      const double x = bufs[s.sb * NBUF + s.src_buf][s.src_off + si];
-      hi = tf32_round((float)x);
-      lo = (float)(x - (double)hi);
-    }
-    const int64_t o = packed_off(s.row0 + r, s.k0 + k, s.KB, s.G);
-    dst[o] = hi;
-    dst[o + tile_floats] = lo;
+    const double x = s.src_fp32 ? (double)((const float *)bufs[s.sb * NBUF + s.src_buf])[s.src_off + si]
+                                : bufs[s.sb * NBUF + s.src_buf][s.src_off + si];
+    put_split(dst, s.row0 + r, s.k0 + k, s.KB, s.G, bf16, x);
   }
 }
 
 __global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *__restrict__ terms,
-                                 double *const *__restrict__ bufs, const int *__restrict__ active) {
+                                 double *const *__restrict__ bufs, const int *__restrict__ active, int bf16) {
   const WTaskP t = tasks[blockIdx.x];
   if (active && !active[t.sb]) return;
   const int r0 = blockIdx.y * PROWS;
@@ -80,7 +102,6 @@ __global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *
   const int r1 = min(t.rows, r0 + PROWS);
   const float *in = (const float *)bufs[t.sb * NBUF + BUF_T1F];
   float *dst = (float *)bufs[t.sb * NBUF + BUF_PA3] + t.dst_off;
-  const int64_t tile_floats = (int64_t)8 * t.G * 32;
   const int n = (r1 - r0) * t.cols;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int r = r0 + e / t.cols, c = e % t.cols;
@@ -89,10 +110,7 @@ __global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *
       const WTerm w = terms[t.term0 + q];
       acc = fmaf((float)w.coef, in[w.in_off + (int64_t)r * w.in_ld + c], acc);
     }
-    const float hi = tf32_round(acc);
-    const int64_t o = packed_off(t.row0 + r, t.k0 + c, t.KB, t.G);
-    dst[o] = hi;
-    dst[o + tile_floats] = acc - hi;
+    put_split(dst, t.row0 + r, t.k0 + c, t.KB, t.G, bf16, (double)acc);
   }
 }
 
@@ -102,6 +120,7 @@ constexpr int B_TILE = TC_TN * 32;      // floats per B tile
 constexpr int STAGE_FLOATS = 2 * A_TILE + 2 * B_TILE;
 constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (about 2 s)
 
+template <bool BF16>
 __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__ tiles,
                                                       const TcTask *__restrict__ tasks,
                                                       double *const *__restrict__ bufs,
@@ -134,7 +153,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
   if (threadIdx.x == 0) {
     const float *A = (const float *)bufs[T.sb * NBUF + T.a_buf] + T.a_off + (int64_t)tile.mt * T.KB * 2 * A_TILE;
     const float *B = (const float *)bufs[T.sb * NBUF + T.b_buf] + T.b_off + (int64_t)tile.nt * T.KB * 2 * B_TILE;
-    constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, 2);
+    constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, BF16 ? 1u : 2u);
     constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TC_TN / 8) * 128, sbo = 128;
     constexpr uint32_t stage_bytes = 4u * STAGE_FLOATS;
     auto issue = [&](int kb) {
@@ -170,9 +189,15 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
         const uint64_t alo = tc::smem_desc(sa + 4u * A_TILE + kk * 2 * lboA, lboA, sbo);
         const uint64_t bhi = tc::smem_desc(sb + kk * 2 * lboB, lboB, sbo);
         const uint64_t blo = tc::smem_desc(sb + 4u * B_TILE + kk * 2 * lboB, lboB, sbo);
-        tc::mma_tf32(tmem, ahi, bhi, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-        tc::mma_tf32(tmem, ahi, blo, idesc, 1u);
-        tc::mma_tf32(tmem, alo, bhi, idesc, 1u);
+        if (BF16) {  // K = 16 per MMA: 32 bytes of every row, as for TF32
+          tc::mma_f16(tmem, ahi, bhi, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_f16(tmem, ahi, blo, idesc, 1u);
+          tc::mma_f16(tmem, alo, bhi, idesc, 1u);
+        } else {
+          tc::mma_tf32(tmem, ahi, bhi, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_tf32(tmem, ahi, blo, idesc, 1u);
+          tc::mma_tf32(tmem, alo, bhi, idesc, 1u);
+        }
       }
       tc::mma_commit(&empty[s]);
     }
@@ -225,29 +250,30 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
 }  // namespace
 
 cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
-                        cudaStream_t st) {
+                        int bf16, cudaStream_t st) {
   if (nseg > 0 && max_rows > 0) {
     dim3 grid(nseg, (max_rows + PROWS - 1) / PROWS);
-    pack_kernel<<<grid, 256, 0, st>>>(segs, bufs, active);
+    pack_kernel<<<grid, 256, 0, st>>>(segs, bufs, active, bf16);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
-                             double *const *bufs, const int *active, cudaStream_t st) {
+                             double *const *bufs, const int *active, int bf16, cudaStream_t st) {
   if (ntasks > 0 && max_rows > 0) {
     dim3 grid(ntasks, (max_rows + PROWS - 1) / PROWS);
-    wstage_tc_kernel<<<grid, 256, 0, st>>>(tasks, terms, bufs, active);
+    wstage_tc_kernel<<<grid, 256, 0, st>>>(tasks, terms, bufs, active, bf16);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
-                           const int *active, int *err, cudaStream_t st) {
+                           const int *active, int *err, int bf16, cudaStream_t st) {
   const int smem = TC_STAGES * STAGE_FLOATS * (int)sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto kern = bf16 ? tc_gemm_kernel<true> : tc_gemm_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (ntiles > 0) tc_gemm_kernel<<<ntiles, 128, smem, st>>>(tiles, tasks, bufs, active, err);
+  if (ntiles > 0) kern<<<ntiles, 128, smem, st>>>(tiles, tasks, bufs, active, err);
   return cudaGetLastError();
 }
 

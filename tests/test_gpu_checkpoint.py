@@ -12,7 +12,7 @@ from gpu_helpers import context
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x3"])
 def test_restored_context_continues_identically(tmp_path, prec):
     mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 7), 8)
     a = context(mpo, 48, prec=prec)
