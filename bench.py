@@ -131,7 +131,8 @@ def source_hash(*names):
 
 KERNEL_SOURCES = {"heff_gemm": ["kernels_f64.cu", "kernels_tc.cu"], "heff_wstage": ["kernels_f64.cu", "kernels_tc.cu"],
                   "lanczos_vec": ["kernels_lanczos.cu"], "lanczos_tri": ["kernels_lanczos.cu"],
-                  "svd": ["kernels_svd.cu"], "env": ["kernels_f64.cu"], "predict": ["kernels_f64.cu"]}
+                  "svd": ["kernels_svd.cu"], "env": ["kernels_f64.cu"], "predict": ["kernels_f64.cu"],
+                  "heff_f64": ["kernels_f64.cu"]}
 
 
 def traffic_for(kclass: str, prec: str):
@@ -165,7 +166,7 @@ def class_roofline(name: str, d: dict, prec: str, pk: dict):
         src = "sustained bf16" if bf else "sustained bf16 x nominal tf32/bf16 (1.1/2.25)"
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "peak_source": f"{pk['src']} {src}; split products counted once"})
-    elif name in ("heff_gemm", "heff_wstage", "svd", "env", "predict"):
+    elif name in ("heff_gemm", "heff_wstage", "heff_f64", "svd", "env", "predict"):
         achieved = d["flops"] / sec / 1e9 if sec > 0 else 0.0
         out.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
                     "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"})

@@ -162,6 +162,16 @@ idmrg_status idmrg_block_to_host(const idmrg_ctx *ctx, int p, int side, double *
  * idmrg_advance. */
 idmrg_status idmrg_heff_apply(idmrg_ctx *ctx, int p, const double *psi_dev, double *out_dev);
 
+/* The same product in one of the FP64-accurate forms, whatever opts.prec:
+ * form 0 = FP64 GEMMs on the CUDA cores; form 1 = BF16 digit slices on the
+ * tensor cores (the Ozaki scheme: eight 7-bit digits per element against a
+ * per-row power of two, exact integer sums per digit level, levels summed in
+ * FP64).  Form 1 exists only in a mixed-precision context (TF32X3 / BF16X3),
+ * and only while every GEMM task's K is at most 768 (exactness of the digit
+ * sums); the Lanczos restarts then use it for their FP64 matvecs.
+ * Otherwise IDMRG_EINVAL. */
+idmrg_status idmrg_heff_apply_fp64(idmrg_ctx *ctx, int p, const double *psi_dev, double *out_dev, int form);
+
 /* Step 3': start vector of superblock p (or all): Eq. wfprediction for
  * n >= 3 when opts.predict, else SplitMix64 numbers in [-1,1) on the target
  * sector.  Writes ||psi~|| if norm_out != NULL (host, l/2 entries for p=-1). */
@@ -235,7 +245,11 @@ typedef enum {
   IDMRG_K_SVD = 4,         /* sector SVD, selection, compaction (Step 4)       */
   IDMRG_K_ENV = 5,         /* block-spin transformation (Step 6)               */
   IDMRG_K_PREDICT = 6,     /* start vectors (Step 3')                          */
-  IDMRG_K_COUNT = 7
+  IDMRG_K_HEFF_F64 = 7,    /* mixed precision only: the FP64 H_eff psi GEMM
+                              stages that start every Lanczos restart (the
+                              true-residual checks); FP64 mode books its
+                              GEMMs under IDMRG_K_HEFF_GEMM                   */
+  IDMRG_K_COUNT = 8
 } idmrg_kernel_class;
 idmrg_status idmrg_profile_enable(idmrg_ctx *ctx, int on);
 idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t *launches, double *flops,

@@ -27,7 +27,7 @@ PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
 EXPORTED_SYMBOLS = [
     "idmrg_default_opts", "idmrg_create", "idmrg_destroy", "idmrg_last_error", "idmrg_set_stream",
     "idmrg_iteration", "idmrg_psi_layout", "idmrg_block_basis", "idmrg_block_to_host",
-    "idmrg_heff_apply", "idmrg_predict_wavefunction", "idmrg_lanczos_solve", "idmrg_get_psi",
+    "idmrg_heff_apply", "idmrg_heff_apply_fp64", "idmrg_predict_wavefunction", "idmrg_lanczos_solve", "idmrg_get_psi",
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = [
 ]
 
 KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
-                  "predict": 6}
+                  "predict": 6, "heff_f64": 7}
 
 
 class IdmrgError(RuntimeError):
@@ -97,6 +97,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_block_basis": (i, [vp, i, i, P(i), i, P(i), P(i)]),
         "idmrg_block_to_host": (i, [vp, i, i, P(d), sz]),
         "idmrg_heff_apply": (i, [vp, i, vp, vp]),
+        "idmrg_heff_apply_fp64": (i, [vp, i, vp, vp, i]),
         "idmrg_predict_wavefunction": (i, [vp, i, P(d)]),
         "idmrg_lanczos_solve": (i, [vp, i, P(d), P(i)]),
         "idmrg_get_psi": (i, [vp, i, P(d), sz]),
@@ -242,6 +243,12 @@ class Context:
         """out = H_eff psi; psi/out are float64 CUDA tensors in the layout of p."""
         self._check(self.lib.idmrg_heff_apply(self.h, p, C.c_void_p(psi.data_ptr()), C.c_void_p(out.data_ptr())),
                     "heff_apply")
+
+    def heff_apply_fp64(self, p: int, psi, out, form: int) -> None:
+        """out = H_eff psi in an FP64-accurate form: 0 = FP64 GEMMs, 1 = BF16
+        digit slices on the tensor cores (mixed-precision contexts)."""
+        self._check(self.lib.idmrg_heff_apply_fp64(self.h, p, C.c_void_p(psi.data_ptr()),
+                                                   C.c_void_p(out.data_ptr()), form), "heff_apply_fp64")
 
     def predict_wavefunction(self, p: int = -1) -> np.ndarray:
         out = np.zeros(self._n_of(p))

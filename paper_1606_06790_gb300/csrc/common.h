@@ -37,7 +37,15 @@ enum BufId {
   BUF_PA3 = 21,   // stage 3 A: T3 = W12 T1 (written by the W stage)
   BUF_PB3 = 22,   // stage 3 B: R blocks concatenated over channels, per out-sector
   BUF_RMAP = 23,  // stage 3 output row -> psi offset (int64)
-  NBUF = 24
+  // FP64-accurate tensor-core form (BF16 digit slices, see kernels_tc.cu)
+  BUF_OA1 = 24,   // stage 1 A digits
+  BUF_OB1 = 25,   // stage 1 B digits (psi, every matvec)
+  BUF_OT1 = 26,   // stage 1 output, FP64
+  BUF_OA3 = 27,   // stage 3 A digits (written by the W stage)
+  BUF_OB3 = 28,   // stage 3 B digits
+  BUF_ORMAP = 29, // stage 3 output row -> psi offset (int64)
+  BUF_OEXP = 30,  // per packed row: exponent of the digit expansion (int32)
+  NBUF = 31
 };
 
 
@@ -243,21 +251,29 @@ cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj
 // tiles ordered [row tile][K block].  `bf16` selects the BF16 split.
 struct PackSeg {
   int64_t dst_off, src_off;
+  int64_t exp_off;        // digit form: exponent of packed row r at exp[exp_off + r]
   int row0, k0, rows, ks;
   int src_ld, trans;      // trans: source element (row, k) at src[k * src_ld + row]
   int KB, G;              // K blocks and row groups of the packed matrix
   int sb, src_buf, dst_buf, src_fp32;
+  int whole;              // digit form: the segment holds the whole K range of its rows
+  int pad;
 };
 struct WTaskP {           // T3 rectangle written into a packed stage-3 A matrix
   int64_t dst_off;
+  int64_t exp_off;        // digit form: exponents of the task's packed rows
   int row0, k0, KB, G;
-  int sb, rows, cols, term0, nterm, pad;
+  int sb, rows, cols, term0, nterm;
+  int in_buf, dst_buf;    // stage-1 output read, packed A written
+  int pad;
 };
 struct TcTask {
   int64_t a_off, b_off, c_off, rmap_off;
+  int64_t a_exp, b_exp;   // digit form: exponent arrays of the A rows and B rows
   int sb, M, N, KB;
   int a_buf, b_buf, c_buf, rmap_buf;
-  int mode, ldc;          // mode 0: FP32 row-major C; 1: FP64 through the row map
+  int mode, ldc;          // mode 0: FP32 row-major C; 1: FP64 through the row map;
+                          // 2: FP64 row-major C
 };
 struct TcTile {
   int task, mt, nt, pad;
@@ -270,5 +286,20 @@ cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, cons
                              double *const *bufs, const int *active, int bf16, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
                            const int *active, int *err, int bf16, cudaStream_t st);
+// FP64-accurate products from BF16 digit slices (OZ_PLANES digits of 7 bits
+// per element, exact integer accumulation per digit level).  K blocks are 32
+// elements; a task's K may not exceed OZ_MAX_K (exactness of the FP32 sums).
+constexpr int OZ_PLANES = 8;
+constexpr int OZ_KBLK = 32;
+constexpr int OZ_MAX_K = 768;
+constexpr int OZ_EXP_EMPTY = (int)0x80808080;  // byte-fill value: row without non-zeros
+cudaError_t launch_oz_exp(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
+                          cudaStream_t st);
+cudaError_t launch_oz_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
+                           cudaStream_t st);
+cudaError_t launch_wstage_oz(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
+                             double *const *bufs, const int *active, int pass, cudaStream_t st);
+cudaError_t launch_oz_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
+                           const int *active, int *err, cudaStream_t st);
 
 }  // namespace idmrg

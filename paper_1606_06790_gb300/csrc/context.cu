@@ -129,6 +129,7 @@ struct idmrg_ctx {
   // mixed precision (tensor cores)
   bool mixed = false;
   int bf16 = 0;  // mixed with BF16 splits (64 K per packed block) instead of TF32 (32)
+  bool o_oz = true;  // FP64 restart matvecs from digit slices when the K bound allows
   std::vector<PackSeg> pk_step, pk_psi;   // per iteration (L, R) and per matvec (psi)
   std::vector<TcTask> tc1k, tc3k;
   std::vector<TcTile> tc1t, tc3t;
@@ -137,6 +138,19 @@ struct idmrg_ctx {
   int pk_step_rows = 0, pk_psi_rows = 0, wtp_rows = 0;
   DevBuf dpks, dpkp, dtc1k, dtc1t, dtc3k, dtc3t, dwtp, dwtpm, dtarget;
   std::vector<DevBuf> bPA1, bPB1, bT1F, bPA3, bPB3, bRMAP;
+  // FP64-accurate digit-slice form of H_eff psi on the tensor cores (the
+  // FP64 matvecs that start every mixed-precision Lanczos restart); usable
+  // while every task's K fits the exactness bound
+  bool oz_ok = false;
+  std::vector<PackSeg> oz_step_w, oz_step_p, oz_psi;  // whole-K (L), part-K (R), psi
+  std::vector<TcTask> oz1k, oz3k;
+  std::vector<TcTile> oz1t, oz3t;
+  std::vector<WTaskP> ozw;
+  int oz_step_w_rows = 0, oz_step_p_rows = 0, oz_psi_rows = 0, ozw_rows = 0;
+  int64_t oz_a3_lo = 0, oz_a3_hi = 0, oz_b3_lo = 0, oz_b3_hi = 0;  // exponent ranges reset before use
+  std::vector<WTerm> wtpm_oz;
+  DevBuf dozsw, dozsp, dozp, doz1k, doz1t, doz3k, doz3t, dozw, dozwm, oexp;
+  std::vector<DevBuf> bOA1, bOB1, bOT1, bOA3, bOB3, bORMAP;
 
   // plan for iteration n
   std::vector<SBPlan> plan;
@@ -372,6 +386,7 @@ idmrg_status gemm_run(idmrg_ctx *c, GemmTune &T, DevBuf &dk, DevBuf &ds, const i
 // planning of iteration n
 // ------------------------------------------------------------------------
 idmrg_status plan_mixed(idmrg_ctx *c);
+idmrg_status plan_oz(idmrg_ctx *c);
 
 idmrg_status plan_iteration(idmrg_ctx *c) {
   const int P = c->P, d = c->d, target = c->o.target_charge;
@@ -572,6 +587,8 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
   if (c->mixed) {
     idmrg_status s = plan_mixed(c);
     if (s != IDMRG_OK) return s;
+    s = plan_oz(c);
+    if (s != IDMRG_OK) return s;
   }
   for (int p = 0; p < P; ++p) c->stage[p] = ST_READY;
   return IDMRG_OK;
@@ -739,6 +756,8 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
               w.sb = p;
               w.rows = BL.dim[i];
               w.cols = BR.dim[jin];
+              w.in_buf = BUF_T1F;
+              w.dst_buf = BUF_PA3;
               w.term0 = (int)c->wtpm.size();
               for (int a = 0; a < wa; ++a) {
                 const int si = BL.find(BL.q[i] - L.lay.chq[a]);
@@ -810,6 +829,317 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
   return IDMRG_OK;
 }
 
+// Digit-slice form (FP64-accurate, see kernels_tc.cu): the stage-1 / W /
+// stage-3 structure of plan_mixed with 32-element K blocks of eight BF16
+// digit planes and one exponent per packed row.  Exponents of every
+// superblock live in one array: [stage-1 A and B rows | stage-3 B rows |
+// stage-3 A rows]; the last two ranges are reset before their atomic
+// maxima are taken.  Left off (oz_ok = false) when some task's K exceeds
+// OZ_MAX_K, the bound of exact digit sums.
+idmrg_status plan_oz(idmrg_ctx *c) {
+  const int P = c->P, d = c->d, target = c->o.target_charge, dd = d * d;
+  const int GA = 16, GB = TC_TN / 8;
+  const int64_t TA = (int64_t)128 * OZ_KBLK * OZ_PLANES, TB = (int64_t)TC_TN * OZ_KBLK * OZ_PLANES;
+  auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+  c->oz_ok = false;
+  c->oz_step_w.clear();
+  c->oz_step_p.clear();
+  c->oz_psi.clear();
+  c->oz1k.clear();
+  c->oz1t.clear();
+  c->oz3k.clear();
+  c->oz3t.clear();
+  c->ozw.clear();
+  c->wtpm_oz.clear();
+  c->oz_step_w_rows = c->oz_step_p_rows = c->oz_psi_rows = c->ozw_rows = 0;
+  // K of every task first: nothing is allocated when the bound fails
+  for (int p = 0; p < P; ++p) {
+    const Env &L = c->envL[p];
+    const Env &R = c->envR[(p + 1) % P];
+    const Basis &BL = L.lay.b, &BR = R.lay.b;
+    for (int si = 0; si < BL.S(); ++si)
+      if (BL.dim[si] > OZ_MAX_K) return IDMRG_OK;
+    for (int jo = 0; jo < BR.S(); ++jo) {
+      int K = 0;
+      for (int cc = 0; cc < R.lay.w; ++cc) {
+        const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+        if (jin >= 0 && R.lay.so[cc * BR.S() + jin] == jo) K += BR.dim[jin];
+      }
+      if (K > OZ_MAX_K) return IDMRG_OK;
+    }
+  }
+  auto seg = [&](std::vector<PackSeg> &v, int &mr, int sb, int dst_buf, int64_t dst_off, int src_buf,
+                 int64_t src_off, int64_t exp_off, int row0, int k0, int rows, int ks, int ld, int trans, int KB,
+                 int G, int whole) {
+    if (rows <= 0 || ks <= 0) return;
+    PackSeg q{};
+    q.dst_off = dst_off;
+    q.src_off = src_off;
+    q.exp_off = exp_off;
+    q.row0 = row0;
+    q.k0 = k0;
+    q.rows = rows;
+    q.ks = ks;
+    q.src_ld = ld;
+    q.trans = trans;
+    q.KB = KB;
+    q.G = G;
+    q.sb = sb;
+    q.src_buf = src_buf;
+    q.dst_buf = dst_buf;
+    q.whole = whole;
+    v.push_back(q);
+    mr = std::max(mr, rows);
+  };
+  int64_t ex1 = 0, exb3 = 0, exa3 = 0;  // the three exponent ranges, relative
+  const size_t b3seg0 = 0;
+  std::vector<size_t> a3_tasks, b3_tasks;  // tasks / items whose offsets get the range bases
+  std::vector<std::vector<int64_t>> rmaps(P);
+  std::vector<int64_t> na1(P), nb1(P), nt1(P), na3(P), nb3(P);
+  for (int p = 0; p < P; ++p) {
+    SBPlan &S = c->plan[p];
+    const Env &L = c->envL[p];
+    const Env &R = c->envR[(p + 1) % P];
+    const Basis &BL = L.lay.b, &BR = R.lay.b;
+    const PsiLayout &psi = S.psi;
+    const int SL = BL.S(), SR = BR.S();
+    const int wa = L.lay.w, wc = R.lay.w;
+    // ---------------- stage 1
+    std::vector<int64_t> t1f(SL, -1);
+    std::vector<std::vector<int>> rs1(SL, std::vector<int>(wa, -1));
+    int64_t pa1n = 0, pb1n = 0, t1n = 0;
+    for (int si = 0; si < SL; ++si) {
+      if (psi.C[si] == 0) continue;
+      int M = 0;
+      for (int a = 0; a < wa; ++a) {
+        const int so = L.lay.so[a * SL + si];
+        if (so < 0) continue;
+        rs1[si][a] = M;
+        M += BL.dim[so];
+      }
+      if (M == 0) continue;
+      const int K = BL.dim[si], N = psi.C[si];
+      const int KB = (int)cdiv(K, OZ_KBLK), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      const int64_t pa = pa1n, pb = pb1n, ea = ex1, eb = ex1 + M;
+      pa1n += (int64_t)MT * KB * TA;
+      pb1n += (int64_t)NT * KB * TB;
+      ex1 += M + N;
+      t1f[si] = t1n;
+      t1n += (int64_t)M * N;
+      for (int a = 0; a < wa; ++a) {
+        if (rs1[si][a] < 0) continue;
+        const int so = L.lay.so[a * SL + si];
+        seg(c->oz_step_w, c->oz_step_w_rows, p, BUF_OA1, pa, BUF_L, L.lay.off[a * SL + si], ea, rs1[si][a], 0,
+            BL.dim[so], K, K, 0, KB, GA, 1);
+      }
+      seg(c->oz_psi, c->oz_psi_rows, p, BUF_OB1, pb, BUF_IN, psi.roff[si], eb, 0, 0, N, K, N, 1, KB, GB, 1);
+      TcTask t{};
+      t.a_off = pa;
+      t.b_off = pb;
+      t.c_off = t1f[si];
+      t.a_exp = ea;
+      t.b_exp = eb;
+      t.sb = p;
+      t.M = M;
+      t.N = N;
+      t.KB = KB;
+      t.a_buf = BUF_OA1;
+      t.b_buf = BUF_OB1;
+      t.c_buf = BUF_OT1;
+      t.mode = 2;
+      t.ldc = N;
+      const int id = (int)c->oz1k.size();
+      c->oz1k.push_back(t);
+      for (int mt = 0; mt < MT; ++mt)
+        for (int nt = 0; nt < NT; ++nt) c->oz1t.push_back(TcTile{id, mt, nt, 0});
+    }
+    // ---------------- stage 3
+    int64_t pa3n = 0, pb3n = 0;
+    std::vector<int64_t> &rmap = rmaps[p];
+    for (int jo = 0; jo < SR; ++jo) {
+      std::vector<int> ks(wc, -1);
+      int K = 0;
+      for (int cc = 0; cc < wc; ++cc) {
+        const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+        if (jin < 0 || R.lay.so[cc * SR + jin] != jo) continue;
+        ks[cc] = K;
+        K += BR.dim[jin];
+      }
+      std::vector<int> rows_of(SL * dd, -1);
+      int M = 0;
+      const int64_t r0 = (int64_t)rmap.size();
+      for (int i = 0; i < SL; ++i)
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const int k = psi.sub(i, s, t);
+            if (psi.sj[k] != jo) continue;
+            rows_of[k] = M;
+            for (int x = 0; x < BL.dim[i]; ++x) rmap.push_back(psi.roff[i] + (int64_t)x * psi.C[i] + psi.scol[k]);
+            M += BL.dim[i];
+          }
+      if (M == 0) continue;
+      const int N = BR.dim[jo];
+      const int KB = (int)cdiv(std::max(K, 1), OZ_KBLK), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      const int64_t pa = pa3n, pb = pb3n, ea = exa3, eb = exb3;
+      pa3n += (int64_t)MT * KB * TA;
+      pb3n += (int64_t)NT * KB * TB;
+      exa3 += M;
+      exb3 += N;
+      for (int cc = 0; cc < wc; ++cc) {
+        if (ks[cc] < 0) continue;
+        const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+        seg(c->oz_step_p, c->oz_step_p_rows, p, BUF_OB3, pb, BUF_R, R.lay.off[cc * SR + jin], eb, 0, ks[cc], N,
+            BR.dim[jin], BR.dim[jin], 0, KB, GB, 0);
+      }
+      for (int i = 0; i < SL; ++i)
+        for (int s = 0; s < d; ++s)
+          for (int t = 0; t < d; ++t) {
+            const int k = psi.sub(i, s, t);
+            if (rows_of[k] < 0) continue;
+            for (int cc = 0; cc < wc; ++cc) {
+              if (ks[cc] < 0) continue;
+              const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+              WTaskP w{};
+              w.dst_off = pa;
+              w.exp_off = ea;
+              w.row0 = rows_of[k];
+              w.k0 = ks[cc];
+              w.KB = KB;
+              w.G = GA;
+              w.sb = p;
+              w.rows = BL.dim[i];
+              w.cols = BR.dim[jin];
+              w.in_buf = BUF_OT1;
+              w.dst_buf = BUF_OA3;
+              w.term0 = (int)c->wtpm_oz.size();
+              for (int a = 0; a < wa; ++a) {
+                const int si = BL.find(BL.q[i] - L.lay.chq[a]);
+                if (si < 0 || L.lay.so[a * SL + si] != i || rs1[si][a] < 0) continue;
+                for (int s2 = 0; s2 < d; ++s2)
+                  for (int t2 = 0; t2 < d; ++t2) {
+                    const double cf = S.W12[(((size_t)a * wc + cc) * dd + s * d + t) * dd + s2 * d + t2];
+                    if (cf == 0.0) continue;
+                    const int k2 = psi.sub(si, s2, t2);
+                    if (psi.sj[k2] != jin) continue;
+                    WTerm term{};
+                    term.in_off = t1f[si] + (int64_t)rs1[si][a] * psi.C[si] + psi.scol[k2];
+                    term.in_ld = psi.C[si];
+                    term.coef = cf;
+                    c->wtpm_oz.push_back(term);
+                  }
+              }
+              w.nterm = (int)c->wtpm_oz.size() - w.term0;
+              if (w.nterm == 0) continue;
+              c->ozw.push_back(w);
+              c->ozw_rows = std::max(c->ozw_rows, w.rows);
+            }
+          }
+      TcTask t{};
+      t.a_off = pa;
+      t.b_off = pb;
+      t.rmap_off = r0;
+      t.a_exp = ea;
+      t.b_exp = eb;
+      t.sb = p;
+      t.M = M;
+      t.N = N;
+      t.KB = K > 0 ? KB : 0;
+      t.a_buf = BUF_OA3;
+      t.b_buf = BUF_OB3;
+      t.c_buf = BUF_OUT;
+      t.rmap_buf = BUF_ORMAP;
+      t.mode = 1;
+      const int id = (int)c->oz3k.size();
+      c->oz3k.push_back(t);
+      for (int mt = 0; mt < MT; ++mt)
+        for (int nt = 0; nt < NT; ++nt) c->oz3t.push_back(TcTile{id, mt, nt, 0});
+    }
+    na1[p] = pa1n;
+    nb1[p] = pb1n;
+    nt1[p] = t1n;
+    na3[p] = pa3n;
+    nb3[p] = pb3n;
+  }
+  (void)b3seg0;
+  (void)target;
+  // exponent ranges: stage-3 B after stage 1, stage-3 A last
+  c->oz_b3_lo = ex1;
+  c->oz_b3_hi = ex1 + exb3;
+  c->oz_a3_lo = c->oz_b3_hi;
+  c->oz_a3_hi = c->oz_a3_lo + exa3;
+  for (PackSeg &q : c->oz_step_p) q.exp_off += c->oz_b3_lo;
+  for (WTaskP &w : c->ozw) w.exp_off += c->oz_a3_lo;
+  for (TcTask &t : c->oz3k) {
+    t.a_exp += c->oz_a3_lo;
+    t.b_exp += c->oz_b3_lo;
+  }
+  NOMEM(c->ensure(c->oexp, 4 * (size_t)std::max<int64_t>(c->oz_a3_hi, 4)));
+  for (int p = 0; p < P; ++p) {
+    NOMEM(c->ensure(c->bOA1[p], 2 * std::max<int64_t>(na1[p], 8)) &&
+          c->ensure(c->bOB1[p], 2 * std::max<int64_t>(nb1[p], 8)) &&
+          c->ensure(c->bOT1[p], 8 * std::max<int64_t>(nt1[p], 1)) &&
+          c->ensure(c->bOA3[p], 2 * std::max<int64_t>(na3[p], 8)) &&
+          c->ensure(c->bOB3[p], 2 * std::max<int64_t>(nb3[p], 8)) && c->upload(c->bORMAP[p], rmaps[p]));
+    // zero digits in the padding (only real elements are rewritten later)
+    CK(cudaMemsetAsync(c->bOA1[p].p, 0, 2 * na1[p], c->st));
+    CK(cudaMemsetAsync(c->bOB1[p].p, 0, 2 * nb1[p], c->st));
+    CK(cudaMemsetAsync(c->bOA3[p].p, 0, 2 * na3[p], c->st));
+    CK(cudaMemsetAsync(c->bOB3[p].p, 0, 2 * nb3[p], c->st));
+    c->hbufs[p * NBUF + BUF_OA1] = c->dp(c->bOA1[p]);
+    c->hbufs[p * NBUF + BUF_OB1] = c->dp(c->bOB1[p]);
+    c->hbufs[p * NBUF + BUF_OT1] = c->dp(c->bOT1[p]);
+    c->hbufs[p * NBUF + BUF_OA3] = c->dp(c->bOA3[p]);
+    c->hbufs[p * NBUF + BUF_OB3] = c->dp(c->bOB3[p]);
+    c->hbufs[p * NBUF + BUF_ORMAP] = c->dp(c->bORMAP[p]);
+    c->hbufs[p * NBUF + BUF_OEXP] = c->dp(c->oexp);
+  }
+  NOMEM(c->upload(c->dozsw, c->oz_step_w) && c->upload(c->dozsp, c->oz_step_p) && c->upload(c->dozp, c->oz_psi) &&
+        c->upload(c->doz1k, c->oz1k) && c->upload(c->doz1t, c->oz1t) && c->upload(c->doz3k, c->oz3k) &&
+        c->upload(c->doz3t, c->oz3t) && c->upload(c->dozw, c->ozw) && c->upload(c->dozwm, c->wtpm_oz));
+  NOMEM(c->upload(c->dbufs, c->hbufs));
+  // digits of L and R once for this iteration (R's rows span several channel
+  // segments: exponents first)
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(cudaMemsetAsync((int *)c->oexp.p + c->oz_b3_lo, 0x80, 4 * (c->oz_b3_hi - c->oz_b3_lo), c->st));
+  double *const *bufs = (double *const *)c->dbufs.p;
+  CK(launch_oz_exp((const PackSeg *)c->dozsp.p, (int)c->oz_step_p.size(), c->oz_step_p_rows, bufs, nullptr, c->st));
+  CK(launch_oz_pack((const PackSeg *)c->dozsp.p, (int)c->oz_step_p.size(), c->oz_step_p_rows, bufs, nullptr, c->st));
+  CK(launch_oz_pack((const PackSeg *)c->dozsw.p, (int)c->oz_step_w.size(), c->oz_step_w_rows, bufs, nullptr, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE);
+  c->launches += 3;
+  c->oz_ok = true;
+  return IDMRG_OK;
+}
+
+// FP64-accurate H_eff psi from digit slices on the tensor cores
+idmrg_status heff_launch_oz(idmrg_ctx *c, const int *active_dev, const int *act) {
+  double *const *bufs = (double *const *)c->dbufs.p;
+  double gf = 0, by = 0, wf = 0;
+  for (int q = 0; q < c->P; ++q)
+    if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(launch_oz_pack((const PackSeg *)c->dozp.p, (int)c->oz_psi.size(), c->oz_psi_rows, bufs, active_dev, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE);
+  c->kbegin(IDMRG_K_HEFF_F64);
+  CK(launch_oz_gemm((const TcTile *)c->doz1t.p, (int)c->oz1t.size(), (const TcTask *)c->doz1k.p, bufs, active_dev,
+                    (int *)c->derr.p, c->st));
+  c->kend(IDMRG_K_HEFF_F64);
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(cudaMemsetAsync((int *)c->oexp.p + c->oz_a3_lo, 0x80, 4 * (c->oz_a3_hi - c->oz_a3_lo), c->st));
+  CK(launch_wstage_oz((const WTaskP *)c->dozw.p, (int)c->ozw.size(), c->ozw_rows, (const WTerm *)c->dozwm.p, bufs,
+                      active_dev, 0, c->st));
+  CK(launch_wstage_oz((const WTaskP *)c->dozw.p, (int)c->ozw.size(), c->ozw_rows, (const WTerm *)c->dozwm.p, bufs,
+                      active_dev, 1, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
+  c->kbegin(IDMRG_K_HEFF_F64);
+  CK(launch_oz_gemm((const TcTile *)c->doz3t.p, (int)c->oz3t.size(), (const TcTask *)c->doz3k.p, bufs, active_dev,
+                    (int *)c->derr.p, c->st));
+  c->kend(IDMRG_K_HEFF_F64, gf, by);
+  c->launches += 5;
+  c->fp64_matvecs += 1;
+  return IDMRG_OK;
+}
+
 // heff on every superblock whose active flag is set (device array); the host
 // copy `act` (may be null = all) only feeds the flop/byte accounting
 idmrg_status heff_launch_fp64(idmrg_ctx *c, const int *active_dev, const int *act);
@@ -842,28 +1172,31 @@ idmrg_status heff_launch(idmrg_ctx *c, const int *active_dev, const int *act, bo
   if (c->mixed && !fp64) return heff_launch_mixed(c, active_dev, act);
   return heff_launch_fp64(c, active_dev, act);
 }
+idmrg_status heff_launch_oz(idmrg_ctx *c, const int *active_dev, const int *act);
 idmrg_status heff_launch_fp64(idmrg_ctx *c, const int *active_dev, const int *act) {
+  if (c->mixed && c->oz_ok && c->o_oz) return heff_launch_oz(c, active_dev, act);
   c->fp64_matvecs += 1;
   double *const *bufs = (double *const *)c->dbufs.p;
   double gf = 0, wf = 0, by = 0;
   for (int q = 0; q < c->P; ++q)
     if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
-  c->kbegin(IDMRG_K_HEFF_GEMM);
+  const int kg = c->mixed ? IDMRG_K_HEFF_F64 : IDMRG_K_HEFF_GEMM;
+  c->kbegin(kg);
   {
     idmrg_status sg_ = gemm_run(c, c->tn_g1, c->dg1k, c->dg1s, active_dev);
     if (sg_ != IDMRG_OK) return sg_;
   }
-  c->kend(IDMRG_K_HEFF_GEMM, 0.0, 0.0);
+  c->kend(kg, 0.0, 0.0);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_wstage_f64((const WTask *)c->dwt.p, (int)c->wl.tasks.size(), c->wl.max_rows, (const WTerm *)c->dwm.p,
                        bufs, active_dev, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
-  c->kbegin(IDMRG_K_HEFF_GEMM);
+  c->kbegin(kg);
   {
     idmrg_status sg_ = gemm_run(c, c->tn_g3, c->dg3k, c->dg3s, active_dev);
     if (sg_ != IDMRG_OK) return sg_;
   }
-  c->kend(IDMRG_K_HEFF_GEMM, gf, by);
+  c->kend(kg, gf, by);
   c->launches += 3;
   return IDMRG_OK;
 }
@@ -2041,7 +2374,9 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
   c->bPsi.resize(P);
   c->bUT.resize(P);
   c->bVT.resize(P);
-  for (auto *v : {&c->bPA1, &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP}) v->resize(P);
+  for (auto *v : {&c->bPA1, &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP, &c->bOA1, &c->bOB1, &c->bOT1,
+                  &c->bOA3, &c->bOB3, &c->bORMAP})
+    v->resize(P);
   c->hbufs.assign((size_t)P * NBUF, nullptr);
   if (!c->ensure(c->derr, 256)) return bail(IDMRG_ENOMEM);
   if (cudaMemsetAsync(c->derr.p, 0, sizeof(int), c->st) != cudaSuccess) return bail(IDMRG_ECUDA);
@@ -2090,7 +2425,8 @@ void idmrg_destroy(idmrg_ctx *c) {
   for (auto *v : {&c->cur, &c->prev, &c->prev2})
     for (auto &t : *v) { rel(t.U); rel(t.V); }
   for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT, &c->bPA1,
-                  &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP})
+                  &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP, &c->bOA1, &c->bOB1, &c->bOT1, &c->bOA3,
+                  &c->bOB3, &c->bORMAP})
     for (auto &b : *v) rel(b);
   for (DevBuf *b : {&c->dbufs, &c->dg1k, &c->dg1s, &c->dg3k, &c->dg3s, &c->dwt, &c->dwm, &c->ddt,
                     &c->ddp, &c->drb, &c->dgpk, &c->dgps, &c->dst, &c->dstab, &c->dge1k,
@@ -2100,7 +2436,8 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
                     &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgk, &c->dsgs,
                     &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
-                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget})
+                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp, &c->doz1k,
+                    &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -2204,9 +2541,11 @@ idmrg_status idmrg_block_to_host(const idmrg_ctx *cc, int p, int side, double *h
   return IDMRG_OK;
 }
 
-idmrg_status idmrg_heff_apply(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev) {
+// form -1: the context's own arithmetic; 0: FP64 GEMMs; 1: digit slices
+static idmrg_status heff_apply_form(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev, int form) {
   if (!c || !psi_dev || !out_dev) return IDMRG_EINVAL;
   if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
+  if (form == 1 && !(c->mixed && c->oz_ok)) return c->fail(IDMRG_EINVAL, "digit-slice form not available");
   std::vector<int> mask(c->P, 0);
   int64_t off = 0;
   std::vector<double *> save_in(c->P), save_out(c->P);
@@ -2221,12 +2560,24 @@ idmrg_status idmrg_heff_apply(idmrg_ctx *c, int p, const double *psi_dev, double
   }
   NOMEM(c->upload(c->dmask, mask));
   NOMEM(sync_bufs(c) == IDMRG_OK);
-  idmrg_status s = heff_launch(c, (const int *)c->dmask.p, mask.data(), false);
+  const bool keep_oz = c->o_oz;
+  if (form >= 0) c->o_oz = form == 1;
+  idmrg_status s = heff_launch(c, (const int *)c->dmask.p, mask.data(), form >= 0);
+  c->o_oz = keep_oz;
   for (int q = 0; q < c->P; ++q) {
     c->hbufs[q * NBUF + BUF_IN] = save_in[q];
     c->hbufs[q * NBUF + BUF_OUT] = save_out[q];
   }
   return s;
+}
+
+idmrg_status idmrg_heff_apply(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev) {
+  return heff_apply_form(c, p, psi_dev, out_dev, -1);
+}
+
+idmrg_status idmrg_heff_apply_fp64(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev, int form) {
+  if (form != 0 && form != 1) return IDMRG_EINVAL;
+  return heff_apply_form(c, p, psi_dev, out_dev, form);
 }
 
 idmrg_status idmrg_predict_wavefunction(idmrg_ctx *c, int p, double *norm_out) {

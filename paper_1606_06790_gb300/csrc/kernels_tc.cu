@@ -100,8 +100,8 @@ __global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *
   const int r0 = blockIdx.y * PROWS;
   if (r0 >= t.rows) return;
   const int r1 = min(t.rows, r0 + PROWS);
-  const float *in = (const float *)bufs[t.sb * NBUF + BUF_T1F];
-  float *dst = (float *)bufs[t.sb * NBUF + BUF_PA3] + t.dst_off;
+  const float *in = (const float *)bufs[t.sb * NBUF + t.in_buf];
+  float *dst = (float *)bufs[t.sb * NBUF + t.dst_buf] + t.dst_off;
   const int n = (r1 - r0) * t.cols;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int r = r0 + e / t.cols, c = e % t.cols;
@@ -247,7 +247,303 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
   if (warp == 0) tc::tmem_dealloc(tmem, TC_TN);
 }
 
+// ------------------------------------------- FP64-accurate digit-slice form
+// The Ozaki scheme (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59, 2012), here with BF16 slices:
+// every packed row r (a row of A, or a column of B) gets an exponent e_r with
+// |x| < 2^(e_r - 1) for all its elements, and each element becomes
+//   x = sum_{p<8} d_p 2^(e_r - 7 (p + 1)),  d_p integer, |d_p| <= 64,
+// exact in BF16 (balanced base-128 digits, 56 bits in all; the rest,
+// below 2^(e_r - 57), is dropped).  A product of digits is an integer of at
+// most 2^12, so the K-sum of the digit products of one level t = p + q is an
+// exact FP32 integer while (t + 1) K 2^12 < 2^24; for K <= OZ_MAX_K that holds
+// up to t = 4, and the rounding of the higher levels is below 2^-53 of the
+// leading terms.  Levels t <= 7 are kept (one 64-column TMEM accumulator
+// each, 36 MMAs per K step); the epilogue sums them in FP64 with their
+// power-of-two scales.
+__device__ __forceinline__ int64_t oz_off(int row, int k, int KB, int G, int p) {
+  const int rows_per_tile = 8 * G;
+  const int rt = row / rows_per_tile, rr = row - rt * rows_per_tile;
+  const int kb = k >> 5, kc = (k & 31) >> 3;
+  const int64_t tile_h = (int64_t)rows_per_tile * OZ_KBLK;
+  return (((int64_t)rt * KB + kb) * OZ_PLANES + p) * tile_h + (((int64_t)kc * G + (rr >> 3)) * 8 + (rr & 7)) * 8 +
+         (k & 7);
+}
+
+// exponent of the expansion for a non-zero magnitude: |x| < 2^(e - 1)
+__device__ __forceinline__ int oz_exp_of(double ax) { return ilogb(ax) + 2; }
+
+__device__ __forceinline__ void oz_put(__nv_bfloat16 *dst, int row, int k, int KB, int G, int e, double x) {
+  double y = (e == OZ_EXP_EMPTY) ? 0.0 : scalbn(x, -e);  // |y| < 1/2, exact
+#pragma unroll
+  for (int p = 0; p < OZ_PLANES; ++p) {
+    y *= 128.0;
+    const double dg = rint(y);
+    y -= dg;
+    dst[oz_off(row, k, KB, G, p)] = __float2bfloat16_rn((float)dg);
+  }
+}
+
+__device__ __forceinline__ double oz_src(const PackSeg &s, double *const *bufs, int r, int k) {
+  const int64_t si = s.trans ? (int64_t)k * s.src_ld + r : (int64_t)r * s.src_ld + k;
+  return s.src_fp32 ? (double)((const float *)bufs[s.sb * NBUF + s.src_buf])[s.src_off + si]
+                    : bufs[s.sb * NBUF + s.src_buf][s.src_off + si];
+}
+
+// exponents of rows whose K range spans several segments
+__global__ void oz_exp_kernel(const PackSeg *__restrict__ segs, double *const *__restrict__ bufs,
+                              const int *__restrict__ active) {
+  const PackSeg s = segs[blockIdx.x];
+  if (active && !active[s.sb]) return;
+  const int r0 = blockIdx.y * PROWS;
+  if (r0 >= s.rows || s.whole) return;
+  const int r1 = min(s.rows, r0 + PROWS);
+  int *ex = (int *)bufs[s.sb * NBUF + BUF_OEXP] + s.exp_off + s.row0;
+  const int n = (r1 - r0) * s.ks;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = r0 + e / s.ks, k = e % s.ks;
+    const double x = oz_src(s, bufs, r, k);
+    if (x != 0.0) atomicMax(ex + r, oz_exp_of(fabs(x)));
+  }
+}
+
+// digits; a segment that holds the whole K range of its rows finds their
+// exponents itself (and stores them), the others read them
+__global__ void oz_pack_kernel(const PackSeg *__restrict__ segs, double *const *__restrict__ bufs,
+                               const int *__restrict__ active) {
+  __shared__ int rexp[PROWS];
+  const PackSeg s = segs[blockIdx.x];
+  if (active && !active[s.sb]) return;
+  const int r0 = blockIdx.y * PROWS;
+  if (r0 >= s.rows) return;
+  const int r1 = min(s.rows, r0 + PROWS);
+  int *ex = (int *)bufs[s.sb * NBUF + BUF_OEXP] + s.exp_off + s.row0;
+  __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>(bufs[s.sb * NBUF + s.dst_buf]) + s.dst_off;
+  const int n = (r1 - r0) * s.ks;
+  if (s.whole) {
+    if (threadIdx.x < PROWS) rexp[threadIdx.x] = OZ_EXP_EMPTY;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int r = r0 + e / s.ks, k = e % s.ks;
+      const double x = oz_src(s, bufs, r, k);
+      if (x != 0.0) atomicMax(&rexp[r - r0], oz_exp_of(fabs(x)));
+    }
+    __syncthreads();
+    if (threadIdx.x < r1 - r0) ex[r0 + threadIdx.x] = rexp[threadIdx.x];
+  } else {
+    if (threadIdx.x < r1 - r0) rexp[threadIdx.x] = ex[r0 + threadIdx.x];
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = r0 + e / s.ks, k = e % s.ks;
+    oz_put(dst, s.row0 + r, s.k0 + k, s.KB, s.G, rexp[r - r0], oz_src(s, bufs, r, k));
+  }
+}
+
+// T3 = sum W12 T1 in FP64 from the FP64 stage-1 output: pass 0 finds the
+// row exponents (atomic max over the tasks sharing a row), pass 1 writes the
+// digits
+__global__ void wstage_oz_kernel(const WTaskP *__restrict__ tasks, const WTerm *__restrict__ terms,
+                                 double *const *__restrict__ bufs, const int *__restrict__ active, int pass) {
+  const WTaskP t = tasks[blockIdx.x];
+  if (active && !active[t.sb]) return;
+  const int r0 = blockIdx.y * PROWS;
+  if (r0 >= t.rows) return;
+  const int r1 = min(t.rows, r0 + PROWS);
+  const double *in = bufs[t.sb * NBUF + t.in_buf];
+  int *ex = (int *)bufs[t.sb * NBUF + BUF_OEXP] + t.exp_off + t.row0;
+  __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>(bufs[t.sb * NBUF + t.dst_buf]) + t.dst_off;
+  const int n = (r1 - r0) * t.cols;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = r0 + e / t.cols, c = e % t.cols;
+    double acc = 0.0;
+    for (int q = 0; q < t.nterm; ++q) {
+      const WTerm w = terms[t.term0 + q];
+      acc = fma(w.coef, in[w.in_off + (int64_t)r * w.in_ld + c], acc);
+    }
+    if (pass == 0) {
+      if (acc != 0.0) atomicMax(ex + r, oz_exp_of(fabs(acc)));
+    } else {
+      oz_put(dst, t.row0 + r, t.k0 + c, t.KB, t.G, ex[r], acc);
+    }
+  }
+}
+
+constexpr int OZ_A_PLANE = TM * OZ_KBLK * 2;       // bytes of one A digit plane of a K block
+constexpr int OZ_B_PLANE = TC_TN * OZ_KBLK * 2;
+constexpr int OZ_STAGE = OZ_PLANES * (OZ_A_PLANE + OZ_B_PLANE);
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_TMEM_COLS = 512;                  // 8 levels x 64 columns
+
+__global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__ tiles,
+                                                      const TcTask *__restrict__ tasks,
+                                                      double *const *__restrict__ bufs,
+                                                      const int *__restrict__ active, int *err) {
+  extern __shared__ __align__(1024) uint8_t osm[];
+  __shared__ __align__(8) uint64_t full[OZ_STAGES], empty[OZ_STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const TcTile tile = tiles[blockIdx.x];
+  const TcTask T = tasks[tile.task];
+  if (active && !active[T.sb]) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, OZ_TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&done, 1);
+    abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  if (threadIdx.x == 0 && T.KB > 0) {
+    const uint8_t *A = reinterpret_cast<const uint8_t *>(bufs[T.sb * NBUF + T.a_buf]) + 2 * T.a_off +
+                       (int64_t)tile.mt * T.KB * OZ_PLANES * OZ_A_PLANE;
+    const uint8_t *B = reinterpret_cast<const uint8_t *>(bufs[T.sb * NBUF + T.b_buf]) + 2 * T.b_off +
+                       (int64_t)tile.nt * T.KB * OZ_PLANES * OZ_B_PLANE;
+    constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, 1u);
+    constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TC_TN / 8) * 128, sbo = 128;
+    auto issue = [&](int kb) {
+      const int s = kb % OZ_STAGES;
+      uint8_t *st = osm + s * OZ_STAGE;
+      tc::mbar_arrive_expect_tx(&full[s], (uint32_t)OZ_STAGE);
+      tc::bulk_g2s(st, A + (int64_t)kb * OZ_PLANES * OZ_A_PLANE, OZ_PLANES * OZ_A_PLANE, &full[s]);
+      tc::bulk_g2s(st + OZ_PLANES * OZ_A_PLANE, B + (int64_t)kb * OZ_PLANES * OZ_B_PLANE, OZ_PLANES * OZ_B_PLANE,
+                   &full[s]);
+    };
+    bool ok = true;
+    for (int kb = 0; kb < T.KB && kb < OZ_STAGES - 1; ++kb) issue(kb);
+    for (int kb = 0; kb < T.KB && ok; ++kb) {
+      const int kn = kb + OZ_STAGES - 1;
+      if (kn < T.KB) {
+        const int sn = kn % OZ_STAGES;
+        if (kn >= OZ_STAGES && !tc::mbar_wait(&empty[sn], ((kn / OZ_STAGES) - 1) & 1, WAIT_BUDGET)) {
+          ok = false;
+          break;
+        }
+        issue(kn);
+      }
+      const int s = kb % OZ_STAGES;
+      if (!tc::mbar_wait(&full[s], (kb / OZ_STAGES) & 1, WAIT_BUDGET)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(osm + s * OZ_STAGE);
+      const uint32_t sb = sa + OZ_PLANES * OZ_A_PLANE;
+#pragma unroll
+      for (int kk = 0; kk < OZ_KBLK / 16; ++kk) {
+#pragma unroll
+        for (int p = 0; p < OZ_PLANES; ++p) {
+          const uint64_t ad = tc::smem_desc(sa + p * OZ_A_PLANE + kk * 2 * lboA, lboA, sbo);
+#pragma unroll
+          for (int q = 0; q < OZ_PLANES - p; ++q) {
+            const uint64_t bd = tc::smem_desc(sb + q * OZ_B_PLANE + kk * 2 * lboB, lboB, sbo);
+            tc::mma_f16(tmem + (uint32_t)(TC_TN * (p + q)), ad, bd, idesc, (kb > 0 || kk > 0 || p > 0) ? 1u : 0u);
+          }
+        }
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    if (!ok) {
+      atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+      abort_flag = 1;
+    }
+  }
+  if (threadIdx.x == 0) tc::mma_commit(&done);  // fires when every MMA issued above has completed
+  const bool ready = tc::mbar_wait(&done, 0, WAIT_BUDGET);
+  if (!ready && lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (ready && !abort_flag) {
+    const int row = tile.mt * TM + 32 * warp + lane;
+    const int col0 = tile.nt * TC_TN;
+    double *cbase = bufs[T.sb * NBUF + T.c_buf];
+    const int *ex = (const int *)bufs[T.sb * NBUF + BUF_OEXP];
+    const int ea = row < T.M ? ex[T.a_exp + row] : OZ_EXP_EMPTY;
+    int64_t obase = 0;
+    if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
+#pragma unroll 1
+    for (int c = 0; c < TC_TN; c += 16) {
+      double acc[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+      if (T.KB > 0) {
+#pragma unroll 1
+        for (int t = OZ_PLANES - 1; t >= 0; --t) {  // small levels first
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(TC_TN * t + c), v);
+          const double sc = scalbn(1.0, -7 * (t + 2));
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[i] = fma((double)v[i], sc, acc[i]);
+        }
+      }
+      if (row < T.M) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int col = col0 + c + i;
+          if (col >= T.N) break;
+          const int eb = ex[T.b_exp + col];
+          const double val = (ea == OZ_EXP_EMPTY || eb == OZ_EXP_EMPTY) ? 0.0 : scalbn(acc[i], ea + eb);
+          if (T.mode == 1)
+            cbase[obase + col] = val;
+          else
+            cbase[T.c_off + (int64_t)row * T.ldc + col] = val;
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, OZ_TMEM_COLS);
+}
+
 }  // namespace
+
+cudaError_t launch_oz_exp(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
+                          cudaStream_t st) {
+  if (nseg > 0 && max_rows > 0) {
+    dim3 grid(nseg, (max_rows + PROWS - 1) / PROWS);
+    oz_exp_kernel<<<grid, 256, 0, st>>>(segs, bufs, active);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
+                           cudaStream_t st) {
+  if (nseg > 0 && max_rows > 0) {
+    dim3 grid(nseg, (max_rows + PROWS - 1) / PROWS);
+    oz_pack_kernel<<<grid, 256, 0, st>>>(segs, bufs, active);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wstage_oz(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
+                             double *const *bufs, const int *active, int pass, cudaStream_t st) {
+  if (ntasks > 0 && max_rows > 0) {
+    dim3 grid(ntasks, (max_rows + PROWS - 1) / PROWS);
+    wstage_oz_kernel<<<grid, 256, 0, st>>>(tasks, terms, bufs, active, pass);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
+                           const int *active, int *err, cudaStream_t st) {
+  const int smem = OZ_STAGES * OZ_STAGE;
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (ntiles > 0) oz_gemm_kernel<<<ntiles, 128, smem, st>>>(tiles, tasks, bufs, active, err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
                         int bf16, cudaStream_t st) {
