@@ -11,7 +11,7 @@ The headline is the mixed-precision path (H_eff psi on the tensor cores in
 TF32x3, Lanczos and SVD in FP64); the same run times the FP64 path on the
 same workload and reports the largest |dE/site| between the two.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|bf16x3|fp64] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|bf16x3|fp64|fp64tc] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own
 disorder realisation (seed 1606 + rank): independent problems, no exchange.
@@ -160,12 +160,14 @@ def class_roofline(name: str, d: dict, prec: str, pk: dict):
     sec = d["ms"] * 1e-3
     out = {"kernel": name, "launch_ms": d["ms"] / max(d["launches"], 1), "traffic": traffic_for(name, prec)}
     if name in ("heff_gemm", "heff_wstage") and prec != "fp64":
-        bf = prec == "bf16x3"
+        bf = prec in ("bf16x3", "fp64tc")
         peak = pk["bf16_sustained"] * (1.0 if bf else 1.1 / 2.25)
         achieved = d["flops"] / sec / 1e12 if sec > 0 else 0.0
         src = "sustained bf16" if bf else "sustained bf16 x nominal tf32/bf16 (1.1/2.25)"
+        what = ("FP64 products counted once (36 BF16 digit products each)" if prec == "fp64tc"
+                else "split products counted once")
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": f"{pk['src']} {src}; split products counted once"})
+                    "peak_source": f"{pk['src']} {src}; {what}"})
     elif name in ("heff_gemm", "heff_wstage", "heff_f64", "svd", "env", "predict"):
         achieved = d["flops"] / sec / 1e9 if sec > 0 else 0.0
         out.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
@@ -320,7 +322,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3", "fp64tc"])
     ap.add_argument("--m", type=int, default=256)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -372,11 +374,13 @@ def main():
         "metric": METRIC, "value": job_value(world, args.steps, t_dev), "unit": "unit-cell steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.prec == "fp64" else f"{args.prec}+f64",
+        "dtype": {"fp64": "f64", "fp64tc": "bf16-digits(f64)+f64"}.get(args.prec, f"{args.prec}+f64"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "ell": 16, "m": args.m, "solves_per_step": 8, "seed": seed,
                    "regime": f"saturated (n > {SATURATE}, D = {int(max(last['kept']))})",
                    "precision": args.prec + ("" if args.prec == "fp64" else " H_eff psi; FP64 Lanczos and SVD"),
+                   "fp64_restart_matvecs": "BF16 digit slices on the tensor cores (FP64-accurate)"
+                   if args.prec in ("tf32x3", "bf16x3") else None,
                    "parallelism": f"{world} independent realisation(s), one per GPU",
                    "l2": "flushed before every timed step (256 MiB write, outside the events)"},
         "roofline": roof,

@@ -53,8 +53,12 @@ typedef enum {
   IDMRG_TF32X3 = 1,  /* tensor cores, TF32 split (hi/lo) operands, three
                         products per term, FP32 accumulation; energies refined
                         by an FP64 Rayleigh quotient                          */
-  IDMRG_BF16X3 = 2   /* as TF32X3 with BF16 splits (kind::f16 MMAs, ~16 bits
+  IDMRG_BF16X3 = 2,  /* as TF32X3 with BF16 splits (kind::f16 MMAs, ~16 bits
                         per product, twice the K per instruction)             */
+  IDMRG_FP64_TC = 3  /* FP64-accurate H_eff psi on the tensor cores from BF16
+                        digit slices (see idmrg_heff_apply_fp64, form 1); one
+                        Lanczos run as in IDMRG_FP64; environments, prediction
+                        and SVD in FP64                                       */
 } idmrg_precision;
 
 /* The MPO of one period (Sec. 2, Eq. mpo; Sec. 3, Eq. mpo2).  Host memory,
@@ -165,11 +169,11 @@ idmrg_status idmrg_heff_apply(idmrg_ctx *ctx, int p, const double *psi_dev, doub
 /* The same product in one of the FP64-accurate forms, whatever opts.prec:
  * form 0 = FP64 GEMMs on the CUDA cores; form 1 = BF16 digit slices on the
  * tensor cores (the Ozaki scheme: eight 7-bit digits per element against a
- * per-row power of two, exact integer sums per digit level, levels summed in
- * FP64).  Form 1 exists only in a mixed-precision context (TF32X3 / BF16X3),
- * and only while every GEMM task's K is at most 768 (exactness of the digit
- * sums); the Lanczos restarts then use it for their FP64 matvecs.
- * Otherwise IDMRG_EINVAL. */
+ * per-row power of two, exact integer sums per digit level over K chunks of
+ * at most 768, levels and chunks summed in FP64).  Form 1 exists in
+ * TF32X3 / BF16X3 contexts (whose Lanczos restarts use it for their FP64
+ * matvecs) and in FP64_TC contexts (every matvec); otherwise
+ * IDMRG_EINVAL. */
 idmrg_status idmrg_heff_apply_fp64(idmrg_ctx *ctx, int p, const double *psi_dev, double *out_dev, int form);
 
 /* Step 3': start vector of superblock p (or all): Eq. wfprediction for
@@ -245,10 +249,10 @@ typedef enum {
   IDMRG_K_SVD = 4,         /* sector SVD, selection, compaction (Step 4)       */
   IDMRG_K_ENV = 5,         /* block-spin transformation (Step 6)               */
   IDMRG_K_PREDICT = 6,     /* start vectors (Step 3')                          */
-  IDMRG_K_HEFF_F64 = 7,    /* mixed precision only: the FP64 H_eff psi GEMM
-                              stages that start every Lanczos restart (the
-                              true-residual checks); FP64 mode books its
-                              GEMMs under IDMRG_K_HEFF_GEMM                   */
+  IDMRG_K_HEFF_F64 = 7,    /* mixed precision only: the FP64-accurate H_eff
+                              psi GEMM stages that start every Lanczos restart
+                              (the true-residual checks); FP64 and FP64_TC
+                              book theirs under IDMRG_K_HEFF_GEMM             */
   IDMRG_K_COUNT = 8
 } idmrg_kernel_class;
 idmrg_status idmrg_profile_enable(idmrg_ctx *ctx, int on);

@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "libidmrg.so")
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ENUMERIC",
           7: "ESTATE"}
-PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "fp64tc": 3}
 
 EXPORTED_SYMBOLS = [
     "idmrg_default_opts", "idmrg_create", "idmrg_destroy", "idmrg_last_error", "idmrg_set_stream",

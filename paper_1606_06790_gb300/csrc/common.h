@@ -45,7 +45,8 @@ enum BufId {
   BUF_OB3 = 28,   // stage 3 B digits
   BUF_ORMAP = 29, // stage 3 output row -> psi offset (int64)
   BUF_OEXP = 30,  // per packed row: exponent of the digit expansion (int32)
-  NBUF = 31
+  BUF_OT3 = 31,   // stage 3 A in FP64 (row-major per task) before its digits
+  NBUF = 32
 };
 
 
@@ -265,7 +266,8 @@ struct WTaskP {           // T3 rectangle written into a packed stage-3 A matrix
   int row0, k0, KB, G;
   int sb, rows, cols, term0, nterm;
   int in_buf, dst_buf;    // stage-1 output read, packed A written
-  int pad;
+  int t3_ld;              // digit form: T3 stored at t3_off, rows of t3_ld (the task's K)
+  int64_t t3_off;
 };
 struct TcTask {
   int64_t a_off, b_off, c_off, rmap_off;
@@ -274,6 +276,8 @@ struct TcTask {
   int a_buf, b_buf, c_buf, rmap_buf;
   int mode, ldc;          // mode 0: FP32 row-major C; 1: FP64 through the row map;
                           // 2: FP64 row-major C
+  int kb0, kb_stride;     // digit form: first K block of this K chunk, K blocks of the packed rows
+  int accum, pad;         // digit form: add to C (later K chunks) instead of storing
 };
 struct TcTile {
   int task, mt, nt, pad;
@@ -288,7 +292,8 @@ cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks,
                            const int *active, int *err, int bf16, cudaStream_t st);
 // FP64-accurate products from BF16 digit slices (OZ_PLANES digits of 7 bits
 // per element, exact integer accumulation per digit level).  K blocks are 32
-// elements; a task's K may not exceed OZ_MAX_K (exactness of the FP32 sums).
+// elements; one launch sums at most OZ_MAX_K of K exactly, longer K runs as
+// successive chunks that add their FP64 results to C.
 constexpr int OZ_PLANES = 8;
 constexpr int OZ_KBLK = 32;
 constexpr int OZ_MAX_K = 768;

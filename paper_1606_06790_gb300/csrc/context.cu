@@ -129,7 +129,9 @@ struct idmrg_ctx {
   // mixed precision (tensor cores)
   bool mixed = false;
   int bf16 = 0;  // mixed with BF16 splits (64 K per packed block) instead of TF32 (32)
-  bool o_oz = true;  // FP64 restart matvecs from digit slices when the K bound allows
+  bool o_oz = true;    // FP64 matvecs from digit slices (mixed restarts, FP64_TC)
+  bool fp64tc = false; // IDMRG_FP64_TC: every matvec from digit slices, one Lanczos run
+  bool oz_active() const { return oz_ok && o_oz && (mixed || fp64tc); }
   std::vector<PackSeg> pk_step, pk_psi;   // per iteration (L, R) and per matvec (psi)
   std::vector<TcTask> tc1k, tc3k;
   std::vector<TcTile> tc1t, tc3t;
@@ -148,9 +150,10 @@ struct idmrg_ctx {
   std::vector<WTaskP> ozw;
   int oz_step_w_rows = 0, oz_step_p_rows = 0, oz_psi_rows = 0, ozw_rows = 0;
   int64_t oz_a3_lo = 0, oz_a3_hi = 0, oz_b3_lo = 0, oz_b3_hi = 0;  // exponent ranges reset before use
+  std::vector<int> oz1_lo, oz3_lo;  // tile ranges of the K chunks (one launch each)
   std::vector<WTerm> wtpm_oz;
   DevBuf dozsw, dozsp, dozp, doz1k, doz1t, doz3k, doz3t, dozw, dozwm, oexp;
-  std::vector<DevBuf> bOA1, bOB1, bOT1, bOA3, bOB3, bORMAP;
+  std::vector<DevBuf> bOA1, bOB1, bOT1, bOA3, bOB3, bORMAP, bOT3;
 
   // plan for iteration n
   std::vector<SBPlan> plan;
@@ -587,7 +590,9 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
   if (c->mixed) {
     idmrg_status s = plan_mixed(c);
     if (s != IDMRG_OK) return s;
-    s = plan_oz(c);
+  }
+  if (c->mixed || c->fp64tc) {
+    idmrg_status s = plan_oz(c);
     if (s != IDMRG_OK) return s;
   }
   for (int p = 0; p < P; ++p) c->stage[p] = ST_READY;
@@ -834,8 +839,9 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
 // digit planes and one exponent per packed row.  Exponents of every
 // superblock live in one array: [stage-1 A and B rows | stage-3 B rows |
 // stage-3 A rows]; the last two ranges are reset before their atomic
-// maxima are taken.  Left off (oz_ok = false) when some task's K exceeds
-// OZ_MAX_K, the bound of exact digit sums.
+// maxima are taken.  Tasks whose K exceeds OZ_MAX_K (the bound of exact
+// digit sums) run in K chunks, one launch per chunk, later chunks adding
+// their FP64 results.
 idmrg_status plan_oz(idmrg_ctx *c) {
   const int P = c->P, d = c->d, target = c->o.target_charge, dd = d * d;
   const int GA = 16, GB = TC_TN / 8;
@@ -852,22 +858,6 @@ idmrg_status plan_oz(idmrg_ctx *c) {
   c->ozw.clear();
   c->wtpm_oz.clear();
   c->oz_step_w_rows = c->oz_step_p_rows = c->oz_psi_rows = c->ozw_rows = 0;
-  // K of every task first: nothing is allocated when the bound fails
-  for (int p = 0; p < P; ++p) {
-    const Env &L = c->envL[p];
-    const Env &R = c->envR[(p + 1) % P];
-    const Basis &BL = L.lay.b, &BR = R.lay.b;
-    for (int si = 0; si < BL.S(); ++si)
-      if (BL.dim[si] > OZ_MAX_K) return IDMRG_OK;
-    for (int jo = 0; jo < BR.S(); ++jo) {
-      int K = 0;
-      for (int cc = 0; cc < R.lay.w; ++cc) {
-        const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
-        if (jin >= 0 && R.lay.so[cc * BR.S() + jin] == jo) K += BR.dim[jin];
-      }
-      if (K > OZ_MAX_K) return IDMRG_OK;
-    }
-  }
   auto seg = [&](std::vector<PackSeg> &v, int &mr, int sb, int dst_buf, int64_t dst_off, int src_buf,
                  int64_t src_off, int64_t exp_off, int row0, int k0, int rows, int ks, int ld, int trans, int KB,
                  int G, int whole) {
@@ -891,11 +881,31 @@ idmrg_status plan_oz(idmrg_ctx *c) {
     v.push_back(q);
     mr = std::max(mr, rows);
   };
+  // a task in K chunks of at most OZ_MAX_K (exact digit sums); the tiles of
+  // chunk c go to lists[c], launched one chunk after the other
+  std::vector<std::vector<TcTile>> t1c, t3c;
+  auto add_task = [&](std::vector<TcTask> &tasks, std::vector<std::vector<TcTile>> &lists, TcTask t, int MT,
+                      int NT) {
+    const int KBt = t.KB, per = OZ_MAX_K / OZ_KBLK;
+    const int nch = KBt > 0 ? (KBt + per - 1) / per : 1;
+    if ((int)lists.size() < nch) lists.resize(nch);
+    for (int ch = 0; ch < nch; ++ch) {
+      TcTask u = t;
+      u.kb_stride = KBt;
+      u.kb0 = ch * per;
+      u.KB = KBt > 0 ? std::min(per, KBt - u.kb0) : 0;
+      u.accum = ch > 0 ? 1 : 0;
+      const int id = (int)tasks.size();
+      tasks.push_back(u);
+      for (int mt = 0; mt < MT; ++mt)
+        for (int nt = 0; nt < NT; ++nt) lists[ch].push_back(TcTile{id, mt, nt, 0});
+    }
+  };
   int64_t ex1 = 0, exb3 = 0, exa3 = 0;  // the three exponent ranges, relative
   const size_t b3seg0 = 0;
   std::vector<size_t> a3_tasks, b3_tasks;  // tasks / items whose offsets get the range bases
   std::vector<std::vector<int64_t>> rmaps(P);
-  std::vector<int64_t> na1(P), nb1(P), nt1(P), na3(P), nb3(P);
+  std::vector<int64_t> na1(P), nb1(P), nt1(P), na3(P), nb3(P), nt3(P);
   for (int p = 0; p < P; ++p) {
     SBPlan &S = c->plan[p];
     const Env &L = c->envL[p];
@@ -948,13 +958,10 @@ idmrg_status plan_oz(idmrg_ctx *c) {
       t.c_buf = BUF_OT1;
       t.mode = 2;
       t.ldc = N;
-      const int id = (int)c->oz1k.size();
-      c->oz1k.push_back(t);
-      for (int mt = 0; mt < MT; ++mt)
-        for (int nt = 0; nt < NT; ++nt) c->oz1t.push_back(TcTile{id, mt, nt, 0});
+      add_task(c->oz1k, t1c, t, MT, NT);
     }
     // ---------------- stage 3
-    int64_t pa3n = 0, pb3n = 0;
+    int64_t pa3n = 0, pb3n = 0, nt3s = 0;
     std::vector<int64_t> &rmap = rmaps[p];
     for (int jo = 0; jo < SR; ++jo) {
       std::vector<int> ks(wc, -1);
@@ -981,6 +988,8 @@ idmrg_status plan_oz(idmrg_ctx *c) {
       const int N = BR.dim[jo];
       const int KB = (int)cdiv(std::max(K, 1), OZ_KBLK), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
       const int64_t pa = pa3n, pb = pb3n, ea = exa3, eb = exb3;
+      const int64_t t3n = nt3s;
+      nt3s += (int64_t)M * K;
       pa3n += (int64_t)MT * KB * TA;
       pb3n += (int64_t)NT * KB * TB;
       exa3 += M;
@@ -1011,6 +1020,8 @@ idmrg_status plan_oz(idmrg_ctx *c) {
               w.cols = BR.dim[jin];
               w.in_buf = BUF_OT1;
               w.dst_buf = BUF_OA3;
+              w.t3_off = t3n;
+              w.t3_ld = K;
               w.term0 = (int)c->wtpm_oz.size();
               for (int a = 0; a < wa; ++a) {
                 const int si = BL.find(BL.q[i] - L.lay.chq[a]);
@@ -1049,19 +1060,27 @@ idmrg_status plan_oz(idmrg_ctx *c) {
       t.c_buf = BUF_OUT;
       t.rmap_buf = BUF_ORMAP;
       t.mode = 1;
-      const int id = (int)c->oz3k.size();
-      c->oz3k.push_back(t);
-      for (int mt = 0; mt < MT; ++mt)
-        for (int nt = 0; nt < NT; ++nt) c->oz3t.push_back(TcTile{id, mt, nt, 0});
+      add_task(c->oz3k, t3c, t, MT, NT);
     }
     na1[p] = pa1n;
     nb1[p] = pb1n;
     nt1[p] = t1n;
     na3[p] = pa3n;
     nb3[p] = pb3n;
+    nt3[p] = nt3s;
   }
   (void)b3seg0;
   (void)target;
+  auto flatten = [](const std::vector<std::vector<TcTile>> &lists, std::vector<TcTile> &out, std::vector<int> &lo) {
+    out.clear();
+    lo.assign(1, 0);
+    for (const auto &l : lists) {
+      out.insert(out.end(), l.begin(), l.end());
+      lo.push_back((int)out.size());
+    }
+  };
+  flatten(t1c, c->oz1t, c->oz1_lo);
+  flatten(t3c, c->oz3t, c->oz3_lo);
   // exponent ranges: stage-3 B after stage 1, stage-3 A last
   c->oz_b3_lo = ex1;
   c->oz_b3_hi = ex1 + exb3;
@@ -1079,7 +1098,8 @@ idmrg_status plan_oz(idmrg_ctx *c) {
           c->ensure(c->bOB1[p], 2 * std::max<int64_t>(nb1[p], 8)) &&
           c->ensure(c->bOT1[p], 8 * std::max<int64_t>(nt1[p], 1)) &&
           c->ensure(c->bOA3[p], 2 * std::max<int64_t>(na3[p], 8)) &&
-          c->ensure(c->bOB3[p], 2 * std::max<int64_t>(nb3[p], 8)) && c->upload(c->bORMAP[p], rmaps[p]));
+          c->ensure(c->bOB3[p], 2 * std::max<int64_t>(nb3[p], 8)) &&
+          c->ensure(c->bOT3[p], 8 * std::max<int64_t>(nt3[p], 1)) && c->upload(c->bORMAP[p], rmaps[p]));
     // zero digits in the padding (only real elements are rewritten later)
     CK(cudaMemsetAsync(c->bOA1[p].p, 0, 2 * na1[p], c->st));
     CK(cudaMemsetAsync(c->bOB1[p].p, 0, 2 * nb1[p], c->st));
@@ -1092,6 +1112,7 @@ idmrg_status plan_oz(idmrg_ctx *c) {
     c->hbufs[p * NBUF + BUF_OB3] = c->dp(c->bOB3[p]);
     c->hbufs[p * NBUF + BUF_ORMAP] = c->dp(c->bORMAP[p]);
     c->hbufs[p * NBUF + BUF_OEXP] = c->dp(c->oexp);
+    c->hbufs[p * NBUF + BUF_OT3] = c->dp(c->bOT3[p]);
   }
   NOMEM(c->upload(c->dozsw, c->oz_step_w) && c->upload(c->dozsp, c->oz_step_p) && c->upload(c->dozp, c->oz_psi) &&
         c->upload(c->doz1k, c->oz1k) && c->upload(c->doz1t, c->oz1t) && c->upload(c->doz3k, c->oz3k) &&
@@ -1120,10 +1141,15 @@ idmrg_status heff_launch_oz(idmrg_ctx *c, const int *active_dev, const int *act)
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_oz_pack((const PackSeg *)c->dozp.p, (int)c->oz_psi.size(), c->oz_psi_rows, bufs, active_dev, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE);
-  c->kbegin(IDMRG_K_HEFF_F64);
-  CK(launch_oz_gemm((const TcTile *)c->doz1t.p, (int)c->oz1t.size(), (const TcTask *)c->doz1k.p, bufs, active_dev,
-                    (int *)c->derr.p, c->st));
-  c->kend(IDMRG_K_HEFF_F64);
+  // booked as the restart matvecs of a mixed context, as the H_eff GEMMs of FP64_TC
+  const int kg = c->mixed ? IDMRG_K_HEFF_F64 : IDMRG_K_HEFF_GEMM;
+  c->kbegin(kg);
+  for (size_t ch = 0; ch + 1 < c->oz1_lo.size(); ++ch) {
+    CK(launch_oz_gemm((const TcTile *)c->doz1t.p + c->oz1_lo[ch], c->oz1_lo[ch + 1] - c->oz1_lo[ch],
+                      (const TcTask *)c->doz1k.p, bufs, active_dev, (int *)c->derr.p, c->st));
+    c->launches += 1;
+  }
+  c->kend(kg);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(cudaMemsetAsync((int *)c->oexp.p + c->oz_a3_lo, 0x80, 4 * (c->oz_a3_hi - c->oz_a3_lo), c->st));
   CK(launch_wstage_oz((const WTaskP *)c->dozw.p, (int)c->ozw.size(), c->ozw_rows, (const WTerm *)c->dozwm.p, bufs,
@@ -1131,11 +1157,14 @@ idmrg_status heff_launch_oz(idmrg_ctx *c, const int *active_dev, const int *act)
   CK(launch_wstage_oz((const WTaskP *)c->dozw.p, (int)c->ozw.size(), c->ozw_rows, (const WTerm *)c->dozwm.p, bufs,
                       active_dev, 1, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
-  c->kbegin(IDMRG_K_HEFF_F64);
-  CK(launch_oz_gemm((const TcTile *)c->doz3t.p, (int)c->oz3t.size(), (const TcTask *)c->doz3k.p, bufs, active_dev,
-                    (int *)c->derr.p, c->st));
-  c->kend(IDMRG_K_HEFF_F64, gf, by);
-  c->launches += 5;
+  c->kbegin(kg);
+  for (size_t ch = 0; ch + 1 < c->oz3_lo.size(); ++ch) {
+    CK(launch_oz_gemm((const TcTile *)c->doz3t.p + c->oz3_lo[ch], c->oz3_lo[ch + 1] - c->oz3_lo[ch],
+                      (const TcTask *)c->doz3k.p, bufs, active_dev, (int *)c->derr.p, c->st));
+    c->launches += 1;
+  }
+  c->kend(kg, gf, by);
+  c->launches += 3;
   c->fp64_matvecs += 1;
   return IDMRG_OK;
 }
@@ -1174,13 +1203,13 @@ idmrg_status heff_launch(idmrg_ctx *c, const int *active_dev, const int *act, bo
 }
 idmrg_status heff_launch_oz(idmrg_ctx *c, const int *active_dev, const int *act);
 idmrg_status heff_launch_fp64(idmrg_ctx *c, const int *active_dev, const int *act) {
-  if (c->mixed && c->oz_ok && c->o_oz) return heff_launch_oz(c, active_dev, act);
+  if (c->oz_active()) return heff_launch_oz(c, active_dev, act);
   c->fp64_matvecs += 1;
   double *const *bufs = (double *const *)c->dbufs.p;
   double gf = 0, wf = 0, by = 0;
   for (int q = 0; q < c->P; ++q)
     if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
-  const int kg = c->mixed ? IDMRG_K_HEFF_F64 : IDMRG_K_HEFF_GEMM;
+  const int kg = c->mixed ? IDMRG_K_HEFF_F64 : IDMRG_K_HEFF_GEMM;  // (FP64 GEMMs)
   c->kbegin(kg);
   {
     idmrg_status sg_ = gemm_run(c, c->tn_g1, c->dg1k, c->dg1s, active_dev);
@@ -1475,7 +1504,8 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
       // fixed (reduced precision, or FP64 with tuned GEMM tiles)
       const bool fp64 = it == 0 || !c->mixed;
       const bool as_graph = graph_ok && !c->prof &&
-                            (fp64 ? (!c->mixed && c->tn_g1.choice >= 0 && c->tn_g3.choice >= 0) : true);
+                            (fp64 ? (c->oz_active() || (!c->mixed && c->tn_g1.choice >= 0 && c->tn_g3.choice >= 0))
+                                  : true);
       if (as_graph && !iter_graph[fp64]) {
         const uint64_t l0 = c->launches, mm0 = c->mixed_matvecs, fm0 = c->fp64_matvecs;
         cudaGraph_t g = nullptr;
@@ -2306,9 +2336,11 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
     return bail(IDMRG_EINVAL);
   if (opts->m < 1 || opts->lanczos_maxit < 2 || opts->lanczos_maxit > 600 || !(opts->lanczos_tol > 0))
     return bail(IDMRG_EINVAL);
-  if (opts->prec != IDMRG_FP64 && opts->prec != IDMRG_TF32X3 && opts->prec != IDMRG_BF16X3)
+  if (opts->prec != IDMRG_FP64 && opts->prec != IDMRG_TF32X3 && opts->prec != IDMRG_BF16X3 &&
+      opts->prec != IDMRG_FP64_TC)
     return bail(IDMRG_EINVAL);
-  c->mixed = opts->prec != IDMRG_FP64;
+  c->mixed = opts->prec == IDMRG_TF32X3 || opts->prec == IDMRG_BF16X3;
+  c->fp64tc = opts->prec == IDMRG_FP64_TC;
   c->bf16 = opts->prec == IDMRG_BF16X3 ? 1 : 0;
   c->ell = ell;
   c->d = d;
@@ -2375,7 +2407,7 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
   c->bUT.resize(P);
   c->bVT.resize(P);
   for (auto *v : {&c->bPA1, &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP, &c->bOA1, &c->bOB1, &c->bOT1,
-                  &c->bOA3, &c->bOB3, &c->bORMAP})
+                  &c->bOA3, &c->bOB3, &c->bORMAP, &c->bOT3})
     v->resize(P);
   c->hbufs.assign((size_t)P * NBUF, nullptr);
   if (!c->ensure(c->derr, 256)) return bail(IDMRG_ENOMEM);
@@ -2426,7 +2458,7 @@ void idmrg_destroy(idmrg_ctx *c) {
     for (auto &t : *v) { rel(t.U); rel(t.V); }
   for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT, &c->bPA1,
                   &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP, &c->bOA1, &c->bOB1, &c->bOT1, &c->bOA3,
-                  &c->bOB3, &c->bORMAP})
+                  &c->bOB3, &c->bORMAP, &c->bOT3})
     for (auto &b : *v) rel(b);
   for (DevBuf *b : {&c->dbufs, &c->dg1k, &c->dg1s, &c->dg3k, &c->dg3s, &c->dwt, &c->dwm, &c->ddt,
                     &c->ddp, &c->drb, &c->dgpk, &c->dgps, &c->dst, &c->dstab, &c->dge1k,
@@ -2545,7 +2577,7 @@ idmrg_status idmrg_block_to_host(const idmrg_ctx *cc, int p, int side, double *h
 static idmrg_status heff_apply_form(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev, int form) {
   if (!c || !psi_dev || !out_dev) return IDMRG_EINVAL;
   if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
-  if (form == 1 && !(c->mixed && c->oz_ok)) return c->fail(IDMRG_EINVAL, "digit-slice form not available");
+  if (form == 1 && !c->oz_ok) return c->fail(IDMRG_EINVAL, "digit-slice form not available");
   std::vector<int> mask(c->P, 0);
   int64_t off = 0;
   std::vector<double *> save_in(c->P), save_out(c->P);

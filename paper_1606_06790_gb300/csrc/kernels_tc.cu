@@ -271,18 +271,43 @@ __device__ __forceinline__ int64_t oz_off(int row, int k, int KB, int G, int p) 
          (k & 7);
 }
 
-// exponent of the expansion for a non-zero magnitude: |x| < 2^(e - 1)
-__device__ __forceinline__ int oz_exp_of(double ax) { return ilogb(ax) + 2; }
+// exponent of the expansion for a non-zero x: |x| < 2^(e - 1)
+__device__ __forceinline__ int oz_exp_of(double x) {
+  const int be = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  return be ? be - 1023 + 2 : ilogb(x) + 2;
+}
 
+// The digits from the bits of x, in integer arithmetic (FP64 instructions are
+// scarce here): Y = round(x 2^(56 - e)), |Y| <= 2^55, then balanced base-128
+// digits (-64..63) from the least significant one up, the leading digit
+// taking what is left (|d_0| <= 64): Y = sum_p d_p 128^(7 - p).
 __device__ __forceinline__ void oz_put(__nv_bfloat16 *dst, int row, int k, int KB, int G, int e, double x) {
-  double y = (e == OZ_EXP_EMPTY) ? 0.0 : scalbn(x, -e);  // |y| < 1/2, exact
-#pragma unroll
-  for (int p = 0; p < OZ_PLANES; ++p) {
-    y *= 128.0;
-    const double dg = rint(y);
-    y -= dg;
-    dst[oz_off(row, k, KB, G, p)] = __float2bfloat16_rn((float)dg);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  long long Y = 0;
+  if (e != OZ_EXP_EMPTY && (bits << 1) != 0) {
+    const int be = (int)((bits >> 52) & 0x7FF);
+    unsigned long long mant = bits & ((1ull << 52) - 1);
+    int ex = -1074;  // x = mant 2^ex
+    if (be) {
+      mant |= 1ull << 52;
+      ex = be - 1075;
+    }
+    const int sh = ex + 56 - e;
+    unsigned long long u = 0;
+    if (sh >= 0)
+      u = mant << sh;  // sh <= 2 since |x| < 2^(e - 1)
+    else if (sh > -62)
+      u = (mant + (1ull << (-sh - 1))) >> (-sh);
+    Y = (bits >> 63) ? -(long long)u : (long long)u;
   }
+#pragma unroll
+  for (int p = OZ_PLANES - 1; p > 0; --p) {
+    int r = (int)(Y & 127);
+    if (r >= 64) r -= 128;
+    Y = (Y - r) >> 7;
+    dst[oz_off(row, k, KB, G, p)] = __float2bfloat16_rn((float)r);
+  }
+  dst[oz_off(row, k, KB, G, 0)] = __float2bfloat16_rn((float)Y);  // what is left: |Y| <= 64
 }
 
 __device__ __forceinline__ double oz_src(const PackSeg &s, double *const *bufs, int r, int k) {
@@ -299,13 +324,18 @@ __global__ void oz_exp_kernel(const PackSeg *__restrict__ segs, double *const *_
   const int r0 = blockIdx.y * PROWS;
   if (r0 >= s.rows || s.whole) return;
   const int r1 = min(s.rows, r0 + PROWS);
+  __shared__ int rexp[PROWS];
   int *ex = (int *)bufs[s.sb * NBUF + BUF_OEXP] + s.exp_off + s.row0;
   const int n = (r1 - r0) * s.ks;
+  if (threadIdx.x < PROWS) rexp[threadIdx.x] = OZ_EXP_EMPTY;
+  __syncthreads();
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int r = r0 + e / s.ks, k = e % s.ks;
     const double x = oz_src(s, bufs, r, k);
-    if (x != 0.0) atomicMax(ex + r, oz_exp_of(fabs(x)));
+    if (x != 0.0) atomicMax(&rexp[r - r0], oz_exp_of(x));
   }
+  __syncthreads();
+  if (threadIdx.x < r1 - r0 && rexp[threadIdx.x] != OZ_EXP_EMPTY) atomicMax(ex + r0 + threadIdx.x, rexp[threadIdx.x]);
 }
 
 // digits; a segment that holds the whole K range of its rows finds their
@@ -327,7 +357,7 @@ __global__ void oz_pack_kernel(const PackSeg *__restrict__ segs, double *const *
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
       const int r = r0 + e / s.ks, k = e % s.ks;
       const double x = oz_src(s, bufs, r, k);
-      if (x != 0.0) atomicMax(&rexp[r - r0], oz_exp_of(fabs(x)));
+      if (x != 0.0) atomicMax(&rexp[r - r0], oz_exp_of(x));
     }
     __syncthreads();
     if (threadIdx.x < r1 - r0) ex[r0 + threadIdx.x] = rexp[threadIdx.x];
@@ -341,31 +371,44 @@ __global__ void oz_pack_kernel(const PackSeg *__restrict__ segs, double *const *
   }
 }
 
-// T3 = sum W12 T1 in FP64 from the FP64 stage-1 output: pass 0 finds the
-// row exponents (atomic max over the tasks sharing a row), pass 1 writes the
-// digits
+// T3 = sum W12 T1 in FP64 from the FP64 stage-1 output.  Pass 0 stores T3
+// (row-major per stage-3 task, K = the task's full K) and takes the row
+// exponents (a maximum per block in shared memory, then one atomic per row
+// and block); pass 1 turns the stored values into digits.
 __global__ void wstage_oz_kernel(const WTaskP *__restrict__ tasks, const WTerm *__restrict__ terms,
                                  double *const *__restrict__ bufs, const int *__restrict__ active, int pass) {
+  __shared__ int rexp[PROWS];
   const WTaskP t = tasks[blockIdx.x];
   if (active && !active[t.sb]) return;
   const int r0 = blockIdx.y * PROWS;
   if (r0 >= t.rows) return;
   const int r1 = min(t.rows, r0 + PROWS);
-  const double *in = bufs[t.sb * NBUF + t.in_buf];
   int *ex = (int *)bufs[t.sb * NBUF + BUF_OEXP] + t.exp_off + t.row0;
-  __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>(bufs[t.sb * NBUF + t.dst_buf]) + t.dst_off;
+  double *t3 = bufs[t.sb * NBUF + BUF_OT3] + t.t3_off + (int64_t)t.row0 * t.t3_ld + t.k0;
   const int n = (r1 - r0) * t.cols;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int r = r0 + e / t.cols, c = e % t.cols;
-    double acc = 0.0;
-    for (int q = 0; q < t.nterm; ++q) {
-      const WTerm w = terms[t.term0 + q];
-      acc = fma(w.coef, in[w.in_off + (int64_t)r * w.in_ld + c], acc);
+  if (pass == 0) {
+    const double *in = bufs[t.sb * NBUF + t.in_buf];
+    if (threadIdx.x < PROWS) rexp[threadIdx.x] = OZ_EXP_EMPTY;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int r = r0 + e / t.cols, c = e % t.cols;
+      double acc = 0.0;
+      for (int q = 0; q < t.nterm; ++q) {
+        const WTerm w = terms[t.term0 + q];
+        acc = fma(w.coef, in[w.in_off + (int64_t)r * w.in_ld + c], acc);
+      }
+      t3[(int64_t)r * t.t3_ld + c] = acc;
+      if (acc != 0.0) atomicMax(&rexp[r - r0], oz_exp_of(acc));
     }
-    if (pass == 0) {
-      if (acc != 0.0) atomicMax(ex + r, oz_exp_of(fabs(acc)));
-    } else {
-      oz_put(dst, t.row0 + r, t.k0 + c, t.KB, t.G, ex[r], acc);
+    __syncthreads();
+    if (threadIdx.x < r1 - r0 && rexp[threadIdx.x] != OZ_EXP_EMPTY) atomicMax(ex + r0 + threadIdx.x, rexp[threadIdx.x]);
+  } else {
+    __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>(bufs[t.sb * NBUF + t.dst_buf]) + t.dst_off;
+    if (threadIdx.x < r1 - r0) rexp[threadIdx.x] = ex[r0 + threadIdx.x];
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int r = r0 + e / t.cols, c = e % t.cols;
+      oz_put(dst, t.row0 + r, t.k0 + c, t.KB, t.G, rexp[r - r0], t3[(int64_t)r * t.t3_ld + c]);
     }
   }
 }
@@ -407,9 +450,9 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
   const uint32_t tmem = tmem_base;
   if (threadIdx.x == 0 && T.KB > 0) {
     const uint8_t *A = reinterpret_cast<const uint8_t *>(bufs[T.sb * NBUF + T.a_buf]) + 2 * T.a_off +
-                       (int64_t)tile.mt * T.KB * OZ_PLANES * OZ_A_PLANE;
+                       ((int64_t)tile.mt * T.kb_stride + T.kb0) * OZ_PLANES * OZ_A_PLANE;
     const uint8_t *B = reinterpret_cast<const uint8_t *>(bufs[T.sb * NBUF + T.b_buf]) + 2 * T.b_off +
-                       (int64_t)tile.nt * T.KB * OZ_PLANES * OZ_B_PLANE;
+                       ((int64_t)tile.nt * T.kb_stride + T.kb0) * OZ_PLANES * OZ_B_PLANE;
     constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, 1u);
     constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TC_TN / 8) * 128, sbo = 128;
     auto issue = [&](int kb) {
@@ -494,10 +537,8 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
           if (col >= T.N) break;
           const int eb = ex[T.b_exp + col];
           const double val = (ea == OZ_EXP_EMPTY || eb == OZ_EXP_EMPTY) ? 0.0 : scalbn(acc[i], ea + eb);
-          if (T.mode == 1)
-            cbase[obase + col] = val;
-          else
-            cbase[T.c_off + (int64_t)row * T.ldc + col] = val;
+          double &dst = T.mode == 1 ? cbase[obase + col] : cbase[T.c_off + (int64_t)row * T.ldc + col];
+          dst = T.accum ? dst + val : val;
         }
       }
     }

@@ -85,6 +85,32 @@ def test_digit_form_at_bench_size():
     ctx.close()
 
 
+def test_digit_form_in_k_chunks():
+    """YC4 J1-J2 cylinder (MPO bond dimension up to 20) at m = 256: stage-3 K
+    (channels x right-sector dimension) passes the 768 bound of one exact
+    digit sum, so those tasks run in K chunks whose FP64 results add up."""
+    mpo, _ = make_config("yc4_j1j2_l8_m1024")
+    ctx = context(mpo, 256, prec="fp64tc")
+    for _ in range(9):
+        ctx.unit_cell_step()
+    import torch
+    rng = np.random.default_rng(9)
+    for p in range(ctx.P):
+        desc, N = ctx.psi_layout(p)
+        x = torch.tensor(rng.standard_normal(N), device="cuda", dtype=torch.float64)
+        y0 = torch.zeros_like(x)
+        y1 = torch.zeros_like(x)
+        ctx.heff_apply_fp64(p, x, y0, 0)
+        l0 = ctx.launch_count()
+        ctx.heff_apply(p, x, y1)
+        chunked = ctx.launch_count() - l0 > 5  # psi digits, 2 W-stage passes, one launch per K chunk
+        torch.cuda.synchronize()
+        err = (y1 - y0).abs().max().item() / y0.abs().max().item()
+        assert err < 1e-13, (p, err)
+        assert chunked, p
+    ctx.close()
+
+
 def test_digit_form_unavailable_in_fp64_context():
     mpo = build_mpo(random_chain_bonds(4, 0.5, 1.5, 3), 4)
     ctx = context(mpo, 16, prec="fp64")

@@ -1,6 +1,6 @@
 """CUDA path against the FP64 oracle, element by element on identical seeded
-inputs (FP64 mode: energies, bond energies and truncation errors within 1e-10
-per site; the matvec within 1e-12 relative)."""
+inputs (FP64 and FP64_TC modes: energies, bond energies and truncation errors
+within 1e-10 per site; the matvec within 1e-12 relative)."""
 import numpy as np
 import pytest
 
@@ -40,14 +40,17 @@ def _compare(g, r, tol=TOL_SITE):
         assert g["e_g"] is None
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp64tc"])
 @pytest.mark.parametrize("name,bonds,ell,m,steps", [
     ("chain_l4_m32", chain_bonds(4), 4, 32, 40),
     ("randchain_l8_m48", random_chain_bonds(8, 0.5, 1.5, 1606), 8, 48, 16),
     ("j1j2_l4_m24", j1j2_chain_bonds(4, 1.0, 0.3), 4, 24, 20),
     ("xx_l4_m20", xx_chain_bonds(4, 0.5, 1.5, 3), 4, 20, 16),
 ])
-def test_full_iteration_parity(name, bonds, ell, m, steps):
-    ctx, ref, out = _run_both(build_mpo(bonds, ell), m, steps)
+def test_full_iteration_parity(name, bonds, ell, m, steps, prec):
+    """FP64 GEMMs (fp64) and FP64-accurate digit slices on the tensor cores
+    (fp64tc) against the oracle, step by step."""
+    ctx, ref, out = _run_both(build_mpo(bonds, ell), m, steps, prec=prec)
     for g, r in out:
         _compare(g, r)
     ctx.close()
