@@ -262,6 +262,14 @@ idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t
 /* Shape of the last truncation's SVD work (Step 4): sector matrices, their
  * largest short side, largest numerical rank, and the Jacobi sweeps taken
  * (maximum and mean over the sectors). */
+/* Sector SVDs of the following truncations on the kernels for large sector
+ * matrices only (global_only = 1: pivoted QR in one CTA, FP32 and FP64
+ * cyclic Jacobi in global memory), or on the size-dependent choice (0, the
+ * default: sectors with at most 320 columns use the shared-memory block
+ * kernels).  The results agree to rounding; this exists to test the
+ * large-sector path on small problems. */
+idmrg_status idmrg_set_svd_path(idmrg_ctx *ctx, int global_only);
+
 idmrg_status idmrg_svd_stats(const idmrg_ctx *ctx, int *jobs, int *max_cols, int *max_rank, int *max_sweeps,
                              double *mean_sweeps);
 

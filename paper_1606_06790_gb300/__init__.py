@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
-    "idmrg_svd_stats", "idmrg_save", "idmrg_load",
+    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_save", "idmrg_load",
 ]
 
 KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
@@ -116,6 +116,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_save": (i, [vp, C.c_char_p]),
         "idmrg_load": (i, [vp, C.c_char_p]),
         "idmrg_svd_stats": (i, [vp, P(i), P(i), P(i), P(i), P(d)]),
+        "idmrg_set_svd_path": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -337,6 +338,10 @@ class Context:
                         "profile_read")
             out[name] = dict(ms=ms.value, launches=int(n.value), flops=f.value, bytes=b.value)
         return out
+
+    def set_svd_path(self, global_only: bool) -> None:
+        """Sector SVDs on the large-sector (global-memory) kernels only."""
+        self._check(self.lib.idmrg_set_svd_path(self.h, int(bool(global_only))), "set_svd_path")
 
     def svd_stats(self) -> Dict[str, float]:
         j, mc, mr, ms, me = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_double()

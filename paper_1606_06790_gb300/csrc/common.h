@@ -204,11 +204,13 @@ cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_e
 cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, double *work, int *iwork, double zero_rel,
                             cudaStream_t st);
 // the pivoted QR on thread-block clusters (groups as launch_svd_jacobi);
-// rows[k], cols[k]: largest rows and columns of block group k+1
+// rows[k], cols[k]: largest rows and columns of block group k+1; rows0,
+// cols0 those of group 0 (one CTA per job when they do not fit a cluster)
 size_t svd_qrc_smem(int rows, int cols, int csize);
 cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *rows,
-                                    const int *cols, double *work, int *iwork, double zero_rel, cudaStream_t st,
-                                    const cudaStream_t *side, const cudaEvent_t *ev);
+                                    const int *cols, int rows0, int cols0, double *work, int *iwork,
+                                    double zero_rel, cudaStream_t st, const cudaStream_t *side,
+                                    const cudaEvent_t *ev);
 // Jacobi groups and shared memory: see kernels_svd.cu
 constexpr size_t SVD_BLOCK_SMEM_MAX = 200 * 1024;
 size_t svd_block_smem(int cols, int csize);

@@ -129,6 +129,7 @@ struct idmrg_ctx {
   // mixed precision (tensor cores)
   bool mixed = false;
   int bf16 = 0;  // mixed with BF16 splits (64 K per packed block) instead of TF32 (32)
+  bool svd_global = false;  // sector SVDs on the global-memory Jacobi kernels only
   bool o_oz = true;    // FP64 matvecs from digit slices (mixed restarts, FP64_TC)
   bool fp64tc = false; // IDMRG_FP64_TC: every matvec from digit slices, one Lanczos run
   bool oz_active() const { return oz_ok && o_oz && (mixed || fp64tc); }
@@ -1623,6 +1624,10 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
 // count of block group k+1.
 void jacobi_groups(const idmrg_ctx *c, const int *ord, int m, int g[4], int gcols[4]) {
   for (int k = 0; k < 4; ++k) g[k] = gcols[k] = 0;
+  if (c->svd_global) {  // every job on the global-memory kernels
+    for (int k = 0; k < 4; ++k) g[k] = m;
+    return;
+  }
   for (int j = 0; j < m; ++j) {
     const int ca = c->jobs[ord[j]].cols_a;
     if (ca >= 128 && svd_block_smem(ca, 16) > SVD_BLOCK_SMEM_MAX) g[0] = j + 1;
@@ -1909,14 +1914,18 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, c->tmaxel_all, bufs, BUF_PSI, c->dp(c->swork), c->st));
   // groups over all jobs (largest first across superblocks): the pivoted QR
   // and both Jacobi stages run each group on clusters of the same size
-  int g[4], gcols[4], grows[4] = {0, 0, 0, 0};
+  int g[4], gcols[4], grows[4] = {0, 0, 0, 0}, rows0 = 0, cols0 = 0;
   jacobi_groups(c, c->torder.data(), nj, g, gcols);
   for (int k = 1; k < 5; ++k) {
     const int lo = g[k - 1], hi = k < 4 ? g[k] : nj;
     for (int j = lo; j < hi; ++j) grows[k - 1] = std::max(grows[k - 1], c->jobs[c->torder[j]].rows_a);
   }
+  for (int j = 0; j < g[0]; ++j) {
+    rows0 = std::max(rows0, c->jobs[c->torder[j]].rows_a);
+    cols0 = std::max(cols0, c->jobs[c->torder[j]].cols_a);
+  }
   if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
-  CK(launch_svd_qrcp_grouped((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, grows, gcols,
+  CK(launch_svd_qrcp_grouped((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, grows, gcols, rows0, cols0,
                              c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, c->st, c->side, c->sev));
   if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
   // FP32 stage: rotations V to FP32 accuracy; Newton-Schulz makes V
@@ -2922,6 +2931,12 @@ idmrg_status idmrg_profile_read(idmrg_ctx *c, int k, double *ms, uint64_t *launc
   if (launches) *launches = c->kt[k].n;
   if (flops) *flops = c->kt[k].flops;
   if (bytes) *bytes = c->kt[k].bytes;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_set_svd_path(idmrg_ctx *c, int global_only) {
+  if (!c) return IDMRG_EINVAL;
+  c->svd_global = global_only != 0;
   return IDMRG_OK;
 }
 

@@ -468,8 +468,9 @@ __device__ __forceinline__ void rotation(double a, double b, double g, double &c
 }
 
 // one column pair (p, q): overlap, rotation of B's and Jm's columns
-__device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, double *jq, int n, int nj,
-                                            int lane, double tol2, double abs_floor) {
+// returns |g| / sqrt(a b) of a rotated pair, -1 when the pair is left alone
+__device__ __forceinline__ float jacobi_pair(double *ap, double *aq, double *jp, double *jq, int n, int nj,
+                                             int lane, double tol2, double abs_floor) {
   double x[JAC_REG], y[JAC_REG];
   double al = 0.0, be = 0.0, ga = 0.0;
   const bool inreg = n <= 32 * JAC_REG;
@@ -498,7 +499,8 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
   be = wsum(be);
   ga = wsum(ga);
   // rotate unless |g| <= tol sqrt(a b) (compared squared) or below the floor
-  if (!(ga * ga > tol2 * (al * be)) || !(fabs(ga) > abs_floor)) return false;
+  if (!(ga * ga > tol2 * (al * be)) || !(fabs(ga) > abs_floor)) return -1.0f;
+  const float ratio = (float)(fabs(ga) / sqrt(al * be));
   double cs = 0.0, sn = 0.0;
   if (lane == 0) rotation(al, be, ga, cs, sn);
   cs = __shfl_sync(0xffffffffu, cs, 0);
@@ -526,7 +528,7 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
     jp[i] = cs * u - sn * v;
     jq[i] = sn * u + cs * v;
   }
-  return true;
+  return ratio;
 }
 
 // One job per cluster (cluster size chosen at launch); the pairs of a round
@@ -534,7 +536,7 @@ __device__ __forceinline__ bool jacobi_pair(double *ap, double *aq, double *jp, 
 // cluster barrier.
 __global__ void __launch_bounds__(JAC_THREADS, 2)
     jacobi_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
-                  int *__restrict__ iwork, double *__restrict__ sv, int *err) {
+                  int *__restrict__ iwork, double *__restrict__ sv, int *err, int jm_init) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int csize = (int)cluster.num_blocks();
@@ -545,15 +547,26 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
   double *Jm = work + Jb.j_off;
   __shared__ double fro_part[JAC_MAX_CLUSTER];
   __shared__ double wred[JAC_THREADS / 32];
-  __shared__ int flag, local_changed;
+  __shared__ int flag, local_changed, sweep_rmax, cl_rmax;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   // pair k of a round goes to CTA k mod csize: the FP64 work of a round is
   // spread over every SM of the cluster (blocked by CTA it piled up on the
   // first few while the others waited at the barrier)
   const int gw = warp * csize + crank, gnw = csize * nw;
   const int64_t nn = (int64_t)n * n, nb = (int64_t)nr * n;
-  for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)csize * blockDim.x)
-    Jm[e] = (e / n == e % n) ? 1.0 : 0.0;
+  if (!jm_init) {
+    for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)csize * blockDim.x)
+      Jm[e] = (e / n == e % n) ? 1.0 : 0.0;
+  } else if (n < Jb.cols_a) {
+    // the given rotations are cols_a x cols_a (leading dimension cols_a);
+    // their n x n block moves to leading dimension n through the x_off area
+    double *tmp = work + Jb.x_off;
+    for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)csize * blockDim.x)
+      tmp[e] = Jm[(e / n) * Jb.cols_a + e % n];
+    cluster.sync();
+    for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nn; e += (int64_t)csize * blockDim.x)
+      Jm[e] = tmp[e];
+  }
   // ||B||_F^2 over the cluster (partials gathered in rank 0's shared memory)
   double fro = 0.0;
   for (int64_t e = (int64_t)crank * blockDim.x + threadIdx.x; e < nb; e += (int64_t)csize * blockDim.x)
@@ -581,29 +594,48 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
   const double abs_floor = 4.0 * DBL_EPSILON * DBL_EPSILON * fro;
   const int np = n + (n & 1);
   int *flag0 = cluster.map_shared_rank(&flag, 0);
+  int *rmax0 = cluster.map_shared_rank(&cl_rmax, 0);
   bool converged = (n < 2);
   int sweep = 0;
   for (; sweep < 40 && !converged; ++sweep) {
-    if (threadIdx.x == 0) local_changed = 0;
-    if (crank == 0 && threadIdx.x == 0) flag = 0;
+    if (threadIdx.x == 0) {
+      local_changed = 0;
+      sweep_rmax = 0;
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      flag = 0;
+      cl_rmax = 0;
+    }
     cluster.sync();
     bool any = false;
+    float rmax = 0.0f;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
       for (int k = gw; k < np / 2; k += gnw) {
         const int i1 = k, i2 = np - 1 - k;
         const int p = i1 == 0 ? 0 : 1 + (i1 - 1 + rnd) % (np - 1);
         const int q = i2 == 0 ? 0 : 1 + (i2 - 1 + rnd) % (np - 1);
         if (p >= n || q >= n) continue;
-        any |= jacobi_pair(B + (int64_t)p * nr, B + (int64_t)q * nr, Jm + (int64_t)p * n, Jm + (int64_t)q * n, nr,
-                           n, lane, tol2, abs_floor);
+        const float r = jacobi_pair(B + (int64_t)p * nr, B + (int64_t)q * nr, Jm + (int64_t)p * n,
+                                    Jm + (int64_t)q * n, nr, n, lane, tol2, abs_floor);
+        if (r >= 0.0f) {
+          any = true;
+          rmax = fmaxf(rmax, r);
+        }
       }
       cluster.sync();
     }
     if (any && lane == 0) local_changed = 1;
+    if (lane == 0) atomicMax(&sweep_rmax, __float_as_int(rmax));  // non-negative floats order as ints
     __syncthreads();
-    if (threadIdx.x == 0 && local_changed) atomicOr(flag0, 1);
+    if (threadIdx.x == 0) {
+      if (local_changed) atomicOr(flag0, 1);
+      atomicMax(rmax0, sweep_rmax);
+    }
     cluster.sync();
-    converged = (*flag0 == 0);
+    // quadratic convergence: after a sweep whose rotations were all below
+    // |g| / sqrt(a b) = 1e-9 the overlaps left are of order n 1e-18, under
+    // the threshold, so the sweep that would only confirm it is skipped
+    converged = (*flag0 == 0) || (__int_as_float(*rmax0) < 1e-9f);
     cluster.sync();
   }
   if (!converged && crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
@@ -622,6 +654,111 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
     if (lane == 0) sv[Jb.sv_off + j] = s;
     const double inv = s > 0.0 ? 1.0 / s : 0.0;
     for (int i = lane; i < nr; i += 32) bj[i] *= inv;
+  }
+}
+
+// FP32 stage (see jacobi32_block_kernel) for sector matrices too large for
+// the block kernels: the cyclic tournament of jacobi_kernel on FP32 copies
+// of B and of the rotations, kept in the job's x_off area (cols_a x cols_a
+// doubles, free until the Newton-Schulz step), one pair per warp, rounds
+// separated by the cluster barrier.  Ends by writing the rotations to V
+// (FP64, leading dimension cols_a) over the identity already there.
+__global__ void __launch_bounds__(JAC_THREADS, 2)
+    jacobi32_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                    const int *__restrict__ iwork) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int csize = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / csize]];
+  const int nr = Jb.cols_a;
+  const int n = iwork[Jb.perm_off + Jb.cols_a];
+  float *B32 = reinterpret_cast<float *>(work + Jb.x_off);  // nr x n, then n x n rotations
+  float *V32 = B32 + (int64_t)nr * n;
+  const double *Bg = work + Jb.b_off;
+  double *Vg = work + Jb.j_off;
+  __shared__ int flag, local_changed, sweep_rmax, cl_rmax;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int gw = warp * csize + crank, gnw = csize * nw;
+  const int64_t stride = (int64_t)csize * blockDim.x, e0 = (int64_t)crank * blockDim.x + threadIdx.x;
+  if (n < 2) return;  // uniform over the cluster
+  for (int64_t e = e0; e < (int64_t)nr * n; e += stride) B32[e] = (float)Bg[e];
+  for (int64_t e = e0; e < (int64_t)n * n; e += stride) V32[e] = (e / n == e % n) ? 1.0f : 0.0f;
+  const float tol = sqrtf((float)nr) * FLT_EPSILON;
+  const int np = n + (n & 1);
+  int *flag0 = cluster.map_shared_rank(&flag, 0);
+  int *rmax0 = cluster.map_shared_rank(&cl_rmax, 0);
+  auto wsumf = [](float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  };
+  bool converged = false;
+  for (int sweep = 0; sweep < 15 && !converged; ++sweep) {
+    if (threadIdx.x == 0) {
+      local_changed = 0;
+      sweep_rmax = 0;
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      flag = 0;
+      cl_rmax = 0;
+    }
+    cluster.sync();
+    bool any = false;
+    float rmax = 0.f;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int k = gw; k < np / 2; k += gnw) {
+        const int i1 = k, i2 = np - 1 - k;
+        const int p = i1 == 0 ? 0 : 1 + (i1 - 1 + rnd) % (np - 1);
+        const int q = i2 == 0 ? 0 : 1 + (i2 - 1 + rnd) % (np - 1);
+        if (p >= n || q >= n) continue;
+        float *xp = B32 + (int64_t)p * nr, *xq = B32 + (int64_t)q * nr;
+        float a = 0.f, b = 0.f, g = 0.f;
+        for (int i = lane; i < nr; i += 32) {
+          const float u = xp[i], v = xq[i];
+          a = fmaf(u, u, a);
+          b = fmaf(v, v, b);
+          g = fmaf(u, v, g);
+        }
+        a = wsumf(a);
+        b = wsumf(b);
+        g = wsumf(g);
+        if (!(a > 0.f) || !(b > 0.f)) continue;
+        const float ratio = fabsf(g) / sqrtf(a) / sqrtf(b);
+        if (!(ratio > tol)) continue;
+        const float z = (b - a) / (2.0f * g);
+        const float t = z == 0.f ? 1.0f : copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
+        if (!(fabsf(t) >= FLT_MIN) || !isfinite(t)) continue;
+        const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
+        for (int i = lane; i < nr; i += 32) {
+          const float u = xp[i], v = xq[i];
+          xp[i] = c * u - sn * v;
+          xq[i] = fmaf(sn, u, c * v);
+        }
+        float *jp = V32 + (int64_t)p * n, *jq = V32 + (int64_t)q * n;
+        for (int i = lane; i < n; i += 32) {
+          const float u = jp[i], v = jq[i];
+          jp[i] = c * u - sn * v;
+          jq[i] = fmaf(sn, u, c * v);
+        }
+        any = true;
+        rmax = fmaxf(rmax, ratio);
+      }
+      cluster.sync();
+    }
+    if (any && lane == 0) local_changed = 1;
+    if (lane == 0) atomicMax(&sweep_rmax, __float_as_int(rmax));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (local_changed) atomicOr(flag0, 1);
+      atomicMax(rmax0, sweep_rmax);
+    }
+    cluster.sync();
+    const float r = __int_as_float(*rmax0);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    cluster.sync();
+  }
+  for (int64_t e = e0; e < (int64_t)n * n; e += stride) {
+    const int64_t j = e / n, i = e - j * n;
+    Vg[j * nr + i] = (double)V32[e];
   }
 }
 
@@ -1400,7 +1537,7 @@ cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, dou
 }
 
 static cudaError_t launch_jacobi_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, double *work,
-                                          int *iwork, double *sv, int *err, cudaStream_t st) {
+                                          int *iwork, double *sv, int *err, int jm_init, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * csize, 1, 1);
   cfg.blockDim = dim3(JAC_THREADS, 1, 1);
@@ -1413,7 +1550,24 @@ static cudaError_t launch_jacobi_clusters(const SvdJob *jobs, const int *order, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, jacobi_kernel, jobs, order, work, iwork, sv, err);
+  return cudaLaunchKernelEx(&cfg, jacobi_kernel, jobs, order, work, iwork, sv, err, jm_init);
+}
+
+static cudaError_t launch_jacobi32_clusters(const SvdJob *jobs, const int *order, int njobs, int csize,
+                                            double *work, const int *iwork, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * csize, 1, 1);
+  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi32_kernel, jobs, order, work, iwork);
 }
 
 // shared memory of the block kernel for a job of `cols` columns in clusters
@@ -1482,10 +1636,10 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     if (e != cudaSuccess) return e;
   }
   if (hi[0] > lo[0]) {
-    e = launch_jacobi_clusters(jobs, order, hi[0], 16, work, iwork, sv, err, st);
+    e = launch_jacobi_clusters(jobs, order, hi[0], 16, work, iwork, sv, err, jm_init, st);
     if (e != cudaSuccess) {
       cudaGetLastError();  // 16-CTA clusters not available here: fall back to 8
-      e = launch_jacobi_clusters(jobs, order, hi[0], 8, work, iwork, sv, err, st);
+      e = launch_jacobi_clusters(jobs, order, hi[0], 8, work, iwork, sv, err, jm_init, st);
     }
     if (e != cudaSuccess) return e;
   }
@@ -1494,7 +1648,7 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     if (e != cudaSuccess) {
       // 16-CTA clusters not available: the global-memory kernel on 8
       cudaGetLastError();
-      e = launch_jacobi_clusters(jobs, order + lo[1], hi[1] - lo[1], 8, work, iwork, sv, err, st);
+      e = launch_jacobi_clusters(jobs, order + lo[1], hi[1] - lo[1], 8, work, iwork, sv, err, jm_init, st);
     }
     if (e != cudaSuccess) return e;
   }
@@ -1572,6 +1726,15 @@ cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs,
     e = cudaEventRecord(ev[k - 1], side[k - 2]);
     if (e != cudaSuccess) return e;
   }
+  if (hi[0] > lo[0]) {  // beyond the block kernels: the global-memory FP32 stage
+    cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = launch_jacobi32_clusters(jobs, order, hi[0], 16, work, iwork, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      e = launch_jacobi32_clusters(jobs, order, hi[0], 8, work, iwork, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
   if (hi[1] > lo[1]) {
     e = launch_block32_clusters(jobs, order + lo[1], hi[1] - lo[1], 16, cols[0], work, iwork, st);
     if (e != cudaSuccess) return e;
@@ -1598,13 +1761,14 @@ size_t svd_qrc_smem(int rows, int cols, int csize) {
   return (size_t)((nloc * ld + 2 * ld + 3 * nloc + 2) * sizeof(double));
 }
 
-// pivoted QR of the jobs order[0..njobs) in groups (as the Jacobi): group
-// 0 and any group whose columns do not fit in shared memory on the single-CTA
-// kernel, groups 1..4 on clusters of 16, 8, 4, 1 CTAs; rows[k], cols[k] are
-// the largest rows and columns of block group k+1
+// pivoted QR of the jobs order[0..njobs) in groups (as the Jacobi): groups
+// 0..4 on clusters of 16, 16, 8, 4, 1 CTAs, any group whose columns do not
+// fit in the shared memory of its cluster on the single-CTA kernel; rows[k],
+// cols[k] are the largest rows and columns of block group k+1
 cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *rows,
-                                    const int *cols, double *work, int *iwork, double zero_rel, cudaStream_t st,
-                                    const cudaStream_t *side, const cudaEvent_t *ev) {
+                                    const int *cols, int rows0, int cols0, double *work, int *iwork,
+                                    double zero_rel, cudaStream_t st, const cudaStream_t *side,
+                                    const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
   cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaError_t e = cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1622,7 +1786,7 @@ cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int nj
       e = cudaStreamWaitEvent(sk, ev[0], 0);
       if (e != cudaSuccess) return e;
     }
-    const size_t smem = k == 0 ? SVD_BLOCK_SMEM_MAX + 1 : svd_qrc_smem(rows[k - 1], cols[k - 1], csz[k]);
+    const size_t smem = k == 0 ? svd_qrc_smem(rows0, cols0, csz[0]) : svd_qrc_smem(rows[k - 1], cols[k - 1], csz[k]);
     if (smem > SVD_BLOCK_SMEM_MAX) {
       e = launch_svd_qrcp(jobs, order + lo[k], hi[k] - lo[k], work, iwork, zero_rel, sk);
     } else {

@@ -56,6 +56,21 @@ def test_full_iteration_parity(name, bonds, ell, m, steps, prec):
     ctx.close()
 
 
+def test_large_sector_svd_path():
+    """The kernels for sector matrices beyond 320 columns (pivoted QR in one
+    CTA, FP32 and FP64 cyclic Jacobi in global memory, the FP64 stage started
+    from the Newton-Schulz-orthogonalised FP32 rotations), forced on a small
+    problem, against the oracle."""
+    mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 1606), 8)
+    ctx = context(mpo, 48)
+    ctx.set_svd_path(True)
+    ref = ParallelIDMRG.from_mpo(mpo, m=48)
+    for _ in range(14):
+        _compare(ctx.unit_cell_step(), ref.step())
+    assert ctx.svd_stats()["max_sweeps"] <= 6  # FP32-preconditioned FP64 sweeps
+    ctx.close()
+
+
 def test_lambda_spectra_parity():
     mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 5), 8)
     ctx, ref, out = _run_both(mpo, 40, 8)
