@@ -53,10 +53,15 @@ def rank_seed(rank: int) -> int:
     return 1606 + rank
 
 
-def make_workload(rank: int):
-    from workloads import build_mpo, random_chain_bonds
-    seed = rank_seed(rank)
-    return build_mpo(random_chain_bonds(16, 0.5, 1.5, seed), 16), seed
+def make_workload(rank: int, name: str = WORKLOAD):
+    """The MPO of a named workload; the random-bond chain draws its couplings
+    from the rank's seed (independent realisations), the cylinder is fixed."""
+    from workloads import build_mpo, make_config, random_chain_bonds
+    if name == WORKLOAD:
+        seed = rank_seed(rank)
+        return build_mpo(random_chain_bonds(16, 0.5, 1.5, seed), 16), seed
+    mpo, _ = make_config(name)
+    return mpo, None
 
 
 def job_value(world: int, steps: int, seconds: float) -> float:
@@ -221,6 +226,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload != WORKLOAD:
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle needs minutes per unit-cell step "
+                          f"at {args.workload}; its timed arm runs on {WORKLOAD}"}), flush=True)
+        return
     mpo, seed = make_workload(0)
     from oracle.idmrg import ParallelIDMRG
     ref = ParallelIDMRG.from_mpo(mpo, m=args.m)
@@ -323,11 +332,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3", "fp64tc"])
-    ap.add_argument("--m", type=int, default=256)
+    ap.add_argument("--m", type=int, default=None, help="kept states (default: the workload's m)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "yc4_j1j2_l8_m1024"],
+                    help="random-bond chain l=16 m=256 (the metric's workload) or the YC4 J1-J2 cylinder")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
+    if args.m is None:
+        args.m = 256 if args.workload == WORKLOAD else 1024
     if args.impl == "reference":
         return run_reference(args)
 
@@ -343,7 +356,8 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    mpo, seed = make_workload(rank)
+    mpo, seed = make_workload(rank, args.workload)
+    ell = len(mpo.W)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     run = timed_run(pkg, mpo, args.m, args.prec, args.steps, args.warmup, dev, flush, dist, True, local)
     cmp = None
@@ -376,7 +390,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp64tc": "bf16-digits(f64)+f64"}.get(args.prec, f"{args.prec}+f64"),
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "ell": 16, "m": args.m, "solves_per_step": 8, "seed": seed,
+        "config": {"workload": args.workload, "ell": ell, "m": args.m, "solves_per_step": ell // 2, "seed": seed,
                    "regime": f"saturated (n > {SATURATE}, D = {int(max(last['kept']))})",
                    "precision": args.prec + ("" if args.prec == "fp64" else " H_eff psi; FP64 Lanczos and SVD"),
                    "fp64_restart_matvecs": "BF16 digit slices on the tensor cores (FP64-accurate)"
@@ -404,7 +418,7 @@ def main():
                         "max_abs_de_per_site": max_de_per_site(run["reports"], cmp["reports"]),
                         "heff_roofline": heff_roofline(cmp["prof"], "fp64", pk)}
         cmp["ctx"].close()
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         _, cb = cpu_baseline(mpo, args.m)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
