@@ -217,11 +217,12 @@ size_t svd_block_smem(int cols, int csize);
 cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
                               double *work, int *iwork, double *sv, int *err, int jm_init, cudaStream_t st,
                               const cudaStream_t *side, const cudaEvent_t *ev);
-// FP32 block Jacobi on the block groups 1..4 (group 0 untouched): writes the
+// FP32 Jacobi on every group (group 0, the sectors beyond the block kernels,
+// with cols0 columns at most, on the large-sector kernels): writes the
 // accumulated rotations of each job to its V (j_off, cols_a x cols_a)
 cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                                double *work, const int *iwork, cudaStream_t st, const cudaStream_t *side,
-                                const cudaEvent_t *ev);
+                                int cols0, double *work, const int *iwork, cudaStream_t st,
+                                const cudaStream_t *side, const cudaEvent_t *ev);
 // per job over cols_a x cols_a elements: 0: V = I; 1: V = 1.5 V - 0.5 W
 // (Newton-Schulz step, W at w_off); 2: B = X (X at w_off)
 cudaError_t launch_svd_elementwise(const SvdJob *jobs, int njobs, int max_cols, int mode, double *work,

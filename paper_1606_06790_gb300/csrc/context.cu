@@ -1935,7 +1935,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   double *sw = c->dp(c->swork);
   double *const *svb = (double *const *)c->dbufs.p;
   CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 0, sw, c->st));
-  CK(launch_svd_jacobi32(dj, (const int *)c->sorder.p, nj, g, gcols, sw, (const int *)c->siw.p, c->st, c->side,
+  CK(launch_svd_jacobi32(dj, (const int *)c->sorder.p, nj, g, gcols, cols0, sw, (const int *)c->siw.p, c->st, c->side,
                          c->sev));
   for (int it = 0; it < 2; ++it) {
     {

@@ -1190,6 +1190,183 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     for (int j = n + (int)threadIdx.x; j < Jb.cols_a; j += blockDim.x) sv[Jb.sv_off + j] = 0.0;
 }
 
+// FP64 stage for sectors beyond the block kernels: the cyclic tournament of
+// jacobi_kernel (columns in global memory, one pair per warp, rounds
+// separated by the cluster barrier) with the scaled rotations and tracked
+// column norms of jacobi_block_kernel (bj_rotation): one dot product and one
+// FMA per element and column instead of three dot products and two
+// operations.  Column scales and squared norms live in the job's w_off area
+// (free once B holds X); every sweep starts by folding the scales back into
+// the columns and recomputing their norms.
+__global__ void __launch_bounds__(JAC_THREADS, 1)
+    jacobi_scaled_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                         int *__restrict__ iwork, double *__restrict__ sv, int *err, int jm_init) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int csize = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / csize]];
+  const int nr = Jb.cols_a;                       // rows of B
+  const int n = iwork[Jb.perm_off + Jb.cols_a];   // columns of B: numerical rank
+  double *B = work + Jb.b_off;
+  double *Jm = work + Jb.j_off;
+  double *dsc = work + Jb.w_off, *nrm = dsc + n;  // scale d_j and squared norm of column j
+  __shared__ double fro_part[JAC_MAX_CLUSTER];
+  __shared__ double wred[JAC_THREADS / 32];
+  __shared__ int flag, local_changed, sweep_lmax, cl_lmax;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int gw = warp * csize + crank, gnw = csize * nw;
+  const int64_t nn = (int64_t)n * n, nb = (int64_t)nr * n;
+  const int64_t stride = (int64_t)csize * blockDim.x, e0 = (int64_t)crank * blockDim.x + threadIdx.x;
+  if (!jm_init) {
+    for (int64_t e = e0; e < nn; e += stride) Jm[e] = (e / n == e % n) ? 1.0 : 0.0;
+  } else if (n < Jb.cols_a) {
+    // the given rotations are cols_a x cols_a (leading dimension cols_a);
+    // their n x n block moves to leading dimension n through the x_off area
+    double *tmp = work + Jb.x_off;
+    for (int64_t e = e0; e < nn; e += stride) tmp[e] = Jm[(e / n) * Jb.cols_a + e % n];
+    cluster.sync();
+    for (int64_t e = e0; e < nn; e += stride) Jm[e] = tmp[e];
+  }
+  for (int64_t e = e0; e < n; e += stride) dsc[e] = 1.0;
+  double fro = 0.0;
+  for (int64_t e = e0; e < nb; e += stride) fro = fma(B[e], B[e], fro);
+  fro = wsum(fro);
+  if (lane == 0) wred[warp] = fro;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += wred[q];
+    *cluster.map_shared_rank(&fro_part[crank], 0) = t;
+  }
+  cluster.sync();
+  const double *fp0 = cluster.map_shared_rank(fro_part, 0);
+  fro = 0.0;
+  for (int q = 0; q < csize; ++q) fro += fp0[q];
+  cluster.sync();
+  const float log2_tol2 = __log2f((float)nr) - 104.0f;  // log2(nr eps^2), eps = 2^-52
+  const Split floor_split = split_f64(4.0 * DBL_EPSILON * DBL_EPSILON * fro);
+  const int small_key = (int)(64.0f * -59.8f);        // 64 log2(1e-18): see jacobi_block_kernel
+  const int np = n + (n & 1);
+  int *flag0 = cluster.map_shared_rank(&flag, 0);
+  int *lmax0 = cluster.map_shared_rank(&cl_lmax, 0);
+  // scales into the columns, exact squared norms
+  auto fold = [&]() {
+    for (int j = gw; j < n; j += gnw) {
+      double *bj = B + (int64_t)j * nr, *jj = Jm + (int64_t)j * n;
+      const double d = dsc[j];
+      double s = 0.0;
+      for (int i = lane; i < nr; i += 32) {
+        const double v = bj[i] * d;
+        bj[i] = v;
+        s = fma(v, v, s);
+      }
+      for (int i = lane; i < n; i += 32) jj[i] *= d;
+      s = wsum(s);
+      __syncwarp();
+      if (lane == 0) {
+        nrm[j] = s;
+        dsc[j] = 1.0;
+      }
+    }
+    cluster.sync();
+  };
+  bool converged = (n < 2);
+  int sweep = 0;
+  for (; sweep < 40 && !converged; ++sweep) {
+    fold();
+    if (threadIdx.x == 0) {
+      local_changed = 0;
+      sweep_lmax = INT_MIN;
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      flag = 0;
+      cl_lmax = INT_MIN;
+    }
+    cluster.sync();
+    bool any = false;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int k = gw; k < np / 2; k += gnw) {
+        const int i1 = k, i2 = np - 1 - k;
+        const int p = i1 == 0 ? 0 : 1 + (i1 - 1 + rnd) % (np - 1);
+        const int q = i2 == 0 ? 0 : 1 + (i2 - 1 + rnd) % (np - 1);
+        if (p >= n || q >= n) continue;
+        double *xp = B + (int64_t)p * nr, *xq = B + (int64_t)q * nr;
+        double ga = 0.0;
+        for (int i = lane; i < nr; i += 32) ga = fma(xp[i], xq[i], ga);
+        ga = wsum(ga);
+        double cp = 0.0, cq = 0.0;
+        int rot = 0;
+        if (lane == 0) {
+          double a = nrm[p], b = nrm[q], d1 = dsc[p], d2 = dsc[q];
+          float lr = -1000.0f;
+          rot = bj_rotation(ga, a, b, d1, d2, log2_tol2, floor_split, cp, cq, lr);
+          if (rot) {
+            nrm[p] = a;
+            nrm[q] = b;
+            dsc[p] = d1;
+            dsc[q] = d2;
+            atomicMax(&sweep_lmax, (int)(lr * 64.0f));
+          }
+        }
+        rot = __shfl_sync(0xffffffffu, rot, 0);
+        if (!rot) continue;
+        any = true;
+        cp = __shfl_sync(0xffffffffu, cp, 0);
+        cq = __shfl_sync(0xffffffffu, cq, 0);
+        double np2 = 0.0, nq2 = 0.0;
+        for (int i = lane; i < nr; i += 32) {
+          const double u = xp[i], v = xq[i];
+          const double u2 = fma(cp, v, u), v2 = fma(cq, u, v);
+          xp[i] = u2;
+          xq[i] = v2;
+          if (rot == 2) {
+            np2 = fma(u2, u2, np2);
+            nq2 = fma(v2, v2, nq2);
+          }
+        }
+        double *jp = Jm + (int64_t)p * n, *jq = Jm + (int64_t)q * n;
+        for (int i = lane; i < n; i += 32) {
+          const double u = jp[i], v = jq[i];
+          jp[i] = fma(cp, v, u);
+          jq[i] = fma(cq, u, v);
+        }
+        if (rot == 2) {  // cancellation: norms from the rotated data
+          np2 = wsum(np2);
+          nq2 = wsum(nq2);
+          if (lane == 0) {
+            nrm[p] = dsc[p] * dsc[p] * np2;
+            nrm[q] = dsc[q] * dsc[q] * nq2;
+          }
+        }
+      }
+      cluster.sync();
+    }
+    if (any && lane == 0) local_changed = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (local_changed) atomicOr(flag0, 1);
+      atomicMax(lmax0, sweep_lmax);
+    }
+    cluster.sync();
+    converged = (*flag0 == 0) || (*lmax0 < small_key);
+    cluster.sync();
+  }
+  fold();
+  if (!converged && crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
+  if (crank == 0 && threadIdx.x == 0) iwork[Jb.perm_off + Jb.cols_a + 1] = sweep;
+  for (int j = gw; j < Jb.cols_a; j += gnw) {
+    if (j >= n) {
+      if (lane == 0) sv[Jb.sv_off + j] = 0.0;
+      continue;
+    }
+    double *bj = B + (int64_t)j * nr;
+    const double s = sqrt(nrm[j]);
+    if (lane == 0) sv[Jb.sv_off + j] = s;
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int i = lane; i < nr; i += 32) bj[i] *= inv;
+  }
+}
+
 // ------------------------------------------------- FP32 stage of the Jacobi SVD
 // The same block tournament in FP32, whose instructions cost a sixteenth of
 // FP64 ones here: it converges the rotations to FP32 accuracy (relative
@@ -1365,6 +1542,178 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
   }
 }
 
+// FP32 stage for sectors of up to 32 * J32B_REG rows whose rotations do not
+// fit next to B in shared memory: the block tournament of
+// jacobi32_block_kernel with only B's columns in shared memory (four slots of
+// bw columns) and the rotations in global memory (FP32, n x n, in the job's
+// x_off area), each column of the rotations updated by the CTA that holds
+// its block in that round; the cluster barrier that ends a round also
+// publishes those updates to the CTA that holds the block next.
+constexpr int J32B_REG = 32;  // rows per lane in registers: up to 1024 rows
+__global__ void __launch_bounds__(BJ_THREADS, 1)
+    jacobi32_big_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                        const int *__restrict__ iwork) {
+  extern __shared__ __align__(16) float bg_sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / C]];
+  const int nr = Jb.cols_a;
+  const int n = iwork[Jb.perm_off + Jb.cols_a];
+  const int P = 2 * C;
+  const int bw = (n + P - 1) / P;
+  const int nreg = (nr + 31) >> 5;
+  const int ldb = 32 * nreg;
+  const int slot = (bw * ldb + 3) & ~3;  // 16-byte aligned blocks
+  __shared__ int flag, local_changed, sweep_rmax, cl_rmax;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const double *Bg = work + Jb.b_off;
+  double *Vg = work + Jb.j_off;
+  float *V32 = reinterpret_cast<float *>(work + Jb.x_off);  // n x n, leading dimension n
+  const int pos[2] = {crank, P - 1 - crank};
+  auto slotp = [&](int buf, int which) { return bg_sm + (buf * 2 + which) * slot; };
+  auto valid = [&](int k) { return max(0, min(bw, n - k * bw)); };
+  if (nreg > J32B_REG || n < 2) return;  // uniform over the cluster
+  for (int w = 0; w < 2; ++w) {
+    const int k = pos[w], nv = valid(k);
+    float *sb = slotp(0, w);
+    for (int e = threadIdx.x; e < bw * ldb; e += blockDim.x) {
+      const int j = e / ldb, i = e - j * ldb;
+      sb[e] = (j < nv && i < nr) ? (float)Bg[(int64_t)(k * bw + j) * nr + i] : 0.0f;
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)nv * n; e += blockDim.x) {
+      const int64_t j = e / n, i = e - j * n;
+      V32[(k * bw + j) * n + i] = (i == k * bw + j) ? 1.0f : 0.0f;
+    }
+  }
+  const float tol = sqrtf((float)nr) * FLT_EPSILON;
+  int *flag0 = cluster.map_shared_rank(&flag, 0);
+  int *rmax0 = cluster.map_shared_rank(&cl_rmax, 0);
+  int cur = 0;
+  bool converged = false;
+  auto wsumf = [](float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  };
+  // one pair, one warp: columns i of s0 (block b0) and j of s1 (block b1)
+  auto pair = [&](float *s0, int b0, int i, float *s1, int b1, int j, float &rmax) -> bool {
+    float *xp = s0 + i * ldb, *xq = s1 + j * ldb;
+    float x[J32B_REG], y[J32B_REG], a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+    for (int r = 0; r < J32B_REG; ++r)
+      if (r < nreg) {
+        x[r] = xp[lane + 32 * r];
+        y[r] = xq[lane + 32 * r];
+        a = fmaf(x[r], x[r], a);
+        b = fmaf(y[r], y[r], b);
+        g = fmaf(x[r], y[r], g);
+      }
+    a = wsumf(a);
+    b = wsumf(b);
+    g = wsumf(g);
+    if (!(a > 0.f) || !(b > 0.f)) return false;
+    const float ratio = fabsf(g) / sqrtf(a) / sqrtf(b);
+    if (!(ratio > tol)) return false;
+    const float z = (b - a) / (2.0f * g);
+    const float t = z == 0.f ? 1.0f : copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
+    if (!(fabsf(t) >= FLT_MIN) || !isfinite(t)) return false;
+    const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
+#pragma unroll
+    for (int r = 0; r < J32B_REG; ++r)
+      if (r < nreg) {
+        xp[lane + 32 * r] = c * x[r] - sn * y[r];
+        xq[lane + 32 * r] = fmaf(sn, x[r], c * y[r]);
+      }
+    float *jp = V32 + (int64_t)(b0 * bw + i) * n, *jq = V32 + (int64_t)(b1 * bw + j) * n;
+    for (int e = lane; e < n; e += 32) {
+      const float u = jp[e], v = jq[e];
+      jp[e] = c * u - sn * v;
+      jq[e] = fmaf(sn, u, c * v);
+    }
+    rmax = fmaxf(rmax, ratio);
+    return true;
+  };
+  for (int sweep = 0; sweep < 15 && !converged; ++sweep) {
+    if (threadIdx.x == 0) {
+      local_changed = 0;
+      sweep_rmax = 0;
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      flag = 0;
+      cl_rmax = 0;
+    }
+    cluster.sync();
+    bool any = false;
+    float rmax = 0.f;
+    for (int rnd = 0; rnd < P - 1; ++rnd) {
+      float *st0 = slotp(cur, 0), *st1 = slotp(cur, 1);
+      const int b0 = bj_block_at(pos[0], rnd, P), b1 = bj_block_at(pos[1], rnd, P);
+      const int nv0 = valid(b0), nv1 = valid(b1);
+      if (rnd == 0) {
+        const int bp = bw + (bw & 1), half = bp / 2, bm = bp - 1;
+        for (int w = 0; w < 2; ++w) {
+          const int nv = w ? nv1 : nv0, bk = w ? b1 : b0;
+          float *sb = w ? st1 : st0;
+          for (int sr = 0; sr < bm; ++sr) {
+            for (int i = warp; i < half; i += nw) {
+              int p = 0, q;
+              if (i != 0) {
+                p = i - 1 + sr;
+                p = 1 + (p >= bm ? p - bm : p);
+              }
+              q = bp - 2 - i + sr;
+              q = 1 + (q >= bm ? q - bm : q);
+              if (p < nv && q < nv) any |= pair(sb, bk, p, sb, bk, q, rmax);
+            }
+            __syncthreads();
+          }
+        }
+      }
+      for (int sr = 0; sr < bw; ++sr) {
+        for (int i = warp; i < bw; i += nw) {
+          int j = i + sr;
+          if (j >= bw) j -= bw;
+          if (i < nv0 && j < nv1) any |= pair(st0, b0, i, st1, b1, j, rmax);
+        }
+        __syncthreads();
+      }
+      if (C > 1) {
+        for (int w = 0; w < 2; ++w) {
+          const int dpn = pos[w] == 0 ? 0 : (pos[w] == P - 1 ? 1 : pos[w] + 1);
+          const int drank = dpn < C ? dpn : P - 1 - dpn, dw = dpn < C ? 0 : 1;
+          float4 *dst = reinterpret_cast<float4 *>(cluster.map_shared_rank(slotp(cur ^ 1, dw), drank));
+          const float4 *src = reinterpret_cast<const float4 *>(w ? st1 : st0);
+          for (int e = threadIdx.x; e < slot / 4; e += blockDim.x) dst[e] = src[e];
+        }
+        cluster.sync();
+        cur ^= 1;
+      } else {
+        __syncthreads();
+      }
+    }
+    if (any && lane == 0) local_changed = 1;
+    if (lane == 0) atomicMax(&sweep_rmax, __float_as_int(rmax));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (local_changed) atomicOr(flag0, 1);
+      atomicMax(rmax0, sweep_rmax);
+    }
+    cluster.sync();
+    const float r = __int_as_float(*rmax0);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    cluster.sync();
+  }
+  // rotations to V (FP64, cols_a x cols_a): the columns of this CTA's two
+  // home blocks (every block is back at its starting position after whole sweeps)
+  for (int w = 0; w < 2; ++w) {
+    const int k = pos[w], nv = valid(k);
+    for (int64_t e = threadIdx.x; e < (int64_t)nv * n; e += blockDim.x) {
+      const int64_t j = e / n, i = e - j * n;
+      Vg[(k * bw + j) * nr + i] = (double)V32[(k * bw + j) * n + i];
+    }
+  }
+}
+
 // per job over cols_a x cols_a elements: 0 V = I, 1 V = 1.5 V - 0.5 W, 2 B = X
 __global__ void svd_elementwise_kernel(const SvdJob *__restrict__ jobs, double *__restrict__ work, int mode) {
   const SvdJob J = jobs[blockIdx.y];
@@ -1536,6 +1885,24 @@ cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, dou
   return cudaGetLastError();
 }
 
+static cudaError_t launch_jacobi_scaled_clusters(const SvdJob *jobs, const int *order, int njobs, int csize,
+                                                 double *work, int *iwork, double *sv, int *err, int jm_init,
+                                                 cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * csize, 1, 1);
+  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_scaled_kernel, jobs, order, work, iwork, sv, err, jm_init);
+}
+
 static cudaError_t launch_jacobi_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, double *work,
                                           int *iwork, double *sv, int *err, int jm_init, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
@@ -1636,10 +2003,11 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     if (e != cudaSuccess) return e;
   }
   if (hi[0] > lo[0]) {
-    e = launch_jacobi_clusters(jobs, order, hi[0], 16, work, iwork, sv, err, jm_init, st);
+    cudaFuncSetAttribute(jacobi_scaled_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = launch_jacobi_scaled_clusters(jobs, order, hi[0], 16, work, iwork, sv, err, jm_init, st);
     if (e != cudaSuccess) {
       cudaGetLastError();  // 16-CTA clusters not available here: fall back to 8
-      e = launch_jacobi_clusters(jobs, order, hi[0], 8, work, iwork, sv, err, jm_init, st);
+      e = launch_jacobi_scaled_clusters(jobs, order, hi[0], 8, work, iwork, sv, err, jm_init, st);
     }
     if (e != cudaSuccess) return e;
   }
@@ -1706,8 +2074,8 @@ static cudaError_t launch_block32_clusters(const SvdJob *jobs, const int *order,
 }
 
 cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                                double *work, const int *iwork, cudaStream_t st, const cudaStream_t *side,
-                                const cudaEvent_t *ev) {
+                                int cols0, double *work, const int *iwork, cudaStream_t st,
+                                const cudaStream_t *side, const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
   cudaFuncSetAttribute(jacobi32_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaError_t e = cudaFuncSetAttribute(jacobi32_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1726,12 +2094,40 @@ cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs,
     e = cudaEventRecord(ev[k - 1], side[k - 2]);
     if (e != cudaSuccess) return e;
   }
-  if (hi[0] > lo[0]) {  // beyond the block kernels: the global-memory FP32 stage
-    cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    e = launch_jacobi32_clusters(jobs, order, hi[0], 16, work, iwork, st);
+  if (hi[0] > lo[0]) {  // beyond the block kernels
+    // B's columns in shared memory, the rotations in global memory, when
+    // 16-CTA clusters are available and the columns fit; else all in
+    // global memory
+    const int64_t bw0 = (cols0 + 31) / 32, ld0 = 32 * (((int64_t)cols0 + 31) / 32);
+    const size_t smem0 = (size_t)(4 * ((bw0 * ld0 + 3) & ~(int64_t)3) * sizeof(float));
+    e = cudaErrorInvalidValue;
+    if (ld0 <= 32 * J32B_REG && smem0 <= SVD_BLOCK_SMEM_MAX) {
+      cudaFuncSetAttribute(jacobi32_big_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = cudaFuncSetAttribute(jacobi32_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
+      if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(hi[0] * 16, 1, 1);
+        cfg.blockDim = dim3(BJ_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, jacobi32_big_kernel, jobs, order, work, iwork);
+      }
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
-      e = launch_jacobi32_clusters(jobs, order, hi[0], 8, work, iwork, st);
+      cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = launch_jacobi32_clusters(jobs, order, hi[0], 16, work, iwork, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = launch_jacobi32_clusters(jobs, order, hi[0], 8, work, iwork, st);
+      }
     }
     if (e != cudaSuccess) return e;
   }
