@@ -46,7 +46,10 @@ enum BufId {
   BUF_ORMAP = 29, // stage 3 output row -> psi offset (int64)
   BUF_OEXP = 30,  // per packed row: exponent of the digit expansion (int32)
   BUF_OT3 = 31,   // stage 3 A in FP64 (row-major per task) before its digits
-  NBUF = 32
+  BUF_GOZ = 32,   // digit arena of the other FP64 GEMM lists (environments,
+                  // prediction, SVD Newton-Schulz), the same for every superblock
+  BUF_GEXP = 33,  // exponents of that arena
+  NBUF = 34
 };
 
 
@@ -261,7 +264,8 @@ struct PackSeg {
   int KB, G;              // K blocks and row groups of the packed matrix
   int sb, src_buf, dst_buf, src_fp32;
   int whole;              // digit form: the segment holds the whole K range of its rows
-  int pad;
+  int exp_buf;            // digit form: slot of the exponent array
+  double alpha;           // digit form: source values scaled by alpha
 };
 struct WTaskP {           // T3 rectangle written into a packed stage-3 A matrix
   int64_t dst_off;
@@ -280,7 +284,7 @@ struct TcTask {
   int mode, ldc;          // mode 0: FP32 row-major C; 1: FP64 through the row map;
                           // 2: FP64 row-major C
   int kb0, kb_stride;     // digit form: first K block of this K chunk, K blocks of the packed rows
-  int accum, pad;         // digit form: add to C (later K chunks) instead of storing
+  int accum, exp_buf;     // digit form: add to C instead of storing; slot of the exponents
 };
 struct TcTile {
   int task, mt, nt, pad;

@@ -80,7 +80,24 @@ uint64_t sm64_at(uint64_t s, uint64_t k) { return sm64_mix(s + (k + 1ull) * 0x9E
 // order), so the first calls of a list try each shape once on real work,
 // timed with CUDA events on the stream, and the fastest is kept until the
 // list's work changes by more than 10 %.
+// A grouped FP64 GEMM list in the digit-slice form (kernels_tc.cu): every
+// task's op(A) (M x K) and op(B)^T (N x K), K concatenated over its segments,
+// become digit planes in the context's digit arena, one exponent per packed
+// row; tasks longer than OZ_MAX_K run in K chunks (one launch each).
+struct OzList {
+  bool ok = false;
+  std::vector<PackSeg> segs;      // A and B packing, one per GEMM segment and operand
+  int seg_rows = 0;
+  std::vector<TcTask> tasks;
+  std::vector<TcTile> tiles;
+  std::vector<int> lo;            // tile ranges of the K chunks
+  int64_t planes = 0, nexp = 0;   // arena use: BF16 elements, exponents
+  DevBuf dsegs, dtasks, dtiles;
+};
+
 struct GemmTune {
+  OzList oz;
+  bool oz_use = false;  // list eligible for the digit-slice form (environments, prediction, SVD)
   DevBuf tiles[GEMM_NSHAPE];
   int ntiles[GEMM_NSHAPE] = {0, 0, 0, 0};
   int choice = -1;
@@ -133,6 +150,8 @@ struct idmrg_ctx {
   bool o_oz = true;    // FP64 matvecs from digit slices (mixed restarts, FP64_TC)
   bool fp64tc = false; // IDMRG_FP64_TC: every matvec from digit slices, one Lanczos run
   bool oz_active() const { return oz_ok && o_oz && (mixed || fp64tc); }
+  // the other FP64 GEMM lists (environments, prediction, SVD) in digit slices
+  bool oz_lists() const { return o_oz && (mixed || fp64tc); }
   std::vector<PackSeg> pk_step, pk_psi;   // per iteration (L, R) and per matvec (psi)
   std::vector<TcTask> tc1k, tc3k;
   std::vector<TcTile> tc1t, tc3t;
@@ -153,6 +172,7 @@ struct idmrg_ctx {
   int64_t oz_a3_lo = 0, oz_a3_hi = 0, oz_b3_lo = 0, oz_b3_hi = 0;  // exponent ranges reset before use
   std::vector<int> oz1_lo, oz3_lo;  // tile ranges of the K chunks (one launch each)
   std::vector<WTerm> wtpm_oz;
+  DevBuf goz_planes, goz_exps;  // digit arena of the FP64 GEMM lists (BUF_GOZ, BUF_GEXP)
   DevBuf dozsw, dozsp, dozp, doz1k, doz1t, doz3k, doz3t, dozw, dozwm, oexp;
   std::vector<DevBuf> bOA1, bOB1, bOT1, bOA3, bOB3, bORMAP, bOT3;
 
@@ -325,9 +345,156 @@ namespace {
     if (!(ok)) return c->fail(IDMRG_ENOMEM, "device allocation failed (%s)", #ok); \
   } while (0)
 
+// K chunks of at most OZ_MAX_K for one digit-slice task (see plan_oz)
+static void oz_add_task(std::vector<TcTask> &tasks, std::vector<std::vector<TcTile>> &lists, TcTask t, int MT,
+                        int NT) {
+  const int KBt = t.KB, per = OZ_MAX_K / OZ_KBLK;
+  const int nch = KBt > 0 ? (KBt + per - 1) / per : 1;
+  if ((int)lists.size() < nch) lists.resize(nch);
+  for (int ch = 0; ch < nch; ++ch) {
+    TcTask u = t;
+    u.kb_stride = KBt;
+    u.kb0 = ch * per;
+    u.KB = KBt > 0 ? std::min(per, KBt - u.kb0) : 0;
+    u.accum = (t.accum || ch > 0) ? 1 : 0;
+    const int id = (int)tasks.size();
+    tasks.push_back(u);
+    for (int mt = 0; mt < MT; ++mt)
+      for (int nt = 0; nt < NT; ++nt) lists[ch].push_back(TcTile{id, mt, nt, 0});
+  }
+}
+
+idmrg_status sync_bufs(idmrg_ctx *c);
+
+// the digit-slice form of an FP64 GEMM list (planned with the list)
+idmrg_status oz_build(idmrg_ctx *c, const GemmList &L, OzList &Z) {
+  auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+  const int64_t TA = (int64_t)128 * OZ_KBLK * OZ_PLANES, TB = (int64_t)TC_TN * OZ_KBLK * OZ_PLANES;
+  Z.ok = false;
+  Z.segs.clear();
+  Z.tasks.clear();
+  Z.tiles.clear();
+  Z.seg_rows = 0;
+  std::vector<std::vector<TcTile>> lists;
+  int64_t an = 0, bn = 0, en = 0;
+  // A planes first, B planes after all of them: B offsets are patched below
+  std::vector<size_t> bseg;
+  std::vector<TcTask> pend;
+  std::vector<int> pmt, pnt;
+  for (const GemmTask &t : L.tasks) {
+    int64_t K = 0;
+    for (int q = t.seg0; q < t.seg0 + t.nseg; ++q) K += L.segs[q].K;
+    const int KB = (int)cdiv(std::max<int64_t>(K, 1), OZ_KBLK), MT = (int)cdiv(t.M, 128),
+              NT = (int)cdiv(t.N, TC_TN);
+    const int64_t pa = an, pb = bn, ea = en, eb = en + t.M;
+    an += (int64_t)MT * KB * TA;
+    bn += (int64_t)NT * KB * TB;
+    en += t.M + t.N;
+    const int whole = t.nseg == 1 ? 1 : 0;
+    int k0 = 0;
+    for (int q = t.seg0; q < t.seg0 + t.nseg; ++q) {
+      const GemmSeg &g = L.segs[q];
+      if (g.K <= 0) continue;
+      PackSeg a{};
+      a.dst_off = pa;
+      a.src_off = g.a_off;
+      a.exp_off = ea;
+      a.row0 = 0;
+      a.k0 = k0;
+      a.rows = t.M;
+      a.ks = g.K;
+      a.src_ld = g.lda;
+      a.trans = (g.flags & 1) ? 1 : 0;  // op(A) = A^T: element (m, k) at A[k lda + m]
+      a.KB = KB;
+      a.G = 16;
+      a.sb = t.sb;
+      a.src_buf = g.a_buf;
+      a.dst_buf = BUF_GOZ;
+      a.whole = whole;
+      a.exp_buf = BUF_GEXP;
+      a.alpha = g.alpha;
+      PackSeg b = a;
+      b.dst_off = pb;
+      b.src_off = g.b_off;
+      b.exp_off = eb;
+      b.rows = t.N;
+      b.src_ld = g.ldb;
+      b.trans = (g.flags & 2) ? 0 : 1;  // packed row n of op(B)^T: B[k ldb + n] unless B is stored N x K
+      b.G = TC_TN / 8;
+      b.src_buf = g.b_buf;
+      b.alpha = 1.0;
+      Z.segs.push_back(a);
+      bseg.push_back(Z.segs.size());
+      Z.segs.push_back(b);
+      Z.seg_rows = std::max(Z.seg_rows, std::max(t.M, t.N));
+      k0 += g.K;
+    }
+    TcTask u{};
+    u.a_off = pa;
+    u.b_off = pb;
+    u.c_off = t.c_off;
+    u.a_exp = ea;
+    u.b_exp = eb;
+    u.sb = t.sb;
+    u.M = t.M;
+    u.N = t.N;
+    u.KB = K > 0 ? KB : 0;
+    u.a_buf = BUF_GOZ;
+    u.b_buf = BUF_GOZ;
+    u.c_buf = t.c_buf;
+    u.mode = 2;
+    u.ldc = t.ldc;
+    u.accum = t.accumulate;
+    u.exp_buf = BUF_GEXP;
+    pend.push_back(u);
+    pmt.push_back(MT);
+    pnt.push_back(NT);
+  }
+  for (size_t i : bseg) Z.segs[i].dst_off += an;
+  for (size_t i = 0; i < pend.size(); ++i) {
+    pend[i].b_off += an;
+    oz_add_task(Z.tasks, lists, pend[i], pmt[i], pnt[i]);
+  }
+  Z.lo.assign(1, 0);
+  for (const auto &l : lists) {
+    Z.tiles.insert(Z.tiles.end(), l.begin(), l.end());
+    Z.lo.push_back((int)Z.tiles.size());
+  }
+  Z.planes = an + bn;
+  Z.nexp = en;
+  const void *p0 = c->goz_planes.p, *e0 = c->goz_exps.p;
+  NOMEM(c->ensure(c->goz_planes, 2 * (size_t)std::max<int64_t>(Z.planes, 8)) &&
+        c->ensure(c->goz_exps, 4 * (size_t)std::max<int64_t>(Z.nexp, 4)));
+  if (c->goz_planes.p != p0 || c->goz_exps.p != e0 || c->hbufs[BUF_GOZ] != c->dp(c->goz_planes)) {
+    for (int q = 0; q < c->P; ++q) {
+      c->hbufs[q * NBUF + BUF_GOZ] = c->dp(c->goz_planes);
+      c->hbufs[q * NBUF + BUF_GEXP] = c->dp(c->goz_exps);
+    }
+    NOMEM(sync_bufs(c) == IDMRG_OK);
+  }
+  NOMEM(c->upload(Z.dsegs, Z.segs) && c->upload(Z.dtasks, Z.tasks) && c->upload(Z.dtiles, Z.tiles));
+  Z.ok = true;
+  return IDMRG_OK;
+}
+
+idmrg_status oz_run(idmrg_ctx *c, OzList &Z) {
+  double *const *bufs = (double *const *)c->dbufs.p;
+  CK(cudaMemsetAsync(c->goz_planes.p, 0, 2 * (size_t)Z.planes, c->st));
+  CK(cudaMemsetAsync(c->goz_exps.p, 0x80, 4 * (size_t)Z.nexp, c->st));
+  CK(launch_oz_exp((const PackSeg *)Z.dsegs.p, (int)Z.segs.size(), Z.seg_rows, bufs, nullptr, c->st));
+  CK(launch_oz_pack((const PackSeg *)Z.dsegs.p, (int)Z.segs.size(), Z.seg_rows, bufs, nullptr, c->st));
+  for (size_t ch = 0; ch + 1 < Z.lo.size(); ++ch)
+    CK(launch_oz_gemm((const TcTile *)Z.dtiles.p + Z.lo[ch], Z.lo[ch + 1] - Z.lo[ch], (const TcTask *)Z.dtasks.p,
+                      bufs, nullptr, (int *)c->derr.p, c->st));
+  c->launches += 2 + (Z.lo.size() - 1);
+  return IDMRG_OK;
+}
+
 // tiles of every shape (L.tiles ends with the 64 x 64 ones) plus tasks and
 // segments to the device
 idmrg_status gemm_upload(idmrg_ctx *c, GemmList &L, DevBuf &dk, DevBuf &ds, GemmTune &T) {
+  T.oz.ok = false;
+  if (T.oz_use && c->oz_lists()) return oz_build(c, L, T.oz);
   for (int sh = GEMM_NSHAPE - 1; sh >= 0; --sh) {
     L.finish(GEMM_TM[sh], GEMM_TN[sh]);
     T.ntiles[sh] = (int)L.tiles.size();
@@ -344,6 +511,7 @@ idmrg_status gemm_upload(idmrg_ctx *c, GemmList &L, DevBuf &dk, DevBuf &ds, Gemm
 }
 
 idmrg_status gemm_run(idmrg_ctx *c, GemmTune &T, DevBuf &dk, DevBuf &ds, const int *active) {
+  if (T.oz.ok) return oz_run(c, T.oz);
   double *const *bufs = (double *const *)c->dbufs.p;
   int sh = T.choice;
   if (sh < 0) {
@@ -879,6 +1047,8 @@ idmrg_status plan_oz(idmrg_ctx *c) {
     q.src_buf = src_buf;
     q.dst_buf = dst_buf;
     q.whole = whole;
+    q.exp_buf = BUF_OEXP;
+    q.alpha = 1.0;
     v.push_back(q);
     mr = std::max(mr, rows);
   };
@@ -895,7 +1065,7 @@ idmrg_status plan_oz(idmrg_ctx *c) {
       u.kb_stride = KBt;
       u.kb0 = ch * per;
       u.KB = KBt > 0 ? std::min(per, KBt - u.kb0) : 0;
-      u.accum = ch > 0 ? 1 : 0;
+      u.accum = (t.accum || ch > 0) ? 1 : 0;
       const int id = (int)tasks.size();
       tasks.push_back(u);
       for (int mt = 0; mt < MT; ++mt)
@@ -957,6 +1127,7 @@ idmrg_status plan_oz(idmrg_ctx *c) {
       t.a_buf = BUF_OA1;
       t.b_buf = BUF_OB1;
       t.c_buf = BUF_OT1;
+      t.exp_buf = BUF_OEXP;
       t.mode = 2;
       t.ldc = N;
       add_task(c->oz1k, t1c, t, MT, NT);
@@ -1060,6 +1231,7 @@ idmrg_status plan_oz(idmrg_ctx *c) {
       t.b_buf = BUF_OB3;
       t.c_buf = BUF_OUT;
       t.rmap_buf = BUF_ORMAP;
+      t.exp_buf = BUF_OEXP;
       t.mode = 1;
       add_task(c->oz3k, t3c, t, MT, NT);
     }
@@ -2350,6 +2522,7 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
     return bail(IDMRG_EINVAL);
   c->mixed = opts->prec == IDMRG_TF32X3 || opts->prec == IDMRG_BF16X3;
   c->fp64tc = opts->prec == IDMRG_FP64_TC;
+  for (GemmTune *t : {&c->tn_gp, &c->tn_env1, &c->tn_env3, &c->tn_svdG, &c->tn_svdW, &c->tn_svdX}) t->oz_use = true;
   c->bf16 = opts->prec == IDMRG_BF16X3 ? 1 : 0;
   c->ell = ell;
   c->d = d;
@@ -2478,7 +2651,8 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgk, &c->dsgs,
                     &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
                     &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp, &c->doz1k,
-                    &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp})
+                    &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp, &c->goz_planes,
+                    &c->goz_exps})
     rel(*b);
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -2487,6 +2661,9 @@ void idmrg_destroy(idmrg_ctx *c) {
   if (c->pin_act) cudaFreeHost(c->pin_act);
   for (GemmTune *t : {&c->tn_g1, &c->tn_g3, &c->tn_gp, &c->tn_env1, &c->tn_env3, &c->tn_svdG, &c->tn_svdW, &c->tn_svdX}) {
     for (auto &b : t->tiles) rel(b);
+    rel(t->oz.dsegs);
+    rel(t->oz.dtasks);
+    rel(t->oz.dtiles);
     for (int k = 0; k < GEMM_NSHAPE; ++k) {
       if (t->e0[k]) cudaEventDestroy(t->e0[k]);
       if (t->e1[k]) cudaEventDestroy(t->e1[k]);

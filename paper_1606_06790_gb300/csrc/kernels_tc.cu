@@ -312,8 +312,9 @@ __device__ __forceinline__ void oz_put(__nv_bfloat16 *dst, int row, int k, int K
 
 __device__ __forceinline__ double oz_src(const PackSeg &s, double *const *bufs, int r, int k) {
   const int64_t si = s.trans ? (int64_t)k * s.src_ld + r : (int64_t)r * s.src_ld + k;
-  return s.src_fp32 ? (double)((const float *)bufs[s.sb * NBUF + s.src_buf])[s.src_off + si]
-                    : bufs[s.sb * NBUF + s.src_buf][s.src_off + si];
+  const double x = s.src_fp32 ? (double)((const float *)bufs[s.sb * NBUF + s.src_buf])[s.src_off + si]
+                              : bufs[s.sb * NBUF + s.src_buf][s.src_off + si];
+  return s.alpha == 1.0 ? x : s.alpha * x;
 }
 
 // exponents of rows whose K range spans several segments
@@ -325,7 +326,7 @@ __global__ void oz_exp_kernel(const PackSeg *__restrict__ segs, double *const *_
   if (r0 >= s.rows || s.whole) return;
   const int r1 = min(s.rows, r0 + PROWS);
   __shared__ int rexp[PROWS];
-  int *ex = (int *)bufs[s.sb * NBUF + BUF_OEXP] + s.exp_off + s.row0;
+  int *ex = (int *)bufs[s.sb * NBUF + s.exp_buf] + s.exp_off + s.row0;
   const int n = (r1 - r0) * s.ks;
   if (threadIdx.x < PROWS) rexp[threadIdx.x] = OZ_EXP_EMPTY;
   __syncthreads();
@@ -348,7 +349,7 @@ __global__ void oz_pack_kernel(const PackSeg *__restrict__ segs, double *const *
   const int r0 = blockIdx.y * PROWS;
   if (r0 >= s.rows) return;
   const int r1 = min(s.rows, r0 + PROWS);
-  int *ex = (int *)bufs[s.sb * NBUF + BUF_OEXP] + s.exp_off + s.row0;
+  int *ex = (int *)bufs[s.sb * NBUF + s.exp_buf] + s.exp_off + s.row0;
   __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>(bufs[s.sb * NBUF + s.dst_buf]) + s.dst_off;
   const int n = (r1 - r0) * s.ks;
   if (s.whole) {
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
     const int row = tile.mt * TM + 32 * warp + lane;
     const int col0 = tile.nt * TC_TN;
     double *cbase = bufs[T.sb * NBUF + T.c_buf];
-    const int *ex = (const int *)bufs[T.sb * NBUF + BUF_OEXP];
+    const int *ex = (const int *)bufs[T.sb * NBUF + T.exp_buf];
     const int ea = row < T.M ? ex[T.a_exp + row] : OZ_EXP_EMPTY;
     int64_t obase = 0;
     if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
