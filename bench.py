@@ -254,6 +254,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, pkg, dev, local, world, rank, dist):
+    """The 64 disorder realisations of uneven unit cells and m, stepped
+    together (idmrg_batch_step: host threads, one stream per realisation).
+    value = realisation unit-cell steps per second (64 per batch step), timed
+    by the wall clock around each batch step with the device synchronised on
+    both sides (the realisations' kernels run on 64 streams)."""
+    import torch
+    from workloads import disorder_batch
+    work = disorder_batch(64)
+    threads = max(1, min(16, len(os.sched_getaffinity(0))))
+    ctxs = [pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=args.prec, lanczos_maxit=160,
+                        stream=torch.cuda.Stream()) for _, mpo, m in work]
+    for _ in range(SATURATE + max(args.warmup, 3)):
+        pkg.batch_step(ctxs, threads)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    launches0 = sum(c.launch_count() for c in ctxs)
+    h2d0 = sum(c.transfer_bytes()[0] for c in ctxs)
+    d2h0 = sum(c.transfer_bytes()[1] for c in ctxs)
+    clocks = Clocks(local)
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall = 0.0
+    reps = None
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        reps = pkg.batch_step(ctxs, threads)
+        torch.cuda.synchronize()
+        wall += time.perf_counter() - t
+    clk = clocks.stop()
+    t_wall = reduce_max([wall], dist, dev)[0]
+    launches = sum(c.launch_count() for c in ctxs) - launches0
+    h2d = (sum(c.transfer_bytes()[0] for c in ctxs) - h2d0) // args.steps
+    d2h = (sum(c.transfer_bytes()[1] for c in ctxs) - d2h0) // args.steps
+    if rank == 0:
+        v = world * len(ctxs) * args.steps / t_wall
+        line = {
+            "metric": METRIC, "value": v, "unit": "realisation unit-cell steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_wall * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp64tc": "bf16-digits(f64)+f64"}.get(args.prec, f"{args.prec}+f64"),
+            "data": "synthetic",
+            "config": {"workload": "disorder64", "realisations": len(ctxs),
+                       "ell": "8/12/16/24 by r mod 4", "m": "128/256/512 by (r div 4) mod 3",
+                       "couplings": "J ~ U[0.2, 1.8], PCG64 seed 1000 + r", "host_threads": threads,
+                       "streams": len(ctxs), "regime": f"n > {SATURATE + max(args.warmup, 3)}",
+                       "kept_max": int(max(int(max(r["kept"])) for r in reps)),
+                       "timing": "wall clock per batch step, device synchronised on both sides",
+                       "l2": "flushed before every timed step (256 MiB write, outside the timing)"},
+            "roofline": None, "gpu_launches": launches,
+            "e2e": {"value": v, "unit": "realisation unit-cell steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "note": "the batch API call is the timed region"},
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def timed_run(pkg, mpo, m: int, prec: str, steps: int, warmup: int, dev, flush, dist, with_clocks: bool, local: int):
     """Saturate, warm up, then two timed regions of `steps` unit-cell steps,
     each step bracketed by CUDA events on the context's stream with the L2
@@ -333,8 +397,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3", "fp64tc"])
     ap.add_argument("--m", type=int, default=None, help="kept states (default: the workload's m)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "yc4_j1j2_l8_m1024"],
-                    help="random-bond chain l=16 m=256 (the metric's workload) or the YC4 J1-J2 cylinder")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "yc4_j1j2_l8_m1024", "disorder64"],
+                    help="random-bond chain l=16 m=256 (the metric's workload), the YC4 J1-J2 cylinder, "
+                         "or 64 disorder realisations stepped together")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -356,6 +421,8 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "disorder64":
+        return run_batch(args, pkg, dev, local, world, rank, dist)
     mpo, seed = make_workload(rank, args.workload)
     ell = len(mpo.W)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)

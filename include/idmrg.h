@@ -211,6 +211,15 @@ idmrg_status idmrg_advance(idmrg_ctx *ctx);
  * superblocks.  rep may be NULL. */
 idmrg_status idmrg_unit_cell_step(idmrg_ctx *ctx, idmrg_step_report *rep);
 
+/* One unit-cell step of each of n independent contexts (for instance disorder
+ * realisations of different unit cells and m), run concurrently by `threads`
+ * host threads; every context must have been created on its own stream, so
+ * that their kernels overlap on the GPU.  A context's results are those of
+ * idmrg_unit_cell_step on it alone.  reps (nullable) holds n reports.
+ * Returns the first status other than IDMRG_OK in context order (every
+ * context is stepped regardless). */
+idmrg_status idmrg_batch_step(idmrg_ctx *const *ctxs, int n, int threads, idmrg_step_report *reps);
+
 /* Step 5': latest e_g = (e^(n)_1 - e^(n-l)_1) / 2l with (n+1) mod l == 0
  * (e^(-1)_1 = 0) and the n it belongs to; ESTATE if there is none yet. */
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *ctx, double *e_g, int *n_of_estimate);

@@ -15,7 +15,7 @@ from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-__all__ = ["load_library", "Context", "STATUS", "PREC", "EXPORTED_SYMBOLS", "IdmrgError"]
+__all__ = ["load_library", "Context", "STATUS", "PREC", "EXPORTED_SYMBOLS", "IdmrgError", "batch_step"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libidmrg.so")
@@ -29,7 +29,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_iteration", "idmrg_psi_layout", "idmrg_block_basis", "idmrg_block_to_host",
     "idmrg_heff_apply", "idmrg_heff_apply_fp64", "idmrg_predict_wavefunction", "idmrg_lanczos_solve", "idmrg_get_psi",
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
-    "idmrg_unit_cell_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
+    "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
     "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_save", "idmrg_load",
 ]
@@ -106,6 +106,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_update_environments": (i, [vp, i]),
         "idmrg_advance": (i, [vp]),
         "idmrg_unit_cell_step": (i, [vp, P(_Report)]),
+        "idmrg_batch_step": (i, [vp, i, i, vp]),
         "idmrg_energy_per_site": (i, [vp, P(d), P(i)]),
         "idmrg_heff_cost": (i, [vp, i, P(d), P(d)]),
         "idmrg_launch_count": (i, [vp, P(C.c_uint64)]),
@@ -290,7 +291,7 @@ class Context:
     def advance(self) -> None:
         self._check(self.lib.idmrg_advance(self.h), "advance")
 
-    def unit_cell_step(self) -> Dict[str, object]:
+    def _report(self):
         P = self.P
         arr = {k: np.zeros(P) for k in ("energy", "eps", "eps_best", "fidelity", "bond")}
         iarr = {k: np.zeros(P, dtype=np.int32) for k in ("iters", "kept")}
@@ -298,10 +299,18 @@ class Context:
                       _dptr(arr["eps"], C.c_double), _dptr(arr["eps_best"], C.c_double),
                       _dptr(arr["fidelity"], C.c_double), _dptr(arr["bond"], C.c_double),
                       _dptr(iarr["kept"], C.c_int), float("nan"))
-        s = self._check(self.lib.idmrg_unit_cell_step(self.h, C.byref(rep)), "unit_cell_step", ok=(0, 4))
-        out: Dict[str, object] = dict(n=rep.n, converged=(s == 0), **arr, **iarr)
+        return rep, arr, iarr
+
+    @staticmethod
+    def _report_dict(rep, arr, iarr, converged: bool) -> Dict[str, object]:
+        out: Dict[str, object] = dict(n=rep.n, converged=converged, **arr, **iarr)
         out["e_g"] = None if math.isnan(rep.e_g) else rep.e_g
         return out
+
+    def unit_cell_step(self) -> Dict[str, object]:
+        rep, arr, iarr = self._report()
+        s = self._check(self.lib.idmrg_unit_cell_step(self.h, C.byref(rep)), "unit_cell_step", ok=(0, 4))
+        return self._report_dict(rep, arr, iarr, s == 0)
 
     def save(self, path: str) -> None:
         """Checkpoint between steps (idmrg_save)."""
@@ -353,6 +362,26 @@ class Context:
         a, b = C.c_uint64(), C.c_uint64()
         self._check(self.lib.idmrg_transfer_bytes(self.h, C.byref(a), C.byref(b)), "transfer_bytes")
         return int(a.value), int(b.value)
+
+
+def batch_step(contexts: Sequence["Context"], threads: int = 16) -> List[Dict[str, object]]:
+    """One unit-cell step of every context (independent problems, e.g. disorder
+    realisations), run concurrently on `threads` host threads; each context
+    must have its own CUDA stream.  Returns the step reports in order."""
+    if not contexts:
+        return []
+    lib = contexts[0].lib
+    reps = [c._report() for c in contexts]
+    arr = (_Report * len(contexts))(*[r[0] for r in reps])
+    hs = (C.c_void_p * len(contexts))(*[c.h for c in contexts])
+    s = lib.idmrg_batch_step(C.cast(hs, C.c_void_p), len(contexts), int(threads), C.cast(arr, C.c_void_p))
+    if s not in (0, 4):
+        raise IdmrgError(s, "batch_step: " + "; ".join(
+            c.lib.idmrg_last_error(c.h).decode() for c in contexts if c.lib.idmrg_last_error(c.h)))
+    out = []
+    for i, (_, a, ia) in enumerate(reps):
+        out.append(Context._report_dict(arr[i], a, ia, True))
+    return out
 
 
 def layout_pack(desc: np.ndarray, N: int, dense: np.ndarray) -> np.ndarray:

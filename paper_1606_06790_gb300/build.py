@@ -54,7 +54,7 @@ def build(verbose: bool = False) -> str:
         logs = list(ex.map(_run, jobs))
     objs = [j[-1] for j in jobs]
     tmp = LIB + ".tmp"
-    logs.append(_run([nvcc, *ARCH, "-shared", "-o", tmp, *objs]))
+    logs.append(_run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]))
     os.replace(tmp, LIB)
     if verbose:
         print("".join(logs))

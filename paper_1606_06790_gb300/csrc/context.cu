@@ -15,7 +15,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
+#include <thread>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1582,7 +1584,9 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   for (int q = 0; q < P; ++q)
     if (want(p, q) && c->stage[q] != ST_STARTED)
       return c->fail(IDMRG_ESTATE, "lanczos_solve: superblock %d has no start vector", q);
-  const int kmax = c->o.lanczos_maxit;
+  // a mixed-precision run stops after 80 iterations and restarts: its Krylov
+  // basis never holds more than 81 vectors
+  const int kmax = c->mixed ? std::min(c->o.lanczos_maxit, 81) : c->o.lanczos_maxit;
   std::vector<int64_t> N(P);
   int64_t nmax = 1;
   for (int q = 0; q < P; ++q) {
@@ -2879,6 +2883,28 @@ idmrg_status idmrg_update_environments(idmrg_ctx *c, int p) {
 idmrg_status idmrg_advance(idmrg_ctx *c) {
   if (!c) return IDMRG_EINVAL;
   return advance(c);
+}
+
+idmrg_status idmrg_batch_step(idmrg_ctx *const *ctxs, int n, int threads, idmrg_step_report *reps) {
+  if (!ctxs || n < 0 || threads < 1) return IDMRG_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return IDMRG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IDMRG_ECUDA;
+  std::vector<idmrg_status> st(n, IDMRG_OK);
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next++; i < n; i = next++) st[i] = idmrg_unit_cell_step(ctxs[i], reps ? &reps[i] : nullptr);
+  };
+  const int nt = std::min(threads, std::max(n, 1));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != IDMRG_OK) return st[i];
+  return IDMRG_OK;
 }
 
 idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {

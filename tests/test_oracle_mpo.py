@@ -69,3 +69,16 @@ def test_kagome_lattice_geometry():
         assert len(nb[s]) == 4
         tri = sum(1 for a in nb[s] for c in nb[s] if a < c and c in nb[a])
         assert tri == 2
+
+
+def test_disorder_batch_recipe():
+    """The 64-realisation workload: uneven unit cells and m as specified, and
+    distinct couplings per realisation."""
+    from workloads import disorder_batch
+    work = disorder_batch(64)
+    assert [len(mpo.W) for _, mpo, _ in work[:8]] == [8, 12, 16, 24] * 2
+    assert [m for _, _, m in work[:12]] == [128] * 4 + [256] * 4 + [512] * 4
+    assert [m for _, _, m in work[12:16]] == [128] * 4
+    w0 = np.concatenate([w.ravel() for w in work[0][1].W])
+    w4 = np.concatenate([w.ravel() for w in work[4][1].W])
+    assert not np.array_equal(w0, w4)

@@ -18,4 +18,4 @@ from .lattices import (  # noqa: F401
     open_chain_bonds,
 )
 from .mpo import MPO, build_mpo  # noqa: F401
-from .configs import CONFIGS, make_config  # noqa: F401
+from .configs import CONFIGS, disorder_batch, make_config  # noqa: F401

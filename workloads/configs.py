@@ -40,3 +40,17 @@ def make_config(name: str, **override):
 def start_vector_seed() -> int:
     """Seed of the Lanczos start vectors for n = 1, 2 (0 for every workload)."""
     return 0
+
+
+def disorder_batch(count: int = 64, lo: float = 0.2, hi: float = 1.8):
+    """Disorder realisations r = 0..count-1 of the random-bond Heisenberg chain
+    with uneven unit cells: l = (8, 12, 16, 24)[r % 4], m = (128, 256,
+    512)[(r // 4) % 3], J_k ~ U[lo, hi] i.i.d. from PCG64 seed 1000 + r.
+    Returns a list of (name, mpo, m)."""
+    out = []
+    for r in range(count):
+        ell = (8, 12, 16, 24)[r % 4]
+        m = (128, 256, 512)[(r // 4) % 3]
+        bonds = lat.random_chain_bonds(ell, lo, hi, 1000 + r)
+        out.append((f"disorder_r{r}_l{ell}_m{m}", build_mpo(bonds, ell), m))
+    return out
