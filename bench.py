@@ -136,8 +136,8 @@ def source_hash(*names):
 
 KERNEL_SOURCES = {"heff_gemm": ["kernels_f64.cu", "kernels_tc.cu"], "heff_wstage": ["kernels_f64.cu", "kernels_tc.cu"],
                   "lanczos_vec": ["kernels_lanczos.cu"], "lanczos_tri": ["kernels_lanczos.cu"],
-                  "svd": ["kernels_svd.cu"], "env": ["kernels_f64.cu"], "predict": ["kernels_f64.cu"],
-                  "heff_f64": ["kernels_f64.cu"]}
+                  "svd": ["kernels_svd.cu", "kernels_tc.cu"], "env": ["kernels_f64.cu", "kernels_tc.cu"],
+                  "predict": ["kernels_f64.cu", "kernels_tc.cu"], "heff_f64": ["kernels_f64.cu", "kernels_tc.cu"]}
 
 
 def traffic_for(kclass: str, prec: str):

@@ -518,17 +518,31 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
     if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
 #pragma unroll 1
     for (int c = 0; c < TC_TN; c += 16) {
-      double acc[16];
+      // Levels 0..4 are exact integers (|sum| < 2^24): Horner in base 128 in
+      // int64 gives H = sum_t L_t 128^(4-t) exactly (|H| < 2^53), in units
+      // of 2^-42.  Levels 5..7 carry FP32 rounding anyway: T = L_5 2^14 +
+      // L_6 2^7 + L_7 in FP32, in units of 2^-63 (its error lies below 2^-58
+      // of the leading term).  Then value = (H 2^-42 + T 2^-63) 2^(ea+eb):
+      // two conversions, one multiply and one FMA in FP64 per output.
+      long long H[16];
+      float Tl[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+      for (int i = 0; i < 16; ++i) {
+        H[i] = 0;
+        Tl[i] = 0.f;
+      }
       if (T.KB > 0) {
 #pragma unroll 1
-        for (int t = OZ_PLANES - 1; t >= 0; --t) {  // small levels first
+        for (int t = 0; t < OZ_PLANES; ++t) {
           float v[16];
           tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(TC_TN * t + c), v);
-          const double sc = scalbn(1.0, -7 * (t + 2));
+          if (t <= 4) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[i] = fma((double)v[i], sc, acc[i]);
+            for (int i = 0; i < 16; ++i) H[i] = H[i] * 128 + (long long)v[i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) Tl[i] = fmaf(Tl[i], 128.0f, v[i]);
+          }
         }
       }
       if (row < T.M) {
@@ -537,7 +551,17 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
           const int col = col0 + c + i;
           if (col >= T.N) break;
           const int eb = ex[T.b_exp + col];
-          const double val = (ea == OZ_EXP_EMPTY || eb == OZ_EXP_EMPTY) ? 0.0 : scalbn(acc[i], ea + eb);
+          double val = 0.0;
+          if (ea != OZ_EXP_EMPTY && eb != OZ_EXP_EMPTY) {
+            const int k = ea + eb;
+            if (k - 63 > -1000 && k - 42 < 1000) {  // both powers of two are normal doubles
+              const double s42 = __longlong_as_double((long long)(k - 42 + 1023) << 52);
+              const double s63 = __longlong_as_double((long long)(k - 63 + 1023) << 52);
+              val = fma((double)Tl[i], s63, (double)H[i] * s42);
+            } else {
+              val = scalbn(fma((double)Tl[i], 0x1p-21, (double)H[i]), k - 42);
+            }
+          }
           double &dst = T.mode == 1 ? cbase[obase + col] : cbase[T.c_off + (int64_t)row * T.ldc + col];
           dst = T.accum ? dst + val : val;
         }
