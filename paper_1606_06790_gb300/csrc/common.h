@@ -190,12 +190,14 @@ struct LanczosDev {
   double tol;            // convergence: |b_k y_k| <= tol max(1, |theta|) ...
   double inner_factor;   // ... or, from the second Krylov vector on, <= target[s]
   double *target;        // [S] set at k = 0: max(tol max(1,|theta|), inner_factor b_0)
+  double **bufs;         // buffer table of the H_eff launches: next_kernel points BUF_IN at V[k]
 };
 cudaError_t lanczos_set_ptrs(const LanczosDev &L, double **bufs, cudaStream_t st);
 cudaError_t lanczos_project(const LanczosDev &L, int pass, cudaStream_t st);   // h = V^T w  (j <= k)
 cudaError_t lanczos_subtract(const LanczosDev &L, int pass, cudaStream_t st);  // w -= V h (+ ||w||^2 partials on pass 1)
+cudaError_t lanczos_sub0_proj1(const LanczosDev &L, cudaStream_t st);  // subtract pass 0 + project pass 1, fused
 cudaError_t lanczos_finalize(const LanczosDev &L, cudaStream_t st);            // alpha, beta, tridiagonal, convergence
-cudaError_t lanczos_next(const LanczosDev &L, cudaStream_t st);                // V[k+1] = w / beta, k++
+cudaError_t lanczos_next(const LanczosDev &L, cudaStream_t st);                // V[k] = w / beta[k-1], BUF_IN -> V[k]
 cudaError_t lanczos_init(const LanczosDev &L, const double *const *start, cudaStream_t st); // V[0] = start/|start|
 cudaError_t lanczos_ritz(const LanczosDev &L, double *const *out, cudaStream_t st);  // out = V y / |V y|
 cudaError_t lanczos_dot(const LanczosDev &L, const double *const *a, const double *const *b, double *res,

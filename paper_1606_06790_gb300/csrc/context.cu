@@ -1560,13 +1560,11 @@ idmrg_status predict(idmrg_ctx *c, int p) {
 // tridiagonal solve and convergence test, next Krylov vector.  `act` and
 // `vb` only feed the per-class timers (act may be null).
 idmrg_status lanczos_iteration(idmrg_ctx *c, const LanczosDev &L, bool fp64, const int *act, double vb) {
-  CK(lanczos_set_ptrs(L, (double **)c->dbufs.p, c->st));
   idmrg_status s = heff_launch(c, L.active, act, fp64);
   if (s != IDMRG_OK) return s;
   c->kbegin(IDMRG_K_LANCZOS_VEC);
   CK(lanczos_project(L, 0, c->st));
-  CK(lanczos_subtract(L, 0, c->st));
-  CK(lanczos_project(L, 1, c->st));
+  CK(lanczos_sub0_proj1(L, c->st));
   CK(lanczos_subtract(L, 1, c->st));
   c->kend(IDMRG_K_LANCZOS_VEC, 0.0, vb);
   c->kbegin(IDMRG_K_LANCZOS_TRI);
@@ -1575,7 +1573,7 @@ idmrg_status lanczos_iteration(idmrg_ctx *c, const LanczosDev &L, bool fp64, con
   c->kbegin(IDMRG_K_LANCZOS_VEC);
   CK(lanczos_next(L, c->st));
   c->kend(IDMRG_K_LANCZOS_VEC);
-  c->launches += 7;
+  c->launches += 5;
   return IDMRG_OK;
 }
 
@@ -1641,6 +1639,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   L.tol = c->o.lanczos_tol;
   NOMEM(c->ensure(c->dtarget, 8 * P));
   L.target = c->dp(c->dtarget);
+  L.bufs = (double **)c->dbufs.p;
   // FP64: one Lanczos run.  Mixed precision: restarts.  Each restart begins
   // with an FP64 matvec on its start vector, so k = 0 checks the true residual
   // against tol (and its alpha_0 is the FP64 Rayleigh quotient); the following
@@ -1674,7 +1673,8 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
     if (!anym) break;
     NOMEM(c->upload(c->lmember, member));
     CK(lanczos_init(L, (const double *const *)c->lpsi.p, c->st));
-    c->launches += 3;
+    CK(lanczos_set_ptrs(L, (double **)c->dbufs.p, c->st));  // later ones: next_kernel
+    c->launches += 4;
     if (r == 0) CK(c->d2h_copy(nrm2.data(), c->lresid.p, 8 * P));  // ||psi~|| for the report
     for (int it = 0; it < inner_cap; ++it) {
       // the same iteration as a graph once the kernels of its matvec are

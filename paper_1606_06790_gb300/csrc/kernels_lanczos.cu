@@ -129,6 +129,54 @@ __global__ void subtract_kernel(LanczosDev L, int pass) {
   }
 }
 
+// Pass 0's subtraction fused with pass 1's projection: each CTA takes one
+// projection chunk of PCH elements, forms alpha from the pass-0 partials (in
+// the fixed order of subtract_kernel), updates its chunk of w (w -= alpha v_k
+// + beta_{k-1} v_{k-1}), keeps it in shared memory and writes the partial
+// dots of every Krylov vector with it (project_kernel, pass 1): the same
+// numbers as the two separate kernels, one launch and one pass over w fewer.
+__global__ void sub0_proj1_kernel(LanczosDev L) {
+  __shared__ double ws[PCH];
+  __shared__ double s_ab[2];
+  const int s = blockIdx.y;
+  if (!L.active[s]) return;
+  const int64_t N = L.N[s];
+  const int64_t e0 = (int64_t)blockIdx.x * PCH;
+  if (e0 >= N) return;
+  const int n = (int)min((int64_t)PCH, N - e0);
+  const int kk = L.k[s];
+  const int npc = (int)((N + PCH - 1) / PCH);
+  if (threadIdx.x == 0) {
+    const double *p = L.part + ((int64_t)s * L.kmax + kk) * L.nchunk_max;  // pass 0
+    double acc = 0.0;
+    for (int c = 0; c < npc; ++c) acc += p[c];
+    s_ab[0] = acc;
+    s_ab[1] = kk > 0 ? L.beta[s * L.kmax + kk - 1] : 0.0;
+    if (blockIdx.x == 0) L.h[(int64_t)s * L.kmax + kk] = acc;
+  }
+  __syncthreads();
+  const double a = s_ab[0], b = s_ab[1];
+  double *w = L.w[s] + e0;
+  const double *vk = L.V[s] + (int64_t)kk * N + e0;
+  const double *vp = L.V[s] + (int64_t)(kk > 0 ? kk - 1 : kk) * N + e0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double acc = fma(-a, vk[i], w[i]);
+    if (kk > 0) acc = fma(-b, vp[i], acc);
+    w[i] = acc;
+    ws[i] = acc;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j <= kk; j += nw) {
+    const double *v = L.V[s] + (int64_t)j * N + e0;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int i = lane; i < n; i += 32) acc = fma(v[i], ws[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) L.part[(((int64_t)L.S + s) * L.kmax + j) * L.nchunk_max + blockIdx.x] = acc;  // pass 1
+  }
+}
+
 // ---- tridiagonal eigen-solver (lowest pair), one warp per superblock ----
 // Sturm count in FP32: the eigenvalue is only bracketed here (to ~1e-7
 // relative); its FP64 value comes from inverse iteration and a Rayleigh
@@ -283,7 +331,8 @@ __global__ void finalize_kernel(LanczosDev L) {
   }
 }
 
-// V[k] = w / beta[k-1] for superblocks still iterating (k already advanced)
+// V[k] = w / beta[k-1] for superblocks still iterating (k already advanced);
+// the next matvec's input pointer moves to V[k] here (no launch of its own)
 __global__ void next_kernel(LanczosDev L) {
   const int s = blockIdx.y;
   if (!L.active[s]) return;
@@ -291,6 +340,7 @@ __global__ void next_kernel(LanczosDev L) {
   const int kk = L.k[s];
   const double inv = 1.0 / L.beta[s * L.kmax + kk - 1];
   double *v = L.V[s] + (int64_t)kk * N;
+  if (blockIdx.x == 0 && threadIdx.x == 0) L.bufs[s * NBUF + BUF_IN] = v;
   const double *w = L.w[s];
   for (int64_t e = (int64_t)blockIdx.x * CH + threadIdx.x; e < min(N, (int64_t)(blockIdx.x + 1) * CH); e += LT)
     v[e] = w[e] * inv;
@@ -398,6 +448,12 @@ cudaError_t lanczos_project(const LanczosDev &L, int pass, cudaStream_t st) {
   // projection chunks of PCH elements: nchunk_max counts chunks of CH <= PCH
   dim3 grid((L.nchunk_max * CH + PCH - 1) / PCH, L.S);
   project_kernel<<<grid, LT, 0, st>>>(L, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_sub0_proj1(const LanczosDev &L, cudaStream_t st) {
+  dim3 grid((L.nchunk_max * CH + PCH - 1) / PCH, L.S);
+  sub0_proj1_kernel<<<grid, LT, 0, st>>>(L);
   return cudaGetLastError();
 }
 
