@@ -1,13 +1,13 @@
 """The bench workload at full size, in the launch configuration bench.py
 times: random-bond chain l = 16, J ~ U[0.5, 1.5] (seed 1606), m = 256, all
 8 superblocks batched, run in lockstep with the FP64 oracle from n = 1 into
-the saturated regime (D = m).  FP64 mode within 1e-10 per site, TF32x3 mode
-within 1e-8 per site, every step; kept dimensions equal except where the
-zero threshold decides them (see _check_kept).
+the saturated regime (D = m).  FP64 and FP64_TC modes within 1e-10 per site,
+TF32x3 and BF16x3 within 1e-8 per site, every step; kept dimensions equal
+except where the zero threshold decides them (see _check_kept).
 
 Also the wider MPOs (w up to 20) and longer unit cells of the two cylinder
 models, at reduced m: J1-J2 on the 4-leg square cylinder (l = 8) and the
-kagome YC8 cylinder (l = 12), FP64 within 1e-10 per site.
+kagome YC8 cylinder (l = 12), FP64 and FP64_TC within 1e-10 per site.
 """
 import numpy as np
 import pytest
@@ -53,24 +53,24 @@ def _check(ctx, g, r, tol):
         assert abs(g["e_g"] - r.e_g) < tol
 
 
-def test_bench_workload_fp64_and_tf32x3_against_oracle():
+def test_bench_workload_all_precisions_against_oracle():
+    """FP64 and FP64_TC (digit slices) within 1e-10 per site, TF32x3 and BF16x3
+    within 1e-8, every step of the same oracle run."""
     mpo, o = make_config("randchain_l16_m256")
     m = o["m"]
     ref = ParallelIDMRG.from_mpo(mpo, m=m)
-    g64 = context(mpo, m, prec="fp64")
-    gmx = context(mpo, m, prec="tf32x3")
+    ctxs = {p: context(mpo, m, prec=p) for p in ("fp64", "fp64tc", "tf32x3", "bf16x3")}
+    tol = {"fp64": 1e-10, "fp64tc": 1e-10, "tf32x3": 1e-8, "bf16x3": 1e-8}
     saturated = 0
     for _ in range(16):
         r = ref.step()
-        a = g64.unit_cell_step()
-        b = gmx.unit_cell_step()
-        _check(g64, a, r, 1e-10)
-        _check(gmx, b, r, 1e-8)
+        for p, ctx in ctxs.items():
+            _check(ctx, ctx.unit_cell_step(), r, tol[p])
         # the cut at m (less the multiplet it would split) decides D
         saturated += int(np.min(r.kept) >= 0.9 * m)
     assert saturated >= 3          # several steps in the benchmarked regime
-    g64.close()
-    gmx.close()
+    for ctx in ctxs.values():
+        ctx.close()
 
 
 @pytest.mark.parametrize("name,bonds,ell,m,steps", [
@@ -78,9 +78,13 @@ def test_bench_workload_fp64_and_tf32x3_against_oracle():
     ("kagome_yc8_l12_m32", kagome_yc8_bonds(1.0), 12, 32, 12),
 ])
 def test_cylinder_models_fp64(name, bonds, ell, m, steps):
+    """FP64 and FP64_TC within 1e-10 per site on the wide MPOs."""
     mpo = build_mpo(bonds, ell)
     ref = ParallelIDMRG.from_mpo(mpo, m=m)
-    ctx = context(mpo, m)
+    ctxs = [context(mpo, m), context(mpo, m, prec="fp64tc")]
     for _ in range(steps):
-        _check(ctx, ctx.unit_cell_step(), ref.step(), 1e-10)
-    ctx.close()
+        r = ref.step()
+        for ctx in ctxs:
+            _check(ctx, ctx.unit_cell_step(), r, 1e-10)
+    for ctx in ctxs:
+        ctx.close()
