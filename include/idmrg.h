@@ -220,6 +220,17 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *ctx, idmrg_step_report *rep);
  * context is stepped regardless). */
 idmrg_status idmrg_batch_step(idmrg_ctx *const *ctxs, int n, int threads, idmrg_step_report *reps);
 
+/* Truncation error of the run (Sec. 5, Eq. tru): the largest eps^(n)_1 over
+ * the last l iterations (one period).  ESTATE before the first step. */
+idmrg_status idmrg_truncation_error(const idmrg_ctx *ctx, double *eps);
+
+/* Unit-cell steps until two successive estimates of e_g (Step 5', one every
+ * l iterations) differ by less than de_tol, or max_steps steps.  Writes the
+ * last e_g, the truncation error and the steps taken (each nullable);
+ * IDMRG_ENOCONV when max_steps ran out first.  One point of the m scan of
+ * Sec. 5 (e_g against eps for several m, extrapolated to eps -> 0). */
+idmrg_status idmrg_run(idmrg_ctx *ctx, int max_steps, double de_tol, double *e_g, double *eps, int *steps);
+
 /* Step 5': latest e_g = (e^(n)_1 - e^(n-l)_1) / 2l with (n+1) mod l == 0
  * (e^(-1)_1 = 0) and the n it belongs to; ESTATE if there is none yet. */
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *ctx, double *e_g, int *n_of_estimate);

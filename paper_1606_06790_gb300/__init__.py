@@ -29,7 +29,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_iteration", "idmrg_psi_layout", "idmrg_block_basis", "idmrg_block_to_host",
     "idmrg_heff_apply", "idmrg_heff_apply_fp64", "idmrg_predict_wavefunction", "idmrg_lanczos_solve", "idmrg_get_psi",
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
-    "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
+    "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
     "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_save", "idmrg_load",
 ]
@@ -107,6 +107,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_advance": (i, [vp]),
         "idmrg_unit_cell_step": (i, [vp, P(_Report)]),
         "idmrg_batch_step": (i, [vp, i, i, vp]),
+        "idmrg_run": (i, [vp, i, d, P(d), P(d), P(i)]),
+        "idmrg_truncation_error": (i, [vp, P(d)]),
         "idmrg_energy_per_site": (i, [vp, P(d), P(i)]),
         "idmrg_heff_cost": (i, [vp, i, P(d), P(d)]),
         "idmrg_launch_count": (i, [vp, P(C.c_uint64)]),
@@ -290,6 +292,20 @@ class Context:
 
     def advance(self) -> None:
         self._check(self.lib.idmrg_advance(self.h), "advance")
+
+    def run(self, max_steps: int, de_tol: float = 1e-8):
+        """Unit-cell steps until successive e_g estimates differ by less than
+        de_tol (or max_steps): (e_g, eps, steps, converged)."""
+        eg, eps, k = C.c_double(), C.c_double(), C.c_int()
+        s = self._check(self.lib.idmrg_run(self.h, int(max_steps), float(de_tol), C.byref(eg), C.byref(eps),
+                                           C.byref(k)), "run", ok=(0, 4))
+        return eg.value, eps.value, k.value, s == 0
+
+    def truncation_error(self) -> float:
+        """Largest eps^(n)_1 over the last l iterations (Eq. tru)."""
+        e = C.c_double()
+        self._check(self.lib.idmrg_truncation_error(self.h, C.byref(e)), "truncation_error")
+        return e.value
 
     def _report(self):
         P = self.P

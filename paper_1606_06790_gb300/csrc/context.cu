@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <map>
 #include <thread>
@@ -140,6 +141,7 @@ struct idmrg_ctx {
   std::vector<Env> envL, envR, newL, newR;
   std::vector<TruncRec> cur, prev, prev2;
   std::map<int, double> e1;   // e^(n)_1
+  std::map<int, double> eps1; // eps^(n)_1 (Eq. tru), for the truncation error of a run
   double eg_last = NAN;
   int eg_n = -1;
   std::vector<double> energy, fidelity, bond, startnorm;
@@ -2375,6 +2377,7 @@ idmrg_status advance(idmrg_ctx *c) {
     std::swap(c->envL[q], c->newL[q]);
     std::swap(c->envR[q], c->newR[q]);
   }
+  c->eps1[c->n] = c->cur[0].eps;
   // lambda history: cur -> prev -> prev2 (buffers recycled)
   for (int q = 0; q < P; ++q) {
     std::swap(c->prev2[q], c->prev[q]);
@@ -2978,6 +2981,14 @@ idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
   }
   F.putv(e1n);
   F.putv(e1v);
+  std::vector<int> ern;
+  std::vector<double> erv;
+  for (const auto &kv : c->eps1) {
+    ern.push_back(kv.first);
+    erv.push_back(kv.second);
+  }
+  F.putv(ern);
+  F.putv(erv);
   for (int q = 0; q < c->P; ++q) {
     for (const Env *E : {&c->envL[q], &c->envR[q]}) {
       ck_put_basis(F, E->lay.b);
@@ -3039,7 +3050,12 @@ idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
   F.get(eg_last);
   F.getv(e1n, 1 << 30);
   F.getv(e1v, 1 << 30);
-  if (!F.ok || n < 1 || e1n.size() != e1v.size()) return c->fail(IDMRG_EINVAL, "load: checkpoint header damaged");
+  std::vector<int> ern;
+  std::vector<double> erv;
+  F.getv(ern, 1 << 30);
+  F.getv(erv, 1 << 30);
+  if (!F.ok || n < 1 || e1n.size() != e1v.size() || ern.size() != erv.size())
+    return c->fail(IDMRG_EINVAL, "load: checkpoint header damaged");
   for (int q = 0; q < P; ++q) {
     for (Env *E : {&c->envL[q], &c->envR[q]}) {
       Basis b;
@@ -3086,7 +3102,39 @@ idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
   c->eg_last = eg_last;
   c->e1.clear();
   for (size_t k = 0; k < e1n.size(); ++k) c->e1[e1n[k]] = e1v[k];
+  c->eps1.clear();
+  for (size_t k = 0; k < ern.size(); ++k) c->eps1[ern[k]] = erv[k];
   return plan_iteration(c);
+}
+
+idmrg_status idmrg_truncation_error(const idmrg_ctx *c, double *eps) {
+  if (!c || !eps) return IDMRG_EINVAL;
+  if (c->eps1.empty()) return IDMRG_ESTATE;
+  double e = 0.0;
+  int k = 0;
+  for (auto it = c->eps1.rbegin(); it != c->eps1.rend() && k < c->ell; ++it, ++k) e = std::max(e, it->second);
+  *eps = e;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_run(idmrg_ctx *c, int max_steps, double de_tol, double *e_g, double *eps, int *steps) {
+  if (!c || max_steps < 1 || !(de_tol > 0)) return IDMRG_EINVAL;
+  double last = NAN;
+  int last_n = -1, k = 0;
+  bool done = false;
+  for (; k < max_steps && !done; ++k) {
+    const idmrg_status s = idmrg_unit_cell_step(c, nullptr);
+    if (s != IDMRG_OK && s != IDMRG_ENOCONV) return s;
+    if (c->eg_n >= 0 && c->eg_n != last_n) {  // a new estimate of e_g
+      done = std::isfinite(last) && fabs(c->eg_last - last) < de_tol;
+      last = c->eg_last;
+      last_n = c->eg_n;
+    }
+  }
+  if (steps) *steps = k;
+  if (e_g) *e_g = c->eg_last;
+  if (eps) idmrg_truncation_error(c, eps);
+  return done ? IDMRG_OK : IDMRG_ENOCONV;
 }
 
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *c, double *e_g, int *n_of_estimate) {
