@@ -886,16 +886,19 @@ __device__ __forceinline__ int bj_rotation(double graw, double &a, double &b, do
   cp = -t * (d2 * recip_split(d1));
   cq = t * (d1 * recip_split(d2));
   // new squared norms cos^2 (a -+ 2 t g + t^2 b); recomputed from the data
-  // when they fall below 2^-20 of the larger input (cancellation)
+  // when one falls below 2^-20 of its old value (cancellation)
   const double c2 = cs * cs, t2 = t * t, tg = t * g;
   const double a2 = c2 * fma(-2.0, tg, fma(t2, b, a)), b2 = c2 * fma(2.0, tg, fma(t2, a, b));
   d1 *= cs;
   d2 *= cs;
   a = a2;
   b = b2;
-  const int emax = max(sa.e, sb.e) - 20;
+  // cancellation: a new norm far below its own old value.  For the
+  // rotation that zeroes g, |t g| and t^2 b are at most of order a (and
+  // |t g|, t^2 a at most of order b), so only a2 << a (b2 << b) loses
+  // digits; a column much smaller than its partner is not a cancellation.
   const Split s2a = split_f64(a2), s2b = split_f64(b2);
-  const bool oka = s2a.m > 0.0f && s2a.e > emax, okb = s2b.m > 0.0f && s2b.e > emax;
+  const bool oka = s2a.m > 0.0f && s2a.e > sa.e - 20, okb = s2b.m > 0.0f && s2b.e > sb.e - 20;
   return (oka && okb) ? 1 : 2;
 }
 
