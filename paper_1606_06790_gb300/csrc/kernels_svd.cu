@@ -216,6 +216,56 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const SvdJob *__restri
 // the owner of k forms the reflector and publishes it; every CTA applies it
 // to its own trailing columns.  The trailing update, which holds the
 // single-CTA kernel at one SM's FP64 rate, is spread over C SMs.
+// Exponent and FP32 mantissa of a double, by integer operations only (an
+// FP64 instruction costs 64 cycles of its sub-partition's FP64 unit here):
+// x = m 2^e with |m| in [1, 2) (mantissa truncated to 23 bits); zero and
+// subnormals give m = 0.
+struct Split {
+  float m;
+  int e;
+};
+__device__ __forceinline__ Split split_f64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int be = (int)((hi >> 20) & 0x7ffu);
+  Split r;
+  if (be == 0) {
+    r.m = 0.0f;
+    r.e = 0;
+    return r;
+  }
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  r.m = __uint_as_float((hi & 0x80000000u) | (127u << 23) | mant);
+  r.e = be - 1023;
+  return r;
+}
+
+// the double of an FP32 number times 2^k (integer operations; f normal or
+// zero, result in the normal range)
+__device__ __forceinline__ double f64_of(float f, int k = 0) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0) return 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((ex + 896u + (unsigned)k) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 0x7u) << 29));
+}
+
+// 1/x for x > 0 in the normal range: FP32 estimate of the mantissa's
+// reciprocal, then two Newton steps e <- e (2 - x e) in FP64
+__device__ __forceinline__ double recip_split(double x) {
+  const Split s = split_f64(x);
+  double e = f64_of(__frcp_rn(s.m), -s.e);
+  e = e * fma(-x, e, 2.0);
+  e = e * fma(-x, e, 2.0);
+  return e;
+}
+
+// 1/x for any finite non-zero x: Newton from an FP32 estimate in the normal
+// range, the FP64 division outside it
+__device__ __forceinline__ double recip_signed(double x) {
+  const double ax = fabs(x);
+  return (ax > 1e-290 && ax < 1e290) ? copysign(recip_split(ax), x) : 1.0 / x;
+}
+
 constexpr int QC_THREADS = 256;
 constexpr int QC_MAX_CLUSTER = 16;
 
@@ -240,7 +290,7 @@ __global__ void __launch_bounds__(QC_THREADS)
   double *vn = swp + ld, *vref = vn + nloc;      // [nloc] squared norms
   int *pl = (int *)(vref + nloc);                // [nloc] original column at each position
   __shared__ double cand_v[QC_MAX_CLUSTER], red_v[QC_THREADS / 32], s_tau, s_beta, s_scale, s_swap_vn, s_swap_vref;
-  __shared__ int cand_i[QC_MAX_CLUSTER], red_i[QC_THREADS / 32], s_piv, s_stop, s_swap_pl;
+  __shared__ int cand_i[QC_MAX_CLUSTER], s_piv, s_stop, s_swap_pl;
   __shared__ double s_vp, s_stop2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   auto pos = [&](int l) { return crank + C * l; };
@@ -269,43 +319,47 @@ __global__ void __launch_bounds__(QC_THREADS)
   int *cand_i0 = cluster.map_shared_rank(cand_i, 0);
   int rank = ca;
   for (int k = 0; k < ca; ++k) {
-    // (a) pivot: local candidate, gathered in rank 0, the same choice everywhere
-    double bv = -1.0;
-    int bi = 0x7fffffff;
-    for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
-      const int j = pos(l);
-      if (j >= k && j < ca && (vn[l] > bv || (vn[l] == bv && j < bi))) {
-        bv = vn[l];
-        bi = j;
+    // (a) pivot: local candidate, gathered in rank 0, the same choice
+    // everywhere.  The squared norms are non-negative, so they order like
+    // their bit patterns as 64-bit integers: the comparisons run on the
+    // integer units (an FP64 compare costs 64 cycles of the FP64 unit here).
+    // A CTA holds at most a few dozen columns: warp 0 scans them.
+    if (warp == 0) {
+      long long bv = -1;
+      int bi = 0x7fffffff;
+      for (int l = lane; l < nloc; l += 32) {
+        const int j = pos(l);
+        const long long v = __double_as_longlong(vn[l]);
+        if (j >= k && j < ca && (v > bv || (v == bv && j < bi))) {
+          bv = v;
+          bi = j;
+        }
       }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int q = 1; q < nw; ++q)
-        if (red_v[q] > red_v[0] || (red_v[q] == red_v[0] && red_i[q] < red_i[0])) { red_v[0] = red_v[q]; red_i[0] = red_i[q]; }
-      cand_v0[crank] = red_v[0];
-      cand_i0[crank] = red_i[0];
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        cand_v0[crank] = __longlong_as_double(bv);
+        cand_i0[crank] = bi;
+      }
     }
     cluster.sync();
     if (warp == 0) {  // one lane per CTA reads its candidate (remote loads in parallel)
-      double v = lane < C ? cand_v0[lane] : -1.0;
+      long long v = lane < C ? __double_as_longlong(cand_v0[lane]) : -1;
       int idx = lane < C ? cand_i0[lane] : 0x7fffffff;
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
       }
       if (lane == 0) {
+        const double vd = __longlong_as_double(v);
         s_piv = idx;
-        s_vp = v;
-        if (k == 0) s_stop2 = v * (0.01 * zero_rel * zero_rel / (double)ca);
-        s_stop = !(v > s_stop2);
+        s_vp = vd;
+        if (k == 0) s_stop2 = vd * (0.01 * zero_rel * zero_rel / (double)ca);
+        s_stop = !(v >= 0 && v > __double_as_longlong(s_stop2));
       }
     }
     __syncthreads();
@@ -369,17 +423,20 @@ __global__ void __launch_bounds__(QC_THREADS)
         for (int o = 4; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
         const double alpha = ak[k];
         if (lane == 0) {
-        if (sig == 0.0) {
-          s_tau = 0.0;
-          s_beta = alpha;
-          s_scale = 1.0;
-        } else {
-          const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
-          s_tau = (beta - alpha) / beta;
-          s_beta = beta;
-          s_scale = 1.0 / (alpha - beta);
-        }
-        tau[k] = s_tau;
+          if (sig == 0.0) {
+            s_tau = 0.0;
+            s_beta = alpha;
+            s_scale = 1.0;
+          } else {
+            // |beta| >= |alpha - beta| / 2 > 0; reciprocals by Newton's
+            // iteration from an FP32 estimate (recip_split), correct to the
+            // last bits, at a fraction of an FP64 division's instructions
+            const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+            s_tau = (beta - alpha) * recip_signed(beta);
+            s_beta = beta;
+            s_scale = recip_signed(alpha - beta);
+          }
+          tau[k] = s_tau;
         }
       }
       __syncthreads();
@@ -803,49 +860,6 @@ struct BjPair {   // per pair of a sub-round, in shared memory
   int i, j;       // column indices within the two blocks (-1: no pair)
   int rot;        // 1 rotate, 2 rotate and recompute both norms from the data
 };
-
-// Exponent and FP32 mantissa of a double, by integer operations only (an
-// FP64 instruction costs 64 cycles of its sub-partition's FP64 unit here):
-// x = m 2^e with |m| in [1, 2) (mantissa truncated to 23 bits); zero and
-// subnormals give m = 0.
-struct Split {
-  float m;
-  int e;
-};
-__device__ __forceinline__ Split split_f64(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const int be = (int)((hi >> 20) & 0x7ffu);
-  Split r;
-  if (be == 0) {
-    r.m = 0.0f;
-    r.e = 0;
-    return r;
-  }
-  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  r.m = __uint_as_float((hi & 0x80000000u) | (127u << 23) | mant);
-  r.e = be - 1023;
-  return r;
-}
-
-// the double of an FP32 number times 2^k (integer operations; f normal or
-// zero, result in the normal range)
-__device__ __forceinline__ double f64_of(float f, int k = 0) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  if (ex == 0) return 0.0;
-  const unsigned hi = (u & 0x80000000u) | ((ex + 896u + (unsigned)k) << 20) | ((u & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)((u & 0x7u) << 29));
-}
-
-// 1/x for x > 0 in the normal range: FP32 estimate of the mantissa's
-// reciprocal, then two Newton steps e <- e (2 - x e) in FP64
-__device__ __forceinline__ double recip_split(double x) {
-  const Split s = split_f64(x);
-  double e = f64_of(__frcp_rn(s.m), -s.e);
-  e = e * fma(-x, e, 2.0);
-  e = e * fma(-x, e, 2.0);
-  return e;
-}
 
 // phase 2 for one pair: norms a, b and scales d1, d2 in, updated in place.
 // The tests and the angle use exponents and FP32 mantissas; FP64 is spent
