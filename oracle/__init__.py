@@ -12,6 +12,12 @@ this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
 * ``oracle.ed`` -- exact diagonalisation of open clusters straight from a bond
   list, and the free-fermion energies of XX chains.  It shares nothing with
   ``oracle.idmrg`` and pins it.
+* ``oracle.observables`` -- the uniform MPS of Eq. mps2 built from a
+  converged state, its transfer matrix (dense, ``numpy.linalg.eig``), bond
+  strengths, spin-spin correlations, Delta+- (Eqs. diff1, diff2) and the
+  correlation length.
+* ``oracle.extrapolate`` -- the m scan of Sec. 5: runs to convergence and the
+  quadratic eps -> 0 fit.
 * ``oracle.rng`` -- the counter-based generator (SplitMix64) of the Lanczos
   start vectors for n = 1, 2.
 
