@@ -376,6 +376,27 @@ def timed_run(pkg, mpo, m: int, prec: str, steps: int, warmup: int, dev, flush, 
     return res
 
 
+def observables_leg(ctx, ell: int) -> dict:
+    """Uniform-MPS observables of the final state (Eq. mps2), outside the timed
+    steps: the l nearest-neighbour bond strengths (unit embedding, both fixed
+    points by power iteration, environments, walks) and the transfer spectrum
+    (correlation length), each timed on the wall clock around its API call."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        v = ctx.spin_dot([(i, i + 1) for i in range(ell)])
+        t1w = time.perf_counter()
+        t1, t2, xi, it, conv = ctx.transfer_spectrum()
+        t2w = time.perf_counter()
+    except Exception as e:  # reported, not fatal: the step measurement stands
+        return {"error": str(e)}
+    return {"bond_strengths_ms": (t1w - t0) * 1e3, "spectrum_ms": (t2w - t1w) * 1e3,
+            "bond_strength_mean": float(sum(v) / len(v)), "bond_strength_min": float(min(v)),
+            "bond_strength_max": float(max(v)), "t1": t1, "t2_abs": t2, "xi_unit_cells": xi,
+            "spectrum_iterations": it, "spectrum_converged": conv}
+
+
 def max_de_per_site(ra, rb):
     """Largest |e_a - e_b| / (2n+2) over the superblocks of steps with equal n."""
     worst = 0.0
@@ -403,6 +424,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-observables", action="store_true")
     args = ap.parse_args()
     if args.m is None:
         args.m = 256 if args.workload == WORKLOAD else 1024
@@ -479,6 +501,8 @@ def main():
         "clocks": run["clocks"],
         "energy_per_site_last": float(last["energy"][0] / (2 * last["n"] + 2)),
     }
+    if not args.no_observables:
+        line["observables"] = observables_leg(ctx, ell)
     if cmp is not None:
         line["fp64"] = {"value": job_value(world, args.steps, t_dev64), "unit": "unit-cell steps/s",
                         "ms_per_step": t_dev64 * 1e3 / args.steps,

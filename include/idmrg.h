@@ -231,6 +231,41 @@ idmrg_status idmrg_truncation_error(const idmrg_ctx *ctx, double *eps);
  * Sec. 5 (e_g against eps for several m, extrapolated to eps -> 0). */
 idmrg_status idmrg_run(idmrg_ctx *ctx, int max_steps, double de_tol, double *e_g, double *eps, int *steps);
 
+/* ---- Uniform-MPS observables (Sec. 3, Eq. mps2; the bond strengths,
+ * spin-spin correlations and correlation length of the paper's benchmarks).
+ * After iteration n the unit of Eq. mps2 is V^(n)_1^T u~^(n)_2 V^(n)_2^T ...
+ * u~^(n)_1, u~^(n)_{i+1} = (lam^(n-1)_{i+1})^-1 u^(n)_{i+1} lam^(n)_{i+1} (the
+ * scaled tensors of Eq. wfprediction, same zero rule), repeated along the
+ * infinite chain.  Expectation values use the dominant left and right
+ * eigenvectors of the unit's transfer map (power iteration to 1e-12), since
+ * the unit is only approximately right-normalised before convergence.  Both
+ * calls need two completed iterations (ESTATE before, or during a step); the
+ * unit and its fixed points are kept until the next step or load.  Lattice
+ * sites are numbered along the chain: site x carries MPO site x mod l. */
+
+/* out[k] = sum_t coef[t] < (op_a[t])_{site_i[k]} (op_b[t])_{site_j[k]} > for
+ * k < npairs.  op_a, op_b: nterms host matrices d x d, row-major,
+ * op[s * d + t] = <s| O |t> in the MPO's physical basis; coef: nterms host
+ * values; site_i, site_j, out: npairs host values with
+ * 0 <= site_i[k] < site_j[k] <= site_i[k] + 2^20.  For spin 1/2,
+ * <s_i . s_j> is the three terms (Sz, Sz, 1), (S+, S-, 1/2), (S-, S+, 1/2).
+ * EINVAL on bad arguments, ENOCONV if the fixed points do not converge. */
+idmrg_status idmrg_correlation(idmrg_ctx *ctx, int nterms, const double *op_a, const double *op_b,
+                               const double *coef, int npairs, const int64_t *site_i, const int64_t *site_j,
+                               double *out);
+
+/* Two largest eigenvalue moduli of the unit's transfer map, t1 (its dominant,
+ * positive eigenvalue) and |t2|, and the correlation length
+ * xi = -1 / ln(|t2| / t1) in unit cells (0 when |t2| = 0).  The map keeps
+ * the U(1) charge difference of an environment's entries; |t2| is the largest
+ * over the sectors of charge difference 0 (deflated of the fixed point), one
+ * and two steps of the smallest difference present at bond 0, each from a
+ * subspace iteration with two vectors stopped when its estimate changes by at
+ * most tol (relative) three times in a row, or after maxit iterations
+ * (ENOCONV, estimate written).  Each output pointer may be NULL. */
+idmrg_status idmrg_transfer_spectrum(idmrg_ctx *ctx, double tol, int maxit, double *t1, double *t2_abs,
+                                     double *xi, int *iters);
+
 /* Step 5': latest e_g = (e^(n)_1 - e^(n-l)_1) / 2l with (n+1) mod l == 0
  * (e^(-1)_1 = 0) and the n it belongs to; ESTATE if there is none yet. */
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *ctx, double *e_g, int *n_of_estimate);

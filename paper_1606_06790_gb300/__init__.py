@@ -32,6 +32,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
     "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_save", "idmrg_load",
+    "idmrg_correlation", "idmrg_transfer_spectrum",
 ]
 
 KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
@@ -120,6 +121,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_load": (i, [vp, C.c_char_p]),
         "idmrg_svd_stats": (i, [vp, P(i), P(i), P(i), P(i), P(d)]),
         "idmrg_set_svd_path": (i, [vp, i]),
+        "idmrg_correlation": (i, [vp, i, P(d), P(d), P(d), i, P(C.c_int64), P(C.c_int64), P(d)]),
+        "idmrg_transfer_spectrum": (i, [vp, d, i, P(d), P(d), P(d), P(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -132,6 +135,27 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
 
 def _dptr(a: np.ndarray, ct):
     return a.ctypes.data_as(C.POINTER(ct))
+
+
+def spin_half_dot_terms(phys_charge):
+    """The terms of s_i . s_j = Sz Sz + (S+ S- + S- S+) / 2 for a spin-1/2 basis
+    whose states carry 2 Sz = phys_charge (one +1, one -1)."""
+    qp = np.asarray(phys_charge).ravel()
+    if sorted(qp.tolist()) != [-1, 1]:
+        raise ValueError("spin 1/2 needs local charges {+1, -1}")
+    up, dn = int(np.argmax(qp)), int(np.argmin(qp))
+    sz = np.diag(qp.astype(np.float64) / 2.0)
+    sp = np.zeros((2, 2))
+    sp[up, dn] = 1.0
+    return [(sz, sz, 1.0), (sp, sp.T.copy(), 0.5), (sp.T.copy(), sp, 0.5)]
+
+
+def delta_pm(values):
+    """Eqs. diff1, diff2 over bond strengths that translational symmetry makes
+    equal: (average, max - average, min - average)."""
+    v = np.asarray(values, dtype=np.float64)
+    avg = float(v.sum() / len(v))
+    return avg, float(v.max()) - avg, float(v.min()) - avg
 
 
 class Context:
@@ -306,6 +330,35 @@ class Context:
         e = C.c_double()
         self._check(self.lib.idmrg_truncation_error(self.h, C.byref(e)), "truncation_error")
         return e.value
+
+    # ---- uniform-MPS observables (Eq. mps2)
+    def correlation(self, terms, pairs) -> np.ndarray:
+        """sum_t coef_t <(A_t)_i (B_t)_j> for each (i, j) in pairs (lattice
+        sites, i < j); terms is a list of (A, B, coef) with d x d operators
+        <s|O|t> in the MPO's physical basis."""
+        d = self.d
+        opa = np.ascontiguousarray(np.array([np.asarray(t[0], dtype=np.float64).reshape(d, d) for t in terms]))
+        opb = np.ascontiguousarray(np.array([np.asarray(t[1], dtype=np.float64).reshape(d, d) for t in terms]))
+        coef = np.ascontiguousarray(np.array([float(t[2]) for t in terms]))
+        pr = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+        si = np.ascontiguousarray(pr[:, 0])
+        sj = np.ascontiguousarray(pr[:, 1])
+        out = np.zeros(len(pr))
+        self._check(self.lib.idmrg_correlation(self.h, len(terms), _dptr(opa, C.c_double), _dptr(opb, C.c_double),
+                                               _dptr(coef, C.c_double), len(pr), _dptr(si, C.c_int64),
+                                               _dptr(sj, C.c_int64), _dptr(out, C.c_double)), "correlation")
+        return out
+
+    def spin_dot(self, pairs) -> np.ndarray:
+        """<s_i . s_j> for spin 1/2 (bond strengths, spin-spin correlations)."""
+        return self.correlation(spin_half_dot_terms(self._qp), pairs)
+
+    def transfer_spectrum(self, tol: float = 1e-10, maxit: int = 2000):
+        """(t1, |t2|, xi in unit cells, iterations, converged) of the unit's transfer map."""
+        t1, t2, xi, it = C.c_double(), C.c_double(), C.c_double(), C.c_int()
+        s = self._check(self.lib.idmrg_transfer_spectrum(self.h, float(tol), int(maxit), C.byref(t1), C.byref(t2),
+                                                         C.byref(xi), C.byref(it)), "transfer_spectrum", ok=(0, 4))
+        return t1.value, t2.value, xi.value, it.value, s == 0
 
     def _report(self):
         P = self.P

@@ -316,4 +316,22 @@ cudaError_t launch_wstage_oz(const WTaskP *tasks, int ntasks, int max_rows, cons
 cudaError_t launch_oz_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
                            const int *active, int *err, cudaStream_t st);
 
+// Uniform-MPS observables (Eq. mps2), see kernels_obs.cu.  An embed task
+// writes dst[x][y] = src(x, y) * scal[cs + y] / scal[rs + x] for x < rows,
+// y < cols, src(x, y) = src[x * src_ld + y] (trans: src[y * src_ld + x]);
+// rs / cs < 0: no scaling; a row scale at or below thr zeroes the row.
+struct EmbedTask {
+  const double *src;
+  double *dst;
+  int rows, cols, src_ld, dst_ld;
+  int trans, rs, cs, pad;
+  double thr;
+};
+cudaError_t launch_obs_embed(const EmbedTask *tasks, int ntasks, int max_rows, const double *scal, cudaStream_t st);
+cudaError_t launch_obs_dot(const double *x, const double *y, int64_t n, double coef, double *out, int accumulate,
+                           cudaStream_t st);
+cudaError_t launch_obs_axpby(const double *x, double *y, int64_t n, double a, double b, cudaStream_t st);
+cudaError_t launch_obs_fill(double *x, int D, int mode, double value, uint64_t seed, cudaStream_t st);
+cudaError_t launch_obs_mask(double *x, int D, const int *q, int delta, cudaStream_t st);
+
 }  // namespace idmrg

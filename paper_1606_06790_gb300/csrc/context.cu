@@ -110,6 +110,56 @@ struct GemmTune {
   double work = -1.0;
 };
 
+// Uniform MPS of Eq. mps2 (observables): the unit's l site tensors A_k
+// (d x D_k x D_k+1, dense), the charge blocks they are non-zero on, the
+// transfer-map task lists, the fixed points and the environments l_k, r_k.
+struct ObsBlock {
+  int s, rb, cb;  // physical state, block of bond k, block of bond k+1
+};
+struct ObsList {
+  int tile0 = 0, ntile = 0;
+};
+// task lists concatenated into one upload (indices rebased on append)
+struct ObsArena {
+  GemmList G;
+  DevBuf dtasks, dsegs, dtiles;
+  void clear() { G.clear(); }
+  ObsList add(const GemmList &L) {
+    ObsList o;
+    const int t0 = (int)G.tasks.size(), s0 = (int)G.segs.size();
+    o.tile0 = (int)G.tiles.size();
+    for (GemmTask t : L.tasks) {
+      t.seg0 += s0;
+      G.tasks.push_back(t);
+    }
+    G.segs.insert(G.segs.end(), L.segs.begin(), L.segs.end());
+    for (GemmTile x : L.tiles) {
+      x.task += t0;
+      G.tiles.push_back(x);
+    }
+    o.ntile = (int)L.tiles.size();
+    G.flops += L.flops;
+    return o;
+  }
+};
+struct ObsState {
+  bool valid = false;   // unit embedded for the current iteration
+  bool fixed = false;   // fixed points and environments computed
+  int s0 = 0;           // lattice site carried by A_0
+  std::vector<int> D;   // bond dimensions D_0 .. D_l (D_l = D_0)
+  std::vector<std::vector<std::pair<int, int>>> bb;  // per bond: blocks (offset, dim)
+  std::vector<std::vector<ObsBlock>> blk;            // per site: non-zero blocks
+  std::vector<std::vector<int>> rb_of, cb_of;        // per site: [s][cb] -> rb, [s][rb] -> cb (or -1)
+  std::vector<int64_t> aoff, eoff;                   // site tensors; environments per bond 0..l
+  int64_t ysize = 0, xsize = 0;                      // largest d D_k D_k+1 and D_k^2
+  double t1 = 0.0, t1r = 0.0, scale = 1.0;           // dominant eigenvalue (left, right), t1^(-1/l)
+  int it_left = 0, it_right = 0;
+  std::vector<std::pair<ObsList, ObsList>> unit_l, unit_r;
+  ObsArena unit, env, walk;
+  std::vector<int> q0;  // charge of every state of bond 0
+  DevBuf A, Y, envl, envr, X[7], res, tab, emb, scal, dq0;
+};
+
 struct idmrg_ctx {
   // problem
   int ell = 0, d = 0, P = 0;
@@ -222,6 +272,7 @@ struct idmrg_ctx {
   double svd_mean_sweeps = 0.0;
 
   std::vector<int> hmask;
+  ObsState obs;
   uint64_t mixed_matvecs = 0, fp64_matvecs = 0;
   int *pin_act = nullptr;  // pinned: active flags of two Lanczos iterations
   cudaEvent_t ev_act[2] = {nullptr, nullptr};
@@ -2373,6 +2424,7 @@ idmrg_status advance(idmrg_ctx *c) {
   for (int q = 0; q < P; ++q)
     if (c->stage[q] != ST_UPDATED) return c->fail(IDMRG_ESTATE, "advance: superblock %d is not updated", q);
   CK(cudaStreamSynchronize(c->st));
+  c->obs.valid = c->obs.fixed = false;
   for (int q = 0; q < P; ++q) {
     std::swap(c->envL[q], c->newL[q]);
     std::swap(c->envR[q], c->newR[q]);
@@ -2391,6 +2443,586 @@ idmrg_status advance(idmrg_ctx *c) {
   }
   c->n += 1;
   return plan_iteration(c);
+}
+
+// ------------------------------------------------------------------------
+// Uniform-MPS observables (Sec. 3, Eq. mps2)
+// ------------------------------------------------------------------------
+// The unit after iteration n is V^(n)_1^T u~^(n)_2 V^(n)_2^T u~^(n)_3 ... with
+// u~^(n)_{i+1} = (lam^(n-1)_{i+1})^-1 u^(n)_{i+1} lam^(n)_{i+1}, the tensors
+// Eq. wfprediction scales for iteration n + 1 (same zero rule); A_2p = V_p^T
+// carries lattice site f(2p + n + 1), A_2p+1 = u~_p+1 the next one.  The unit
+// is not exactly right-normalised, so expectation values use the dominant
+// left and right eigenvectors of its transfer map.  Environments are D x D
+// dense; the site tensors are multiplied block by block (charge blocks).
+enum ObsBuf { OB_A = 0, OB_Y = 1, OB_EL = 2, OB_ER = 3, OB_X0 = 4 };  // X_i at OB_X0 + i
+
+double *obs_x(idmrg_ctx *c, int i) { return (double *)c->obs.X[i].p; }
+
+// out = alpha sum_{s,t} O[s][t] A_k[s]^T in A_k[t]   (O null: identity)
+void obs_left_map(const ObsState &S, int d, int k, const double *O, double alpha, int in_buf, int64_t in_off,
+                  int out_buf, int64_t out_off, GemmList &g1, GemmList &g2) {
+  const int Dk = S.D[k], Dk1 = S.D[k + 1];
+  const int64_t plane = (int64_t)Dk * Dk1;
+  const auto &B0 = S.bb[k], &B1 = S.bb[k + 1];
+  const int nb1 = (int)B1.size();
+  auto o_at = [&](int s, int t) { return O ? O[s * d + t] : (s == t ? 1.0 : 0.0); };
+  g1.clear();
+  g2.clear();
+  // Y[t] = in A_k[t], every column block written (zero where A has no block)
+  for (int t = 0; t < d; ++t) {
+    bool used = false;
+    for (int s = 0; s < d; ++s) used = used || o_at(s, t) != 0.0;
+    if (!used) continue;
+    for (int cb = 0; cb < nb1; ++cb) {
+      g1.task(0, OB_Y, t * plane + B1[cb].first, Dk, B1[cb].second, Dk1);
+      const int rb = S.rb_of[k][t * nb1 + cb];
+      if (rb >= 0)
+        g1.seg(in_buf, in_off + B0[rb].first, Dk, OB_A, S.aoff[k] + t * plane + (int64_t)B0[rb].first * Dk1 +
+               B1[cb].first, Dk1, B0[rb].second, 0);
+    }
+  }
+  // out[cb rows] = sum_{s,t} alpha O[s][t] A_k[s][rb, cb]^T Y[t][rb rows]
+  for (int cb = 0; cb < nb1; ++cb) {
+    g2.task(0, out_buf, out_off + (int64_t)B1[cb].first * Dk1, B1[cb].second, Dk1, Dk1);
+    for (int s = 0; s < d; ++s) {
+      const int rb = S.rb_of[k][s * nb1 + cb];
+      if (rb < 0) continue;
+      for (int t = 0; t < d; ++t) {
+        const double o = o_at(s, t);
+        if (o == 0.0) continue;
+        g2.seg(OB_A, S.aoff[k] + s * plane + (int64_t)B0[rb].first * Dk1 + B1[cb].first, Dk1, OB_Y,
+               t * plane + (int64_t)B0[rb].first * Dk1, Dk1, B0[rb].second, 1, alpha * o);
+      }
+    }
+  }
+  g1.finish(32, 32);
+  g2.finish(32, 32);
+}
+
+// out = alpha sum_t A_k[t] in A_k[t]^T
+void obs_right_map(const ObsState &S, int d, int k, double alpha, int in_buf, int64_t in_off, int out_buf,
+                   int64_t out_off, GemmList &g1, GemmList &g2) {
+  const int Dk = S.D[k], Dk1 = S.D[k + 1];
+  const int64_t plane = (int64_t)Dk * Dk1;
+  const auto &B0 = S.bb[k], &B1 = S.bb[k + 1];
+  const int nb0 = (int)B0.size();
+  g1.clear();
+  g2.clear();
+  // Y[t] = A_k[t] in, every row block written
+  for (int t = 0; t < d; ++t)
+    for (int rb = 0; rb < nb0; ++rb) {
+      g1.task(0, OB_Y, t * plane + (int64_t)B0[rb].first * Dk1, B0[rb].second, Dk1, Dk1);
+      const int cb = S.cb_of[k][t * nb0 + rb];
+      if (cb >= 0)
+        g1.seg(OB_A, S.aoff[k] + t * plane + (int64_t)B0[rb].first * Dk1 + B1[cb].first, Dk1, in_buf,
+               in_off + (int64_t)B1[cb].first * Dk1, Dk1, B1[cb].second, 0);
+    }
+  // out[:, rb] = sum_t alpha Y[t][:, cb] A_k[t][rb, cb]^T
+  for (int rb = 0; rb < nb0; ++rb) {
+    g2.task(0, out_buf, out_off + B0[rb].first, Dk, B0[rb].second, Dk);
+    for (int t = 0; t < d; ++t) {
+      const int cb = S.cb_of[k][t * nb0 + rb];
+      if (cb < 0) continue;
+      g2.seg(OB_Y, t * plane + B1[cb].first, Dk1, OB_A,
+             S.aoff[k] + t * plane + (int64_t)B0[rb].first * Dk1 + B1[cb].first, Dk1, B1[cb].second, 2, alpha);
+    }
+  }
+  g1.finish(32, 32);
+  g2.finish(32, 32);
+}
+
+idmrg_status obs_upload(idmrg_ctx *c, ObsArena &a) {
+  NOMEM(c->upload(a.dtasks, a.G.tasks) && c->upload(a.dsegs, a.G.segs) && c->upload(a.dtiles, a.G.tiles));
+  return IDMRG_OK;
+}
+
+idmrg_status obs_run(idmrg_ctx *c, ObsArena &a, const ObsList &L) {
+  CK(launch_gemm_f64((const GemmTile *)a.dtiles.p + L.tile0, L.ntile, (const GemmTask *)a.dtasks.p,
+                     (const GemmSeg *)a.dsegs.p, (double *const *)c->obs.tab.p, nullptr, c->st, GEMM_32x32));
+  c->launches += 1;
+  return IDMRG_OK;
+}
+
+idmrg_status obs_read(idmrg_ctx *c, double *host, int n) {
+  CK(c->d2h_copy(host, c->obs.res.p, sizeof(double) * n));
+  CK(cudaStreamSynchronize(c->st));
+  return IDMRG_OK;
+}
+
+idmrg_status obs_dot(idmrg_ctx *c, const double *x, const double *y, int64_t n, double coef, int slot, int acc) {
+  CK(launch_obs_dot(x, y, n, coef, (double *)c->obs.res.p + slot, acc, c->st));
+  c->launches += 1;
+  return IDMRG_OK;
+}
+
+idmrg_status obs_axpby(idmrg_ctx *c, const double *x, double *y, int64_t n, double a, double b) {
+  CK(launch_obs_axpby(x, y, n, a, b, c->st));
+  c->launches += 1;
+  return IDMRG_OK;
+}
+
+#define OBS_TRY(call)                  \
+  do {                                 \
+    const idmrg_status s_ = (call);    \
+    if (s_ != IDMRG_OK) return s_;     \
+  } while (0)
+
+// Embeds the unit of the last completed iteration and builds its block tables
+// and the unit-map task lists.
+idmrg_status obs_build(idmrg_ctx *c) {
+  ObsState &S = c->obs;
+  if (S.valid) return IDMRG_OK;
+  const int P = c->P, d = c->d, ell = c->ell;
+  if (c->n < 3) return c->fail(IDMRG_ESTATE, "observables need two completed iterations");
+  for (int q = 0; q < P; ++q)
+    if (!c->prev[q].valid || !c->prev2[q].valid)
+      return c->fail(IDMRG_ESTATE, "observables need two completed iterations");
+  S.fixed = false;
+  S.s0 = (c->n - 1 + 1) % ell;
+  S.D.assign(ell + 1, 0);
+  S.bb.assign(ell + 1, {});
+  S.blk.assign(ell, {});
+  for (int p = 0; p < P; ++p) {
+    const TruncRec &A = c->prev[p], &B = c->prev[(p + 1) % P];
+    if (A.rightB.D != B.leftB.D || A.rightB.dim != B.leftB.dim)
+      return c->fail(IDMRG_ESTATE, "observables: bases of superblocks %d and %d do not meet", p, (p + 1) % P);
+    if ((int)c->prev2[(p + 1) % P].lam.size() != B.leftB.D)
+      return c->fail(IDMRG_ESTATE, "observables: lambda^(n-1) of superblock %d has the wrong length", (p + 1) % P);
+    for (const SecInfo &s : A.sec) S.bb[2 * p].push_back({s.lam_off, s.k});
+    for (int j = 0; j < (int)A.rightB.dim.size(); ++j) S.bb[2 * p + 1].push_back({A.rightB.off[j], A.rightB.dim[j]});
+    S.D[2 * p] = (int)A.lam.size();
+    S.D[2 * p + 1] = A.rightB.D;
+    for (int a = 0; a < (int)A.sec.size(); ++a)
+      for (const auto &g : A.sec[a].cg) S.blk[2 * p].push_back({g[0], a, g[1]});
+    for (int g = 0; g < (int)B.sec.size(); ++g)
+      for (const auto &r : B.sec[g].rg) S.blk[2 * p + 1].push_back({r[1], r[0], g});
+  }
+  S.D[ell] = S.D[0];
+  S.bb[ell] = S.bb[0];
+  S.q0.clear();
+  for (const SecInfo &s : c->prev[0].sec) S.q0.insert(S.q0.end(), s.k, s.Q);
+  NOMEM(c->upload(S.dq0, S.q0));
+  S.aoff.assign(ell + 1, 0);
+  S.eoff.assign(ell + 2, 0);
+  S.ysize = S.xsize = 0;
+  S.rb_of.assign(ell, {});
+  S.cb_of.assign(ell, {});
+  for (int k = 0; k < ell; ++k) {
+    const int64_t plane = (int64_t)S.D[k] * S.D[k + 1];
+    S.aoff[k + 1] = S.aoff[k] + d * plane;
+    S.ysize = std::max<int64_t>(S.ysize, d * plane);
+    const int nb0 = (int)S.bb[k].size(), nb1 = (int)S.bb[k + 1].size();
+    S.rb_of[k].assign((size_t)d * nb1, -1);
+    S.cb_of[k].assign((size_t)d * nb0, -1);
+    for (const ObsBlock &b : S.blk[k]) {
+      S.rb_of[k][b.s * nb1 + b.cb] = b.rb;
+      S.cb_of[k][b.s * nb0 + b.rb] = b.cb;
+    }
+  }
+  for (int k = 0; k <= ell; ++k) {
+    S.eoff[k + 1] = S.eoff[k] + (int64_t)S.D[k] * S.D[k];
+    S.xsize = std::max<int64_t>(S.xsize, (int64_t)S.D[k] * S.D[k]);
+  }
+  NOMEM(c->ensure(S.A, 8 * std::max<int64_t>(S.aoff[ell], 1)) && c->ensure(S.Y, 8 * std::max<int64_t>(S.ysize, 1)) &&
+        c->ensure(S.envl, 8 * S.eoff[ell + 1]) && c->ensure(S.envr, 8 * S.eoff[ell + 1]) &&
+        c->ensure(S.res, 8 * 64));
+  for (auto &x : S.X) NOMEM(c->ensure(x, 8 * S.xsize));
+  // pointer table of the GEMM lists (superblock 0, slots OB_*)
+  std::vector<double *> tab(NBUF, nullptr);
+  tab[OB_A] = (double *)S.A.p;
+  tab[OB_Y] = (double *)S.Y.p;
+  tab[OB_EL] = (double *)S.envl.p;
+  tab[OB_ER] = (double *)S.envr.p;
+  for (int i = 0; i < 7; ++i) tab[OB_X0 + i] = (double *)S.X[i].p;
+  NOMEM(c->upload(S.tab, tab));
+  // embed: V^T (transposed copy) and u~ (rows / lam'', columns * lam)
+  std::vector<double> scal;
+  std::vector<EmbedTask> et;
+  int max_rows = 0;
+  double *Abase = (double *)S.A.p;
+  for (int p = 0; p < P; ++p) {
+    const int q = (p + 1) % P;
+    const TruncRec &A = c->prev[p], &B = c->prev[q], &B2 = c->prev2[q];
+    {
+      const int k = 2 * p, D1 = S.D[k + 1];
+      const int64_t plane = (int64_t)S.D[k] * D1;
+      for (const SecInfo &s : A.sec)
+        for (const auto &g : s.cg) {
+          EmbedTask t{};
+          t.src = (const double *)A.V.p + s.v_off + (int64_t)g[2] * s.k;
+          t.dst = Abase + S.aoff[k] + g[0] * plane + (int64_t)s.lam_off * D1 + A.rightB.off[g[1]];
+          t.rows = s.k;
+          t.cols = A.rightB.dim[g[1]];
+          t.src_ld = s.k;
+          t.dst_ld = D1;
+          t.trans = 1;
+          t.rs = t.cs = -1;
+          et.push_back(t);
+          max_rows = std::max(max_rows, t.rows);
+        }
+    }
+    {
+      const int k = 2 * p + 1, D1 = S.D[k + 1];
+      const int64_t plane = (int64_t)S.D[k] * D1;
+      const int lam_at = (int)scal.size();
+      scal.insert(scal.end(), B.lam.begin(), B.lam.end());
+      const int lam2_at = (int)scal.size();
+      scal.insert(scal.end(), B2.lam.begin(), B2.lam.end());
+      const double thr = c->o.lambda_zero_rel * (B2.lam_all.empty() ? 0.0 : B2.lam_all[0]);
+      for (const SecInfo &s : B.sec)
+        for (const auto &r : s.rg) {
+          EmbedTask t{};
+          t.src = (const double *)B.U.p + s.u_off + (int64_t)r[2] * s.k;
+          t.dst = Abase + S.aoff[k] + r[1] * plane + (int64_t)B.leftB.off[r[0]] * D1 + s.lam_off;
+          t.rows = B.leftB.dim[r[0]];
+          t.cols = s.k;
+          t.src_ld = s.k;
+          t.dst_ld = D1;
+          t.trans = 0;
+          t.rs = lam2_at + B.leftB.off[r[0]];
+          t.cs = lam_at + s.lam_off;
+          t.thr = thr;
+          et.push_back(t);
+          max_rows = std::max(max_rows, t.rows);
+        }
+    }
+  }
+  NOMEM(c->upload(S.emb, et) && c->upload(S.scal, scal));
+  CK(cudaMemsetAsync(S.A.p, 0, 8 * S.aoff[ell], c->st));
+  CK(launch_obs_embed((const EmbedTask *)S.emb.p, (int)et.size(), max_rows, (const double *)S.scal.p, c->st));
+  c->launches += 1;
+  // unit maps (alpha 1), ping-pong X0 <-> X1, ending in X0 (l is even)
+  S.unit.clear();
+  S.unit_l.clear();
+  S.unit_r.clear();
+  GemmList g1, g2;
+  for (int k = 0; k < ell; ++k) {
+    const int in = (k % 2 == 0) ? OB_X0 : OB_X0 + 1, out = (k % 2 == 0) ? OB_X0 + 1 : OB_X0;
+    obs_left_map(S, d, k, nullptr, 1.0, in, 0, out, 0, g1, g2);
+    S.unit_l.push_back({S.unit.add(g1), S.unit.add(g2)});
+  }
+  for (int i = 0; i < ell; ++i) {
+    const int k = ell - 1 - i;
+    const int in = (i % 2 == 0) ? OB_X0 : OB_X0 + 1, out = (i % 2 == 0) ? OB_X0 + 1 : OB_X0;
+    obs_right_map(S, d, k, 1.0, in, 0, out, 0, g1, g2);
+    S.unit_r.push_back({S.unit.add(g1), S.unit.add(g2)});
+  }
+  OBS_TRY(obs_upload(c, S.unit));
+  S.valid = true;
+  return IDMRG_OK;
+}
+
+idmrg_status obs_unit_map(idmrg_ctx *c, bool left) {
+  for (const auto &pr : left ? c->obs.unit_l : c->obs.unit_r) {
+    OBS_TRY(obs_run(c, c->obs.unit, pr.first));
+    OBS_TRY(obs_run(c, c->obs.unit, pr.second));
+  }
+  return IDMRG_OK;
+}
+
+// Two-vector subspace iteration of the unit map on charge-difference sector
+// `delta` of bond 0 (the map keeps the charge difference of an environment's
+// entries), Rayleigh-Ritz on the 2 x 2 projection H = X^T T X.
+//  mode 0 (fixed point): the unscaled left or right map on sector 0 until the
+//    dominant Ritz pair (theta real, largest) has |T x - theta x| <= tol theta
+//    |x|; x (unit Frobenius norm) is written to dst, theta to *lam.  Its error
+//    falls as |t3 / t1| per iteration, not |t2 / t1| as in a power iteration.
+//  mode 1 (spectrum): the left map scaled by 1/t1, on sector 0 also deflated
+//    of the fixed point (T(x)/t1 - l_0 (r_0|x), (l_0|r_0) = 1), until the
+//    largest Ritz modulus changes by at most tol (relative) three times in a
+//    row; it is written to *lam (a complex pair gives sqrt(det H)).
+idmrg_status obs_subspace(idmrg_ctx *c, bool left, int delta, int mode, double tol, int maxit, double *lam,
+                          int *iters, double *dst) {
+  ObsState &S = c->obs;
+  const int ell = c->ell, D0 = S.D[0];
+  const int64_t n = (int64_t)D0 * D0;
+  const double *l0 = (const double *)S.envl.p, *r0 = (const double *)S.envr.p + S.eoff[ell];
+  double *x0 = obs_x(c, 0), *xr = obs_x(c, 2), *v[2] = {obs_x(c, 3), obs_x(c, 4)}, *y[2] = {obs_x(c, 5), obs_x(c, 6)};
+  double h[4];
+  const double tiny = 1e-280;
+  const bool deflated = mode == 1 && delta == 0;
+  for (int a = 0; a < 2; ++a) {
+    CK(launch_obs_fill(v[a], D0, 1, 0.0, c->o.seed * 2654435761ull + 7919ull * (a + 1) + 104729ull * delta +
+                       15485863ull * (left ? 1 : 2) * (mode + 1), c->st));
+    CK(launch_obs_mask(v[a], D0, (const int *)S.dq0.p, delta, c->st));
+    c->launches += 2;
+  }
+  auto deflate = [&](double *w) -> idmrg_status {
+    if (!deflated) return IDMRG_OK;
+    OBS_TRY(obs_dot(c, r0, w, n, 1.0, 0, 0));
+    OBS_TRY(obs_read(c, h, 1));
+    return obs_axpby(c, l0, w, n, -h[0], 1.0);
+  };
+  // orthonormalise (w0, w1) into (v0, v1); a vanishing second direction
+  // becomes zero, a vanishing first one ends the iteration
+  auto orth = [&](double *w0, double *w1, bool *dead) -> idmrg_status {
+    OBS_TRY(obs_dot(c, w0, w0, n, 1.0, 0, 0));
+    OBS_TRY(obs_read(c, h, 1));
+    if (!(h[0] > tiny)) {
+      *dead = true;
+      return IDMRG_OK;
+    }
+    OBS_TRY(obs_axpby(c, w0, v[0], n, 1.0 / std::sqrt(h[0]), 0.0));
+    OBS_TRY(obs_dot(c, v[0], w1, n, 1.0, 0, 0));
+    OBS_TRY(obs_read(c, h, 1));
+    OBS_TRY(obs_axpby(c, v[0], w1, n, -h[0], 1.0));
+    OBS_TRY(obs_dot(c, w1, w1, n, 1.0, 0, 0));
+    OBS_TRY(obs_read(c, h, 1));
+    if (h[0] > tiny)
+      OBS_TRY(obs_axpby(c, w1, v[1], n, 1.0 / std::sqrt(h[0]), 0.0));
+    else
+      OBS_TRY(obs_axpby(c, w1, v[1], n, 0.0, 0.0));
+    return IDMRG_OK;
+  };
+  bool dead = false;
+  OBS_TRY(deflate(v[0]));
+  OBS_TRY(deflate(v[1]));
+  OBS_TRY(orth(v[0], v[1], &dead));
+  double last = -1.0;
+  int stable = 0;
+  bool done = false;
+  *lam = 0.0;
+  *iters = 0;
+  for (int it = 1; it <= maxit && !dead && !done; ++it) {
+    for (int a = 0; a < 2; ++a) {
+      CK(cudaMemcpyAsync(x0, v[a], 8 * n, cudaMemcpyDeviceToDevice, c->st));
+      OBS_TRY(obs_unit_map(c, left));
+      OBS_TRY(obs_axpby(c, x0, y[a], n, mode == 1 ? 1.0 / S.t1 : 1.0, 0.0));
+      OBS_TRY(deflate(y[a]));
+    }
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) OBS_TRY(obs_dot(c, v[a], y[b], n, 1.0, 2 * a + b, 0));
+    OBS_TRY(obs_read(c, h, 4));
+    // H = [[h0, h1], [h2, h3]] (H[a][b] = (v_a | T v_b))
+    const double tr = h[0] + h[3], det = h[0] * h[3] - h[1] * h[2];
+    const double disc = 0.25 * tr * tr - det;
+    if (!std::isfinite(tr) || !std::isfinite(det))
+      return c->fail(IDMRG_ENUMERIC, "observables: transfer map gave non-finite values");
+    *iters = it;
+    if (mode == 1) {
+      const double m = disc >= 0.0 ? std::max(std::fabs(0.5 * tr + std::sqrt(disc)), std::fabs(0.5 * tr - std::sqrt(disc)))
+                                   : std::sqrt(std::max(det, 0.0));
+      stable = (std::fabs(m - last) <= tol * std::max(m, tiny)) ? stable + 1 : 0;
+      last = m;
+      *lam = m;
+      done = stable >= 3;
+    } else if (disc >= 0.0) {
+      // dominant real Ritz pair: theta, y with H y = theta y; x = V y
+      const double th = 0.5 * tr + std::sqrt(disc);
+      double ya = h[1], yb = th - h[0];          // from the first row of (H - theta)
+      const double za = th - h[3], zb = h[2];    // from the second row
+      if (za * za + zb * zb > ya * ya + yb * yb) { ya = za; yb = zb; }
+      if (ya * ya + yb * yb > tiny && th > 0.0) {
+        // x = ya v0 + yb v1 (in xr), T x = ya y0 + yb y1 (in x0), residual in x0
+        OBS_TRY(obs_axpby(c, v[0], xr, n, ya, 0.0));
+        OBS_TRY(obs_axpby(c, v[1], xr, n, yb, 1.0));
+        OBS_TRY(obs_axpby(c, y[0], x0, n, ya, 0.0));
+        OBS_TRY(obs_axpby(c, y[1], x0, n, yb, 1.0));
+        OBS_TRY(obs_axpby(c, xr, x0, n, -th, 1.0));
+        OBS_TRY(obs_dot(c, x0, x0, n, 1.0, 0, 0));
+        OBS_TRY(obs_dot(c, xr, xr, n, 1.0, 1, 0));
+        OBS_TRY(obs_read(c, h, 2));
+        *lam = th;
+        if (h[1] > tiny && std::sqrt(h[0]) <= tol * th * std::sqrt(h[1])) {
+          double tracev[1];
+          // unit norm, sign fixed by the trace (the fixed point is positive semidefinite)
+          CK(launch_obs_fill(x0, D0, 0, 1.0, 0, c->st));
+          c->launches += 1;
+          OBS_TRY(obs_dot(c, x0, xr, n, 1.0, 0, 0));
+          OBS_TRY(obs_read(c, tracev, 1));
+          const double sg = tracev[0] < 0.0 ? -1.0 : 1.0;
+          OBS_TRY(obs_axpby(c, xr, dst, n, sg / std::sqrt(h[1]), 0.0));
+          done = true;
+        }
+      }
+    }
+    if (!done) OBS_TRY(orth(y[0], y[1], &dead));
+  }
+  if (mode == 1) {
+    if (dead) *lam = 0.0;
+    if (!dead && !done)
+      return c->fail(IDMRG_ENOCONV, "observables: subspace iteration (charge difference %d) did not converge in %d "
+                     "steps", delta, maxit);
+    return IDMRG_OK;
+  }
+  if (dead) return c->fail(IDMRG_ENUMERIC, "observables: the transfer map annihilated its start vectors");
+  if (!done)
+    return c->fail(IDMRG_ENOCONV, "observables: fixed point of the transfer map not converged in %d steps", maxit);
+  return IDMRG_OK;
+}
+
+// Fixed points l_0, r_0 with (l_0|r_0) = 1, the per-site factor t1^(-1/l)
+// and the environments l_k (k = 0..l-1), r_k (k = 1..l) of the scaled maps.
+idmrg_status obs_fixed(idmrg_ctx *c, double tol, int maxit) {
+  OBS_TRY(obs_build(c));
+  ObsState &S = c->obs;
+  if (S.fixed) return IDMRG_OK;
+  const int ell = c->ell, d = c->d, D0 = S.D[0];
+  const int64_t n = (int64_t)D0 * D0;
+  double *EL = (double *)S.envl.p, *ER = (double *)S.envr.p;
+  OBS_TRY(obs_subspace(c, true, 0, 0, tol, maxit, &S.t1, &S.it_left, EL));
+  OBS_TRY(obs_subspace(c, false, 0, 0, tol, maxit, &S.t1r, &S.it_right, ER + S.eoff[ell]));
+  double h[1];
+  OBS_TRY(obs_dot(c, EL, ER + S.eoff[ell], n, 1.0, 0, 0));
+  OBS_TRY(obs_read(c, h, 1));
+  if (!(std::fabs(h[0]) > 0.0) || !std::isfinite(h[0]))
+    return c->fail(IDMRG_ENUMERIC, "observables: fixed points with overlap %g", h[0]);
+  OBS_TRY(obs_axpby(c, ER + S.eoff[ell], ER + S.eoff[ell], n, 0.0, 1.0 / h[0]));
+  S.scale = std::pow(S.t1, -1.0 / ell);
+  S.env.clear();
+  GemmList g1, g2;
+  std::vector<std::pair<ObsList, ObsList>> le, re;
+  for (int k = 0; k + 1 < ell; ++k) {
+    obs_left_map(S, d, k, nullptr, S.scale, OB_EL, S.eoff[k], OB_EL, S.eoff[k + 1], g1, g2);
+    le.push_back({S.env.add(g1), S.env.add(g2)});
+  }
+  for (int k = ell - 1; k >= 1; --k) {
+    obs_right_map(S, d, k, S.scale, OB_ER, S.eoff[k + 1], OB_ER, S.eoff[k], g1, g2);
+    re.push_back({S.env.add(g1), S.env.add(g2)});
+  }
+  OBS_TRY(obs_upload(c, S.env));
+  for (const auto &pr : le) {
+    OBS_TRY(obs_run(c, S.env, pr.first));
+    OBS_TRY(obs_run(c, S.env, pr.second));
+  }
+  for (const auto &pr : re) {
+    OBS_TRY(obs_run(c, S.env, pr.first));
+    OBS_TRY(obs_run(c, S.env, pr.second));
+  }
+  S.fixed = true;
+  return IDMRG_OK;
+}
+
+constexpr double OBS_TOL = 1e-12;
+constexpr int OBS_MAXIT = 5000;
+
+// Two-point functions: one walk per distinct first site and term.  The left
+// environment at site i's bond takes O^a_i, then every later site an identity
+// step; at each requested j a branch applies O^b_j and closes with r_{j+1}.
+idmrg_status obs_correlation(idmrg_ctx *c, int nterms, const double *opa, const double *opb, const double *coef,
+                             int npairs, const int64_t *si, const int64_t *sj, double *out) {
+  OBS_TRY(obs_fixed(c, OBS_TOL, OBS_MAXIT));
+  ObsState &S = c->obs;
+  const int ell = c->ell, d = c->d;
+  std::map<int64_t, std::vector<int64_t>> groups;  // i -> sorted distinct j
+  for (int k = 0; k < npairs; ++k) groups[si[k]].push_back(sj[k]);
+  std::map<std::pair<int64_t, int64_t>, int> slot;  // (i, j) -> result slot
+  for (auto &g : groups) {
+    std::sort(g.second.begin(), g.second.end());
+    g.second.erase(std::unique(g.second.begin(), g.second.end()), g.second.end());
+    for (int64_t j : g.second) slot.emplace(std::make_pair(g.first, j), (int)slot.size());
+  }
+  NOMEM(c->ensure(S.res, 8 * std::max<size_t>(slot.size(), 64)));
+  // operations: a map (two lists) or a closing dot
+  struct Op {
+    int kind;  // 0 map, 1 dot
+    ObsList a, b;
+    int x_buf, slot;
+    int64_t r_off, n;
+    double coef;
+  };
+  std::vector<Op> ops;
+  S.walk.clear();
+  GemmList g1, g2;
+  std::map<std::tuple<int, int, int>, std::pair<ObsList, ObsList>> idmaps;  // (site, in, out)
+  auto unit_pos = [&](int64_t x) { return (int)(((x - S.s0) % ell + ell) % ell); };
+  auto push_map = [&](int k, const double *O, int in_buf, int64_t in_off, int out_buf) {
+    Op o{};
+    o.kind = 0;
+    if (!O && in_buf != OB_EL) {
+      auto key = std::make_tuple(k, in_buf, out_buf);
+      auto it = idmaps.find(key);
+      if (it == idmaps.end()) {
+        obs_left_map(S, d, k, nullptr, S.scale, in_buf, in_off, out_buf, 0, g1, g2);
+        it = idmaps.emplace(key, std::make_pair(S.walk.add(g1), S.walk.add(g2))).first;
+      }
+      o.a = it->second.first;
+      o.b = it->second.second;
+    } else {
+      obs_left_map(S, d, k, O, S.scale, in_buf, in_off, out_buf, 0, g1, g2);
+      o.a = S.walk.add(g1);
+      o.b = S.walk.add(g2);
+    }
+    ops.push_back(o);
+  };
+  const int XM = OB_X0 + 6;  // measurement branch
+  for (const auto &g : groups) {
+    const int64_t i = g.first;
+    const std::vector<int64_t> &js = g.second;
+    for (int t = 0; t < nterms; ++t) {
+      const double *Oa = opa + (size_t)t * d * d, *Ob = opb + (size_t)t * d * d;
+      int cur = OB_X0, other = OB_X0 + 1;
+      const int ki = unit_pos(i);
+      push_map(ki, Oa, OB_EL, S.eoff[ki], cur);
+      size_t next = 0;
+      for (int64_t x = i + 1; x <= js.back(); ++x) {
+        const int kx = unit_pos(x);
+        if (js[next] == x) {
+          push_map(kx, Ob, cur, 0, XM);
+          Op o{};
+          o.kind = 1;
+          o.x_buf = XM;
+          o.r_off = S.eoff[kx + 1];
+          o.n = (int64_t)S.D[kx + 1] * S.D[kx + 1];
+          o.slot = slot[{i, x}];
+          o.coef = coef[t];
+          ops.push_back(o);
+          ++next;
+        }
+        if (x < js.back()) {
+          push_map(kx, nullptr, cur, 0, other);
+          std::swap(cur, other);
+        }
+      }
+    }
+  }
+  OBS_TRY(obs_upload(c, S.walk));
+  CK(cudaMemsetAsync(S.res.p, 0, 8 * slot.size(), c->st));
+  const double *ER = (const double *)S.envr.p;
+  for (const Op &o : ops) {
+    if (o.kind == 0) {
+      OBS_TRY(obs_run(c, S.walk, o.a));
+      OBS_TRY(obs_run(c, S.walk, o.b));
+    } else {
+      OBS_TRY(obs_dot(c, obs_x(c, o.x_buf - OB_X0), ER + o.r_off, o.n, o.coef, o.slot, 1));
+    }
+  }
+  std::vector<double> h(slot.size());
+  if (!h.empty()) OBS_TRY(obs_read(c, h.data(), (int)h.size()));
+  for (int k = 0; k < npairs; ++k) out[k] = h[slot[{si[k], sj[k]}]];
+  return IDMRG_OK;
+}
+
+// |t2| / t1 of the unit's transfer map: finite-m truncation splits SU(2)
+// multiplets across the charge-difference sectors by small amounts, so each
+// sector (differences 0, 1 and 2 steps of the smallest one present at bond 0)
+// is iterated on its own (mode 1 of obs_subspace) and the largest modulus
+// over the sectors is taken.
+idmrg_status obs_spectrum(idmrg_ctx *c, double tol, int maxit, double *ratio, int *iters) {
+  OBS_TRY(obs_fixed(c, OBS_TOL, OBS_MAXIT));
+  const std::vector<int> &q = c->obs.q0;
+  std::vector<int> diffs;
+  for (int a : q)
+    for (int b : q)
+      if (a > b) diffs.push_back(a - b);
+  int step = 0;
+  for (int x : diffs) step = step == 0 ? x : std::min(step, x);
+  idmrg_status worst = IDMRG_OK;
+  *ratio = 0.0;
+  *iters = 0;
+  for (int k = 0; k < 3; ++k) {
+    const int delta = k * step;
+    if (k > 0 && (step == 0 || std::find(diffs.begin(), diffs.end(), delta) == diffs.end())) continue;
+    double r = 0.0;
+    int it = 0;
+    const idmrg_status s = obs_subspace(c, true, delta, 1, tol, maxit, &r, &it, nullptr);
+    if (s != IDMRG_OK && s != IDMRG_ENOCONV) return s;
+    if (s == IDMRG_ENOCONV) worst = s;
+    *ratio = std::max(*ratio, r);
+    *iters += it;
+  }
+  return worst;
 }
 
 }  // namespace
@@ -2661,6 +3293,14 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp, &c->goz_planes,
                     &c->goz_exps})
     rel(*b);
+  {
+    ObsState &S = c->obs;
+    for (DevBuf *b : {&S.A, &S.Y, &S.envl, &S.envr, &S.res, &S.tab, &S.emb, &S.scal, &S.dq0, &S.unit.dtasks, &S.unit.dsegs,
+                      &S.unit.dtiles, &S.env.dtasks, &S.env.dsegs, &S.env.dtiles, &S.walk.dtasks, &S.walk.dsegs,
+                      &S.walk.dtiles})
+      rel(*b);
+    for (auto &x : S.X) rel(x);
+  }
   for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (cudaStream_t x : c->side)
@@ -3024,6 +3664,7 @@ idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
   if (!c || !path) return IDMRG_EINVAL;
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "load: a step is in progress");
+  c->obs.valid = c->obs.fixed = false;
   CkFile F;
   F.f = fopen(path, "rb");
   if (!F.f) return c->fail(IDMRG_EINVAL, "load: cannot open %s", path);
@@ -3135,6 +3776,35 @@ idmrg_status idmrg_run(idmrg_ctx *c, int max_steps, double de_tol, double *e_g, 
   if (e_g) *e_g = c->eg_last;
   if (eps) idmrg_truncation_error(c, eps);
   return done ? IDMRG_OK : IDMRG_ENOCONV;
+}
+
+idmrg_status idmrg_correlation(idmrg_ctx *c, int nterms, const double *op_a, const double *op_b, const double *coef,
+                               int npairs, const int64_t *site_i, const int64_t *site_j, double *out) {
+  if (!c || nterms < 1 || nterms > 64 || npairs < 0 || !op_a || !op_b || !coef) return IDMRG_EINVAL;
+  if (npairs > 0 && (!site_i || !site_j || !out)) return IDMRG_EINVAL;
+  for (int k = 0; k < npairs; ++k)
+    if (site_i[k] < 0 || site_j[k] <= site_i[k] || site_j[k] - site_i[k] > (int64_t)1 << 20)
+      return c->fail(IDMRG_EINVAL, "correlation: pair %d needs 0 <= i < j <= i + 2^20", k);
+  for (int q = 0; q < c->P; ++q)
+    if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "correlation: a step is in progress");
+  if (npairs == 0) return IDMRG_OK;
+  return obs_correlation(c, nterms, op_a, op_b, coef, npairs, site_i, site_j, out);
+}
+
+idmrg_status idmrg_transfer_spectrum(idmrg_ctx *c, double tol, int maxit, double *t1, double *t2_abs, double *xi,
+                                     int *iters) {
+  if (!c || !(tol > 0.0) || maxit < 1) return IDMRG_EINVAL;
+  for (int q = 0; q < c->P; ++q)
+    if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "transfer_spectrum: a step is in progress");
+  double ratio = 0.0;
+  int it = 0;
+  const idmrg_status s = obs_spectrum(c, tol, maxit, &ratio, &it);
+  if (s != IDMRG_OK && s != IDMRG_ENOCONV) return s;
+  if (t1) *t1 = c->obs.t1;
+  if (t2_abs) *t2_abs = ratio * c->obs.t1;
+  if (xi) *xi = ratio > 0.0 ? -1.0 / std::log(ratio) : 0.0;
+  if (iters) *iters = it;
+  return s;
 }
 
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *c, double *e_g, int *n_of_estimate) {
