@@ -249,9 +249,9 @@ struct CompactJob {
   int lam_off;         // destination of lambda (k entries)
   int pad;
 };
-cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, double *work,
-                               const int *iwork, const double *sv, const int *perm, const int *kept_per_job,
-                               double *const *bufs, double *lam, cudaStream_t st);
+cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, int max_rows,
+                               double *work, const int *iwork, const double *sv, const int *perm,
+                               const int *kept_per_job, double *const *bufs, double *lam, cudaStream_t st);
 
 // ---- tensor-core path (kernels_tc.cu)
 // Packed operand matrix: tiles of (8 G) rows x 128 bytes of K (32 TF32 or 64

@@ -2117,8 +2117,10 @@ idmrg_status trunc_compact(idmrg_ctx *c, DevBuf &dcj, const std::vector<CompactJ
   NOMEM(c->ensure(dcj, std::max<size_t>(cj.size() * sizeof(CompactJob), 16)));
   CK(cudaMemcpyAsync(dcj.p, cj.data(), cj.size() * sizeof(CompactJob), cudaMemcpyHostToDevice, s));
   c->h2d += cj.size() * sizeof(CompactJob);
+  int max_rows = 0;
+  for (const CompactJob &j : cj) max_rows = std::max(max_rows, c->jobs[j.job].rows_a);
   CK(launch_svd_compact((const SvdJob *)c->sjobs.p, (const CompactJob *)dcj.p, (int)cj.size(), std::max(1, max_kept),
-                        c->dp(c->swork), (const int *)c->siw.p, c->dp(c->ssv), (const int *)c->sperm.p,
+                        max_rows, c->dp(c->swork), (const int *)c->siw.p, c->dp(c->ssv), (const int *)c->sperm.p,
                         (const int *)c->skpj.p, (double *const *)c->dbufs.p, c->dp(c->slamk), s));
   c->launches += 1;
   return IDMRG_OK;

@@ -1881,6 +1881,90 @@ __global__ void compact_kernel(const SvdJob *__restrict__ jobs, const CompactJob
   }
 }
 
+// The same for jobs of at most CP_R * 32 rows: each warp keeps its column in
+// registers (row lane + 32 r in x[r]) and every reflector is staged once per
+// CTA in shared memory (double-buffered: the next one loads while the current
+// one is applied), so a reflector costs one dot product, one shuffle
+// reduction and one axpy on registers instead of dependent global loads.
+constexpr int CP_R = 24;
+constexpr int CP_WARPS = 8;
+__global__ void __launch_bounds__(32 * CP_WARPS) compact_reg_kernel(
+    const SvdJob *__restrict__ jobs, const CompactJob *__restrict__ cjs, const double *__restrict__ work,
+    const int *__restrict__ iwork, const double *__restrict__ sv, const int *__restrict__ perm,
+    const int *__restrict__ kept_per_job, double *const *__restrict__ bufs, double *__restrict__ lam) {
+  __shared__ double vs[2][CP_R * 32];
+  const CompactJob cj = cjs[blockIdx.x];
+  const SvdJob J = jobs[cj.job];
+  const int k = kept_per_job[cj.job];
+  const int ra = J.rows_a, ca = J.cols_a;
+  const double *A = work + J.a_off;
+  const double *tau = work + J.tau_off;
+  const double *Jm = work + J.j_off;
+  const double *Bn = work + J.b_off;
+  const int *qperm = iwork + J.perm_off;
+  const int rk = qperm[ca];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = blockIdx.y * CP_WARPS + warp;
+  if (blockIdx.y * CP_WARPS >= k) return;  // whole CTA idle (uniform)
+  const bool active = slot < k;
+  const int col = active ? perm[J.sv_off + slot] : 0;
+  double x[CP_R];
+#pragma unroll
+  for (int r = 0; r < CP_R; ++r) {
+    const int i = lane + 32 * r;
+    x[r] = (active && i < rk) ? Jm[(int64_t)col * rk + i] : 0.0;
+  }
+  // reflector kk staged as (0 .. 0, 1, v[kk+1] .. v[ra-1]) (its unit entry at
+  // kk written out); CP_R * 32 / (32 * CP_WARPS) entries per thread
+  constexpr int SPT = CP_R * 32 / (32 * CP_WARPS);
+  static_assert(SPT * 32 * CP_WARPS == CP_R * 32, "staging split");
+  int b = 0;
+  if (rk > 0) {
+    const double *v = A + (int64_t)(rk - 1) * ra;
+#pragma unroll
+    for (int e = 0; e < SPT; ++e) {
+      const int i = threadIdx.x + e * 32 * CP_WARPS;
+      vs[0][i] = i == rk - 1 ? 1.0 : (i > rk - 1 && i < ra) ? v[i] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int kk = rk - 1; kk >= 0; --kk) {
+    if (kk > 0) {
+      const double *v = A + (int64_t)(kk - 1) * ra;
+#pragma unroll
+      for (int e = 0; e < SPT; ++e) {
+        const int i = threadIdx.x + e * 32 * CP_WARPS;
+        vs[b ^ 1][i] = i == kk - 1 ? 1.0 : (i > kk - 1 && i < ra) ? v[i] : 0.0;
+      }
+    }
+    const double t = tau[kk];
+    if (t != 0.0) {
+      double w = 0.0;
+#pragma unroll
+      for (int r = 0; r < CP_R; ++r)
+        if (32 * r < ra) w = fma(vs[b][lane + 32 * r], x[r], w);
+      w = wsum(w) * t;
+#pragma unroll
+      for (int r = 0; r < CP_R; ++r)
+        if (32 * r < ra) x[r] = fma(-w, vs[b][lane + 32 * r], x[r]);
+    }
+    __syncthreads();
+    b ^= 1;
+  }
+  if (!active) return;
+  double *U = bufs[J.sb * NBUF + BUF_U] + cj.u_off;
+  double *V = bufs[J.sb * NBUF + BUF_V] + cj.v_off;
+  double *Lout = !J.transposed ? U : V;
+  double *Rout = !J.transposed ? V : U;
+#pragma unroll
+  for (int r = 0; r < CP_R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < ra) Lout[(int64_t)i * k + slot] = x[r];
+  }
+  for (int i = lane; i < ca; i += 32) Rout[(int64_t)qperm[i] * k + slot] = Bn[(int64_t)col * ca + i];
+  if (lane == 0) lam[cj.lam_off + slot] = sv[J.sv_off + col];
+}
+
 }  // namespace
 
 cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_elems, double *const *bufs,
@@ -2057,10 +2141,13 @@ cudaError_t launch_svd_select(const SvdJob *jobs, const int *sb_job0, const int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, double *work,
-                               const int *iwork, const double *sv, const int *perm, const int *kept_per_job,
-                               double *const *bufs, double *lam, cudaStream_t st) {
-  if (ncj > 0) {
+cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, int max_rows,
+                               double *work, const int *iwork, const double *sv, const int *perm,
+                               const int *kept_per_job, double *const *bufs, double *lam, cudaStream_t st) {
+  if (ncj > 0 && max_rows <= CP_R * 32) {
+    dim3 grid(ncj, (unsigned)std::max(1, (max_kept + CP_WARPS - 1) / CP_WARPS));
+    compact_reg_kernel<<<grid, 32 * CP_WARPS, 0, st>>>(jobs, cj, work, iwork, sv, perm, kept_per_job, bufs, lam);
+  } else if (ncj > 0) {
     const int warps = 8;
     dim3 grid(ncj, (unsigned)std::max(1, (max_kept + warps - 1) / warps));
     compact_kernel<<<grid, 32 * warps, 0, st>>>(jobs, cj, work, iwork, sv, perm, kept_per_job, bufs, lam);
