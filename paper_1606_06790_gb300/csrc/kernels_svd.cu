@@ -1881,21 +1881,25 @@ __global__ void compact_kernel(const SvdJob *__restrict__ jobs, const CompactJob
   }
 }
 
-// The same for jobs of at most CP_R * 32 rows: each warp keeps its column in
-// registers (row lane + 32 r in x[r]) and every reflector is staged once per
-// CTA in shared memory (double-buffered: the next one loads while the current
-// one is applied), so a reflector costs one dot product, one shuffle
-// reduction and one axpy on registers instead of dependent global loads.
-constexpr int CP_R = 24;
+// The same with each warp's column and the current reflector in shared
+// memory: every reflector is staged once per CTA (double-buffered, so the
+// next one loads while the current one is applied) and each warp runs the
+// dot product and the axpy over rows kk .. ra-1 only.  On this part a
+// warp-wide FP64 instruction holds its sub-partition's FP64 unit for 64
+// cycles even when predicated off, so the loops have exact trip counts
+// instead of an unrolled register array.  Shared memory: (2 + CP_WARPS) rs
+// doubles, rs >= every job's rows.
 constexpr int CP_WARPS = 8;
-__global__ void __launch_bounds__(32 * CP_WARPS) compact_reg_kernel(
+constexpr int CP_MAX_ROWS = 2048;
+__global__ void __launch_bounds__(32 * CP_WARPS) compact_smem_kernel(
     const SvdJob *__restrict__ jobs, const CompactJob *__restrict__ cjs, const double *__restrict__ work,
     const int *__restrict__ iwork, const double *__restrict__ sv, const int *__restrict__ perm,
-    const int *__restrict__ kept_per_job, double *const *__restrict__ bufs, double *__restrict__ lam) {
-  __shared__ double vs[2][CP_R * 32];
+    const int *__restrict__ kept_per_job, double *const *__restrict__ bufs, double *__restrict__ lam, int rs) {
+  extern __shared__ double csm[];
   const CompactJob cj = cjs[blockIdx.x];
   const SvdJob J = jobs[cj.job];
   const int k = kept_per_job[cj.job];
+  if (blockIdx.y * CP_WARPS >= k) return;  // whole CTA idle (uniform)
   const int ra = J.rows_a, ca = J.cols_a;
   const double *A = work + J.a_off;
   const double *tau = work + J.tau_off;
@@ -1905,62 +1909,38 @@ __global__ void __launch_bounds__(32 * CP_WARPS) compact_reg_kernel(
   const int rk = qperm[ca];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slot = blockIdx.y * CP_WARPS + warp;
-  if (blockIdx.y * CP_WARPS >= k) return;  // whole CTA idle (uniform)
   const bool active = slot < k;
   const int col = active ? perm[J.sv_off + slot] : 0;
-  double x[CP_R];
-#pragma unroll
-  for (int r = 0; r < CP_R; ++r) {
-    const int i = lane + 32 * r;
-    x[r] = (active && i < rk) ? Jm[(int64_t)col * rk + i] : 0.0;
-  }
-  // reflector kk staged as (0 .. 0, 1, v[kk+1] .. v[ra-1]) (its unit entry at
-  // kk written out); CP_R * 32 / (32 * CP_WARPS) entries per thread
-  constexpr int SPT = CP_R * 32 / (32 * CP_WARPS);
-  static_assert(SPT * 32 * CP_WARPS == CP_R * 32, "staging split");
-  int b = 0;
+  double *vs0 = csm, *vs1 = csm + rs, *x = csm + (2 + warp) * rs;
+  if (active)
+    for (int i = lane; i < ra; i += 32) x[i] = i < rk ? Jm[(int64_t)col * rk + i] : 0.0;
+  // reflector kk as (1, v[kk+1] .. v[ra-1]) at rows kk .. ra-1
   if (rk > 0) {
     const double *v = A + (int64_t)(rk - 1) * ra;
-#pragma unroll
-    for (int e = 0; e < SPT; ++e) {
-      const int i = threadIdx.x + e * 32 * CP_WARPS;
-      vs[0][i] = i == rk - 1 ? 1.0 : (i > rk - 1 && i < ra) ? v[i] : 0.0;
-    }
+    for (int i = rk - 1 + threadIdx.x; i < ra; i += 32 * CP_WARPS) vs0[i] = i == rk - 1 ? 1.0 : v[i];
   }
   __syncthreads();
   for (int kk = rk - 1; kk >= 0; --kk) {
+    double *cur = ((rk - 1 - kk) & 1) ? vs1 : vs0, *nxt = ((rk - 1 - kk) & 1) ? vs0 : vs1;
     if (kk > 0) {
       const double *v = A + (int64_t)(kk - 1) * ra;
-#pragma unroll
-      for (int e = 0; e < SPT; ++e) {
-        const int i = threadIdx.x + e * 32 * CP_WARPS;
-        vs[b ^ 1][i] = i == kk - 1 ? 1.0 : (i > kk - 1 && i < ra) ? v[i] : 0.0;
-      }
+      for (int i = kk - 1 + threadIdx.x; i < ra; i += 32 * CP_WARPS) nxt[i] = i == kk - 1 ? 1.0 : v[i];
     }
     const double t = tau[kk];
-    if (t != 0.0) {
+    if (active && t != 0.0) {
       double w = 0.0;
-#pragma unroll
-      for (int r = 0; r < CP_R; ++r)
-        if (32 * r < ra) w = fma(vs[b][lane + 32 * r], x[r], w);
+      for (int i = kk + lane; i < ra; i += 32) w = fma(cur[i], x[i], w);
       w = wsum(w) * t;
-#pragma unroll
-      for (int r = 0; r < CP_R; ++r)
-        if (32 * r < ra) x[r] = fma(-w, vs[b][lane + 32 * r], x[r]);
+      for (int i = kk + lane; i < ra; i += 32) x[i] = fma(-w, cur[i], x[i]);
     }
     __syncthreads();
-    b ^= 1;
   }
   if (!active) return;
   double *U = bufs[J.sb * NBUF + BUF_U] + cj.u_off;
   double *V = bufs[J.sb * NBUF + BUF_V] + cj.v_off;
   double *Lout = !J.transposed ? U : V;
   double *Rout = !J.transposed ? V : U;
-#pragma unroll
-  for (int r = 0; r < CP_R; ++r) {
-    const int i = lane + 32 * r;
-    if (i < ra) Lout[(int64_t)i * k + slot] = x[r];
-  }
+  for (int i = lane; i < ra; i += 32) Lout[(int64_t)i * k + slot] = x[i];
   for (int i = lane; i < ca; i += 32) Rout[(int64_t)qperm[i] * k + slot] = Bn[(int64_t)col * ca + i];
   if (lane == 0) lam[cj.lam_off + slot] = sv[J.sv_off + col];
 }
@@ -2144,9 +2124,14 @@ cudaError_t launch_svd_select(const SvdJob *jobs, const int *sb_job0, const int 
 cudaError_t launch_svd_compact(const SvdJob *jobs, const CompactJob *cj, int ncj, int max_kept, int max_rows,
                                double *work, const int *iwork, const double *sv, const int *perm,
                                const int *kept_per_job, double *const *bufs, double *lam, cudaStream_t st) {
-  if (ncj > 0 && max_rows <= CP_R * 32) {
+  if (ncj > 0 && max_rows <= CP_MAX_ROWS) {
+    const int rs = std::max(32, (max_rows + 31) & ~31);
+    const size_t smem = (size_t)(2 + CP_WARPS) * rs * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(compact_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     dim3 grid(ncj, (unsigned)std::max(1, (max_kept + CP_WARPS - 1) / CP_WARPS));
-    compact_reg_kernel<<<grid, 32 * CP_WARPS, 0, st>>>(jobs, cj, work, iwork, sv, perm, kept_per_job, bufs, lam);
+    compact_smem_kernel<<<grid, 32 * CP_WARPS, smem, st>>>(jobs, cj, work, iwork, sv, perm, kept_per_job, bufs,
+                                                            lam, rs);
   } else if (ncj > 0) {
     const int warps = 8;
     dim3 grid(ncj, (unsigned)std::max(1, (max_kept + warps - 1) / warps));
