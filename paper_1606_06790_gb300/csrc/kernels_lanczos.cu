@@ -275,18 +275,33 @@ __global__ void finalize_kernel(LanczosDev L) {
   // the FP32 bracket.  Lane 0 runs the recurrence; theta - a_j, the norm and
   // the scaling are spread over the warp.
   const double *ib = L.ibeta + (int64_t)s * km;
-  double *dd = sm + 5 * km;  // theta - a_j, after the FP32 copies (2 km floats at sm + 4 km)
-  double theta = shift, nrm2 = 1.0;
+  // x_{j-1} = p_j x_j - q_j x_{j+1} with p_j = (theta - a_j) / beta_{j-1},
+  // q_j = beta_j / beta_{j-1} formed by the whole warp, so the serial chain of
+  // lane 0 is one FMA per row (q_j x_{j+1} is ready a row earlier); overflow
+  // is caught on the exponent bits (|x| >= 2^498) instead of an FP64 compare.
+  double *pp = sm + 5 * km, *qq = sm + 6 * km;  // after the FP32 copies (2 km floats at sm + 4 km)
+  for (int j = 1 + lane; j <= n - 2; j += 32) qq[j] = b[j] * ib[j - 1];
+  double theta = shift, nrm2 = 1.0, dd0 = 0.0;
   for (int it = 0; it < 4; ++it) {
-    for (int i = lane; i < n; i += 32) dd[i] = theta - a[i];
+    for (int j = 1 + lane; j <= n - 2; j += 32) pp[j] = (theta - a[j]) * ib[j - 1];
+    dd0 = theta - a[0];
     __syncwarp();
     if (lane == 0) {
       x[n - 1] = 1.0;
-      if (n >= 2) x[n - 2] = dd[n - 1] * ib[n - 2];
-      for (int j = n - 2; j >= 1; --j) {
-        x[j - 1] = fma(dd[j], x[j], -b[j] * x[j + 1]) * ib[j - 1];
-        if (fabs(x[j - 1]) > 1e150)
-          for (int i = j - 1; i < n; ++i) x[i] *= 1e-150;
+      if (n >= 2) {
+        double xj1 = 1.0, xj = (theta - a[n - 1]) * ib[n - 2];
+        x[n - 2] = xj;
+        for (int j = n - 2; j >= 1; --j) {
+          const double xm = fma(pp[j], xj, -qq[j] * xj1);
+          x[j - 1] = xm;
+          xj1 = xj;
+          xj = xm;
+          if ((int)(((unsigned long long)__double_as_longlong(xm) >> 52) & 0x7ffu) > 1023 + 498) {
+            for (int i = j - 1; i < n; ++i) x[i] *= 1e-150;
+            xj *= 1e-150;
+            xj1 *= 1e-150;
+          }
+        }
       }
     }
     __syncwarp();
@@ -294,7 +309,7 @@ __global__ void finalize_kernel(LanczosDev L) {
     for (int i = lane; i < n; i += 32) s2 = fma(x[i], x[i], s2);
     for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     nrm2 = s2;
-    const double r = (n >= 2) ? fma(-dd[0], x[0], b[0] * x[1]) : -dd[0] * x[0];
+    const double r = (n >= 2) ? fma(-dd0, x[0], b[0] * x[1]) : -dd0 * x[0];
     const double dth = r * x[0] / nrm2;
     theta += dth;
     __syncwarp();
@@ -464,7 +479,7 @@ cudaError_t lanczos_subtract(const LanczosDev &L, int pass, cudaStream_t st) {
 }
 
 cudaError_t lanczos_finalize(const LanczosDev &L, cudaStream_t st) {
-  const size_t smem = (size_t)L.kmax * 6 * sizeof(double);  // a, b, b^2, x, FP32 copies, theta - a
+  const size_t smem = (size_t)L.kmax * 7 * sizeof(double);  // a, b, b^2, x, FP32 copies, p, q
   finalize_kernel<<<L.S, 32, smem, st>>>(L);
   return cudaGetLastError();
 }
