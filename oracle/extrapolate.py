@@ -1,7 +1,8 @@
 """Sec. 5 of the paper (oracle side, test infrastructure): a run at fixed m
 until e_g converges, the truncation error eps of the run (Eq. tru, reading
-R6: the largest eps^(n)_1 over the last l iterations), and the quadratic
-extrapolation of e_g to eps -> 0, written from the normal equations.
+R6: the largest eps^(n)_1 over the last l iterations), the quadratic
+extrapolation of e_g to eps -> 0, and the exponential fit of a correlation
+function for the correlation length, both written from the normal equations.
 
 Imported only by tests, smoke() and bench.py's reference arm."""
 from __future__ import annotations
@@ -41,3 +42,23 @@ def quadratic_fit(eps, e) -> Tuple[float, float]:
     res = y - (c[0] + c[1] * x + c[2] * x * x)
     s2 = float(np.sum(res * res)) / (len(x) - 3)
     return float(c[0]), float(np.sqrt(max(s2 * np.linalg.inv(G)[0, 0], 0.0)))
+
+
+def exponential_fit(r, c, r_min: float = 5.0) -> Tuple[float, float]:
+    """ln|c| = a + b r over the points with r > r_min, by the 2 x 2 normal
+    equations; xi = -1 / b and its standard deviation sd(b) / b^2 with
+    sd(b)^2 = s^2 [(A^T A)^-1]_11, s^2 = RSS / (N - 2)."""
+    x = np.asarray(r, dtype=np.float64)
+    y = np.abs(np.asarray(c, dtype=np.float64))
+    keep = (x > r_min) & (y > 0.0)
+    x, y = x[keep], np.log(y[keep])
+    G = np.array([[len(x), np.sum(x)], [np.sum(x), np.sum(x * x)]])
+    rhs = np.array([np.sum(y), np.sum(x * y)])
+    a, b = np.linalg.solve(G, rhs)
+    xi = -1.0 / b
+    if len(x) <= 2:
+        return float(xi), 0.0
+    res = y - (a + b * x)
+    s2 = float(np.sum(res * res)) / (len(x) - 2)
+    sd_b = float(np.sqrt(max(s2 * np.linalg.inv(G)[1, 1], 0.0)))
+    return float(xi), sd_b / (b * b)

@@ -1,6 +1,8 @@
 """The m scan of Sec. 5: e_g against the truncation error eps for several m,
 extrapolated to eps -> 0 with a quadratic polynomial (the paper's Eq. tru
-and the quadratic fit of its Fig. ene_vs_tru).
+and the quadratic fit of its Fig. ene_vs_tru); the same fit serves the bond
+strengths and Delta+- of Eqs. diff1, diff2.  Also the exponential fit of a
+spin-spin correlation function that gives the paper's correlation length.
 
 Every point runs through the C ABI (`idmrg_run`: unit-cell steps until two
 successive e_g estimates agree to `de_tol`); only the final least-squares fit
@@ -43,3 +45,27 @@ def extrapolate(eps: Sequence[float], e: Sequence[float], degree: int = 2) -> Tu
     s2 = float(r @ r) / dof
     cov = s2 * np.linalg.inv(A.T @ A)
     return float(coef[0]), float(np.sqrt(max(cov[0, 0], 0.0)))
+
+
+def fit_correlation_length(r: Sequence[float], c: Sequence[float], r_min: float = 5.0) -> Tuple[float, float]:
+    """Least-squares fit of ln|c(r)| = a - r / xi over the points with r > r_min
+    (Sec. 5: |<s_i . s_2>| decays as exp(-|r_i - r_2| / xi)); returns xi and its
+    standard deviation from the residual variance of the fit (0 with two
+    points).  Points with c = 0 are skipped."""
+    x = np.asarray(r, dtype=np.float64)
+    y = np.abs(np.asarray(c, dtype=np.float64))
+    keep = (x > r_min) & (y > 0.0)
+    x, y = x[keep], np.log(y[keep])
+    if len(x) < 2:
+        raise ValueError("need two points beyond r_min")
+    A = np.vander(x, 2, increasing=True)
+    coef, _, _, _ = np.linalg.lstsq(A, y, rcond=None)
+    slope = float(coef[1])
+    xi = -1.0 / slope
+    dof = len(x) - 2
+    if dof <= 0:
+        return xi, 0.0
+    res = y - A @ coef
+    s2 = float(res @ res) / dof
+    sd_slope = float(np.sqrt(max(s2 * np.linalg.inv(A.T @ A)[1, 1], 0.0)))
+    return xi, sd_slope / (slope * slope)

@@ -54,3 +54,46 @@ def test_eps_decreases_with_m_and_extrapolation_nears_bethe():
     bethe = 0.25 - np.log(2.0)
     assert e0 < e[-1] + 1e-12
     assert abs(e0 - bethe) < 2e-3
+
+
+def test_exponential_fit_pins():
+    from oracle.extrapolate import exponential_fit
+    from oracle import observables as ob
+    # exact exponential: xi recovered, no spread
+    r = np.arange(1, 30, dtype=float)
+    xi, sd = exponential_fit(r, 0.7 * np.exp(-r / 3.25) * (-1.0) ** r, r_min=5)
+    assert xi == pytest.approx(3.25, rel=1e-12) and sd < 1e-12
+    # closed-form spread: ln|c| = a + b x + d (1, -2, 1) at x = 0, 1, 2 gives
+    # RSS = 6 d^2, s^2 = 6 d^2, [(A^T A)^-1]_11 = 1/2, sd(b) = d sqrt(3)
+    a, b, d = 0.3, -0.5, 1e-3
+    x = np.array([0.0, 1.0, 2.0])
+    c = np.exp(a + b * x + d * np.array([1.0, -2.0, 1.0]))
+    xi, sd = exponential_fit(x, c, r_min=-1)
+    assert xi == pytest.approx(2.0, rel=1e-12)
+    assert sd == pytest.approx(d * np.sqrt(3.0) / b ** 2, rel=1e-9)
+    # AKLT: |<S^z_0 S^z_r>| = (4/3) 3^-r, so xi = 1 / ln 3 sites
+    sp = np.array([[0.0, 1.0], [0.0, 0.0]])
+    A = np.array([np.sqrt(2 / 3) * sp, -np.sqrt(1 / 3) * np.diag([1.0, -1.0]), -np.sqrt(2 / 3) * sp.T])
+    Sz = np.diag([1.0, 0.0, -1.0])
+    rr = np.arange(1, 12)
+    cc = [ob.correlation([A, A], 0, Sz, Sz, 0, int(k)) for k in rr]
+    xi, _ = exponential_fit(rr, cc, r_min=0)
+    assert xi == pytest.approx(1 / np.log(3.0), rel=1e-9)
+
+
+def test_package_fits_match_the_oracle():
+    # host post-processing of the library's outputs (no GPU): the package's
+    # least-squares fits against the oracle's normal-equation versions
+    from oracle.extrapolate import exponential_fit
+    from paper_1606_06790_gb300.scan import extrapolate, fit_correlation_length
+    rng = np.random.default_rng(5)
+    r = np.arange(2, 40, dtype=float)
+    c = np.exp(-r / 4.7) * (1 + 0.05 * rng.standard_normal(len(r)))
+    x1, s1 = fit_correlation_length(r, c, r_min=5)
+    x2, s2 = exponential_fit(r, c, r_min=5)
+    assert x1 == pytest.approx(x2, rel=1e-10) and s1 == pytest.approx(s2, rel=1e-8)
+    eps = np.array([1e-6, 3e-6, 7e-6, 2e-5, 5e-5])
+    e = -0.43838 + 12.5 * eps - 3.0e4 * eps ** 2 + 1e-9 * rng.standard_normal(5)
+    c0, sd = extrapolate(eps, e)
+    q0, qsd = quadratic_fit(eps, e)
+    assert c0 == pytest.approx(q0, abs=1e-12) and sd == pytest.approx(qsd, rel=1e-6)
