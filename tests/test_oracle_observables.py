@@ -2,6 +2,9 @@
 ``oracle.observables``): closed forms of the AKLT chain and of a singlet
 product, the transfer spectrum of a two-state MPS in closed form, brute force
 on a periodic ring, and the iDMRG states of exactly solvable chains."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -22,9 +25,13 @@ SZ1 = np.diag([1.0, 0.0, -1.0])
 SP1 = np.sqrt(2.0) * np.diag([1.0, 1.0], 1)
 
 
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
 def test_aklt_correlations_and_length():
     # <S^z_0 S^z_r> = (4/3)(-1/3)^r and <S_0 . S_r> = 4 (-1/3)^r for r >= 1;
     # xi = 1 / ln 3 sites = 1 / (2 ln 3) two-site unit cells
+    assert GOLDEN["aklt_spin_correlation"]["xi_sites"] == pytest.approx(1 / np.log(3.0), rel=1e-15)
     unit = aklt_unit()
     for i in (0, 1, 5):
         for r in range(1, 7):
@@ -33,7 +40,7 @@ def test_aklt_correlations_and_length():
             mp = ob.correlation(unit, 0, SP1.T, SP1, i, i + r)
             assert zz == pytest.approx((4 / 3) * (-1 / 3) ** r, rel=1e-12, abs=1e-15)
             assert zz + 0.5 * (pm + mp) == pytest.approx(4 * (-1 / 3) ** r, rel=1e-12, abs=1e-15)
-    assert ob.correlation_length(unit) == pytest.approx(1 / (2 * np.log(3.0)), rel=1e-12)
+    assert ob.correlation_length(unit) == pytest.approx(GOLDEN["aklt_spin_correlation"]["xi_sites"] / 2, rel=1e-12)
 
 
 def test_two_state_transfer_spectrum_closed_form():
@@ -62,7 +69,8 @@ def test_singlet_product():
     A1[1, 0, 0] = 1 / np.sqrt(2)
     A1[0, 1, 0] = -1 / np.sqrt(2)
     unit = [A0, A1]
-    for (i, j), v in {(0, 1): -0.75, (2, 3): -0.75, (1, 2): 0.0, (0, 3): 0.0, (1, 4): 0.0}.items():
+    sing = GOLDEN["singlet_bond_strength"]["value"]
+    for (i, j), v in {(0, 1): sing, (2, 3): sing, (1, 2): 0.0, (0, 3): 0.0, (1, 4): 0.0}.items():
         assert ob.spin_dot(unit, 0, i, j) == pytest.approx(v, abs=1e-15)
 
 
