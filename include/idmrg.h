@@ -8,7 +8,10 @@
  * solves the l/2 superblocks H^(n)_i = L^(n-1)_{2i-1} W W R^(n-1)_{2i+2}
  * (Step 2'), starting from the predicted wavefunction of Eq. wfprediction
  * (Step 3'), splits each ground state by SVD (Step 4), renormalises the
- * blocks (Step 6) and estimates the energy per site (Step 5').
+ * blocks (Step 6) and estimates the energy per site (Step 5').  Between
+ * steps, the uniform MPS of Eq. mps2 built from the last two iterations gives
+ * two-point functions and the transfer spectrum (idmrg_correlation,
+ * idmrg_transfer_spectrum).
  *
  * Conventions shared by every call
  * --------------------------------
