@@ -184,6 +184,16 @@ idmrg_status idmrg_heff_apply_fp64(idmrg_ctx *ctx, int p, const double *psi_dev,
  * sector.  Writes ||psi~|| if norm_out != NULL (host, l/2 entries for p=-1). */
 idmrg_status idmrg_predict_wavefunction(idmrg_ctx *ctx, int p, double *norm_out);
 
+/* Step 3 start vector given by the caller instead of Step 3': copies psi_dev
+ * (device, the idmrg_psi_layout of p, or every superblock's vector
+ * concatenated for p = -1) into the start vector of the next
+ * idmrg_lanczos_solve, which normalises it.  Allowed before that solve
+ * (after, or in place of, idmrg_predict_wavefunction); ESTATE otherwise.  A
+ * start vector with zero or non-finite norm makes the solve return
+ * IDMRG_ENUMERIC.  The step report's fidelity (Eq. fid1) then refers to this
+ * vector. */
+idmrg_status idmrg_set_start_vector(idmrg_ctx *ctx, int p, const double *psi_dev);
+
 /* Step 3 solve by FP64 Lanczos with full re-orthogonalisation.  All
  * requested superblocks are solved together, matvecs batched.  e_out and
  * iters_out: host, one entry (p >= 0) or l/2 entries (p = -1). */
@@ -277,9 +287,11 @@ idmrg_status idmrg_energy_per_site(const idmrg_ctx *ctx, double *e_g, int *n_of_
  * of e^(n)_1 behind Step 5', every pair's current environments (Step 6) and
  * the last two truncations (bases, U, V, lambda) that the prediction of
  * Step 3' reads.  idmrg_save writes them to `path` (binary, host byte order);
- * idmrg_load reads them into a context created with the same MPO and options
- * (checked: EINVAL otherwise), which then continues exactly as the saved one
- * would.  Both synchronise the context's stream; ESTATE while a step is in
+ * idmrg_load reads them into a context created with the same MPO, m and
+ * target charge (checked: EINVAL otherwise), which then continues exactly as
+ * the saved one would when its other options are the same too.  Every
+ * precision keeps this state in FP64, so a state saved under one precision
+ * loads into a context of another (the file records the saving one).  Both synchronise the context's stream; ESTATE while a step is in
  * progress; EINVAL on I/O errors or a damaged file. */
 idmrg_status idmrg_save(const idmrg_ctx *ctx, const char *path);
 idmrg_status idmrg_load(idmrg_ctx *ctx, const char *path);
@@ -340,12 +352,18 @@ idmrg_status idmrg_transfer_bytes(const idmrg_ctx *ctx, uint64_t *h2d, uint64_t 
  * thread or while work is queued).  The paper has no counterpart; this is a
  * deployment variant of idmrg_heff_apply.  psi_dev and out_dev are the
  * caller's device vectors in the layout of idmrg_psi_layout(p); the
- * intermediates live in a fixed 16 MiB device array inside the library, which
- * every GPU that loads the library holds until the process exits.  The call
- * itself allocates nothing (no cudaMalloc, no allocator callback).
- *  - The first call on a device looks up that array's device address
- *    (cudaGetSymbolAddress) with the device current; make that first call
- *    before any stream capture.
+ * intermediates and the launch's pointer table live in a fixed 16 MiB device
+ * array inside the library, which every GPU that loads the library holds
+ * until the process exits.  The call itself allocates nothing (no cudaMalloc,
+ * no allocator callback, no library routine that allocates).
+ *  - Call it with the context's device current: every call looks up the
+ *    array's device address on the current device (cudaGetSymbolAddress).
+ *    The first call in a process may load the library's device code; make
+ *    that first call before any stream capture.
+ *  - It computes FP64 whatever opts.prec is (the FP64 GEMMs of form 0 of
+ *    idmrg_heff_apply_fp64).
+ *  - Valid from idmrg_create / idmrg_advance until the iteration's first
+ *    idmrg_truncate; IDMRG_ESTATE from then until the next idmrg_advance.
  *  - Superblocks whose intermediates exceed the array return IDMRG_EINVAL
  *    with the sizes in idmrg_last_error.
  *  - All calls share the array and it keeps the last call's contents; every

@@ -247,7 +247,7 @@ struct idmrg_ctx {
   std::vector<double *> hbufs;
   DevBuf dbufs, dg1k, dg1s, dg3k, dg3s, dwt, dwm, ddt, ddp, drb, dgpk, dgps, dst, dstab;
   DevBuf dge1k, dge1s, dge3k, dge3s, dwet, dwem, dmask, derr;
-  std::vector<DevBuf> bT1, bT3, bX, bY, bV, bW, bPsi, bUT, bVT;
+  std::vector<DevBuf> bT1, bT3, bX, bY, bV, bW, bPsi, bUT, bVT, bStart;
   // lanczos
   DevBuf lN, lV, lw, lalpha, lbeta, libeta, lh, lpart, lk, lmember, lactive, lconv, ltheta, ly, lresid, lpsi, lv0, ldot;
   int kmax = 0, nchunk = 0;
@@ -1646,13 +1646,17 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   }
   const int CHK = 1024;
   const int nchunk = (int)((nmax + CHK - 1) / CHK);
-  std::vector<double *> Vp(P), wp(P), psip(P), v0p(P);
+  std::vector<double *> Vp(P), wp(P), psip(P), v0p(P), startp(P, nullptr);
   for (int q = 0; q < P; ++q) {
     NOMEM(c->ensure(c->bV[q], 8 * std::max<int64_t>((int64_t)kmax * N[q], 1)));
     Vp[q] = c->dp(c->bV[q]);
     wp[q] = c->dp(c->bW[q]);
     psip[q] = c->dp(c->bPsi[q]);
     v0p[q] = Vp[q];
+    if (c->mixed) {
+      NOMEM(c->ensure(c->bStart[q], 8 * std::max<int64_t>(N[q], 1)));
+      startp[q] = c->dp(c->bStart[q]);
+    }
   }
   NOMEM(c->upload(c->lN, N) && c->upload(c->lV, Vp) && c->upload(c->lw, wp) && c->upload(c->lpsi, psip) &&
         c->upload(c->lv0, v0p));
@@ -1786,11 +1790,15 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
     }
     CK(lanczos_ritz(L, (double *const *)c->lpsi.p, c->st));
     c->launches += 4;
-    if (r == 0) {
+    if (r == 0 && !c->mixed) {  // one run: V[0] is still the normalised start vector
       CK(lanczos_dot(L, (const double *const *)c->lv0.p, (const double *const *)c->lpsi.p, c->dp(c->ldot), c->st));
       c->launches += 2;
       CK(c->d2h_copy(dots.data(), c->ldot.p, 8 * P));
     }
+    if (r == 0 && c->mixed)  // restarts overwrite V[0]: keep the normalised start for Eq. fid1
+      for (int q = 0; q < P; ++q)
+        if (want(p, q) && N[q] > 0)
+          CK(cudaMemcpyAsync(startp[q], Vp[q], 8 * (size_t)N[q], cudaMemcpyDeviceToDevice, c->st));
     std::vector<double> th(P);
     CK(c->d2h_copy(th.data(), c->ltheta.p, 8 * P));
     CK(c->d2h_copy(kk.data(), c->lk.p, 4 * P));
@@ -1808,6 +1816,15 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
         member[q] = 0;
       }
     }
+  }
+  if (c->mixed) {  // Eq. fid1 against the final Ritz vector
+    std::vector<int> all(P);
+    for (int q = 0; q < P; ++q) all[q] = want(p, q) ? 1 : 0;
+    NOMEM(c->upload(c->lmember, all) && c->upload(c->lv0, startp));
+    CK(lanczos_dot(L, (const double *const *)c->lv0.p, (const double *const *)c->lpsi.p, c->dp(c->ldot), c->st));
+    c->launches += 2;
+    CK(c->d2h_copy(dots.data(), c->ldot.p, 8 * P));
+    CK(cudaStreamSynchronize(c->st));
   }
   for (int q = 0; q < P; ++q) {
     if (!want(p, q)) continue;
@@ -3229,6 +3246,7 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
   c->bPsi.resize(P);
   c->bUT.resize(P);
   c->bVT.resize(P);
+  c->bStart.resize(P);
   for (auto *v : {&c->bPA1, &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP, &c->bOA1, &c->bOB1, &c->bOT1,
                   &c->bOA3, &c->bOB3, &c->bORMAP, &c->bOT3})
     v->resize(P);
@@ -3279,7 +3297,7 @@ void idmrg_destroy(idmrg_ctx *c) {
   for (auto &e : c->newR) rel(e.data);
   for (auto *v : {&c->cur, &c->prev, &c->prev2})
     for (auto &t : *v) { rel(t.U); rel(t.V); }
-  for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT, &c->bPA1,
+  for (auto *v : {&c->bT1, &c->bT3, &c->bX, &c->bY, &c->bV, &c->bW, &c->bPsi, &c->bUT, &c->bVT, &c->bStart, &c->bPA1,
                   &c->bPB1, &c->bT1F, &c->bPA3, &c->bPB3, &c->bRMAP, &c->bOA1, &c->bOB1, &c->bOT1, &c->bOA3,
                   &c->bOB3, &c->bORMAP, &c->bOT3})
     for (auto &b : *v) rel(b);
@@ -3452,16 +3470,46 @@ idmrg_status idmrg_predict_wavefunction(idmrg_ctx *c, int p, double *norm_out) {
   if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
   idmrg_status s = predict(c, p);
   if (s != IDMRG_OK || !norm_out) return s;
-  // ||psi~|| on request (one norm per requested superblock)
+  // ||psi~|| on request: one device reduction per requested superblock
+  const int P = c->P;
+  std::vector<int64_t> N(P);
+  std::vector<double *> x(P);
+  std::vector<int> mask(P);
+  int64_t nmax = 1;
+  for (int q = 0; q < P; ++q) {
+    N[q] = c->plan[q].psi.N;
+    x[q] = c->dp(c->bPsi[q]);
+    mask[q] = want(p, q) ? 1 : 0;
+    nmax = std::max(nmax, N[q]);
+  }
+  const int nchunk = (int)((nmax + norm_chunk() - 1) / norm_chunk());
+  NOMEM(c->upload(c->lN, N) && c->upload(c->lpsi, x) && c->upload(c->lmember, mask) &&
+        c->ensure(c->lpart, 8 * (size_t)P * nchunk) && c->ensure(c->lresid, 8 * (size_t)P));
+  CK(launch_norms((const int64_t *)c->lN.p, P, (const double *const *)c->lpsi.p, (const int *)c->lmember.p,
+                  c->dp(c->lpart), nchunk, c->dp(c->lresid), c->st));
+  c->launches += 2;
+  std::vector<double> nr(P);
+  CK(c->d2h_copy(nr.data(), c->lresid.p, 8 * (size_t)P));
   CK(cudaStreamSynchronize(c->st));
   int k = 0;
+  for (int q = 0; q < P; ++q)
+    if (want(p, q)) norm_out[k++] = nr[q];
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_set_start_vector(idmrg_ctx *c, int p, const double *psi_dev) {
+  if (!c || !psi_dev) return IDMRG_EINVAL;
+  if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
+  for (int q = 0; q < c->P; ++q)
+    if (want(p, q) && c->stage[q] != ST_READY && c->stage[q] != ST_STARTED)
+      return c->fail(IDMRG_ESTATE, "set_start_vector: superblock %d already past its start", q);
+  int64_t off = 0;
   for (int q = 0; q < c->P; ++q) {
     if (!want(p, q)) continue;
-    std::vector<double> h(c->plan[q].psi.N);
-    CK(cudaMemcpy(h.data(), c->bPsi[q].p, 8 * h.size(), cudaMemcpyDeviceToHost));
-    double nn = 0.0;
-    for (double v : h) nn += v * v;
-    norm_out[k++] = sqrt(nn);
+    const int64_t N = c->plan[q].psi.N;
+    if (N > 0) CK(cudaMemcpyAsync(c->bPsi[q].p, psi_dev + off, 8 * (size_t)N, cudaMemcpyDeviceToDevice, c->st));
+    off += N;
+    c->stage[q] = ST_STARTED;
   }
   return IDMRG_OK;
 }
@@ -3681,8 +3729,9 @@ idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
   F.get(prec);
   F.get(target);
   F.getv(adim, 1 << 20);
-  if (!F.ok || ell != c->ell || d != c->d || P != c->P || m != c->o.m || prec != (int)c->o.prec ||
-      target != c->o.target_charge || adim != c->adim)
+  (void)prec;  // every precision keeps the state in FP64: a state moves between precisions
+  if (!F.ok || ell != c->ell || d != c->d || P != c->P || m != c->o.m || target != c->o.target_charge ||
+      adim != c->adim)
     return c->fail(IDMRG_EINVAL, "load: %s is not a checkpoint of this MPO and these options", path);
   int n = 0, eg_n = 0;
   double eg_last = 0.0;
@@ -3894,33 +3943,50 @@ idmrg_status idmrg_transfer_bytes(const idmrg_ctx *c, uint64_t *h2d, uint64_t *d
 // contractions) and its pointer table in the file-scope device array below,
 // a fixed 16 MiB that every GPU loading this library holds until the process
 // exits.  Host code sees the array's name only as a stand-in for the symbol,
-// so the device address is looked up with cudaGetSymbolAddress, once per
-// device, on the first call made with that device current.
+// so every call looks its device address up with cudaGetSymbolAddress (with
+// the context's device current; the lookup allocates nothing), and the
+// pointer table is built on the device from the context's own device table
+// and values passed to a one-thread kernel, so no host memory is read by the
+// queued work.
 // --------------------------------------------------------------------------
 namespace {
 constexpr size_t kNoallocBytes = (size_t)16 << 20;
-constexpr int kNoallocMaxDevices = 64;
-constexpr int kNoallocMaxPairs = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
-static unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// table = src (all P * NBUF entries), then superblock p's operands patched in;
+// active[q] = (q == p).  One block; the entries are independent.
+__global__ void noalloc_table_kernel(double *const *src, double **table, int *active, int P, int p, double *L,
+                                     double *R, double *in, double *out, double *t1, double *t3) {
+  for (int i = threadIdx.x; i < P * NBUF; i += blockDim.x) {
+    const int q = i / NBUF, b = i % NBUF;
+    double *v = src[i];
+    if (q == p) {
+      if (b == BUF_L) v = L;
+      else if (b == BUF_R) v = R;
+      else if (b == BUF_IN) v = in;
+      else if (b == BUF_OUT) v = out;
+      else if (b == BUF_T1) v = t1;
+      else if (b == BUF_T3) v = t3;
+    }
+    table[i] = v;
+  }
+  for (int q = threadIdx.x; q < P; q += blockDim.x) active[q] = q == p ? 1 : 0;
+}
 }  // namespace
 
 extern "C" idmrg_status idmrg_heff_apply_noalloc(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev) {
   if (!c || !psi_dev || !out_dev || p < 0 || p >= c->P) return IDMRG_EINVAL;
-  if (c->P > kNoallocMaxPairs) return c->fail(IDMRG_EINVAL, "heff_apply_noalloc: more than %d superblocks", kNoallocMaxPairs);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices)
-    return c->fail(IDMRG_ECUDA, "heff_apply_noalloc: no usable current device");
-  if (!g_noalloc_ptr[dev]) {
-    void *ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return c->fail(IDMRG_ECUDA, "heff_apply_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = (unsigned char *)ptr;
-  }
-  unsigned char *base = g_noalloc_ptr[dev];
+  for (int q = 0; q < c->P; ++q)
+    if (c->stage[q] >= ST_TRUNCATED)
+      return c->fail(IDMRG_ESTATE, "heff_apply_noalloc: iteration %d is being truncated; call after idmrg_advance",
+                     c->n);
+  void *ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return c->fail(IDMRG_ECUDA, "heff_apply_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  unsigned char *base = (unsigned char *)ptr;
   const SBPlan &S = c->plan[p];
   const size_t table_bytes = round256(sizeof(double *) * (size_t)c->P * NBUF);
   const size_t mask_bytes = round256(sizeof(int) * (size_t)c->P);
@@ -3930,26 +3996,20 @@ extern "C" idmrg_status idmrg_heff_apply_noalloc(idmrg_ctx *c, int p, const doub
   if (need > kNoallocBytes)
     return c->fail(IDMRG_EINVAL, "heff_apply_noalloc: superblock %d needs %zu bytes of scratch, the limit is %zu", p,
                    need, kNoallocBytes);
-  // pointer table and activity mask, built on the host stack and copied in
-  double *table[kNoallocMaxPairs * NBUF];
-  int mask[kNoallocMaxPairs];
-  for (int q = 0; q < c->P; ++q) {
-    mask[q] = q == p ? 1 : 0;
-    for (int b = 0; b < NBUF; ++b) table[q * NBUF + b] = c->hbufs[q * NBUF + b];
-  }
-  table[p * NBUF + BUF_IN] = const_cast<double *>(psi_dev);
-  table[p * NBUF + BUF_OUT] = out_dev;
-  table[p * NBUF + BUF_T1] = (double *)(base + table_bytes + mask_bytes);
-  table[p * NBUF + BUF_T3] = (double *)(base + table_bytes + mask_bytes + t1_bytes);
-  CK(cudaMemcpyAsync(base, table, sizeof(double *) * (size_t)c->P * NBUF, cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemcpyAsync(base + table_bytes, mask, sizeof(int) * (size_t)c->P, cudaMemcpyHostToDevice, c->st));
-  double *const *bufs = (double *const *)base;
-  const int *active = (const int *)(base + table_bytes);
+  double **bufs = (double **)base;
+  int *active = (int *)(base + table_bytes);
+  double *t1 = (double *)(base + table_bytes + mask_bytes);
+  double *t3 = (double *)(base + table_bytes + mask_bytes + t1_bytes);
+  noalloc_table_kernel<<<1, 256, 0, c->st>>>((double *const *)c->dbufs.p, bufs, active, c->P, p,
+                                             c->hbufs[p * NBUF + BUF_L], c->hbufs[p * NBUF + BUF_R],
+                                             const_cast<double *>(psi_dev), out_dev, t1, t3);
+  CK(cudaGetLastError());
   CK(launch_gemm_f64((const GemmTile *)c->tn_g1.tiles[GEMM_64x64].p, c->tn_g1.ntiles[GEMM_64x64],
                      (const GemmTask *)c->dg1k.p, (const GemmSeg *)c->dg1s.p, bufs, active, c->st, GEMM_64x64));
   CK(launch_wstage_f64((const WTask *)c->dwt.p, (int)c->wl.tasks.size(), c->wl.max_rows, (const WTerm *)c->dwm.p,
                        bufs, active, c->st));
   CK(launch_gemm_f64((const GemmTile *)c->tn_g3.tiles[GEMM_64x64].p, c->tn_g3.ntiles[GEMM_64x64],
                      (const GemmTask *)c->dg3k.p, (const GemmSeg *)c->dg3s.p, bufs, active, c->st, GEMM_64x64));
+  c->launches += 4;
   return IDMRG_OK;
 }
