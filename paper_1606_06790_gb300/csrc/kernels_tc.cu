@@ -22,7 +22,9 @@
 //              memory (tcgen05.ld) and store it as FP32 (stage 1) or, through a
 //              row map, as FP64 into the output wavefunction (stage 3).
 //              Every mbarrier wait is bounded; a timeout sets the context's
-//              error word.
+//              error word, waits (bounded) for the CTA's copies in flight, and
+//              skips the epilogue; tensor memory is released unless the wait
+//              for the MMAs themselves ran out (they may still write it).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -164,7 +166,11 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
       tc::bulk_g2s(st + 2 * A_TILE, B + (int64_t)kb * 2 * B_TILE, 4u * 2 * B_TILE, &full[s]);
     };
     bool ok = true;
-    for (int kb = 0; kb < T.KB && kb < TC_STAGES - 1; ++kb) issue(kb);
+    int issued = 0, consumed = 0;  // K blocks whose copies were issued / whose MMAs were issued
+    for (int kb = 0; kb < T.KB && kb < TC_STAGES - 1; ++kb) {
+      issue(kb);
+      issued = kb + 1;
+    }
     for (int kb = 0; kb < T.KB && ok; ++kb) {
       const int kn = kb + TC_STAGES - 1;
       if (kn < T.KB) {
@@ -174,6 +180,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
           break;
         }
         issue(kn);
+        issued = kn + 1;
       }
       const int s = kb % TC_STAGES;
       if (!tc::mbar_wait(&full[s], (kb / TC_STAGES) & 1, WAIT_BUDGET)) {
@@ -200,19 +207,28 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
         }
       }
       tc::mma_commit(&empty[s]);
+      consumed = kb + 1;
     }
     if (!ok) {
       atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
-      abort_flag = 1;
+      atomicOr(&abort_flag, 1);
+      // wait (bounded) for this CTA's copies still in flight before it may exit
+      for (int j = consumed; j < issued; ++j) tc::mbar_wait(&full[j % TC_STAGES], (j / TC_STAGES) & 1, WAIT_BUDGET);
     }
     tc::mma_commit(&done);  // fires when every MMA issued above has completed
   }
-  // epilogue: every thread waits for the accumulator
+  // epilogue: every thread waits for the accumulator; if that wait runs out,
+  // MMAs may still write the accumulator, so neither the epilogue nor the
+  // TMEM release runs (the error word reports the timeout)
   const bool ready = tc::mbar_wait(&done, 0, WAIT_BUDGET);
-  if (!ready && lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+  if (!ready) {
+    atomicOr(&abort_flag, 2);
+    if (lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+  }
   __syncthreads();
   tc::fence_after_sync();
-  if (ready && !abort_flag) {
+  const int aborted = abort_flag;
+  if (!aborted) {
     const int row = tile.mt * TM + 32 * warp + lane;
     const int col0 = tile.nt * TC_TN;
     double *cbase = bufs[T.sb * NBUF + T.c_buf];
@@ -244,7 +260,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, TC_TN);
+  if (warp == 0 && !(aborted & 2)) tc::tmem_dealloc(tmem, TC_TN);
 }
 
 // ------------------------------------------- FP64-accurate digit-slice form
@@ -465,7 +481,11 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
                    &full[s]);
     };
     bool ok = true;
-    for (int kb = 0; kb < T.KB && kb < OZ_STAGES - 1; ++kb) issue(kb);
+    int issued = 0, consumed = 0;
+    for (int kb = 0; kb < T.KB && kb < OZ_STAGES - 1; ++kb) {
+      issue(kb);
+      issued = kb + 1;
+    }
     for (int kb = 0; kb < T.KB && ok; ++kb) {
       const int kn = kb + OZ_STAGES - 1;
       if (kn < T.KB) {
@@ -475,6 +495,7 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
           break;
         }
         issue(kn);
+        issued = kn + 1;
       }
       const int s = kb % OZ_STAGES;
       if (!tc::mbar_wait(&full[s], (kb / OZ_STAGES) & 1, WAIT_BUDGET)) {
@@ -497,18 +518,24 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
         }
       }
       tc::mma_commit(&empty[s]);
+      consumed = kb + 1;
     }
     if (!ok) {
       atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
-      abort_flag = 1;
+      atomicOr(&abort_flag, 1);
+      for (int j = consumed; j < issued; ++j) tc::mbar_wait(&full[j % OZ_STAGES], (j / OZ_STAGES) & 1, WAIT_BUDGET);
     }
   }
   if (threadIdx.x == 0) tc::mma_commit(&done);  // fires when every MMA issued above has completed
   const bool ready = tc::mbar_wait(&done, 0, WAIT_BUDGET);
-  if (!ready && lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+  if (!ready) {
+    atomicOr(&abort_flag, 2);
+    if (lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+  }
   __syncthreads();
   tc::fence_after_sync();
-  if (ready && !abort_flag) {
+  const int aborted = abort_flag;
+  if (!aborted) {
     const int row = tile.mt * TM + 32 * warp + lane;
     const int col0 = tile.nt * TC_TN;
     double *cbase = bufs[T.sb * NBUF + T.c_buf];
@@ -570,7 +597,7 @@ __global__ void __launch_bounds__(128) oz_gemm_kernel(const TcTile *__restrict__
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, OZ_TMEM_COLS);
+  if (warp == 0 && !(aborted & 2)) tc::tmem_dealloc(tmem, OZ_TMEM_COLS);
 }
 
 }  // namespace
