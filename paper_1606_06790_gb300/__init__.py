@@ -27,7 +27,8 @@ PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "fp64tc": 3}
 EXPORTED_SYMBOLS = [
     "idmrg_default_opts", "idmrg_create", "idmrg_destroy", "idmrg_last_error", "idmrg_set_stream",
     "idmrg_iteration", "idmrg_psi_layout", "idmrg_block_basis", "idmrg_block_to_host",
-    "idmrg_heff_apply", "idmrg_heff_apply_fp64", "idmrg_predict_wavefunction", "idmrg_lanczos_solve", "idmrg_get_psi",
+    "idmrg_heff_apply", "idmrg_heff_apply_fp64", "idmrg_predict_wavefunction", "idmrg_set_start_vector",
+    "idmrg_lanczos_solve", "idmrg_get_psi",
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
@@ -100,6 +101,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_heff_apply": (i, [vp, i, vp, vp]),
         "idmrg_heff_apply_fp64": (i, [vp, i, vp, vp, i]),
         "idmrg_predict_wavefunction": (i, [vp, i, P(d)]),
+        "idmrg_set_start_vector": (i, [vp, i, vp]),
         "idmrg_lanczos_solve": (i, [vp, i, P(d), P(i)]),
         "idmrg_get_psi": (i, [vp, i, P(d), sz]),
         "idmrg_truncate": (i, [vp, i, P(d), P(d), P(i)]),
@@ -282,6 +284,11 @@ class Context:
         out = np.zeros(self._n_of(p))
         self._check(self.lib.idmrg_predict_wavefunction(self.h, p, _dptr(out, C.c_double)), "predict_wavefunction")
         return out
+
+    def set_start_vector(self, p: int, psi) -> None:
+        """Start vector of the next solve (float64 CUDA tensor in the layout of
+        p, or all superblocks' vectors concatenated for p = -1)."""
+        self._check(self.lib.idmrg_set_start_vector(self.h, p, C.c_void_p(psi.data_ptr())), "set_start_vector")
 
     def lanczos_solve(self, p: int = -1):
         e = np.zeros(self._n_of(p))

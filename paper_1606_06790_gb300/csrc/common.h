@@ -202,6 +202,11 @@ cudaError_t lanczos_init(const LanczosDev &L, const double *const *start, cudaSt
 cudaError_t lanczos_ritz(const LanczosDev &L, double *const *out, cudaStream_t st);  // out = V y / |V y|
 cudaError_t lanczos_dot(const LanczosDev &L, const double *const *a, const double *const *b, double *res,
                         cudaStream_t st);  // res[s] = a_s . b_s
+// res[s] = ||x_s|| for the superblocks with mask[s] (mask may be NULL): part
+// holds S x nchunk partial sums, nchunk >= ceil(N_s / norm_chunk())
+cudaError_t launch_norms(const int64_t *Ns, int S, const double *const *x, const int *mask, double *part,
+                         int nchunk, double *res, cudaStream_t st);
+int64_t norm_chunk();
 
 // SVD (FP64 one-sided Jacobi), see kernels_svd.cu
 cudaError_t launch_svd_gather_sized(const SvdJob *jobs, int njobs, int64_t max_elems, double *const *bufs,

@@ -412,6 +412,17 @@ __global__ void sum_partials_kernel(const int64_t *Ns, int S, const double *part
   res[s] = acc;
 }
 
+// res[s] = sqrt(sum of the partials of x_s . x_s): Euclidean norms
+__global__ void norm_finish_kernel(const int64_t *Ns, int S, const double *part, int nchunk, double *res,
+                                   const int *mask) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || (mask && !mask[s])) return;
+  const int nch = (int)((Ns[s] + CH - 1) / CH);
+  double acc = 0.0;
+  for (int c = 0; c < nch; ++c) acc += part[(int64_t)s * nchunk + c];
+  res[s] = sqrt(acc);
+}
+
 // dst = src / sqrt(nrm2)  and resets the Lanczos state of that superblock
 __global__ void init_scale_kernel(LanczosDev L, const double *const *src, const double *nrm2) {
   const int s = blockIdx.y;
@@ -499,6 +510,17 @@ cudaError_t lanczos_init(const LanczosDev &L, const double *const *start, cudaSt
   init_scale_kernel<<<grid, LT, 0, st>>>(L, start, L.resid);
   return cudaGetLastError();
 }
+
+cudaError_t launch_norms(const int64_t *Ns, int S, const double *const *x, const int *mask, double *part,
+                         int nchunk, double *res, cudaStream_t st) {
+  if (S <= 0 || nchunk <= 0) return cudaGetLastError();
+  dim3 grid(nchunk, S);
+  norm_partial_kernel<<<grid, LT, 0, st>>>(Ns, S, x, part, nchunk, mask);
+  norm_finish_kernel<<<(S + 63) / 64, 64, 0, st>>>(Ns, S, part, nchunk, res, mask);
+  return cudaGetLastError();
+}
+
+int64_t norm_chunk() { return CH; }
 
 cudaError_t lanczos_ritz(const LanczosDev &L, double *const *out, cudaStream_t st) {
   dim3 grid(L.nchunk_max, L.S);

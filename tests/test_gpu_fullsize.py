@@ -3,7 +3,8 @@ times: random-bond chain l = 16, J ~ U[0.5, 1.5] (seed 1606), m = 256, all
 8 superblocks batched, run in lockstep with the FP64 oracle from n = 1 into
 the saturated regime (D = m).  FP64 and FP64_TC modes within 1e-10 per site,
 TF32x3 and BF16x3 within 1e-8 per site, every step; kept dimensions equal
-except where the zero threshold decides them (see _check_kept).
+except where the zero threshold decides them (see _check_kept); the fidelity
+error of the predicted start vector (Eq. fid1) per superblock from n = 3 on.
 
 Also the wider MPOs (w up to 20) and longer unit cells of the two cylinder
 models, at reduced m: J1-J2 on the 4-leg square cylinder (l = 8) and the
@@ -42,6 +43,17 @@ def _check_kept(ctx, g, r):
         assert np.all(lg[lo:min(hi, len(lg))] <= band * lg[0]), (r.n, p, kg, kr, lg[lo:hi] / lg[0])
 
 
+def _check_fidelity(g, r, tol_abs, tol_rel):
+    """Eq. fid1 per superblock: NaN on both sides while no prediction is made
+    (n < 3), else |eps_gpu - eps_oracle| <= tol_abs + tol_rel eps."""
+    fg, fr = np.asarray(g["fidelity"]), np.asarray(r.fidelity)
+    if r.n < 3:
+        assert np.all(np.isnan(fg)) and np.all(np.isnan(fr))
+        return
+    assert np.all(np.isfinite(fg)), (r.n, fg)
+    assert np.all(np.abs(fg - fr) <= tol_abs + tol_rel * np.abs(fr)), (r.n, fg, fr)
+
+
 def _check(ctx, g, r, tol):
     sites = 2 * r.n + 2
     assert g["n"] == r.n
@@ -61,11 +73,19 @@ def test_bench_workload_all_precisions_against_oracle():
     ref = ParallelIDMRG.from_mpo(mpo, m=m)
     ctxs = {p: context(mpo, m, prec=p) for p in ("fp64", "fp64tc", "tf32x3", "bf16x3")}
     tol = {"fp64": 1e-10, "fp64tc": 1e-10, "tf32x3": 1e-8, "bf16x3": 1e-8}
+    # Eq. fid1: the prediction divides by lambda'' down to the zero threshold
+    # (1e-12 lambda_max), which magnifies the rounding of the smallest singular
+    # values of two correct implementations (measured: 2e-10 at eps = 7e-9);
+    # a wrong reading of R3/R4 moves eps by more than 1e-6 (CPU test
+    # test_wrong_prediction_reading_is_visible)
+    ftol = {"fp64": (1e-9, 1e-3), "fp64tc": (1e-9, 1e-3), "tf32x3": (1e-8, 1e-3), "bf16x3": (1e-8, 1e-3)}
     saturated = 0
     for _ in range(16):
         r = ref.step()
         for p, ctx in ctxs.items():
-            _check(ctx, ctx.unit_cell_step(), r, tol[p])
+            g = ctx.unit_cell_step()
+            _check(ctx, g, r, tol[p])
+            _check_fidelity(g, r, *ftol[p])
         # the cut at m (less the multiplet it would split) decides D
         saturated += int(np.min(r.kept) >= 0.9 * m)
     assert saturated >= 3          # several steps in the benchmarked regime

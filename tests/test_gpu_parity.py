@@ -216,3 +216,49 @@ def test_seed_changes_start_not_result():
         assert np.max(np.abs(ga["energy"] - gb["energy"])) < 1e-10
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64tc"])
+def test_prediction_parity(prec):
+    """Step 3' (Eq. wfprediction, readings R3 and R4) against the oracle: the
+    fidelity error of Eq. fid1 per superblock and step, the Lanczos matvec
+    counts it buys, and ||psi~|| before each solve (idmrg_predict_wavefunction
+    with norm_out) -- quantities the converged energies do not depend on.  A
+    wrong lambda^(n-2) or a U taken from the wrong superblock moves the
+    fidelity error by orders of magnitude (the CPU test
+    test_wrong_prediction_reading_is_visible plants that mistake in the
+    oracle)."""
+    mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 1606), 8)
+    ctx, ref, out = _run_both(mpo, 48, 14, prec=prec)
+    for g, r in out:
+        _compare(g, r)
+        if r.n < 3:
+            assert np.all(np.isnan(g["fidelity"]))
+            continue
+        fg, fr = g["fidelity"], r.fidelity
+        # lambda'' is inverted down to the zero threshold, which magnifies the
+        # rounding of the smallest singular values (see test_gpu_fullsize)
+        assert np.all(np.abs(fg - fr) <= 1e-9 + 1e-3 * np.abs(fr)), (r.n, fg, fr)
+        # the same start vector and operator: matvec counts within the
+        # rounding of the two re-orthogonalisation schemes
+        assert np.all(np.abs(g["iters"] - r.iters) <= 2), (r.n, g["iters"], r.iters)
+    ctx.close()
+    # the prediction pays (Sec. 4: ~3x fewer iterations): the oracle without it
+    nopred = ParallelIDMRG.from_mpo(mpo, m=48, predict=False)
+    its = [nopred.step().iters for _ in range(14)]
+    late_gpu = np.mean([np.mean(g["iters"]) for g, r in out if r.n >= 8])
+    late_np = np.mean([np.mean(x) for x in its[7:]])
+    assert late_gpu < 0.7 * late_np, (late_gpu, late_np)
+    # ||psi~|| through the step-by-step calls
+    ctx = context(mpo, 48, prec=prec)
+    ref = ParallelIDMRG.from_mpo(mpo, m=48)
+    for _ in range(12):
+        want = np.array([np.linalg.norm(ref.start_vector(p)) for p in range(ref.P)])
+        got = ctx.predict_wavefunction(-1)
+        assert np.all(np.abs(got - want) <= 1e-9 * want), (ref.n, got, want)
+        ctx.lanczos_solve(-1)
+        ctx.truncate(-1)
+        ctx.update_environments(-1)
+        ctx.advance()
+        ref.step()
+    ctx.close()

@@ -135,3 +135,40 @@ def test_splitmix64_published_vectors():
     g = GOLDEN["splitmix64_seed0"]["values_hex"]
     assert [int(x) for x in rng.splitmix64(0, 3)] == [int(h, 16) for h in g]
     assert [int(x) for x in rng.splitmix64(1234567, 5)] == GOLDEN["splitmix64_seed1234567"]["values"]
+
+
+def test_wrong_prediction_reading_is_visible():
+    """The prediction parity test on the GPU compares Eq. fid1 per superblock
+    within 1e-9 + 1e-3 eps.  Planting a wrong reading of R4 in the oracle --
+    lambda'' and u taken from superblock i instead of i + 1 -- moves the
+    fidelity error far outside that bound (and costs Lanczos iterations), so a
+    GPU path with that mistake would fail there even though its converged
+    energies stay correct."""
+    from oracle.idmrg import predict
+
+    class WrongR4(ParallelIDMRG):
+        def start_vector(self, p):
+            if self.n < 3 or not self.use_prediction:
+                return super().start_vector(p)
+            from oracle.idmrg import sector_mask
+            L, W1, W2, R = self.superblock(p)
+            mask = sector_mask(L.q, self.qp, R.q, self.target)
+            j = (p + 1) % self.P
+            a, b, c = self.prev[p], self.prev[j], self.prev2[p]   # lambda'' of i, not i + 1
+            if c.lam.shape[0] != b.U.shape[0]:
+                return super().start_vector(p)
+            v = predict(a.lam, a.V, b.U, b.lam, c.lam, self.zero_rel)
+            return np.where(mask, v, 0.0)
+
+    mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 1606), 8)
+    good = ParallelIDMRG.from_mpo(mpo, m=24)
+    bad = WrongR4.from_mpo(mpo, m=24)
+    moved = 0
+    for _ in range(12):
+        rg, rb = good.step(), bad.step()
+        if rg.n < 5:
+            continue
+        assert np.max(np.abs(rg.energies - rb.energies)) / (2 * rg.n + 2) < 1e-10  # energies agree
+        d = np.abs(rg.fidelity - rb.fidelity)
+        moved += int(np.any(d > 1e-9 + 1e-3 * np.abs(rg.fidelity) + 1e-6))
+    assert moved >= 6
