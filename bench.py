@@ -3,18 +3,20 @@
 
 A step is one parallel iteration n (Sec. 3): the l/2 two-site superblocks
 of the unit cell are solved (Lanczos on H_eff psi), truncated by SVD and
-renormalised, all through the C ABI of libidmrg.  Workload: S=1/2 random-bond
-Heisenberg chain, l = 16 (8 superblocks per step), J_k ~ U[0.5, 1.5] from
-PCG64 seed 1606, m = 256, measured in the saturated regime (D = m).
+renormalised, all through the C ABI of libidmrg.  Default workload: the
+spin-1/2 Heisenberg model on the kagome YC8 cylinder (the paper's benchmark
+model, Sec. 4; 12-site unit cell, 6 superblocks per step, MPO bond dimension
+up to 20) at m = 2048, measured in the saturated regime (D = m).
 
 The headline is the mixed-precision path (H_eff psi on the tensor cores in
-TF32x3, Lanczos and SVD in FP64); the same run times the FP64 path on the
-same workload and reports the largest |dE/site| between the two.
+BF16x3, Lanczos and SVD in FP64); the same run times the plain FP64 path from
+the state the timed region started from and reports the largest |dE/site|
+between the two at equal n.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|bf16x3|fp64|fp64tc] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec P] [--impl reference]
 
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own
-disorder realisation (seed 1606 + rank): independent problems, no exchange.
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica (the random-bond chain: its own disorder realisation); no exchange.
 """
 from __future__ import annotations
 
@@ -22,17 +24,27 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "iDMRG unit-cell steps/sec and H_eff·ψ TFLOP/s (mixed vs FP64) at |ΔE/site|≤1e-8"
-WORKLOAD = "randchain_l16_m256"
-SATURATE = 11            # iterations until every block holds m states (n >= log2 m + 2)
+CHAIN = "randchain_l16_m256"
+# workload -> default precision of the headline, Krylov cap of the FP64 runs
+WORKLOADS = {
+    "kagome_yc8_l12_m2048": dict(prec="bf16x3", m=2048, maxit=300),
+    "yc4_j1j2_l8_m1024": dict(prec="bf16x3", m=1024, maxit=300),
+    CHAIN: dict(prec="tf32x3", m=256, maxit=300),
+}
+DEFAULT_WORKLOAD = "kagome_yc8_l12_m2048"
+SATURATE_MAX = 40        # iterations allowed to reach D >= 0.9 m
+PAPER_LANCZOS_ITERS = 40  # Sec. 4: about 40 Lanczos iterations per solve with the prediction
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 HBM_FALLBACK, BF16_FALLBACK, BF16_SUST_FALLBACK = 6800.0, 1900.0, 1700.0
 FP64_ALU_PEAK = 152 * 2070e6 * 4 / 1e9   # GFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
@@ -46,38 +58,6 @@ def peaks() -> dict:
                 "bf16_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]), "src": "measured"}
     except Exception:
         return {"hbm": HBM_FALLBACK, "bf16": BF16_FALLBACK, "bf16_sustained": BF16_SUST_FALLBACK, "src": "fallback"}
-
-
-def rank_seed(rank: int) -> int:
-    """Disorder realisation of a rank: independent problems, one per GPU."""
-    return 1606 + rank
-
-
-def make_workload(rank: int, name: str = WORKLOAD):
-    """The MPO of a named workload; the random-bond chain draws its couplings
-    from the rank's seed (independent realisations), the cylinder is fixed."""
-    from workloads import build_mpo, make_config, random_chain_bonds
-    if name == WORKLOAD:
-        seed = rank_seed(rank)
-        return build_mpo(random_chain_bonds(16, 0.5, 1.5, seed), 16), seed
-    mpo, _ = make_config(name)
-    return mpo, None
-
-
-def job_value(world: int, steps: int, seconds: float) -> float:
-    """Whole-job throughput: every rank ran `steps` steps of its own problem;
-    `seconds` is the slowest rank's time."""
-    return world * steps / seconds
-
-
-def reduce_max(values, dist, device):
-    """Max over ranks of a few timings (the job takes as long as its slowest rank)."""
-    import torch
-    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
-        return [float(v) for v in values]
-    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return [float(x) for x in t.tolist()]
 
 
 class Clocks:
@@ -196,44 +176,169 @@ def heff_roofline(prof: dict, prec: str, pk: dict):
     return r
 
 
-def cpu_baseline(mpo, m: int, budget_s: float = 25.0, timed_steps: int = 2):
-    """The FP64 oracle as it stands on this host's cores: iterate from n = 1
-    (untimed) into the saturated regime, then time up to `timed_steps` steps."""
-    from oracle.idmrg import ParallelIDMRG
-    cores = len(os.sched_getaffinity(0))
-    ref = ParallelIDMRG.from_mpo(mpo, m=m)
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def saturate(ctx, m: int):
+    """Unit-cell steps from n = 1 until every superblock keeps >= 0.9 m states
+    (the cut at m less the multiplet it would split), at most SATURATE_MAX."""
+    steps = 0
+    while steps < SATURATE_MAX:
+        r = ctx.unit_cell_step()
+        steps += 1
+        if min(int(k) for k in r["kept"]) >= 0.9 * m:
+            break
+    return steps
+
+
+def rank_seed(rank: int) -> int:
+    """Disorder realisation of a rank on the random-bond chain: independent
+    problems, one per GPU."""
+    return 1606 + rank
+
+
+def make_workload(rank: int, name: str):
+    """The MPO of a named workload; the random-bond chain draws its couplings
+    from the rank's seed (independent realisations), the cylinders are fixed."""
+    from workloads import build_mpo, make_config, random_chain_bonds
+    if name == CHAIN:
+        seed = rank_seed(rank)
+        return build_mpo(random_chain_bonds(16, 0.5, 1.5, seed), 16), seed
+    mpo, _ = make_config(name)
+    return mpo, None
+
+
+def job_value(world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank ran `steps` steps of its own problem;
+    `seconds` is the slowest rank's time."""
+    return world * steps / seconds
+
+
+def reduce_max(values, dist, device):
+    """Max over ranks of a few timings (the job takes as long as its slowest rank)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def oracle_sample(ref, p: int):
+    """Times (s) of the oracle's pieces of one superblock solve at its current
+    state: the start vector (Step 3'), one H_eff psi (Step 3), the
+    truncation (Step 4) and both block updates (Step 6).  The oracle is dense,
+    so its cost depends only on the shapes."""
+    import numpy as np
+    from oracle.idmrg import heff_apply, truncate, update_left, update_right
+    L, W1, W2, R = ref.superblock(p)
     t0 = time.perf_counter()
-    while ref.n <= SATURATE:
-        ref.step()
-        if time.perf_counter() - t0 > 4 * budget_s:
-            break
-    times = []
-    for _ in range(timed_steps):
-        t = time.perf_counter()
-        ref.step()
-        times.append(time.perf_counter() - t)
-        if sum(times) > budget_s:
-            break
-    per = sum(times) / len(times)
-    return ref, {"value": 1.0 / per, "unit": "unit-cell steps/s", "cores": cores, "kind": "oracle",
-                 "sample": f"FP64 numpy oracle, same workload, {len(times)} step(s) timed at "
-                           f"n={ref.n - len(times)}..{ref.n - 1} after {SATURATE} untimed steps from n=1",
-                 "sec_per_step": per}
+    v = ref.start_vector(p)
+    t1 = time.perf_counter()
+    y = heff_apply(L, W1, W2, R, v)
+    t2 = time.perf_counter()
+    psi = v / np.linalg.norm(v)
+    tr = truncate(psi, L.q, ref.qp, R.q, ref.m, ref.tie_rel, ref.zero_rel, ref.target)
+    t3 = time.perf_counter()
+    update_left(L, W1, tr.U, tr.q)
+    update_right(R, W2, tr.V, ref.target - tr.q)
+    t4 = time.perf_counter()
+    del y
+    return {"start": t1 - t0, "matvec": t2 - t1, "truncate": t3 - t2, "update": t4 - t3}
 
 
-def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores, same metric and workload."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    if args.workload != WORKLOAD:
-        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle needs minutes per unit-cell step "
-                          f"at {args.workload}; its timed arm runs on {WORKLOAD}"}), flush=True)
-        return
-    mpo, seed = make_workload(0)
+def step_estimate(P: int, s: dict, iters: float) -> float:
+    """Seconds of one oracle unit-cell step from the pieces of one superblock:
+    P superblocks x (start + iters matvecs + truncation + updates).  The
+    Lanczos vector work of the oracle (O(k N) per iteration) is far below one
+    dense matvec (O(w d^2 D^3)) and is left out."""
+    return P * (s["start"] + iters * s["matvec"] + s["truncate"] + s["update"])
+
+
+_ONE_THREAD = r"""
+import sys, time, numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle.idmrg import Block, heff_apply
+D, w1, w2, d = (int(x) for x in sys.argv[2:6])
+g = np.random.default_rng(0)
+L = Block(g.standard_normal((w1, D, D)), np.zeros(D, dtype=np.int64))
+R = Block(g.standard_normal((w2, D, D)), np.zeros(D, dtype=np.int64))
+W1 = g.standard_normal((w1, w1, d, d)); W2 = g.standard_normal((w1, w2, d, d))
+x = g.standard_normal((D, d, d, D))
+t = time.perf_counter(); heff_apply(L, W1, W2, R, x); print(time.perf_counter() - t)
+"""
+
+
+def thread_ratio(D: int, w1: int, w2: int, d: int) -> dict:
+    """Time of one dense oracle H_eff psi on synthetic blocks of size D with
+    all host threads and with one (OPENBLAS/OMP_NUM_THREADS=1), in separate
+    processes: the 1-thread factor of the oracle at this shape."""
+    out = {}
+    for label, env in (("all", {}), ("one", {"OPENBLAS_NUM_THREADS": "1", "OMP_NUM_THREADS": "1",
+                                             "MKL_NUM_THREADS": "1"})):
+        e = dict(os.environ)
+        e.update(env)
+        r = subprocess.run([sys.executable, "-c", _ONE_THREAD, ROOT, str(D), str(w1), str(w2), str(d)],
+                           capture_output=True, text=True, env=e, timeout=900)
+        out[label] = float(r.stdout.strip().splitlines()[-1])
+    return out
+
+
+def cpu_baseline(mpo, m: int, path: str, iters: float, n: int, P: int):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the same workload: it reads the GPU run's saved state at the start of the
+    timed region (the file as data) and times the pieces of one superblock's
+    step there; the unit-cell step time is that of P superblocks with `iters`
+    matvecs each (the FP64 leg's measured Lanczos count at the same n).  The
+    1-thread figure scales it by the oracle's 1-thread / all-thread time of
+    one H_eff psi at half the size."""
+    from oracle.checkpoint import load_state
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    ref = load_state(path, mpo, m)
+    s = oracle_sample(ref, 0)
+    L, W1, W2, R = ref.superblock(0)
+    D = L.op.shape[1]
+    w1, w2 = L.op.shape[0], R.op.shape[0]
+    del ref, L, R
+    per = step_estimate(P, s, iters)
+    tr = thread_ratio(max(D // 2, 1), w1, w2, mpo.d)
+    one = per * tr["one"] / tr["all"]
+    return {"value": 1.0 / per, "unit": "unit-cell steps/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": (f"FP64 numpy oracle on the GPU run's saved state at n={n} (read as data): superblock 0's "
+                       f"start vector, one H_eff psi, truncation and block updates timed "
+                       f"({s['start']:.2f}+{s['matvec']:.2f}+{s['truncate']:.2f}+{s['update']:.2f} s), "
+                       f"step = {P} superblocks x ({iters:.1f} matvecs + the rest); {iters:.1f} = the FP64 "
+                       f"leg's mean Lanczos count at that n"),
+            "sec_per_step": per, "sample_wall_s": time.perf_counter() - t0,
+            "one_thread": {"value": 1.0 / one, "sec_per_step": one,
+                           "how": f"x {tr['one'] / tr['all']:.2f}: one dense H_eff psi at D={max(D // 2, 1)} took "
+                                  f"{tr['one']:.2f} s on 1 thread and {tr['all']:.2f} s on {cores}"}}
+
+
+def run_reference_full(args, mpo, seed):
+    """--impl reference on the random-bond chain (m = 256): whole oracle steps,
+    n = 1 into the saturated regime untimed, then W untimed and K timed."""
     from oracle.idmrg import ParallelIDMRG
     ref = ParallelIDMRG.from_mpo(mpo, m=args.m)
-    while ref.n <= SATURATE:
+    while ref.n <= 11:
         ref.step()
     for _ in range(args.warmup):
         ref.step()
@@ -246,10 +351,80 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": "unit-cell steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "ell": 16, "m": args.m, "solves_per_step": 8, "seed": seed,
-                       "regime": f"saturated (n > {SATURATE})"},
+            "config": {"workload": CHAIN, "ell": 16, "m": args.m, "solves_per_step": 8, "seed": seed,
+                       "regime": "saturated (n > 11)"},
             "cpu_baseline": {"value": v, "unit": "unit-cell steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} timed oracle steps after {SATURATE}+{args.warmup} untimed"},
+                             "cpu_model": cpu_model(),
+                             "sample": f"{args.steps} timed oracle steps after 11+{args.warmup} untimed"},
+            "e2e": {"value": v, "unit": "unit-cell steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same metric and
+    workload, each step a bounded sample: one dense H_eff psi of a saturated
+    superblock (D = m, the MPO channels of superblock 0) timed per step, the
+    start vector, truncation and block updates timed once in the warm-up; a
+    unit-cell step is l/2 superblocks x (PAPER_LANCZOS_ITERS matvecs + the
+    rest).  The oracle is dense, so synthetic blocks of the saturated shape
+    cost what the real ones do."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle.idmrg import Block, heff_apply, truncate, update_left, update_right
+    name = args.workload if args.workload != "disorder64" else CHAIN
+    mpo, seed = make_workload(0, name)
+    m = args.m
+    if name == CHAIN:
+        return run_reference_full(args, mpo, seed)
+    ell = len(mpo.W)
+    P = ell // 2
+    d = mpo.d
+    g = np.random.default_rng(20160622)
+    # superblock 0 at a saturated iteration: its MPO channels, D = m on both
+    # sides, charges spread as in a U(1) block (the dense oracle ignores them
+    # apart from the truncation's sectors)
+    n = 2 * ell + 1
+    c1, c2 = n % ell, (n + 1) % ell
+    w1, w2 = mpo.W[c1].shape[0], mpo.W[c2].shape[1]
+    q = np.sort(np.clip(np.round(g.normal(0.0, 3.0, m)).astype(np.int64) * 2, -40, 40))
+    L = Block(g.standard_normal((w1, m, m)) / m, q)
+    R = Block(g.standard_normal((w2, m, m)) / m, -q[::-1].copy())
+    from oracle.idmrg import sector_mask
+    mask = sector_mask(L.q, mpo.phys_charge.astype(np.int64), R.q)
+    x = np.where(mask, g.standard_normal(mask.shape), 0.0)
+    x /= np.linalg.norm(x)
+    W1, W2 = mpo.W[c1], mpo.W[c2]
+    t = time.perf_counter()
+    tr = truncate(x, L.q, mpo.phys_charge.astype(np.int64), R.q, m)
+    t_tr = time.perf_counter() - t
+    t = time.perf_counter()
+    update_left(L, W1, tr.U, tr.q)
+    update_right(R, W2, tr.V, -tr.q)
+    t_up = time.perf_counter() - t
+    for _ in range(args.warmup):
+        heff_apply(L, W1, W2, R, x)
+    samples = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        heff_apply(L, W1, W2, R, x)
+        t_mv = time.perf_counter() - t
+        samples.append(step_estimate(P, {"start": 0.0, "matvec": t_mv, "truncate": t_tr, "update": t_up},
+                                     PAPER_LANCZOS_ITERS))
+    per = sum(samples) / len(samples)
+    v = 1.0 / per
+    cores = len(os.sched_getaffinity(0))
+    sample = (f"per step: one dense FP64 H_eff psi of superblock 0 at D={m} (w={w1},{w2}) timed; truncation "
+              f"({t_tr:.2f} s) and block updates ({t_up:.2f} s) timed once; step = {P} superblocks x "
+              f"({PAPER_LANCZOS_ITERS} matvecs, the paper's count with the prediction, + the rest)")
+    line = {"metric": METRIC, "value": v, "unit": "unit-cell steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": name, "ell": ell, "m": m, "solves_per_step": P, "seed": seed,
+                       "regime": "saturated shape (D = m)"},
+            "cpu_baseline": {"value": v, "unit": "unit-cell steps/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": v, "unit": "unit-cell steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -266,7 +441,7 @@ def run_batch(args, pkg, dev, local, world, rank, dist):
     threads = max(1, min(16, len(os.sched_getaffinity(0))))
     ctxs = [pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=args.prec, lanczos_maxit=160,
                         stream=torch.cuda.Stream()) for _, mpo, m in work]
-    for _ in range(SATURATE + max(args.warmup, 3)):
+    for _ in range(11 + max(args.warmup, 3)):
         pkg.batch_step(ctxs, threads)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     launches0 = sum(c.launch_count() for c in ctxs)
@@ -302,7 +477,7 @@ def run_batch(args, pkg, dev, local, world, rank, dist):
             "config": {"workload": "disorder64", "realisations": len(ctxs),
                        "ell": "8/12/16/24 by r mod 4", "m": "128/256/512 by (r div 4) mod 3",
                        "couplings": "J ~ U[0.2, 1.8], PCG64 seed 1000 + r", "host_threads": threads,
-                       "streams": len(ctxs), "regime": f"n > {SATURATE + max(args.warmup, 3)}",
+                       "streams": len(ctxs), "regime": f"n > {11 + max(args.warmup, 3)}",
                        "kept_max": int(max(int(max(r["kept"])) for r in reps)),
                        "timing": "wall clock per batch step, device synchronised on both sides",
                        "l2": "flushed before every timed step (256 MiB write, outside the timing)"},
@@ -316,64 +491,6 @@ def run_batch(args, pkg, dev, local, world, rank, dist):
         c.close()
     if world > 1:
         dist.destroy_process_group()
-
-
-def timed_run(pkg, mpo, m: int, prec: str, steps: int, warmup: int, dev, flush, dist, with_clocks: bool, local: int):
-    """Saturate, warm up, then two timed regions of `steps` unit-cell steps,
-    each step bracketed by CUDA events on the context's stream with the L2
-    flushed before it (outside the events): the first without per-class
-    timers (the step time, e2e wall clock and clocks), the second with the
-    per-class event timers on (kernel classes and rooflines)."""
-    import torch
-    ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=prec)
-    for _ in range(SATURATE):
-        ctx.unit_cell_step()
-    for _ in range(max(warmup, 3)):
-        ctx.unit_cell_step()
-    stream = ctx.stream
-
-    def region(profiled: bool, clocks):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        launches0 = ctx.launch_count()
-        h2d0, d2h0 = ctx.transfer_bytes()
-        ctx.profile_enable(profiled)
-        if dist is not None and dist.is_initialized():
-            dist.barrier()
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        torch.cuda.nvtx.range_push("timed")
-        wall, reports = [], []
-        for k in range(steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            ev[k][0].record(stream)
-            reports.append(ctx.unit_cell_step())
-            ev[k][1].record(stream)
-            torch.cuda.synchronize()
-            wall.append(time.perf_counter() - t)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        clk = clocks.stop() if clocks else None
-        if dist is not None and dist.is_initialized():
-            dist.barrier()
-        out = {"step_ms": sum(a.elapsed_time(b) for a, b in ev), "wall_s": sum(wall), "reports": reports,
-               "clocks": clk, "launches": ctx.launch_count() - launches0}
-        h2d1, d2h1 = ctx.transfer_bytes()
-        out["h2d"] = (h2d1 - h2d0) // steps
-        out["d2h"] = (d2h1 - d2h0) // steps
-        if profiled:
-            out["prof"] = ctx.profile_read()
-        ctx.profile_enable(False)
-        return out
-
-    res = region(False, Clocks(local) if with_clocks else None)
-    prof = region(True, None)
-    res["prof"] = prof["prof"]
-    res["prof_step_ms"] = prof["step_ms"]
-    res["ctx"] = ctx
-    return res
 
 
 def observables_leg(ctx, ell: int) -> dict:
@@ -411,23 +528,114 @@ def max_de_per_site(ra, rb):
     return worst
 
 
+def timed_run(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, prof_steps: int, dev, flush, dist,
+              local: int, save_path=None):
+    """Saturate (D = m), warm up, save the state if asked, then two timed
+    regions, each step bracketed by CUDA events on the context's stream with
+    the L2 flushed before it (outside the events): `steps` steps without
+    per-class timers (the step time, e2e wall clock and clocks), then
+    `prof_steps` steps with the per-class event timers on (kernel classes and
+    rooflines)."""
+    import torch
+    ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=prec, lanczos_maxit=maxit)
+    nsat = saturate(ctx, m)
+    for _ in range(max(warmup, 3)):
+        ctx.unit_cell_step()
+    n0 = ctx.iteration
+    if save_path:
+        ctx.save(save_path)
+    stream = ctx.stream
+
+    def region(k_steps: int, profiled: bool, clocks):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
+        launches0 = ctx.launch_count()
+        h2d0, d2h0 = ctx.transfer_bytes()
+        ctx.profile_enable(profiled)
+        if dist is not None and dist.is_initialized():
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        torch.cuda.nvtx.range_push("timed")
+        wall, reports = [], []
+        for k in range(k_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ev[k][0].record(stream)
+            reports.append(ctx.unit_cell_step())
+            ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            wall.append(time.perf_counter() - t)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        clk = clocks.stop() if clocks else None
+        if dist is not None and dist.is_initialized():
+            dist.barrier()
+        out = {"step_ms": sum(a.elapsed_time(b) for a, b in ev), "wall_s": sum(wall), "reports": reports,
+               "clocks": clk, "launches": ctx.launch_count() - launches0, "steps": k_steps}
+        h2d1, d2h1 = ctx.transfer_bytes()
+        out["h2d"] = (h2d1 - h2d0) // k_steps
+        out["d2h"] = (d2h1 - d2h0) // k_steps
+        if profiled:
+            out["prof"] = ctx.profile_read()
+        ctx.profile_enable(False)
+        return out
+
+    res = region(steps, False, Clocks(local))
+    prof = region(prof_steps, True, None)
+    res.update(prof=prof["prof"], prof_step_ms=prof["step_ms"], prof_steps=prof_steps, ctx=ctx, n0=n0,
+               saturate_steps=nsat)
+    return res
+
+
+def fp64_leg(pkg, mpo, m: int, maxit: int, path: str, steps: int):
+    """The plain FP64 path from the state the mixed run's timed region started
+    from (idmrg_load of the same file): `steps` unit-cell steps timed with
+    CUDA events on its stream."""
+    import torch
+    ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec="fp64", lanczos_maxit=maxit)
+    ctx.load(path)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ctx.profile_enable(True)
+    torch.cuda.synchronize()
+    reports = []
+    for k in range(steps):
+        ev[k][0].record(ctx.stream)
+        reports.append(ctx.unit_cell_step())
+        ev[k][1].record(ctx.stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ctx.close()
+    return {"step_ms": ms, "reports": reports, "prof": prof, "steps": steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3", "fp64tc"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS) + ["disorder64"],
+                    help="kagome YC8 cylinder m=2048 (default), J1-J2 YC4 cylinder m=1024, random-bond chain "
+                         "l=16 m=256, or 64 disorder realisations stepped together")
+    ap.add_argument("--prec", default=None, choices=["fp64", "tf32x3", "bf16x3", "fp64tc"],
+                    help="headline precision (default: bf16x3 on the cylinders, tf32x3 on the chains)")
     ap.add_argument("--m", type=int, default=None, help="kept states (default: the workload's m)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "yc4_j1j2_l8_m1024", "disorder64"],
-                    help="random-bond chain l=16 m=256 (the metric's workload), the YC4 J1-J2 cylinder, "
-                         "or 64 disorder realisations stepped together")
+    ap.add_argument("--prof-steps", type=int, default=3, help="steps of the second region (class timers on)")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 steps from the timed region's start")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--no-observables", action="store_true")
+    ap.add_argument("--observables", choices=["auto", "on", "off"], default="auto",
+                    help="uniform-MPS observables of the final state (auto: on for the chain only; at m = 2048 "
+                         "the launch-bound transfer-spectrum iteration takes minutes)")
     args = ap.parse_args()
+    wl = WORKLOADS.get(args.workload, WORKLOADS[CHAIN])
     if args.m is None:
-        args.m = 256 if args.workload == WORKLOAD else 1024
+        args.m = wl["m"] if args.workload != "disorder64" else 256
+    if args.prec is None:
+        args.prec = wl["prec"] if args.workload != "disorder64" else "tf32x3"
     if args.impl == "reference":
         return run_reference(args)
 
@@ -448,31 +656,37 @@ def main():
     mpo, seed = make_workload(rank, args.workload)
     ell = len(mpo.W)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    run = timed_run(pkg, mpo, args.m, args.prec, args.steps, args.warmup, dev, flush, dist, True, local)
-    cmp = None
-    if args.prec != "fp64" and not args.no_fp64_compare:
-        cmp = timed_run(pkg, mpo, args.m, "fp64", args.steps, args.warmup, dev, flush, dist, False, local)
+    tmpdir = tempfile.mkdtemp(prefix="idmrg_bench_")
+    state = os.path.join(tmpdir, f"state_rank{rank}.ck")
+    run = timed_run(pkg, mpo, args.m, args.prec, wl["maxit"], args.steps, args.warmup, max(args.prof_steps, 1),
+                    dev, flush, dist, local, save_path=state)
     t_dev, t_wall = run["step_ms"] * 1e-3, run["wall_s"]
-    t_dev64 = cmp["step_ms"] * 1e-3 if cmp else 0.0
-    t_dev, t_wall, t_dev64 = reduce_max([t_dev, t_wall, t_dev64], dist, dev)
+    t_dev, t_wall = reduce_max([t_dev, t_wall], dist, dev)
     pk = peaks()
     prof = run["prof"]
+    ps = run["prof_steps"]
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    roof = class_roofline(dom, prof[dom], args.prec, pk)
-    kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+    kernels = {k: {"ms_per_step": v["ms"] / ps, "launches_per_step": v["launches"] / ps,
                    "gflops_per_s": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0,
                    "gbytes_per_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
                for k, v in prof.items()}
     ctx = run["ctx"]
     flops, _ = ctx.heff_cost(-1)
     last = run["reports"][-1]
+    first = run["reports"][0]
+    want_obs = args.observables == "on" or (args.observables == "auto" and args.workload == CHAIN)
+    obs = observables_leg(ctx, ell) if (rank == 0 and want_obs) else None
+    ctx.close()
+    del run["ctx"]
+    torch.cuda.empty_cache()
+    cmp = None
+    if args.prec != "fp64" and not args.no_fp64_compare:
+        cmp = fp64_leg(pkg, mpo, args.m, wl["maxit"], state, max(args.fp64_steps, 1))
     if rank != 0:
-        ctx.close()
-        if cmp is not None:
-            cmp["ctx"].close()
         if world > 1:
             dist.destroy_process_group()
         return
+    heff = heff_roofline(prof, args.prec, pk)
     line = {
         "metric": METRIC, "value": job_value(world, args.steps, t_dev), "unit": "unit-cell steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps,
@@ -480,40 +694,55 @@ def main():
         "dtype": {"fp64": "f64", "fp64tc": "bf16-digits(f64)+f64"}.get(args.prec, f"{args.prec}+f64"),
         "data": "synthetic",
         "config": {"workload": args.workload, "ell": ell, "m": args.m, "solves_per_step": ell // 2, "seed": seed,
-                   "regime": f"saturated (n > {SATURATE}, D = {int(max(last['kept']))})",
+                   "regime": f"saturated: D >= 0.9 m after {run['saturate_steps']} steps, "
+                             f"{max(args.warmup, 3)} warm-up steps, timed n = {first['n']}..{last['n']}, "
+                             f"kept {int(min(last['kept']))}..{int(max(last['kept']))}",
                    "precision": args.prec + ("" if args.prec == "fp64" else " H_eff psi; FP64 Lanczos and SVD"),
                    "fp64_restart_matvecs": "BF16 digit slices on the tensor cores (FP64-accurate)"
                    if args.prec in ("tf32x3", "bf16x3") else None,
-                   "parallelism": f"{world} independent realisation(s), one per GPU",
-                   "l2": "flushed before every timed step (256 MiB write, outside the events)"},
-        "roofline": roof,
-        "roofline_heff": heff_roofline(prof, args.prec, pk),
+                   "parallelism": f"{world} independent replica(s), one per GPU",
+                   "l2": "flushed before every timed step (256 MiB write, outside the events); the working set "
+                         "(environments, Krylov vectors) is far larger than L2"},
+        "roofline": heff,
+        "roofline_dominant": class_roofline(dom, prof[dom], args.prec, pk),
+        "roofline_classes": {k: class_roofline(k, v, args.prec, pk) for k, v in prof.items() if v["ms"] > 0},
         "gpu_launches": run["launches"],
         "e2e": {"value": job_value(world, args.steps, t_wall), "unit": "unit-cell steps/s",
                 "h2d_bytes_per_step": run["h2d"], "d2h_bytes_per_step": run["d2h"],
                 "note": "wall clock around idmrg_unit_cell_step: host block tables in, step report out"},
         "kernels": kernels,
-        "kernels_note": ("per-class CUDA-event timers of a second timed region of the same length "
-                         f"({run['prof_step_ms'] / args.steps:.2f} ms per step with the timers on)"),
-        "svd": ctx.svd_stats(),
+        "kernels_note": (f"per-class CUDA-event timers of a second timed region of {ps} step(s) "
+                         f"({run['prof_step_ms'] / ps:.1f} ms per step with the timers on)"),
         "heff": {"flops_per_matvec_all_superblocks": flops,
-                 "lanczos_iters_last_step": [int(x) for x in last["iters"]]},
+                 "lanczos_iters": [[int(x) for x in r["iters"]] for r in run["reports"]]},
         "clocks": run["clocks"],
         "energy_per_site_last": float(last["energy"][0] / (2 * last["n"] + 2)),
     }
-    if not args.no_observables:
-        line["observables"] = observables_leg(ctx, ell)
+    if obs is not None:
+        line["observables"] = obs
     if cmp is not None:
-        line["fp64"] = {"value": job_value(world, args.steps, t_dev64), "unit": "unit-cell steps/s",
-                        "ms_per_step": t_dev64 * 1e3 / args.steps,
+        ms64 = cmp["step_ms"] / cmp["steps"]
+        line["fp64"] = {"value": 1e3 / ms64 * world, "unit": "unit-cell steps/s", "ms_per_step": ms64,
+                        "steps": cmp["steps"], "from": f"the saved state at n = {run['n0']} (idmrg_load)",
                         "max_abs_de_per_site": max_de_per_site(run["reports"], cmp["reports"]),
+                        "lanczos_iters": [[int(x) for x in r["iters"]] for r in cmp["reports"]],
                         "heff_roofline": heff_roofline(cmp["prof"], "fp64", pk)}
-        cmp["ctx"].close()
-    if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
-        _, cb = cpu_baseline(mpo, args.m)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["mixed_vs_fp64_speedup"] = ms64 / (t_dev * 1e3 / args.steps)
+    if world == 1 and not args.no_cpu_baseline:
+        iters = (sum(float(x) for x in cmp["reports"][0]["iters"]) / len(cmp["reports"][0]["iters"])
+                 if cmp is not None else float(PAPER_LANCZOS_ITERS))
+        try:
+            cb = cpu_baseline(mpo, args.m, state, iters, run["n0"], ell // 2)
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "cpu_model", "sample",
+                                                       "one_thread")}
+        except Exception as e:  # reported, not fatal: the GPU measurement stands
+            line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        os.remove(state)
+        os.rmdir(tmpdir)
+    except OSError:
+        pass
     print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 

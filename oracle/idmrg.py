@@ -330,6 +330,20 @@ class ParallelIDMRG:
         e, psi, it, conv = lanczos(mv, v0.ravel(), self.tol, self.maxit)
         return e, psi.reshape(shape), it, conv
 
+    def superblock_step(self, p: int) -> dict:
+        """Steps 3', 3, 4 and 6 of superblock p at the current n, without
+        changing the state (the superblocks of one iteration are independent):
+        start vector, solve, truncation, the new blocks and the reported
+        quantities."""
+        L, W1, W2, R = self.superblock(p)
+        v0 = self.start_vector(p)
+        e, psi, it, _ = self.solve(p, v0)
+        t = truncate(psi, L.q, self.qp, R.q, self.m, self.tie_rel, self.zero_rel, self.target)
+        fid = fidelity_error(v0, psi) if (self.n >= 3 and self.use_prediction) else np.nan
+        return dict(energy=e, iters=it, psi=psi, trunc=t, fidelity=fid, bond=bond_energy(psi, W1, W2),
+                    newL=update_left(L, W1, t.U, t.q), newR=update_right(R, W2, t.V, self.target - t.q),
+                    start_norm=float(np.linalg.norm(v0)))
+
     def step(self) -> StepReport:
         n, P = self.n, self.P
         newL, newR, trunc = [None] * P, [None] * P, [None] * P
@@ -337,21 +351,17 @@ class ParallelIDMRG:
                    eps_best=np.zeros(P), fidelity=np.full(P, np.nan), bond=np.zeros(P),
                    kept=np.zeros(P, dtype=int), lam_all=[None] * P)
         for p in range(P):
-            L, W1, W2, R = self.superblock(p)
-            v0 = self.start_vector(p)
-            e, psi, it, _ = self.solve(p, v0)
-            t = truncate(psi, L.q, self.qp, R.q, self.m, self.tie_rel, self.zero_rel, self.target)
-            newL[p] = update_left(L, W1, t.U, t.q)
-            newR[p] = update_right(R, W2, t.V, self.target - t.q)
+            r = self.superblock_step(p)
+            t = r["trunc"]
+            newL[p], newR[p] = r["newL"], r["newR"]
             trunc[p] = t
-            self.last_psi[p] = psi
-            rep["energies"][p] = e
-            rep["iters"][p] = it
+            self.last_psi[p] = r["psi"]
+            rep["energies"][p] = r["energy"]
+            rep["iters"][p] = r["iters"]
             rep["eps"][p] = t.eps
             rep["eps_best"][p] = t.eps_best
-            if n >= 3 and self.use_prediction:
-                rep["fidelity"][p] = fidelity_error(v0, psi)
-            rep["bond"][p] = bond_energy(psi, W1, W2)
+            rep["fidelity"][p] = r["fidelity"]
+            rep["bond"][p] = r["bond"]
             rep["kept"][p] = len(t.lam)
             rep["lam_all"][p] = t.lam_all
         # Step 7 with the rotation of Step 2': R^(n) of pair p+1 is the right
