@@ -70,10 +70,10 @@ __global__ void project_kernel(LanczosDev L, int pass) {
   }
 }
 
-// Pass 0: w -= alpha v_k + beta_{k-1} v_{k-1} with alpha the summed
-// partials (stored in L.h[0][k]).  Pass 1: w -= sum_j V_j h_j with h_j the
-// summed partials (stored in L.h[1][j]), and the partial squared norm of the
-// new w at part2 slot 0 of pass 2.  The CTA with chunk 0 stores h.
+// Pass 0: w -= alpha v_k + beta_{k-1} v_{k-1} with alpha = L.h[0][k].
+// Pass 1: w -= sum_j V_j h_j with h_j = L.h[1][j], and the partial squared
+// norm of the new w at part2 slot 0 of pass 2.  The coefficients were summed
+// from their partials once, by reduce_kernel.
 __global__ void subtract_kernel(LanczosDev L, int pass) {
   extern __shared__ double hs[];  // [kmax] + [LT/32]
   const int s = blockIdx.y;
@@ -82,15 +82,8 @@ __global__ void subtract_kernel(LanczosDev L, int pass) {
   const int64_t e0 = (int64_t)blockIdx.x * CH;
   if (e0 >= N) return;
   const int kk = L.k[s];
-  const int npc = (int)((N + PCH - 1) / PCH);  // projection chunks
   const int jmin = pass == 0 ? kk : 0;
-  for (int j = jmin + threadIdx.x; j <= kk; j += LT) {
-    const double *p = L.part + (((int64_t)pass * L.S + s) * L.kmax + j) * L.nchunk_max;
-    double acc = 0.0;
-    for (int c = 0; c < npc; ++c) acc += p[c];
-    hs[j] = acc;
-    if (blockIdx.x == 0) L.h[((int64_t)pass * L.S + s) * L.kmax + j] = acc;
-  }
+  for (int j = jmin + threadIdx.x; j <= kk; j += LT) hs[j] = L.h[((int64_t)pass * L.S + s) * L.kmax + j];
   if (pass == 0 && threadIdx.x == 0 && kk > 0) hs[kk - 1] = L.beta[s * L.kmax + kk - 1];
   __syncthreads();
   double *w = L.w[s];
@@ -130,11 +123,32 @@ __global__ void subtract_kernel(LanczosDev L, int pass) {
 }
 
 // Pass 0's subtraction fused with pass 1's projection: each CTA takes one
-// projection chunk of PCH elements, forms alpha from the pass-0 partials (in
-// the fixed order of subtract_kernel), updates its chunk of w (w -= alpha v_k
-// + beta_{k-1} v_{k-1}), keeps it in shared memory and writes the partial
-// dots of every Krylov vector with it (project_kernel, pass 1): the same
-// numbers as the two separate kernels, one launch and one pass over w fewer.
+// projection chunk of PCH elements, reads alpha (reduce_kernel, pass 0),
+// updates its chunk of w (w -= alpha v_k + beta_{k-1} v_{k-1}), keeps it in
+// shared memory and writes the partial dots of every Krylov vector with it
+// (project_kernel, pass 1): one launch and one pass over w fewer than the
+// two separate kernels.
+
+// The partials of one projection pass summed once per (superblock, vector):
+// one warp per coefficient j (pass 0: j = k only), lane-strided over the
+// chunks and a fixed shuffle tree, so the sum is the same on every run.
+// Summing them inside every CTA of the consumer instead costs each CTA a
+// serial FP64 chain as long as the number of chunks (N / 1024), which grows
+// with the vector length.
+__global__ void reduce_kernel(LanczosDev L, int pass) {
+  const int s = blockIdx.y;
+  if (!L.active[s]) return;
+  const int kk = L.k[s];
+  const int j = (pass == 0 ? kk : 0) + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j > kk) return;
+  const int lane = threadIdx.x & 31;
+  const int npc = (int)((L.N[s] + PCH - 1) / PCH);
+  const double *p = L.part + (((int64_t)pass * L.S + s) * L.kmax + j) * L.nchunk_max;
+  double acc = 0.0;
+  for (int c = lane; c < npc; c += 32) acc += p[c];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) L.h[((int64_t)pass * L.S + s) * L.kmax + j] = acc;
+}
 __global__ void sub0_proj1_kernel(LanczosDev L) {
   __shared__ double ws[PCH];
   __shared__ double s_ab[2];
@@ -145,14 +159,9 @@ __global__ void sub0_proj1_kernel(LanczosDev L) {
   if (e0 >= N) return;
   const int n = (int)min((int64_t)PCH, N - e0);
   const int kk = L.k[s];
-  const int npc = (int)((N + PCH - 1) / PCH);
   if (threadIdx.x == 0) {
-    const double *p = L.part + ((int64_t)s * L.kmax + kk) * L.nchunk_max;  // pass 0
-    double acc = 0.0;
-    for (int c = 0; c < npc; ++c) acc += p[c];
-    s_ab[0] = acc;
+    s_ab[0] = L.h[(int64_t)s * L.kmax + kk];  // alpha (pass 0), summed by reduce_kernel
     s_ab[1] = kk > 0 ? L.beta[s * L.kmax + kk - 1] : 0.0;
-    if (blockIdx.x == 0) L.h[(int64_t)s * L.kmax + kk] = acc;
   }
   __syncthreads();
   const double a = s_ab[0], b = s_ab[1];
@@ -353,7 +362,7 @@ __global__ void next_kernel(LanczosDev L) {
   if (!L.active[s]) return;
   const int64_t N = L.N[s];
   const int kk = L.k[s];
-  const double inv = 1.0 / L.beta[s * L.kmax + kk - 1];
+  const double inv = L.ibeta[s * L.kmax + kk - 1];  // 1 / beta_{k-1}, from finalize_kernel
   double *v = L.V[s] + (int64_t)kk * N;
   if (blockIdx.x == 0 && threadIdx.x == 0) L.bufs[s * NBUF + BUF_IN] = v;
   const double *w = L.w[s];
@@ -474,6 +483,13 @@ cudaError_t lanczos_project(const LanczosDev &L, int pass, cudaStream_t st) {
   // projection chunks of PCH elements: nchunk_max counts chunks of CH <= PCH
   dim3 grid((L.nchunk_max * CH + PCH - 1) / PCH, L.S);
   project_kernel<<<grid, LT, 0, st>>>(L, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_reduce(const LanczosDev &L, int pass, cudaStream_t st) {
+  constexpr int WPB = 8;  // warps (coefficients) per CTA
+  dim3 grid(pass == 0 ? 1 : (L.kmax + WPB - 1) / WPB, L.S);
+  reduce_kernel<<<grid, 32 * WPB, 0, st>>>(L, pass);
   return cudaGetLastError();
 }
 

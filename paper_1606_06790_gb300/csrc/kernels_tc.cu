@@ -116,6 +116,44 @@ __global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *
   }
 }
 
+// W stage by blocks (see WBlk): the CTA stages its tile of every input slice
+// in shared memory (each T1 element read once from memory), then each thread
+// forms outputs of one element from the staged values and writes their hi/lo
+// split into the packed stage-3 operand.
+__global__ void __launch_bounds__(256) wstage_blk_kernel(const int2 *__restrict__ tiles, const WBlk *__restrict__ blks,
+                                  const WIn *__restrict__ ins, const WOut *__restrict__ outs,
+                                  const WTermI *__restrict__ terms, double *const *__restrict__ bufs,
+                                  const int *__restrict__ active, int bf16) {
+  extern __shared__ float vin[];  // [nin][WBLK_TE]
+  const int2 tl = tiles[blockIdx.x];  // (block, element tile)
+  const WBlk b = blks[tl.x];
+  if (active && !active[b.sb]) return;
+  const int elems = b.rows * b.cols;
+  const int e0 = tl.y * WBLK_TE;
+  if (e0 >= elems) return;
+  // thread -> (element e, half h): element coordinates once per thread
+  const int e = threadIdx.x % WBLK_TE, h = threadIdx.x / WBLK_TE, nh = blockDim.x / WBLK_TE;
+  const bool live = e0 + e < elems;
+  const int x = live ? (e0 + e) / b.cols : 0, y = live ? (e0 + e) - x * b.cols : 0;
+  const float *t1 = (const float *)bufs[b.sb * NBUF + BUF_T1F];
+  for (int in = h; in < b.nin; in += nh) {
+    const WIn w = ins[b.in0 + in];
+    vin[in * WBLK_TE + e] = live ? t1[w.off + (int64_t)x * w.ld + y] : 0.f;
+  }
+  __syncthreads();
+  if (!live) return;
+  float *dst = (float *)bufs[b.sb * NBUF + BUF_PA3];
+  for (int o = h; o < b.nout; o += nh) {
+    const WOut w = outs[b.out0 + o];
+    float acc = 0.f;
+    for (int q = 0; q < w.nterm; ++q) {
+      const WTermI t = terms[w.term0 + q];
+      acc = fmaf(t.coef, vin[t.in * WBLK_TE + e], acc);
+    }
+    put_split(dst + w.dst_off, w.row0 + x, w.k0 + y, w.KB, w.G, bf16, (double)acc);
+  }
+}
+
 constexpr int TM = 128;
 constexpr int A_TILE = TM * 32;         // floats per A tile (one of hi/lo)
 constexpr int B_TILE = TC_TN * 32;      // floats per B tile
@@ -652,6 +690,18 @@ cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, cons
   if (ntasks > 0 && max_rows > 0) {
     dim3 grid(ntasks, (max_rows + PROWS - 1) / PROWS);
     wstage_tc_kernel<<<grid, 256, 0, st>>>(tasks, terms, bufs, active, bf16);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wstage_blk(const int2 *tiles, int ntiles, int max_in, const WBlk *blks, const WIn *ins,
+                              const WOut *outs, const WTermI *terms, double *const *bufs, const int *active,
+                              int bf16, cudaStream_t st) {
+  if (ntiles > 0) {
+    const int smem = max_in * WBLK_TE * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(wstage_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    wstage_blk_kernel<<<ntiles, 256, smem, st>>>(tiles, blks, ins, outs, terms, bufs, active, bf16);
   }
   return cudaGetLastError();
 }
