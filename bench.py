@@ -589,6 +589,40 @@ def timed_run(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, 
     return res
 
 
+def timed_run_shard(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, dist, local: int):
+    """One problem over the ranks (Sec. 3, Step 2'): contiguous pair ranges,
+    one ring shift of the boundary pair per step (shard.ShardedRun, NCCL
+    point-to-point), the step reports gathered.  Every rank runs the same
+    number of steps; the timed region is bracketed by a barrier and a device
+    synchronisation on both sides, each rank's wall clock taken, the max over
+    ranks reported."""
+    import torch
+    from paper_1606_06790_gb300.shard import ShardedRun
+    ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=prec, lanczos_maxit=maxit)
+    run = ShardedRun(ctx, dist)
+    nsat = 0
+    while nsat < SATURATE_MAX:
+        r = run.step()
+        nsat += 1
+        if min(int(k) for k in r["kept"]) >= 0.9 * m:
+            break
+    for _ in range(max(warmup, 3)):
+        run.step()
+    launches0 = ctx.launch_count()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    reports = [run.step() for _ in range(steps)]
+    torch.cuda.synchronize()
+    dist.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    return {"wall_s": wall, "reports": reports, "clocks": clk, "launches": ctx.launch_count() - launches0,
+            "saturate_steps": nsat, "ranges": run.ranges, "bytes_per_step": run.bytes_sent, "ctx": ctx}
+
+
 def fp64_leg(pkg, mpo, m: int, maxit: int, path: str, steps: int):
     """The plain FP64 path from the state the mixed run's timed region started
     from (idmrg_load of the same file): `steps` unit-cell steps timed with
@@ -611,6 +645,43 @@ def fp64_leg(pkg, mpo, m: int, maxit: int, path: str, steps: int):
     return {"step_ms": ms, "reports": reports, "prof": prof, "steps": steps}
 
 
+def run_shard(args, pkg, mpo, world, rank, local, dist, ell, wl):
+    """--gpus N with N <= l/2: the one problem sharded over the ranks."""
+    from workloads import build_mpo, random_chain_bonds
+    if args.workload == CHAIN:  # every rank steps the same realisation
+        mpo = build_mpo(random_chain_bonds(16, 0.5, 1.5, rank_seed(0)), 16)
+    res = timed_run_shard(pkg, mpo, args.m, args.prec, wl["maxit"], args.steps, args.warmup, dist, local)
+    import torch
+    t_wall = reduce_max([res["wall_s"]], dist, torch.device("cuda", local))[0]
+    launches = reduce_max([res["launches"]], dist, torch.device("cuda", local))[0]
+    last = res["reports"][-1]
+    if rank == 0:
+        v = args.steps / t_wall
+        line = {
+            "metric": METRIC, "value": v, "unit": "unit-cell steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_wall * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp64tc": "bf16-digits(f64)+f64"}.get(args.prec, f"{args.prec}+f64"),
+            "data": "synthetic",
+            "config": {"workload": args.workload, "ell": ell, "m": args.m, "solves_per_step": ell // 2,
+                       "parallelism": f"one problem over {world} GPUs: pair ranges {res['ranges']}, one ring "
+                                      "shift of the boundary pair per step (NCCL send/recv)",
+                       "exchange_bytes_per_step_rank0": res["bytes_per_step"] // max(
+                           args.steps + args.warmup + res["saturate_steps"], 1),
+                       "regime": f"D >= 0.9 m after {res['saturate_steps']} steps, timed n = "
+                                 f"{res['reports'][0]['n']}..{last['n']}",
+                       "timing": "wall clock per rank, barrier and device synchronisation on both sides, max"},
+            "roofline": None, "gpu_launches": int(launches),
+            "e2e": {"value": v, "unit": "unit-cell steps/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                    "note": "the timed region is the API call sequence itself (steps, ring shift, gather)"},
+            "clocks": res["clocks"],
+            "energy_per_site_last": float(last["energy"][0] / (2 * last["n"] + 2)),
+        }
+        print(json.dumps(line), flush=True)
+    res["ctx"].close()
+    dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,6 +696,8 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=3, help="steps of the second region (class timers on)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 steps from the timed region's start")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "shard", "replica"],
+                    help="N > 1: one problem sharded over the GPUs (auto when N <= l/2) or N independent replicas")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--observables", choices=["auto", "on", "off"], default="auto",
@@ -655,6 +728,8 @@ def main():
         return run_batch(args, pkg, dev, local, world, rank, dist)
     mpo, seed = make_workload(rank, args.workload)
     ell = len(mpo.W)
+    if world > 1 and args.mode != "replica" and world <= ell // 2:
+        return run_shard(args, pkg, mpo, world, rank, local, dist, ell, wl)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tmpdir = tempfile.mkdtemp(prefix="idmrg_bench_")
     state = os.path.join(tmpdir, f"state_rank{rank}.ck")

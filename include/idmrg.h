@@ -233,7 +233,37 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *ctx, idmrg_step_report *rep);
  * context is stepped regardless). */
 idmrg_status idmrg_batch_step(idmrg_ctx *const *ctxs, int n, int threads, idmrg_step_report *reps);
 
-/* Truncation error of the run (Sec. 5, Eq. tru): the largest eps^(n)_1 over
+/* ---- One problem over several workers (Sec. 3, Step 2').  The l/2
+ * superblocks of an iteration are independent; consecutive iterations are
+ * coupled only through the rotation of Step 2' (superblock p at n + 1 takes
+ * R^(n) of pair p + 1) and the prediction of Step 3' (U^(n), lambda^(n) and
+ * lambda^(n-1) of pair p + 1).  A worker that owns the contiguous pairs
+ * p0 .. p1-1 therefore needs, after every iteration, only pair p1's data
+ * (pair 0 after the last pair), which the next worker exports.
+ *
+ * idmrg_set_pair_range: from the next step on, this context steps only the
+ * superblocks p0 .. p1-1 (all calls with p = -1 act on them; other p are
+ * EINVAL).  Between steps; ESTATE during a step.  Every worker creates its
+ * context with the whole MPO and the same options.
+ *
+ * idmrg_export_pair: after a step, pair q's R^(n) and the truncation of its
+ * superblock (U, V, lambda, bases) in a host byte buffer (the checkpoint's
+ * layout for one pair).  *len = bytes needed; the data is written when host
+ * is not NULL and cap >= *len (EINVAL otherwise).  q must be in the range.
+ *
+ * idmrg_import_pair: after a step of a context with a partial range, the
+ * data of pair p1 mod l/2 exported by its owner after the same iteration;
+ * the context then plans the next iteration (until the import, stepping calls
+ * return ESTATE).  EINVAL for another pair or iteration.
+ *
+ * Energies per site (Step 5') and the truncation error of a run are kept by
+ * the context that owns pair 0.  idmrg_save / idmrg_load and the observables
+ * need the whole unit cell (ESTATE otherwise). */
+idmrg_status idmrg_set_pair_range(idmrg_ctx *ctx, int p0, int p1);
+idmrg_status idmrg_export_pair(const idmrg_ctx *ctx, int q, void *host, size_t cap, size_t *len);
+idmrg_status idmrg_import_pair(idmrg_ctx *ctx, int q, const void *host, size_t len);
+
+/* Truncation error of the run (Sec. 4.4, Eq. tru): the largest eps^(n)_1 over
  * the last l iterations (one period).  ESTATE before the first step. */
 idmrg_status idmrg_truncation_error(const idmrg_ctx *ctx, double *eps);
 
@@ -241,7 +271,7 @@ idmrg_status idmrg_truncation_error(const idmrg_ctx *ctx, double *eps);
  * l iterations) differ by less than de_tol, or max_steps steps.  Writes the
  * last e_g, the truncation error and the steps taken (each nullable);
  * IDMRG_ENOCONV when max_steps ran out first.  One point of the m scan of
- * Sec. 5 (e_g against eps for several m, extrapolated to eps -> 0). */
+ * Sec. 4.4 (e_g against eps for several m, extrapolated to eps -> 0). */
 idmrg_status idmrg_run(idmrg_ctx *ctx, int max_steps, double de_tol, double *e_g, double *eps, int *steps);
 
 /* ---- Uniform-MPS observables (Sec. 3, Eq. mps2; the bond strengths,
@@ -278,6 +308,28 @@ idmrg_status idmrg_correlation(idmrg_ctx *ctx, int nterms, const double *op_a, c
  * (ENOCONV, estimate written).  Each output pointer may be NULL. */
 idmrg_status idmrg_transfer_spectrum(idmrg_ctx *ctx, double tol, int maxit, double *t1, double *t2_abs,
                                      double *xi, int *iters);
+
+/* ---- Host post-processing of Secs. 4.4-4.6 (no context, no device work). */
+
+/* Eqs. diff1, diff2 over n values the lattice makes equivalent (the bond
+ * strengths of one kind): their average, Delta+ = max - average and
+ * Delta- = min - average.  EINVAL for n < 1 or a non-finite value; each
+ * output pointer may be NULL. */
+idmrg_status idmrg_delta_pm(const double *values, int n, double *avg, double *dplus, double *dminus);
+
+/* Least-squares polynomial of the given degree (0..6) through the n points
+ * (eps_k, value_k), by Householder QR; *v0 = its value at eps = 0 (the eps -> 0
+ * extrapolation of Sec. 4.4, degree 2 for the energy), *sd its standard
+ * deviation s sqrt([(A^T A)^-1]_00), s^2 = RSS / (n - degree - 1) (0 when
+ * n = degree + 1).  EINVAL for too few points or a singular design. */
+idmrg_status idmrg_extrapolate(const double *eps, const double *value, int n, int degree, double *v0, double *sd);
+
+/* Correlation length of Sec. 4.6: least-squares line ln|c_k| = a + b r_k over
+ * the points with r_k > r_min and c_k != 0; *xi = -1/b and its standard
+ * deviation sd(b) / b^2 (0 with two points).  EINVAL with fewer than two
+ * such points or b = 0. */
+idmrg_status idmrg_fit_correlation_length(const double *r, const double *c, int n, double r_min, double *xi,
+                                          double *sd);
 
 /* Step 5': latest e_g = (e^(n)_1 - e^(n-l)_1) / 2l with (n+1) mod l == 0
  * (e^(-1)_1 = 0) and the n it belongs to; ESTATE if there is none yet. */

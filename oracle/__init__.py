@@ -16,7 +16,7 @@ this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
   converged state, its transfer matrix (dense, ``numpy.linalg.eig``), bond
   strengths, spin-spin correlations, Delta+- (Eqs. diff1, diff2) and the
   correlation length.
-* ``oracle.extrapolate`` -- the m scan of Sec. 5: runs to convergence and the
+* ``oracle.extrapolate`` -- the m scan of Sec. 4.4: runs to convergence and the
   quadratic eps -> 0 fit.
 * ``oracle.rng`` -- the counter-based generator (SplitMix64) of the Lanczos
   start vectors for n = 1, 2.

@@ -1,4 +1,4 @@
-"""Sec. 5 of the paper (oracle side, test infrastructure): a run at fixed m
+"""Sec. 4.4 of the paper (oracle side, test infrastructure): a run at fixed m
 until e_g converges, the truncation error eps of the run (Eq. tru, reading
 R6: the largest eps^(n)_1 over the last l iterations), the quadratic
 extrapolation of e_g to eps -> 0, and the exponential fit of a correlation
@@ -52,6 +52,8 @@ def exponential_fit(r, c, r_min: float = 5.0) -> Tuple[float, float]:
     y = np.abs(np.asarray(c, dtype=np.float64))
     keep = (x > r_min) & (y > 0.0)
     x, y = x[keep], np.log(y[keep])
+    if len(x) < 2:
+        raise ValueError("the fit needs two points with r > r_min and c != 0")
     G = np.array([[len(x), np.sum(x)], [np.sum(x), np.sum(x * x)]])
     rhs = np.array([np.sum(y), np.sum(x * y)])
     a, b = np.linalg.solve(G, rhs)

@@ -345,12 +345,20 @@ class ParallelIDMRG:
                     start_norm=float(np.linalg.norm(v0)))
 
     def step(self) -> StepReport:
+        return self.step_range(0, self.P)
+
+    def step_range(self, p0: int, p1: int) -> StepReport:
+        """One parallel iteration on the superblocks p0 .. p1-1 only (the
+        others are another worker's, Sec. 3): their blocks and truncations are
+        renewed, those of the other pairs keep their old values (a worker
+        receives the one it needs from its neighbour); entries of the report
+        outside the range are left at zero / NaN.  e_g needs superblock 0."""
         n, P = self.n, self.P
-        newL, newR, trunc = [None] * P, [None] * P, [None] * P
+        newL, newR, trunc = list(self.L), list(self.R), list(self.prev)
         rep = dict(energies=np.zeros(P), iters=np.zeros(P, dtype=int), eps=np.zeros(P),
                    eps_best=np.zeros(P), fidelity=np.full(P, np.nan), bond=np.zeros(P),
                    kept=np.zeros(P, dtype=int), lam_all=[None] * P)
-        for p in range(P):
+        for p in range(p0, p1):
             r = self.superblock_step(p)
             t = r["trunc"]
             newL[p], newR[p] = r["newL"], r["newR"]
@@ -368,9 +376,11 @@ class ParallelIDMRG:
         # block of superblock p at n+1; lambda^(n-1) becomes lambda^(n-2).
         self.L, self.R = newL, newR
         self.prev2, self.prev = self.prev, trunc
-        self.e1[n] = float(rep["energies"][0])
-        self.eps1[n] = float(rep["eps"][0])
-        e_g = self.energy_per_site(n)
+        e_g = None
+        if p0 == 0 < p1:
+            self.e1[n] = float(rep["energies"][0])
+            self.eps1[n] = float(rep["eps"][0])
+            e_g = self.energy_per_site(n)
         self.n = n + 1
         return StepReport(n=n, e_g=e_g, **rep)
 

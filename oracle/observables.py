@@ -29,7 +29,7 @@ R7 the unit of Eq. mps2 after iteration n is V^(n)_1^T u~^(n)_2 ... V^(n)_{l/2}^
    expectation value uses the dominant left and right eigenvectors of its
    transfer matrix instead of assuming a canonical form.
 R8 <s_i . s_i'> = <Sz Sz> + (<S+ S-> + <S- S+>) / 2, evaluated on the uniform MPS
-   (Sec. 5, bond strength); Delta+- of Eqs. diff1, diff2 are taken over the
+   (Sec. 4.5, bond strength); Delta+- of Eqs. diff1, diff2 are taken over the
    values a caller groups as equivalent.
 R9 the correlation length is xi = -1 / ln(|t2| / t1) unit cells, t1 > |t2| the
    two largest moduli of the unit's transfer-matrix eigenvalues (the paper fits

@@ -33,7 +33,8 @@ EXPORTED_SYMBOLS = [
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
     "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_save", "idmrg_load",
-    "idmrg_correlation", "idmrg_transfer_spectrum",
+    "idmrg_correlation", "idmrg_transfer_spectrum", "idmrg_delta_pm", "idmrg_extrapolate",
+    "idmrg_fit_correlation_length", "idmrg_set_pair_range", "idmrg_export_pair", "idmrg_import_pair",
 ]
 
 KERNEL_CLASSES = {"heff_gemm": 0, "heff_wstage": 1, "lanczos_vec": 2, "lanczos_tri": 3, "svd": 4, "env": 5,
@@ -125,6 +126,12 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_set_svd_path": (i, [vp, i]),
         "idmrg_correlation": (i, [vp, i, P(d), P(d), P(d), i, P(C.c_int64), P(C.c_int64), P(d)]),
         "idmrg_transfer_spectrum": (i, [vp, d, i, P(d), P(d), P(d), P(i)]),
+        "idmrg_delta_pm": (i, [P(d), i, P(d), P(d), P(d)]),
+        "idmrg_extrapolate": (i, [P(d), P(d), i, i, P(d), P(d)]),
+        "idmrg_fit_correlation_length": (i, [P(d), P(d), i, d, P(d), P(d)]),
+        "idmrg_set_pair_range": (i, [vp, i, i]),
+        "idmrg_export_pair": (i, [vp, i, vp, sz, P(sz)]),
+        "idmrg_import_pair": (i, [vp, i, vp, sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -154,10 +161,13 @@ def spin_half_dot_terms(phys_charge):
 
 def delta_pm(values):
     """Eqs. diff1, diff2 over bond strengths that translational symmetry makes
-    equal: (average, max - average, min - average)."""
-    v = np.asarray(values, dtype=np.float64)
-    avg = float(v.sum() / len(v))
-    return avg, float(v.max()) - avg, float(v.min()) - avg
+    equal: (average, max - average, min - average), by idmrg_delta_pm."""
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).ravel())
+    a, dp, dm = C.c_double(), C.c_double(), C.c_double()
+    s = load_library().idmrg_delta_pm(_dptr(v, C.c_double), len(v), C.byref(a), C.byref(dp), C.byref(dm))
+    if s != 0:
+        raise ValueError("delta_pm needs at least one finite value")
+    return a.value, dp.value, dm.value
 
 
 class Context:
@@ -198,7 +208,10 @@ class Context:
         # torch caching allocator as the library's device memory provider
         dev, st = self.device, self.stream
 
+        self.alloc_calls = 0
+
         def _alloc(nbytes, user):
+            self.alloc_calls += 1
             try:
                 return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=st)
             except Exception:  # out of memory -> NULL -> IDMRG_ENOMEM
@@ -387,6 +400,28 @@ class Context:
         rep, arr, iarr = self._report()
         s = self._check(self.lib.idmrg_unit_cell_step(self.h, C.byref(rep)), "unit_cell_step", ok=(0, 4))
         return self._report_dict(rep, arr, iarr, s == 0)
+
+    # ---- one problem over several workers (shard.ShardedRun)
+    def step_range(self, p0: int, p1: int) -> Dict[str, object]:
+        """One unit-cell step of superblocks p0..p1-1 (idmrg_set_pair_range
+        when the range changes, then idmrg_unit_cell_step)."""
+        if getattr(self, "_range", (0, self.P)) != (p0, p1):
+            self._check(self.lib.idmrg_set_pair_range(self.h, int(p0), int(p1)), "set_pair_range")
+            self._range = (p0, p1)
+        return self.unit_cell_step()
+
+    def export_pair(self, q: int) -> bytes:
+        """Pair q's R^(n) and truncation after a step (idmrg_export_pair)."""
+        n = C.c_size_t()
+        self._check(self.lib.idmrg_export_pair(self.h, int(q), None, 0, C.byref(n)), "export_pair")
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.idmrg_export_pair(self.h, int(q), buf, n.value, C.byref(n)), "export_pair")
+        return buf.raw[: n.value]
+
+    def import_pair(self, q: int, data: bytes) -> None:
+        """The next worker's first pair after the same step (idmrg_import_pair)."""
+        buf = C.create_string_buffer(bytes(data), len(data))
+        self._check(self.lib.idmrg_import_pair(self.h, int(q), buf, len(data)), "import_pair")
 
     def save(self, path: str) -> None:
         """Checkpoint between steps (idmrg_save)."""

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libidmrg.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 CU_SOURCES = ["kernels_f64.cu", "kernels_lanczos.cu", "kernels_svd.cu", "kernels_tc.cu", "kernels_obs.cu", "context.cu"]
-CXX_SOURCES = ["plan.cpp"]
+CXX_SOURCES = ["plan.cpp", "fits.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -185,6 +185,13 @@ struct idmrg_ctx {
   std::string err;
   uint64_t launches = 0;
 
+  // superblocks this context steps (a contiguous range of pairs; the others
+  // belong to other workers, whose boundary pair arrives by idmrg_import_pair)
+  int own0 = 0, own1 = 0;
+  bool plan_pending = false;  // advance() of a partial range waits for the import before planning
+  bool owns(int q) const { return q >= own0 && q < own1; }
+  bool owns_all() const { return own0 == 0 && own1 == P; }
+
   // iteration state
   int n = 1;
   std::vector<int> stage;
@@ -636,6 +643,7 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
   c->rmax_rows = 0;
   const uint64_t state0 = c->o.seed;
   for (int p = 0; p < P; ++p) {
+    if (!c->owns(p)) continue;  // another worker's superblock
     SBPlan &S = c->plan[p];
     S.c1 = c->site_of(2 * p + c->n);
     S.c2 = c->site_of(2 * p + c->n + 1);
@@ -888,6 +896,7 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
     mr = std::max(mr, rows);
   };
   for (int p = 0; p < P; ++p) {
+    if (!c->owns(p)) continue;
     SBPlan &S = c->plan[p];
     const Env &L = c->envL[p];
     const Env &R = c->envR[(p + 1) % P];
@@ -1213,6 +1222,7 @@ idmrg_status plan_oz(idmrg_ctx *c) {
   std::vector<std::vector<int64_t>> rmaps(P);
   std::vector<int64_t> na1(P), nb1(P), nt1(P), na3(P), nb3(P), nt3(P);
   for (int p = 0; p < P; ++p) {
+    if (!c->owns(p)) continue;
     SBPlan &S = c->plan[p];
     const Env &L = c->envL[p];
     const Env &R = c->envR[(p + 1) % P];
@@ -1555,10 +1565,12 @@ idmrg_status check_dev_err(idmrg_ctx *c) {
   return IDMRG_OK;
 }
 
-bool want(int p, int q) { return p < 0 || p == q; }
+bool want(const idmrg_ctx *c, int p, int q) { return p < 0 ? c->owns(q) : p == q; }
 
 idmrg_status check_p(idmrg_ctx *c, int p) {
   if (p < -1 || p >= c->P) return c->fail(IDMRG_EINVAL, "superblock index %d out of range", p);
+  if (p >= 0 && !c->owns(p)) return c->fail(IDMRG_EINVAL, "superblock %d is outside this context's range", p);
+  if (c->plan_pending) return c->fail(IDMRG_ESTATE, "the boundary pair of this range has not been imported");
   return IDMRG_OK;
 }
 
@@ -1569,7 +1581,7 @@ idmrg_status predict(idmrg_ctx *c, int p) {
   const int P = c->P, d = c->d;
   const bool use_pred = c->o.predict && c->n >= 3;
   for (int q = 0; q < P; ++q)
-    if (want(p, q) && c->stage[q] != ST_READY && c->stage[q] != ST_STARTED)
+    if (want(c, p, q) && c->stage[q] != ST_READY && c->stage[q] != ST_STARTED)
       return c->fail(IDMRG_ESTATE, "predict_wavefunction: superblock %d already past its start", q);
   double *const *bufs = (double *const *)c->dbufs.p;
   if (!use_pred) {
@@ -1578,7 +1590,7 @@ idmrg_status predict(idmrg_ctx *c, int p) {
     std::vector<RandBlock> rb;
     int mr = 0;
     for (const RandBlock &b : c->rblocks)
-      if (want(p, b.sb)) { rb.push_back(b); mr = std::max(mr, b.rows); }
+      if (want(c, p, b.sb)) { rb.push_back(b); mr = std::max(mr, b.rows); }
     c->kbegin(IDMRG_K_PREDICT);
     if (p >= 0) {
       NOMEM(c->upload(c->dst, rb));
@@ -1595,7 +1607,7 @@ idmrg_status predict(idmrg_ctx *c, int p) {
     c->smax_rows = 0;
     c->gp.clear();
     for (int q = 0; q < P; ++q) {
-      if (!want(p, q)) continue;
+      if (!want(c, p, q)) continue;
       const int q1 = (q + 1) % P;
       const TruncRec &A = c->prev[q], &B = c->prev[q1], &B2 = c->prev2[q1];
       if (!A.valid || !B.valid || !B2.valid) return c->fail(IDMRG_ESTATE, "prediction needs two earlier iterations");
@@ -1686,7 +1698,7 @@ idmrg_status predict(idmrg_ctx *c, int p) {
     c->launches += 2;
   }
   for (int q = 0; q < P; ++q)
-    if (want(p, q)) c->stage[q] = ST_STARTED;
+    if (want(c, p, q)) c->stage[q] = ST_STARTED;
   return IDMRG_OK;
 }
 
@@ -1720,7 +1732,7 @@ idmrg_status lanczos_iteration(idmrg_ctx *c, const LanczosDev &L, bool fp64, con
 idmrg_status lanczos(idmrg_ctx *c, int p) {
   const int P = c->P;
   for (int q = 0; q < P; ++q)
-    if (want(p, q) && c->stage[q] != ST_STARTED)
+    if (want(c, p, q) && c->stage[q] != ST_STARTED)
       return c->fail(IDMRG_ESTATE, "lanczos_solve: superblock %d has no start vector", q);
   // a mixed-precision run stops after 80 iterations and restarts: its Krylov
   // basis never holds more than 81 vectors
@@ -1754,7 +1766,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
         c->ensure(c->lresid, 8 * P) && c->ensure(c->ldot, 8 * P) && c->ensure(c->lk, 4 * P) &&
         c->ensure(c->lactive, 4 * P) && c->ensure(c->lconv, 4 * P));
   std::vector<int> member(P);
-  for (int q = 0; q < P; ++q) member[q] = want(p, q) ? 1 : 0;
+  for (int q = 0; q < P; ++q) member[q] = want(c, p, q) ? 1 : 0;
   NOMEM(c->upload(c->lmember, member));
   if (!c->pin_act) {
     CK(cudaHostAlloc((void **)&c->pin_act, 2 * 4 * (size_t)P, cudaHostAllocDefault));
@@ -1884,7 +1896,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
     }
     if (r == 0 && c->mixed)  // restarts overwrite V[0]: keep the normalised start for Eq. fid1
       for (int q = 0; q < P; ++q)
-        if (want(p, q) && N[q] > 0)
+        if (want(c, p, q) && N[q] > 0)
           CK(cudaMemcpyAsync(startp[q], Vp[q], 8 * (size_t)N[q], cudaMemcpyDeviceToDevice, c->st));
     std::vector<double> th(P);
     CK(c->d2h_copy(th.data(), c->ltheta.p, 8 * P));
@@ -1906,7 +1918,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   }
   if (c->mixed) {  // Eq. fid1 against the final Ritz vector
     std::vector<int> all(P);
-    for (int q = 0; q < P; ++q) all[q] = want(p, q) ? 1 : 0;
+    for (int q = 0; q < P; ++q) all[q] = want(c, p, q) ? 1 : 0;
     NOMEM(c->upload(c->lmember, all) && c->upload(c->lv0, startp));
     CK(lanczos_dot(L, (const double *const *)c->lv0.p, (const double *const *)c->lpsi.p, c->dp(c->ldot), c->st));
     c->launches += 2;
@@ -1914,7 +1926,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
     CK(cudaStreamSynchronize(c->st));
   }
   for (int q = 0; q < P; ++q) {
-    if (!want(p, q)) continue;
+    if (!want(c, p, q)) continue;
     c->energy[q] = theta[q];
     c->iters[q] = total[q];
     c->conv[q] = final_[q];
@@ -1927,7 +1939,7 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   std::vector<DotTerm> dt;
   std::vector<int> dsb;
   for (size_t k = 0; k < c->dterms.size(); ++k)
-    if (want(p, c->dterm_sb[k])) { dt.push_back(c->dterms[k]); dsb.push_back(c->dterm_sb[k]); }
+    if (want(c, p, c->dterm_sb[k])) { dt.push_back(c->dterms[k]); dsb.push_back(c->dterm_sb[k]); }
   if (!dt.empty()) {
     NOMEM(c->upload(c->dst, dt) && c->ensure(c->ddp, 8 * dt.size()));
     CK(launch_dot_terms((const DotTerm *)c->dst.p, (int)dt.size(), (double *const *)c->dbufs.p, c->dp(c->ddp), c->st));
@@ -1936,11 +1948,11 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
     CK(c->d2h_copy(part.data(), c->ddp.p, 8 * dt.size()));
     CK(cudaStreamSynchronize(c->st));
     for (int q = 0; q < P; ++q)
-      if (want(p, q)) c->bond[q] = 0.0;
+      if (want(c, p, q)) c->bond[q] = 0.0;
     for (size_t k = 0; k < dt.size(); ++k) c->bond[dsb[k]] += part[k];
   } else {
     for (int q = 0; q < P; ++q)
-      if (want(p, q)) c->bond[q] = 0.0;
+      if (want(c, p, q)) c->bond[q] = 0.0;
   }
   return allconv ? IDMRG_OK : c->fail(IDMRG_ENOCONV, "Lanczos reached lanczos_maxit before converging");
 }
@@ -1994,7 +2006,7 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
   c->tmaxel_all = 0;
   for (int q = 0; q < P; ++q) {
     c->tjob0[q] = (int)c->jobs.size();
-    if (!want(p, q)) continue;
+    if (!want(c, p, q)) continue;
     const Env &L = c->envL[q];
     const Env &R = c->envR[(q + 1) % P];
     const Basis &BL = L.lay.b, &BR = R.lay.b;
@@ -2239,7 +2251,7 @@ void svd_stats_reset(idmrg_ctx *c) {
 idmrg_status truncate(idmrg_ctx *c, int p) {
   const int P = c->P;
   for (int q = 0; q < P; ++q)
-    if (want(p, q) && c->stage[q] != ST_SOLVED)
+    if (want(c, p, q) && c->stage[q] != ST_SOLVED)
       return c->fail(IDMRG_ESTATE, "truncate: superblock %d has not been solved", q);
   idmrg_status s0 = trunc_plan(c, p);
   if (s0 != IDMRG_OK) return s0;
@@ -2294,7 +2306,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   // select: one launch, one CTA per superblock (no jobs: nothing kept)
   std::vector<int> sbl;
   for (int q = 0; q < P; ++q)
-    if (want(p, q)) sbl.push_back(q);
+    if (want(c, p, q)) sbl.push_back(q);
   CK(launch_svd_select((const SvdJob *)c->sjobs.p, (const int *)c->sjob0.p, (const int *)c->snjob.p, P,
                        c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, select_out(c, 0), c->tentries_max,
                        c->st));
@@ -2485,13 +2497,13 @@ idmrg_status env_build(idmrg_ctx *c, int q, GemmList &g1, GemmList &g3, WList &w
 idmrg_status update_envs(idmrg_ctx *c, int p) {
   const int P = c->P;
   for (int q = 0; q < P; ++q)
-    if (want(p, q) && c->stage[q] != ST_TRUNCATED)
+    if (want(c, p, q) && c->stage[q] != ST_TRUNCATED)
       return c->fail(IDMRG_ESTATE, "update_environments: superblock %d is not truncated", q);
   c->genv1.clear();
   c->genv3.clear();
   c->wenv.clear();
   for (int q = 0; q < P; ++q) {
-    if (!want(p, q)) continue;
+    if (!want(c, p, q)) continue;
     idmrg_status s = env_build(c, q, c->genv1, c->genv3, c->wenv);
     if (s != IDMRG_OK) return s;
   }
@@ -2518,7 +2530,7 @@ idmrg_status update_envs(idmrg_ctx *c, int p) {
   c->kend(IDMRG_K_ENV, c->genv1.flops + c->wenv.flops + c->genv3.flops, 0.0);
   c->launches += 3;
   for (int q = 0; q < P; ++q)
-    if (want(p, q)) c->stage[q] = ST_UPDATED;
+    if (want(c, p, q)) c->stage[q] = ST_UPDATED;
   return IDMRG_OK;
 }
 
@@ -2528,26 +2540,35 @@ idmrg_status update_envs(idmrg_ctx *c, int p) {
 idmrg_status advance(idmrg_ctx *c) {
   const int P = c->P;
   for (int q = 0; q < P; ++q)
-    if (c->stage[q] != ST_UPDATED) return c->fail(IDMRG_ESTATE, "advance: superblock %d is not updated", q);
+    if (c->owns(q) && c->stage[q] != ST_UPDATED)
+      return c->fail(IDMRG_ESTATE, "advance: superblock %d is not updated", q);
   CK(cudaStreamSynchronize(c->st));
   c->obs.valid = c->obs.fixed = false;
   for (int q = 0; q < P; ++q) {
     std::swap(c->envL[q], c->newL[q]);
     std::swap(c->envR[q], c->newR[q]);
   }
-  c->eps1[c->n] = c->cur[0].eps;
-  // lambda history: cur -> prev -> prev2 (buffers recycled)
+  // lambda history: cur -> prev -> prev2 (buffers recycled); for another
+  // worker's pair the stale record moves along and the import replaces prev
   for (int q = 0; q < P; ++q) {
     std::swap(c->prev2[q], c->prev[q]);
     std::swap(c->prev[q], c->cur[q]);
   }
-  c->e1[c->n] = c->energy[0];
-  if ((c->n + 1) % c->ell == 0) {
-    const double before = (c->n - c->ell == -1) ? 0.0 : c->e1[c->n - c->ell];
-    c->eg_last = (c->e1[c->n] - before) / (2.0 * c->ell);
-    c->eg_n = c->n;
+  if (c->owns(0)) {  // Step 5' (superblock 1 of the paper)
+    c->eps1[c->n] = c->prev[0].eps;
+    c->e1[c->n] = c->energy[0];
+    if ((c->n + 1) % c->ell == 0) {
+      const double before = (c->n - c->ell == -1) ? 0.0 : c->e1[c->n - c->ell];
+      c->eg_last = (c->e1[c->n] - before) / (2.0 * c->ell);
+      c->eg_n = c->n;
+    }
   }
   c->n += 1;
+  if (!c->owns_all()) {  // the right block of the last superblock comes from the next worker
+    c->plan_pending = true;
+    for (int q = 0; q < P; ++q) c->stage[q] = ST_READY;
+    return IDMRG_OK;
+  }
   return plan_iteration(c);
 }
 
@@ -3225,6 +3246,57 @@ idmrg_status ck_get_dev(idmrg_ctx *c, CkFile &F, DevBuf &b, int64_t n) {
   return IDMRG_OK;
 }
 
+namespace {
+// one truncation record (bases, sector tables, lambda, U and V)
+idmrg_status ck_put_trunc_dev(idmrg_ctx *c, CkFile &F, const TruncRec &T) {
+  F.put((int)T.valid);
+  ck_put_basis(F, T.leftB);
+  ck_put_basis(F, T.rightB);
+  ck_put_basis(F, T.bU);
+  ck_put_basis(F, T.bV);
+  F.put((int64_t)T.sec.size());
+  for (const SecInfo &si : T.sec) ck_put_sec(F, si);
+  F.putv(T.lam);
+  F.putv(T.lam_all);
+  F.put(T.eps);
+  F.put(T.eps_best);
+  F.put(T.usize);
+  F.put(T.vsize);
+  idmrg_status s = ck_put_dev(c, F, T.U, T.valid ? T.usize : 0);
+  if (s != IDMRG_OK) return s;
+  return ck_put_dev(c, F, T.V, T.valid ? T.vsize : 0);
+}
+
+idmrg_status ck_get_trunc(idmrg_ctx *c, CkFile &F, TruncRec &T) {
+  const DevBuf keepU = T.U, keepV = T.V;  // device buffers are recycled
+  T = TruncRec();
+  T.U = keepU;
+  T.V = keepV;
+  int valid = 0;
+  F.get(valid);
+  T.valid = valid != 0;
+  ck_get_basis(F, T.leftB);
+  ck_get_basis(F, T.rightB);
+  ck_get_basis(F, T.bU);
+  ck_get_basis(F, T.bV);
+  int64_t ns = 0;
+  F.get(ns);
+  if (!F.ok || ns < 0 || ns > (1 << 20)) return c->fail(IDMRG_EINVAL, "truncation record damaged");
+  T.sec.resize((size_t)ns);
+  for (SecInfo &si : T.sec) ck_get_sec(F, si);
+  F.getv(T.lam);
+  F.getv(T.lam_all);
+  F.get(T.eps);
+  F.get(T.eps_best);
+  F.get(T.usize);
+  F.get(T.vsize);
+  if (!F.ok) return c->fail(IDMRG_EINVAL, "truncation record truncated");
+  idmrg_status s = ck_get_dev(c, F, T.U, T.valid ? T.usize : 0);
+  if (s != IDMRG_OK) return s;
+  return ck_get_dev(c, F, T.V, T.valid ? T.vsize : 0);
+}
+}  // namespace
+
 extern "C" {
 
 void idmrg_default_opts(idmrg_opts *o) {
@@ -3272,6 +3344,8 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
   c->ell = ell;
   c->d = d;
   c->P = ell / 2;
+  c->own0 = 0;
+  c->own1 = c->P;
   c->adim.assign(mpo->bond_dim, mpo->bond_dim + ell + 1);
   if (c->adim[ell] != c->adim[0]) return bail(IDMRG_EINVAL);
   for (int k = 0; k <= ell; ++k)
@@ -3525,7 +3599,7 @@ static idmrg_status heff_apply_form(idmrg_ctx *c, int p, const double *psi_dev, 
   for (int q = 0; q < c->P; ++q) {
     save_in[q] = c->hbufs[q * NBUF + BUF_IN];
     save_out[q] = c->hbufs[q * NBUF + BUF_OUT];
-    if (!want(p, q)) continue;
+    if (!want(c, p, q)) continue;
     mask[q] = 1;
     c->hbufs[q * NBUF + BUF_IN] = const_cast<double *>(psi_dev) + off;
     c->hbufs[q * NBUF + BUF_OUT] = out_dev + off;
@@ -3567,7 +3641,7 @@ idmrg_status idmrg_predict_wavefunction(idmrg_ctx *c, int p, double *norm_out) {
   for (int q = 0; q < P; ++q) {
     N[q] = c->plan[q].psi.N;
     x[q] = c->dp(c->bPsi[q]);
-    mask[q] = want(p, q) ? 1 : 0;
+    mask[q] = want(c, p, q) ? 1 : 0;
     nmax = std::max(nmax, N[q]);
   }
   const int nchunk = (int)((nmax + norm_chunk() - 1) / norm_chunk());
@@ -3581,7 +3655,7 @@ idmrg_status idmrg_predict_wavefunction(idmrg_ctx *c, int p, double *norm_out) {
   CK(cudaStreamSynchronize(c->st));
   int k = 0;
   for (int q = 0; q < P; ++q)
-    if (want(p, q)) norm_out[k++] = nr[q];
+    if (want(c, p, q)) norm_out[k++] = nr[q];
   return IDMRG_OK;
 }
 
@@ -3589,11 +3663,11 @@ idmrg_status idmrg_set_start_vector(idmrg_ctx *c, int p, const double *psi_dev) 
   if (!c || !psi_dev) return IDMRG_EINVAL;
   if (check_p(c, p) != IDMRG_OK) return IDMRG_EINVAL;
   for (int q = 0; q < c->P; ++q)
-    if (want(p, q) && c->stage[q] != ST_READY && c->stage[q] != ST_STARTED)
+    if (want(c, p, q) && c->stage[q] != ST_READY && c->stage[q] != ST_STARTED)
       return c->fail(IDMRG_ESTATE, "set_start_vector: superblock %d already past its start", q);
   int64_t off = 0;
   for (int q = 0; q < c->P; ++q) {
-    if (!want(p, q)) continue;
+    if (!want(c, p, q)) continue;
     const int64_t N = c->plan[q].psi.N;
     if (N > 0) CK(cudaMemcpyAsync(c->bPsi[q].p, psi_dev + off, 8 * (size_t)N, cudaMemcpyDeviceToDevice, c->st));
     off += N;
@@ -3609,7 +3683,7 @@ idmrg_status idmrg_lanczos_solve(idmrg_ctx *c, int p, double *e_out, int *iters_
   if (s != IDMRG_OK && s != IDMRG_ENOCONV) return s;
   int k = 0;
   for (int q = 0; q < c->P; ++q) {
-    if (!want(p, q)) continue;
+    if (!want(c, p, q)) continue;
     if (e_out) e_out[k] = c->energy[q];
     if (iters_out) iters_out[k] = c->iters[q];
     ++k;
@@ -3635,7 +3709,7 @@ idmrg_status idmrg_truncate(idmrg_ctx *c, int p, double *eps_out, double *eps_be
   if (s != IDMRG_OK) return s;
   int k = 0;
   for (int q = 0; q < c->P; ++q) {
-    if (!want(p, q)) continue;
+    if (!want(c, p, q)) continue;
     if (eps_out) eps_out[k] = c->cur[q].eps;
     if (eps_best_out) eps_best_out[k] = c->cur[q].eps_best;
     if (kept_out) kept_out[k] = c->cur[q].bU.D;
@@ -3690,8 +3764,10 @@ idmrg_status idmrg_batch_step(idmrg_ctx *const *ctxs, int n, int threads, idmrg_
 
 idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {
   if (!c) return IDMRG_EINVAL;
+  if (c->plan_pending) return c->fail(IDMRG_ESTATE, "unit_cell_step: the boundary pair has not been imported");
   for (int q = 0; q < c->P; ++q)
-    if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "unit_cell_step: iteration %d already in progress", c->n);
+    if (c->owns(q) && c->stage[q] != ST_READY)
+      return c->fail(IDMRG_ESTATE, "unit_cell_step: iteration %d already in progress", c->n);
   idmrg_status s = predict(c, -1);
   if (s != IDMRG_OK) return s;
   idmrg_status sl = lanczos(c, -1);
@@ -3727,6 +3803,88 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {
 }
 
 // ------------------------------------------------------------------------
+// One problem over several workers (Sec. 3, Step 2'): a context steps a
+// contiguous range of pairs; after each step the first pair of the range is
+// exported (R^(n) of that pair and its truncation: U^(n), V^(n), lambda^(n),
+// bases and sector tables) and imported by the worker whose range ends just
+// before it.  The byte layout is the checkpoint's, for one pair.
+// ------------------------------------------------------------------------
+idmrg_status idmrg_set_pair_range(idmrg_ctx *c, int p0, int p1) {
+  if (!c) return IDMRG_EINVAL;
+  if (p0 < 0 || p1 > c->P || p0 >= p1) return c->fail(IDMRG_EINVAL, "pair range %d..%d outside 0..%d", p0, p1, c->P);
+  for (int q = 0; q < c->P; ++q)
+    if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "set_pair_range: a step is in progress");
+  if (c->plan_pending) return c->fail(IDMRG_ESTATE, "set_pair_range: the boundary pair has not been imported");
+  c->own0 = p0;
+  c->own1 = p1;
+  c->obs.valid = c->obs.fixed = false;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_export_pair(const idmrg_ctx *cc, int q, void *host, size_t cap, size_t *len) {
+  idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);
+  if (!c || !len || q < 0 || q >= c->P) return IDMRG_EINVAL;
+  if (!c->owns(q)) return c->fail(IDMRG_EINVAL, "export_pair: pair %d is not stepped by this context", q);
+  for (int k = 0; k < c->P; ++k)
+    if (c->stage[k] != ST_READY) return c->fail(IDMRG_ESTATE, "export_pair: a step is in progress");
+  if (!c->prev[q].valid) return c->fail(IDMRG_ESTATE, "export_pair: pair %d has no completed iteration", q);
+  CK(cudaStreamSynchronize(c->st));
+  char *buf = nullptr;
+  size_t n = 0;
+  CkFile F;
+  F.f = open_memstream(&buf, &n);
+  if (!F.f) return c->fail(IDMRG_ENOMEM, "export_pair: no host memory");
+  F.put(c->n);
+  F.put(q);
+  const Env &E = c->envR[q];
+  ck_put_basis(F, E.lay.b);
+  F.putv(E.lay.chq);
+  idmrg_status s = ck_put_dev(c, F, E.data, E.lay.size);
+  if (s == IDMRG_OK) s = ck_put_trunc_dev(c, F, c->prev[q]);
+  fclose(F.f);
+  F.f = nullptr;
+  if (s == IDMRG_OK && !F.ok) s = c->fail(IDMRG_ENOMEM, "export_pair: serialisation failed");
+  if (s == IDMRG_OK) {
+    *len = n;
+    if (host && cap >= n) memcpy(host, buf, n);
+    else if (host) s = c->fail(IDMRG_EINVAL, "export_pair: %zu bytes needed, %zu given", n, cap);
+  }
+  free(buf);
+  return s;
+}
+
+idmrg_status idmrg_import_pair(idmrg_ctx *c, int q, const void *host, size_t len) {
+  if (!c || !host || q < 0 || q >= c->P) return IDMRG_EINVAL;
+  if (c->owns(q)) return c->fail(IDMRG_EINVAL, "import_pair: pair %d is stepped by this context", q);
+  if (q != c->own1 % c->P) return c->fail(IDMRG_EINVAL, "import_pair: pair %d does not follow this range", q);
+  CkFile F;
+  F.f = fmemopen(const_cast<void *>(host), len, "rb");
+  if (!F.f) return c->fail(IDMRG_EINVAL, "import_pair: cannot read the buffer");
+  int n = 0, qq = -1;
+  F.get(n);
+  F.get(qq);
+  if (!F.ok || qq != q || n != c->n - 1)
+    return c->fail(IDMRG_EINVAL, "import_pair: data of pair %d after iteration %d, expected pair %d after %d", qq, n,
+                   q, c->n - 1);
+  Env &E = c->envR[q];
+  Basis b;
+  std::vector<int> chq;
+  ck_get_basis(F, b);
+  F.getv(chq, 1 << 20);
+  if (!F.ok) return c->fail(IDMRG_EINVAL, "import_pair: data truncated");
+  E.lay.build(b, chq);
+  idmrg_status s = ck_get_dev(c, F, E.data, E.lay.size);
+  if (s != IDMRG_OK) return s;
+  s = ck_get_trunc(c, F, c->prev[q]);
+  if (s != IDMRG_OK) return s;
+  if (c->plan_pending) {
+    c->plan_pending = false;
+    return plan_iteration(c);
+  }
+  return IDMRG_OK;
+}
+
+// ------------------------------------------------------------------------
 // Checkpoint between unit-cell steps: n, the e_g bookkeeping, every pair's
 // current environments and the last two truncations (bases, sector tables,
 // U, V, lambda) that the prediction reads.  Binary, host byte order.
@@ -3734,6 +3892,7 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {
 idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
   if (!cc || !path) return IDMRG_EINVAL;
   idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);  // errors are recorded in the context
+  if (!c->owns_all()) return c->fail(IDMRG_ESTATE, "save: the context steps only superblocks %d..%d", c->own0, c->own1 - 1);
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "save: a step is in progress");
   CK(cudaStreamSynchronize(c->st));
@@ -3775,22 +3934,7 @@ idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
       if (s != IDMRG_OK) return s;
     }
     for (const TruncRec *T : {&c->prev[q], &c->prev2[q]}) {
-      F.put((int)T->valid);
-      ck_put_basis(F, T->leftB);
-      ck_put_basis(F, T->rightB);
-      ck_put_basis(F, T->bU);
-      ck_put_basis(F, T->bV);
-      F.put((int64_t)T->sec.size());
-      for (const SecInfo &si : T->sec) ck_put_sec(F, si);
-      F.putv(T->lam);
-      F.putv(T->lam_all);
-      F.put(T->eps);
-      F.put(T->eps_best);
-      F.put(T->usize);
-      F.put(T->vsize);
-      idmrg_status s = ck_put_dev(c, F, T->U, T->valid ? T->usize : 0);
-      if (s != IDMRG_OK) return s;
-      s = ck_put_dev(c, F, T->V, T->valid ? T->vsize : 0);
+      idmrg_status s = ck_put_trunc_dev(c, F, *T);
       if (s != IDMRG_OK) return s;
     }
   }
@@ -3800,6 +3944,7 @@ idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
 
 idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
   if (!c || !path) return IDMRG_EINVAL;
+  if (!c->owns_all()) return c->fail(IDMRG_ESTATE, "load: the context steps only superblocks %d..%d", c->own0, c->own1 - 1);
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "load: a step is in progress");
   c->obs.valid = c->obs.fixed = false;
@@ -3848,32 +3993,7 @@ idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
       if (s != IDMRG_OK) return s;
     }
     for (TruncRec *T : {&c->prev[q], &c->prev2[q]}) {
-      const DevBuf keepU = T->U, keepV = T->V;
-      *T = TruncRec();
-      T->U = keepU;
-      T->V = keepV;
-      int valid = 0;
-      F.get(valid);
-      T->valid = valid != 0;
-      ck_get_basis(F, T->leftB);
-      ck_get_basis(F, T->rightB);
-      ck_get_basis(F, T->bU);
-      ck_get_basis(F, T->bV);
-      int64_t ns = 0;
-      F.get(ns);
-      if (!F.ok || ns < 0 || ns > (1 << 20)) return c->fail(IDMRG_EINVAL, "load: checkpoint truncated");
-      T->sec.resize((size_t)ns);
-      for (SecInfo &si : T->sec) ck_get_sec(F, si);
-      F.getv(T->lam);
-      F.getv(T->lam_all);
-      F.get(T->eps);
-      F.get(T->eps_best);
-      F.get(T->usize);
-      F.get(T->vsize);
-      if (!F.ok) return c->fail(IDMRG_EINVAL, "load: checkpoint truncated");
-      idmrg_status s = ck_get_dev(c, F, T->U, T->valid ? T->usize : 0);
-      if (s != IDMRG_OK) return s;
-      s = ck_get_dev(c, F, T->V, T->valid ? T->vsize : 0);
+      idmrg_status s = ck_get_trunc(c, F, *T);
       if (s != IDMRG_OK) return s;
     }
   }
@@ -3921,6 +4041,7 @@ idmrg_status idmrg_correlation(idmrg_ctx *c, int nterms, const double *op_a, con
                                int npairs, const int64_t *site_i, const int64_t *site_j, double *out) {
   if (!c || nterms < 1 || nterms > 64 || npairs < 0 || !op_a || !op_b || !coef) return IDMRG_EINVAL;
   if (npairs > 0 && (!site_i || !site_j || !out)) return IDMRG_EINVAL;
+  if (!c->owns_all() || c->plan_pending) return c->fail(IDMRG_ESTATE, "correlation: needs the whole unit cell");
   for (int k = 0; k < npairs; ++k)
     if (site_i[k] < 0 || site_j[k] <= site_i[k] || site_j[k] - site_i[k] > (int64_t)1 << 20)
       return c->fail(IDMRG_EINVAL, "correlation: pair %d needs 0 <= i < j <= i + 2^20", k);
@@ -3933,6 +4054,7 @@ idmrg_status idmrg_correlation(idmrg_ctx *c, int nterms, const double *op_a, con
 idmrg_status idmrg_transfer_spectrum(idmrg_ctx *c, double tol, int maxit, double *t1, double *t2_abs, double *xi,
                                      int *iters) {
   if (!c || !(tol > 0.0) || maxit < 1) return IDMRG_EINVAL;
+  if (!c->owns_all() || c->plan_pending) return c->fail(IDMRG_ESTATE, "transfer_spectrum: needs the whole unit cell");
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "transfer_spectrum: a step is in progress");
   double ratio = 0.0;
@@ -3958,7 +4080,7 @@ idmrg_status idmrg_heff_cost(const idmrg_ctx *c, int p, double *flops, double *b
   if (!c || p < -1 || p >= c->P) return IDMRG_EINVAL;
   double f = 0, b = 0;
   for (int q = 0; q < c->P; ++q)
-    if (want(p, q)) { f += c->plan[q].heff_flops; b += c->plan[q].heff_bytes; }
+    if (want(c, p, q)) { f += c->plan[q].heff_flops; b += c->plan[q].heff_bytes; }
   if (flops) *flops = f;
   if (bytes) *bytes = b;
   return IDMRG_OK;
@@ -4066,6 +4188,8 @@ __global__ void noalloc_table_kernel(double *const *src, double **table, int *ac
 
 extern "C" idmrg_status idmrg_heff_apply_noalloc(idmrg_ctx *c, int p, const double *psi_dev, double *out_dev) {
   if (!c || !psi_dev || !out_dev || p < 0 || p >= c->P) return IDMRG_EINVAL;
+  if (!c->owns(p) || c->plan_pending)
+    return c->fail(IDMRG_ESTATE, "heff_apply_noalloc: superblock %d is not planned in this context", p);
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] >= ST_TRUNCATED)
       return c->fail(IDMRG_ESTATE, "heff_apply_noalloc: iteration %d is being truncated; call after idmrg_advance",

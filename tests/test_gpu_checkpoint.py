@@ -51,3 +51,4 @@ def test_checkpoint_of_another_model_is_refused(tmp_path):
         a.save(str(tmp_path / "mid.ck"))
     a.close()
     b.close()
+

@@ -1,4 +1,4 @@
-"""The m scan and eps -> 0 extrapolation of Sec. 5 through the library
+"""The m scan and eps -> 0 extrapolation of Sec. 4.4 through the library
 (idmrg_run per m, idmrg_truncation_error) against the oracle's."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""Pins of the eps -> 0 extrapolation (Sec. 5) and of the run's truncation
+"""Pins of the eps -> 0 extrapolation (Sec. 4.4) and of the run's truncation
 error (Eq. tru, reading R6)."""
 import numpy as np
 import pytest
@@ -97,3 +97,44 @@ def test_package_fits_match_the_oracle():
     c0, sd = extrapolate(eps, e)
     q0, qsd = quadratic_fit(eps, e)
     assert c0 == pytest.approx(q0, abs=1e-12) and sd == pytest.approx(qsd, rel=1e-6)
+
+
+def test_exponential_fit_needs_two_points():
+    from oracle.extrapolate import exponential_fit
+    from paper_1606_06790_gb300.scan import fit_correlation_length
+    r = np.array([1.0, 2.0, 6.0])
+    c = np.array([0.5, 0.2, 0.01])
+    for fit in (exponential_fit, fit_correlation_length):
+        with pytest.raises(ValueError):
+            fit(r, c, r_min=5)            # one point beyond r_min
+        with pytest.raises(ValueError):
+            fit(r, np.zeros(3), r_min=0)  # zeros are skipped
+
+
+def test_library_fits_special_cases():
+    """The C ABI's host fits on cases with known answers: an exact polynomial
+    of each degree is recovered at eps = 0 with zero spread; a straight line
+    with residuals (1, -3, 3, -1) d at x = 0..3 (orthogonal to 1 and x) is
+    recovered exactly with the closed-form spread d sqrt(7); Delta+- on given
+    values."""
+    import paper_1606_06790_gb300 as pkg
+    from paper_1606_06790_gb300.scan import extrapolate
+    x = np.linspace(0.0, 1e-4, 7)
+    for deg in range(0, 4):
+        coef = np.array([-0.4, 3.0, -2e4, 5e7][: deg + 1])
+        y = sum(c * x ** k for k, c in enumerate(coef))
+        v0, sd = extrapolate(x, y, degree=deg)
+        assert v0 == pytest.approx(coef[0], abs=1e-13) and sd < 1e-11
+    # line fit of y = 1 + 2x + d (1, -3, 3, -1) at x = 0..3: RSS = 20 d^2,
+    # s^2 = 10 d^2, [(A^T A)^-1]_00 = 7/10, so sd(c0) = d sqrt(7)
+    d = 1e-3
+    xx = np.arange(4.0)
+    yy = 1 + 2 * xx + d * np.array([1.0, -3.0, 3.0, -1.0])
+    v0, sd = extrapolate(xx, yy, degree=1)
+    assert v0 == pytest.approx(1.0 + d * (0.7 * 1 + 0.4 * -3 + 0.1 * 3 - 0.2 * -1), abs=1e-12)
+    assert sd == pytest.approx(d * np.sqrt(7.0), rel=1e-9)
+    avg, dp, dm = pkg.delta_pm([-0.2, -0.25, -0.21])
+    assert avg == pytest.approx(-0.22, abs=1e-15) and dp == pytest.approx(0.02, abs=1e-15)
+    assert dm == pytest.approx(-0.03, abs=1e-15)
+    with pytest.raises(ValueError):
+        pkg.delta_pm([])
