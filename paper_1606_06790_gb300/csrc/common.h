@@ -284,31 +284,6 @@ struct WTaskP {           // T3 rectangle written into a packed stage-3 A matrix
   int t3_ld;              // digit form: T3 stored at t3_off, rows of t3_ld (the task's K)
   int64_t t3_off;
 };
-// The W stage grouped by (superblock, left sector i, right input sector j):
-// every T3 rectangle (c, s, t) of such a group is a D_i x D_j matrix and a
-// combination of the same D_i x D_j slices of T1 (channel a, s', t'), so one
-// CTA loads each T1 element of a tile once and forms every output from it.
-struct WBlk {
-  int sb, rows, cols;     // superblock, D_i, D_j
-  int in0, nin;           // input slices WIn[in0 .. in0 + nin)
-  int out0, nout;         // output rectangles WOut[out0 .. out0 + nout)
-  int pad;
-};
-struct WIn {              // T1 slice: element (x, y) at off + x * ld + y (FP32)
-  int64_t off;
-  int ld, pad;
-};
-struct WOut {             // packed stage-3 A: element (x, y) at (row0 + x, k0 + y)
-  int64_t dst_off;
-  int row0, k0, KB, G;
-  int term0, nterm;       // WTermI[term0 .. term0 + nterm)
-};
-struct WTermI {
-  int in;                 // input slice within the block
-  float coef;             // two-site MPO coefficient (FP32, the stage's arithmetic)
-};
-constexpr int WBLK_TE = 128;     // elements per CTA
-constexpr int WBLK_MAXIN = 128;  // input slices per block (shared-memory tile)
 struct TcTask {
   int64_t a_off, b_off, c_off, rmap_off;
   int64_t a_exp, b_exp;   // digit form: exponent arrays of the A rows and B rows
@@ -330,10 +305,6 @@ cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, cons
                              double *const *bufs, const int *active, int bf16, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
                            const int *active, int *err, int bf16, cudaStream_t st);
-// tiles[k] = (block, element tile of WBLK_TE elements); max_in = largest nin
-cudaError_t launch_wstage_blk(const int2 *tiles, int ntiles, int max_in, const WBlk *blks, const WIn *ins,
-                              const WOut *outs, const WTermI *terms, double *const *bufs, const int *active,
-                              int bf16, cudaStream_t st);
 // FP64-accurate products from BF16 digit slices (OZ_PLANES digits of 7 bits
 // per element, exact integer accumulation per digit level).  K blocks are 32
 // elements; one launch sums at most OZ_MAX_K of K exactly, longer K runs as

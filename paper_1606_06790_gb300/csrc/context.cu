@@ -218,15 +218,7 @@ struct idmrg_ctx {
   std::vector<TcTile> tc1t, tc3t;
   std::vector<WTaskP> wtp;
   std::vector<WTerm> wtpm;
-  // the same W stage grouped by (superblock, left sector, right input sector)
-  std::vector<WBlk> wblk;
-  std::vector<WIn> wblk_in;
-  std::vector<WOut> wblk_out;
-  std::vector<WTermI> wblk_term;
-  std::vector<int2> wblk_tiles;
-  int wblk_maxin = 0;
-  bool wblk_ok = false;
-  DevBuf dwblk, dwbin, dwbout, dwbterm, dwbtiles;
+
   int pk_step_rows = 0, pk_psi_rows = 0, wtp_rows = 0;
   DevBuf dpks, dpkp, dtc1k, dtc1t, dtc3k, dtc3t, dwtp, dwtpm, dtarget;
   std::vector<DevBuf> bPA1, bPB1, bT1F, bPA3, bPB3, bRMAP;
@@ -866,13 +858,6 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
   c->tc3t.clear();
   c->wtp.clear();
   c->wtpm.clear();
-  c->wblk.clear();
-  c->wblk_in.clear();
-  c->wblk_out.clear();
-  c->wblk_term.clear();
-  c->wblk_tiles.clear();
-  c->wblk_maxin = 0;
-  c->wblk_ok = true;
   c->pk_step_rows = c->pk_psi_rows = c->wtp_rows = 0;
   auto seg = [&](std::vector<PackSeg> &v, int &mr, int sb, int dst_buf, int64_t dst_off, int src_buf,
                  int64_t src_off, int row0, int k0, int rows, int ks, int ld, int trans, int KB, int G) {
@@ -952,14 +937,6 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
         for (int nt = 0; nt < NT; ++nt) c->tc1t.push_back(TcTile{id, mt, nt, 0});
     }
     // ---------------- stage 3
-    struct BlkBuild {
-      int rows = 0, cols = 0;
-      std::vector<WIn> in;
-      std::map<std::pair<int64_t, int>, int> inmap;
-      std::vector<WOut> out;
-      std::vector<std::vector<WTermI>> tm;
-    };
-    std::map<std::pair<int, int>, BlkBuild> blocks;  // (left sector i, right input sector jin)
     std::vector<int64_t> pa3(SR, -1), pb3(SR, -1), rmo(SR, -1);
     std::vector<int64_t> rmap;
     int64_t pa3n = 0, pb3n = 0;
@@ -1041,34 +1018,6 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
               if (w.nterm == 0) continue;  // the packed rectangle stays zero
               c->wtp.push_back(w);
               c->wtp_rows = std::max(c->wtp_rows, w.rows);
-              BlkBuild &B = blocks[{i, jin}];
-              B.rows = BL.dim[i];
-              B.cols = BR.dim[jin];
-              WOut o{};
-              o.dst_off = pa3[jo];
-              o.row0 = rows_of[k];
-              o.k0 = ks[cc];
-              o.KB = KB;
-              o.G = GA;
-              std::vector<WTermI> tl;
-              for (int q = w.term0; q < w.term0 + w.nterm; ++q) {
-                const std::pair<int64_t, int> key{c->wtpm[q].in_off, c->wtpm[q].in_ld};
-                auto it = B.inmap.find(key);
-                int idx;
-                if (it == B.inmap.end()) {
-                  idx = (int)B.in.size();
-                  B.inmap[key] = idx;
-                  WIn wi{};
-                  wi.off = key.first;
-                  wi.ld = key.second;
-                  B.in.push_back(wi);
-                } else {
-                  idx = it->second;
-                }
-                tl.push_back(WTermI{idx, (float)c->wtpm[q].coef});
-              }
-              B.out.push_back(o);
-              B.tm.push_back(tl);
             }
           }
       TcTask t{};
@@ -1088,31 +1037,6 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
       c->tc3k.push_back(t);
       for (int mt = 0; mt < MT; ++mt)
         for (int nt = 0; nt < NT; ++nt) c->tc3t.push_back(TcTile{id, mt, nt, 0});
-    }
-    for (auto &kv : blocks) {
-      BlkBuild &B = kv.second;
-      WBlk b{};
-      b.sb = p;
-      b.rows = B.rows;
-      b.cols = B.cols;
-      b.in0 = (int)c->wblk_in.size();
-      b.nin = (int)B.in.size();
-      b.out0 = (int)c->wblk_out.size();
-      b.nout = (int)B.out.size();
-      if (b.nin > WBLK_MAXIN) c->wblk_ok = false;
-      c->wblk_maxin = std::max(c->wblk_maxin, b.nin);
-      c->wblk_in.insert(c->wblk_in.end(), B.in.begin(), B.in.end());
-      for (size_t o = 0; o < B.out.size(); ++o) {
-        WOut w = B.out[o];
-        w.term0 = (int)c->wblk_term.size();
-        w.nterm = (int)B.tm[o].size();
-        c->wblk_term.insert(c->wblk_term.end(), B.tm[o].begin(), B.tm[o].end());
-        c->wblk_out.push_back(w);
-      }
-      const int id = (int)c->wblk.size();
-      c->wblk.push_back(b);
-      const int64_t nt = ((int64_t)b.rows * b.cols + WBLK_TE - 1) / WBLK_TE;
-      for (int64_t t = 0; t < nt; ++t) c->wblk_tiles.push_back(make_int2(id, (int)t));
     }
     NOMEM(c->ensure(c->bPA1[p], 4 * std::max<int64_t>(pa1n, 4)) &&
           c->ensure(c->bPB1[p], 4 * std::max<int64_t>(pb1n, 4)) &&
@@ -1134,9 +1058,6 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
   NOMEM(c->upload(c->dpks, c->pk_step) && c->upload(c->dpkp, c->pk_psi) && c->upload(c->dtc1k, c->tc1k) &&
         c->upload(c->dtc1t, c->tc1t) && c->upload(c->dtc3k, c->tc3k) && c->upload(c->dtc3t, c->tc3t) &&
         c->upload(c->dwtp, c->wtp) && c->upload(c->dwtpm, c->wtpm));
-  if (c->wblk_ok)
-    NOMEM(c->upload(c->dwblk, c->wblk) && c->upload(c->dwbin, c->wblk_in) && c->upload(c->dwbout, c->wblk_out) &&
-          c->upload(c->dwbterm, c->wblk_term) && c->upload(c->dwbtiles, c->wblk_tiles));
   NOMEM(c->upload(c->dbufs, c->hbufs));
   // split the environments once for this iteration
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
@@ -1504,13 +1425,8 @@ idmrg_status heff_launch_mixed(idmrg_ctx *c, const int *active_dev, const int *a
                     (int *)c->derr.p, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_GEMM);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
-  if (c->wblk_ok)
-    CK(launch_wstage_blk((const int2 *)c->dwbtiles.p, (int)c->wblk_tiles.size(), c->wblk_maxin,
-                         (const WBlk *)c->dwblk.p, (const WIn *)c->dwbin.p, (const WOut *)c->dwbout.p,
-                         (const WTermI *)c->dwbterm.p, bufs, active_dev, c->bf16, c->st));
-  else
-    CK(launch_wstage_tc((const WTaskP *)c->dwtp.p, (int)c->wtp.size(), c->wtp_rows, (const WTerm *)c->dwtpm.p,
-                        bufs, active_dev, c->bf16, c->st));
+  CK(launch_wstage_tc((const WTaskP *)c->dwtp.p, (int)c->wtp.size(), c->wtp_rows, (const WTerm *)c->dwtpm.p, bufs,
+                      active_dev, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
   c->kbegin(IDMRG_K_HEFF_GEMM);
   CK(launch_tc_gemm((const TcTile *)c->dtc3t.p, (int)c->tc3t.size(), (const TcTask *)c->dtc3k.p, bufs, active_dev,
@@ -3470,8 +3386,7 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
                     &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgk, &c->dsgs,
                     &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
-                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dwblk, &c->dwbin, &c->dwbout, &c->dwbterm,
-                    &c->dwbtiles, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp, &c->doz1k,
+                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp, &c->doz1k,
                     &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp, &c->goz_planes,
                     &c->goz_exps})
     rel(*b);
@@ -3863,9 +3778,9 @@ idmrg_status idmrg_import_pair(idmrg_ctx *c, int q, const void *host, size_t len
   int n = 0, qq = -1;
   F.get(n);
   F.get(qq);
-  if (!F.ok || qq != q || n != c->n - 1)
-    return c->fail(IDMRG_EINVAL, "import_pair: data of pair %d after iteration %d, expected pair %d after %d", qq, n,
-                   q, c->n - 1);
+  if (!F.ok || qq != q || n != c->n)  // both sides have advanced to the next iteration
+    return c->fail(IDMRG_EINVAL, "import_pair: data of pair %d for iteration %d, expected pair %d for %d", qq, n, q,
+                   c->n);
   Env &E = c->envR[q];
   Basis b;
   std::vector<int> chq;

@@ -435,7 +435,16 @@ __global__ void norm_finish_kernel(const int64_t *Ns, int S, const double *part,
 // dst = src / sqrt(nrm2)  and resets the Lanczos state of that superblock
 __global__ void init_scale_kernel(LanczosDev L, const double *const *src, const double *nrm2) {
   const int s = blockIdx.y;
-  if (!L.member[s]) return;
+  if (!L.member[s]) {
+    // a superblock outside this solve: inactive, its vector pointer at V[0]
+    // (the flags live in reused device memory and are read by every kernel
+    // of the iteration, so they are set here, not assumed)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      L.active[s] = 0;
+      L.k[s] = 0;
+    }
+    return;
+  }
   const int64_t N = L.N[s];
   const double inv = 1.0 / sqrt(nrm2[s]);
   for (int64_t e = (int64_t)blockIdx.x * CH + threadIdx.x; e < min(N, (int64_t)(blockIdx.x + 1) * CH); e += LT)

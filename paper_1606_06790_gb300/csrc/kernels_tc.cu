@@ -95,62 +95,111 @@ __global__ void pack_kernel(const PackSeg *__restrict__ segs, double *const *__r
   }
 }
 
+// T3 = sum W12 T1 into the packed stage-3 A operand.  The two-site MPO is
+// mostly pass-through (a T3 rectangle copies one T1 rectangle), so the stage
+// is bound by instructions per element rather than by arithmetic: a thread
+// takes one row and one 16-byte core-matrix row of the packed K range (8
+// BF16 or 4 TF32 elements), forms those elements from nterm T1 rows, and
+// stores the hi and lo parts with one 16-byte store each; only the partial
+// groups at the edges of a rectangle are written element by element.
+constexpr int WROWS = 8;  // rectangle rows per CTA
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+template <int GW>  // elements per 16-byte group: 8 (BF16) or 4 (TF32)
+__device__ __forceinline__ void wstage_group(const WTaskP &t, const WTerm *__restrict__ terms, const float *in,
+                                             float *dst, int r, int kg) {
+  // kg: first packed k of the group (a multiple of GW); columns c = kg + j - k0
+  const int cbeg = max(kg, t.k0) - t.k0, cend = min(kg + GW, t.k0 + t.cols) - t.k0;
+  float acc[GW];
+#pragma unroll
+  for (int j = 0; j < GW; ++j) acc[j] = 0.f;
+  const int j0 = cbeg - (kg - t.k0);  // first valid lane of the group
+  for (int q = 0; q < t.nterm; ++q) {
+    const WTerm w = terms[t.term0 + q];
+    const float cf = (float)w.coef;
+    const float *src = in + w.in_off + (int64_t)r * w.in_ld + (kg - t.k0);
+#pragma unroll
+    for (int j = 0; j < GW; ++j)
+      if (j >= j0 && j < j0 + (cend - cbeg)) acc[j] = fmaf(cf, src[j], acc[j]);
+  }
+  const int row = t.row0 + r, rpt = 8 * t.G;
+  const int rt = row / rpt, rr = row - rt * rpt;
+  if (GW == 8) {  // BF16 pairs, 64 elements per K block
+    const int kb = kg >> 6, kc = (kg & 63) >> 3;
+    const int64_t tile_h = (int64_t)rpt * 64;
+    const int64_t o = ((int64_t)rt * t.KB + kb) * 2 * tile_h + (((int64_t)kc * t.G + (rr >> 3)) * 8 + (rr & 7)) * 8;
+    __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      hi[j] = __float2bfloat16_rn(acc[j]);
+      lo[j] = __float2bfloat16_rn(acc[j] - __bfloat162float(hi[j]));
+    }
+    __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(dst) + o;
+    if (cend - cbeg == 8) {
+      uint4 hv, lv;
+      hv.x = pack_bf16x2(hi[0], hi[1]);
+      hv.y = pack_bf16x2(hi[2], hi[3]);
+      hv.z = pack_bf16x2(hi[4], hi[5]);
+      hv.w = pack_bf16x2(hi[6], hi[7]);
+      lv.x = pack_bf16x2(lo[0], lo[1]);
+      lv.y = pack_bf16x2(lo[2], lo[3]);
+      lv.z = pack_bf16x2(lo[4], lo[5]);
+      lv.w = pack_bf16x2(lo[6], lo[7]);
+      *reinterpret_cast<uint4 *>(h) = hv;
+      *reinterpret_cast<uint4 *>(h + tile_h) = lv;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j >= j0 && j < j0 + (cend - cbeg)) {
+          h[j] = hi[j];
+          h[tile_h + j] = lo[j];
+        }
+    }
+  } else {  // TF32 pairs, 32 elements per K block
+    const int kb = kg >> 5, kc = (kg & 31) >> 2;
+    const int64_t tile_f = (int64_t)rpt * 32;
+    const int64_t o = ((int64_t)rt * t.KB + kb) * 2 * tile_f + (((int64_t)kc * t.G + (rr >> 3)) * 8 + (rr & 7)) * 4;
+    float hi[4], lo[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      hi[j] = tf32_round(acc[j]);
+      lo[j] = acc[j] - hi[j];
+    }
+    float *f = dst + o;
+    if (cend - cbeg == 4) {
+      *reinterpret_cast<float4 *>(f) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<float4 *>(f + tile_f) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j >= j0 && j < j0 + (cend - cbeg)) {
+          f[j] = hi[j];
+          f[tile_f + j] = lo[j];
+        }
+    }
+  }
+}
+
 __global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *__restrict__ terms,
                                  double *const *__restrict__ bufs, const int *__restrict__ active, int bf16) {
   const WTaskP t = tasks[blockIdx.x];
   if (active && !active[t.sb]) return;
-  const int r0 = blockIdx.y * PROWS;
+  const int r0 = blockIdx.y * WROWS;
   if (r0 >= t.rows) return;
-  const int r1 = min(t.rows, r0 + PROWS);
+  const int nr = min(t.rows - r0, WROWS);
   const float *in = (const float *)bufs[t.sb * NBUF + t.in_buf];
   float *dst = (float *)bufs[t.sb * NBUF + t.dst_buf] + t.dst_off;
-  const int n = (r1 - r0) * t.cols;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int r = r0 + e / t.cols, c = e % t.cols;
-    float acc = 0.f;
-    for (int q = 0; q < t.nterm; ++q) {
-      const WTerm w = terms[t.term0 + q];
-      acc = fmaf((float)w.coef, in[w.in_off + (int64_t)r * w.in_ld + c], acc);
-    }
-    put_split(dst, t.row0 + r, t.k0 + c, t.KB, t.G, bf16, (double)acc);
-  }
-}
-
-// W stage by blocks (see WBlk): the CTA stages its tile of every input slice
-// in shared memory (each T1 element read once from memory), then each thread
-// forms outputs of one element from the staged values and writes their hi/lo
-// split into the packed stage-3 operand.
-__global__ void __launch_bounds__(256) wstage_blk_kernel(const int2 *__restrict__ tiles, const WBlk *__restrict__ blks,
-                                  const WIn *__restrict__ ins, const WOut *__restrict__ outs,
-                                  const WTermI *__restrict__ terms, double *const *__restrict__ bufs,
-                                  const int *__restrict__ active, int bf16) {
-  extern __shared__ float vin[];  // [nin][WBLK_TE]
-  const int2 tl = tiles[blockIdx.x];  // (block, element tile)
-  const WBlk b = blks[tl.x];
-  if (active && !active[b.sb]) return;
-  const int elems = b.rows * b.cols;
-  const int e0 = tl.y * WBLK_TE;
-  if (e0 >= elems) return;
-  // thread -> (element e, half h): element coordinates once per thread
-  const int e = threadIdx.x % WBLK_TE, h = threadIdx.x / WBLK_TE, nh = blockDim.x / WBLK_TE;
-  const bool live = e0 + e < elems;
-  const int x = live ? (e0 + e) / b.cols : 0, y = live ? (e0 + e) - x * b.cols : 0;
-  const float *t1 = (const float *)bufs[b.sb * NBUF + BUF_T1F];
-  for (int in = h; in < b.nin; in += nh) {
-    const WIn w = ins[b.in0 + in];
-    vin[in * WBLK_TE + e] = live ? t1[w.off + (int64_t)x * w.ld + y] : 0.f;
-  }
-  __syncthreads();
-  if (!live) return;
-  float *dst = (float *)bufs[b.sb * NBUF + BUF_PA3];
-  for (int o = h; o < b.nout; o += nh) {
-    const WOut w = outs[b.out0 + o];
-    float acc = 0.f;
-    for (int q = 0; q < w.nterm; ++q) {
-      const WTermI t = terms[w.term0 + q];
-      acc = fmaf(t.coef, vin[t.in * WBLK_TE + e], acc);
-    }
-    put_split(dst + w.dst_off, w.row0 + x, w.k0 + y, w.KB, w.G, bf16, (double)acc);
+  const int gw = bf16 ? 8 : 4;
+  const int g0 = t.k0 / gw, ng = (t.k0 + t.cols - 1) / gw - g0 + 1;
+  for (int i = threadIdx.x; i < nr * ng; i += blockDim.x) {
+    const int rr = i / ng, g = i - rr * ng;
+    if (bf16)
+      wstage_group<8>(t, terms, in, dst, r0 + rr, (g0 + g) * 8);
+    else
+      wstage_group<4>(t, terms, in, dst, r0 + rr, (g0 + g) * 4);
   }
 }
 
@@ -299,6 +348,210 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0 && !(aborted & 2)) tc::tmem_dealloc(tmem, TC_TN);
+}
+
+// ---------------------------------------------- persistent grouped GEMM
+// The same tiles and operands as tc_gemm_kernel, with one CTA per SM looping
+// over the tile list (tile t = blockIdx.x + i gridDim.x) and three roles:
+// warp 0 streams the K blocks of successive tiles through a PS_STAGES-deep
+// ring of shared memory (bulk copies), warp 1 issues the MMA chain of a tile
+// into one of two TMEM accumulators, warps 2-5 read the other accumulator out
+// (tcgen05.ld) and store it.  Set-up, pipeline fill and epilogue of a tile
+// thereby overlap the next tile's copies and MMAs, which matters when K is a
+// few blocks (stage 1 of H_eff psi: K = one sector of the left block).
+// Ring and accumulator buffers are handed over by mbarriers whose phases
+// follow from running counters; every wait is bounded, a timeout sets the
+// error word and makes every role leave its loop, and the accumulators are
+// released only once every MMA issued has completed.
+constexpr int PS_STAGES = 4;
+constexpr int PS_THREADS = 192;
+
+template <bool BF16>
+__global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile *__restrict__ tiles, int ntiles,
+                                                                   const TcTask *__restrict__ tasks,
+                                                                   double *const *__restrict__ bufs,
+                                                                   const int *__restrict__ active, int *err) {
+  extern __shared__ __align__(1024) float sm[];
+  __shared__ __align__(8) uint64_t full[PS_STAGES], empty[PS_STAGES], accf[2], acce[2], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 2 * TC_TN);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < PS_STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&accf[a], 1);
+      tc::mbar_init(&acce[a], 4);  // one arrival per epilogue warp
+    }
+    tc::mbar_init(&done, 1);
+    abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  volatile int *abort_v = &abort_flag;
+  constexpr uint32_t stage_bytes = 4u * STAGE_FLOATS;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- producer
+      long long it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TcTile tile = tiles[t];
+        const TcTask T = tasks[tile.task];
+        if (active && !active[T.sb]) continue;
+        const float *A = (const float *)bufs[T.sb * NBUF + T.a_buf] + T.a_off + (int64_t)tile.mt * T.KB * 2 * A_TILE;
+        const float *B = (const float *)bufs[T.sb * NBUF + T.b_buf] + T.b_off + (int64_t)tile.nt * T.KB * 2 * B_TILE;
+        for (int kb = 0; kb < T.KB; ++kb, ++it) {
+          const int s = (int)(it % PS_STAGES);
+          const long long u = it / PS_STAGES;
+          if (*abort_v || (u > 0 && !tc::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), WAIT_BUDGET))) {
+            ok = false;
+            break;
+          }
+          float *st = sm + s * STAGE_FLOATS;
+          tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+          tc::bulk_g2s(st, A + (int64_t)kb * 2 * A_TILE, 4u * 2 * A_TILE, &full[s]);
+          tc::bulk_g2s(st + 2 * A_TILE, B + (int64_t)kb * 2 * B_TILE, 4u * 2 * B_TILE, &full[s]);
+        }
+      }
+      if (!ok) {
+        atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+        atomicOr(&abort_flag, 1);
+      }
+      // the copies of the last ring window may still be in flight: wait for them
+      for (long long j = it > PS_STAGES ? it - PS_STAGES : 0; j < it; ++j)
+        tc::mbar_wait(&full[j % PS_STAGES], (uint32_t)((j / PS_STAGES) & 1), WAIT_BUDGET);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, BF16 ? 1u : 2u);
+      constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TC_TN / 8) * 128, sbo = 128;
+      long long it = 0;
+      int lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TcTile tile = tiles[t];
+        const TcTask T = tasks[tile.task];
+        if (active && !active[T.sb]) continue;
+        const int a = lt & 1, v = lt >> 1;
+        if (*abort_v || (v > 0 && !tc::mbar_wait(&acce[a], (uint32_t)((v - 1) & 1), WAIT_BUDGET))) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(a * TC_TN);
+        for (int kb = 0; kb < T.KB; ++kb, ++it) {
+          const int s = (int)(it % PS_STAGES);
+          if (!tc::mbar_wait(&full[s], (uint32_t)((it / PS_STAGES) & 1), WAIT_BUDGET)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(sm + s * STAGE_FLOATS);
+          const uint32_t sb = sa + 4u * 2 * A_TILE;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ahi = tc::smem_desc(sa + kk * 2 * lboA, lboA, sbo);
+            const uint64_t alo = tc::smem_desc(sa + 4u * A_TILE + kk * 2 * lboA, lboA, sbo);
+            const uint64_t bhi = tc::smem_desc(sb + kk * 2 * lboB, lboB, sbo);
+            const uint64_t blo = tc::smem_desc(sb + 4u * B_TILE + kk * 2 * lboB, lboB, sbo);
+            const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+            if (BF16) {
+              tc::mma_f16(d, ahi, bhi, idesc, acc0);
+              tc::mma_f16(d, ahi, blo, idesc, 1u);
+              tc::mma_f16(d, alo, bhi, idesc, 1u);
+            } else {
+              tc::mma_tf32(d, ahi, bhi, idesc, acc0);
+              tc::mma_tf32(d, ahi, blo, idesc, 1u);
+              tc::mma_tf32(d, alo, bhi, idesc, 1u);
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&accf[a]);  // the accumulator of this tile is complete
+        ++lt;
+      }
+      if (!ok) {
+        atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+        atomicOr(&abort_flag, 1);
+      }
+      tc::mma_commit(&done);  // fires once every MMA issued above has completed
+    }
+  } else {  // ---- epilogue, warps 2..5: TMEM lane quarter q = warp % 4
+    const int q = warp & 3;
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TcTile tile = tiles[t];
+      const TcTask T = tasks[tile.task];
+      if (active && !active[T.sb]) continue;
+      const int a = lt & 1, v = lt >> 1;
+      // every lane waits; the warp goes on only together (tcgen05.ld is warp-wide)
+      const bool got = !*abort_v && tc::mbar_wait(&accf[a], (uint32_t)(v & 1), WAIT_BUDGET);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) {
+          atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+          atomicOr(&abort_flag, 1);
+        }
+        break;
+      }
+      tc::fence_after_sync();
+      const int row = tile.mt * TM + 32 * q + lane;
+      const int col0 = tile.nt * TC_TN;
+      double *cbase = bufs[T.sb * NBUF + T.c_buf];
+      int64_t obase = 0;
+      if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
+#pragma unroll
+      for (int c = 0; c < TC_TN; c += 16) {
+        float vv[16];
+        if (T.KB > 0) {
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TC_TN + c), vv);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) vv[i] = 0.f;
+        }
+        if (row < T.M) {
+          if (T.mode == 0) {
+            float *out = (float *)cbase + T.c_off + (int64_t)row * T.ldc + col0 + c;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (col0 + c + i < T.N) out[i] = vv[i];
+          } else {
+            double *out = cbase + obase + col0 + c;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (col0 + c + i < T.N) out[i] = (double)vv[i];
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[a]);  // this quarter of the accumulator is free
+      ++lt;
+    }
+  }
+  __syncthreads();
+  const bool ready = tc::mbar_wait(&done, 0, WAIT_BUDGET);
+  if (!ready) {
+    atomicOr(&abort_flag, 2);
+    if (lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  const int aborted = abort_flag;
+  if (warp == 0 && !(aborted & 2)) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * TC_TN);
+  }
 }
 
 // ------------------------------------------- FP64-accurate digit-slice form
@@ -688,31 +941,28 @@ cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *con
 cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
                              double *const *bufs, const int *active, int bf16, cudaStream_t st) {
   if (ntasks > 0 && max_rows > 0) {
-    dim3 grid(ntasks, (max_rows + PROWS - 1) / PROWS);
-    wstage_tc_kernel<<<grid, 256, 0, st>>>(tasks, terms, bufs, active, bf16);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_wstage_blk(const int2 *tiles, int ntiles, int max_in, const WBlk *blks, const WIn *ins,
-                              const WOut *outs, const WTermI *terms, double *const *bufs, const int *active,
-                              int bf16, cudaStream_t st) {
-  if (ntiles > 0) {
-    const int smem = max_in * WBLK_TE * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(wstage_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    wstage_blk_kernel<<<ntiles, 256, smem, st>>>(tiles, blks, ins, outs, terms, bufs, active, bf16);
+    dim3 grid(ntasks, (max_rows + WROWS - 1) / WROWS);
+    wstage_tc_kernel<<<grid, 128, 0, st>>>(tasks, terms, bufs, active, bf16);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
                            const int *active, int *err, int bf16, cudaStream_t st) {
-  const int smem = TC_STAGES * STAGE_FLOATS * (int)sizeof(float);
-  auto kern = bf16 ? tc_gemm_kernel<true> : tc_gemm_kernel<false>;
+  if (ntiles <= 0) return cudaGetLastError();
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || sms <= 0) return e != cudaSuccess ? e : cudaErrorInvalidValue;
+  }
+  const int smem = PS_STAGES * STAGE_FLOATS * (int)sizeof(float);
+  auto kern = bf16 ? tc_gemm_ps_kernel<true> : tc_gemm_ps_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (ntiles > 0) kern<<<ntiles, 128, smem, st>>>(tiles, tasks, bufs, active, err);
+  const int grid = ntiles < sms ? ntiles : sms;
+  kern<<<grid, PS_THREADS, smem, st>>>(tiles, ntiles, tasks, bufs, active, err);
   return cudaGetLastError();
 }
 
