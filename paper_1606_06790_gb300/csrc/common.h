@@ -297,11 +297,14 @@ struct TcTask {
 struct TcTile {
   int task, mt, nt, pad;
 };
-constexpr int TC_TN = 64;      // N tile (TMEM columns)
-constexpr int TC_STAGES = 2;   // shared-memory ring depth
+constexpr int TC_TN = 64;      // N tile of the digit-slice GEMM (TMEM columns per level)
+constexpr int MIX_TN = 64;     // N tile of the split-operand (TF32x3 / BF16x3) GEMM
 cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
                         int bf16, cudaStream_t st);
-cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
+// W stage work units: units[k] = (task, first row, rows), sized so that a
+// unit holds about WUNIT_ITEMS (row, 16-byte group) items, one per thread
+constexpr int WUNIT_ITEMS = 256;
+cudaError_t launch_wstage_tc(const int4 *units, int nunits, const WTaskP *tasks, const WTerm *terms,
                              double *const *bufs, const int *active, int bf16, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
                            const int *active, int *err, int bf16, cudaStream_t st);

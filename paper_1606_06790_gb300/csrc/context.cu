@@ -218,6 +218,8 @@ struct idmrg_ctx {
   std::vector<TcTile> tc1t, tc3t;
   std::vector<WTaskP> wtp;
   std::vector<WTerm> wtpm;
+  std::vector<int4> wunits;  // W stage work units (task, first row, rows)
+  DevBuf dwunits;
 
   int pk_step_rows = 0, pk_psi_rows = 0, wtp_rows = 0;
   DevBuf dpks, dpkp, dtc1k, dtc1t, dtc3k, dtc3t, dwtp, dwtpm, dtarget;
@@ -845,9 +847,9 @@ idmrg_status sync_bufs(idmrg_ctx *c) {
 //     the R channels, N = y in jo.
 idmrg_status plan_mixed(idmrg_ctx *c) {
   const int P = c->P, d = c->d, target = c->o.target_charge, dd = d * d;
-  const int GA = 16, GB = TC_TN / 8;
+  const int GA = 16, GB = MIX_TN / 8;
   // one packed K block is 128 bytes of every row: TA / TB floats per hi or lo tile
-  const int64_t TA = 128 * 32, TB = (int64_t)TC_TN * 32;
+  const int64_t TA = 128 * 32, TB = (int64_t)MIX_TN * 32;
   const int kblk = c->bf16 ? 64 : 32;
   auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
   c->pk_step.clear();
@@ -904,7 +906,7 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
       }
       if (M == 0) continue;
       const int K = BL.dim[si], N = psi.C[si];
-      const int KB = (int)cdiv(K, kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      const int KB = (int)cdiv(K, kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, MIX_TN);
       pa1[si] = pa1n;
       pa1n += (int64_t)MT * KB * 2 * TA;
       pb1[si] = pb1n;
@@ -965,7 +967,7 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
           }
       if (M == 0) continue;
       const int N = BR.dim[jo];
-      const int KB = (int)cdiv(std::max(K, 1), kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, TC_TN);
+      const int KB = (int)cdiv(std::max(K, 1), kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, MIX_TN);
       pa3[jo] = pa3n;
       pa3n += (int64_t)MT * KB * 2 * TA;
       pb3[jo] = pb3n;
@@ -1055,6 +1057,19 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
     c->hbufs[p * NBUF + BUF_PB3] = c->dp(c->bPB3[p]);
     c->hbufs[p * NBUF + BUF_RMAP] = c->dp(c->bRMAP[p]);
   }
+  // W stage units: rows of a rectangle grouped so that a unit has about
+  // WUNIT_ITEMS (row, 16-byte group) items
+  c->wunits.clear();
+  {
+    const int gw = c->bf16 ? 8 : 4;
+    for (size_t k = 0; k < c->wtp.size(); ++k) {
+      const WTaskP &w = c->wtp[k];
+      const int ng = (w.k0 + w.cols - 1) / gw - w.k0 / gw + 1;
+      const int rpu = std::max(1, WUNIT_ITEMS / ng);
+      for (int r0 = 0; r0 < w.rows; r0 += rpu) c->wunits.push_back(make_int4((int)k, r0, std::min(rpu, w.rows - r0), 0));
+    }
+  }
+  NOMEM(c->upload(c->dwunits, c->wunits));
   NOMEM(c->upload(c->dpks, c->pk_step) && c->upload(c->dpkp, c->pk_psi) && c->upload(c->dtc1k, c->tc1k) &&
         c->upload(c->dtc1t, c->tc1t) && c->upload(c->dtc3k, c->tc3k) && c->upload(c->dtc3t, c->tc3t) &&
         c->upload(c->dwtp, c->wtp) && c->upload(c->dwtpm, c->wtpm));
@@ -1425,8 +1440,8 @@ idmrg_status heff_launch_mixed(idmrg_ctx *c, const int *active_dev, const int *a
                     (int *)c->derr.p, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_GEMM);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
-  CK(launch_wstage_tc((const WTaskP *)c->dwtp.p, (int)c->wtp.size(), c->wtp_rows, (const WTerm *)c->dwtpm.p, bufs,
-                      active_dev, c->bf16, c->st));
+  CK(launch_wstage_tc((const int4 *)c->dwunits.p, (int)c->wunits.size(), (const WTaskP *)c->dwtp.p,
+                      (const WTerm *)c->dwtpm.p, bufs, active_dev, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
   c->kbegin(IDMRG_K_HEFF_GEMM);
   CK(launch_tc_gemm((const TcTile *)c->dtc3t.p, (int)c->tc3t.size(), (const TcTask *)c->dtc3k.p, bufs, active_dev,
@@ -3386,7 +3401,8 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
                     &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgk, &c->dsgs,
                     &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
-                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp, &c->doz1k,
+                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dwunits, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp,
+                    &c->doz1k,
                     &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp, &c->goz_planes,
                     &c->goz_exps})
     rel(*b);

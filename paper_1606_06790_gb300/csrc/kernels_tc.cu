@@ -15,16 +15,18 @@
 //              contiguous range that a single bulk (TMA) copy moves.
 //  wstage_tc : T3[c] = sum W12 T1[a] from the FP32 stage-1 output, written
 //              straight into the packed A operand of stage 3.
-//  tc_gemm   : grouped GEMM, one 128 x 64 output tile per CTA.  Thread 0
-//              streams the hi/lo tiles of A and B through a ring of shared
-//              memory stages with cp.async.bulk and issues the tcgen05.mma
-//              chain; the four warps then read the accumulator out of tensor
-//              memory (tcgen05.ld) and store it as FP32 (stage 1) or, through a
-//              row map, as FP64 into the output wavefunction (stage 3).
-//              Every mbarrier wait is bounded; a timeout sets the context's
-//              error word, waits (bounded) for the CTA's copies in flight, and
-//              skips the epilogue; tensor memory is released unless the wait
-//              for the MMAs themselves ran out (they may still write it).
+//  tc_gemm   : persistent grouped GEMM over a list of 128 x MIX_TN output
+//              tiles, one CTA per SM: a producer warp streams the hi/lo tiles
+//              of A and B through a ring of shared-memory stages with
+//              cp.async.bulk, an MMA warp issues the tcgen05.mma chain into one
+//              of two tensor-memory accumulators, four epilogue warps read the
+//              other out (tcgen05.ld) and store it as FP32 (stage 1) or,
+//              through a row map, as FP64 into the output wavefunction
+//              (stage 3).  Every mbarrier wait is bounded; a timeout sets the
+//              context's error word and ends every role's loop, the copies in
+//              flight are waited for (bounded), and tensor memory is released
+//              unless the wait for the MMAs themselves ran out (they may still
+//              write it).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -102,7 +104,6 @@ __global__ void pack_kernel(const PackSeg *__restrict__ segs, double *const *__r
 // BF16 or 4 TF32 elements), forms those elements from nterm T1 rows, and
 // stores the hi and lo parts with one 16-byte store each; only the partial
 // groups at the edges of a rectangle are written element by element.
-constexpr int WROWS = 8;  // rectangle rows per CTA
 
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
@@ -183,13 +184,13 @@ __device__ __forceinline__ void wstage_group(const WTaskP &t, const WTerm *__res
   }
 }
 
-__global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *__restrict__ terms,
-                                 double *const *__restrict__ bufs, const int *__restrict__ active, int bf16) {
-  const WTaskP t = tasks[blockIdx.x];
+__global__ void wstage_tc_kernel(const int4 *__restrict__ units, const WTaskP *__restrict__ tasks,
+                                 const WTerm *__restrict__ terms, double *const *__restrict__ bufs,
+                                 const int *__restrict__ active, int bf16) {
+  const int4 u = units[blockIdx.x];  // (task, first row, rows)
+  const WTaskP t = tasks[u.x];
   if (active && !active[t.sb]) return;
-  const int r0 = blockIdx.y * WROWS;
-  if (r0 >= t.rows) return;
-  const int nr = min(t.rows - r0, WROWS);
+  const int r0 = u.y, nr = u.z;
   const float *in = (const float *)bufs[t.sb * NBUF + t.in_buf];
   float *dst = (float *)bufs[t.sb * NBUF + t.dst_buf] + t.dst_off;
   const int gw = bf16 ? 8 : 4;
@@ -205,154 +206,13 @@ __global__ void wstage_tc_kernel(const WTaskP *__restrict__ tasks, const WTerm *
 
 constexpr int TM = 128;
 constexpr int A_TILE = TM * 32;         // floats per A tile (one of hi/lo)
-constexpr int B_TILE = TC_TN * 32;      // floats per B tile
+constexpr int B_TILE = MIX_TN * 32;     // floats per B tile
 constexpr int STAGE_FLOATS = 2 * A_TILE + 2 * B_TILE;
 constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (about 2 s)
 
-template <bool BF16>
-__global__ void __launch_bounds__(128) tc_gemm_kernel(const TcTile *__restrict__ tiles,
-                                                      const TcTask *__restrict__ tasks,
-                                                      double *const *__restrict__ bufs,
-                                                      const int *__restrict__ active, int *err) {
-  extern __shared__ __align__(1024) float sm[];
-  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
-  __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
-  const TcTile tile = tiles[blockIdx.x];
-  const TcTask T = tasks[tile.task];
-  if (active && !active[T.sb]) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, TC_TN);
-    tc::tmem_relinquish();
-  }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
-    }
-    tc::mbar_init(&done, 1);
-    abort_flag = 0;
-    tc::fence_mbar_init();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = tmem_base;
-  if (threadIdx.x == 0) {
-    const float *A = (const float *)bufs[T.sb * NBUF + T.a_buf] + T.a_off + (int64_t)tile.mt * T.KB * 2 * A_TILE;
-    const float *B = (const float *)bufs[T.sb * NBUF + T.b_buf] + T.b_off + (int64_t)tile.nt * T.KB * 2 * B_TILE;
-    constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, BF16 ? 1u : 2u);
-    constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TC_TN / 8) * 128, sbo = 128;
-    constexpr uint32_t stage_bytes = 4u * STAGE_FLOATS;
-    auto issue = [&](int kb) {
-      const int s = kb % TC_STAGES;
-      float *st = sm + s * STAGE_FLOATS;
-      tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
-      tc::bulk_g2s(st, A + (int64_t)kb * 2 * A_TILE, 4u * 2 * A_TILE, &full[s]);
-      tc::bulk_g2s(st + 2 * A_TILE, B + (int64_t)kb * 2 * B_TILE, 4u * 2 * B_TILE, &full[s]);
-    };
-    bool ok = true;
-    int issued = 0, consumed = 0;  // K blocks whose copies were issued / whose MMAs were issued
-    for (int kb = 0; kb < T.KB && kb < TC_STAGES - 1; ++kb) {
-      issue(kb);
-      issued = kb + 1;
-    }
-    for (int kb = 0; kb < T.KB && ok; ++kb) {
-      const int kn = kb + TC_STAGES - 1;
-      if (kn < T.KB) {
-        const int sn = kn % TC_STAGES;
-        if (kn >= TC_STAGES && !tc::mbar_wait(&empty[sn], ((kn / TC_STAGES) - 1) & 1, WAIT_BUDGET)) {
-          ok = false;
-          break;
-        }
-        issue(kn);
-        issued = kn + 1;
-      }
-      const int s = kb % TC_STAGES;
-      if (!tc::mbar_wait(&full[s], (kb / TC_STAGES) & 1, WAIT_BUDGET)) {
-        ok = false;
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t sa = tc::smem_u32(sm + s * STAGE_FLOATS);
-      const uint32_t sb = sa + 4u * 2 * A_TILE;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t ahi = tc::smem_desc(sa + kk * 2 * lboA, lboA, sbo);
-        const uint64_t alo = tc::smem_desc(sa + 4u * A_TILE + kk * 2 * lboA, lboA, sbo);
-        const uint64_t bhi = tc::smem_desc(sb + kk * 2 * lboB, lboB, sbo);
-        const uint64_t blo = tc::smem_desc(sb + 4u * B_TILE + kk * 2 * lboB, lboB, sbo);
-        if (BF16) {  // K = 16 per MMA: 32 bytes of every row, as for TF32
-          tc::mma_f16(tmem, ahi, bhi, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_f16(tmem, ahi, blo, idesc, 1u);
-          tc::mma_f16(tmem, alo, bhi, idesc, 1u);
-        } else {
-          tc::mma_tf32(tmem, ahi, bhi, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_tf32(tmem, ahi, blo, idesc, 1u);
-          tc::mma_tf32(tmem, alo, bhi, idesc, 1u);
-        }
-      }
-      tc::mma_commit(&empty[s]);
-      consumed = kb + 1;
-    }
-    if (!ok) {
-      atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
-      atomicOr(&abort_flag, 1);
-      // wait (bounded) for this CTA's copies still in flight before it may exit
-      for (int j = consumed; j < issued; ++j) tc::mbar_wait(&full[j % TC_STAGES], (j / TC_STAGES) & 1, WAIT_BUDGET);
-    }
-    tc::mma_commit(&done);  // fires when every MMA issued above has completed
-  }
-  // epilogue: every thread waits for the accumulator; if that wait runs out,
-  // MMAs may still write the accumulator, so neither the epilogue nor the
-  // TMEM release runs (the error word reports the timeout)
-  const bool ready = tc::mbar_wait(&done, 0, WAIT_BUDGET);
-  if (!ready) {
-    atomicOr(&abort_flag, 2);
-    if (lane == 0) atomicOr(err, IDMRG_DEV_ERR_TIMEOUT);
-  }
-  __syncthreads();
-  tc::fence_after_sync();
-  const int aborted = abort_flag;
-  if (!aborted) {
-    const int row = tile.mt * TM + 32 * warp + lane;
-    const int col0 = tile.nt * TC_TN;
-    double *cbase = bufs[T.sb * NBUF + T.c_buf];
-    int64_t obase = 0;
-    if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
-#pragma unroll
-    for (int c = 0; c < TC_TN; c += 16) {
-      float v[16];
-      if (T.KB > 0) {
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c, v);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
-      }
-      if (row < T.M) {
-        if (T.mode == 0) {
-          float *out = (float *)cbase + T.c_off + (int64_t)row * T.ldc + col0 + c;
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (col0 + c + i < T.N) out[i] = v[i];
-        } else {
-          double *out = cbase + obase + col0 + c;
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (col0 + c + i < T.N) out[i] = (double)v[i];
-        }
-      }
-    }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0 && !(aborted & 2)) tc::tmem_dealloc(tmem, TC_TN);
-}
-
 // ---------------------------------------------- persistent grouped GEMM
-// The same tiles and operands as tc_gemm_kernel, with one CTA per SM looping
-// over the tile list (tile t = blockIdx.x + i gridDim.x) and three roles:
+// Output tiles of 128 rows x MIX_TN columns, one CTA per SM looping over the
+// tile list (tile t = blockIdx.x + i gridDim.x), with three roles:
 // warp 0 streams the K blocks of successive tiles through a PS_STAGES-deep
 // ring of shared memory (bulk copies), warp 1 issues the MMA chain of a tile
 // into one of two TMEM accumulators, warps 2-5 read the other accumulator out
@@ -377,7 +237,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 2 * TC_TN);
+    tc::tmem_alloc(&tmem_base, 2 * MIX_TN);
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 32) {
@@ -433,8 +293,8 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      constexpr uint32_t idesc = tc::instr_desc(TM, TC_TN, BF16 ? 1u : 2u);
-      constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TC_TN / 8) * 128, sbo = 128;
+      constexpr uint32_t idesc = tc::instr_desc(TM, MIX_TN, BF16 ? 1u : 2u);
+      constexpr uint32_t lboA = (TM / 8) * 128, lboB = (MIX_TN / 8) * 128, sbo = 128;
       long long it = 0;
       int lt = 0;
       bool ok = true;
@@ -448,7 +308,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
           break;
         }
         tc::fence_after_sync();
-        const uint32_t d = tmem + (uint32_t)(a * TC_TN);
+        const uint32_t d = tmem + (uint32_t)(a * MIX_TN);
         for (int kb = 0; kb < T.KB; ++kb, ++it) {
           const int s = (int)(it % PS_STAGES);
           if (!tc::mbar_wait(&full[s], (uint32_t)((it / PS_STAGES) & 1), WAIT_BUDGET)) {
@@ -506,15 +366,15 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
       }
       tc::fence_after_sync();
       const int row = tile.mt * TM + 32 * q + lane;
-      const int col0 = tile.nt * TC_TN;
+      const int col0 = tile.nt * MIX_TN;
       double *cbase = bufs[T.sb * NBUF + T.c_buf];
       int64_t obase = 0;
       if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
 #pragma unroll
-      for (int c = 0; c < TC_TN; c += 16) {
+      for (int c = 0; c < MIX_TN; c += 16) {
         float vv[16];
         if (T.KB > 0) {
-          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TC_TN + c), vv);
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * MIX_TN + c), vv);
         } else {
 #pragma unroll
           for (int i = 0; i < 16; ++i) vv[i] = 0.f;
@@ -550,7 +410,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
   const int aborted = abort_flag;
   if (warp == 0 && !(aborted & 2)) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 2 * TC_TN);
+    tc::tmem_dealloc(tmem, 2 * MIX_TN);
   }
 }
 
@@ -938,12 +798,9 @@ cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *con
   return cudaGetLastError();
 }
 
-cudaError_t launch_wstage_tc(const WTaskP *tasks, int ntasks, int max_rows, const WTerm *terms,
+cudaError_t launch_wstage_tc(const int4 *units, int nunits, const WTaskP *tasks, const WTerm *terms,
                              double *const *bufs, const int *active, int bf16, cudaStream_t st) {
-  if (ntasks > 0 && max_rows > 0) {
-    dim3 grid(ntasks, (max_rows + WROWS - 1) / WROWS);
-    wstage_tc_kernel<<<grid, 128, 0, st>>>(tasks, terms, bufs, active, bf16);
-  }
+  if (nunits > 0) wstage_tc_kernel<<<nunits, WUNIT_ITEMS, 0, st>>>(units, tasks, terms, bufs, active, bf16);
   return cudaGetLastError();
 }
 
