@@ -220,8 +220,8 @@ cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, dou
 size_t svd_qrc_smem(int rows, int cols, int csize);
 cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *rows,
                                     const int *cols, int rows0, int cols0, double *work, int *iwork,
-                                    double zero_rel, cudaStream_t st, const cudaStream_t *side,
-                                    const cudaEvent_t *ev);
+                                    double zero_rel, bool force_global_cols, cudaStream_t st,
+                                    const cudaStream_t *side, const cudaEvent_t *ev);
 // Jacobi groups and shared memory: see kernels_svd.cu
 constexpr size_t SVD_BLOCK_SMEM_MAX = 200 * 1024;
 size_t svd_block_smem(int cols, int csize);

@@ -2204,7 +2204,8 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   }
   if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
   CK(launch_svd_qrcp_grouped((const SvdJob *)c->sjobs.p, (const int *)c->sorder.p, nj, g, grows, gcols, rows0, cols0,
-                             c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, c->st, c->side, c->sev));
+                             c->dp(c->swork), (int *)c->siw.p, c->o.lambda_zero_rel, c->svd_global, c->st, c->side,
+                             c->sev));
   if (c->side_streams() != IDMRG_OK) return c->fail(IDMRG_ECUDA, "truncate: cannot create the SVD side streams");
   // FP32 stage: rotations V to FP32 accuracy; Newton-Schulz makes V
   // orthogonal to FP64 precision (V <- 1.5 V - 0.5 V V^T V, twice); X = B V;

@@ -269,6 +269,10 @@ __device__ __forceinline__ double recip_signed(double x) {
 constexpr int QC_THREADS = 256;
 constexpr int QC_MAX_CLUSTER = 16;
 
+// GCOLS: the columns stay in global memory (the job's A) instead of the
+// CTAs' shared memory, for sectors too large for a cluster's shared memory;
+// the algorithm and the cluster's division of labour are the same.
+template <bool GCOLS>
 __global__ void __launch_bounds__(QC_THREADS)
     qrcp_cluster_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
                         int *__restrict__ iwork, double zero_rel) {
@@ -284,8 +288,8 @@ __global__ void __launch_bounds__(QC_THREADS)
   int *perm = iwork + Jb.perm_off;
   const int nloc = (ca + C - 1) / C;
   const int ld = (ra + 1) & ~1;                  // 16-byte aligned columns
-  double *cols = qc_sm;                          // [nloc][ld]
-  double *bcast = cols + (size_t)nloc * ld;      // [ld] reflector of the step
+  double *cols = qc_sm;                          // [nloc][ld] (shared-memory columns only)
+  double *bcast = cols + (GCOLS ? (size_t)0 : (size_t)nloc * ld);  // [ld] reflector of the step
   double *swp = bcast + ld;                      // [ld] incoming column of a swap
   double *vn = swp + ld, *vref = vn + nloc;      // [nloc] squared norms
   int *pl = (int *)(vref + nloc);                // [nloc] original column at each position
@@ -294,18 +298,23 @@ __global__ void __launch_bounds__(QC_THREADS)
   __shared__ double s_vp, s_stop2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   auto pos = [&](int l) { return crank + C * l; };
+  // column at local slot l: shared memory, or the job's A in global memory
+  auto colp = [&](int l) -> double * { return GCOLS ? A + (int64_t)pos(l) * ra : cols + (size_t)l * ld; };
   // load the owned columns and their squared norms
-  for (int l = 0; l < nloc; ++l) {
-    const int j = pos(l);
-    if (j >= ca) break;
-    for (int i = threadIdx.x; i < ra; i += blockDim.x) cols[(size_t)l * ld + i] = A[(int64_t)j * ra + i];
+  if (!GCOLS) {
+    for (int l = 0; l < nloc; ++l) {
+      const int j = pos(l);
+      if (j >= ca) break;
+      for (int i = threadIdx.x; i < ra; i += blockDim.x) cols[(size_t)l * ld + i] = A[(int64_t)j * ra + i];
+    }
   }
   __syncthreads();
   for (int l = warp; l < nloc; l += nw) {
     const int j = pos(l);
     if (j >= ca) continue;
     double s2 = 0.0;
-    for (int i = lane; i < ra; i += 32) s2 = fma(cols[(size_t)l * ld + i], cols[(size_t)l * ld + i], s2);
+    const double *cl = colp(l);
+    for (int i = lane; i < ra; i += 32) s2 = fma(cl[i], cl[i], s2);
     s2 = wsum(s2);
     if (lane == 0) {
       vn[l] = s2;
@@ -373,10 +382,11 @@ __global__ void __launch_bounds__(QC_THREADS)
     if (p != k) {
       if (ok == op) {
         if (crank == ok) {
+          double *ck = colp(lk), *cp = colp(lp);
           for (int i = threadIdx.x; i < ra; i += blockDim.x) {
-            const double t = cols[(size_t)lk * ld + i];
-            cols[(size_t)lk * ld + i] = cols[(size_t)lp * ld + i];
-            cols[(size_t)lp * ld + i] = t;
+            const double t = ck[i];
+            ck[i] = cp[i];
+            cp[i] = t;
           }
           if (threadIdx.x == 0) {
             double t = vn[lk]; vn[lk] = vn[lp]; vn[lp] = t;
@@ -386,11 +396,21 @@ __global__ void __launch_bounds__(QC_THREADS)
         }
         cluster.sync();  // every CTA passes the same barriers
       } else {
-        // each owner writes its column into the other's swap buffer
+        // each owner writes its column into the other's swap buffer (with
+        // global columns the owner of k swaps both columns in place)
         if (crank == ok || crank == op) {
           const int mine = crank == ok ? lk : lp, other = crank == ok ? op : ok;
-          double *dst = cluster.map_shared_rank(swp, other);
-          for (int i = threadIdx.x; i < ra; i += blockDim.x) dst[i] = cols[(size_t)mine * ld + i];
+          if (!GCOLS) {
+            double *dst = cluster.map_shared_rank(swp, other);
+            for (int i = threadIdx.x; i < ra; i += blockDim.x) dst[i] = cols[(size_t)mine * ld + i];
+          } else if (crank == ok) {
+            double *ck = A + (int64_t)k * ra, *cp = A + (int64_t)p * ra;
+            for (int i = threadIdx.x; i < ra; i += blockDim.x) {
+              const double t = ck[i];
+              ck[i] = cp[i];
+              cp[i] = t;
+            }
+          }
           if (threadIdx.x == 0) {
             *cluster.map_shared_rank(&s_swap_vn, other) = vn[mine];
             *cluster.map_shared_rank(&s_swap_vref, other) = vref[mine];
@@ -400,7 +420,8 @@ __global__ void __launch_bounds__(QC_THREADS)
         cluster.sync();
         if (crank == ok || crank == op) {
           const int mine = crank == ok ? lk : lp;
-          for (int i = threadIdx.x; i < ra; i += blockDim.x) cols[(size_t)mine * ld + i] = swp[i];
+          if (!GCOLS)
+            for (int i = threadIdx.x; i < ra; i += blockDim.x) cols[(size_t)mine * ld + i] = swp[i];
           if (threadIdx.x == 0) {
             vn[mine] = s_swap_vn;
             vref[mine] = s_swap_vref;
@@ -412,7 +433,7 @@ __global__ void __launch_bounds__(QC_THREADS)
     }
     // (c) the owner of position k forms the reflector (rows k..ra-1)
     if (crank == ok) {
-      double *ak = cols + (size_t)lk * ld;
+      double *ak = colp(lk);
       double s2 = 0.0;
       for (int i = k + 1 + threadIdx.x; i < ra; i += blockDim.x) s2 = fma(ak[i], ak[i], s2);
       s2 = wsum(s2);
@@ -459,7 +480,7 @@ __global__ void __launch_bounds__(QC_THREADS)
       for (int l = warp; l < nloc; l += nw) {
         const int j = pos(l);
         if (j <= k || j >= ca) continue;
-        double *aj = cols + (size_t)l * ld;
+        double *aj = colp(l);
         double w = 0.0;
         for (int i = k + 1 + lane; i < ra; i += 32) w = fma(bcast[i], aj[i], w);
         w = (wsum(w) + aj[k]) * tk;
@@ -473,7 +494,7 @@ __global__ void __launch_bounds__(QC_THREADS)
     for (int l = warp; l < nloc; l += nw) {
       const int j = pos(l);
       if (j <= k || j >= ca) continue;
-      const double *aj = cols + (size_t)l * ld;
+      const double *aj = colp(l);
       double nv = vn[l] - aj[k] * aj[k];
       if (!(nv > 1e-8 * vref[l])) {
         double s2 = 0.0;
@@ -489,10 +510,11 @@ __global__ void __launch_bounds__(QC_THREADS)
   for (int l = 0; l < nloc; ++l) {
     const int j = pos(l);
     if (j >= ca) break;
-    for (int i = threadIdx.x; i < ra; i += blockDim.x) A[(int64_t)j * ra + i] = cols[(size_t)l * ld + i];
+    const double *cl = colp(l);
+    if (!GCOLS)
+      for (int i = threadIdx.x; i < ra; i += blockDim.x) A[(int64_t)j * ra + i] = cl[i];
     if (threadIdx.x == 0) perm[j] = pl[l];
-    for (int b = threadIdx.x; b < ca; b += blockDim.x)
-      B[(int64_t)b * ca + j] = (b <= j && b < rank) ? cols[(size_t)l * ld + b] : 0.0;
+    for (int b = threadIdx.x; b < ca; b += blockDim.x) B[(int64_t)b * ca + j] = (b <= j && b < rank) ? cl[b] : 0.0;
   }
   if (crank == 0 && threadIdx.x == 0) perm[ca] = rank;
   cluster.sync();  // no CTA leaves while another may still read its shared memory
@@ -720,6 +742,52 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
 // doubles, free until the Newton-Schulz step), one pair per warp, rounds
 // separated by the cluster barrier.  Ends by writing the rotations to V
 // (FP64, leading dimension cols_a) over the identity already there.
+// A pair's columns are read and written in batches of J32_BATCH elements per
+// lane whose loads are all issued before they are used: with the columns in
+// L2 or HBM, a plain strided loop waits on the load latency once per 32
+// elements of each column.
+constexpr int J32_BATCH = 8;
+constexpr int J64_BATCH = 8;
+
+__device__ __forceinline__ void dots32(const float *xp, const float *xq, int len, int lane, float &a, float &b,
+                                       float &g) {
+  for (int i0 = 0; i0 < len; i0 += 32 * J32_BATCH) {
+    float u[J32_BATCH], v[J32_BATCH];
+#pragma unroll
+    for (int r = 0; r < J32_BATCH; ++r) {
+      const int i = i0 + lane + 32 * r;
+      u[r] = i < len ? xp[i] : 0.f;
+      v[r] = i < len ? xq[i] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < J32_BATCH; ++r) {
+      a = fmaf(u[r], u[r], a);
+      b = fmaf(v[r], v[r], b);
+      g = fmaf(u[r], v[r], g);
+    }
+  }
+}
+
+__device__ __forceinline__ void rot32(float *xp, float *xq, int len, int lane, float c, float sn) {
+  for (int i0 = 0; i0 < len; i0 += 32 * J32_BATCH) {
+    float u[J32_BATCH], v[J32_BATCH];
+#pragma unroll
+    for (int r = 0; r < J32_BATCH; ++r) {
+      const int i = i0 + lane + 32 * r;
+      u[r] = i < len ? xp[i] : 0.f;
+      v[r] = i < len ? xq[i] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < J32_BATCH; ++r) {
+      const int i = i0 + lane + 32 * r;
+      if (i < len) {
+        xp[i] = c * u[r] - sn * v[r];
+        xq[i] = fmaf(sn, u[r], c * v[r]);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(JAC_THREADS, 2)
     jacobi32_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
                     const int *__restrict__ iwork) {
@@ -769,12 +837,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
         if (p >= n || q >= n) continue;
         float *xp = B32 + (int64_t)p * nr, *xq = B32 + (int64_t)q * nr;
         float a = 0.f, b = 0.f, g = 0.f;
-        for (int i = lane; i < nr; i += 32) {
-          const float u = xp[i], v = xq[i];
-          a = fmaf(u, u, a);
-          b = fmaf(v, v, b);
-          g = fmaf(u, v, g);
-        }
+        dots32(xp, xq, nr, lane, a, b, g);
         a = wsumf(a);
         b = wsumf(b);
         g = wsumf(g);
@@ -785,17 +848,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
         const float t = z == 0.f ? 1.0f : copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
         if (!(fabsf(t) >= FLT_MIN) || !isfinite(t)) continue;
         const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
-        for (int i = lane; i < nr; i += 32) {
-          const float u = xp[i], v = xq[i];
-          xp[i] = c * u - sn * v;
-          xq[i] = fmaf(sn, u, c * v);
-        }
-        float *jp = V32 + (int64_t)p * n, *jq = V32 + (int64_t)q * n;
-        for (int i = lane; i < n; i += 32) {
-          const float u = jp[i], v = jq[i];
-          jp[i] = c * u - sn * v;
-          jq[i] = fmaf(sn, u, c * v);
-        }
+        rot32(xp, xq, nr, lane, c, sn);
+        rot32(V32 + (int64_t)p * n, V32 + (int64_t)q * n, n, lane, c, sn);
         any = true;
         rmax = fmaxf(rmax, ratio);
       }
@@ -1309,7 +1363,19 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
         if (p >= n || q >= n) continue;
         double *xp = B + (int64_t)p * nr, *xq = B + (int64_t)q * nr;
         double ga = 0.0;
-        for (int i = lane; i < nr; i += 32) ga = fma(xp[i], xq[i], ga);
+        // loads in batches of J64_BATCH per lane, all issued before their
+        // FMAs; each lane still adds its elements in index order
+        for (int i0 = 0; i0 < nr; i0 += 32 * J64_BATCH) {
+          double u[J64_BATCH], v[J64_BATCH];
+#pragma unroll
+          for (int r = 0; r < J64_BATCH; ++r) {
+            const int i = i0 + lane + 32 * r;
+            u[r] = i < nr ? xp[i] : 0.0;
+            v[r] = i < nr ? xq[i] : 0.0;
+          }
+#pragma unroll
+          for (int r = 0; r < J64_BATCH; ++r) ga = fma(u[r], v[r], ga);
+        }
         ga = wsum(ga);
         double cp = 0.0, cq = 0.0;
         int rot = 0;
@@ -1331,21 +1397,45 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
         cp = __shfl_sync(0xffffffffu, cp, 0);
         cq = __shfl_sync(0xffffffffu, cq, 0);
         double np2 = 0.0, nq2 = 0.0;
-        for (int i = lane; i < nr; i += 32) {
-          const double u = xp[i], v = xq[i];
-          const double u2 = fma(cp, v, u), v2 = fma(cq, u, v);
-          xp[i] = u2;
-          xq[i] = v2;
-          if (rot == 2) {
-            np2 = fma(u2, u2, np2);
-            nq2 = fma(v2, v2, nq2);
+        for (int i0 = 0; i0 < nr; i0 += 32 * J64_BATCH) {
+          double u[J64_BATCH], v[J64_BATCH];
+#pragma unroll
+          for (int r = 0; r < J64_BATCH; ++r) {
+            const int i = i0 + lane + 32 * r;
+            u[r] = i < nr ? xp[i] : 0.0;
+            v[r] = i < nr ? xq[i] : 0.0;
+          }
+#pragma unroll
+          for (int r = 0; r < J64_BATCH; ++r) {
+            const int i = i0 + lane + 32 * r;
+            if (i < nr) {
+              const double u2 = fma(cp, v[r], u[r]), v2 = fma(cq, u[r], v[r]);
+              xp[i] = u2;
+              xq[i] = v2;
+              if (rot == 2) {
+                np2 = fma(u2, u2, np2);
+                nq2 = fma(v2, v2, nq2);
+              }
+            }
           }
         }
         double *jp = Jm + (int64_t)p * n, *jq = Jm + (int64_t)q * n;
-        for (int i = lane; i < n; i += 32) {
-          const double u = jp[i], v = jq[i];
-          jp[i] = fma(cp, v, u);
-          jq[i] = fma(cq, u, v);
+        for (int i0 = 0; i0 < n; i0 += 32 * J64_BATCH) {
+          double u[J64_BATCH], v[J64_BATCH];
+#pragma unroll
+          for (int r = 0; r < J64_BATCH; ++r) {
+            const int i = i0 + lane + 32 * r;
+            u[r] = i < n ? jp[i] : 0.0;
+            v[r] = i < n ? jq[i] : 0.0;
+          }
+#pragma unroll
+          for (int r = 0; r < J64_BATCH; ++r) {
+            const int i = i0 + lane + 32 * r;
+            if (i < n) {
+              jp[i] = fma(cp, v[r], u[r]);
+              jq[i] = fma(cq, u[r], v[r]);
+            }
+          }
         }
         if (rot == 2) {  // cancellation: norms from the rotated data
           np2 = wsum(np2);
@@ -2246,19 +2336,30 @@ size_t svd_qrc_smem(int rows, int cols, int csize) {
   return (size_t)((nloc * ld + 2 * ld + 3 * nloc + 2) * sizeof(double));
 }
 
+// the same with the columns in global memory (reflector, swap buffer and the
+// per-column norms in shared memory)
+static size_t svd_qrc_smem_global(int rows, int cols, int csize) {
+  const int64_t nloc = (cols + csize - 1) / csize, ld = (rows + 1) & ~1;
+  return (size_t)((2 * ld + 3 * nloc + 2) * sizeof(double));
+}
+
 // pivoted QR of the jobs order[0..njobs) in groups (as the Jacobi): groups
-// 0..4 on clusters of 16, 16, 8, 4, 1 CTAs, any group whose columns do not
-// fit in the shared memory of its cluster on the single-CTA kernel; rows[k],
-// cols[k] are the largest rows and columns of block group k+1
+// 0..4 on clusters of 16, 16, 8, 4, 1 CTAs; a group whose columns do not fit
+// in the shared memory of its cluster keeps them in global memory
+// (force_global_cols: every clustered group does), one that does not fit
+// either way runs on the single-CTA kernel; rows[k], cols[k] are the
+// largest rows and columns of block group k+1
 cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *rows,
                                     const int *cols, int rows0, int cols0, double *work, int *iwork,
-                                    double zero_rel, cudaStream_t st, const cudaStream_t *side,
-                                    const cudaEvent_t *ev) {
+                                    double zero_rel, bool force_global_cols, cudaStream_t st,
+                                    const cudaStream_t *side, const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
-  cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaError_t e = cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SVD_BLOCK_SMEM_MAX);
-  if (e != cudaSuccess) return e;
+  for (auto kern : {qrcp_cluster_kernel<false>, qrcp_cluster_kernel<true>}) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SVD_BLOCK_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaSuccess;
   const int lo[5] = {0, g[0], g[1], g[2], g[3]}, hi[5] = {g[0], g[1], g[2], g[3], njobs};
   const int csz[5] = {16, 16, 8, 4, 1};
   // groups 2..4 on the side streams, concurrent with groups 0 and 1
@@ -2271,7 +2372,10 @@ cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int nj
       e = cudaStreamWaitEvent(sk, ev[0], 0);
       if (e != cudaSuccess) return e;
     }
-    const size_t smem = k == 0 ? svd_qrc_smem(rows0, cols0, csz[0]) : svd_qrc_smem(rows[k - 1], cols[k - 1], csz[k]);
+    const int kr = k == 0 ? rows0 : rows[k - 1], kc = k == 0 ? cols0 : cols[k - 1];
+    size_t smem = svd_qrc_smem(kr, kc, csz[k]);
+    const bool global_cols = (force_global_cols || smem > SVD_BLOCK_SMEM_MAX) && csz[k] > 1;
+    if (global_cols) smem = svd_qrc_smem_global(kr, kc, csz[k]);
     if (smem > SVD_BLOCK_SMEM_MAX) {
       e = launch_svd_qrcp(jobs, order + lo[k], hi[k] - lo[k], work, iwork, zero_rel, sk);
     } else {
@@ -2287,7 +2391,9 @@ cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int nj
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, jobs, order + lo[k], work, iwork, zero_rel);
+      e = global_cols ? cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<true>, jobs, order + lo[k], work, iwork, zero_rel)
+                      : cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<false>, jobs, order + lo[k], work, iwork,
+                                           zero_rel);
     }
     if (e != cudaSuccess) return e;
     if (k >= 2) {
