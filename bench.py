@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -44,6 +46,13 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "kagome_yc8_l12_m2048"
 SATURATE_MAX = 40        # iterations allowed to reach D >= 0.9 m
+# Timed window: after the prediction of Step 3' has settled.  Sec. 4 finds
+# the Eq. fid1 fidelity error comparable with the truncation error once the
+# run is past its transient, and times the iDMRG as the average over
+# n <= 1200 iterations (Fig. 3), i.e. in that regime.
+SETTLE_RATIO = 10.0      # max_i fidelity error <= SETTLE_RATIO max_i eps (+ 1e-9)
+SETTLE_RUN = 3           # ... on this many consecutive steps
+SETTLE_MAX_N = 90        # or until this iteration
 PAPER_LANCZOS_ITERS = 40  # Sec. 4: about 40 Lanczos iterations per solve with the prediction
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 HBM_FALLBACK, BF16_FALLBACK, BF16_SUST_FALLBACK = 6800.0, 1900.0, 1700.0
@@ -137,32 +146,43 @@ def traffic_for(kclass: str, prec: str):
 def class_roofline(name: str, d: dict, prec: str, pk: dict):
     """Roofline of one kernel class from its event-timed launches.
 
-    FP64 arithmetic (SVD, FP64 H_eff, environments, prediction) is bound by
-    the FP64 units: 152 SMs x 2 FMA/clk x 2.07 GHz; the reduced-precision
-    H_eff by the tensor pipe of its split type (measured sustained bf16, times
-    the nominal tf32/bf16 ratio for TF32); the Lanczos vector kernels by HBM
-    bandwidth."""
+    Contractions on the tensor cores count each algorithmic product once
+    against the measured sustained bf16 peak (times the nominal tf32/bf16
+    ratio for TF32): the split H_eff GEMMs (3 MMAs per product) and, in the
+    mixed and FP64_TC forms, the FP64-accurate digit-slice GEMMs of the
+    environments, the prediction and the restart matvecs (36 BF16 MMAs per
+    FP64 product).  `executed_frac` is the same fraction with the MMAs the
+    pipe executes.  The W stage and psi split of the mixed H_eff and the
+    Lanczos vector kernels are HBM streams (algorithmic bytes booked by the
+    library); the FP64 SVD and the FP64 forms run on the FP64 units: 152 SMs
+    x 2 FMA/clk x 2.07 GHz."""
     sec = d["ms"] * 1e-3
     out = {"kernel": name, "launch_ms": d["ms"] / max(d["launches"], 1), "traffic": traffic_for(name, prec)}
-    if name in ("heff_gemm", "heff_wstage") and prec != "fp64":
-        bf = prec in ("bf16x3", "fp64tc")
+    mixed = prec != "fp64"
+    digit = name in ("env", "predict", "heff_f64") and mixed or name == "heff_gemm" and prec == "fp64tc"
+    if name == "heff_gemm" and prec in ("bf16x3", "tf32x3") or digit:
+        bf = prec in ("bf16x3", "fp64tc") or digit
         peak = pk["bf16_sustained"] * (1.0 if bf else 1.1 / 2.25)
         achieved = d["flops"] / sec / 1e12 if sec > 0 else 0.0
         src = "sustained bf16" if bf else "sustained bf16 x nominal tf32/bf16 (1.1/2.25)"
-        what = ("FP64 products counted once (36 BF16 digit products each)" if prec == "fp64tc"
-                else "split products counted once")
+        prod = 36 if digit else 3
+        what = ("FP64-accurate products counted once (36 BF16 digit MMAs each)" if digit
+                else "split products counted once (3 MMAs each)")
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": f"{pk['src']} {src}; {what}"})
-    elif name in ("heff_gemm", "heff_wstage", "heff_f64", "svd", "env", "predict"):
-        achieved = d["flops"] / sec / 1e9 if sec > 0 else 0.0
-        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
-                    "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"})
-    else:
+                    "peak_source": f"{pk['src']} {src}; {what}", "products_per_flop": prod})
+    elif name == "heff_wstage" and prec in ("bf16x3", "tf32x3") or name in ("lanczos_vec", "lanczos_tri"):
         achieved = d["bytes"] / sec / 1e9 if sec > 0 else 0.0
         out.update({"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
                     "peak_source": f"{pk['src']} copy bandwidth"})
+    else:
+        achieved = d["flops"] / sec / 1e9 if sec > 0 else 0.0
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
+                    "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"})
     out["frac"] = out["achieved"] / out["peak"]
-    keys = ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "launch_ms", "peak_source")
+    keys = ["bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "launch_ms", "peak_source"]
+    if "products_per_flop" in out:
+        out["executed_frac"] = out["frac"] * out["products_per_flop"]
+        keys += ["products_per_flop", "executed_frac"]
     return {k: out[k] for k in keys}
 
 
@@ -203,6 +223,26 @@ def saturate(ctx, m: int):
         r = ctx.unit_cell_step()
         steps += 1
         if min(int(k) for k in r["kept"]) >= 0.9 * m:
+            break
+    return steps
+
+
+def settled(r) -> bool:
+    """The prediction of this step has settled (Sec. 4): every superblock's
+    Eq. fid1 fidelity error within SETTLE_RATIO of the largest truncation error."""
+    fid = np.asarray(r["fidelity"], dtype=np.float64)
+    eps = np.asarray(r["eps"], dtype=np.float64)
+    return bool(np.all(np.isfinite(fid))) and float(fid.max()) <= SETTLE_RATIO * float(eps.max()) + 1e-9
+
+
+def settle(step, iteration) -> int:
+    """Unit-cell steps until `settled` holds on SETTLE_RUN consecutive steps
+    or the run reaches iteration SETTLE_MAX_N; returns the steps taken."""
+    run = steps = 0
+    while iteration() < SETTLE_MAX_N:
+        run = run + 1 if settled(step()) else 0
+        steps += 1
+        if run >= SETTLE_RUN:
             break
     return steps
 
@@ -529,16 +569,17 @@ def max_de_per_site(ra, rb):
 
 
 def timed_run(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, prof_steps: int, dev, flush, dist,
-              local: int, save_path=None):
-    """Saturate (D = m), warm up, save the state if asked, then two timed
-    regions, each step bracketed by CUDA events on the context's stream with
-    the L2 flushed before it (outside the events): `steps` steps without
-    per-class timers (the step time, e2e wall clock and clocks), then
-    `prof_steps` steps with the per-class event timers on (kernel classes and
-    rooflines)."""
+              local: int, save_path=None, window: str = "settled"):
+    """Saturate (D = m), let the prediction settle (window "settled"), warm
+    up, save the state if asked, then two timed regions, each step bracketed
+    by CUDA events on the context's stream with the L2 flushed before it
+    (outside the events): `steps` steps without per-class timers (the step
+    time, e2e wall clock and clocks), then `prof_steps` steps with the
+    per-class event timers on (kernel classes and rooflines)."""
     import torch
     ctx = pkg.Context(mpo.W, mpo.phys_charge, mpo.bond_charge, m=m, prec=prec, lanczos_maxit=maxit)
     nsat = saturate(ctx, m)
+    nset = settle(ctx.unit_cell_step, lambda: ctx.iteration) if window == "settled" else 0
     for _ in range(max(warmup, 3)):
         ctx.unit_cell_step()
     n0 = ctx.iteration
@@ -585,11 +626,12 @@ def timed_run(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, 
     res = region(steps, False, Clocks(local))
     prof = region(prof_steps, True, None)
     res.update(prof=prof["prof"], prof_step_ms=prof["step_ms"], prof_steps=prof_steps, ctx=ctx, n0=n0,
-               saturate_steps=nsat)
+               saturate_steps=nsat, settle_steps=nset)
     return res
 
 
-def timed_run_shard(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, dist, local: int):
+def timed_run_shard(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, dist, local: int,
+                    window: str = "settled"):
     """One problem over the ranks (Sec. 3, Step 2'): contiguous pair ranges,
     one ring shift of the boundary pair per step (shard.ShardedRun, NCCL
     point-to-point), the step reports gathered.  Every rank runs the same
@@ -606,6 +648,8 @@ def timed_run_shard(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup:
         nsat += 1
         if min(int(k) for k in r["kept"]) >= 0.9 * m:
             break
+    # the gathered reports are the same on every rank: the same decision
+    nset = settle(run.step, lambda: ctx.iteration) if window == "settled" else 0
     for _ in range(max(warmup, 3)):
         run.step()
     launches0 = ctx.launch_count()
@@ -620,7 +664,8 @@ def timed_run_shard(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup:
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     return {"wall_s": wall, "reports": reports, "clocks": clk, "launches": ctx.launch_count() - launches0,
-            "saturate_steps": nsat, "ranges": run.ranges, "bytes_per_step": run.bytes_sent, "ctx": ctx}
+            "saturate_steps": nsat, "settle_steps": nset, "ranges": run.ranges, "bytes_per_step": run.bytes_sent,
+            "ctx": ctx}
 
 
 def fp64_leg(pkg, mpo, m: int, maxit: int, path: str, steps: int):
@@ -650,7 +695,8 @@ def run_shard(args, pkg, mpo, world, rank, local, dist, ell, wl):
     from workloads import build_mpo, random_chain_bonds
     if args.workload == CHAIN:  # every rank steps the same realisation
         mpo = build_mpo(random_chain_bonds(16, 0.5, 1.5, rank_seed(0)), 16)
-    res = timed_run_shard(pkg, mpo, args.m, args.prec, wl["maxit"], args.steps, args.warmup, dist, local)
+    res = timed_run_shard(pkg, mpo, args.m, args.prec, wl["maxit"], args.steps, args.warmup, dist, local,
+                          args.window)
     import torch
     t_wall = reduce_max([res["wall_s"]], dist, torch.device("cuda", local))[0]
     launches = reduce_max([res["launches"]], dist, torch.device("cuda", local))[0]
@@ -667,9 +713,10 @@ def run_shard(args, pkg, mpo, world, rank, local, dist, ell, wl):
                        "parallelism": f"one problem over {world} GPUs: pair ranges {res['ranges']}, one ring "
                                       "shift of the boundary pair per step (NCCL send/recv)",
                        "exchange_bytes_per_step_rank0": res["bytes_per_step"] // max(
-                           args.steps + args.warmup + res["saturate_steps"], 1),
-                       "regime": f"D >= 0.9 m after {res['saturate_steps']} steps, timed n = "
-                                 f"{res['reports'][0]['n']}..{last['n']}",
+                           args.steps + max(args.warmup, 3) + res["saturate_steps"] + res["settle_steps"], 1),
+                       "regime": f"D >= 0.9 m after {res['saturate_steps']} steps, "
+                                 f"{res['settle_steps']} more until the prediction settled ({args.window} window), "
+                                 f"timed n = {res['reports'][0]['n']}..{last['n']}",
                        "timing": "wall clock per rank, barrier and device synchronisation on both sides, max"},
             "roofline": None, "gpu_launches": int(launches),
             "e2e": {"value": v, "unit": "unit-cell steps/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
@@ -698,6 +745,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "shard", "replica"],
                     help="N > 1: one problem sharded over the GPUs (auto when N <= l/2) or N independent replicas")
+    ap.add_argument("--window", default="settled", choices=["settled", "transient"],
+                    help="time after the prediction has settled (Sec. 4) or right after saturation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--observables", choices=["auto", "on", "off"], default="auto",
@@ -734,7 +783,7 @@ def main():
     tmpdir = tempfile.mkdtemp(prefix="idmrg_bench_")
     state = os.path.join(tmpdir, f"state_rank{rank}.ck")
     run = timed_run(pkg, mpo, args.m, args.prec, wl["maxit"], args.steps, args.warmup, max(args.prof_steps, 1),
-                    dev, flush, dist, local, save_path=state)
+                    dev, flush, dist, local, save_path=state, window=args.window)
     t_dev, t_wall = run["step_ms"] * 1e-3, run["wall_s"]
     t_dev, t_wall = reduce_max([t_dev, t_wall], dist, dev)
     pk = peaks()
@@ -769,9 +818,14 @@ def main():
         "dtype": {"fp64": "f64", "fp64tc": "bf16-digits(f64)+f64"}.get(args.prec, f"{args.prec}+f64"),
         "data": "synthetic",
         "config": {"workload": args.workload, "ell": ell, "m": args.m, "solves_per_step": ell // 2, "seed": seed,
-                   "regime": f"saturated: D >= 0.9 m after {run['saturate_steps']} steps, "
-                             f"{max(args.warmup, 3)} warm-up steps, timed n = {first['n']}..{last['n']}, "
-                             f"kept {int(min(last['kept']))}..{int(max(last['kept']))}",
+                   "regime": f"saturated: D >= 0.9 m after {run['saturate_steps']} steps; "
+                             + (f"prediction settled (Eq. fid1 fidelity error <= {SETTLE_RATIO:g} x truncation "
+                                f"error on {SETTLE_RUN} consecutive steps, or n = {SETTLE_MAX_N}) after "
+                                f"{run['settle_steps']} more; " if args.window == "settled" else
+                                "transient window (no settling); ")
+                             + f"{max(args.warmup, 3)} warm-up steps, timed n = {first['n']}..{last['n']}, "
+                             f"kept {int(min(last['kept']))}..{int(max(last['kept']))}, last max fidelity error "
+                             f"{float(np.max(last['fidelity'])):.2e}, max eps {float(np.max(last['eps'])):.2e}",
                    "precision": args.prec + ("" if args.prec == "fp64" else " H_eff psi; FP64 Lanczos and SVD"),
                    "fp64_restart_matvecs": "BF16 digit slices on the tensor cores (FP64-accurate)"
                    if args.prec in ("tf32x3", "bf16x3") else None,

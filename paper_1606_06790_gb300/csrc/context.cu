@@ -65,6 +65,9 @@ struct SBPlan {
   std::vector<double> h2;   // centre bond operator [d*d][d*d]
   double heff_flops = 0, heff_bytes = 0;
   double gemm_flops = 0, w_flops = 0;
+  // mixed forms: algorithmic bytes of the psi split (FP64 in, hi/lo out) and
+  // of the W stage (FP32 T1 in once, hi/lo T3 out), per hi/lo word size
+  double wpack_elems = 0, wt1_elems = 0, wt3_elems = 0;
   int njob0 = 0, njob = 0;  // SVD jobs
 };
 
@@ -757,6 +760,9 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
     S.w_flops = c->wl.flops - fw0;
     S.heff_flops = S.gemm_flops + S.w_flops;
     S.heff_bytes = 8.0 * (L.lay.size + R.lay.size + 2.0 * psi.N);
+    S.wpack_elems = (double)psi.N;
+    S.wt1_elems = (double)S.t1size;
+    S.wt3_elems = (double)S.t3size;
     // ---- centre-bond energy terms
     for (int i = 0; i < SL; ++i)
       for (int x = 0; x < dd; ++x)
@@ -1428,13 +1434,21 @@ idmrg_status heff_launch_oz(idmrg_ctx *c, const int *active_dev, const int *act)
 idmrg_status heff_launch_fp64(idmrg_ctx *c, const int *active_dev, const int *act);
 idmrg_status heff_launch_mixed(idmrg_ctx *c, const int *active_dev, const int *act) {
   double *const *bufs = (double *const *)c->dbufs.p;
-  double gf = 0, by = 0, wf = 0;
+  double gf = 0, by = 0, wf = 0, pb = 0, wb = 0;
+  const double hl = c->bf16 ? 4.0 : 8.0;  // bytes of one hi/lo pair
   for (int q = 0; q < c->P; ++q)
-    if (!act || act[q]) { gf += c->plan[q].gemm_flops; wf += c->plan[q].w_flops; by += c->plan[q].heff_bytes; }
+    if (!act || act[q]) {
+      const SBPlan &S = c->plan[q];
+      gf += S.gemm_flops;
+      wf += S.w_flops;
+      by += S.heff_bytes;
+      pb += (8.0 + hl) * S.wpack_elems;
+      wb += 4.0 * S.wt1_elems + hl * S.wt3_elems;
+    }
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_pack((const PackSeg *)c->dpkp.p, (int)c->pk_psi.size(), c->pk_psi_rows, bufs, active_dev, c->bf16,
                  c->st));
-  c->kend(IDMRG_K_HEFF_WSTAGE);
+  c->kend(IDMRG_K_HEFF_WSTAGE, 0.0, pb);
   c->kbegin(IDMRG_K_HEFF_GEMM);
   CK(launch_tc_gemm((const TcTile *)c->dtc1t.p, (int)c->tc1t.size(), (const TcTask *)c->dtc1k.p, bufs, active_dev,
                     (int *)c->derr.p, c->bf16, c->st));
@@ -1442,7 +1456,7 @@ idmrg_status heff_launch_mixed(idmrg_ctx *c, const int *active_dev, const int *a
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_wstage_tc((const int4 *)c->dwunits.p, (int)c->wunits.size(), (const WTaskP *)c->dwtp.p,
                       (const WTerm *)c->dwtpm.p, bufs, active_dev, c->bf16, c->st));
-  c->kend(IDMRG_K_HEFF_WSTAGE, wf, 0.0);
+  c->kend(IDMRG_K_HEFF_WSTAGE, wf, wb);
   c->kbegin(IDMRG_K_HEFF_GEMM);
   CK(launch_tc_gemm((const TcTile *)c->dtc3t.p, (int)c->tc3t.size(), (const TcTask *)c->dtc3k.p, bufs, active_dev,
                     (int *)c->derr.p, c->bf16, c->st));
