@@ -796,6 +796,8 @@ def main():
                for k, v in prof.items()}
     ctx = run["ctx"]
     flops, _ = ctx.heff_cost(-1)
+    tiles = ({f"stage{k}": ctx.gemm_tuning(k) for k in (1, 3)} if args.prec in ("bf16x3", "tf32x3") else None)
+    svd_stats = ctx.svd_stats()
     last = run["reports"][-1]
     first = run["reports"][0]
     want_obs = args.observables == "on" or (args.observables == "auto" and args.workload == CHAIN)
@@ -833,6 +835,8 @@ def main():
                    "l2": "flushed before every timed step (256 MiB write, outside the events); the working set "
                          "(environments, Krylov vectors) is far larger than L2"},
         "roofline": heff,
+        "gemm_tiles": tiles,
+        "svd_stats": svd_stats,
         "roofline_dominant": class_roofline(dom, prof[dom], args.prec, pk),
         "roofline_classes": {k: class_roofline(k, v, args.prec, pk) for k, v in prof.items() if v["ms"] > 0},
         "gpu_launches": run["launches"],

@@ -385,8 +385,9 @@ idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t
  * largest short side, largest numerical rank, and the Jacobi sweeps taken
  * (maximum and mean over the sectors). */
 /* Sector SVDs of the following truncations on the kernels for large sector
- * matrices only (global_only = 1: pivoted QR in one CTA, FP32 and FP64
- * cyclic Jacobi in global memory), or on the size-dependent choice (0, the
+ * matrices only (global_only = 1: pivoted QR on thread-block clusters with
+ * the columns in global memory, FP32 and FP64 cyclic Jacobi in global
+ * memory), or on the size-dependent choice (0, the
  * default: sectors with at most 320 columns use the shared-memory block
  * kernels).  The results agree to rounding; this exists to test the
  * large-sector path on small problems. */
@@ -394,6 +395,24 @@ idmrg_status idmrg_set_svd_path(idmrg_ctx *ctx, int global_only);
 
 idmrg_status idmrg_svd_stats(const idmrg_ctx *ctx, int *jobs, int *max_cols, int *max_rank, int *max_sweeps,
                              double *mean_sweeps);
+
+/* The N tile of the split-operand tensor-core GEMMs of H_eff psi (Sec. 3,
+ * Step 3; mixed precisions only) that the context's tuner chose for stage 1
+ * (stage = 1: L psi) or stage 3 (stage = 3: T3 R^T).  The tuner times 64-,
+ * 128- and 256-column tiles on the plan's own task list whenever the stage's
+ * work has moved by more than 10 % since it last ran, and keeps the fastest.
+ * tn (may be NULL): 64, 128 or 256, 0 before the first mixed plan; ms (may
+ * be NULL, 3 entries): each candidate's timed run at the last tuning, in
+ * milliseconds; tunings (may be NULL): tuning passes of this context (both
+ * stages counted).  EINVAL for another stage number. */
+idmrg_status idmrg_gemm_tuning(const idmrg_ctx *ctx, int stage, int *tn, float *ms, int *tunings);
+
+/* Fixes the N tile of stage 1 (tn1) and stage 3 (tn3) of the split-operand
+ * GEMMs instead of tuning it: 64, 128 or 256, or 0 to tune (the default).
+ * Takes effect from the next iteration's plan; the results agree to
+ * rounding whatever the tile (the K order of every product is the same).
+ * EINVAL for any other value. */
+idmrg_status idmrg_set_gemm_tile(idmrg_ctx *ctx, int tn1, int tn3);
 
 /* Bytes this context has copied host->device and device->host so far. */
 idmrg_status idmrg_transfer_bytes(const idmrg_ctx *ctx, uint64_t *h2d, uint64_t *d2h);

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
-    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_save", "idmrg_load",
+    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_save", "idmrg_load",
     "idmrg_correlation", "idmrg_transfer_spectrum", "idmrg_delta_pm", "idmrg_extrapolate",
     "idmrg_fit_correlation_length", "idmrg_set_pair_range", "idmrg_export_pair", "idmrg_import_pair",
 ]
@@ -124,6 +124,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_load": (i, [vp, C.c_char_p]),
         "idmrg_svd_stats": (i, [vp, P(i), P(i), P(i), P(i), P(d)]),
         "idmrg_set_svd_path": (i, [vp, i]),
+        "idmrg_gemm_tuning": (i, [vp, i, P(i), P(C.c_float), P(i)]),
+        "idmrg_set_gemm_tile": (i, [vp, i, i]),
         "idmrg_correlation": (i, [vp, i, P(d), P(d), P(d), i, P(C.c_int64), P(C.c_int64), P(d)]),
         "idmrg_transfer_spectrum": (i, [vp, d, i, P(d), P(d), P(d), P(i)]),
         "idmrg_delta_pm": (i, [P(d), i, P(d), P(d), P(d)]),
@@ -468,6 +470,17 @@ class Context:
         self._check(self.lib.idmrg_svd_stats(self.h, C.byref(j), C.byref(mc), C.byref(mr), C.byref(ms), C.byref(me)),
                     "svd_stats")
         return dict(jobs=j.value, max_cols=mc.value, max_rank=mr.value, max_sweeps=ms.value, mean_sweeps=me.value)
+
+    def set_gemm_tile(self, tn1: int, tn3: int) -> None:
+        """Fix the N tiles of H_eff stages 1 and 3 (0 = tuned) from the next plan on."""
+        self._check(self.lib.idmrg_set_gemm_tile(self.h, tn1, tn3), "set_gemm_tile")
+
+    def gemm_tuning(self, stage: int) -> Dict[str, object]:
+        """The tuner's N tile for H_eff stage 1 or 3 and its candidates' times."""
+        tn, nt = C.c_int(), C.c_int()
+        ms = (C.c_float * 3)()
+        self._check(self.lib.idmrg_gemm_tuning(self.h, stage, C.byref(tn), ms, C.byref(nt)), "gemm_tuning")
+        return dict(tn=tn.value, ms={64: ms[0], 128: ms[1], 256: ms[2]}, tunings=nt.value)
 
     def transfer_bytes(self):
         a, b = C.c_uint64(), C.c_uint64()

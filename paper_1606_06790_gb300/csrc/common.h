@@ -298,7 +298,9 @@ struct TcTile {
   int task, mt, nt, pad;
 };
 constexpr int TC_TN = 64;      // N tile of the digit-slice GEMM (TMEM columns per level)
-constexpr int MIX_TN = 64;     // N tile of the split-operand (TF32x3 / BF16x3) GEMM
+// N tiles of the split-operand (TF32x3 / BF16x3) GEMM the tuner chooses from
+constexpr int MIX_NTN = 3;
+constexpr int MIX_TNS[MIX_NTN] = {64, 128, 256};
 cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
                         int bf16, cudaStream_t st);
 // W stage work units: units[k] = (task, first row, rows), sized so that a
@@ -307,7 +309,7 @@ constexpr int WUNIT_ITEMS = 256;
 cudaError_t launch_wstage_tc(const int4 *units, int nunits, const WTaskP *tasks, const WTerm *terms,
                              double *const *bufs, const int *active, int bf16, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
-                           const int *active, int *err, int bf16, cudaStream_t st);
+                           const int *active, int *err, int bf16, int tn, cudaStream_t st);
 // FP64-accurate products from BF16 digit slices (OZ_PLANES digits of 7 bits
 // per element, exact integer accumulation per digit level).  K blocks are 32
 // elements; one launch sums at most OZ_MAX_K of K exactly, longer K runs as

@@ -216,16 +216,30 @@ struct idmrg_ctx {
   bool oz_active() const { return oz_ok && o_oz && (mixed || fp64tc); }
   // the other FP64 GEMM lists (environments, prediction, SVD) in digit slices
   bool oz_lists() const { return o_oz && (mixed || fp64tc); }
-  std::vector<PackSeg> pk_step, pk_psi;   // per iteration (L, R) and per matvec (psi)
-  std::vector<TcTask> tc1k, tc3k;
-  std::vector<TcTile> tc1t, tc3t;
+  // split-operand GEMM lists: the L split (once per iteration) and, for
+  // every N-tile candidate k (MIX_TNS[k] columns), the psi split (every
+  // matvec), the R split (once per iteration, the chosen candidate's only)
+  // and the tasks and tiles of both GEMM stages; tt1 / tt3 hold the tuner's
+  // choice for stage 1 / stage 3
+  std::vector<PackSeg> pk_L, pk_psi[MIX_NTN], pk_R[MIX_NTN];
+  std::vector<TcTask> tc1k[MIX_NTN], tc3k[MIX_NTN];
+  std::vector<TcTile> tc1t[MIX_NTN], tc3t[MIX_NTN];
   std::vector<WTaskP> wtp;
   std::vector<WTerm> wtpm;
   std::vector<int4> wunits;  // W stage work units (task, first row, rows)
   DevBuf dwunits;
+  struct TcTune {
+    int choice = -1;
+    double work = -1.0;
+    float ms[MIX_NTN] = {0, 0, 0};
+    cudaEvent_t e0[MIX_NTN] = {}, e1[MIX_NTN] = {};
+  } tt1, tt3;
+  int tc_tunes = 0;  // tuning passes run (each times every candidate of a stage)
+  int force_tn[2] = {0, 0};  // N tile fixed by the caller for stage 1 / stage 3 (0: tuned)
 
-  int pk_step_rows = 0, pk_psi_rows = 0, wtp_rows = 0;
-  DevBuf dpks, dpkp, dtc1k, dtc1t, dtc3k, dtc3t, dwtp, dwtpm, dtarget;
+  int pk_L_rows = 0, pk_psi_rows = 0, pk_R_rows = 0, wtp_rows = 0;
+  DevBuf dpkL, dpkp[MIX_NTN], dpkR[MIX_NTN], dtc1k[MIX_NTN], dtc1t[MIX_NTN], dtc3k[MIX_NTN], dtc3t[MIX_NTN];
+  DevBuf dwtp, dwtpm, dtarget, dtune_out;
   std::vector<DevBuf> bPA1, bPB1, bT1F, bPA3, bPB3, bRMAP;
   // FP64-accurate digit-slice form of H_eff psi on the tensor cores (the
   // FP64 matvecs that start every mixed-precision Lanczos restart); usable
@@ -851,22 +865,94 @@ idmrg_status sync_bufs(idmrg_ctx *c) {
 //   stage 3, per out-sector jo of the right block: rows = (i, s, t, x) of the
 //     psi sub-blocks with right sector jo, K = (channel c, y') concatenated over
 //     the R channels, N = y in jo.
+// N-tile tuner of one split-operand GEMM stage (1: L psi, 3: T3 R^T): each
+// candidate of MIX_TNS runs twice on the current plan's operands (the second
+// run timed with events on the context's stream) and the fastest is kept.
+// It runs again only when the stage's work has moved by more than 10 %.
+// The operands may hold zeros or values left from another layout; the tuning
+// runs only write buffers that the next matvec rewrites (stage 1: T1; stage 3:
+// a scratch vector put in the output slot meanwhile).  Stage 3 packs R in each
+// candidate's layout before timing it; the caller packs the chosen one.
+idmrg_status check_dev_err(idmrg_ctx *c);
+idmrg_status tc_tune(idmrg_ctx *c, idmrg_ctx::TcTune &T, int stage, double work, int64_t max_psi) {
+  const int forced = c->force_tn[stage == 1 ? 0 : 1];
+  if (forced > 0) {
+    for (int k = 0; k < MIX_NTN; ++k)
+      if (MIX_TNS[k] == forced) T.choice = k;
+    T.work = -1.0;  // tune again once the tile is no longer fixed
+    return IDMRG_OK;
+  }
+  if (T.choice >= 0 && T.work > 0.0 && fabs(work - T.work) <= 0.1 * T.work) return IDMRG_OK;
+  T.work = work;
+  T.choice = 0;
+  auto &tiles = stage == 1 ? c->tc1t : c->tc3t;
+  bool any = false;
+  for (int k = 0; k < MIX_NTN; ++k) any |= !tiles[k].empty();
+  if (!any) return IDMRG_OK;
+  const int P = c->P;
+  std::vector<double *> keep(P, nullptr);
+  if (stage == 3) {
+    NOMEM(c->ensure(c->dtune_out, 8 * (size_t)max_psi));
+    for (int p = 0; p < P; ++p) {
+      keep[p] = c->hbufs[p * NBUF + BUF_OUT];
+      if (c->owns(p)) c->hbufs[p * NBUF + BUF_OUT] = c->dp(c->dtune_out);
+    }
+    NOMEM(c->upload(c->dbufs, c->hbufs));
+  }
+  double *const *bufs = (double *const *)c->dbufs.p;
+  for (int k = 0; k < MIX_NTN; ++k) {
+    if (!T.e0[k]) CK(cudaEventCreate(&T.e0[k]));
+    if (!T.e1[k]) CK(cudaEventCreate(&T.e1[k]));
+    if (stage == 3) {
+      CK(launch_pack((const PackSeg *)c->dpkR[k].p, (int)c->pk_R[k].size(), c->pk_R_rows, bufs, nullptr, c->bf16,
+                     c->st));
+      c->launches += 1;
+    }
+    const TcTile *dt = (const TcTile *)(stage == 1 ? c->dtc1t[k].p : c->dtc3t[k].p);
+    const TcTask *dk = (const TcTask *)(stage == 1 ? c->dtc1k[k].p : c->dtc3k[k].p);
+    const int nt = (int)tiles[k].size();
+    for (int rep = 0; rep < 2; ++rep) {
+      if (rep == 1) CK(cudaEventRecord(T.e0[k], c->st));
+      CK(launch_tc_gemm(dt, nt, dk, bufs, nullptr, (int *)c->derr.p, c->bf16, MIX_TNS[k], c->st));
+      c->launches += 1;
+    }
+    CK(cudaEventRecord(T.e1[k], c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  for (int k = 0; k < MIX_NTN; ++k) {
+    CK(cudaEventElapsedTime(&T.ms[k], T.e0[k], T.e1[k]));
+    if (T.ms[k] < T.ms[T.choice]) T.choice = k;
+  }
+  c->tc_tunes += 1;
+  if (stage == 3) {
+    for (int p = 0; p < P; ++p) c->hbufs[p * NBUF + BUF_OUT] = keep[p];
+    NOMEM(c->upload(c->dbufs, c->hbufs));
+  }
+  return check_dev_err(c);
+}
+
 idmrg_status plan_mixed(idmrg_ctx *c) {
   const int P = c->P, d = c->d, target = c->o.target_charge, dd = d * d;
-  const int GA = 16, GB = MIX_TN / 8;
-  // one packed K block is 128 bytes of every row: TA / TB floats per hi or lo tile
-  const int64_t TA = 128 * 32, TB = (int64_t)MIX_TN * 32;
+  const int GA = 16;
+  // one packed K block is 128 bytes of every row: TA floats per hi or lo A
+  // tile, 32 per row of a B tile
+  const int64_t TA = 128 * 32;
   const int kblk = c->bf16 ? 64 : 32;
   auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
-  c->pk_step.clear();
-  c->pk_psi.clear();
-  c->tc1k.clear();
-  c->tc1t.clear();
-  c->tc3k.clear();
-  c->tc3t.clear();
+  c->pk_L.clear();
+  for (int k = 0; k < MIX_NTN; ++k) {
+    c->pk_psi[k].clear();
+    c->pk_R[k].clear();
+    c->tc1k[k].clear();
+    c->tc1t[k].clear();
+    c->tc3k[k].clear();
+    c->tc3t[k].clear();
+  }
   c->wtp.clear();
   c->wtpm.clear();
-  c->pk_step_rows = c->pk_psi_rows = c->wtp_rows = 0;
+  c->pk_L_rows = c->pk_psi_rows = c->pk_R_rows = c->wtp_rows = 0;
+  double work1 = 0.0, work3 = 0.0;
+  int64_t max_psi = 1;
   auto seg = [&](std::vector<PackSeg> &v, int &mr, int sb, int dst_buf, int64_t dst_off, int src_buf,
                  int64_t src_off, int row0, int k0, int rows, int ks, int ld, int trans, int KB, int G) {
     if (rows <= 0 || ks <= 0) return;
@@ -898,9 +984,10 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
     const int SL = BL.S(), SR = BR.S();
     const int wa = L.lay.w, wc = R.lay.w;
     // ---------------- stage 1
-    std::vector<int64_t> pa1(SL, -1), pb1(SL, -1), t1f(SL, -1);
+    std::vector<int64_t> pa1(SL, -1), t1f(SL, -1);
     std::vector<std::vector<int>> rs1(SL, std::vector<int>(wa, -1));
-    int64_t pa1n = 0, pb1n = 0, t1fn = 0;
+    int64_t pa1n = 0, pb1n[MIX_NTN] = {0, 0, 0}, t1fn = 0;
+    max_psi = std::max<int64_t>(max_psi, psi.N);
     for (int si = 0; si < SL; ++si) {
       if (psi.C[si] == 0) continue;
       int M = 0;
@@ -912,42 +999,46 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
       }
       if (M == 0) continue;
       const int K = BL.dim[si], N = psi.C[si];
-      const int KB = (int)cdiv(K, kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, MIX_TN);
+      const int KB = (int)cdiv(K, kblk), MT = (int)cdiv(M, 128);
       pa1[si] = pa1n;
       pa1n += (int64_t)MT * KB * 2 * TA;
-      pb1[si] = pb1n;
-      pb1n += (int64_t)NT * KB * 2 * TB;
       t1f[si] = t1fn;
       t1fn += (int64_t)M * N;
+      work1 += 2.0 * M * K * N;
       for (int a = 0; a < wa; ++a) {
         if (rs1[si][a] < 0) continue;
         const int so = L.lay.so[a * SL + si];
-        seg(c->pk_step, c->pk_step_rows, p, BUF_PA1, pa1[si], BUF_L, L.lay.off[a * SL + si], rs1[si][a], 0,
+        seg(c->pk_L, c->pk_L_rows, p, BUF_PA1, pa1[si], BUF_L, L.lay.off[a * SL + si], rs1[si][a], 0,
             BL.dim[so], K, K, 0, KB, GA);
       }
-      seg(c->pk_psi, c->pk_psi_rows, p, BUF_PB1, pb1[si], BUF_IN, psi.roff[si], 0, 0, N, K, N, 1, KB, GB);
-      TcTask t{};
-      t.a_off = pa1[si];
-      t.b_off = pb1[si];
-      t.c_off = t1f[si];
-      t.sb = p;
-      t.M = M;
-      t.N = N;
-      t.KB = KB;
-      t.a_buf = BUF_PA1;
-      t.b_buf = BUF_PB1;
-      t.c_buf = BUF_T1F;
-      t.mode = 0;
-      t.ldc = N;
-      const int id = (int)c->tc1k.size();
-      c->tc1k.push_back(t);
-      for (int mt = 0; mt < MT; ++mt)
-        for (int nt = 0; nt < NT; ++nt) c->tc1t.push_back(TcTile{id, mt, nt, 0});
+      for (int k = 0; k < MIX_NTN; ++k) {  // B (psi) layout, task and tiles per N tile
+        const int TN = MIX_TNS[k], NT = (int)cdiv(N, TN);
+        const int64_t pb = pb1n[k];
+        pb1n[k] += (int64_t)NT * KB * 2 * TN * 32;
+        seg(c->pk_psi[k], c->pk_psi_rows, p, BUF_PB1, pb, BUF_IN, psi.roff[si], 0, 0, N, K, N, 1, KB, TN / 8);
+        TcTask t{};
+        t.a_off = pa1[si];
+        t.b_off = pb;
+        t.c_off = t1f[si];
+        t.sb = p;
+        t.M = M;
+        t.N = N;
+        t.KB = KB;
+        t.a_buf = BUF_PA1;
+        t.b_buf = BUF_PB1;
+        t.c_buf = BUF_T1F;
+        t.mode = 0;
+        t.ldc = N;
+        const int id = (int)c->tc1k[k].size();
+        c->tc1k[k].push_back(t);
+        for (int mt = 0; mt < MT; ++mt)
+          for (int nt = 0; nt < NT; ++nt) c->tc1t[k].push_back(TcTile{id, mt, nt, 0});
+      }
     }
     // ---------------- stage 3
-    std::vector<int64_t> pa3(SR, -1), pb3(SR, -1), rmo(SR, -1);
+    std::vector<int64_t> pa3(SR, -1), rmo(SR, -1);
     std::vector<int64_t> rmap;
-    int64_t pa3n = 0, pb3n = 0;
+    int64_t pa3n = 0, pb3n[MIX_NTN] = {0, 0, 0};
     for (int jo = 0; jo < SR; ++jo) {
       // K: channels c whose R_c block lands in jo
       std::vector<int> ks(wc, -1);
@@ -973,17 +1064,22 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
           }
       if (M == 0) continue;
       const int N = BR.dim[jo];
-      const int KB = (int)cdiv(std::max(K, 1), kblk), MT = (int)cdiv(M, 128), NT = (int)cdiv(N, MIX_TN);
+      const int KB = (int)cdiv(std::max(K, 1), kblk), MT = (int)cdiv(M, 128);
       pa3[jo] = pa3n;
       pa3n += (int64_t)MT * KB * 2 * TA;
-      pb3[jo] = pb3n;
-      pb3n += (int64_t)NT * KB * 2 * TB;
       rmo[jo] = r0;
-      for (int cc = 0; cc < wc; ++cc) {
-        if (ks[cc] < 0) continue;
-        const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
-        seg(c->pk_step, c->pk_step_rows, p, BUF_PB3, pb3[jo], BUF_R, R.lay.off[cc * SR + jin], 0, ks[cc], N,
-            BR.dim[jin], BR.dim[jin], 0, KB, GB);
+      work3 += 2.0 * M * K * N;
+      int64_t pb3[MIX_NTN];
+      for (int k = 0; k < MIX_NTN; ++k) {  // B (R) layout per N tile
+        const int TN = MIX_TNS[k], NT = (int)cdiv(N, TN);
+        pb3[k] = pb3n[k];
+        pb3n[k] += (int64_t)NT * KB * 2 * TN * 32;
+        for (int cc = 0; cc < wc; ++cc) {
+          if (ks[cc] < 0) continue;
+          const int jin = BR.find(BR.q[jo] - R.lay.chq[cc]);
+          seg(c->pk_R[k], c->pk_R_rows, p, BUF_PB3, pb3[k], BUF_R, R.lay.off[cc * SR + jin], 0, ks[cc], N,
+              BR.dim[jin], BR.dim[jin], 0, KB, TN / 8);
+        }
       }
       // W stage: T3[c](i,s,t) into rows rows_of(i,s,t), columns ks[c]
       for (int i = 0; i < SL; ++i)
@@ -1028,34 +1124,41 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
               c->wtp_rows = std::max(c->wtp_rows, w.rows);
             }
           }
-      TcTask t{};
-      t.a_off = pa3[jo];
-      t.b_off = pb3[jo];
-      t.rmap_off = rmo[jo];
-      t.sb = p;
-      t.M = M;
-      t.N = N;
-      t.KB = K > 0 ? KB : 0;
-      t.a_buf = BUF_PA3;
-      t.b_buf = BUF_PB3;
-      t.c_buf = BUF_OUT;
-      t.rmap_buf = BUF_RMAP;
-      t.mode = 1;
-      const int id = (int)c->tc3k.size();
-      c->tc3k.push_back(t);
-      for (int mt = 0; mt < MT; ++mt)
-        for (int nt = 0; nt < NT; ++nt) c->tc3t.push_back(TcTile{id, mt, nt, 0});
+      for (int k = 0; k < MIX_NTN; ++k) {
+        const int NT = (int)cdiv(N, MIX_TNS[k]);
+        TcTask t{};
+        t.a_off = pa3[jo];
+        t.b_off = pb3[k];
+        t.rmap_off = rmo[jo];
+        t.sb = p;
+        t.M = M;
+        t.N = N;
+        t.KB = K > 0 ? KB : 0;
+        t.a_buf = BUF_PA3;
+        t.b_buf = BUF_PB3;
+        t.c_buf = BUF_OUT;
+        t.rmap_buf = BUF_RMAP;
+        t.mode = 1;
+        const int id = (int)c->tc3k[k].size();
+        c->tc3k[k].push_back(t);
+        for (int mt = 0; mt < MT; ++mt)
+          for (int nt = 0; nt < NT; ++nt) c->tc3t[k].push_back(TcTile{id, mt, nt, 0});
+      }
     }
+    // B operands sized for the widest layout of any candidate
+    const int64_t pb1max = std::max({pb1n[0], pb1n[1], pb1n[2]}), pb3max = std::max({pb3n[0], pb3n[1], pb3n[2]});
     NOMEM(c->ensure(c->bPA1[p], 4 * std::max<int64_t>(pa1n, 4)) &&
-          c->ensure(c->bPB1[p], 4 * std::max<int64_t>(pb1n, 4)) &&
+          c->ensure(c->bPB1[p], 4 * std::max<int64_t>(pb1max, 4)) &&
           c->ensure(c->bT1F[p], 4 * std::max<int64_t>(t1fn, 4)) &&
           c->ensure(c->bPA3[p], 4 * std::max<int64_t>(pa3n, 4)) &&
-          c->ensure(c->bPB3[p], 4 * std::max<int64_t>(pb3n, 4)) && c->upload(c->bRMAP[p], rmap));
-    // zero padding of every packed operand (only real elements are rewritten later)
+          c->ensure(c->bPB3[p], 4 * std::max<int64_t>(pb3max, 4)) && c->upload(c->bRMAP[p], rmap));
+    // zero padding of every packed operand (only real elements are rewritten
+    // later; a K block's padding is zero in A, so B's padding only has to
+    // hold finite values, which a switch of B layouts leaves behind)
     CK(cudaMemsetAsync(c->bPA1[p].p, 0, 4 * pa1n, c->st));
-    CK(cudaMemsetAsync(c->bPB1[p].p, 0, 4 * pb1n, c->st));
+    CK(cudaMemsetAsync(c->bPB1[p].p, 0, 4 * pb1max, c->st));
     CK(cudaMemsetAsync(c->bPA3[p].p, 0, 4 * pa3n, c->st));
-    CK(cudaMemsetAsync(c->bPB3[p].p, 0, 4 * pb3n, c->st));
+    CK(cudaMemsetAsync(c->bPB3[p].p, 0, 4 * pb3max, c->st));
     c->hbufs[p * NBUF + BUF_PA1] = c->dp(c->bPA1[p]);
     c->hbufs[p * NBUF + BUF_PB1] = c->dp(c->bPB1[p]);
     c->hbufs[p * NBUF + BUF_T1F] = c->dp(c->bT1F[p]);
@@ -1076,14 +1179,29 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
     }
   }
   NOMEM(c->upload(c->dwunits, c->wunits));
-  NOMEM(c->upload(c->dpks, c->pk_step) && c->upload(c->dpkp, c->pk_psi) && c->upload(c->dtc1k, c->tc1k) &&
-        c->upload(c->dtc1t, c->tc1t) && c->upload(c->dtc3k, c->tc3k) && c->upload(c->dtc3t, c->tc3t) &&
-        c->upload(c->dwtp, c->wtp) && c->upload(c->dwtpm, c->wtpm));
+  NOMEM(c->upload(c->dpkL, c->pk_L) && c->upload(c->dwtp, c->wtp) && c->upload(c->dwtpm, c->wtpm));
+  for (int k = 0; k < MIX_NTN; ++k)
+    NOMEM(c->upload(c->dpkp[k], c->pk_psi[k]) && c->upload(c->dpkR[k], c->pk_R[k]) &&
+          c->upload(c->dtc1k[k], c->tc1k[k]) && c->upload(c->dtc1t[k], c->tc1t[k]) &&
+          c->upload(c->dtc3k[k], c->tc3k[k]) && c->upload(c->dtc3t[k], c->tc3t[k]));
   NOMEM(c->upload(c->dbufs, c->hbufs));
-  // split the environments once for this iteration
+  // split L once for this iteration
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
-  CK(launch_pack((const PackSeg *)c->dpks.p, (int)c->pk_step.size(), c->pk_step_rows, (double *const *)c->dbufs.p,
+  CK(launch_pack((const PackSeg *)c->dpkL.p, (int)c->pk_L.size(), c->pk_L_rows, (double *const *)c->dbufs.p,
                  nullptr, c->bf16, c->st));
+  c->kend(IDMRG_K_HEFF_WSTAGE);
+  c->launches += 1;
+  // N tiles: tuned whenever a stage's work moved by more than 10 % since
+  // its last tuning (every iteration while the blocks grow, rarely after)
+  idmrg_status ts = tc_tune(c, c->tt1, 1, work1, max_psi);
+  if (ts != IDMRG_OK) return ts;
+  ts = tc_tune(c, c->tt3, 3, work3, max_psi);
+  if (ts != IDMRG_OK) return ts;
+  // split R once for this iteration, in the chosen stage-3 layout
+  const int k3 = c->tt3.choice;
+  c->kbegin(IDMRG_K_HEFF_WSTAGE);
+  CK(launch_pack((const PackSeg *)c->dpkR[k3].p, (int)c->pk_R[k3].size(), c->pk_R_rows,
+                 (double *const *)c->dbufs.p, nullptr, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE);
   c->launches += 1;
   return IDMRG_OK;
@@ -1445,21 +1563,22 @@ idmrg_status heff_launch_mixed(idmrg_ctx *c, const int *active_dev, const int *a
       pb += (8.0 + hl) * S.wpack_elems;
       wb += 4.0 * S.wt1_elems + hl * S.wt3_elems;
     }
+  const int k1 = std::max(c->tt1.choice, 0), k3 = std::max(c->tt3.choice, 0);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
-  CK(launch_pack((const PackSeg *)c->dpkp.p, (int)c->pk_psi.size(), c->pk_psi_rows, bufs, active_dev, c->bf16,
-                 c->st));
+  CK(launch_pack((const PackSeg *)c->dpkp[k1].p, (int)c->pk_psi[k1].size(), c->pk_psi_rows, bufs, active_dev,
+                 c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, 0.0, pb);
   c->kbegin(IDMRG_K_HEFF_GEMM);
-  CK(launch_tc_gemm((const TcTile *)c->dtc1t.p, (int)c->tc1t.size(), (const TcTask *)c->dtc1k.p, bufs, active_dev,
-                    (int *)c->derr.p, c->bf16, c->st));
+  CK(launch_tc_gemm((const TcTile *)c->dtc1t[k1].p, (int)c->tc1t[k1].size(), (const TcTask *)c->dtc1k[k1].p, bufs,
+                    active_dev, (int *)c->derr.p, c->bf16, MIX_TNS[k1], c->st));
   c->kend(IDMRG_K_HEFF_GEMM);
   c->kbegin(IDMRG_K_HEFF_WSTAGE);
   CK(launch_wstage_tc((const int4 *)c->dwunits.p, (int)c->wunits.size(), (const WTaskP *)c->dwtp.p,
                       (const WTerm *)c->dwtpm.p, bufs, active_dev, c->bf16, c->st));
   c->kend(IDMRG_K_HEFF_WSTAGE, wf, wb);
   c->kbegin(IDMRG_K_HEFF_GEMM);
-  CK(launch_tc_gemm((const TcTile *)c->dtc3t.p, (int)c->tc3t.size(), (const TcTask *)c->dtc3k.p, bufs, active_dev,
-                    (int *)c->derr.p, c->bf16, c->st));
+  CK(launch_tc_gemm((const TcTile *)c->dtc3t[k3].p, (int)c->tc3t[k3].size(), (const TcTask *)c->dtc3k[k3].p, bufs,
+                    active_dev, (int *)c->derr.p, c->bf16, MIX_TNS[k3], c->st));
   c->kend(IDMRG_K_HEFF_GEMM, gf, by);
   c->launches += 4;
   c->mixed_matvecs += 1;
@@ -3415,12 +3534,19 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
                     &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgk, &c->dsgs,
-                    &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpks, &c->dpkp, &c->dtc1k, &c->dtc1t, &c->dtc3k,
-                    &c->dtc3t, &c->dwtp, &c->dwtpm, &c->dwunits, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp,
+                    &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpkL, &c->dtune_out,
+                    &c->dwtp, &c->dwtpm, &c->dwunits, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp,
                     &c->doz1k,
                     &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp, &c->goz_planes,
                     &c->goz_exps})
     rel(*b);
+  for (int k = 0; k < MIX_NTN; ++k)
+    for (DevBuf *b : {&c->dpkp[k], &c->dpkR[k], &c->dtc1k[k], &c->dtc1t[k], &c->dtc3k[k], &c->dtc3t[k]}) rel(*b);
+  for (auto *t : {&c->tt1, &c->tt3})
+    for (int k = 0; k < MIX_NTN; ++k) {
+      if (t->e0[k]) cudaEventDestroy(t->e0[k]);
+      if (t->e1[k]) cudaEventDestroy(t->e1[k]);
+    }
   {
     ObsState &S = c->obs;
     for (DevBuf *b : {&S.A, &S.Y, &S.envl, &S.envr, &S.res, &S.tab, &S.emb, &S.scal, &S.dq0, &S.unit.dtasks, &S.unit.dsegs,
@@ -4076,6 +4202,25 @@ idmrg_status idmrg_svd_stats(const idmrg_ctx *c, int *jobs, int *max_cols, int *
   if (max_rank) *max_rank = c->svd_max_rank;
   if (max_sweeps) *max_sweeps = c->svd_max_sweeps;
   if (mean_sweeps) *mean_sweeps = c->svd_mean_sweeps;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_set_gemm_tile(idmrg_ctx *c, int tn1, int tn3) {
+  if (!c) return IDMRG_EINVAL;
+  auto ok = [](int t) { return t == 0 || t == 64 || t == 128 || t == 256; };
+  if (!ok(tn1) || !ok(tn3)) return c->fail(IDMRG_EINVAL, "set_gemm_tile: N tiles are 0 (tuned), 64, 128 or 256");
+  c->force_tn[0] = tn1;
+  c->force_tn[1] = tn3;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_gemm_tuning(const idmrg_ctx *c, int stage, int *tn, float *ms, int *tunings) {
+  if (!c || (stage != 1 && stage != 3)) return IDMRG_EINVAL;
+  const idmrg_ctx::TcTune &T = stage == 1 ? c->tt1 : c->tt3;
+  if (tn) *tn = T.choice >= 0 ? MIX_TNS[T.choice] : 0;
+  if (ms)
+    for (int k = 0; k < MIX_NTN; ++k) ms[k] = T.ms[k];
+  if (tunings) *tunings = c->tc_tunes;
   return IDMRG_OK;
 }
 

@@ -57,9 +57,14 @@ __global__ void __launch_bounds__(DOT_THREADS) obs_dot_kernel(const double *__re
 }
 
 // y = a x + b y
+// y = a x + b y; a zero coefficient does not read its operand (b = 0
+// overwrites y, which may hold anything, including NaN bit patterns left in
+// freshly allocated memory)
 __global__ void obs_axpby_kernel(const double *x, double *y, int64_t n, double a, double b) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ax = a == 0.0 ? 0.0 : a * x[i];
+    y[i] = b == 0.0 ? ax : ax + b * y[i];
+  }
 }
 
 __device__ __forceinline__ uint64_t obs_mix64(uint64_t z) {

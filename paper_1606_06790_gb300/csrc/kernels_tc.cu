@@ -15,8 +15,9 @@
 //              contiguous range that a single bulk (TMA) copy moves.
 //  wstage_tc : T3[c] = sum W12 T1[a] from the FP32 stage-1 output, written
 //              straight into the packed A operand of stage 3.
-//  tc_gemm   : persistent grouped GEMM over a list of 128 x MIX_TN output
-//              tiles, one CTA per SM: a producer warp streams the hi/lo tiles
+//  tc_gemm   : persistent grouped GEMM over a list of 128 x TN output tiles
+//              (TN = 64, 128 or 256, picked per list by the context's tuner),
+//              one CTA per SM: a producer warp streams the hi/lo tiles
 //              of A and B through a ring of shared-memory stages with
 //              cp.async.bulk, an MMA warp issues the tcgen05.mma chain into one
 //              of two tensor-memory accumulators, four epilogue warps read the
@@ -206,12 +207,23 @@ __global__ void wstage_tc_kernel(const int4 *__restrict__ units, const WTaskP *_
 
 constexpr int TM = 128;
 constexpr int A_TILE = TM * 32;         // floats per A tile (one of hi/lo)
-constexpr int B_TILE = MIX_TN * 32;     // floats per B tile
-constexpr int STAGE_FLOATS = 2 * A_TILE + 2 * B_TILE;
 constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (about 2 s)
 
+// Shapes of the persistent GEMM for an N tile of TN columns: a ring stage
+// holds one K block of the A tile and of the B tile, hi and lo; as many
+// stages as fit in 192 KB of shared memory (4, 3, 2 for TN = 64, 128, 256).
+template <int TN>
+struct PsShape {
+  static_assert(TN == 64 || TN == 128 || TN == 256, "N tile");
+  static constexpr int B_TILE = TN * 32;  // floats per B tile (one of hi/lo)
+  static constexpr int STAGE_FLOATS = 2 * A_TILE + 2 * B_TILE;
+  static constexpr int STAGES = (192 * 1024) / (STAGE_FLOATS * 4);
+  static constexpr int SMEM = STAGES * STAGE_FLOATS * 4;
+  static_assert(STAGES >= 2, "ring depth");
+};
+
 // ---------------------------------------------- persistent grouped GEMM
-// Output tiles of 128 rows x MIX_TN columns, one CTA per SM looping over the
+// Output tiles of 128 rows x TN columns, one CTA per SM looping over the
 // tile list (tile t = blockIdx.x + i gridDim.x), with three roles:
 // warp 0 streams the K blocks of successive tiles through a PS_STAGES-deep
 // ring of shared memory (bulk copies), warp 1 issues the MMA chain of a tile
@@ -222,22 +234,28 @@ constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (about 2 s)
 // Ring and accumulator buffers are handed over by mbarriers whose phases
 // follow from running counters; every wait is bounded, a timeout sets the
 // error word and makes every role leave its loop, and the accumulators are
-// released only once every MMA issued has completed.
-constexpr int PS_STAGES = 4;
+// released only once every MMA issued has completed.  The N tile (64, 128
+// or 256 columns) is chosen per GEMM list by the plan's tuner: a wider tile
+// reads each A tile from L2 fewer times, a narrower one wastes less of a
+// ragged N.
 constexpr int PS_THREADS = 192;
 
-template <bool BF16>
+template <bool BF16, int TN>
 __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile *__restrict__ tiles, int ntiles,
                                                                    const TcTask *__restrict__ tasks,
                                                                    double *const *__restrict__ bufs,
                                                                    const int *__restrict__ active, int *err) {
+  using Sh = PsShape<TN>;
+  constexpr int PS_STAGES = Sh::STAGES;
+  constexpr int B_TILE = Sh::B_TILE;
+  constexpr int STAGE_FLOATS = Sh::STAGE_FLOATS;
   extern __shared__ __align__(1024) float sm[];
   __shared__ __align__(8) uint64_t full[PS_STAGES], empty[PS_STAGES], accf[2], acce[2], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 2 * MIX_TN);
+    tc::tmem_alloc(&tmem_base, 2 * TN);
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 32) {
@@ -293,8 +311,8 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      constexpr uint32_t idesc = tc::instr_desc(TM, MIX_TN, BF16 ? 1u : 2u);
-      constexpr uint32_t lboA = (TM / 8) * 128, lboB = (MIX_TN / 8) * 128, sbo = 128;
+      constexpr uint32_t idesc = tc::instr_desc(TM, TN, BF16 ? 1u : 2u);
+      constexpr uint32_t lboA = (TM / 8) * 128, lboB = (TN / 8) * 128, sbo = 128;
       long long it = 0;
       int lt = 0;
       bool ok = true;
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
           break;
         }
         tc::fence_after_sync();
-        const uint32_t d = tmem + (uint32_t)(a * MIX_TN);
+        const uint32_t d = tmem + (uint32_t)(a * TN);
         for (int kb = 0; kb < T.KB; ++kb, ++it) {
           const int s = (int)(it % PS_STAGES);
           if (!tc::mbar_wait(&full[s], (uint32_t)((it / PS_STAGES) & 1), WAIT_BUDGET)) {
@@ -366,15 +384,15 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
       }
       tc::fence_after_sync();
       const int row = tile.mt * TM + 32 * q + lane;
-      const int col0 = tile.nt * MIX_TN;
+      const int col0 = tile.nt * TN;
       double *cbase = bufs[T.sb * NBUF + T.c_buf];
       int64_t obase = 0;
       if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
 #pragma unroll
-      for (int c = 0; c < MIX_TN; c += 16) {
+      for (int c = 0; c < TN; c += 16) {
         float vv[16];
         if (T.KB > 0) {
-          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * MIX_TN + c), vv);
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TN + c), vv);
         } else {
 #pragma unroll
           for (int i = 0; i < 16; ++i) vv[i] = 0.f;
@@ -410,7 +428,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
   const int aborted = abort_flag;
   if (warp == 0 && !(aborted & 2)) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 2 * MIX_TN);
+    tc::tmem_dealloc(tmem, 2 * TN);
   }
 }
 
@@ -804,8 +822,20 @@ cudaError_t launch_wstage_tc(const int4 *units, int nunits, const WTaskP *tasks,
   return cudaGetLastError();
 }
 
+template <int TN>
+static cudaError_t launch_tc_gemm_tn(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
+                                     const int *active, int *err, int bf16, int sms, cudaStream_t st) {
+  constexpr int smem = PsShape<TN>::SMEM;
+  auto kern = bf16 ? tc_gemm_ps_kernel<true, TN> : tc_gemm_ps_kernel<false, TN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = ntiles < sms ? ntiles : sms;
+  kern<<<grid, PS_THREADS, smem, st>>>(tiles, ntiles, tasks, bufs, active, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,
-                           const int *active, int *err, int bf16, cudaStream_t st) {
+                           const int *active, int *err, int bf16, int tn, cudaStream_t st) {
   if (ntiles <= 0) return cudaGetLastError();
   static int sms = 0;
   if (sms == 0) {
@@ -814,13 +844,12 @@ cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess || sms <= 0) return e != cudaSuccess ? e : cudaErrorInvalidValue;
   }
-  const int smem = PS_STAGES * STAGE_FLOATS * (int)sizeof(float);
-  auto kern = bf16 ? tc_gemm_ps_kernel<true> : tc_gemm_ps_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  const int grid = ntiles < sms ? ntiles : sms;
-  kern<<<grid, PS_THREADS, smem, st>>>(tiles, ntiles, tasks, bufs, active, err);
-  return cudaGetLastError();
+  switch (tn) {
+    case 64: return launch_tc_gemm_tn<64>(tiles, ntiles, tasks, bufs, active, err, bf16, sms, st);
+    case 128: return launch_tc_gemm_tn<128>(tiles, ntiles, tasks, bufs, active, err, bf16, sms, st);
+    case 256: return launch_tc_gemm_tn<256>(tiles, ntiles, tasks, bufs, active, err, bf16, sms, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace idmrg

@@ -27,10 +27,14 @@ pytestmark = pytest.mark.gpu
 HEFF_BOUND = {"tf32x3": 3e-5, "bf16x3": 5e-4}
 
 
+@pytest.mark.parametrize("tiles", [(0, 0), (64, 256), (128, 128), (256, 64)])
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
-def test_mixed_heff_against_oracle(prec):
+def test_mixed_heff_against_oracle(prec, tiles):
+    """Every N tile of the split-operand GEMMs (the tuner's pick, and each
+    width forced on stages 1 and 3)."""
     mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 77), 8)
     ctx = context(mpo, 96, prec=prec)
+    ctx.set_gemm_tile(*tiles)
     for _ in range(8):
         ctx.unit_cell_step()
     rng = np.random.default_rng(4)
@@ -44,6 +48,9 @@ def test_mixed_heff_against_oracle(prec):
         assert err < HEFF_BOUND[prec], err
         assert err > 0.0  # really the reduced-precision path
         assert np.all(y[~mask] == 0.0)
+    for stage, tn in zip((1, 3), tiles):
+        t = ctx.gemm_tuning(stage)
+        assert t["tn"] == tn if tn else t["tn"] in (64, 128, 256)
     ctx.close()
 
 
