@@ -212,13 +212,18 @@ constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (about 2 s)
 // Shapes of the persistent GEMM for an N tile of TN columns: a ring stage
 // holds one K block of the A tile and of the B tile, hi and lo; as many
 // stages as fit in 192 KB of shared memory (4, 3, 2 for TN = 64, 128, 256).
+// Behind the ring, each epilogue warp has a 32 x 32 staging block (row
+// stride 33 floats) through which its accumulator rows reach global memory
+// as whole-row segments.
+constexpr int EPI_COLS = 32, EPI_LD = EPI_COLS + 1;
+constexpr int EPI_FLOATS = 4 * 32 * EPI_LD;
 template <int TN>
 struct PsShape {
   static_assert(TN == 64 || TN == 128 || TN == 256, "N tile");
   static constexpr int B_TILE = TN * 32;  // floats per B tile (one of hi/lo)
   static constexpr int STAGE_FLOATS = 2 * A_TILE + 2 * B_TILE;
   static constexpr int STAGES = (192 * 1024) / (STAGE_FLOATS * 4);
-  static constexpr int SMEM = STAGES * STAGE_FLOATS * 4;
+  static constexpr int SMEM = STAGES * STAGE_FLOATS * 4 + EPI_FLOATS * 4;
   static_assert(STAGES >= 2, "ring depth");
 };
 
@@ -250,6 +255,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
   constexpr int B_TILE = Sh::B_TILE;
   constexpr int STAGE_FLOATS = Sh::STAGE_FLOATS;
   extern __shared__ __align__(1024) float sm[];
+  float *epi = sm + PS_STAGES * STAGE_FLOATS;  // epilogue staging, EPI_FLOATS
   __shared__ __align__(8) uint64_t full[PS_STAGES], empty[PS_STAGES], accf[2], acce[2], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
@@ -383,33 +389,42 @@ __global__ void __launch_bounds__(PS_THREADS, 1) tc_gemm_ps_kernel(const TcTile 
         break;
       }
       tc::fence_after_sync();
-      const int row = tile.mt * TM + 32 * q + lane;
+      // lane l holds accumulator row r0 + l; 32 columns at a time go through
+      // the warp's staging block, then out row by row with the lanes along
+      // the columns (one 128-byte FP32 or 256-byte FP64 store per row)
+      const int r0 = tile.mt * TM + 32 * q;
       const int col0 = tile.nt * TN;
+      const int nrows = min(32, T.M - r0);
       double *cbase = bufs[T.sb * NBUF + T.c_buf];
       int64_t obase = 0;
-      if (T.mode == 1 && row < T.M) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + row];
+      if (T.mode == 1 && lane < nrows) obase = ((const int64_t *)bufs[T.sb * NBUF + T.rmap_buf])[T.rmap_off + r0 + lane];
+      float *stg = epi + q * 32 * EPI_LD;
+      for (int c = 0; c < TN && col0 + c < T.N; c += EPI_COLS) {
 #pragma unroll
-      for (int c = 0; c < TN; c += 16) {
-        float vv[16];
-        if (T.KB > 0) {
-          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TN + c), vv);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) vv[i] = 0.f;
-        }
-        if (row < T.M) {
-          if (T.mode == 0) {
-            float *out = (float *)cbase + T.c_off + (int64_t)row * T.ldc + col0 + c;
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (col0 + c + i < T.N) out[i] = vv[i];
+        for (int h = 0; h < EPI_COLS; h += 16) {
+          float vv[16];
+          if (T.KB > 0) {
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TN + c + h), vv);
           } else {
-            double *out = cbase + obase + col0 + c;
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (col0 + c + i < T.N) out[i] = (double)vv[i];
+            for (int i = 0; i < 16; ++i) vv[i] = 0.f;
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) stg[lane * EPI_LD + h + i] = vv[i];
+        }
+        __syncwarp();
+        const int col = col0 + c + lane;
+        if (T.mode == 0) {
+          float *out = (float *)cbase + T.c_off + (int64_t)r0 * T.ldc + col;
+          for (int r = 0; r < nrows; ++r)
+            if (col < T.N) out[(int64_t)r * T.ldc] = stg[r * EPI_LD + lane];
+        } else {
+          for (int r = 0; r < nrows; ++r) {
+            const int64_t ob = __shfl_sync(0xffffffffu, obase, r);
+            if (col < T.N) cbase[ob + col] = (double)stg[r * EPI_LD + lane];
           }
         }
+        __syncwarp();
       }
       tc::fence_before_sync();
       __syncwarp();
