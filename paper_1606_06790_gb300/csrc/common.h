@@ -303,9 +303,8 @@ constexpr int MIX_NTN = 3;
 constexpr int MIX_TNS[MIX_NTN] = {64, 128, 256};
 cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *const *bufs, const int *active,
                         int bf16, cudaStream_t st);
-// W stage work units: units[k] = (task, first row, rows), sized so that a
-// unit holds about WUNIT_ITEMS (row, 16-byte group) items, one per thread
-constexpr int WUNIT_ITEMS = 256;
+// W stage work units: units[k] = (task, first row, K window): 32 rows of the
+// task's rectangle and the packed K columns [64 w, 64 w + 64) it overlaps
 cudaError_t launch_wstage_tc(const int4 *units, int nunits, const WTaskP *tasks, const WTerm *terms,
                              double *const *bufs, const int *active, int bf16, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcTile *tiles, int ntiles, const TcTask *tasks, double *const *bufs,

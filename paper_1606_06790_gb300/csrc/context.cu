@@ -1166,17 +1166,12 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
     c->hbufs[p * NBUF + BUF_PB3] = c->dp(c->bPB3[p]);
     c->hbufs[p * NBUF + BUF_RMAP] = c->dp(c->bRMAP[p]);
   }
-  // W stage units: rows of a rectangle grouped so that a unit has about
-  // WUNIT_ITEMS (row, 16-byte group) items
+  // W stage units: windows of 32 rows x 64 packed K columns of each rectangle
   c->wunits.clear();
-  {
-    const int gw = c->bf16 ? 8 : 4;
-    for (size_t k = 0; k < c->wtp.size(); ++k) {
-      const WTaskP &w = c->wtp[k];
-      const int ng = (w.k0 + w.cols - 1) / gw - w.k0 / gw + 1;
-      const int rpu = std::max(1, WUNIT_ITEMS / ng);
-      for (int r0 = 0; r0 < w.rows; r0 += rpu) c->wunits.push_back(make_int4((int)k, r0, std::min(rpu, w.rows - r0), 0));
-    }
+  for (size_t k = 0; k < c->wtp.size(); ++k) {
+    const WTaskP &w = c->wtp[k];
+    for (int r0 = 0; r0 < w.rows; r0 += 32)
+      for (int kw = w.k0 / 64; kw <= (w.k0 + w.cols - 1) / 64; ++kw) c->wunits.push_back(make_int4((int)k, r0, kw, 0));
   }
   NOMEM(c->upload(c->dwunits, c->wunits));
   NOMEM(c->upload(c->dpkL, c->pk_L) && c->upload(c->dwtp, c->wtp) && c->upload(c->dwtpm, c->wtpm));

@@ -99,48 +99,43 @@ __global__ void pack_kernel(const PackSeg *__restrict__ segs, double *const *__r
 }
 
 // T3 = sum W12 T1 into the packed stage-3 A operand.  The two-site MPO is
-// mostly pass-through (a T3 rectangle copies one T1 rectangle), so the stage
-// is bound by instructions per element rather than by arithmetic: a thread
-// takes one row and one 16-byte core-matrix row of the packed K range (8
-// BF16 or 4 TF32 elements), forms those elements from nterm T1 rows, and
-// stores the hi and lo parts with one 16-byte store each; only the partial
-// groups at the edges of a rectangle are written element by element.
+// mostly pass-through (a T3 rectangle copies one T1 rectangle, or sums a
+// few), so the stage streams T1 in and T3 out.  A CTA takes a window of 32
+// rows and 64 packed K columns (aligned to 64) of one rectangle.  Phase 1:
+// warps read T1 rows with the lanes along K (coalesced) and accumulate the
+// terms.  Phase 2: through a shared-memory tile, each thread takes one row
+// and one 16-byte group of the packed layout (8 BF16 or 4 TF32 elements),
+// the lanes along the rows, so that a warp's hi (and lo) stores fill 512
+// contiguous bytes of a K block.  Groups cut by the rectangle's K edges
+// belong partly to the neighbouring rectangle and are written element by
+// element.
 
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-template <int GW>  // elements per 16-byte group: 8 (BF16) or 4 (TF32)
-__device__ __forceinline__ void wstage_group(const WTaskP &t, const WTerm *__restrict__ terms, const float *in,
-                                             float *dst, int r, int kg) {
-  // kg: first packed k of the group (a multiple of GW); columns c = kg + j - k0
-  const int cbeg = max(kg, t.k0) - t.k0, cend = min(kg + GW, t.k0 + t.cols) - t.k0;
-  float acc[GW];
-#pragma unroll
-  for (int j = 0; j < GW; ++j) acc[j] = 0.f;
-  const int j0 = cbeg - (kg - t.k0);  // first valid lane of the group
-  for (int q = 0; q < t.nterm; ++q) {
-    const WTerm w = terms[t.term0 + q];
-    const float cf = (float)w.coef;
-    const float *src = in + w.in_off + (int64_t)r * w.in_ld + (kg - t.k0);
-#pragma unroll
-    for (int j = 0; j < GW; ++j)
-      if (j >= j0 && j < j0 + (cend - cbeg)) acc[j] = fmaf(cf, src[j], acc[j]);
-  }
-  const int row = t.row0 + r, rpt = 8 * t.G;
+constexpr int WT_ROWS = 32, WT_K = 64, WT_LD = WT_K + 4;  // window and tile row stride (floats)
+
+// group of GW packed elements [kg, kg + GW) of packed row `row` from the tile
+// row v[0..GW); elements outside [ka, kb) are left to their owners
+template <int GW>
+__device__ __forceinline__ void wt_store(float *dst, const WTaskP &t, int row, int kg, int ka, int kb,
+                                         const float *v) {
+  const int rpt = 8 * t.G;
   const int rt = row / rpt, rr = row - rt * rpt;
+  const bool full = kg >= ka && kg + GW <= kb;
   if (GW == 8) {  // BF16 pairs, 64 elements per K block
-    const int kb = kg >> 6, kc = (kg & 63) >> 3;
+    const int kbk = kg >> 6, kc = (kg & 63) >> 3;
     const int64_t tile_h = (int64_t)rpt * 64;
-    const int64_t o = ((int64_t)rt * t.KB + kb) * 2 * tile_h + (((int64_t)kc * t.G + (rr >> 3)) * 8 + (rr & 7)) * 8;
+    const int64_t o = ((int64_t)rt * t.KB + kbk) * 2 * tile_h + (((int64_t)kc * t.G + (rr >> 3)) * 8 + (rr & 7)) * 8;
     __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      hi[j] = __float2bfloat16_rn(acc[j]);
-      lo[j] = __float2bfloat16_rn(acc[j] - __bfloat162float(hi[j]));
+      hi[j] = __float2bfloat16_rn(v[j]);
+      lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
     }
     __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(dst) + o;
-    if (cend - cbeg == 8) {
+    if (full) {
       uint4 hv, lv;
       hv.x = pack_bf16x2(hi[0], hi[1]);
       hv.y = pack_bf16x2(hi[2], hi[3]);
@@ -155,29 +150,29 @@ __device__ __forceinline__ void wstage_group(const WTaskP &t, const WTerm *__res
     } else {
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (j >= j0 && j < j0 + (cend - cbeg)) {
+        if (kg + j >= ka && kg + j < kb) {
           h[j] = hi[j];
           h[tile_h + j] = lo[j];
         }
     }
   } else {  // TF32 pairs, 32 elements per K block
-    const int kb = kg >> 5, kc = (kg & 31) >> 2;
+    const int kbk = kg >> 5, kc = (kg & 31) >> 2;
     const int64_t tile_f = (int64_t)rpt * 32;
-    const int64_t o = ((int64_t)rt * t.KB + kb) * 2 * tile_f + (((int64_t)kc * t.G + (rr >> 3)) * 8 + (rr & 7)) * 4;
+    const int64_t o = ((int64_t)rt * t.KB + kbk) * 2 * tile_f + (((int64_t)kc * t.G + (rr >> 3)) * 8 + (rr & 7)) * 4;
     float hi[4], lo[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      hi[j] = tf32_round(acc[j]);
-      lo[j] = acc[j] - hi[j];
+      hi[j] = tf32_round(v[j]);
+      lo[j] = v[j] - hi[j];
     }
     float *f = dst + o;
-    if (cend - cbeg == 4) {
+    if (full) {
       *reinterpret_cast<float4 *>(f) = make_float4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<float4 *>(f + tile_f) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (j >= j0 && j < j0 + (cend - cbeg)) {
+        if (kg + j >= ka && kg + j < kb) {
           f[j] = hi[j];
           f[tile_f + j] = lo[j];
         }
@@ -185,23 +180,64 @@ __device__ __forceinline__ void wstage_group(const WTaskP &t, const WTerm *__res
   }
 }
 
-__global__ void wstage_tc_kernel(const int4 *__restrict__ units, const WTaskP *__restrict__ tasks,
-                                 const WTerm *__restrict__ terms, double *const *__restrict__ bufs,
-                                 const int *__restrict__ active, int bf16) {
-  const int4 u = units[blockIdx.x];  // (task, first row, rows)
+__global__ void __launch_bounds__(256) wstage_tc_kernel(const int4 *__restrict__ units,
+                                                        const WTaskP *__restrict__ tasks,
+                                                        const WTerm *__restrict__ terms,
+                                                        double *const *__restrict__ bufs,
+                                                        const int *__restrict__ active, int bf16) {
+  __shared__ __align__(16) float tile[WT_ROWS * WT_LD];
+  const int4 u = units[blockIdx.x];  // (task, first row, K window)
   const WTaskP t = tasks[u.x];
   if (active && !active[t.sb]) return;
-  const int r0 = u.y, nr = u.z;
+  const int r0 = u.y, kw = u.z * WT_K;
+  const int nr = min(WT_ROWS, t.rows - r0);
+  const int ka = max(kw, t.k0), kb = min(kw + WT_K, t.k0 + t.cols);  // packed K of the rectangle in the window
   const float *in = (const float *)bufs[t.sb * NBUF + t.in_buf];
   float *dst = (float *)bufs[t.sb * NBUF + t.dst_buf] + t.dst_off;
-  const int gw = bf16 ? 8 : 4;
-  const int g0 = t.k0 / gw, ng = (t.k0 + t.cols - 1) / gw - g0 + 1;
-  for (int i = threadIdx.x; i < nr * ng; i += blockDim.x) {
-    const int rr = i / ng, g = i - rr * ng;
-    if (bf16)
-      wstage_group<8>(t, terms, in, dst, r0 + rr, (g0 + g) * 8);
-    else
-      wstage_group<4>(t, terms, in, dst, r0 + rr, (g0 + g) * 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // phase 1: warp w holds rows w, w + 8, w + 16, w + 24; lane l columns kw + l, kw + l + 32
+  float acc[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.f;
+  for (int q = 0; q < t.nterm; ++q) {
+    const WTerm w = terms[t.term0 + q];
+    const float cf = (float)w.coef;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = warp + 8 * i;
+      if (r < nr) {
+        const float *src = in + w.in_off + (int64_t)(r0 + r) * w.in_ld;  // packed k at src[k - k0]
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = kw + lane + 32 * h;
+          if (k >= ka && k < kb) acc[i][h] = fmaf(cf, src[k - t.k0], acc[i][h]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    tile[(warp + 8 * i) * WT_LD + lane] = acc[i][0];
+    tile[(warp + 8 * i) * WT_LD + lane + 32] = acc[i][1];
+  }
+  __syncthreads();
+  // phase 2: item (group g, row r), r fastest, so a warp covers 32 rows of one group
+  const int gw = bf16 ? 8 : 4, ngr = WT_K / gw;
+  for (int it = threadIdx.x; it < ngr * WT_ROWS; it += blockDim.x) {
+    const int g = it >> 5, r = it & 31;
+    const int kg = kw + g * gw;
+    if (r >= nr || kg + gw <= ka || kg >= kb) continue;
+    const float *v = tile + r * WT_LD + g * gw;
+    if (bf16) {
+      float x[8];
+      *reinterpret_cast<float4 *>(x) = *reinterpret_cast<const float4 *>(v);
+      *reinterpret_cast<float4 *>(x + 4) = *reinterpret_cast<const float4 *>(v + 4);
+      wt_store<8>(dst, t, t.row0 + r0 + r, kg, ka, kb, x);
+    } else {
+      float x[4];
+      *reinterpret_cast<float4 *>(x) = *reinterpret_cast<const float4 *>(v);
+      wt_store<4>(dst, t, t.row0 + r0 + r, kg, ka, kb, x);
+    }
   }
 }
 
@@ -833,7 +869,7 @@ cudaError_t launch_pack(const PackSeg *segs, int nseg, int max_rows, double *con
 
 cudaError_t launch_wstage_tc(const int4 *units, int nunits, const WTaskP *tasks, const WTerm *terms,
                              double *const *bufs, const int *active, int bf16, cudaStream_t st) {
-  if (nunits > 0) wstage_tc_kernel<<<nunits, WUNIT_ITEMS, 0, st>>>(units, tasks, terms, bufs, active, bf16);
+  if (nunits > 0) wstage_tc_kernel<<<nunits, 256, 0, st>>>(units, tasks, terms, bufs, active, bf16);
   return cudaGetLastError();
 }
 
