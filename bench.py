@@ -620,12 +620,14 @@ def timed_run(pkg, mpo, m: int, prec: str, maxit: int, steps: int, warmup: int, 
         out["d2h"] = (d2h1 - d2h0) // k_steps
         if profiled:
             out["prof"] = ctx.profile_read()
+            out["svd_phases"] = ctx.svd_phase_ms()
         ctx.profile_enable(False)
         return out
 
     res = region(steps, False, Clocks(local))
     prof = region(prof_steps, True, None)
-    res.update(prof=prof["prof"], prof_step_ms=prof["step_ms"], prof_steps=prof_steps, ctx=ctx, n0=n0,
+    res.update(prof=prof["prof"], svd_phases=prof["svd_phases"], prof_step_ms=prof["step_ms"], prof_steps=prof_steps,
+               ctx=ctx, n0=n0,
                saturate_steps=nsat, settle_steps=nset)
     return res
 
@@ -837,6 +839,7 @@ def main():
         "roofline": heff,
         "gemm_tiles": tiles,
         "svd_stats": svd_stats,
+        "svd_phases_ms_per_step": {k: v / ps for k, v in run["svd_phases"].items()},
         "roofline_dominant": class_roofline(dom, prof[dom], args.prec, pk),
         "roofline_classes": {k: class_roofline(k, v, args.prec, pk) for k, v in prof.items() if v["ms"] > 0},
         "gpu_launches": run["launches"],

@@ -396,6 +396,18 @@ idmrg_status idmrg_set_svd_path(idmrg_ctx *ctx, int global_only);
 idmrg_status idmrg_svd_stats(const idmrg_ctx *ctx, int *jobs, int *max_cols, int *max_rank, int *max_sweeps,
                              double *mean_sweeps);
 
+/* Sweeps of the FP32 Jacobi stage of the last truncation's sector SVDs
+ * (those of rank 2 or more): the largest and the mean. */
+idmrg_status idmrg_svd_sweeps32(const idmrg_ctx *ctx, int *max_sweeps, double *mean_sweeps);
+
+/* Milliseconds spent, since profiling was last enabled, in the phases of the
+ * sector SVD of Step 4 (parts of IDMRG_K_SVD, event-timed on the context's
+ * stream): ms[0] gather and pivoted QR, ms[1] FP32 Jacobi, ms[2]
+ * Newton-Schulz orthogonalisation and X = B V, ms[3] FP64 Jacobi, ms[4]
+ * selection of the kept states, ms[5] compaction into U and V.  ms holds 6
+ * entries. */
+idmrg_status idmrg_svd_phase_ms(idmrg_ctx *ctx, double *ms);
+
 /* The N tile of the split-operand tensor-core GEMMs of H_eff psi (Sec. 3,
  * Step 3; mixed precisions only) that the context's tuner chose for stage 1
  * (stage = 1: L psi) or stage 3 (stage = 3: T3 R^T).  The tuner times 64-,

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
-    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_save", "idmrg_load",
+    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_svd_phase_ms", "idmrg_svd_sweeps32", "idmrg_save", "idmrg_load",
     "idmrg_correlation", "idmrg_transfer_spectrum", "idmrg_delta_pm", "idmrg_extrapolate",
     "idmrg_fit_correlation_length", "idmrg_set_pair_range", "idmrg_export_pair", "idmrg_import_pair",
 ]
@@ -126,6 +126,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_set_svd_path": (i, [vp, i]),
         "idmrg_gemm_tuning": (i, [vp, i, P(i), P(C.c_float), P(i)]),
         "idmrg_set_gemm_tile": (i, [vp, i, i]),
+        "idmrg_svd_phase_ms": (i, [vp, P(d)]),
+        "idmrg_svd_sweeps32": (i, [vp, P(i), P(d)]),
         "idmrg_correlation": (i, [vp, i, P(d), P(d), P(d), i, P(C.c_int64), P(C.c_int64), P(d)]),
         "idmrg_transfer_spectrum": (i, [vp, d, i, P(d), P(d), P(d), P(i)]),
         "idmrg_delta_pm": (i, [P(d), i, P(d), P(d), P(d)]),
@@ -469,7 +471,18 @@ class Context:
         j, mc, mr, ms, me = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_double()
         self._check(self.lib.idmrg_svd_stats(self.h, C.byref(j), C.byref(mc), C.byref(mr), C.byref(ms), C.byref(me)),
                     "svd_stats")
-        return dict(jobs=j.value, max_cols=mc.value, max_rank=mr.value, max_sweeps=ms.value, mean_sweeps=me.value)
+        m32, e32 = C.c_int(), C.c_double()
+        self._check(self.lib.idmrg_svd_sweeps32(self.h, C.byref(m32), C.byref(e32)), "svd_sweeps32")
+        return dict(jobs=j.value, max_cols=mc.value, max_rank=mr.value, max_sweeps=ms.value, mean_sweeps=me.value,
+                    max_sweeps32=m32.value, mean_sweeps32=e32.value)
+
+    SVD_PHASES = ("qr", "jacobi32", "newton_schulz_xbv", "jacobi64", "select", "compact")
+
+    def svd_phase_ms(self) -> Dict[str, float]:
+        """Event-timed milliseconds of the SVD's phases since profiling was enabled."""
+        ms = (C.c_double * len(self.SVD_PHASES))()
+        self._check(self.lib.idmrg_svd_phase_ms(self.h, ms), "svd_phase_ms")
+        return {k: ms[i] for i, k in enumerate(self.SVD_PHASES)}
 
     def set_gemm_tile(self, tn1: int, tn3: int) -> None:
         """Fix the N tiles of H_eff stages 1 and 3 (0 = tuned) from the next plan on."""

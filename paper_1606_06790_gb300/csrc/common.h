@@ -229,11 +229,15 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
                               double *work, int *iwork, double *sv, int *err, int jm_init, cudaStream_t st,
                               const cudaStream_t *side, const cudaEvent_t *ev);
 // FP32 Jacobi on every group (group 0, the sectors beyond the block kernels,
-// with cols0 columns at most, on the large-sector kernels): writes the
-// accumulated rotations of each job to its V (j_off, cols_a x cols_a)
+// with cols0 columns at most, on the large-sector kernels; its jobs from g0b
+// on, of at most cols0b columns, fit the shared-memory tournament): writes
+// the accumulated rotations of each job to its V (j_off, cols_a x cols_a).
+// side: 4 streams, ev: 5 events.
 cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                                int cols0, double *work, const int *iwork, cudaStream_t st,
+                                int cols0, int g0b, int cols0b, double *work, const int *iwork, cudaStream_t st,
                                 const cudaStream_t *side, const cudaEvent_t *ev);
+// the largest sector (columns) the shared-memory FP32 tournament holds
+int svd_jacobi32_big_max_cols();
 // per job over cols_a x cols_a elements: 0: V = I; 1: V = 1.5 V - 0.5 W
 // (Newton-Schulz step, W at w_off); 2: B = X (X at w_off)
 cudaError_t launch_svd_elementwise(const SvdJob *jobs, int njobs, int max_cols, int mode, double *work,

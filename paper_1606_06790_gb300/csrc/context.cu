@@ -174,8 +174,8 @@ struct idmrg_ctx {
   cudaStream_t st = nullptr;
   // side streams of the SVD (small Jacobi groups run beside the large one),
   // forked from and joined back to st by events
-  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t sev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   idmrg_status side_streams() {
     for (auto &x : side)
       if (!x && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return IDMRG_ECUDA;
@@ -297,6 +297,9 @@ struct idmrg_ctx {
 
   int svd_jobs = 0, svd_max_cols = 0, svd_max_rank = 0, svd_max_sweeps = 0;
   double svd_mean_sweeps = 0.0;
+  int svd_max_sweeps32 = 0;  // FP32 stage, over the jobs of rank >= 2
+  double svd_mean_sweeps32 = 0.0;
+  int svd_jobs32 = 0;
 
   std::vector<int> hmask;
   ObsState obs;
@@ -312,7 +315,11 @@ struct idmrg_ctx {
     uint64_t n = 0;
   };
   bool prof = false;
-  KTimer kt[IDMRG_K_COUNT];
+  // the public classes, then the phases of the sector SVD (timed inside
+  // IDMRG_K_SVD, read by idmrg_svd_phase_ms)
+  static constexpr int SVD_PHASES = 6;
+  static constexpr int KT_ALL = IDMRG_K_COUNT + SVD_PHASES;
+  KTimer kt[KT_ALL];
   std::vector<cudaEvent_t> evpool;
   uint64_t h2d = 0, d2h = 0;
 
@@ -2127,7 +2134,7 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
       J.w_off = work;
       work += (int64_t)J.cols_a * J.cols_a;
       J.perm_off = iw;
-      iw += J.cols_a + 2;
+      iw += J.cols_a + 3;  // permutation, rank, FP64 and FP32 Jacobi sweeps
       J.sv_off = sv;
       sv += J.cols_a;
       entries += J.cols_a;
@@ -2234,6 +2241,12 @@ idmrg_status trunc_host(idmrg_ctx *c, int q, const int *kpj, const double *lam, 
     c->svd_max_rank = std::max(c->svd_max_rank, rk);
     c->svd_max_sweeps = std::max(c->svd_max_sweeps, sw);
     c->svd_mean_sweeps += (double)sw / std::max(c->svd_jobs, 1);
+    if (rk >= 2) {
+      const int s32 = iwh[J.perm_off + J.cols_a + 2];
+      c->svd_max_sweeps32 = std::max(c->svd_max_sweeps32, s32);
+      c->svd_mean_sweeps32 += s32;
+      c->svd_jobs32 += 1;
+    }
   }
   TruncRec &T = c->cur[q];
   {
@@ -2305,6 +2318,9 @@ void svd_stats_reset(idmrg_ctx *c) {
   c->svd_jobs = (int)c->jobs.size();
   c->svd_max_cols = c->svd_max_rank = c->svd_max_sweeps = 0;
   c->svd_mean_sweeps = 0.0;
+  c->svd_max_sweeps32 = 0;
+  c->svd_mean_sweeps32 = 0.0;
+  c->svd_jobs32 = 0;
 }
 
 idmrg_status truncate(idmrg_ctx *c, int p) {
@@ -2316,7 +2332,10 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   if (s0 != IDMRG_OK) return s0;
   const int nj = (int)c->jobs.size();
   double *const *bufs = (double *const *)c->dbufs.p;
+  const int PH = IDMRG_K_COUNT;  // SVD phases: 0 gather + QR, 1 FP32 Jacobi, 2 Newton-Schulz + X = B V,
+                                // 3 FP64 Jacobi, 4 select, 5 compact
   c->kbegin(IDMRG_K_SVD);
+  c->kbegin(PH + 0);
   CK(launch_svd_gather_sized((const SvdJob *)c->sjobs.p, nj, c->tmaxel_all, bufs, BUF_PSI, c->dp(c->swork), c->st));
   // groups over all jobs (largest first across superblocks): the pivoted QR
   // and both Jacobi stages run each group on clusters of the same size
@@ -2341,9 +2360,21 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   const SvdJob *dj = (const SvdJob *)c->sjobs.p;
   double *sw = c->dp(c->swork);
   double *const *svb = (double *const *)c->dbufs.p;
+  c->kend(PH + 0);
+  c->kbegin(PH + 1);
   CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 0, sw, c->st));
-  CK(launch_svd_jacobi32(dj, (const int *)c->sorder.p, nj, g, gcols, cols0, sw, (const int *)c->siw.p, c->st, c->side,
-                         c->sev));
+  {
+    // group 0 from g0b on fits the shared-memory FP32 tournament (none in
+    // the forced large-sector mode, which exercises the all-global kernel)
+    const int bmax = c->svd_global ? 0 : svd_jacobi32_big_max_cols();
+    int g0b = 0;
+    while (g0b < g[0] && c->jobs[c->torder[g0b]].cols_a > bmax) ++g0b;
+    const int cols0b = g0b < g[0] ? c->jobs[c->torder[g0b]].cols_a : 0;
+    CK(launch_svd_jacobi32(dj, (const int *)c->sorder.p, nj, g, gcols, cols0, g0b, cols0b, sw, (const int *)c->siw.p,
+                           c->st, c->side, c->sev));
+  }
+  c->kend(PH + 1);
+  c->kbegin(PH + 2);
   for (int it = 0; it < 2; ++it) {
     {
     idmrg_status sg_ = gemm_run(c, c->tn_svdG, c->dsgk, c->dsgs, nullptr);
@@ -2360,16 +2391,21 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
     if (sg_ != IDMRG_OK) return sg_;
   }
   CK(launch_svd_elementwise(dj, nj, c->tmaxcols, 2, sw, c->st));
+  c->kend(PH + 2);
+  c->kbegin(PH + 3);
   CK(launch_svd_jacobi(dj, (const int *)c->sorder.p, nj, g, gcols, sw, (int *)c->siw.p, c->dp(c->ssv),
                        (int *)c->derr.p, 1, c->st, c->side, c->sev));
+  c->kend(PH + 3);
   c->launches += 12;
   // select: one launch, one CTA per superblock (no jobs: nothing kept)
   std::vector<int> sbl;
   for (int q = 0; q < P; ++q)
     if (want(c, p, q)) sbl.push_back(q);
+  c->kbegin(PH + 4);
   CK(launch_svd_select((const SvdJob *)c->sjobs.p, (const int *)c->sjob0.p, (const int *)c->snjob.p, P,
                        c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, select_out(c, 0), c->tentries_max,
                        c->st));
+  c->kend(PH + 4);
   c->kend(IDMRG_K_SVD, svd_flops(c, -1), 0.0);
   c->launches += 3;
   std::vector<int> kpj(std::max(nj, 1)), iwh(std::max(c->tiw, 1));
@@ -2391,8 +2427,10 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   int max_kept = 1;
   for (int v : kpj) max_kept = std::max(max_kept, v);
   c->kbegin(IDMRG_K_SVD);
+  c->kbegin(PH + 5);
   s = trunc_compact(c, c->scj, cj, max_kept, c->st);
   if (s != IDMRG_OK) return s;
+  c->kend(PH + 5);
   c->kend(IDMRG_K_SVD);
   const int stride = std::max(1, c->o.m);
   std::vector<double> lamk((size_t)P * stride);
@@ -3550,7 +3588,7 @@ void idmrg_destroy(idmrg_ctx *c) {
       rel(*b);
     for (auto &x : S.X) rel(x);
   }
-  for (int k = 0; k < IDMRG_K_COUNT; ++k) c->collapse(k);
+  for (int k = 0; k < idmrg_ctx::KT_ALL; ++k) c->collapse(k);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (cudaStream_t x : c->side)
     if (x) cudaStreamDestroy(x);
@@ -4162,7 +4200,7 @@ idmrg_status idmrg_launch_count(const idmrg_ctx *c, uint64_t *count) {
 idmrg_status idmrg_profile_enable(idmrg_ctx *c, int on) {
   if (!c) return IDMRG_EINVAL;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return IDMRG_ECUDA;
-  for (int k = 0; k < IDMRG_K_COUNT; ++k) {
+  for (int k = 0; k < idmrg_ctx::KT_ALL; ++k) {
     c->collapse(k);
     c->kt[k].ms = c->kt[k].flops = c->kt[k].bytes = 0.0;
     c->kt[k].n = 0;
@@ -4183,9 +4221,26 @@ idmrg_status idmrg_profile_read(idmrg_ctx *c, int k, double *ms, uint64_t *launc
   return IDMRG_OK;
 }
 
+idmrg_status idmrg_svd_phase_ms(idmrg_ctx *c, double *ms) {
+  if (!c || !ms) return IDMRG_EINVAL;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return IDMRG_ECUDA;
+  for (int k = 0; k < idmrg_ctx::SVD_PHASES; ++k) {
+    c->collapse(IDMRG_K_COUNT + k);
+    ms[k] = c->kt[IDMRG_K_COUNT + k].ms;
+  }
+  return IDMRG_OK;
+}
+
 idmrg_status idmrg_set_svd_path(idmrg_ctx *c, int global_only) {
   if (!c) return IDMRG_EINVAL;
   c->svd_global = global_only != 0;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_svd_sweeps32(const idmrg_ctx *c, int *max_sweeps, double *mean_sweeps) {
+  if (!c) return IDMRG_EINVAL;
+  if (max_sweeps) *max_sweeps = c->svd_max_sweeps32;
+  if (mean_sweeps) *mean_sweeps = c->svd_jobs32 ? c->svd_mean_sweeps32 / c->svd_jobs32 : 0.0;
   return IDMRG_OK;
 }
 

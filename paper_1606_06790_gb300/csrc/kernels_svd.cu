@@ -736,6 +736,12 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
   }
 }
 
+// the FP32 stage's sweep count of a job, in the slot after its rank and FP64
+// sweep count (read back for the statistics only)
+__device__ __forceinline__ void iwork32_sweeps(const int *iwork, const SvdJob &J, int sweep) {
+  const_cast<int *>(iwork)[J.perm_off + J.cols_a + 2] = sweep;
+}
+
 // FP32 stage (see jacobi32_block_kernel) for sector matrices too large for
 // the block kernels: the cyclic tournament of jacobi_kernel on FP32 copies
 // of B and of the rotations, kept in the job's x_off area (cols_a x cols_a
@@ -751,16 +757,17 @@ constexpr int J64_BATCH = 8;
 
 __device__ __forceinline__ void dots32(const float *xp, const float *xq, int len, int lane, float &a, float &b,
                                        float &g) {
-  for (int i0 = 0; i0 < len; i0 += 32 * J32_BATCH) {
-    float u[J32_BATCH], v[J32_BATCH];
+  // two batches in flight; each lane adds its elements in index order
+  for (int i0 = 0; i0 < len; i0 += 64 * J32_BATCH) {
+    float u[2 * J32_BATCH], v[2 * J32_BATCH];
 #pragma unroll
-    for (int r = 0; r < J32_BATCH; ++r) {
+    for (int r = 0; r < 2 * J32_BATCH; ++r) {
       const int i = i0 + lane + 32 * r;
       u[r] = i < len ? xp[i] : 0.f;
       v[r] = i < len ? xq[i] : 0.f;
     }
 #pragma unroll
-    for (int r = 0; r < J32_BATCH; ++r) {
+    for (int r = 0; r < 2 * J32_BATCH; ++r) {
       a = fmaf(u[r], u[r], a);
       b = fmaf(v[r], v[r], b);
       g = fmaf(u[r], v[r], g);
@@ -768,14 +775,19 @@ __device__ __forceinline__ void dots32(const float *xp, const float *xq, int len
   }
 }
 
-__device__ __forceinline__ void rot32(float *xp, float *xq, int len, int lane, float c, float sn) {
+// the rotation of a pair of B columns (length len) and of the same pair of
+// rotation columns (length lenv <= len) in one pass
+__device__ __forceinline__ void rot32x2(float *xp, float *xq, int len, float *vp, float *vq, int lenv, int lane,
+                                        float c, float sn) {
   for (int i0 = 0; i0 < len; i0 += 32 * J32_BATCH) {
-    float u[J32_BATCH], v[J32_BATCH];
+    float u[J32_BATCH], v[J32_BATCH], y[J32_BATCH], z[J32_BATCH];
 #pragma unroll
     for (int r = 0; r < J32_BATCH; ++r) {
       const int i = i0 + lane + 32 * r;
       u[r] = i < len ? xp[i] : 0.f;
       v[r] = i < len ? xq[i] : 0.f;
+      y[r] = i < lenv ? vp[i] : 0.f;
+      z[r] = i < lenv ? vq[i] : 0.f;
     }
 #pragma unroll
     for (int r = 0; r < J32_BATCH; ++r) {
@@ -783,6 +795,10 @@ __device__ __forceinline__ void rot32(float *xp, float *xq, int len, int lane, f
       if (i < len) {
         xp[i] = c * u[r] - sn * v[r];
         xq[i] = fmaf(sn, u[r], c * v[r]);
+      }
+      if (i < lenv) {
+        vp[i] = c * y[r] - sn * z[r];
+        vq[i] = fmaf(sn, y[r], c * z[r]);
       }
     }
   }
@@ -817,7 +833,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
     return v;
   };
   bool converged = false;
-  for (int sweep = 0; sweep < 15 && !converged; ++sweep) {
+  int sweep = 0;
+  for (; sweep < 15 && !converged; ++sweep) {
     if (threadIdx.x == 0) {
       local_changed = 0;
       sweep_rmax = 0;
@@ -848,8 +865,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
         const float t = z == 0.f ? 1.0f : copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
         if (!(fabsf(t) >= FLT_MIN) || !isfinite(t)) continue;
         const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
-        rot32(xp, xq, nr, lane, c, sn);
-        rot32(V32 + (int64_t)p * n, V32 + (int64_t)q * n, n, lane, c, sn);
+        rot32x2(xp, xq, nr, V32 + (int64_t)p * n, V32 + (int64_t)q * n, n, lane, c, sn);
         any = true;
         rmax = fmaxf(rmax, ratio);
       }
@@ -867,6 +883,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
     converged = (*flag0 == 0) || ((float)n * r * r < tol);
     cluster.sync();
   }
+  if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
   for (int64_t e = e0; e < (int64_t)n * n; e += stride) {
     const int64_t j = e / n, i = e - j * n;
     Vg[j * nr + i] = (double)V32[e];
@@ -1363,18 +1380,18 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
         if (p >= n || q >= n) continue;
         double *xp = B + (int64_t)p * nr, *xq = B + (int64_t)q * nr;
         double ga = 0.0;
-        // loads in batches of J64_BATCH per lane, all issued before their
-        // FMAs; each lane still adds its elements in index order
-        for (int i0 = 0; i0 < nr; i0 += 32 * J64_BATCH) {
-          double u[J64_BATCH], v[J64_BATCH];
+        // loads in batches of J64_BATCH per lane, two batches issued before
+        // their FMAs; each lane still adds its elements in index order
+        for (int i0 = 0; i0 < nr; i0 += 64 * J64_BATCH) {
+          double u[2 * J64_BATCH], v[2 * J64_BATCH];
 #pragma unroll
-          for (int r = 0; r < J64_BATCH; ++r) {
+          for (int r = 0; r < 2 * J64_BATCH; ++r) {
             const int i = i0 + lane + 32 * r;
             u[r] = i < nr ? xp[i] : 0.0;
             v[r] = i < nr ? xq[i] : 0.0;
           }
 #pragma unroll
-          for (int r = 0; r < J64_BATCH; ++r) ga = fma(u[r], v[r], ga);
+          for (int r = 0; r < 2 * J64_BATCH; ++r) ga = fma(u[r], v[r], ga);
         }
         ga = wsum(ga);
         double cp = 0.0, cq = 0.0;
@@ -1396,14 +1413,19 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
         any = true;
         cp = __shfl_sync(0xffffffffu, cp, 0);
         cq = __shfl_sync(0xffffffffu, cq, 0);
+        // B's and Jm's pair of columns in one pass (n <= nr): the four
+        // columns' loads of a batch are issued together
         double np2 = 0.0, nq2 = 0.0;
+        double *jp = Jm + (int64_t)p * n, *jq = Jm + (int64_t)q * n;
         for (int i0 = 0; i0 < nr; i0 += 32 * J64_BATCH) {
-          double u[J64_BATCH], v[J64_BATCH];
+          double u[J64_BATCH], v[J64_BATCH], y[J64_BATCH], z[J64_BATCH];
 #pragma unroll
           for (int r = 0; r < J64_BATCH; ++r) {
             const int i = i0 + lane + 32 * r;
             u[r] = i < nr ? xp[i] : 0.0;
             v[r] = i < nr ? xq[i] : 0.0;
+            y[r] = i < n ? jp[i] : 0.0;
+            z[r] = i < n ? jq[i] : 0.0;
           }
 #pragma unroll
           for (int r = 0; r < J64_BATCH; ++r) {
@@ -1417,23 +1439,9 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
                 nq2 = fma(v2, v2, nq2);
               }
             }
-          }
-        }
-        double *jp = Jm + (int64_t)p * n, *jq = Jm + (int64_t)q * n;
-        for (int i0 = 0; i0 < n; i0 += 32 * J64_BATCH) {
-          double u[J64_BATCH], v[J64_BATCH];
-#pragma unroll
-          for (int r = 0; r < J64_BATCH; ++r) {
-            const int i = i0 + lane + 32 * r;
-            u[r] = i < n ? jp[i] : 0.0;
-            v[r] = i < n ? jq[i] : 0.0;
-          }
-#pragma unroll
-          for (int r = 0; r < J64_BATCH; ++r) {
-            const int i = i0 + lane + 32 * r;
             if (i < n) {
-              jp[i] = fma(cp, v[r], u[r]);
-              jq[i] = fma(cq, u[r], v[r]);
+              jp[i] = fma(cp, z[r], y[r]);
+              jq[i] = fma(cq, y[r], z[r]);
             }
           }
         }
@@ -1569,7 +1577,8 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     rmax = fmaxf(rmax, ratio);
     return true;
   };
-  for (int sweep = 0; sweep < 15 && !converged; ++sweep) {
+  int sweep = 0;
+  for (; sweep < 15 && !converged; ++sweep) {
     if (threadIdx.x == 0) {
       local_changed = 0;
       sweep_rmax = 0;
@@ -1638,6 +1647,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     converged = (*flag0 == 0) || ((float)n * r * r < tol);
     cluster.sync();
   }
+  if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
   // rotations to V (FP64, cols_a x cols_a, identity outside the rank)
   for (int w = 0; w < 2; ++w) {
     const int k = pos[w], nv = valid(k);
@@ -1740,7 +1750,8 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
     rmax = fmaxf(rmax, ratio);
     return true;
   };
-  for (int sweep = 0; sweep < 15 && !converged; ++sweep) {
+  int sweep = 0;
+  for (; sweep < 15 && !converged; ++sweep) {
     if (threadIdx.x == 0) {
       local_changed = 0;
       sweep_rmax = 0;
@@ -1810,6 +1821,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
     converged = (*flag0 == 0) || ((float)n * r * r < tol);
     cluster.sync();
   }
+  if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
   // rotations to V (FP64, cols_a x cols_a): the columns of this CTA's two
   // home blocks (every block is back at its starting position after whole sweeps)
   for (int w = 0; w < 2; ++w) {
@@ -1818,6 +1830,245 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
       const int64_t j = e / n, i = e - j * n;
       Vg[(k * bw + j) * nr + i] = (double)V32[(k * bw + j) * n + i];
     }
+  }
+}
+
+// FP32 stage for sectors too large for jacobi32_big_kernel: the same block
+// tournament, with the blocks kept in global memory (the FP32 copy of B in
+// the job's x_off area) and streamed through shared memory.  The rank-n
+// columns are cut into P = 2 C k blocks of bw columns, bw small enough that
+// one pair of blocks fits in a CTA's shared memory; in every round each CTA
+// visits k of the round's P/2 block pairs in turn: it loads both blocks,
+// rotates every column of one against every column of the other (bw
+// sub-rounds of bw disjoint pairs; in the first round of a sweep also the
+// pairs inside each block), writes them back and applies the visit's
+// rotations, accumulated in a 2bw x 2bw matrix Q, to the same columns of the
+// FP32 rotations V (n x n, after B32) in one pass.  Rounds are separated by
+// the cluster barrier; blocks written in one round are read by other CTAs of
+// the cluster in the next, through L2 (loads bypass L1).  A sweep costs
+// P - 1 cluster barriers instead of n - 1.
+constexpr int JS_THREADS = 512;
+constexpr int JS_BW_MAX = 20;  // columns per block: a row of the two blocks of V fits in registers
+
+// shared memory of jacobi32_stream_kernel: two blocks of bw_cap columns of
+// ldb floats, Q (2 bw_cap columns of leading dimension qld), two norm arrays
+__host__ __device__ constexpr int js_qld(int bw_cap) { return (2 * bw_cap + 3) & ~3; }
+__host__ __device__ constexpr int64_t js_smem_floats(int bw_cap, int ldb) {
+  return 2 * (int64_t)bw_cap * ldb + (int64_t)js_qld(bw_cap) * 2 * bw_cap + 2 * bw_cap;
+}
+
+__global__ void __launch_bounds__(JS_THREADS, 1)
+    jacobi32_stream_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
+                           const int *__restrict__ iwork, int bw_cap, int ldb) {
+  extern __shared__ __align__(16) float js_sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const SvdJob Jb = jobs[order[blockIdx.x / C]];
+  const int nr = Jb.cols_a;                      // rows of B
+  const int n = iwork[Jb.perm_off + Jb.cols_a];  // columns: numerical rank
+  if (n < 2) return;  // uniform over the cluster
+  // blocks: bw <= bw_cap, P a multiple of 2C with P bw >= n, then bw = ceil(n / P)
+  int bw = min(bw_cap, (n + 2 * C - 1) / (2 * C));
+  const int nb = (n + bw - 1) / bw;
+  const int P = 2 * C * ((nb + 2 * C - 1) / (2 * C));
+  bw = (n + P - 1) / P;
+  const int k = P / (2 * C), qd = 2 * bw, qld = js_qld(bw_cap);
+  float *S0 = js_sm, *S1 = js_sm + (size_t)bw_cap * ldb;
+  float *Q = S1 + (size_t)bw_cap * ldb;            // column c at Q + c qld, rows 0 .. qd-1 (padding rows zero)
+  float *N0 = Q + (size_t)qld * 2 * bw_cap, *N1 = N0 + bw_cap;  // squared column norms of S0, S1
+  __shared__ int flag, local_changed, sweep_rmax, cl_rmax;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const double *Bg = work + Jb.b_off;
+  double *Vg = work + Jb.j_off;
+  float *B32 = reinterpret_cast<float *>(work + Jb.x_off);  // nr x n (column j at j nr), then V32
+  float *V32 = B32 + (int64_t)nr * n;                        // n x n (column j at j n)
+  const int64_t stride = (int64_t)C * blockDim.x, e0 = (int64_t)crank * blockDim.x + threadIdx.x;
+  for (int64_t e = e0; e < (int64_t)nr * n; e += stride) B32[e] = (float)Bg[e];
+  for (int64_t e = e0; e < (int64_t)n * n; e += stride) V32[e] = (e / n == e % n) ? 1.0f : 0.0f;
+  cluster.sync();
+  auto valid = [&](int b) { return max(0, min(bw, n - b * bw)); };
+  const float tol = sqrtf((float)nr) * FLT_EPSILON;
+  int *flag0 = cluster.map_shared_rank(&flag, 0);
+  int *rmax0 = cluster.map_shared_rank(&cl_rmax, 0);
+  auto wsumf = [](float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  };
+  const int l4 = ldb >> 2;  // float4 per column (ldb is a multiple of 32)
+  // one pair, one warp: column i of sA (squared norm na[i]) and column j of
+  // sB (nb_[j]), Q's columns qi and qj.  One dot product per pair: the
+  // rotation that zeroes the overlap g moves the squared norms to a - t g
+  // and b + t g, exactly in exact arithmetic; they are recomputed from the
+  // data whenever a block is loaded.
+  auto pair = [&](float *sA, float *na, int i, float *sB, float *nb_, int j, int qi, int qj, float &rmax) -> bool {
+    float4 *xp = reinterpret_cast<float4 *>(sA + i * ldb), *xq = reinterpret_cast<float4 *>(sB + j * ldb);
+    float g = 0.f;
+    for (int r = lane; r < l4; r += 32) {
+      const float4 x = xp[r], y = xq[r];
+      g = fmaf(x.x, y.x, g);
+      g = fmaf(x.y, y.y, g);
+      g = fmaf(x.z, y.z, g);
+      g = fmaf(x.w, y.w, g);
+    }
+    g = wsumf(g);
+    const float a = na[i], b = nb_[j];
+    if (!(a > 0.f) || !(b > 0.f)) return false;
+    const float ratio = fabsf(g) / sqrtf(a) / sqrtf(b);
+    if (!(ratio > tol)) return false;
+    const float z = (b - a) / (2.0f * g);
+    const float t = z == 0.f ? 1.0f : copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
+    if (!(fabsf(t) >= FLT_MIN) || !isfinite(t)) return false;
+    const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
+    for (int r = lane; r < l4; r += 32) {
+      const float4 x = xp[r], y = xq[r];
+      xp[r] = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z, c * x.w - sn * y.w);
+      xq[r] = make_float4(fmaf(sn, x.x, c * y.x), fmaf(sn, x.y, c * y.y), fmaf(sn, x.z, c * y.z),
+                          fmaf(sn, x.w, c * y.w));
+    }
+    float *cp = Q + qi * qld, *cq = Q + qj * qld;
+    for (int r = lane; r < qd; r += 32) {
+      const float x = cp[r], y = cq[r];
+      cp[r] = c * x - sn * y;
+      cq[r] = fmaf(sn, x, c * y);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      na[i] = fmaxf(a - t * g, 0.f);
+      nb_[j] = fmaxf(b + t * g, 0.f);
+    }
+    __syncwarp();
+    rmax = fmaxf(rmax, ratio);
+    return true;
+  };
+  // the intra-block pairs of one block in shared memory (round robin)
+  auto inner = [&](float *sb, float *nv_, int nv, int q0, bool &any, float &rmax) {
+    const int bp = bw + (bw & 1), half = bp / 2, bm = bp - 1;
+    for (int sr = 0; sr < bm; ++sr) {
+      for (int i = warp; i < half; i += nw) {
+        int p = 0, q;
+        if (i != 0) {
+          p = i - 1 + sr;
+          p = 1 + (p >= bm ? p - bm : p);
+        }
+        q = bp - 2 - i + sr;
+        q = 1 + (q >= bm ? q - bm : q);
+        if (p < nv && q < nv) any |= pair(sb, nv_, p, sb, nv_, q, q0 + p, q0 + q, rmax);
+      }
+      __syncthreads();
+    }
+  };
+  bool converged = false;
+  int sweep = 0;
+  for (; sweep < 15 && !converged; ++sweep) {
+    if (threadIdx.x == 0) {
+      local_changed = 0;
+      sweep_rmax = 0;
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      flag = 0;
+      cl_rmax = 0;
+    }
+    cluster.sync();
+    bool any = false;
+    float rmax = 0.f;
+    for (int rnd = 0; rnd < P - 1; ++rnd) {
+      for (int v = 0; v < k; ++v) {
+        const int pi = crank + C * v;  // this visit's pair of positions (pi, P - 1 - pi)
+        const int b0 = bj_block_at(pi, rnd, P), b1 = bj_block_at(P - 1 - pi, rnd, P);
+        const int nv0 = valid(b0), nv1 = valid(b1);
+        if (nv0 == 0 && nv1 == 0) continue;  // uniform over the CTA
+        // load both blocks (rows >= nr and columns >= nv zero), Q = I
+        for (int e = threadIdx.x; e < bw * ldb; e += blockDim.x) {
+          const int j = e / ldb, r = e - j * ldb;
+          S0[e] = (j < nv0 && r < nr) ? __ldcg(B32 + (int64_t)(b0 * bw + j) * nr + r) : 0.0f;
+          S1[e] = (j < nv1 && r < nr) ? __ldcg(B32 + (int64_t)(b1 * bw + j) * nr + r) : 0.0f;
+        }
+        for (int e = threadIdx.x; e < qld * qd; e += blockDim.x) Q[e] = (e / qld == e % qld) ? 1.0f : 0.0f;
+        __syncthreads();
+        for (int j = warp; j < 2 * bw; j += nw) {  // squared column norms
+          const float4 *x = reinterpret_cast<const float4 *>((j < bw ? S0 : S1) + (j < bw ? j : j - bw) * ldb);
+          float a = 0.f;
+          for (int r = lane; r < l4; r += 32) {
+            const float4 u = x[r];
+            a = fmaf(u.x, u.x, a);
+            a = fmaf(u.y, u.y, a);
+            a = fmaf(u.z, u.z, a);
+            a = fmaf(u.w, u.w, a);
+          }
+          a = wsumf(a);
+          if (lane == 0) (j < bw ? N0 : N1)[j < bw ? j : j - bw] = a;
+        }
+        __syncthreads();
+        if (rnd == 0) {
+          inner(S0, N0, nv0, 0, any, rmax);
+          inner(S1, N1, nv1, bw, any, rmax);
+        }
+        for (int sr = 0; sr < bw; ++sr) {
+          for (int i = warp; i < bw; i += nw) {
+            int j = i + sr;
+            if (j >= bw) j -= bw;
+            if (i < nv0 && j < nv1) any |= pair(S0, N0, i, S1, N1, j, i, bw + j, rmax);
+          }
+          __syncthreads();
+        }
+        // blocks back; V's columns of the two blocks times Q, one row per
+        // thread (x[r]: V's entry in the column of Q's row r)
+        for (int e = threadIdx.x; e < bw * ldb; e += blockDim.x) {
+          const int j = e / ldb, r = e - j * ldb;
+          if (r < nr) {
+            if (j < nv0) B32[(int64_t)(b0 * bw + j) * nr + r] = S0[e];
+            if (j < nv1) B32[(int64_t)(b1 * bw + j) * nr + r] = S1[e];
+          }
+        }
+        for (int row = threadIdx.x; row < n; row += blockDim.x) {
+          float x[2 * JS_BW_MAX];
+#pragma unroll
+          for (int r = 0; r < 2 * JS_BW_MAX; ++r) {
+            const bool first = r < bw;
+            const int lc = first ? r : r - bw, nv = first ? nv0 : nv1, bb = first ? b0 : b1;
+            x[r] = (r < qd && lc < nv) ? __ldcg(V32 + (int64_t)(bb * bw + lc) * n + row) : 0.0f;
+          }
+#pragma unroll 1
+          for (int oc = 0; oc < qd; ++oc) {
+            const bool first = oc < bw;
+            const int lo = first ? oc : oc - bw, nv = first ? nv0 : nv1, bb = first ? b0 : b1;
+            if (lo >= nv) continue;
+            const float4 *qc = reinterpret_cast<const float4 *>(Q + oc * qld);
+            float acc = 0.f;
+#pragma unroll
+            for (int r4 = 0; r4 < (2 * JS_BW_MAX) / 4; ++r4)
+              if (4 * r4 < qd) {
+                const float4 w = qc[r4];
+                acc = fmaf(x[4 * r4], w.x, acc);
+                acc = fmaf(x[4 * r4 + 1], w.y, acc);
+                acc = fmaf(x[4 * r4 + 2], w.z, acc);
+                acc = fmaf(x[4 * r4 + 3], w.w, acc);
+              }
+            V32[(int64_t)(bb * bw + lo) * n + row] = acc;
+          }
+        }
+        __syncthreads();
+      }
+      cluster.sync();  // this round's blocks and V columns are written before the next round reads them
+    }
+    if (any && lane == 0) local_changed = 1;
+    if (lane == 0) atomicMax(&sweep_rmax, __float_as_int(rmax));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (local_changed) atomicOr(flag0, 1);
+      atomicMax(rmax0, sweep_rmax);
+    }
+    cluster.sync();
+    const float r = __int_as_float(*rmax0);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    cluster.sync();
+  }
+  if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
+  // rotations to V (FP64, leading dimension nr) over the identity already there
+  for (int64_t e = e0; e < (int64_t)n * n; e += stride) {
+    const int64_t j = e / n, i = e - j * n;
+    Vg[j * nr + i] = (double)__ldcg(V32 + e);
   }
 }
 
@@ -2252,8 +2503,24 @@ static cudaError_t launch_block32_clusters(const SvdJob *jobs, const int *order,
   return cudaLaunchKernelEx(&cfg, jacobi32_block_kernel, jobs, order, work, iwork);
 }
 
+// shared memory of jacobi32_big_kernel for sectors of up to `cols` columns,
+// and whether such sectors fit it
+static size_t big32_smem(int cols) {
+  const int64_t bw = (cols + 31) / 32, ld = 32 * (((int64_t)cols + 31) / 32);
+  return (size_t)(4 * ((bw * ld + 3) & ~(int64_t)3) * sizeof(float));
+}
+static bool big32_fits(int cols) {
+  return 32 * (((int64_t)cols + 31) / 32) <= 32 * J32B_REG && big32_smem(cols) <= SVD_BLOCK_SMEM_MAX;
+}
+
+int svd_jacobi32_big_max_cols() {
+  int c = 32 * J32B_REG;
+  while (c > 0 && !big32_fits(c)) --c;
+  return c;
+}
+
 cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                                int cols0, double *work, const int *iwork, cudaStream_t st,
+                                int cols0, int g0b, int cols0b, double *work, const int *iwork, cudaStream_t st,
                                 const cudaStream_t *side, const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
   cudaFuncSetAttribute(jacobi32_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -2273,21 +2540,63 @@ cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs,
     e = cudaEventRecord(ev[k - 1], side[k - 2]);
     if (e != cudaSuccess) return e;
   }
-  if (hi[0] > lo[0]) {  // beyond the block kernels
-    // B's columns in shared memory, the rotations in global memory, when
-    // 16-CTA clusters are available and the columns fit; else all in
-    // global memory
-    const int64_t bw0 = (cols0 + 31) / 32, ld0 = 32 * (((int64_t)cols0 + 31) / 32);
-    const size_t smem0 = (size_t)(4 * ((bw0 * ld0 + 3) & ~(int64_t)3) * sizeof(float));
-    e = cudaErrorInvalidValue;
-    if (ld0 <= 32 * J32B_REG && smem0 <= SVD_BLOCK_SMEM_MAX) {
+  // beyond the block kernels (jobs 0 .. g[0], largest first): the jobs from
+  // g0b on (at most cols0b columns) on jacobi32_big_kernel (B's columns in
+  // shared memory, the rotations in global memory) on side stream 3,
+  // concurrently with the larger ones on the all-global kernel; every job
+  // on the all-global kernel if 16-CTA clusters or the shared memory are
+  // not available
+  bool big_on_side = false;
+  int nglob = hi[0];
+  if (hi[0] > lo[0]) {
+    const int split = g0b < 0 ? 0 : (g0b > hi[0] ? hi[0] : g0b);
+    const int bcols = split == 0 ? cols0 : cols0b;
+    if (split < hi[0] && big32_fits(bcols)) {
+      const size_t smem0 = big32_smem(bcols);
       cudaFuncSetAttribute(jacobi32_big_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       e = cudaFuncSetAttribute(jacobi32_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(side[3], ev[0], 0);
       if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(hi[0] * 16, 1, 1);
+        cfg.gridDim = dim3((hi[0] - split) * 16, 1, 1);
         cfg.blockDim = dim3(BJ_THREADS, 1, 1);
         cfg.dynamicSmemBytes = smem0;
+        cfg.stream = side[3];
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, jacobi32_big_kernel, jobs, order + split, work, iwork);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev[4], side[3]);
+      if (e == cudaSuccess) {
+        big_on_side = true;
+        nglob = split;
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
+  if (nglob > 0) {
+    // the block tournament streamed through shared memory; the all-global
+    // pair kernel if that launch is not possible
+    const int ldb0 = 32 * ((cols0 + 31) / 32);
+    const int64_t budget = 200 * 1024 / (int)sizeof(float);
+    int bw_cap = JS_BW_MAX;
+    while (bw_cap >= 1 && js_smem_floats(bw_cap, ldb0) > budget) --bw_cap;
+    e = cudaErrorInvalidValue;
+    if (bw_cap >= 1) {
+      const size_t smem = (size_t)js_smem_floats(bw_cap, ldb0) * sizeof(float);
+      cudaFuncSetAttribute(jacobi32_stream_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = cudaFuncSetAttribute(jacobi32_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nglob * 16, 1, 1);
+        cfg.blockDim = dim3(JS_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -2296,16 +2605,16 @@ cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs,
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, jacobi32_big_kernel, jobs, order, work, iwork);
+        e = cudaLaunchKernelEx(&cfg, jacobi32_stream_kernel, jobs, order, work, iwork, bw_cap, ldb0);
       }
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
       cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      e = launch_jacobi32_clusters(jobs, order, hi[0], 16, work, iwork, st);
+      e = launch_jacobi32_clusters(jobs, order, nglob, 16, work, iwork, st);
       if (e != cudaSuccess) {
         cudaGetLastError();
-        e = launch_jacobi32_clusters(jobs, order, hi[0], 8, work, iwork, st);
+        e = launch_jacobi32_clusters(jobs, order, nglob, 8, work, iwork, st);
       }
     }
     if (e != cudaSuccess) return e;
@@ -2317,6 +2626,10 @@ cudaError_t launch_svd_jacobi32(const SvdJob *jobs, const int *order, int njobs,
   for (int k = 2; k < 5; ++k) {
     if (hi[k] <= lo[k]) continue;
     e = cudaStreamWaitEvent(st, ev[k - 1], 0);
+    if (e != cudaSuccess) return e;
+  }
+  if (big_on_side) {
+    e = cudaStreamWaitEvent(st, ev[4], 0);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();

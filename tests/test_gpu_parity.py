@@ -57,11 +57,11 @@ def test_full_iteration_parity(name, bonds, ell, m, steps, prec):
 
 
 def test_large_sector_svd_path():
-    """The kernels for sector matrices beyond 320 columns (pivoted QR on a
-    cluster with the columns in global memory, FP32 and FP64 cyclic Jacobi
-    in global memory, the FP64 stage started from the
-    Newton-Schulz-orthogonalised FP32 rotations), forced on a small problem,
-    against the oracle."""
+    """The kernels for sector matrices beyond the shared-memory ones (pivoted
+    QR on a cluster with the columns in global memory, the FP32 block
+    tournament streamed through shared memory, the FP64 cyclic Jacobi in
+    global memory started from the Newton-Schulz-orthogonalised FP32
+    rotations), forced on a small problem, against the oracle."""
     mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 1606), 8)
     ctx = context(mpo, 48)
     ctx.set_svd_path(True)
