@@ -134,6 +134,25 @@ void idmrg_default_opts(idmrg_opts *opts);
  * later call is ordered.  alloc may be NULL (cudaMalloc/cudaFree). */
 idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cuda_stream,
                           const idmrg_allocator *alloc, idmrg_ctx **out);
+
+/* One context over nmpo independent problems (e.g. disorder realisations
+ * of Sec. 3's random-bond chains), all with the same local basis (d and
+ * phys_charge) but each with its own unit cell length l_r, couplings, and
+ * kept states m_per[r] (NULL: opts->m for all).  The problems are "rings":
+ * superblock q of problem r is superblock p0_r + q of the context, p0_r =
+ * sum_{r' < r} l_r'/2, and its pairs close on themselves (Step 2': the
+ * ring's last pair takes its right block from the ring's first).  Every
+ * call covers the superblocks of all problems, so each kernel launch (and
+ * each CUDA graph of a Lanczos iteration) serves all of them together;
+ * start vectors are drawn per problem exactly as in a context of its own.
+ * Step reports list every superblock in this order; their e_g is problem
+ * 0's, idmrg_ring_energy reads any problem's.  opts->m becomes the largest
+ * m.  Checkpoints, observables, pair ranges, idmrg_run and
+ * idmrg_truncation_error need a context of one problem (EINVAL).  EINVAL
+ * for nmpo < 1, a differing d or phys_charge, or an m_per below 1; each MPO
+ * is checked as by idmrg_create. */
+idmrg_status idmrg_create_batch(const idmrg_mpo *mpos, int nmpo, const int *m_per, const idmrg_opts *opts,
+                                void *cuda_stream, const idmrg_allocator *alloc, idmrg_ctx **out);
 void idmrg_destroy(idmrg_ctx *ctx);
 const char *idmrg_last_error(const idmrg_ctx *ctx);
 idmrg_status idmrg_set_stream(idmrg_ctx *ctx, void *cuda_stream);
@@ -334,6 +353,10 @@ idmrg_status idmrg_fit_correlation_length(const double *r, const double *c, int 
 /* Step 5': latest e_g = (e^(n)_1 - e^(n-l)_1) / 2l with (n+1) mod l == 0
  * (e^(-1)_1 = 0) and the n it belongs to; ESTATE if there is none yet. */
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *ctx, double *e_g, int *n_of_estimate);
+
+/* The same for problem r of a context made by idmrg_create_batch (its own
+ * unit cell length l_r); EINVAL for r outside the problems. */
+idmrg_status idmrg_ring_energy(const idmrg_ctx *ctx, int r, double *e_g, int *n_of_estimate);
 
 /* Checkpoint between unit-cell steps (Step 7): the iteration n, the history
  * of e^(n)_1 behind Step 5', every pair's current environments (Step 6) and

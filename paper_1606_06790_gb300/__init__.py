@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
-    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_svd_phase_ms", "idmrg_svd_sweeps32", "idmrg_save", "idmrg_load",
+    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_create_batch", "idmrg_ring_energy", "idmrg_svd_phase_ms", "idmrg_svd_sweeps32", "idmrg_save", "idmrg_load",
     "idmrg_correlation", "idmrg_transfer_spectrum", "idmrg_delta_pm", "idmrg_extrapolate",
     "idmrg_fit_correlation_length", "idmrg_set_pair_range", "idmrg_export_pair", "idmrg_import_pair",
 ]
@@ -126,6 +126,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_set_svd_path": (i, [vp, i]),
         "idmrg_gemm_tuning": (i, [vp, i, P(i), P(C.c_float), P(i)]),
         "idmrg_set_gemm_tile": (i, [vp, i, i]),
+        "idmrg_create_batch": (i, [P(_MPO), i, P(i), P(_Opts), vp, P(_Allocator), P(vp)]),
+        "idmrg_ring_energy": (i, [vp, i, P(d), P(i)]),
         "idmrg_svd_phase_ms": (i, [vp, P(d)]),
         "idmrg_svd_sweeps32": (i, [vp, P(i), P(d)]),
         "idmrg_correlation": (i, [vp, i, P(d), P(d), P(d), i, P(C.c_int64), P(C.c_int64), P(d)]),
@@ -185,26 +187,54 @@ class Context:
                  prec: str = "fp64", lanczos_tol: float = 1e-12, lanczos_maxit: int = 300,
                  predict: bool = True, seed: int = 0, lambda_zero_rel: float = 1e-12,
                  tie_rel: float = 1e-7, target_charge: int = 0, stream=None):
+        self._create([(W, phys_charge, bond_charge)], [m], prec, lanczos_tol, lanczos_maxit, predict, seed,
+                     lambda_zero_rel, tie_rel, target_charge, stream)
+
+    @classmethod
+    def batch(cls, problems, m, **kw) -> "Context":
+        """One context over several independent problems (idmrg_create_batch):
+        ``problems`` a list of (W, phys_charge, bond_charge) with the same
+        local basis, ``m`` one int or one per problem.  Superblocks are
+        numbered problem after problem (``rings``: first superblock and count
+        of each); every call steps all of them together."""
+        self = cls.__new__(cls)
+        ms = list(m) if hasattr(m, "__len__") else [int(m)] * len(problems)
+        self._create(list(problems), ms, **kw)
+        return self
+
+    def _create(self, problems, ms, prec: str = "fp64", lanczos_tol: float = 1e-12, lanczos_maxit: int = 300,
+                predict: bool = True, seed: int = 0, lambda_zero_rel: float = 1e-12, tie_rel: float = 1e-7,
+                target_charge: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        if len(problems) < 1 or len(ms) != len(problems):
+            raise ValueError("one m per problem")
         self._torch = torch
         self.lib = load_library()
-        self.ell = len(W)
-        self.P = self.ell // 2
-        self.d = int(np.asarray(W[0]).shape[2])
+        self.ell = len(problems[0][0])
+        self.d = int(np.asarray(problems[0][0][0]).shape[2])
         self.device = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        dims = np.array([w.shape[0] for w in W] + [W[0].shape[0]], dtype=np.int32)
-        self._W = np.ascontiguousarray(np.concatenate([np.asarray(w, dtype=np.float64).ravel() for w in W]))
-        self._dims = dims
-        self._qp = np.ascontiguousarray(np.asarray(phys_charge, dtype=np.int32))
-        self._bq = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.int32) for b in bond_charge]))
-        mpo = _MPO(self.ell, self.d, _dptr(dims, C.c_int), _dptr(self._W, C.c_double),
-                   _dptr(self._qp, C.c_int), _dptr(self._bq, C.c_int))
+        self._keep = []
+        mpos = (_MPO * len(problems))()
+        self.rings, p0 = [], 0
+        for r, (W, phys_charge, bond_charge) in enumerate(problems):
+            dims = np.array([w.shape[0] for w in W] + [W[0].shape[0]], dtype=np.int32)
+            Wf = np.ascontiguousarray(np.concatenate([np.asarray(w, dtype=np.float64).ravel() for w in W]))
+            qp = np.ascontiguousarray(np.asarray(phys_charge, dtype=np.int32))
+            bq = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.int32) for b in bond_charge]))
+            self._keep += [dims, Wf, qp, bq]
+            mpos[r] = _MPO(len(W), int(np.asarray(W[0]).shape[2]), _dptr(dims, C.c_int), _dptr(Wf, C.c_double),
+                           _dptr(qp, C.c_int), _dptr(bq, C.c_int))
+            self.rings.append((p0, len(W) // 2))
+            p0 += len(W) // 2
+        self.P = p0
+        self._qp = self._keep[2]
+        self._ms = np.ascontiguousarray(np.asarray(ms, dtype=np.int32))
         o = _Opts()
         self.lib.idmrg_default_opts(C.byref(o))
-        o.m, o.target_charge, o.lanczos_tol, o.lanczos_maxit = m, target_charge, lanczos_tol, lanczos_maxit
+        o.m, o.target_charge, o.lanczos_tol, o.lanczos_maxit = int(max(ms)), target_charge, lanczos_tol, lanczos_maxit
         o.prec, o.predict, o.seed = PREC[prec], int(bool(predict)), seed
         o.lambda_zero_rel, o.tie_rel = lambda_zero_rel, tie_rel
         self.opts = o
@@ -227,11 +257,21 @@ class Context:
         self._cb = (_ALLOC(_alloc), _FREE(_free))
         self._alloc = _Allocator(self._cb[0], self._cb[1], None)
         h = C.c_void_p()
-        s = self.lib.idmrg_create(C.byref(mpo), C.byref(o), C.c_void_p(self.stream.cuda_stream),
-                                  C.byref(self._alloc), C.byref(h))
+        if len(problems) == 1:
+            s = self.lib.idmrg_create(C.byref(mpos[0]), C.byref(o), C.c_void_p(self.stream.cuda_stream),
+                                      C.byref(self._alloc), C.byref(h))
+        else:
+            s = self.lib.idmrg_create_batch(mpos, len(problems), _dptr(self._ms, C.c_int), C.byref(o),
+                                            C.c_void_p(self.stream.cuda_stream), C.byref(self._alloc), C.byref(h))
         if s != 0:
             raise IdmrgError(s, "idmrg_create failed (invalid MPO or options, or no device memory)")
         self.h = h
+
+    def ring_energy(self, r: int):
+        """Problem r's latest Step 5' estimate (e_g, n), or None before the first."""
+        e, n = C.c_double(), C.c_int()
+        s = self._check(self.lib.idmrg_ring_energy(self.h, int(r), C.byref(e), C.byref(n)), "ring_energy", ok=(0, 7))
+        return None if s != 0 else (e.value, n.value)
 
     # ------------------------------------------------------------ helpers
     def _check(self, s: int, what: str, ok=(0,)):

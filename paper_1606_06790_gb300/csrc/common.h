@@ -251,7 +251,7 @@ struct SelectOut {
   int *kept;           // [S]
 };
 cudaError_t launch_svd_select(const SvdJob *jobs, const int *sb_job0, const int *sb_njob, int S, const double *sv,
-                              int m, double zero_rel, double tie_rel, SelectOut out, int max_entries,
+                              const int *m_sb, double zero_rel, double tie_rel, SelectOut out, int max_entries,
                               cudaStream_t st);
 struct CompactJob {
   int job;             // SvdJob index

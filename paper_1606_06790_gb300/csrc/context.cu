@@ -164,12 +164,29 @@ struct ObsState {
 };
 
 struct idmrg_ctx {
-  // problem
+  // problem: one or more independent unit cells ("rings": a problem each,
+  // e.g. disorder realisations), numbered ring after ring: ring r has
+  // rings[r].ell sites from site (and bond) rings[r].s0 on and ell/2
+  // superblocks from rings[r].p0 on, whose pairs close on themselves (the
+  // ring's last pair takes its right block from its first).  ell is ring
+  // 0's unit cell, P the superblocks of all rings.
   int ell = 0, d = 0, P = 0;
-  std::vector<int> adim;                 // a_k, k = 0..ell
+  struct Ring {
+    int p0 = 0, np = 0;  // first superblock, superblocks
+    int s0 = 0, ell = 0; // first site, sites
+    int m = 0;           // kept states
+    std::map<int, double> e1;   // e^(n)_1 of the ring's first superblock (Step 5')
+    std::map<int, double> eps1; // eps^(n)_1 (Eq. tru), for the truncation error of a run
+    double eg_last = NAN;
+    int eg_n = -1;
+  };
+  std::vector<Ring> rings;
+  std::vector<int> ring_of, ring_of_site;  // per superblock, per site
+  std::vector<int> adim;                 // a_k per bond k (left of site k), every ring's sites
   std::vector<std::vector<double>> W;    // per site [a_k][a_k+1][d][d]
   std::vector<int> qp;                   // phys charges
   std::vector<std::vector<int>> bq;      // per bond k (left of site k) channel charges
+  DevBuf dmsb;                           // kept states of every superblock (its ring's m)
   idmrg_opts o{};
   cudaStream_t st = nullptr;
   // side streams of the SVD (small Jacobi groups run beside the large one),
@@ -200,10 +217,6 @@ struct idmrg_ctx {
   std::vector<int> stage;
   std::vector<Env> envL, envR, newL, newR;
   std::vector<TruncRec> cur, prev, prev2;
-  std::map<int, double> e1;   // e^(n)_1
-  std::map<int, double> eps1; // eps^(n)_1 (Eq. tru), for the truncation error of a run
-  double eg_last = NAN;
-  int eg_n = -1;
   std::vector<double> energy, fidelity, bond, startnorm;
   std::vector<int> iters, conv;
 
@@ -415,11 +428,27 @@ struct idmrg_ctx {
   }
   double *dp(DevBuf &b) { return (double *)b.p; }
 
+  // the bond right of site s (the ring's first bond after its last site)
+  int bond_right(int s) const {
+    const Ring &R = rings[ring_of_site[s]];
+    return s + 1 < R.s0 + R.ell ? s + 1 : R.s0;
+  }
+  // the pair after superblock p in its ring (Step 2': p takes its right block)
+  int nxt(int p) const {
+    const Ring &R = rings[ring_of[p]];
+    return p + 1 < R.p0 + R.np ? p + 1 : R.p0;
+  }
+  // site of superblock p at iteration n: the ring's site 2 (p - p0) + n + off (mod its ell)
+  int site_at(int p, int off) const {
+    const Ring &R = rings[ring_of[p]];
+    const int k = 2 * (p - R.p0) + n + off;
+    return R.s0 + ((k % R.ell) + R.ell) % R.ell;
+  }
+  bool one_ring() const { return rings.size() == 1; }
   const double &Wat(int site, int a, int b, int s, int t) const {
-    const int B = adim[site + 1];
+    const int B = adim[bond_right(site)];
     return W[site][(((size_t)a * B + b) * d + s) * d + t];
   }
-  int site_of(int k) const { return ((k % ell) + ell) % ell; }
 };
 
 namespace {
@@ -663,14 +692,14 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
   for (int p = 0; p < P; ++p) {
     if (!c->owns(p)) continue;  // another worker's superblock
     SBPlan &S = c->plan[p];
-    S.c1 = c->site_of(2 * p + c->n);
-    S.c2 = c->site_of(2 * p + c->n + 1);
+    S.c1 = c->site_at(p, 0);
+    S.c2 = c->site_at(p, 1);
     const Env &L = c->envL[p];
-    const Env &R = c->envR[(p + 1) % P];
+    const Env &R = c->envR[c->nxt(p)];
     const Basis &BL = L.lay.b, &BR = R.lay.b;
     S.psi.build(BL, BR, c->qp, target);
     const PsiLayout &psi = S.psi;
-    const int wa = c->adim[S.c1], wb = c->adim[S.c1 + 1], wc = c->adim[S.c2 + 1];
+    const int wa = c->adim[S.c1], wb = c->adim[c->bond_right(S.c1)], wc = c->adim[c->bond_right(S.c2)];
     if (wb != c->adim[S.c2] || wa != L.lay.w || wc != R.lay.w)
       return c->fail(IDMRG_EINVAL, "MPO bond dimensions do not chain at superblock %d", p);
     // two-site MPO W12[a][c][(s,t)][(s',t')] = sum_b W_c1(a,b) W_c2(b,c)
@@ -805,7 +834,8 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
           c->dterm_sb.push_back(p);
         }
     // ---- random start blocks (Step 3, n = 1, 2)
-    const uint64_t sstate = sm64_at(state0, (uint64_t)(1024 * (int64_t)c->n + p));
+    // ring-local index: a problem draws the same start as in a context of its own
+    const uint64_t sstate = sm64_at(state0, (uint64_t)(1024 * (int64_t)c->n + (p - c->rings[c->ring_of[p]].p0)));
     for (int i = 0; i < SL; ++i)
       for (int s = 0; s < d; ++s)
         for (int t = 0; t < d; ++t) {
@@ -843,7 +873,7 @@ idmrg_status plan_iteration(idmrg_ctx *c) {
     NOMEM(c->ensure(c->bPsi[p], 8 * std::max<int64_t>(S.psi.N, 1)));
     NOMEM(c->ensure(c->bW[p], 8 * std::max<int64_t>(S.psi.N, 1)));
     c->hbufs[p * NBUF + BUF_L] = c->dp(c->envL[p].data);
-    c->hbufs[p * NBUF + BUF_R] = c->dp(c->envR[(p + 1) % P].data);
+    c->hbufs[p * NBUF + BUF_R] = c->dp(c->envR[c->nxt(p)].data);
     c->hbufs[p * NBUF + BUF_T1] = c->dp(c->bT1[p]);
     c->hbufs[p * NBUF + BUF_T3] = c->dp(c->bT3[p]);
     c->hbufs[p * NBUF + BUF_PSI] = c->dp(c->bPsi[p]);
@@ -985,7 +1015,7 @@ idmrg_status plan_mixed(idmrg_ctx *c) {
     if (!c->owns(p)) continue;
     SBPlan &S = c->plan[p];
     const Env &L = c->envL[p];
-    const Env &R = c->envR[(p + 1) % P];
+    const Env &R = c->envR[c->nxt(p)];
     const Basis &BL = L.lay.b, &BR = R.lay.b;
     const PsiLayout &psi = S.psi;
     const int SL = BL.S(), SR = BR.S();
@@ -1287,7 +1317,7 @@ idmrg_status plan_oz(idmrg_ctx *c) {
     if (!c->owns(p)) continue;
     SBPlan &S = c->plan[p];
     const Env &L = c->envL[p];
-    const Env &R = c->envR[(p + 1) % P];
+    const Env &R = c->envR[c->nxt(p)];
     const Basis &BL = L.lay.b, &BR = R.lay.b;
     const PsiLayout &psi = S.psi;
     const int SL = BL.S(), SR = BR.S();
@@ -1674,7 +1704,7 @@ idmrg_status predict(idmrg_ctx *c, int p) {
     c->gp.clear();
     for (int q = 0; q < P; ++q) {
       if (!want(c, p, q)) continue;
-      const int q1 = (q + 1) % P;
+      const int q1 = c->nxt(q);
       const TruncRec &A = c->prev[q], &B = c->prev[q1], &B2 = c->prev2[q1];
       if (!A.valid || !B.valid || !B2.valid) return c->fail(IDMRG_ESTATE, "prediction needs two earlier iterations");
       NOMEM(c->ensure(c->bVT[q], 8 * std::max<int64_t>(A.vsize, 1)));
@@ -2074,7 +2104,7 @@ idmrg_status trunc_plan(idmrg_ctx *c, int p) {
     c->tjob0[q] = (int)c->jobs.size();
     if (!want(c, p, q)) continue;
     const Env &L = c->envL[q];
-    const Env &R = c->envR[(q + 1) % P];
+    const Env &R = c->envR[c->nxt(q)];
     const Basis &BL = L.lay.b, &BR = R.lay.b;
     const PsiLayout &psi = c->plan[q].psi;
     std::vector<int> Qs;
@@ -2257,7 +2287,7 @@ idmrg_status trunc_host(idmrg_ctx *c, int q, const int *kpj, const double *lam, 
   }
   T.valid = true;
   T.leftB = c->envL[q].lay.b;
-  T.rightB = c->envR[(q + 1) % P].lay.b;
+  T.rightB = c->envR[c->nxt(q)].lay.b;
   T.eps = eps[q];
   T.eps_best = epsb[q];
   int lam_off = 0;
@@ -2403,7 +2433,8 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
     if (want(c, p, q)) sbl.push_back(q);
   c->kbegin(PH + 4);
   CK(launch_svd_select((const SvdJob *)c->sjobs.p, (const int *)c->sjob0.p, (const int *)c->snjob.p, P,
-                       c->dp(c->ssv), c->o.m, c->o.lambda_zero_rel, c->o.tie_rel, select_out(c, 0), c->tentries_max,
+                       c->dp(c->ssv), (const int *)c->dmsb.p, c->o.lambda_zero_rel, c->o.tie_rel, select_out(c, 0),
+                       c->tentries_max,
                        c->st));
   c->kend(PH + 4);
   c->kend(IDMRG_K_SVD, svd_flops(c, -1), 0.0);
@@ -2454,11 +2485,11 @@ idmrg_status env_build(idmrg_ctx *c, int q, GemmList &g1, GemmList &g3, WList &w
   const int P = c->P, d = c->d, target = c->o.target_charge;
   const SBPlan &S = c->plan[q];
   const Env &L = c->envL[q];
-  const Env &R = c->envR[(q + 1) % P];
+  const Env &R = c->envR[c->nxt(q)];
   const Basis &BL = L.lay.b, &BR = R.lay.b;
   const TruncRec &T = c->cur[q];
   const int SL = BL.S(), SR = BR.S();
-  const int wa = L.lay.w, wb = c->adim[S.c1 + 1], wc = R.lay.w;
+  const int wa = L.lay.w, wb = c->adim[c->bond_right(S.c1)], wc = R.lay.w;
   std::map<int, int> secQ;
   for (int k = 0; k < (int)T.sec.size(); ++k) secQ[T.sec[k].Q] = k;
   auto sec_of = [&](int Q) { auto it = secQ.find(Q); return it == secQ.end() ? -1 : it->second; };
@@ -2485,7 +2516,7 @@ idmrg_status env_build(idmrg_ctx *c, int q, GemmList &g1, GemmList &g3, WList &w
       }
     }
   // Y[b](so, s) = sum_{a,s'} W_c1(a,b,s,s') X[a](so,s')
-  std::vector<int> bchq(c->bq[(S.c1 + 1) % c->ell]);
+  std::vector<int> bchq(c->bq[c->bond_right(S.c1)]);
   for (int b = 0; b < wb; ++b)
     for (int so = 0; so < SL; ++so)
       for (int s = 0; s < d; ++s) {
@@ -2652,13 +2683,14 @@ idmrg_status advance(idmrg_ctx *c) {
     std::swap(c->prev2[q], c->prev[q]);
     std::swap(c->prev[q], c->cur[q]);
   }
-  if (c->owns(0)) {  // Step 5' (superblock 1 of the paper)
-    c->eps1[c->n] = c->prev[0].eps;
-    c->e1[c->n] = c->energy[0];
-    if ((c->n + 1) % c->ell == 0) {
-      const double before = (c->n - c->ell == -1) ? 0.0 : c->e1[c->n - c->ell];
-      c->eg_last = (c->e1[c->n] - before) / (2.0 * c->ell);
-      c->eg_n = c->n;
+  for (idmrg_ctx::Ring &R : c->rings) {
+    if (!c->owns(R.p0)) continue;  // Step 5' (superblock 1 of the paper) of each ring
+    R.eps1[c->n] = c->prev[R.p0].eps;
+    R.e1[c->n] = c->energy[R.p0];
+    if ((c->n + 1) % R.ell == 0) {
+      const double before = (c->n - R.ell == -1) ? 0.0 : R.e1[c->n - R.ell];
+      R.eg_last = (R.e1[c->n] - before) / (2.0 * R.ell);
+      R.eg_n = c->n;
     }
   }
   c->n += 1;
@@ -2809,11 +2841,11 @@ idmrg_status obs_build(idmrg_ctx *c) {
   S.bb.assign(ell + 1, {});
   S.blk.assign(ell, {});
   for (int p = 0; p < P; ++p) {
-    const TruncRec &A = c->prev[p], &B = c->prev[(p + 1) % P];
+    const TruncRec &A = c->prev[p], &B = c->prev[c->nxt(p)];
     if (A.rightB.D != B.leftB.D || A.rightB.dim != B.leftB.dim)
-      return c->fail(IDMRG_ESTATE, "observables: bases of superblocks %d and %d do not meet", p, (p + 1) % P);
-    if ((int)c->prev2[(p + 1) % P].lam.size() != B.leftB.D)
-      return c->fail(IDMRG_ESTATE, "observables: lambda^(n-1) of superblock %d has the wrong length", (p + 1) % P);
+      return c->fail(IDMRG_ESTATE, "observables: bases of superblocks %d and %d do not meet", p, c->nxt(p));
+    if ((int)c->prev2[c->nxt(p)].lam.size() != B.leftB.D)
+      return c->fail(IDMRG_ESTATE, "observables: lambda^(n-1) of superblock %d has the wrong length", c->nxt(p));
     for (const SecInfo &s : A.sec) S.bb[2 * p].push_back({s.lam_off, s.k});
     for (int j = 0; j < (int)A.rightB.dim.size(); ++j) S.bb[2 * p + 1].push_back({A.rightB.off[j], A.rightB.dim[j]});
     S.D[2 * p] = (int)A.lam.size();
@@ -2867,7 +2899,7 @@ idmrg_status obs_build(idmrg_ctx *c) {
   int max_rows = 0;
   double *Abase = (double *)S.A.p;
   for (int p = 0; p < P; ++p) {
-    const int q = (p + 1) % P;
+    const int q = c->nxt(p);
     const TruncRec &A = c->prev[p], &B = c->prev[q], &B2 = c->prev2[q];
     {
       const int k = 2 * p, D1 = S.D[k + 1];
@@ -3412,12 +3444,16 @@ void idmrg_default_opts(idmrg_opts *o) {
 
 idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cuda_stream,
                           const idmrg_allocator *alloc, idmrg_ctx **out) {
-  if (!mpo || !opts || !out) return IDMRG_EINVAL;
+  return idmrg_create_batch(mpo, 1, nullptr, opts, cuda_stream, alloc, out);
+}
+
+idmrg_status idmrg_create_batch(const idmrg_mpo *mpos, int nmpo, const int *m_per, const idmrg_opts *opts,
+                                void *cuda_stream, const idmrg_allocator *alloc, idmrg_ctx **out) {
+  if (!mpos || nmpo < 1 || !opts || !out) return IDMRG_EINVAL;
   *out = nullptr;
   idmrg_ctx *c = new idmrg_ctx();
   auto bail = [&](idmrg_status s) {
-    // keep the context so the caller can read the message? the ABI returns no
-    // context on failure: print nothing, free everything
+    // the ABI returns no context on failure: free everything
     idmrg_destroy(c);
     return s;
   };
@@ -3427,9 +3463,16 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
     c->alloc = *alloc;
     c->own_alloc = false;
   }
-  const int ell = mpo->ell, d = mpo->d;
-  if (ell < 2 || ell % 2 || d < 1 || d > 4 || !mpo->bond_dim || !mpo->W || !mpo->phys_charge || !mpo->bond_charge)
-    return bail(IDMRG_EINVAL);
+  const int d = mpos[0].d;
+  if (d < 1 || d > 4 || !mpos[0].phys_charge) return bail(IDMRG_EINVAL);
+  for (int r = 0; r < nmpo; ++r) {
+    const idmrg_mpo &M = mpos[r];
+    if (M.ell < 2 || M.ell % 2 || M.d != d || !M.bond_dim || !M.W || !M.phys_charge || !M.bond_charge)
+      return bail(IDMRG_EINVAL);
+    for (int s = 0; s < d; ++s)
+      if (M.phys_charge[s] != mpos[0].phys_charge[s]) return bail(IDMRG_EINVAL);  // one local basis
+    if (m_per && m_per[r] < 1) return bail(IDMRG_EINVAL);
+  }
   if (opts->m < 1 || opts->lanczos_maxit < 2 || opts->lanczos_maxit > 600 || !(opts->lanczos_tol > 0))
     return bail(IDMRG_EINVAL);
   if (opts->prec != IDMRG_FP64 && opts->prec != IDMRG_TF32X3 && opts->prec != IDMRG_BF16X3 &&
@@ -3439,33 +3482,61 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
   c->fp64tc = opts->prec == IDMRG_FP64_TC;
   for (GemmTune *t : {&c->tn_gp, &c->tn_env1, &c->tn_env3, &c->tn_svdG, &c->tn_svdW, &c->tn_svdX}) t->oz_use = true;
   c->bf16 = opts->prec == IDMRG_BF16X3 ? 1 : 0;
-  c->ell = ell;
   c->d = d;
-  c->P = ell / 2;
+  c->ell = mpos[0].ell;
+  // rings: superblocks and sites numbered problem after problem
+  int nsb = 0, nsite = 0, mmax = 0;
+  for (int r = 0; r < nmpo; ++r) {
+    idmrg_ctx::Ring R;
+    R.p0 = nsb;
+    R.np = mpos[r].ell / 2;
+    R.s0 = nsite;
+    R.ell = mpos[r].ell;
+    R.m = m_per ? m_per[r] : opts->m;
+    mmax = std::max(mmax, R.m);
+    nsb += R.np;
+    nsite += R.ell;
+    c->rings.push_back(R);
+  }
+  c->o.m = mmax;  // the largest m: strides of the per-superblock lambda arrays
+  c->P = nsb;
   c->own0 = 0;
   c->own1 = c->P;
-  c->adim.assign(mpo->bond_dim, mpo->bond_dim + ell + 1);
-  if (c->adim[ell] != c->adim[0]) return bail(IDMRG_EINVAL);
-  for (int k = 0; k <= ell; ++k)
-    if (c->adim[k] < 2) return bail(IDMRG_EINVAL);
-  c->qp.assign(mpo->phys_charge, mpo->phys_charge + d);
+  c->ring_of.resize(nsb);
+  c->ring_of_site.resize(nsite);
+  for (int r = 0; r < nmpo; ++r) {
+    const idmrg_ctx::Ring &R = c->rings[r];
+    for (int q = 0; q < R.np; ++q) c->ring_of[R.p0 + q] = r;
+    for (int k = 0; k < R.ell; ++k) c->ring_of_site[R.s0 + k] = r;
+  }
+  c->qp.assign(mpos[0].phys_charge, mpos[0].phys_charge + d);
   for (int s = 0; s < d; ++s)
     for (int t = s + 1; t < d; ++t)
       if (c->qp[s] == c->qp[t]) return bail(IDMRG_EINVAL);  // one state per physical charge
-  size_t woff = 0, qoff = 0;
-  c->W.resize(ell);
-  c->bq.resize(ell);
-  for (int k = 0; k < ell; ++k) {
-    const size_t n = (size_t)c->adim[k] * c->adim[k + 1] * d * d;
-    c->W[k].assign(mpo->W + woff, mpo->W + woff + n);
-    woff += n;
-    c->bq[k].assign(mpo->bond_charge + qoff, mpo->bond_charge + qoff + c->adim[k]);
-    qoff += c->adim[k];
+  c->adim.resize(nsite);
+  c->W.resize(nsite);
+  c->bq.resize(nsite);
+  for (int r = 0; r < nmpo; ++r) {
+    const idmrg_mpo &M = mpos[r];
+    const int ell = M.ell, s0 = c->rings[r].s0;
+    if (M.bond_dim[ell] != M.bond_dim[0]) return bail(IDMRG_EINVAL);
+    for (int k = 0; k <= ell; ++k)
+      if (M.bond_dim[k] < 2) return bail(IDMRG_EINVAL);
+    size_t woff = 0, qoff = 0;
+    for (int k = 0; k < ell; ++k) {
+      c->adim[s0 + k] = M.bond_dim[k];
+      const size_t n = (size_t)M.bond_dim[k] * M.bond_dim[k + 1] * d * d;
+      c->W[s0 + k].assign(M.W + woff, M.W + woff + n);
+      woff += n;
+      c->bq[s0 + k].assign(M.bond_charge + qoff, M.bond_charge + qoff + M.bond_dim[k]);
+      qoff += M.bond_dim[k];
+    }
   }
   // lower-triangular FSA form and charge conservation (Sec. 2, Eq. mpo)
-  for (int k = 0; k < ell; ++k) {
-    const int A = c->adim[k], B = c->adim[k + 1];
-    const std::vector<int> &qa = c->bq[k], &qb = c->bq[(k + 1) % ell];
+  for (int k = 0; k < nsite; ++k) {
+    const int kb = c->bond_right(k);
+    const int A = c->adim[k], B = c->adim[kb];
+    const std::vector<int> &qa = c->bq[k], &qb = c->bq[kb];
     for (int a = 0; a < A; ++a)
       for (int b = 0; b < B; ++b)
         for (int s = 0; s < d; ++s)
@@ -3480,6 +3551,11 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
             if (a == 0 || b == B - 1) return bail(IDMRG_EINVAL);
             if (c->qp[s] - c->qp[t] != qb[b] - qa[a]) return bail(IDMRG_EINVAL);
           }
+  }
+  {
+    std::vector<int> msb(nsb);
+    for (int q = 0; q < nsb; ++q) msb[q] = c->rings[c->ring_of[q]].m;
+    if (!c->upload(c->dmsb, msb)) return bail(IDMRG_ENOMEM);
   }
   const int P = c->P;
   c->stage.assign(P, ST_READY);
@@ -3519,7 +3595,7 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
     b.finish();
     const int sL = 2 * p, sR = 2 * p + 1;
     Env &L = c->envL[p];
-    L.lay.build(b, c->bq[(sL + 1) % ell]);
+    L.lay.build(b, c->bq[c->bond_right(sL)]);
     std::vector<double> hl(L.lay.size, 0.0);
     for (int a = 0; a < L.lay.w; ++a)
       for (int si = 0; si < d; ++si) {
@@ -3539,7 +3615,7 @@ idmrg_status idmrg_create(const idmrg_mpo *mpo, const idmrg_opts *opts, void *cu
     if (!c->upload(L.data, hl) || !c->upload(R.data, hr)) return bail(IDMRG_ENOMEM);
   }
   c->n = 1;
-  c->e1[-1] = 0.0;
+  for (idmrg_ctx::Ring &R : c->rings) R.e1[-1] = 0.0;
   if (plan_iteration(c) != IDMRG_OK) return bail(IDMRG_ENOMEM);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(IDMRG_ECUDA);
   *out = c;
@@ -3567,7 +3643,7 @@ void idmrg_destroy(idmrg_ctx *c) {
                     &c->lconv, &c->ltheta, &c->ly, &c->lresid, &c->lpsi, &c->lv0, &c->ldot, &c->sjobs, &c->swork,
                     &c->ssv, &c->sjob0, &c->snjob, &c->skpj, &c->sperm, &c->slam, &c->seps, &c->sepsb, &c->skept,
                     &c->scj, &c->slamk, &c->siw, &c->sorder, &c->sorderq, &c->dsgk, &c->dsgs,
-                    &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpkL, &c->dtune_out,
+                    &c->dswk, &c->dsws, &c->dsxk, &c->dsxs, &c->dpkL, &c->dtune_out, &c->dmsb,
                     &c->dwtp, &c->dwtpm, &c->dwunits, &c->dtarget, &c->dozsw, &c->dozsp, &c->dozp,
                     &c->doz1k,
                     &c->doz1t, &c->doz3k, &c->doz3t, &c->dozw, &c->dozwm, &c->oexp, &c->goz_planes,
@@ -3628,7 +3704,7 @@ idmrg_status idmrg_psi_layout(const idmrg_ctx *cc, int p, int *desc, int cap, in
   idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);
   if (!c || p < 0 || p >= c->P) return IDMRG_EINVAL;
   const PsiLayout &psi = c->plan[p].psi;
-  const Basis &BL = c->envL[p].lay.b, &BR = c->envR[(p + 1) % c->P].lay.b;
+  const Basis &BL = c->envL[p].lay.b, &BR = c->envR[c->nxt(p)].lay.b;
   int nb = 0;
   for (int i = 0; i < BL.S(); ++i)
     for (int s = 0; s < c->d; ++s)
@@ -3656,7 +3732,7 @@ idmrg_status idmrg_psi_layout(const idmrg_ctx *cc, int p, int *desc, int cap, in
 
 idmrg_status idmrg_block_basis(const idmrg_ctx *c, int p, int side, int *charges, int cap, int *dim, int *channels) {
   if (!c || p < 0 || p >= c->P || (side != 0 && side != 1)) return IDMRG_EINVAL;
-  const Env &E = side == 0 ? c->envL[p] : c->envR[(p + 1) % c->P];
+  const Env &E = side == 0 ? c->envL[p] : c->envR[c->nxt(p)];
   const Basis &b = E.lay.b;
   if (charges) {
     int k = 0;
@@ -3672,7 +3748,7 @@ idmrg_status idmrg_block_basis(const idmrg_ctx *c, int p, int side, int *charges
 idmrg_status idmrg_block_to_host(const idmrg_ctx *cc, int p, int side, double *host, size_t cap) {
   idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);
   if (!c || !host || p < 0 || p >= c->P || (side != 0 && side != 1)) return IDMRG_EINVAL;
-  const Env &E = side == 0 ? c->envL[p] : c->envR[(p + 1) % c->P];
+  const Env &E = side == 0 ? c->envL[p] : c->envR[c->nxt(p)];
   const Basis &b = E.lay.b;
   const size_t D = b.D;
   if (cap < (size_t)E.lay.w * D * D) return c->fail(IDMRG_EINVAL, "block_to_host: buffer too small");
@@ -3902,7 +3978,7 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {
       if (rep->bond) rep->bond[q] = c->bond[q];
       if (rep->kept) rep->kept[q] = kept[q];
     }
-    rep->e_g = (c->eg_n == n_done) ? c->eg_last : NAN;
+    rep->e_g = (c->rings[0].eg_n == n_done) ? c->rings[0].eg_last : NAN;
   }
   return sl;
 }
@@ -3916,6 +3992,7 @@ idmrg_status idmrg_unit_cell_step(idmrg_ctx *c, idmrg_step_report *rep) {
 // ------------------------------------------------------------------------
 idmrg_status idmrg_set_pair_range(idmrg_ctx *c, int p0, int p1) {
   if (!c) return IDMRG_EINVAL;
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "set_pair_range: needs a context of one problem");
   if (p0 < 0 || p1 > c->P || p0 >= p1) return c->fail(IDMRG_EINVAL, "pair range %d..%d outside 0..%d", p0, p1, c->P);
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "set_pair_range: a step is in progress");
@@ -3929,6 +4006,7 @@ idmrg_status idmrg_set_pair_range(idmrg_ctx *c, int p0, int p1) {
 idmrg_status idmrg_export_pair(const idmrg_ctx *cc, int q, void *host, size_t cap, size_t *len) {
   idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);
   if (!c || !len || q < 0 || q >= c->P) return IDMRG_EINVAL;
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "export_pair: needs a context of one problem");
   if (!c->owns(q)) return c->fail(IDMRG_EINVAL, "export_pair: pair %d is not stepped by this context", q);
   for (int k = 0; k < c->P; ++k)
     if (c->stage[k] != ST_READY) return c->fail(IDMRG_ESTATE, "export_pair: a step is in progress");
@@ -3960,6 +4038,7 @@ idmrg_status idmrg_export_pair(const idmrg_ctx *cc, int q, void *host, size_t ca
 
 idmrg_status idmrg_import_pair(idmrg_ctx *c, int q, const void *host, size_t len) {
   if (!c || !host || q < 0 || q >= c->P) return IDMRG_EINVAL;
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "import_pair: needs a context of one problem");
   if (c->owns(q)) return c->fail(IDMRG_EINVAL, "import_pair: pair %d is stepped by this context", q);
   if (q != c->own1 % c->P) return c->fail(IDMRG_EINVAL, "import_pair: pair %d does not follow this range", q);
   CkFile F;
@@ -3997,6 +4076,7 @@ idmrg_status idmrg_import_pair(idmrg_ctx *c, int q, const void *host, size_t len
 idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
   if (!cc || !path) return IDMRG_EINVAL;
   idmrg_ctx *c = const_cast<idmrg_ctx *>(cc);  // errors are recorded in the context
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "save: needs a context of one problem");
   if (!c->owns_all()) return c->fail(IDMRG_ESTATE, "save: the context steps only superblocks %d..%d", c->own0, c->own1 - 1);
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "save: a step is in progress");
@@ -4011,13 +4091,17 @@ idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
   F.put(c->o.m);
   F.put((int)c->o.prec);
   F.put(c->o.target_charge);
-  F.putv(c->adim);
+  {  // the bond dimensions of the unit cell with its closing bond (l + 1 entries)
+    std::vector<int> ad(c->adim);
+    ad.push_back(c->adim[0]);
+    F.putv(ad);
+  }
   F.put(c->n);
-  F.put(c->eg_n);
-  F.put(c->eg_last);
+  F.put(c->rings[0].eg_n);
+  F.put(c->rings[0].eg_last);
   std::vector<int> e1n;
   std::vector<double> e1v;
-  for (const auto &kv : c->e1) {
+  for (const auto &kv : c->rings[0].e1) {
     e1n.push_back(kv.first);
     e1v.push_back(kv.second);
   }
@@ -4025,7 +4109,7 @@ idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
   F.putv(e1v);
   std::vector<int> ern;
   std::vector<double> erv;
-  for (const auto &kv : c->eps1) {
+  for (const auto &kv : c->rings[0].eps1) {
     ern.push_back(kv.first);
     erv.push_back(kv.second);
   }
@@ -4049,6 +4133,7 @@ idmrg_status idmrg_save(const idmrg_ctx *cc, const char *path) {
 
 idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
   if (!c || !path) return IDMRG_EINVAL;
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "load: needs a context of one problem");
   if (!c->owns_all()) return c->fail(IDMRG_ESTATE, "load: the context steps only superblocks %d..%d", c->own0, c->own1 - 1);
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "load: a step is in progress");
@@ -4069,7 +4154,8 @@ idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
   F.getv(adim, 1 << 20);
   (void)prec;  // every precision keeps the state in FP64: a state moves between precisions
   if (!F.ok || ell != c->ell || d != c->d || P != c->P || m != c->o.m || target != c->o.target_charge ||
-      adim != c->adim)
+      adim.size() != c->adim.size() + 1 || !std::equal(c->adim.begin(), c->adim.end(), adim.begin()) ||
+      adim.back() != c->adim[0])
     return c->fail(IDMRG_EINVAL, "load: %s is not a checkpoint of this MPO and these options", path);
   int n = 0, eg_n = 0;
   double eg_last = 0.0;
@@ -4103,41 +4189,43 @@ idmrg_status idmrg_load(idmrg_ctx *c, const char *path) {
     }
   }
   c->n = n;
-  c->eg_n = eg_n;
-  c->eg_last = eg_last;
-  c->e1.clear();
-  for (size_t k = 0; k < e1n.size(); ++k) c->e1[e1n[k]] = e1v[k];
-  c->eps1.clear();
-  for (size_t k = 0; k < ern.size(); ++k) c->eps1[ern[k]] = erv[k];
+  c->rings[0].eg_n = eg_n;
+  c->rings[0].eg_last = eg_last;
+  c->rings[0].e1.clear();
+  for (size_t k = 0; k < e1n.size(); ++k) c->rings[0].e1[e1n[k]] = e1v[k];
+  c->rings[0].eps1.clear();
+  for (size_t k = 0; k < ern.size(); ++k) c->rings[0].eps1[ern[k]] = erv[k];
   return plan_iteration(c);
 }
 
 idmrg_status idmrg_truncation_error(const idmrg_ctx *c, double *eps) {
   if (!c || !eps) return IDMRG_EINVAL;
-  if (c->eps1.empty()) return IDMRG_ESTATE;
+  if (!c->one_ring()) return IDMRG_EINVAL;
+  if (c->rings[0].eps1.empty()) return IDMRG_ESTATE;
   double e = 0.0;
   int k = 0;
-  for (auto it = c->eps1.rbegin(); it != c->eps1.rend() && k < c->ell; ++it, ++k) e = std::max(e, it->second);
+  for (auto it = c->rings[0].eps1.rbegin(); it != c->rings[0].eps1.rend() && k < c->ell; ++it, ++k) e = std::max(e, it->second);
   *eps = e;
   return IDMRG_OK;
 }
 
 idmrg_status idmrg_run(idmrg_ctx *c, int max_steps, double de_tol, double *e_g, double *eps, int *steps) {
   if (!c || max_steps < 1 || !(de_tol > 0)) return IDMRG_EINVAL;
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "run: needs a context of one problem");
   double last = NAN;
   int last_n = -1, k = 0;
   bool done = false;
   for (; k < max_steps && !done; ++k) {
     const idmrg_status s = idmrg_unit_cell_step(c, nullptr);
     if (s != IDMRG_OK && s != IDMRG_ENOCONV) return s;
-    if (c->eg_n >= 0 && c->eg_n != last_n) {  // a new estimate of e_g
-      done = std::isfinite(last) && fabs(c->eg_last - last) < de_tol;
-      last = c->eg_last;
-      last_n = c->eg_n;
+    if (c->rings[0].eg_n >= 0 && c->rings[0].eg_n != last_n) {  // a new estimate of e_g
+      done = std::isfinite(last) && fabs(c->rings[0].eg_last - last) < de_tol;
+      last = c->rings[0].eg_last;
+      last_n = c->rings[0].eg_n;
     }
   }
   if (steps) *steps = k;
-  if (e_g) *e_g = c->eg_last;
+  if (e_g) *e_g = c->rings[0].eg_last;
   if (eps) idmrg_truncation_error(c, eps);
   return done ? IDMRG_OK : IDMRG_ENOCONV;
 }
@@ -4145,6 +4233,7 @@ idmrg_status idmrg_run(idmrg_ctx *c, int max_steps, double de_tol, double *e_g, 
 idmrg_status idmrg_correlation(idmrg_ctx *c, int nterms, const double *op_a, const double *op_b, const double *coef,
                                int npairs, const int64_t *site_i, const int64_t *site_j, double *out) {
   if (!c || nterms < 1 || nterms > 64 || npairs < 0 || !op_a || !op_b || !coef) return IDMRG_EINVAL;
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "correlation: needs a context of one problem");
   if (npairs > 0 && (!site_i || !site_j || !out)) return IDMRG_EINVAL;
   if (!c->owns_all() || c->plan_pending) return c->fail(IDMRG_ESTATE, "correlation: needs the whole unit cell");
   for (int k = 0; k < npairs; ++k)
@@ -4159,6 +4248,7 @@ idmrg_status idmrg_correlation(idmrg_ctx *c, int nterms, const double *op_a, con
 idmrg_status idmrg_transfer_spectrum(idmrg_ctx *c, double tol, int maxit, double *t1, double *t2_abs, double *xi,
                                      int *iters) {
   if (!c || !(tol > 0.0) || maxit < 1) return IDMRG_EINVAL;
+  if (!c->one_ring()) return c->fail(IDMRG_EINVAL, "transfer_spectrum: needs a context of one problem");
   if (!c->owns_all() || c->plan_pending) return c->fail(IDMRG_ESTATE, "transfer_spectrum: needs the whole unit cell");
   for (int q = 0; q < c->P; ++q)
     if (c->stage[q] != ST_READY) return c->fail(IDMRG_ESTATE, "transfer_spectrum: a step is in progress");
@@ -4173,11 +4263,20 @@ idmrg_status idmrg_transfer_spectrum(idmrg_ctx *c, double tol, int maxit, double
   return s;
 }
 
+idmrg_status idmrg_ring_energy(const idmrg_ctx *c, int r, double *e_g, int *n_of_estimate) {
+  if (!c || r < 0 || r >= (int)c->rings.size()) return IDMRG_EINVAL;
+  const idmrg_ctx::Ring &R = c->rings[r];
+  if (R.eg_n < 0) return IDMRG_ESTATE;
+  if (e_g) *e_g = R.eg_last;
+  if (n_of_estimate) *n_of_estimate = R.eg_n;
+  return IDMRG_OK;
+}
+
 idmrg_status idmrg_energy_per_site(const idmrg_ctx *c, double *e_g, int *n_of_estimate) {
   if (!c) return IDMRG_EINVAL;
-  if (c->eg_n < 0) return IDMRG_ESTATE;
-  if (e_g) *e_g = c->eg_last;
-  if (n_of_estimate) *n_of_estimate = c->eg_n;
+  if (c->rings[0].eg_n < 0) return IDMRG_ESTATE;
+  if (e_g) *e_g = c->rings[0].eg_last;
+  if (n_of_estimate) *n_of_estimate = c->rings[0].eg_n;
   return IDMRG_OK;
 }
 

@@ -2103,8 +2103,8 @@ __device__ __forceinline__ bool before(const Entry &a, const Entry &b, const Svd
 }
 
 __global__ void select_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ sb_job0,
-                              const int *__restrict__ sb_njob, const double *__restrict__ sv, int m,
-                              double zero_rel, double tie_rel, SelectOut out, int P) {
+                              const int *__restrict__ sb_njob, const double *__restrict__ sv,
+                              const int *__restrict__ m_sb, double zero_rel, double tie_rel, SelectOut out, int P) {
   extern __shared__ unsigned char smraw[];
   Entry *E = (Entry *)smraw;
   int *cnt = (int *)(E + P);
@@ -2156,7 +2156,7 @@ __global__ void select_kernel(const SvdJob *__restrict__ jobs, const int *__rest
     const double smax = E[0].s;
     int nz = 0;
     while (nz < total && E[nz].s > zero_rel * smax) ++nz;
-    const int top = min(m, nz);
+    const int top = min(m_sb[s], nz);
     int D = top;
     while (D > 0 && D < nz && !(E[D].s < E[D - 1].s * (1.0 - tie_rel))) --D;
     if (D == 0) D = top;
@@ -2451,14 +2451,14 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
 }
 
 cudaError_t launch_svd_select(const SvdJob *jobs, const int *sb_job0, const int *sb_njob, int S, const double *sv,
-                              int m, double zero_rel, double tie_rel, SelectOut out, int max_entries,
+                              const int *m_sb, double zero_rel, double tie_rel, SelectOut out, int max_entries,
                               cudaStream_t st) {
   int P = 1;
   while (P < max_entries) P <<= 1;
   const size_t smem = (size_t)P * sizeof(Entry) + 256 * sizeof(int);
   cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (S > 0) select_kernel<<<S, 512, smem, st>>>(jobs, sb_job0, sb_njob, sv, m, zero_rel, tie_rel, out, P);
+  if (S > 0) select_kernel<<<S, 512, smem, st>>>(jobs, sb_job0, sb_njob, sv, m_sb, zero_rel, tie_rel, out, P);
   return cudaGetLastError();
 }
 
