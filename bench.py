@@ -49,7 +49,8 @@ SATURATE_MAX = 40        # iterations allowed to reach D >= 0.9 m
 # Timed window: after the prediction of Step 3' has settled.  Sec. 4 finds
 # the Eq. fid1 fidelity error comparable with the truncation error once the
 # run is past its transient, and times the iDMRG as the average over
-# n <= 1200 iterations (Fig. 3), i.e. in that regime.
+# n <= 1200 iterations (the parallel-performance figure of Sec. 4.1), i.e. in
+# that regime.
 SETTLE_RATIO = 10.0      # max_i fidelity error <= SETTLE_RATIO max_i eps (+ 1e-9)
 SETTLE_RUN = 3           # ... on this many consecutive steps
 SETTLE_MAX_N = 90        # or until this iteration
