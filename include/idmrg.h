@@ -442,6 +442,16 @@ idmrg_status idmrg_svd_phase_ms(idmrg_ctx *ctx, double *ms);
  * stages counted).  EINVAL for another stage number. */
 idmrg_status idmrg_gemm_tuning(const idmrg_ctx *ctx, int stage, int *tn, float *ms, int *tunings);
 
+/* Mixed precisions (TF32X3, BF16X3): Step 3's Lanczos runs as restarts, each
+ * starting with an FP64-accurate matvec (the true residual, checked against
+ * lanczos_tol) and continuing on the tensor cores until the residual estimate
+ * has fallen by inner_factor (default 1e-2 for BF16X3, 1e-3 for TF32X3: a
+ * restart gains about what the split precision allows, so a smaller factor
+ * only adds matvecs) or inner_cap matvecs (default 80) have run; the Ritz
+ * vector starts the next restart.  EINVAL unless
+ * 0 < inner_factor < 1 and inner_cap >= 2.  No effect in FP64 and FP64_TC. */
+idmrg_status idmrg_set_mixed_restart(idmrg_ctx *ctx, double inner_factor, int inner_cap);
+
 /* Fixes the N tile of stage 1 (tn1) and stage 3 (tn3) of the split-operand
  * GEMMs instead of tuning it: 64, 128 or 256, or 0 to tune (the default).
  * Takes effect from the next iteration's plan; the results agree to

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
-    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_create_batch", "idmrg_ring_energy", "idmrg_svd_phase_ms", "idmrg_svd_sweeps32", "idmrg_save", "idmrg_load",
+    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_create_batch", "idmrg_ring_energy", "idmrg_set_mixed_restart", "idmrg_svd_phase_ms", "idmrg_svd_sweeps32", "idmrg_save", "idmrg_load",
     "idmrg_correlation", "idmrg_transfer_spectrum", "idmrg_delta_pm", "idmrg_extrapolate",
     "idmrg_fit_correlation_length", "idmrg_set_pair_range", "idmrg_export_pair", "idmrg_import_pair",
 ]
@@ -128,6 +128,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_set_gemm_tile": (i, [vp, i, i]),
         "idmrg_create_batch": (i, [P(_MPO), i, P(i), P(_Opts), vp, P(_Allocator), P(vp)]),
         "idmrg_ring_energy": (i, [vp, i, P(d), P(i)]),
+        "idmrg_set_mixed_restart": (i, [vp, d, i]),
         "idmrg_svd_phase_ms": (i, [vp, P(d)]),
         "idmrg_svd_sweeps32": (i, [vp, P(i), P(d)]),
         "idmrg_correlation": (i, [vp, i, P(d), P(d), P(d), i, P(C.c_int64), P(C.c_int64), P(d)]),
@@ -523,6 +524,11 @@ class Context:
         ms = (C.c_double * len(self.SVD_PHASES))()
         self._check(self.lib.idmrg_svd_phase_ms(self.h, ms), "svd_phase_ms")
         return {k: ms[i] for i, k in enumerate(self.SVD_PHASES)}
+
+    def set_mixed_restart(self, inner_factor: float, inner_cap: int) -> None:
+        """Restart rule of the mixed-precision Lanczos (idmrg_set_mixed_restart)."""
+        self._check(self.lib.idmrg_set_mixed_restart(self.h, float(inner_factor), int(inner_cap)),
+                    "set_mixed_restart")
 
     def set_gemm_tile(self, tn1: int, tn3: int) -> None:
         """Fix the N tiles of H_eff stages 1 and 3 (0 = tuned) from the next plan on."""

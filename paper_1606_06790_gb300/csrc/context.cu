@@ -249,6 +249,13 @@ struct idmrg_ctx {
   } tt1, tt3;
   int tc_tunes = 0;  // tuning passes run (each times every candidate of a stage)
   int force_tn[2] = {0, 0};  // N tile fixed by the caller for stage 1 / stage 3 (0: tuned)
+  // mixed-precision Lanczos restarts: the inner (reduced-precision) run of a
+  // restart stops when its residual estimate has fallen by inner_factor, or
+  // after inner_cap matvecs.  A restart cannot gain much more than the split
+  // precision allows (about 1e-2 with BF16 pairs at m = 2048): a smaller
+  // factor only adds matvecs.  Set at creation by precision.
+  double inner_factor = 1e-3;
+  int inner_cap = 80;
 
   int pk_L_rows = 0, pk_psi_rows = 0, pk_R_rows = 0, wtp_rows = 0;
   DevBuf dpkL, dpkp[MIX_NTN], dpkR[MIX_NTN], dtc1k[MIX_NTN], dtc1t[MIX_NTN], dtc3k[MIX_NTN], dtc3t[MIX_NTN];
@@ -1899,9 +1906,9 @@ idmrg_status lanczos(idmrg_ctx *c, int p) {
   // inner factor; the Ritz vector starts the next restart.
   // (BF16 splits carry ~16 bits per product against ~21 for TF32: each
   // restart gains less, so more of them are allowed)
-  L.inner_factor = c->mixed ? 1e-3 : 0.0;
+  L.inner_factor = c->mixed ? c->inner_factor : 0.0;
   const int max_restarts = c->mixed ? (c->bf16 ? 12 : 8) : 1;
-  const int inner_cap = c->mixed ? std::min(kmax, 80) : kmax;
+  const int inner_cap = c->mixed ? std::min(kmax, c->inner_cap) : kmax;
   for (int q = 0; q < P; ++q) c->hbufs[q * NBUF + BUF_PSI] = psip[q];
   NOMEM(sync_bufs(c) == IDMRG_OK);
   std::vector<double> nrm2(P, 0.0), theta(P, 0.0), dots(P, 0.0);
@@ -3482,6 +3489,7 @@ idmrg_status idmrg_create_batch(const idmrg_mpo *mpos, int nmpo, const int *m_pe
   c->fp64tc = opts->prec == IDMRG_FP64_TC;
   for (GemmTune *t : {&c->tn_gp, &c->tn_env1, &c->tn_env3, &c->tn_svdG, &c->tn_svdW, &c->tn_svdX}) t->oz_use = true;
   c->bf16 = opts->prec == IDMRG_BF16X3 ? 1 : 0;
+  c->inner_factor = c->bf16 ? 1e-2 : 1e-3;
   c->d = d;
   c->ell = mpos[0].ell;
   // rings: superblocks and sites numbered problem after problem
@@ -4351,6 +4359,15 @@ idmrg_status idmrg_svd_stats(const idmrg_ctx *c, int *jobs, int *max_cols, int *
   if (max_rank) *max_rank = c->svd_max_rank;
   if (max_sweeps) *max_sweeps = c->svd_max_sweeps;
   if (mean_sweeps) *mean_sweeps = c->svd_mean_sweeps;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_set_mixed_restart(idmrg_ctx *c, double inner_factor, int inner_cap) {
+  if (!c) return IDMRG_EINVAL;
+  if (!(inner_factor > 0.0 && inner_factor < 1.0) || inner_cap < 2)
+    return c->fail(IDMRG_EINVAL, "set_mixed_restart: need 0 < inner_factor < 1 and inner_cap >= 2");
+  c->inner_factor = inner_factor;
+  c->inner_cap = inner_cap;
   return IDMRG_OK;
 }
 
