@@ -124,7 +124,7 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"heff_gemm": ["kernels_f64.cu", "kernels_tc.cu"], "heff_wstage": ["kernels_f64.cu", "kernels_tc.cu"],
+KERNEL_SOURCES = {"heff": ["kernels_tc.cu"], "heff_gemm": ["kernels_tc.cu"], "heff_wstage": ["kernels_tc.cu"],
                   "lanczos_vec": ["kernels_lanczos.cu"], "lanczos_tri": ["kernels_lanczos.cu"],
                   "svd": ["kernels_svd.cu", "kernels_tc.cu"], "env": ["kernels_f64.cu", "kernels_tc.cu"],
                   "predict": ["kernels_f64.cu", "kernels_tc.cu"], "heff_f64": ["kernels_f64.cu", "kernels_tc.cu"]}
@@ -193,7 +193,7 @@ def heff_roofline(prof: dict, prec: str, pk: dict):
          "flops": prof["heff_gemm"]["flops"] + prof["heff_wstage"]["flops"], "bytes": 0.0}
     r = class_roofline("heff_gemm", d, prec, pk)
     r["kernel"] = "heff (gemm + wstage)"
-    r["traffic"] = None
+    r["traffic"] = traffic_for("heff", prec)
     return r
 
 
