@@ -111,3 +111,33 @@ def test_einval_invalid_mpo(flaw):
     with pytest.raises(pkg.IdmrgError) as ei:
         pkg.Context(W, mpo.phys_charge, mpo.bond_charge, m=8)
     assert ei.value.status == 1  # IDMRG_EINVAL
+
+
+def test_settings_and_instrumentation():
+    """The restart rule, the tile setting and the SVD instrumentation through
+    the C ABI: invalid arguments are EINVAL, the reports are consistent."""
+    import paper_1606_06790_gb300 as pkg
+    mpo = _mpo()
+    ctx = context(mpo, 16, prec="bf16x3")
+    for bad in ((0.0, 80), (1.0, 80), (1e-2, 1)):
+        with pytest.raises(pkg.IdmrgError) as ei:
+            ctx.set_mixed_restart(*bad)
+        assert ei.value.status == 1
+    with pytest.raises(pkg.IdmrgError) as ei:
+        ctx.set_gemm_tile(96, 0)
+    assert ei.value.status == 1
+    ctx.set_mixed_restart(1e-2, 40)
+    ctx.profile_enable(True)
+    for _ in range(4):
+        r = ctx.unit_cell_step()
+        assert r["converged"]
+    ph = ctx.svd_phase_ms()
+    assert set(ph) == set(ctx.SVD_PHASES) and all(v >= 0.0 for v in ph.values())
+    assert ph["jacobi64"] > 0.0 and ph["qr"] > 0.0
+    st = ctx.svd_stats()
+    assert st["max_sweeps32"] >= 1 and 1.0 <= st["mean_sweeps32"] <= st["max_sweeps32"]
+    for stage in (1, 3):
+        t = ctx.gemm_tuning(stage)
+        assert t["tn"] in (64, 128, 256) and t["tunings"] >= 1
+        assert t["ms"][t["tn"]] == min(t["ms"].values())
+    ctx.close()
