@@ -736,6 +736,14 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
   }
 }
 
+// The FP32 stage only preconditions the FP64 one: once a sweep's largest
+// rotation (|cos| between two columns) is below J32_PRECOND_R, the columns
+// are orthogonal to about its square, the level of FP32 rounding itself, and
+// the FP64 stage starts from there whatever further FP32 sweeps would do
+// (the maximum over all pairs of the FP32 rounding noise in the overlaps can
+// otherwise keep the tighter test open for several sweeps).
+constexpr float J32_PRECOND_R = 1e-3f;
+
 // the FP32 stage's sweep count of a job, in the slot after its rank and FP64
 // sweep count (read back for the statistics only)
 __device__ __forceinline__ void iwork32_sweeps(const int *iwork, const SvdJob &J, int sweep) {
@@ -880,7 +888,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 2)
     }
     cluster.sync();
     const float r = __int_as_float(*rmax0);
-    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol) || r < J32_PRECOND_R;
     cluster.sync();
   }
   if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
@@ -1644,7 +1652,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     // done when nothing rotated, or the largest rotation leaves overlaps of
     // order n r^2 below the FP32 threshold
     const float r = __int_as_float(*rmax0);
-    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol) || r < J32_PRECOND_R;
     cluster.sync();
   }
   if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
@@ -1818,7 +1826,7 @@ __global__ void __launch_bounds__(BJ_THREADS, 1)
     }
     cluster.sync();
     const float r = __int_as_float(*rmax0);
-    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol) || r < J32_PRECOND_R;
     cluster.sync();
   }
   if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
@@ -2061,7 +2069,7 @@ __global__ void __launch_bounds__(JS_THREADS, 1)
     }
     cluster.sync();
     const float r = __int_as_float(*rmax0);
-    converged = (*flag0 == 0) || ((float)n * r * r < tol);
+    converged = (*flag0 == 0) || ((float)n * r * r < tol) || r < J32_PRECOND_R;
     cluster.sync();
   }
   if (crank == 0 && threadIdx.x == 0) iwork32_sweeps(iwork, Jb, sweep);
