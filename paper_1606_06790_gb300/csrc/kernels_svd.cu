@@ -2058,7 +2058,7 @@ __global__ void __launch_bounds__(JS_THREADS, 1)
         }
         __syncthreads();
       }
-      cluster.sync();  // this round's blocks and V columns are written before the next round reads them
+      cluster.sync();  // the blocks and V columns of this tournament round are written before the next reads them
     }
     if (any && lane == 0) local_changed = 1;
     if (lane == 0) atomicMax(&sweep_rmax, __float_as_int(rmax));

@@ -1,4 +1,4 @@
-"""The ring-shift sharding of one problem (Sec. 3, Step 2'; SURVEY 8(e)) on
+"""The ring-shift sharding of one problem (Sec. 3, Step 2') on
 CPU processes with gloo: each rank steps its contiguous range of pairs with
 the FP64 oracle, exchanges the boundary pair's R^(n), U^(n), lambda^(n) with
 its ring neighbours, and the gathered step reports equal a single-process
