@@ -401,6 +401,134 @@ def run_reference_full(args, mpo, seed):
     print(json.dumps(line), flush=True)
 
 
+def synthetic_superblock(mpo, m: int, g):
+    """Superblock 0 of `mpo` at a saturated iteration for the dense oracle:
+    its MPO channels, D = m on both sides, charges spread as in a U(1) block
+    (the dense oracle ignores them apart from the truncation's sectors), and a
+    unit start vector in the target sector.  The dense oracle's cost depends
+    on these shapes only, so synthetic entries cost what real ones do."""
+    from oracle.idmrg import Block, sector_mask
+    ell = len(mpo.W)
+    n = 2 * ell + 1
+    c1, c2 = n % ell, (n + 1) % ell
+    w1, w2 = mpo.W[c1].shape[0], mpo.W[c2].shape[1]
+    q = np.sort(np.clip(np.round(g.normal(0.0, 3.0, m)).astype(np.int64) * 2, -40, 40))
+    L = Block(g.standard_normal((w1, m, m)) / m, q)
+    R = Block(g.standard_normal((w2, m, m)) / m, -q[::-1].copy())
+    mask = sector_mask(L.q, mpo.phys_charge.astype(np.int64), R.q)
+    x = np.where(mask, g.standard_normal(mask.shape), 0.0)
+    x /= np.linalg.norm(x)
+    return L, mpo.W[c1], mpo.W[c2], R, x
+
+
+def synthetic_rest(mpo, L, W1, W2, R, x, m: int):
+    """Seconds of the oracle's truncation (Step 4) and block updates (Step 6)
+    on a synthetic superblock."""
+    from oracle.idmrg import truncate, update_left, update_right
+    t = time.perf_counter()
+    tr = truncate(x, L.q, mpo.phys_charge.astype(np.int64), R.q, m)
+    t_tr = time.perf_counter() - t
+    t = time.perf_counter()
+    update_left(L, W1, tr.U, tr.q)
+    update_right(R, W2, tr.V, -tr.q)
+    return t_tr, time.perf_counter() - t
+
+
+def disorder_pieces(work, g, matvecs: int = 1):
+    """Oracle pieces of one superblock solve (as oracle_sample) at each m of
+    the disorder batch, on the first realisation with that m (all realisations
+    share the MPO shape, w = 5): the mean of `matvecs` timed H_eff psi, one
+    truncation and one pair of block updates."""
+    from oracle.idmrg import heff_apply
+    out = {}
+    for _, mpo, m in work:
+        if m in out:
+            continue
+        L, W1, W2, R, x = synthetic_superblock(mpo, m, g)
+        t_tr, t_up = synthetic_rest(mpo, L, W1, W2, R, x, m)
+        heff_apply(L, W1, W2, R, x)
+        t = time.perf_counter()
+        for _ in range(matvecs):
+            heff_apply(L, W1, W2, R, x)
+        out[m] = {"start": 0.0, "matvec": (time.perf_counter() - t) / matvecs, "truncate": t_tr, "update": t_up}
+    return out
+
+
+def disorder_step_estimate(work, pieces: dict, iters) -> float:
+    """Seconds of one oracle step of every realisation: realisation r costs
+    l_r / 2 superblocks x (iters[r] matvecs + the rest) at its own m."""
+    return sum(step_estimate(len(mpo.W) // 2, pieces[m], iters[r]) for r, (_, mpo, m) in enumerate(work))
+
+
+def disorder_cpu_baseline(work, iters):
+    """cpu_baseline of the disorder batch: the FP64 oracle's pieces timed at
+    the saturated shape of each m (128, 256, 512; the matvec as the mean of
+    five solves' worth of them, about 10 s of host work), one batch step =
+    every realisation's l_r / 2 superblocks with its measured Lanczos
+    count."""
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    pieces = disorder_pieces(work, np.random.default_rng(20160622), matvecs=5 * PAPER_LANCZOS_ITERS)
+    per = disorder_step_estimate(work, pieces, iters)
+    mv = ", ".join(f"m={m}: {p['matvec']:.3f}+{p['truncate']:.2f}+{p['update']:.2f} s" for m, p in pieces.items())
+    return {"value": len(work) / per, "unit": "realisation unit-cell steps/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": (f"FP64 numpy oracle, one superblock at the saturated shape D = m of each m (synthetic "
+                       f"blocks of the realisations' MPO shape): mean of {5 * PAPER_LANCZOS_ITERS} H_eff psi + "
+                       f"truncation + block updates ({mv}); "
+                       f"batch step = every realisation's l/2 superblocks x (its mean Lanczos count in the timed "
+                       f"GPU steps, {float(np.mean(iters)):.1f} on average, matvecs + the rest)"),
+            "sec_per_step": per, "sample_wall_s": time.perf_counter() - t0}
+
+
+def run_reference_disorder(args):
+    """--impl reference --workload disorder64: the FP64 oracle on the host
+    cores, same metric unit as the GPU arm (realisation unit-cell steps/s).
+    Truncation and block updates are timed once per m in the warm-up; every
+    timed step times one H_eff psi at each m again; a batch step is every
+    realisation's l/2 superblocks x (PAPER_LANCZOS_ITERS matvecs + the rest)."""
+    from workloads import disorder_batch
+    work = disorder_batch(64)
+    g = np.random.default_rng(20160622)
+    pieces = disorder_pieces(work, g, matvecs=max(args.warmup, 1))
+    iters = [PAPER_LANCZOS_ITERS] * len(work)
+    samples = []
+    for _ in range(args.steps):
+        samples.append(disorder_step_estimate(work, disorder_pieces_matvec(work, pieces, g), iters))
+    per = sum(samples) / len(samples)
+    v = len(work) / per
+    cores = len(os.sched_getaffinity(0))
+    sample = (f"per step: one dense FP64 H_eff psi per m (128, 256, 512) timed; truncation and block updates "
+              f"timed once per m; batch step = 64 realisations x l/2 superblocks x ({PAPER_LANCZOS_ITERS} matvecs, "
+              f"the paper's count with the prediction, + the rest)")
+    line = {"metric": METRIC, "value": v, "unit": "realisation unit-cell steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "disorder64", "realisations": len(work),
+                       "ell": "8/12/16/24 by r mod 4", "m": "128/256/512 by (r div 4) mod 3",
+                       "regime": "saturated shape (D = m)"},
+            "cpu_baseline": {"value": v, "unit": "realisation unit-cell steps/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": sample},
+            "e2e": {"value": v, "unit": "realisation unit-cell steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def disorder_pieces_matvec(work, pieces: dict, g) -> dict:
+    """`pieces` with the H_eff psi time of each m measured again (one matvec
+    on a fresh synthetic superblock)."""
+    from oracle.idmrg import heff_apply
+    out = {}
+    for _, mpo, m in work:
+        if m in out:
+            continue
+        L, W1, W2, R, x = synthetic_superblock(mpo, m, g)
+        t = time.perf_counter()
+        heff_apply(L, W1, W2, R, x)
+        out[m] = dict(pieces[m], matvec=time.perf_counter() - t)
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, same metric and
     workload, each step a bounded sample: one dense H_eff psi of a saturated
@@ -412,38 +540,20 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-    from oracle.idmrg import Block, heff_apply, truncate, update_left, update_right
-    name = args.workload if args.workload != "disorder64" else CHAIN
+    from oracle.idmrg import heff_apply
+    if args.workload == "disorder64":
+        return run_reference_disorder(args)
+    name = args.workload
     mpo, seed = make_workload(0, name)
     m = args.m
     if name == CHAIN:
         return run_reference_full(args, mpo, seed)
     ell = len(mpo.W)
     P = ell // 2
-    d = mpo.d
     g = np.random.default_rng(20160622)
-    # superblock 0 at a saturated iteration: its MPO channels, D = m on both
-    # sides, charges spread as in a U(1) block (the dense oracle ignores them
-    # apart from the truncation's sectors)
-    n = 2 * ell + 1
-    c1, c2 = n % ell, (n + 1) % ell
-    w1, w2 = mpo.W[c1].shape[0], mpo.W[c2].shape[1]
-    q = np.sort(np.clip(np.round(g.normal(0.0, 3.0, m)).astype(np.int64) * 2, -40, 40))
-    L = Block(g.standard_normal((w1, m, m)) / m, q)
-    R = Block(g.standard_normal((w2, m, m)) / m, -q[::-1].copy())
-    from oracle.idmrg import sector_mask
-    mask = sector_mask(L.q, mpo.phys_charge.astype(np.int64), R.q)
-    x = np.where(mask, g.standard_normal(mask.shape), 0.0)
-    x /= np.linalg.norm(x)
-    W1, W2 = mpo.W[c1], mpo.W[c2]
-    t = time.perf_counter()
-    tr = truncate(x, L.q, mpo.phys_charge.astype(np.int64), R.q, m)
-    t_tr = time.perf_counter() - t
-    t = time.perf_counter()
-    update_left(L, W1, tr.U, tr.q)
-    update_right(R, W2, tr.V, -tr.q)
-    t_up = time.perf_counter() - t
+    L, W1, W2, R, x = synthetic_superblock(mpo, m, g)
+    w1, w2 = L.op.shape[0], R.op.shape[0]
+    t_tr, t_up = synthetic_rest(mpo, L, W1, W2, R, x, m)
     for _ in range(args.warmup):
         heff_apply(L, W1, W2, R, x)
     samples = []
@@ -481,7 +591,7 @@ class _RingBatch:
 
     def step(self):
         r = self.ctx.unit_cell_step()
-        return [{"kept": r["kept"][p0:p0 + k]} for p0, k in self.ctx.rings]
+        return [{"kept": r["kept"][p0:p0 + k], "iters": r["iters"][p0:p0 + k]} for p0, k in self.ctx.rings]
 
     def contexts(self):
         return [self.ctx]
@@ -512,6 +622,7 @@ def run_batch(args, pkg, dev, local, world, rank, dist):
     clocks.start()
     wall = 0.0
     reps = None
+    iters = np.zeros(B.n)
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -519,6 +630,7 @@ def run_batch(args, pkg, dev, local, world, rank, dist):
         reps = B.step()
         torch.cuda.synchronize()
         wall += time.perf_counter() - t
+        iters += [float(np.mean(r["iters"])) for r in reps]
     clk = clocks.stop()
     t_wall = reduce_max([wall], dist, dev)[0]
     launches = sum(c.launch_count() for c in ctxs) - launches0
@@ -545,6 +657,11 @@ def run_batch(args, pkg, dev, local, world, rank, dist):
                     "d2h_bytes_per_step": d2h, "note": "the batch API call is the timed region"},
             "clocks": clk,
         }
+        if world == 1 and not args.no_cpu_baseline:
+            try:
+                line["cpu_baseline"] = disorder_cpu_baseline(work, iters / args.steps)
+            except Exception as e:  # the baseline must not cost the measured line
+                line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
