@@ -155,8 +155,10 @@ def class_roofline(name: str, d: dict, prec: str, pk: dict):
     FP64 product).  `executed_frac` is the same fraction with the MMAs the
     pipe executes.  The W stage and psi split of the mixed H_eff and the
     Lanczos vector kernels are HBM streams (algorithmic bytes booked by the
-    library); the FP64 SVD and the FP64 forms run on the FP64 units: 152 SMs
-    x 2 FMA/clk x 2.07 GHz."""
+    library); the SVD (its R-SVD flop count at FP64 accuracy) and the FP64
+    forms against the FP64 units: 152 SMs x 2 FMA/clk x 2.07 GHz.  In the
+    mixed precisions the final Jacobi of large sectors runs in FP32 pairs,
+    so the SVD's fraction is an FP64-equivalent rate there."""
     sec = d["ms"] * 1e-3
     out = {"kernel": name, "launch_ms": d["ms"] / max(d["launches"], 1), "traffic": traffic_for(name, prec)}
     mixed = prec != "fp64"
@@ -177,8 +179,11 @@ def class_roofline(name: str, d: dict, prec: str, pk: dict):
                     "peak_source": f"{pk['src']} copy bandwidth"})
     else:
         achieved = d["flops"] / sec / 1e9 if sec > 0 else 0.0
+        src = "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"
+        if name == "svd" and prec in ("bf16x3", "tf32x3"):
+            src += " (R-SVD flops at FP64 accuracy; the large sectors' final Jacobi runs in FP32 pairs)"
         out.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK, "unit": "GFLOP/s",
-                    "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"})
+                    "peak_source": src})
     out["frac"] = out["achieved"] / out["peak"]
     keys = ["bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "launch_ms", "peak_source"]
     if "products_per_flop" in out:
@@ -966,7 +971,9 @@ def main():
                              + f"{max(args.warmup, 3)} warm-up steps, timed n = {first['n']}..{last['n']}, "
                              f"kept {int(min(last['kept']))}..{int(max(last['kept']))}, last max fidelity error "
                              f"{float(np.max(last['fidelity'])):.2e}, max eps {float(np.max(last['eps'])):.2e}",
-                   "precision": args.prec + ("" if args.prec == "fp64" else " H_eff psi; FP64 Lanczos and SVD"),
+                   "precision": args.prec + ("" if args.prec == "fp64" else " H_eff psi; FP64 Lanczos and SVD"
+                                             + ("; final Jacobi of sectors beyond 320 columns in FP32 pairs "
+                                                "(48 bits)" if args.prec in ("tf32x3", "bf16x3") else "")),
                    "fp64_restart_matvecs": "BF16 digit slices on the tensor cores (FP64-accurate)"
                    if args.prec in ("tf32x3", "bf16x3") else None,
                    "parallelism": f"{world} independent replica(s), one per GPU",

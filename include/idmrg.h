@@ -404,9 +404,6 @@ idmrg_status idmrg_profile_enable(idmrg_ctx *ctx, int on);
 idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t *launches, double *flops,
                                 double *bytes);
 
-/* Shape of the last truncation's SVD work (Step 4): sector matrices, their
- * largest short side, largest numerical rank, and the Jacobi sweeps taken
- * (maximum and mean over the sectors). */
 /* Sector SVDs of the following truncations on the kernels for large sector
  * matrices only (global_only = 1: pivoted QR on thread-block clusters with
  * the columns in global memory, FP32 and FP64 cyclic Jacobi in global
@@ -416,6 +413,21 @@ idmrg_status idmrg_profile_read(idmrg_ctx *ctx, int kclass, double *ms, uint64_t
  * large-sector path on small problems. */
 idmrg_status idmrg_set_svd_path(idmrg_ctx *ctx, int global_only);
 
+/* Arithmetic of the final (FP64-accuracy) one-sided Jacobi of the sector
+ * SVDs of Step 4 on the large-sector path (sectors beyond 320 columns, or
+ * every sector under idmrg_set_svd_path(ctx, 1)): mode 1 = FP64 on the FP64
+ * units; mode 2 = pairs of FP32 numbers (48 significant bits: exact
+ * products by FMA, exact sums by two-sum) for the dot products and column
+ * rotations, FP64 for column norms, scales and rotation scalars -- GB300
+ * issues 64 FP32 FMAs per FP64 FMA; the singular values then agree with the
+ * FP64 ones to about 1e-13 relative; mode 0 (the default) = mode 2 for the
+ * mixed precisions (TF32X3, BF16X3), mode 1 for FP64 and FP64_TC.  Takes
+ * effect at the next truncation; EINVAL for another mode. */
+idmrg_status idmrg_set_jacobi_arithmetic(idmrg_ctx *ctx, int mode);
+
+/* Shape of the last truncation's SVD work (Step 4): sector matrices, their
+ * largest short side, largest numerical rank, and the Jacobi sweeps taken
+ * (maximum and mean over the sectors). */
 idmrg_status idmrg_svd_stats(const idmrg_ctx *ctx, int *jobs, int *max_cols, int *max_rank, int *max_sweeps,
                              double *mean_sweeps);
 

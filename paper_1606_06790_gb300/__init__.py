@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "idmrg_truncate", "idmrg_get_lambda", "idmrg_update_environments", "idmrg_advance",
     "idmrg_unit_cell_step", "idmrg_batch_step", "idmrg_run", "idmrg_truncation_error", "idmrg_energy_per_site", "idmrg_heff_cost", "idmrg_launch_count",
     "idmrg_profile_enable", "idmrg_profile_read", "idmrg_transfer_bytes", "idmrg_heff_apply_noalloc",
-    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_create_batch", "idmrg_ring_energy", "idmrg_set_mixed_restart", "idmrg_svd_phase_ms", "idmrg_svd_sweeps32", "idmrg_save", "idmrg_load",
+    "idmrg_svd_stats", "idmrg_set_svd_path", "idmrg_set_jacobi_arithmetic", "idmrg_gemm_tuning", "idmrg_set_gemm_tile", "idmrg_create_batch", "idmrg_ring_energy", "idmrg_set_mixed_restart", "idmrg_svd_phase_ms", "idmrg_svd_sweeps32", "idmrg_save", "idmrg_load",
     "idmrg_correlation", "idmrg_transfer_spectrum", "idmrg_delta_pm", "idmrg_extrapolate",
     "idmrg_fit_correlation_length", "idmrg_set_pair_range", "idmrg_export_pair", "idmrg_import_pair",
 ]
@@ -124,6 +124,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "idmrg_load": (i, [vp, C.c_char_p]),
         "idmrg_svd_stats": (i, [vp, P(i), P(i), P(i), P(i), P(d)]),
         "idmrg_set_svd_path": (i, [vp, i]),
+        "idmrg_set_jacobi_arithmetic": (i, [vp, i]),
         "idmrg_gemm_tuning": (i, [vp, i, P(i), P(C.c_float), P(i)]),
         "idmrg_set_gemm_tile": (i, [vp, i, i]),
         "idmrg_create_batch": (i, [P(_MPO), i, P(i), P(_Opts), vp, P(_Allocator), P(vp)]),
@@ -507,6 +508,14 @@ class Context:
     def set_svd_path(self, global_only: bool) -> None:
         """Sector SVDs on the large-sector (global-memory) kernels only."""
         self._check(self.lib.idmrg_set_svd_path(self.h, int(bool(global_only))), "set_svd_path")
+
+    JACOBI_ARITHMETIC = {"auto": 0, "fp64": 1, "pairs": 2}
+
+    def set_jacobi_arithmetic(self, mode: str) -> None:
+        """Arithmetic of the final Jacobi of large sectors: "fp64", "pairs"
+        (FP32 pairs) or "auto" (pairs for the mixed precisions)."""
+        self._check(self.lib.idmrg_set_jacobi_arithmetic(self.h, self.JACOBI_ARITHMETIC[mode]),
+                    "set_jacobi_arithmetic")
 
     def svd_stats(self) -> Dict[str, float]:
         j, mc, mr, ms, me = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_double()

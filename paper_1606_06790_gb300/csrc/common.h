@@ -225,9 +225,10 @@ cudaError_t launch_svd_qrcp_grouped(const SvdJob *jobs, const int *order, int nj
 // Jacobi groups and shared memory: see kernels_svd.cu
 constexpr size_t SVD_BLOCK_SMEM_MAX = 200 * 1024;
 size_t svd_block_smem(int cols, int csize);
+// pairs: the FP64 stage of group 0 in FP32-pair arithmetic (48 bits)
 cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                              double *work, int *iwork, double *sv, int *err, int jm_init, cudaStream_t st,
-                              const cudaStream_t *side, const cudaEvent_t *ev);
+                              double *work, int *iwork, double *sv, int *err, int jm_init, bool pairs,
+                              cudaStream_t st, const cudaStream_t *side, const cudaEvent_t *ev);
 // FP32 Jacobi on every group (group 0, the sectors beyond the block kernels,
 // with cols0 columns at most, on the large-sector kernels; its jobs from g0b
 // on, of at most cols0b columns, fit the shared-memory tournament): writes

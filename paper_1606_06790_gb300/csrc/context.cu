@@ -224,9 +224,14 @@ struct idmrg_ctx {
   bool mixed = false;
   int bf16 = 0;  // mixed with BF16 splits (64 K per packed block) instead of TF32 (32)
   bool svd_global = false;  // sector SVDs on the global-memory Jacobi kernels only
+  int jac_arith = 0;        // final Jacobi of large sectors: 0 by precision, 1 FP64, 2 FP32 pairs
   bool o_oz = true;    // FP64 matvecs from digit slices (mixed restarts, FP64_TC)
   bool fp64tc = false; // IDMRG_FP64_TC: every matvec from digit slices, one Lanczos run
   bool oz_active() const { return oz_ok && o_oz && (mixed || fp64tc); }
+  // FP32-pair arithmetic for the final Jacobi of large sectors: by default
+  // with the mixed precisions, whose H_eff psi is far less accurate anyway;
+  // FP64 and FP64_TC keep the FP64 units
+  bool jac_pairs() const { return jac_arith == 2 || (jac_arith == 0 && mixed); }
   // the other FP64 GEMM lists (environments, prediction, SVD) in digit slices
   bool oz_lists() const { return o_oz && (mixed || fp64tc); }
   // split-operand GEMM lists: the L split (once per iteration) and, for
@@ -2431,7 +2436,7 @@ idmrg_status truncate(idmrg_ctx *c, int p) {
   c->kend(PH + 2);
   c->kbegin(PH + 3);
   CK(launch_svd_jacobi(dj, (const int *)c->sorder.p, nj, g, gcols, sw, (int *)c->siw.p, c->dp(c->ssv),
-                       (int *)c->derr.p, 1, c->st, c->side, c->sev));
+                       (int *)c->derr.p, 1, c->jac_pairs(), c->st, c->side, c->sev));
   c->kend(PH + 3);
   c->launches += 12;
   // select: one launch, one CTA per superblock (no jobs: nothing kept)
@@ -4341,6 +4346,13 @@ idmrg_status idmrg_svd_phase_ms(idmrg_ctx *c, double *ms) {
 idmrg_status idmrg_set_svd_path(idmrg_ctx *c, int global_only) {
   if (!c) return IDMRG_EINVAL;
   c->svd_global = global_only != 0;
+  return IDMRG_OK;
+}
+
+idmrg_status idmrg_set_jacobi_arithmetic(idmrg_ctx *c, int mode) {
+  if (!c) return IDMRG_EINVAL;
+  if (mode < 0 || mode > 2) return c->fail(IDMRG_EINVAL, "set_jacobi_arithmetic: mode %d is not 0, 1 or 2", mode);
+  c->jac_arith = mode;
   return IDMRG_OK;
 }
 

@@ -1286,6 +1286,67 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
     for (int j = n + (int)threadIdx.x; j < Jb.cols_a; j += blockDim.x) sv[Jb.sv_off + j] = 0.0;
 }
 
+// Element arithmetic of the FP64 stage below in pairs of FP32 numbers
+// (x = h + l, |l| <= ulp(h) / 2: 48 significant bits), for GB300, whose
+// SMs issue 64 FP32 FMAs per FP64 FMA.  The products are exact by FMA
+// (Dekker's two-product), the sums by Knuth's two-sum; the explicit _rn
+// intrinsics keep the compiler from contracting them.  The dot products and
+// rotations of the sweeps run in this arithmetic; column norms, scales and
+// the rotation scalars stay in FP64.
+struct __align__(8) DF2 {
+  float h, l;
+};
+__device__ __forceinline__ DF2 df_of(double x) {
+  DF2 r;
+  r.h = __double2float_rn(x);
+  r.l = __double2float_rn(x - (double)r.h);
+  return r;
+}
+__device__ __forceinline__ double df_to(DF2 x) { return (double)x.h + (double)x.l; }
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (sh, sl) += a b, the accumulator left unnormalised (|sl| grows by at most
+// one ulp of sh per term; it is folded in by df_wsum)
+__device__ __forceinline__ void df_dot_acc(DF2 a, DF2 b, float &sh, float &sl) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  float s, t;
+  two_sum(sh, p, s, t);
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+  sh = s;
+}
+// u + c v, renormalised
+__device__ __forceinline__ DF2 df_axpy(DF2 c, DF2 v, DF2 u) {
+  const float p = __fmul_rn(c.h, v.h);
+  float e = __fmaf_rn(c.h, v.h, -p);
+  e = __fmaf_rn(c.h, v.l, e);
+  e = __fmaf_rn(c.l, v.h, e);
+  float s, t;
+  two_sum(u.h, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(u.l, e));
+  DF2 r;
+  r.h = __fadd_rn(s, t);
+  r.l = __fsub_rn(t, __fsub_rn(r.h, s));
+  return r;
+}
+// warp sum of pair accumulators; every lane gets the same value (each
+// butterfly step adds the same two pairs on both partners)
+__device__ __forceinline__ double df_wsum(float h, float l) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum(h, oh, s, e);
+    l = __fadd_rn(__fadd_rn(l, ol), e);
+    h = s;
+  }
+  return (double)h + (double)l;
+}
+
 // FP64 stage for sectors beyond the block kernels: the cyclic tournament of
 // jacobi_kernel (columns in global memory, one pair per warp, rounds
 // separated by the cluster barrier) with the scaled rotations and tracked
@@ -1293,7 +1354,13 @@ __global__ void __launch_bounds__(BJ_THREADS, 2)
 // FMA per element and column instead of three dot products and two
 // operations.  Column scales and squared norms live in the job's w_off area
 // (free once B holds X); every sweep starts by folding the scales back into
-// the columns and recomputing their norms.
+// the columns and recomputing their norms (in FP64).  PAIRS: B and the
+// rotations are held as FP32 pairs (in place, 8 bytes an element as before)
+// from the first sweep to the last, dot products and rotations run in pair
+// arithmetic, and a rotation is applied when its relative overlap exceeds
+// sqrt(rows) 2^-48 instead of sqrt(rows) 2^-52; the convergence test (all
+// rotations of a sweep below 1e-9) is the same.
+template <bool PAIRS>
 __global__ void __launch_bounds__(JAC_THREADS, 1)
     jacobi_scaled_kernel(const SvdJob *__restrict__ jobs, const int *__restrict__ order, double *__restrict__ work,
                          int *__restrict__ iwork, double *__restrict__ sv, int *err, int jm_init) {
@@ -1305,6 +1372,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
   const int n = iwork[Jb.perm_off + Jb.cols_a];   // columns of B: numerical rank
   double *B = work + Jb.b_off;
   double *Jm = work + Jb.j_off;
+  DF2 *Bp = reinterpret_cast<DF2 *>(B);           // the same memory as pairs (PAIRS)
+  DF2 *Jp = reinterpret_cast<DF2 *>(Jm);
   double *dsc = work + Jb.w_off, *nrm = dsc + n;  // scale d_j and squared norm of column j
   __shared__ double fro_part[JAC_MAX_CLUSTER];
   __shared__ double wred[JAC_THREADS / 32];
@@ -1325,7 +1394,13 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
   }
   for (int64_t e = e0; e < n; e += stride) dsc[e] = 1.0;
   double fro = 0.0;
-  for (int64_t e = e0; e < nb; e += stride) fro = fma(B[e], B[e], fro);
+  for (int64_t e = e0; e < nb; e += stride) {
+    const double v = B[e];
+    fro = fma(v, v, fro);
+    if (PAIRS) Bp[e] = df_of(v);  // each element is read and rewritten by the same thread
+  }
+  if (PAIRS)
+    for (int64_t e = e0; e < nn; e += stride) Jp[e] = df_of(Jm[e]);
   fro = wsum(fro);
   if (lane == 0) wred[warp] = fro;
   __syncthreads();
@@ -1339,7 +1414,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
   fro = 0.0;
   for (int q = 0; q < csize; ++q) fro += fp0[q];
   cluster.sync();
-  const float log2_tol2 = __log2f((float)nr) - 104.0f;  // log2(nr eps^2), eps = 2^-52
+  // log2(nr eps^2), eps = 2^-52 (FP64) or 2^-48 (pairs)
+  const float log2_tol2 = __log2f((float)nr) - (PAIRS ? 96.0f : 104.0f);
   const Split floor_split = split_f64(4.0 * DBL_EPSILON * DBL_EPSILON * fro);
   const int small_key = (int)(64.0f * -59.8f);        // 64 log2(1e-18): see jacobi_block_kernel
   const int np = n + (n & 1);
@@ -1348,15 +1424,26 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
   // scales into the columns, exact squared norms
   auto fold = [&]() {
     for (int j = gw; j < n; j += gnw) {
-      double *bj = B + (int64_t)j * nr, *jj = Jm + (int64_t)j * n;
       const double d = dsc[j];
       double s = 0.0;
-      for (int i = lane; i < nr; i += 32) {
-        const double v = bj[i] * d;
-        bj[i] = v;
-        s = fma(v, v, s);
+      if (PAIRS) {
+        DF2 *bj = Bp + (int64_t)j * nr, *jj = Jp + (int64_t)j * n;
+        for (int i = lane; i < nr; i += 32) {
+          const double v = df_to(bj[i]) * d;
+          bj[i] = df_of(v);
+          s = fma(v, v, s);
+        }
+        if (d != 1.0)
+          for (int i = lane; i < n; i += 32) jj[i] = df_of(df_to(jj[i]) * d);
+      } else {
+        double *bj = B + (int64_t)j * nr, *jj = Jm + (int64_t)j * n;
+        for (int i = lane; i < nr; i += 32) {
+          const double v = bj[i] * d;
+          bj[i] = v;
+          s = fma(v, v, s);
+        }
+        for (int i = lane; i < n; i += 32) jj[i] *= d;
       }
-      for (int i = lane; i < n; i += 32) jj[i] *= d;
       s = wsum(s);
       __syncwarp();
       if (lane == 0) {
@@ -1386,22 +1473,40 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
         const int p = i1 == 0 ? 0 : 1 + (i1 - 1 + rnd) % (np - 1);
         const int q = i2 == 0 ? 0 : 1 + (i2 - 1 + rnd) % (np - 1);
         if (p >= n || q >= n) continue;
-        double *xp = B + (int64_t)p * nr, *xq = B + (int64_t)q * nr;
-        double ga = 0.0;
-        // loads in batches of J64_BATCH per lane, two batches issued before
-        // their FMAs; each lane still adds its elements in index order
-        for (int i0 = 0; i0 < nr; i0 += 64 * J64_BATCH) {
-          double u[2 * J64_BATCH], v[2 * J64_BATCH];
+        double ga;
+        if (PAIRS) {
+          const DF2 *xp = Bp + (int64_t)p * nr, *xq = Bp + (int64_t)q * nr;
+          float sh = 0.0f, sl = 0.0f;
+          for (int i0 = 0; i0 < nr; i0 += 64 * J64_BATCH) {
+            DF2 u[2 * J64_BATCH], v[2 * J64_BATCH];
 #pragma unroll
-          for (int r = 0; r < 2 * J64_BATCH; ++r) {
-            const int i = i0 + lane + 32 * r;
-            u[r] = i < nr ? xp[i] : 0.0;
-            v[r] = i < nr ? xq[i] : 0.0;
+            for (int r = 0; r < 2 * J64_BATCH; ++r) {
+              const int i = i0 + lane + 32 * r;
+              u[r] = i < nr ? xp[i] : DF2{0.0f, 0.0f};
+              v[r] = i < nr ? xq[i] : DF2{0.0f, 0.0f};
+            }
+#pragma unroll
+            for (int r = 0; r < 2 * J64_BATCH; ++r) df_dot_acc(u[r], v[r], sh, sl);
           }
+          ga = df_wsum(sh, sl);
+        } else {
+          const double *xp = B + (int64_t)p * nr, *xq = B + (int64_t)q * nr;
+          ga = 0.0;
+          // loads in batches of J64_BATCH per lane, two batches issued before
+          // their FMAs; each lane still adds its elements in index order
+          for (int i0 = 0; i0 < nr; i0 += 64 * J64_BATCH) {
+            double u[2 * J64_BATCH], v[2 * J64_BATCH];
 #pragma unroll
-          for (int r = 0; r < 2 * J64_BATCH; ++r) ga = fma(u[r], v[r], ga);
+            for (int r = 0; r < 2 * J64_BATCH; ++r) {
+              const int i = i0 + lane + 32 * r;
+              u[r] = i < nr ? xp[i] : 0.0;
+              v[r] = i < nr ? xq[i] : 0.0;
+            }
+#pragma unroll
+            for (int r = 0; r < 2 * J64_BATCH; ++r) ga = fma(u[r], v[r], ga);
+          }
+          ga = wsum(ga);
         }
-        ga = wsum(ga);
         double cp = 0.0, cq = 0.0;
         int rot = 0;
         if (lane == 0) {
@@ -1424,42 +1529,82 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
         // B's and Jm's pair of columns in one pass (n <= nr): the four
         // columns' loads of a batch are issued together
         double np2 = 0.0, nq2 = 0.0;
-        double *jp = Jm + (int64_t)p * n, *jq = Jm + (int64_t)q * n;
-        for (int i0 = 0; i0 < nr; i0 += 32 * J64_BATCH) {
-          double u[J64_BATCH], v[J64_BATCH], y[J64_BATCH], z[J64_BATCH];
+        if (PAIRS) {
+          const DF2 cpp = df_of(cp), cqp = df_of(cq);
+          DF2 *xp = Bp + (int64_t)p * nr, *xq = Bp + (int64_t)q * nr;
+          DF2 *jp = Jp + (int64_t)p * n, *jq = Jp + (int64_t)q * n;
+          float ph = 0.0f, pl = 0.0f, qh = 0.0f, ql = 0.0f;
+          for (int i0 = 0; i0 < nr; i0 += 32 * J64_BATCH) {
+            DF2 u[J64_BATCH], v[J64_BATCH], y[J64_BATCH], z[J64_BATCH];
 #pragma unroll
-          for (int r = 0; r < J64_BATCH; ++r) {
-            const int i = i0 + lane + 32 * r;
-            u[r] = i < nr ? xp[i] : 0.0;
-            v[r] = i < nr ? xq[i] : 0.0;
-            y[r] = i < n ? jp[i] : 0.0;
-            z[r] = i < n ? jq[i] : 0.0;
-          }
+            for (int r = 0; r < J64_BATCH; ++r) {
+              const int i = i0 + lane + 32 * r;
+              u[r] = i < nr ? xp[i] : DF2{0.0f, 0.0f};
+              v[r] = i < nr ? xq[i] : DF2{0.0f, 0.0f};
+              y[r] = i < n ? jp[i] : DF2{0.0f, 0.0f};
+              z[r] = i < n ? jq[i] : DF2{0.0f, 0.0f};
+            }
 #pragma unroll
-          for (int r = 0; r < J64_BATCH; ++r) {
-            const int i = i0 + lane + 32 * r;
-            if (i < nr) {
-              const double u2 = fma(cp, v[r], u[r]), v2 = fma(cq, u[r], v[r]);
-              xp[i] = u2;
-              xq[i] = v2;
-              if (rot == 2) {
-                np2 = fma(u2, u2, np2);
-                nq2 = fma(v2, v2, nq2);
+            for (int r = 0; r < J64_BATCH; ++r) {
+              const int i = i0 + lane + 32 * r;
+              if (i < nr) {
+                const DF2 u2 = df_axpy(cpp, v[r], u[r]), v2 = df_axpy(cqp, u[r], v[r]);
+                xp[i] = u2;
+                xq[i] = v2;
+                if (rot == 2) {
+                  df_dot_acc(u2, u2, ph, pl);
+                  df_dot_acc(v2, v2, qh, ql);
+                }
+              }
+              if (i < n) {
+                jp[i] = df_axpy(cpp, z[r], y[r]);
+                jq[i] = df_axpy(cqp, y[r], z[r]);
               }
             }
-            if (i < n) {
-              jp[i] = fma(cp, z[r], y[r]);
-              jq[i] = fma(cq, y[r], z[r]);
+          }
+          if (rot == 2) {
+            np2 = df_wsum(ph, pl);
+            nq2 = df_wsum(qh, ql);
+          }
+        } else {
+          double *xp = B + (int64_t)p * nr, *xq = B + (int64_t)q * nr;
+          double *jp = Jm + (int64_t)p * n, *jq = Jm + (int64_t)q * n;
+          for (int i0 = 0; i0 < nr; i0 += 32 * J64_BATCH) {
+            double u[J64_BATCH], v[J64_BATCH], y[J64_BATCH], z[J64_BATCH];
+#pragma unroll
+            for (int r = 0; r < J64_BATCH; ++r) {
+              const int i = i0 + lane + 32 * r;
+              u[r] = i < nr ? xp[i] : 0.0;
+              v[r] = i < nr ? xq[i] : 0.0;
+              y[r] = i < n ? jp[i] : 0.0;
+              z[r] = i < n ? jq[i] : 0.0;
+            }
+#pragma unroll
+            for (int r = 0; r < J64_BATCH; ++r) {
+              const int i = i0 + lane + 32 * r;
+              if (i < nr) {
+                const double u2 = fma(cp, v[r], u[r]), v2 = fma(cq, u[r], v[r]);
+                xp[i] = u2;
+                xq[i] = v2;
+                if (rot == 2) {
+                  np2 = fma(u2, u2, np2);
+                  nq2 = fma(v2, v2, nq2);
+                }
+              }
+              if (i < n) {
+                jp[i] = fma(cp, z[r], y[r]);
+                jq[i] = fma(cq, y[r], z[r]);
+              }
             }
           }
-        }
-        if (rot == 2) {  // cancellation: norms from the rotated data
-          np2 = wsum(np2);
-          nq2 = wsum(nq2);
-          if (lane == 0) {
-            nrm[p] = dsc[p] * dsc[p] * np2;
-            nrm[q] = dsc[q] * dsc[q] * nq2;
+          if (rot == 2) {
+            np2 = wsum(np2);
+            nq2 = wsum(nq2);
           }
+        }
+        if (rot == 2 && lane == 0) {  // cancellation: norms from the rotated data
+          nrm[p] = dsc[p] * dsc[p] * np2;
+          nrm[q] = dsc[q] * dsc[q] * nq2;
         }
       }
       cluster.sync();
@@ -1477,6 +1622,10 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
   fold();
   if (!converged && crank == 0 && threadIdx.x == 0) atomicOr(err, IDMRG_DEV_ERR_JACOBI);
   if (crank == 0 && threadIdx.x == 0) iwork[Jb.perm_off + Jb.cols_a + 1] = sweep;
+  // the rotations back to FP64 (fold ended with the cluster barrier, so every
+  // pair is final; each element is read and rewritten by the same thread)
+  if (PAIRS)
+    for (int64_t e = e0; e < nn; e += stride) Jm[e] = df_to(Jp[e]);
   for (int j = gw; j < Jb.cols_a; j += gnw) {
     if (j >= n) {
       if (lane == 0) sv[Jb.sv_off + j] = 0.0;
@@ -1486,7 +1635,12 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
     const double s = sqrt(nrm[j]);
     if (lane == 0) sv[Jb.sv_off + j] = s;
     const double inv = s > 0.0 ? 1.0 / s : 0.0;
-    for (int i = lane; i < nr; i += 32) bj[i] *= inv;
+    if (PAIRS) {
+      const DF2 *bp = Bp + (int64_t)j * nr;
+      for (int i = lane; i < nr; i += 32) bj[i] = df_to(bp[i]) * inv;
+    } else {
+      for (int i = lane; i < nr; i += 32) bj[i] *= inv;
+    }
   }
 }
 
@@ -2317,7 +2471,7 @@ cudaError_t launch_svd_qrcp(const SvdJob *jobs, const int *order, int njobs, dou
 
 static cudaError_t launch_jacobi_scaled_clusters(const SvdJob *jobs, const int *order, int njobs, int csize,
                                                  double *work, int *iwork, double *sv, int *err, int jm_init,
-                                                 cudaStream_t st) {
+                                                 bool pairs, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * csize, 1, 1);
   cfg.blockDim = dim3(JAC_THREADS, 1, 1);
@@ -2330,7 +2484,9 @@ static cudaError_t launch_jacobi_scaled_clusters(const SvdJob *jobs, const int *
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, jacobi_scaled_kernel, jobs, order, work, iwork, sv, err, jm_init);
+  void (*kern)(const SvdJob *, const int *, double *, int *, double *, int *, int) =
+      pairs ? jacobi_scaled_kernel<true> : jacobi_scaled_kernel<false>;
+  return cudaLaunchKernelEx(&cfg, kern, jobs, order, work, iwork, sv, err, jm_init);
 }
 
 static cudaError_t launch_jacobi_clusters(const SvdJob *jobs, const int *order, int njobs, int csize, double *work,
@@ -2407,10 +2563,10 @@ static cudaError_t launch_block_clusters(const SvdJob *jobs, const int *order, i
 // 1..4 block Jacobi on clusters of 16, 8, 4 and 1 CTAs; cols[k-1] is the
 // largest column count of block group k.  Groups 0 and 1 run on `st`, the others on the side
 // streams side[0..2], forked from and joined back to `st` by the events
-// ev[0..3].
+// ev[0..3].  pairs: group 0 in FP32-pair arithmetic (jacobi_scaled_kernel).
 cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, const int *g, const int *cols,
-                              double *work, int *iwork, double *sv, int *err, int jm_init, cudaStream_t st,
-                              const cudaStream_t *side, const cudaEvent_t *ev) {
+                              double *work, int *iwork, double *sv, int *err, int jm_init, bool pairs,
+                              cudaStream_t st, const cudaStream_t *side, const cudaEvent_t *ev) {
   if (njobs <= 0) return cudaGetLastError();
   cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(jacobi_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -2433,11 +2589,12 @@ cudaError_t launch_svd_jacobi(const SvdJob *jobs, const int *order, int njobs, c
     if (e != cudaSuccess) return e;
   }
   if (hi[0] > lo[0]) {
-    cudaFuncSetAttribute(jacobi_scaled_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    e = launch_jacobi_scaled_clusters(jobs, order, hi[0], 16, work, iwork, sv, err, jm_init, st);
+    cudaFuncSetAttribute(jacobi_scaled_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(jacobi_scaled_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = launch_jacobi_scaled_clusters(jobs, order, hi[0], 16, work, iwork, sv, err, jm_init, pairs, st);
     if (e != cudaSuccess) {
       cudaGetLastError();  // 16-CTA clusters not available here: fall back to 8
-      e = launch_jacobi_scaled_clusters(jobs, order, hi[0], 8, work, iwork, sv, err, jm_init, st);
+      e = launch_jacobi_scaled_clusters(jobs, order, hi[0], 8, work, iwork, sv, err, jm_init, pairs, st);
     }
     if (e != cudaSuccess) return e;
   }

@@ -114,8 +114,9 @@ def test_einval_invalid_mpo(flaw):
 
 
 def test_settings_and_instrumentation():
-    """The restart rule, the tile setting and the SVD instrumentation through
-    the C ABI: invalid arguments are EINVAL, the reports are consistent."""
+    """The restart rule, the tile setting, the Jacobi arithmetic and the SVD
+    instrumentation through the C ABI: invalid arguments are EINVAL, the
+    reports are consistent."""
     import paper_1606_06790_gb300 as pkg
     mpo = _mpo()
     ctx = context(mpo, 16, prec="bf16x3")
@@ -126,6 +127,8 @@ def test_settings_and_instrumentation():
     with pytest.raises(pkg.IdmrgError) as ei:
         ctx.set_gemm_tile(96, 0)
     assert ei.value.status == 1
+    for bad in (-1, 3):
+        assert ctx.lib.idmrg_set_jacobi_arithmetic(ctx.h, bad) == 1
     ctx.set_mixed_restart(1e-2, 40)
     ctx.profile_enable(True)
     for _ in range(4):

@@ -56,19 +56,26 @@ def test_full_iteration_parity(name, bonds, ell, m, steps, prec):
     ctx.close()
 
 
-def test_large_sector_svd_path():
+@pytest.mark.parametrize("arith", ["fp64", "pairs"])
+def test_large_sector_svd_path(arith):
     """The kernels for sector matrices beyond the shared-memory ones (pivoted
     QR on a cluster with the columns in global memory, the FP32 block
-    tournament streamed through shared memory, the FP64 cyclic Jacobi in
+    tournament streamed through shared memory, the final cyclic Jacobi in
     global memory started from the Newton-Schulz-orthogonalised FP32
-    rotations), forced on a small problem, against the oracle."""
+    rotations, in FP64 or in FP32-pair arithmetic), forced on a small
+    problem, against the oracle: the step reports at 1e-10 per site and the
+    lambda spectra at 1e-10 every step."""
     mpo = build_mpo(random_chain_bonds(8, 0.5, 1.5, 1606), 8)
     ctx = context(mpo, 48)
     ctx.set_svd_path(True)
+    ctx.set_jacobi_arithmetic(arith)
     ref = ParallelIDMRG.from_mpo(mpo, m=48)
     for _ in range(14):
         _compare(ctx.unit_cell_step(), ref.step())
-    assert ctx.svd_stats()["max_sweeps"] <= 6  # FP32-preconditioned FP64 sweeps
+        for p in range(ctx.P):
+            lg, lr = ctx.get_lambda(p), ref.prev[p].lam_all
+            assert len(lg) == len(lr) and np.max(np.abs(lg - lr)) < 1e-10
+    assert ctx.svd_stats()["max_sweeps"] <= 6  # FP32-preconditioned final sweeps
     ctx.close()
 
 
