@@ -1669,7 +1669,8 @@ idmrg_status check_dev_err(idmrg_ctx *c) {
   if (e & IDMRG_DEV_ERR_NUMERIC) return c->fail(IDMRG_ENUMERIC, "non-finite Lanczos coefficient (n=%d)", c->n);
   if (e & IDMRG_DEV_ERR_ZERONORM)
     return c->fail(IDMRG_ENUMERIC, "start vector with zero norm (n=%d, superblock mask 0x%x)", c->n, e >> 4);
-  if (e & IDMRG_DEV_ERR_JACOBI) return c->fail(IDMRG_ENUMERIC, "SVD sweeps exhausted (n=%d)", c->n);
+  if (e & IDMRG_DEV_ERR_JACOBI)
+    return c->fail(IDMRG_ENUMERIC, "SVD: sweeps exhausted, or a rotation beyond FP32-pair range (n=%d)", c->n);
   return IDMRG_OK;
 }
 

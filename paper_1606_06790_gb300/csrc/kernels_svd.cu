@@ -1519,6 +1519,11 @@ __global__ void __launch_bounds__(JAC_THREADS, 1)
             dsc[p] = d1;
             dsc[q] = d2;
             atomicMax(&sweep_lmax, (int)(lr * 64.0f));
+            // a coefficient of 2^101 or more (or not finite) has no FP32
+            // pair: report it (exponent bits, no FP64 instruction)
+            if (PAIRS && (((__double2hiint(cp) >> 20) & 0x7ff) > 1023 + 100 ||
+                          ((__double2hiint(cq) >> 20) & 0x7ff) > 1023 + 100))
+              atomicOr(err, IDMRG_DEV_ERR_JACOBI);
           }
         }
         rot = __shfl_sync(0xffffffffu, rot, 0);
