@@ -55,6 +55,12 @@ SETTLE_RATIO = 10.0      # max_i fidelity error <= SETTLE_RATIO max_i eps (+ 1e-
 SETTLE_RUN = 3           # ... on this many consecutive steps
 SETTLE_MAX_N = 90        # or until this iteration
 PAPER_LANCZOS_ITERS = 40  # Sec. 4: about 40 Lanczos iterations per solve with the prediction
+# Lanczos matvecs per solve of the FP64 path in the settled window at a
+# workload's own m (the bench's FP64 leg at n = 59 on the kagome cylinder,
+# m = 2048: 111-115, mean 113.2).  The reference arm's step model takes it,
+# so that it prices the same work as cpu_baseline, which reads the count of
+# the FP64 leg of the same run; workloads without one take the paper's count.
+SETTLED_FP64_ITERS = {"kagome_yc8_l12_m2048": 113.2}
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 HBM_FALLBACK, BF16_FALLBACK, BF16_SUST_FALLBACK = 6800.0, 1900.0, 1700.0
 FP64_ALU_PEAK = 152 * 2070e6 * 4 / 1e9   # GFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
@@ -539,9 +545,9 @@ def run_reference(args):
     workload, each step a bounded sample: one dense H_eff psi of a saturated
     superblock (D = m, the MPO channels of superblock 0) timed per step, the
     start vector, truncation and block updates timed once in the warm-up; a
-    unit-cell step is l/2 superblocks x (PAPER_LANCZOS_ITERS matvecs + the
-    rest).  The oracle is dense, so synthetic blocks of the saturated shape
-    cost what the real ones do."""
+    unit-cell step is l/2 superblocks x (SETTLED_FP64_ITERS, else
+    PAPER_LANCZOS_ITERS, matvecs + the rest).  The oracle is dense, so
+    synthetic blocks of the saturated shape cost what the real ones do."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -559,6 +565,10 @@ def run_reference(args):
     L, W1, W2, R, x = synthetic_superblock(mpo, m, g)
     w1, w2 = L.op.shape[0], R.op.shape[0]
     t_tr, t_up = synthetic_rest(mpo, L, W1, W2, R, x, m)
+    measured = m == WORKLOADS[name]["m"] and name in SETTLED_FP64_ITERS
+    iters = SETTLED_FP64_ITERS[name] if measured else float(PAPER_LANCZOS_ITERS)
+    why = ("the FP64 path's mean count in the settled window at this m" if measured
+           else "the paper's count with the prediction")
     for _ in range(args.warmup):
         heff_apply(L, W1, W2, R, x)
     samples = []
@@ -567,13 +577,13 @@ def run_reference(args):
         heff_apply(L, W1, W2, R, x)
         t_mv = time.perf_counter() - t
         samples.append(step_estimate(P, {"start": 0.0, "matvec": t_mv, "truncate": t_tr, "update": t_up},
-                                     PAPER_LANCZOS_ITERS))
+                                     iters))
     per = sum(samples) / len(samples)
     v = 1.0 / per
     cores = len(os.sched_getaffinity(0))
     sample = (f"per step: one dense FP64 H_eff psi of superblock 0 at D={m} (w={w1},{w2}) timed; truncation "
               f"({t_tr:.2f} s) and block updates ({t_up:.2f} s) timed once; step = {P} superblocks x "
-              f"({PAPER_LANCZOS_ITERS} matvecs, the paper's count with the prediction, + the rest)")
+              f"({iters:.1f} matvecs, {why}, + the rest)")
     line = {"metric": METRIC, "value": v, "unit": "unit-cell steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
