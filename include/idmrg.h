@@ -49,8 +49,10 @@ typedef enum {
 } idmrg_status;
 
 /* Arithmetic of the H_eff psi and environment contractions.  The Lanczos
- * recurrence, re-orthogonalisation, tridiagonal eigensolve and the SVD are
- * FP64 in every mode. */
+ * recurrence, re-orthogonalisation and tridiagonal eigensolve are FP64 in
+ * every mode, and the SVD is FP64-accurate in every mode: it preconditions
+ * in FP32 and finishes with FP64 sweeps, whose element arithmetic on large
+ * sectors is FP32 pairs in TF32X3 and BF16X3 (idmrg_set_jacobi_arithmetic). */
 typedef enum {
   IDMRG_FP64 = 0,    /* FP64 everywhere                                       */
   IDMRG_TF32X3 = 1,  /* tensor cores, TF32 split (hi/lo) operands, three
@@ -221,7 +223,8 @@ idmrg_status idmrg_lanczos_solve(idmrg_ctx *ctx, int p, double *e_out, int *iter
 /* Copies the Lanczos ground state of superblock p to host (layout as above). */
 idmrg_status idmrg_get_psi(const idmrg_ctx *ctx, int p, double *host, size_t cap);
 
-/* Step 4 + truncation of Step 6: FP64 SVD per charge sector, descending
+/* Step 4 + truncation of Step 6: FP64-accurate SVD per charge sector (the
+ * arithmetic is described at idmrg_precision), descending
  * singular values, cut at <= m without splitting near-equal values.  Host
  * outputs (one or l/2 entries, each may be NULL): eps (Eq. tru), eps_best
  * (Eq. fid2), states kept. */
