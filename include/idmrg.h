@@ -369,8 +369,9 @@ idmrg_status idmrg_ring_energy(const idmrg_ctx *ctx, int r, double *e_g, int *n_
  * target charge (checked: EINVAL otherwise), which then continues exactly as
  * the saved one would when its other options are the same too.  Every
  * precision keeps this state in FP64, so a state saved under one precision
- * loads into a context of another (the file records the saving one).  Both synchronise the context's stream; ESTATE while a step is in
- * progress; EINVAL on I/O errors or a damaged file. */
+ * loads into a context of another (the file records the saving one).  Both
+ * synchronise the context's stream; ESTATE while a step is in progress;
+ * EINVAL on I/O errors or a damaged file. */
 idmrg_status idmrg_save(const idmrg_ctx *ctx, const char *path);
 idmrg_status idmrg_load(idmrg_ctx *ctx, const char *path);
 
